@@ -1,0 +1,164 @@
+"""Element library of the oracle: Lagrange hexahedra of degree k = 1..3.
+
+Section 2.1 (finite element types): rectangular prismatic elements, three
+displacement DOFs per node, Lagrange elements with (k+1)^3 nodes.
+Section 3.3 (assembly, Eq. matrixK_mr): a displacement element split into
+n^3 density elements ("subcells"); the subcell matrices
+    K^(e_i) = int_{Omega_{e_i}} B^T D B dOmega
+are computed once for a regular mesh and K^(e) = sum_i w_i K^(e_i).
+
+Conventions (shared with the C ABI by documentation only, not by code):
+  * reference element [-1,1]^3, physical cube of edge h, so x = h/2 * xi;
+  * local nodes on the equispaced (k+1)^3 lattice, index ix + (k+1)*(iy +
+    (k+1)*iz), xi_ix = -1 + 2*ix/k;
+  * element DOF 3*a + c for local node a and component c;
+  * subcell (a, b, c) in 0..n-1 per axis has index a + n*(b + n*c) and covers
+    xi in [-1 + 2a/n, -1 + 2(a+1)/n] (same for eta, zeta);
+  * Voigt strain order (xx, yy, zz, xy, yz, zx) with engineering shears.
+"""
+from __future__ import annotations
+
+import numpy as np
+from numpy.polynomial import polynomial as npoly
+from numpy.polynomial import legendre as nleg
+
+
+def lagrange_1d(k: int):
+    """Coefficients of the equispaced 1D Lagrange basis on [-1, 1].
+
+    Returns (nodes, C, dC) with N_j(xi) = sum_p C[j, p] xi^p and
+    N_j'(xi) = sum_p dC[j, p] xi^p.
+    """
+    nodes = np.linspace(-1.0, 1.0, k + 1)
+    C = np.zeros((k + 1, k + 1))
+    dC = np.zeros((k + 1, k + 1))
+    for j in range(k + 1):
+        others = np.delete(nodes, j)
+        c = npoly.polyfromroots(others)  # prod (xi - xi_m)
+        c = c / npoly.polyval(nodes[j], c)
+        C[j, : len(c)] = c
+        d = npoly.polyder(c)
+        dC[j, : len(d)] = d
+    return nodes, C, dC
+
+
+def shape_1d(k: int, xi: float):
+    """Values and derivatives of the k+1 1D basis functions at xi."""
+    _, C, dC = lagrange_1d(k)
+    return npoly.polyval(xi, C.T), npoly.polyval(xi, dC.T)
+
+
+def shape_3d(k: int, xi: float, eta: float, zeta: float, h: float = 1.0):
+    """Tensor-product shape functions at (xi, eta, zeta).
+
+    Returns N (nn,) and dNdx (nn, 3), the physical gradient for a cube of
+    edge h (d/dx = (2/h) d/dxi)."""
+    Nx, dNx = shape_1d(k, xi)
+    Ny, dNy = shape_1d(k, eta)
+    Nz, dNz = shape_1d(k, zeta)
+    nn = (k + 1) ** 3
+    N = np.zeros(nn)
+    dN = np.zeros((nn, 3))
+    for iz in range(k + 1):
+        for iy in range(k + 1):
+            for ix in range(k + 1):
+                a = ix + (k + 1) * (iy + (k + 1) * iz)
+                N[a] = Nx[ix] * Ny[iy] * Nz[iz]
+                dN[a, 0] = dNx[ix] * Ny[iy] * Nz[iz]
+                dN[a, 1] = Nx[ix] * dNy[iy] * Nz[iz]
+                dN[a, 2] = Nx[ix] * Ny[iy] * dNz[iz]
+    return N, dN * (2.0 / h)
+
+
+def elasticity_D(nu: float, E: float = 1.0) -> np.ndarray:
+    """Isotropic linear-elastic constitutive matrix (Voigt, engineering
+    shear strains), the D of Eq. matrixK."""
+    c = E / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = c * nu
+    for i in range(3):
+        D[i, i] = c * (1.0 - nu)
+    for i in range(3, 6):
+        D[i, i] = c * (1.0 - 2.0 * nu) / 2.0
+    return D
+
+
+def strain_displacement(dNdx: np.ndarray) -> np.ndarray:
+    """B (6 x 3nn): strain = B u_e for element DOFs ordered 3*a + c."""
+    nn = dNdx.shape[0]
+    B = np.zeros((6, 3 * nn))
+    for a in range(nn):
+        gx, gy, gz = dNdx[a]
+        B[0, 3 * a + 0] = gx
+        B[1, 3 * a + 1] = gy
+        B[2, 3 * a + 2] = gz
+        B[3, 3 * a + 0] = gy
+        B[3, 3 * a + 1] = gx
+        B[4, 3 * a + 1] = gz
+        B[4, 3 * a + 2] = gy
+        B[5, 3 * a + 0] = gz
+        B[5, 3 * a + 2] = gx
+    return B
+
+
+def subcell_stiffness(k: int, n: int, nu: float, h: float = 1.0) -> np.ndarray:
+    """The stacked subcell stiffness table of Eq. matrixK_mr.
+
+    K[i] = int over subcell i of B^T D B dx (E = 1), for the n^3 subcells of a
+    degree-k Lagrange cube of edge h.  Each subcell is integrated with its own
+    tensor Gauss-Legendre rule of k+1 points per axis, which is exact: the
+    integrand is a polynomial of degree at most 2k in each coordinate.
+    Returns an array (n^3, d, d), d = 3 (k+1)^3.
+    """
+    D = elasticity_D(nu)
+    d = 3 * (k + 1) ** 3
+    gp, gw = nleg.leggauss(k + 1)
+    jac = (h / 2.0) ** 3  # dx dy dz = (h/2)^3 dxi deta dzeta
+    half = 1.0 / n  # half-width of a subinterval in xi
+    out = np.zeros((n ** 3, d, d))
+    for c in range(n):
+        for b in range(n):
+            for a in range(n):
+                i = a + n * (b + n * c)
+                cx = -1.0 + (2 * a + 1) / n
+                cy = -1.0 + (2 * b + 1) / n
+                cz = -1.0 + (2 * c + 1) / n
+                Ki = np.zeros((d, d))
+                for qz in range(k + 1):
+                    for qy in range(k + 1):
+                        for qx in range(k + 1):
+                            xi = cx + half * gp[qx]
+                            eta = cy + half * gp[qy]
+                            zeta = cz + half * gp[qz]
+                            wq = gw[qx] * gw[qy] * gw[qz] * half ** 3
+                            _, dN = shape_3d(k, xi, eta, zeta, h)
+                            B = strain_displacement(dN)
+                            Ki += wq * jac * (B.T @ D @ B)
+                out[i] = Ki
+    return out
+
+
+def element_stiffness(k: int, nu: float, h: float = 1.0) -> np.ndarray:
+    """Whole-element matrix int_{Omega_e} B^T D B (Eq. matrixK with E = 1)."""
+    return subcell_stiffness(k, 1, nu, h)[0]
+
+
+def rigid_body_modes(k: int, h: float = 1.0) -> np.ndarray:
+    """The six rigid-body displacement fields of one element, (6, d):
+    three translations and three infinitesimal rotations about the centre."""
+    nodes = np.linspace(-1.0, 1.0, k + 1) * (h / 2.0)
+    nn = (k + 1) ** 3
+    R = np.zeros((6, 3 * nn))
+    for iz in range(k + 1):
+        for iy in range(k + 1):
+            for ix in range(k + 1):
+                a = ix + (k + 1) * (iy + (k + 1) * iz)
+                x, y, z = nodes[ix], nodes[iy], nodes[iz]
+                R[0, 3 * a + 0] = 1.0
+                R[1, 3 * a + 1] = 1.0
+                R[2, 3 * a + 2] = 1.0
+                # rotation about z: (-y, x, 0); about x: (0, -z, y); about y: (z, 0, -x)
+                R[3, 3 * a: 3 * a + 3] = (-y, x, 0.0)
+                R[4, 3 * a: 3 * a + 3] = (0.0, -z, y)
+                R[5, 3 * a: 3 * a + 3] = (z, 0.0, -x)
+    return R

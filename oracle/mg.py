@@ -1,0 +1,157 @@
+"""Geometric multigrid cycle and MG-preconditioned CG (oracle).
+
+Section 2.3, Algorithm 1 (two-grid cycle), applied recursively for more
+levels: smooth eta1 times, residual, restrict with R = P^T, solve (or recurse
+gamma times: gamma = 1 is a V-cycle, 2 a W-cycle) on the coarse grid, prolong
+and correct, smooth eta2 times.  Section 2.3: a coarse element holds 2x2x2
+fine elements and P is linear interpolation between the node lattices.
+Section 7 (intro): damped Jacobi, omega = 0.5, eta1 = eta2 = 1.
+Section 7.2: the coarsest system is solved by a Cholesky factorization; PCG
+stops when ||r|| / ||f|| < 1e-8 (the denominator reading: ||f||).
+
+Readings taken here (the paper does not say):
+  * coarse operators are re-discretised from the density field itself: a
+    level-l element (edge 2^l) covers (n 2^l)^3 density cells and its matrix
+    is Eq. matrixK_mr with that many subcells.  For Lagrange Q1 this equals
+    the Galerkin product P^T A P exactly (tested), since trilinear
+    interpolation reproduces the coarse shape functions;
+  * supports: a coarse DOF is fixed iff the coincident fine DOF is fixed;
+    fixed rows/columns of every level operator are replaced by identity and
+    P is masked on both sides, P = M_f P_lin M_c;
+  * the prolongation for every degree is trilinear interpolation on the node
+    lattices (the paper's choice for Lagrange elements).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from . import fem, mesh
+from .fe import simp_weights
+
+
+def _interp_1d(nf: int) -> sp.csr_matrix:
+    """Linear interpolation from a lattice of (nf-1)/2+1 nodes to nf nodes."""
+    nc = (nf - 1) // 2 + 1
+    rows, cols, vals = [], [], []
+    for i in range(nf):
+        if i % 2 == 0:
+            rows.append(i); cols.append(i // 2); vals.append(1.0)
+        else:
+            rows += [i, i]; cols += [(i - 1) // 2, (i + 1) // 2]; vals += [0.5, 0.5]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(nf, nc))
+
+
+def prolongation(lat_fine) -> sp.csr_matrix:
+    """Unmasked trilinear P_lin between node lattices, DOF-interleaved."""
+    Lx, Ly, Lz = lat_fine
+    Pn = sp.kron(sp.kron(_interp_1d(Lz), _interp_1d(Ly)), _interp_1d(Lx))
+    return sp.kron(Pn, sp.identity(3), format="csr")
+
+
+def coarse_mask(mask_f: np.ndarray, lat_fine) -> np.ndarray:
+    """Coarse DOF fixed iff the coincident fine DOF is fixed."""
+    Lx, Ly, Lz = lat_fine
+    m = mask_f.reshape(Lz, Ly, Lx, 3)
+    return np.ascontiguousarray(m[::2, ::2, ::2, :]).reshape(-1)
+
+
+class Level:
+    pass
+
+
+class Hierarchy:
+    """Level operators A_l (supports -> identity), Jacobi diagonals, P_l and
+    the dense Cholesky factor of the coarsest operator."""
+
+    def __init__(self, prob, rho: np.ndarray, levels: int):
+        k, n = prob.degree, prob.n_mr
+        nx, ny, nz = prob.nx, prob.ny, prob.nz
+        w_cells = simp_weights(rho, prob.E0, prob.Emin, prob.penal)
+        self.levels = []
+        mask = prob.mask.astype(np.uint8)
+        for l in range(levels):
+            s = 2 ** l
+            if nx % s or ny % s or nz % s:
+                raise ValueError("mesh not divisible for this many levels")
+            L = Level()
+            L.nx, L.ny, L.nz = nx // s, ny // s, nz // s
+            L.nsub = n * s
+            L.lat = (k * L.nx + 1, k * L.ny + 1, k * L.nz + 1)
+            L.ndof = 3 * L.lat[0] * L.lat[1] * L.lat[2]
+            L.mask = mask
+            Ktab = fem.subcell_stiffness(k, L.nsub, prob.nu, h=float(s))
+            m, d, _ = Ktab.shape
+            w_e = w_cells[mesh.subcell_density_index(L.nx, L.ny, L.nz, L.nsub)]
+            Ke = (w_e @ Ktab.reshape(m, d * d)).reshape(-1, d, d)
+            ed = mesh.element_dofs(L.nx, L.ny, L.nz, k)
+            rows = np.repeat(ed, d, axis=1).reshape(-1)
+            cols = np.tile(ed, (1, d)).reshape(-1)
+            K = sp.coo_matrix((Ke.reshape(-1), (rows, cols)), shape=(L.ndof, L.ndof)).tocsr()
+            free = (mask == 0).astype(np.float64)
+            Mf = sp.diags(free)
+            L.A = (Mf @ K @ Mf + sp.diags(1.0 - free)).tocsr()
+            L.Dinv = 1.0 / L.A.diagonal()
+            self.levels.append(L)
+            if l + 1 < levels:
+                mask = coarse_mask(mask, L.lat)
+        for l in range(levels - 1):
+            F, C = self.levels[l], self.levels[l + 1]
+            P = prolongation(F.lat)
+            Mf = sp.diags((F.mask == 0).astype(np.float64))
+            Mc = sp.diags((C.mask == 0).astype(np.float64))
+            F.P = (Mf @ P @ Mc).tocsr()
+        last = self.levels[-1]
+        last.chol = sla.cho_factor(last.A.toarray(), lower=True)
+
+
+def vcycle(h: Hierarchy, b: np.ndarray, l: int = 0, omega: float = 0.5, eta1: int = 1,
+           eta2: int = 1, gamma: int = 1) -> np.ndarray:
+    """Approximate A_l^{-1} b by one multigrid cycle from a zero initial guess
+    (Algorithm 1 applied recursively)."""
+    L = h.levels[l]
+    if l == len(h.levels) - 1:
+        return sla.cho_solve(L.chol, b)
+    v = np.zeros_like(b)
+    for _ in range(eta1):  # step 1: pre-smoothing, damped Jacobi
+        v = v + omega * L.Dinv * (b - L.A @ v)
+    r = b - L.A @ v  # step 2: residual
+    rH = L.P.T @ r  # step 3: restriction R = P^T
+    eH = np.zeros_like(rH)
+    for _ in range(gamma):  # step 4: coarse solve by recursion
+        eH = eH + vcycle(h, rH - h.levels[l + 1].A @ eH, l + 1, omega, eta1, eta2, gamma)
+    v = v + L.P @ eH  # steps 5-6: prolong and correct
+    for _ in range(eta2):  # step 7: post-smoothing
+        v = v + omega * L.Dinv * (b - L.A @ v)
+    return v
+
+
+def pcg(h: Hierarchy, f: np.ndarray, u0: np.ndarray | None = None, rtol: float = 1e-8,
+        maxit: int = 1000, **cyc):
+    """Preconditioned CG on A_0 u = f (supports are identity rows; f must be
+    zero there).  Stops when ||f - A u|| / ||f|| <= rtol.  Returns
+    (u, iterations, relative residual history)."""
+    A = h.levels[0].A
+    u = np.zeros_like(f) if u0 is None else u0.copy()
+    r = f - A @ u
+    nf = np.linalg.norm(f)
+    hist = [np.linalg.norm(r) / nf]
+    if hist[-1] <= rtol:
+        return u, 0, hist
+    z = vcycle(h, r, **cyc)
+    p = z.copy()
+    rz = r @ z
+    for it in range(1, maxit + 1):
+        q = A @ p
+        alpha = rz / (p @ q)
+        u += alpha * p
+        r -= alpha * q
+        hist.append(np.linalg.norm(r) / nf)
+        if hist[-1] <= rtol:
+            return u, it, hist
+        z = vcycle(h, r, **cyc)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return u, maxit, hist

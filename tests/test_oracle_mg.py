@@ -1,0 +1,89 @@
+"""Pins of the oracle's multigrid (oracle/mg.py).
+
+  * Galerkin identity: for Lagrange Q1 with nested meshes the coarse
+    operator re-discretised from the density field equals P^T A P on the
+    free DOFs (clamped face: the coarse space is a subspace of the fine one);
+    this pins the coarse element tables, the density-cell bookkeeping of the
+    coarse levels and the interpolation P at once;
+  * P reproduces trilinear fields exactly;
+  * a cycle with eta1 = eta2 and the same Jacobi smoother is a symmetric
+    operator (Algorithm 1 pre/post structure);
+  * with a single level the cycle is the exact (Cholesky) solve;
+  * MG-PCG converges to the direct solution.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import fe, mg, mesh
+
+
+def _setup(nx, ny, nz, n, levels, rmin=0.0, seed=0, k=1):
+    p = workloads.cantilever(nx, ny, nz, degree=k, n_mr=n, rmin=rmin, seed=seed)
+    m = fe.Model(p)
+    rho = m.densities(p.x)
+    return p, m, rho, mg.Hierarchy(p, rho, levels)
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_coarse_operator_is_galerkin_product(n):
+    p, m, rho, h = _setup(8, 4, 4, n, 3, seed=4)
+    for l in range(2):
+        F, C = h.levels[l], h.levels[l + 1]
+        G = (F.P.T @ F.A @ F.P).toarray()
+        freec = C.mask == 0
+        A = C.A.toarray()
+        Gf = G[np.ix_(freec, freec)]
+        Af = A[np.ix_(freec, freec)]
+        assert np.abs(Gf - Af).max() <= 1e-12 * np.abs(Af).max()
+
+
+def test_prolongation_reproduces_trilinear_fields():
+    lat_f = (9, 5, 5)
+    P = mg.prolongation(lat_f)
+    Xc = mesh.node_coords(4, 2, 2, 1) * 2.0
+    Xf = mesh.node_coords(8, 4, 4, 1)
+    f = lambda X: 1 + 2 * X[:, 0] - X[:, 1] + 0.5 * X[:, 2] + 0.25 * X[:, 0] * X[:, 1] * X[:, 2]
+    vc = np.zeros(3 * len(Xc)); vc[1::3] = f(Xc)
+    vf = P @ vc
+    np.testing.assert_allclose(vf[1::3], f(Xf), atol=1e-13)
+    assert np.abs(vf[0::3]).max() == 0 and np.abs(vf[2::3]).max() == 0
+
+
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_cycle_is_symmetric(gamma):
+    p, m, rho, h = _setup(8, 4, 4, 2, 3, rmin=1.0, seed=9)
+    free = h.levels[0].mask == 0
+    rng = np.random.default_rng(3)
+    x = np.where(free, rng.normal(size=free.size), 0.0)
+    y = np.where(free, rng.normal(size=free.size), 0.0)
+    a = y @ mg.vcycle(h, x, gamma=gamma)
+    b = x @ mg.vcycle(h, y, gamma=gamma)
+    assert abs(a - b) <= 1e-10 * abs(a)
+
+
+def test_single_level_cycle_is_exact_solve():
+    p, m, rho, h = _setup(4, 2, 2, 1, 1, seed=1)
+    f = np.where(p.mask == 0, p.f[0], 0.0)
+    z = mg.vcycle(h, f)
+    u = m.solve(m.weights(rho), f)
+    np.testing.assert_allclose(z, u, rtol=0, atol=1e-12 * np.abs(u).max())
+
+
+def test_mg_pcg_converges_to_direct_solution():
+    p, m, rho, h = _setup(8, 4, 4, 2, 3, rmin=1.0, seed=6)
+    f = np.where(p.mask == 0, p.f[0], 0.0)
+    u, its, hist = mg.pcg(h, f, rtol=1e-12)
+    ud = m.solve(m.weights(rho), f)
+    assert hist[-1] <= 1e-12 and its < 200
+    assert np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud)
+
+
+def test_run_with_mg_matches_direct_run():
+    p = workloads.cantilever(8, 4, 4, degree=1, n_mr=2, rmin=1.0, seed=12, mg_levels=3)
+    m = fe.Model(p)
+    a = m.run(method="mg", rtol=1e-13)
+    b = m.run(method="dense")
+    assert np.linalg.norm(a["u"] - b["u"]) <= 1e-9 * np.linalg.norm(b["u"])
+    assert abs(a["c"][0] - b["c"][0]) <= 1e-11 * b["c"][0]
+    assert np.linalg.norm(a["g_x"] - b["g_x"]) <= 1e-9 * np.linalg.norm(b["g_x"])
