@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark: solved DOFs/s to a 1e-8 true residual, mixed-precision vs FP64
+MG-PCG, on the multiresolution cantilever (density 96x48x48, Q1 48x24x24,
+n_mr = 2, smooth design field, filter radius 1.5, 4-level V-cycle).
+
+One step = one pass of the whole hot path on device-resident inputs:
+set_densities (filter, SIMP weights, every level's operator, coarse
+Cholesky), solve from u0 = 0 to ||f - K u|| / ||f|| <= 1e-8, compliance and
+design gradient.  value = free DOFs / step time (all ranks' DOFs over the
+slowest rank's time; one independent replica per GPU under torchrun).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  The reference arm times the CPU FP64 oracle
+on the same input on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="cantilever_mr_96x48x48_q1_48x24x24_n2", nx=48, ny=24, nz=24, n_mr=2,
+                rmin=1.5, density="smooth", seed=0, levels=4, rtol=1e-8)
+METRIC = "Solved DOFs/s to 1e-8 residual (mixed vs FP64 MG-PCG); p50/p99 solve latency"
+UNIT = "DOF/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+# Derived FP64 peak: 2 DFMA lanes/clk/SM (from the measured 1.19 TFLOP/s
+# DFMA rate at ~1.96 GHz) x 2 flop x 152 SMs x 2070 MHz max SM clock.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+# DRAM traffic per launch of the dominant kernel from an ncu capture of the
+# same workload (profiles/), valid while the kernel source is unchanged.
+NCU_TRAFFIC = {}
+
+
+def problem():
+    import workloads
+
+    w = WORKLOAD
+    return workloads.cantilever(w["nx"], w["ny"], w["nz"], n_mr=w["n_mr"], rmin=w["rmin"],
+                                density=w["density"], seed=w["seed"], mg_levels=w["levels"])
+
+
+def source_hash(name: str) -> str:
+    p = os.path.join(ROOT, "paper_2311_05595_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:12]
+
+
+# ---- clocks ------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"tosolve_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- CPU oracle (reference arm and cpu_baseline) ------------------------------
+
+def oracle_step_seconds() -> tuple[float, int, int]:
+    """One full oracle step on the workload, in a fresh single-threaded
+    process (spawned: never forked from a CUDA process)."""
+    code = (
+        "import os,sys,time; sys.path.insert(0, %r)\n"
+        "import bench, numpy as np\n"
+        "from oracle import fe\n"
+        "p = bench.problem()\n"
+        "t = time.perf_counter()\n"
+        "m = fe.Model(p)\n"
+        "out = m.run(method='mg', rtol=%r, levels=%d)\n"
+        "dt = time.perf_counter() - t\n"
+        "print(dt, p.nfree, p.nrhs)\n" % (ROOT, WORKLOAD["rtol"], WORKLOAD["levels"]))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       cwd=ROOT, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    dt, nfree, nrhs = r.stdout.split()[-3:]
+    return float(dt), int(nfree), int(nrhs)
+
+
+def cpu_baseline_entry():
+    dt, nfree, nrhs = oracle_step_seconds()
+    return {"value": nfree * nrhs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one full oracle step (filter, assembly, MG hierarchy, MG-PCG to 1e-8, "
+                      "gradient) on the exact benchmark input, single-threaded, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_step_seconds()
+    times = []
+    nfree = nrhs = 1
+    for _ in range(args.steps):
+        dt, nfree, nrhs = oracle_step_seconds()
+        times.append(dt)
+    T = sum(times)
+    value = nfree * nrhs * len(times) / T
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * T / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "precision": "fp64 (CPU oracle, scipy sparse)"},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                         "sample": "full oracle step on the benchmark input per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---- GPU arm -------------------------------------------------------------------
+
+def kernel_launches(levels: int, iterations: int, attempts: int = 1) -> int:
+    """Our kernels per step: set_densities (filter; fine element matrices,
+    assembly, two FP32 casts; 2 per coarse level; coarse dense + factor),
+    solve (prep, residual, check; per PCG iteration: 4 per non-coarsest
+    level + 1 coarse solve + 5 CG kernels; true residual + final), gradient
+    (masked dot + sum, energies, scale, filter transpose)."""
+    setd = 1 + 4 + 2 * (levels - 1) + 2
+    per_it = 4 * (levels - 1) + 1 + 5
+    solve = attempts * 5 + per_it * iterations
+    return setd + solve + 5
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2311_05595_gb300 import tosolve as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    p = problem()
+    rtol = WORKLOAD["rtol"]
+    maxit = 2000
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    x = torch.tensor(p.x, device=dev)
+    f = torch.tensor(p.f, device=dev)
+    u = torch.zeros_like(f)
+    gx = torch.zeros_like(x)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def make(precision):
+        d = T.make_desc(p.nx, p.ny, p.nz, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin, nu=p.nu,
+                        penal=p.penal, mg_levels=WORKLOAD["levels"], precision=precision)
+        return T.Solver(d, p.mask, stream)
+
+    def step(s):
+        T.tosolve_set_densities(s.h, x)
+        u.zero_()
+        info = T.tosolve_solve(s.h, f, 1, u, rtol, maxit)
+        c = T.tosolve_compliance_grad(s.h, u, f, 1, gx)
+        return info, c
+
+    def timed(s, steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                step(s)
+            stream.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(steps)]
+            infos = []
+            t0 = time.perf_counter()
+            for e0, e1 in evs:
+                flush.zero_()
+                e0.record(stream)
+                info, c = step(s)
+                e1.record(stream)
+                infos.append((info.iterations, info.total_iterations, info.rel_residual,
+                              info.ms, float(c[0])))
+            stream.synchronize()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, infos, wall
+
+    sampler = ClockSampler(local)
+    out = {}
+    for label, prec in (("mixed", T.PREC_FP32), ("fp64", T.PREC_FP64)):
+        s = make(prec)
+        if label == "mixed":
+            sampler.start()
+        ms, infos, wall = timed(s, args.steps, args.warmup)
+        if label == "mixed":
+            clocks = sampler.stop()
+        tot = sum(ms)
+        if world > 1:
+            t = torch.tensor([tot], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        solve_ms = sorted(i[3] for i in infos)
+        out[label] = dict(ms=ms, tot=tot, infos=infos, wall=wall, solve_ms=solve_ms, solver=s)
+    free_dofs = p.nfree * p.nrhs
+    mixed = out["mixed"]
+    fp64 = out["fp64"]
+    value = world * free_dofs * args.steps / (mixed["tot"] * 1e-3)
+    fp64_value = world * free_dofs * args.steps / (fp64["tot"] * 1e-3)
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+
+    # ---- end to end through the host-buffer entry point ----
+    s = mixed["solver"]
+    xh = torch.tensor(p.x).pin_memory()
+    fh = torch.tensor(p.f).pin_memory()
+    uh = torch.zeros(p.f.shape, dtype=torch.float64).pin_memory()
+    gh = torch.zeros(p.x.size, dtype=torch.float64).pin_memory()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            T.tosolve_step_host(s.h, xh.numpy(), fh.numpy(), 1, rtol, maxit, 0, uh.numpy(), gh.numpy())
+        stream.synchronize()
+        barrier()
+        e2e_times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            T.tosolve_step_host(s.h, xh.numpy(), fh.numpy(), 1, rtol, maxit, 0, uh.numpy(), gh.numpy())
+            e2e_times.append(time.perf_counter() - t0)
+        barrier()
+    e2e_tot = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = world * free_dofs * args.steps / e2e_tot
+    h2d = (p.x.size + p.f.size) * 8
+    d2h = (p.f.size + p.x.size + 1) * 8
+
+    # ---- dominant kernel: the FP64 operator apply (q = K p in PCG) ----
+    xa = torch.randn(p.ndof, dtype=torch.float64, device=dev)
+    ya = torch.zeros_like(xa)
+    nrep = 200
+    with torch.cuda.stream(stream):
+        T.tosolve_set_densities(s.h, x)
+        for _ in range(10):
+            T.tosolve_apply(s.h, 0, 0, xa, ya)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(nrep):
+            T.tosolve_apply(s.h, 0, 0, xa, ya)
+        a1.record(stream)
+        stream.synchronize()
+    us = a0.elapsed_time(a1) * 1e3 / nrep
+    Lx, Ly, Lz = p.lattice
+    pairs = (3 * Lx - 2) * (3 * Ly - 2) * (3 * Lz - 2)  # (node, neighbour) couplings
+    flops = 18.0 * pairs
+    nn = Lx * Ly * Lz
+    bytes_alg = nn * (243 * 8 + 3 * 8 * 2)
+    achieved = flops / (us * 1e-6) / 1e12
+    traffic = NCU_TRAFFIC.get(("k_apply_diag<double>", source_hash("k_solve.cu")))
+
+    its = [i[0] for i in mixed["infos"]]
+    its64 = [i[0] for i in fp64["infos"]]
+    res = max(i[2] for i in mixed["infos"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed["tot"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "free_dofs": p.nfree, "load_cases": p.nrhs,
+                   "density_cells": int(p.x.size), "mg_levels": WORKLOAD["levels"],
+                   "smoother": "damped Jacobi omega=0.5, 1+1, V-cycle",
+                   "precision": "FP64 CG + FP32 V-cycle (value); FP64 MG-PCG (fp64_value)",
+                   "rtol": rtol, "start": "u0 = 0 every step",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "fp64_value": fp64_value, "speedup_vs_fp64": value / fp64_value,
+        "fp64_ms_per_step": fp64["tot"] / args.steps,
+        "pcg_iterations": {"mixed": statistics.median(its), "fp64": statistics.median(its64)},
+        "true_rel_residual_max": res,
+        "solve_latency_ms": {"p50": pct(mixed["solve_ms"], 0.5), "p99": pct(mixed["solve_ms"], 0.99),
+                             "fp64_p50": pct(fp64["solve_ms"], 0.5),
+                             "fp64_p99": pct(fp64["solve_ms"], 0.99)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": kernel_launches(WORKLOAD["levels"], int(statistics.median(its))) * args.steps,
+        "roofline": {"kernel": "k_apply_diag<double> (FP64 27-point block stencil, K u)",
+                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "us_per_launch": us, "alg_bytes_per_launch": bytes_alg,
+                     "achieved_gbs": bytes_alg / (us * 1e-6) / 1e9,
+                     "peak_note": "FP64 peak derived from unit count and 2070 MHz; "
+                                  "HBM peak 6797.9 GB/s of measured"},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_entry()
+        except Exception as e:  # reported, never silently dropped
+            line["cpu_baseline"] = {"error": str(e)[-300:]}
+    for lab in ("mixed", "fp64"):
+        out[lab]["solver"].close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

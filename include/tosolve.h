@@ -1,0 +1,192 @@
+/*
+ * tosolve.h -- C ABI of the GB300 (sm_103a) multigrid-preconditioned CG
+ * solver for the multiresolution SIMP elasticity problem of Vitorino & Gomes,
+ * "An efficient topology optimization algorithm for large-scale
+ * three-dimensional structures" (arXiv 2311.05595).
+ *
+ * The library computes, on one GPU, the hot path of one SLP iteration:
+ *   design variables x  --(density filter / projection, Sec. 2.2 and 3.2)-->
+ *   densities rho       --(SIMP weights, Eq. matrixK_mr)-->  K(rho)
+ *   K(rho) u = f        --(MG-preconditioned CG, Alg. 1, Sec. 2.3, 7.2)-->  u
+ *   c = f^T u and dc/dx --(Sec. 3.4)-->  back to the host optimizer.
+ *
+ * Mesh and numbering (shared by every call):
+ *   * nx*ny*nz cubic displacement elements of edge 1 (Sec. 7.1);
+ *   * Lagrange degree k = 1: node lattice (nx+1)*(ny+1)*(nz+1),
+ *     node id = i + Lx*(j + Ly*l) (x fastest), DOF = 3*node + component;
+ *   * each element holds n_mr^3 density cells (Sec. 3.1); the density grid
+ *     and the design grid (d_mr = n_mr) are (n_mr*nx)*(n_mr*ny)*(n_mr*nz)
+ *     cells, flattened x fastest;
+ *   * the Dirichlet mask has one byte per DOF, 1 = fixed (u = 0 there).
+ *
+ * Conventions of every call:
+ *   * pointers named *_dev are device pointers (any allocator) on the
+ *     device that was current at tosolve_create; *_host are host pointers;
+ *     the caller owns every buffer it passes and the library keeps no
+ *     reference to it after the call returns;
+ *   * the library owns its workspace (allocated in tosolve_create, freed in
+ *     tosolve_destroy); no call other than create/destroy allocates device
+ *     memory;
+ *   * work is issued on the stream given to tosolve_create; calls that return
+ *     host values (tosolve_solve's info, tosolve_compliance_grad's c_host,
+ *     tosolve_step_host) synchronise that stream before returning, the others
+ *     are asynchronous;
+ *   * every call returns a tosolve_status; on failure tosolve_last_error
+ *     gives a one-line reason.  No call aborts the process or traps on the
+ *     GPU.
+ */
+#ifndef TOSOLVE_H_
+#define TOSOLVE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tosolve_s* tosolve_t;
+
+typedef enum {
+  TOSOLVE_OK = 0,
+  TOSOLVE_EINVAL = 1,      /* bad descriptor, size, pointer or argument      */
+  TOSOLVE_ENOMEM = 2,      /* device allocation failed in tosolve_create     */
+  TOSOLVE_ENOTCONV = 3,    /* maxit reached before the tolerance; info valid */
+  TOSOLVE_EBREAKDOWN = 4,  /* NaN/Inf, p^T K p <= 0 or a non-positive pivot  */
+  TOSOLVE_ECUDA = 5        /* a CUDA runtime call failed                     */
+} tosolve_status;
+
+/* Precision of the multigrid preconditioner (the outer CG, its dot
+ * products, the true residual, the coarse Cholesky factor, the compliance
+ * and the gradient are always FP64). */
+typedef enum {
+  TOSOLVE_PREC_FP64 = 0, /* plain FP64 MG-PCG                                */
+  TOSOLVE_PREC_FP32 = 1  /* FP32 V-cycle operators and vectors, FP32 accum.  */
+} tosolve_precision;
+
+/* Problem and solver description (Sec. 2, 3.1, 7 intro). */
+typedef struct {
+  int nx, ny, nz;         /* displacement elements per axis, >= 1           */
+  int degree;             /* Lagrange degree k (this build: 1)              */
+  int n_mr;               /* density cells per element edge, 1..8           */
+  int d_mr;               /* design cells per element edge; must equal n_mr */
+  double E0, Emin;        /* SIMP: E(rho) = Emin + rho^p (E0 - Emin), Eq.   */
+  double nu;              /*   matrixK; Poisson ratio nu in (-1, 0.5)       */
+  double penal;           /*   penalty p >= 1                               */
+  double rmin;            /* filter radius in element units; 0 => rho = x  */
+  int mg_levels;          /* multigrid levels >= 1 (each halves the mesh;   */
+                          /*   nx, ny, nz divisible by 2^(levels-1))        */
+  int precision;          /* tosolve_precision of the preconditioner        */
+  double omega;           /* damped-Jacobi factor (0 => 0.5, Sec. 7 intro)  */
+  int cycle_gamma;        /* cycles per level: 1 = V-cycle (0 => 1; the     */
+                          /*   only value this build accepts)               */
+  int max_rhs;            /* load cases per solve call, >= 1 (0 => 1)       */
+} tosolve_desc;
+
+typedef struct {
+  int iterations;       /* PCG iterations of the last right-hand side        */
+  int total_iterations; /* summed over the right-hand sides of the call      */
+  double rel_residual;  /* max over rhs of the FP64 true ||f - K u|| / ||f|| */
+  double ms;            /* device time of the solve (CUDA events)            */
+  int status;           /* tosolve_status of the call                        */
+} tosolve_info;
+
+/* Builds the solver for one mesh: validates the descriptor, allocates all
+ * device memory, computes the stacked subcell stiffness table K^(e_i)
+ * (Sec. 3.3, Eq. matrixK_mr: computed once for a regular mesh), the filter
+ * stencil and the multigrid level descriptors, and records the CUDA graph of
+ * the PCG loop.
+ *   desc:        problem description (copied).
+ *   mask_host:   3*(nx+1)*(ny+1)*(nz+1) bytes, 1 = fixed DOF (copied).
+ *   cuda_stream: cudaStream_t to run on; NULL makes the library create
+ *                (and own) a blocking stream, ordered with the legacy
+ *                default stream.  Must not be the legacy stream handle
+ *                itself when non-NULL (the PCG loop is graph-captured).
+ *   out:         receives the handle.
+ * Errors: EINVAL (checked before any CUDA call), ENOMEM, ECUDA. */
+tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host,
+                              void* cuda_stream, tosolve_t* out);
+
+/* Device memory tosolve_create would allocate for desc, in bytes (host
+ * only; used for HBM admission).  Errors: EINVAL. */
+tosolve_status tosolve_footprint(const tosolve_desc* desc, size_t* bytes);
+
+/* New design: x_dev (design grid, FP64) -> rho = H x (Sec. 2.2 Eq.
+ * filter_weights, Sec. 3.2 Eq. projdsgn), SIMP weights w = Emin +
+ * rho^p (E0 - Emin), and the multigrid refresh of Sec. 7.2: every level's
+ * operator from the densities, the Jacobi diagonals and the dense Cholesky
+ * factor (with its inverse) of the coarsest operator.  Asynchronous.
+ * Errors: EINVAL, ECUDA. */
+tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev);
+
+/* Solves K(rho) u = f for nrhs load cases by MG-preconditioned CG (Sec. 2.3,
+ * 7.2) until the true FP64 residual ||f - K u||_2 / ||f||_2 <= rtol.
+ *   f_dev: nrhs x ndof FP64 (rows contiguous); f at fixed DOFs is ignored.
+ *   u_dev: nrhs x ndof FP64; in: initial guess (warm start, Sec. 7.2.1),
+ *          out: solution, 0 at fixed DOFs.
+ *   info:  may be NULL; always written when non-NULL.
+ * maxit is in 1..100000 (bounds the device-side loop).
+ * Synchronises the stream.  Errors: EINVAL, ENOTCONV (maxit reached),
+ * EBREAKDOWN, ECUDA. */
+tosolve_status tosolve_solve(tosolve_t h, const double* f_dev, int nrhs, double* u_dev,
+                             double rtol, int maxit, tosolve_info* info);
+
+/* Compliance and sensitivities for nrhs solutions (Sec. 3.4):
+ *   c_host[r]  = f_r^T u_r                                  (FP64, host)
+ *   dcdrho_dev = sum_r -p rho^(p-1) (E0-Emin) u_e^T K^(e_i) u_e  (density
+ *                grid, may be NULL)
+ *   dcdx_dev   = H^T dcdrho (design grid, may be NULL).
+ * Synchronises the stream (c_host).  Errors: EINVAL, ECUDA. */
+tosolve_status tosolve_compliance_grad(tosolve_t h, const double* u_dev, const double* f_dev,
+                                       int nrhs, double* c_host, double* dcdx_dev,
+                                       double* dcdrho_dev);
+
+/* One whole SLP-iteration step from host buffers: copies x and f from the
+ * host, runs set_densities, solve and compliance_grad, and copies u, c and
+ * dc/dx back.  warm != 0 starts the solve from this handle's previous
+ * solution (zero at the first call; Sec. 7.2.1 reuses the last solution),
+ * warm == 0 from zero.  Buffers as above but on the host (pinned memory
+ * makes the copies asynchronous); u_host and dcdx_host may be NULL.
+ * Synchronises.  Errors: as the calls it makes. */
+tosolve_status tosolve_step_host(tosolve_t h, const double* x_host, const double* f_host,
+                                 int nrhs, double rtol, int maxit, int warm, double* u_host,
+                                 double* c_host, double* dcdx_host, tosolve_info* info);
+
+/* ---- Single steps of the path, for verification ------------------------ */
+
+/* Number of multigrid levels and, for level l, its node lattice (Lx, Ly, Lz)
+ * into dims[0..2].  Host only.  Errors: EINVAL. */
+tosolve_status tosolve_level_dims(tosolve_t h, int level, int* dims);
+
+/* Copies the stacked subcell stiffness table of the finest level, m x d x d
+ * FP64 (m = n_mr^3, d = 24, E = 1), into table_dev (Sec. 3.3). */
+tosolve_status tosolve_subcell_table(tosolve_t h, double* table_dev);
+
+/* Copies the densities rho and SIMP weights w of the last set_densities
+ * (density grid, FP64) into rho_dev / w_dev (either may be NULL). */
+tosolve_status tosolve_densities(tosolve_t h, double* rho_dev, double* w_dev);
+
+/* y = A_l x for the level-l operator (fixed rows/columns replaced by
+ * identity), computed in FP64 (precision 0) or in the preconditioner's FP32
+ * form (precision 1; inputs/outputs still FP64).  x_dev, y_dev: 3*nodes(l).
+ * Level 0 FP64 is K(rho) of Eq. matrixK_mr; coarser levels are re-discretised
+ * from the density field (Sec. 7.2: system matrices of each mesh level). */
+tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double* x_dev,
+                             double* y_dev);
+
+/* z = B b: one multigrid cycle (Algorithm 1, recursive, zero initial guess)
+ * of the preconditioner in its configured precision; b_dev, z_dev FP64,
+ * length 3*nodes(0); b must be 0 at fixed DOFs. */
+tosolve_status tosolve_precondition(tosolve_t h, const double* b_dev, double* z_dev);
+
+/* Reason for the last failure on this handle (never NULL). */
+const char* tosolve_last_error(tosolve_t h);
+
+/* Frees everything owned by the handle (NULL is accepted). */
+void tosolve_destroy(tosolve_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOSOLVE_H_ */

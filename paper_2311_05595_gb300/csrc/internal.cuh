@@ -1,0 +1,199 @@
+// Internal declarations of the tosolve library (not part of the C ABI).
+//
+// Data layout in HBM (all arrays owned by the handle, allocated once in
+// tosolve_create):
+//   * DOF vectors: 3 values per lattice node, node id i + Lx*(j + Ly*l);
+//   * level operators: a 27-point stencil of 3x3 blocks per node, stored
+//     structure-of-arrays S[(o*9 + r*3 + c)*nn + node] with neighbour offset
+//     o = (dx+1) + 3*((dy+1) + 3*(dz+1)), so one warp reads 32 consecutive
+//     nodes' coefficient of the same (o, r, c) in one transaction;
+//   * element matrices: upper triangle (300 of 24x24) per element;
+//   * density / design grid: one FP64 per cell, x fastest.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/tosolve.h"
+
+namespace tos {
+
+constexpr int kBS = 256;       // threads per block of the vector / stencil kernels
+constexpr int kMaxPart = 608;  // partial sums per reduction (4 blocks per SM)
+constexpr int kMaxLevels = 8;
+constexpr int kEdofQ1 = 24;    // DOFs of a trilinear hexahedron
+constexpr int kSym = 300;      // entries of a 24x24 symmetric upper triangle
+constexpr int kNB = 32;        // block size of the coarse Cholesky
+constexpr int kMaxCoarse = 4096;  // largest coarse system (DOFs)
+
+// Scalars of the PCG loop, kept on the device so the loop runs as a CUDA
+// graph with a device-side while condition.
+struct DevState {
+  double ff;       // ||f||^2
+  double rr;       // ||r||^2 (recursive residual)
+  double rz;       // r^T z of the current direction
+  double rz_next;  // r^T z of the next direction (written by cg_dir)
+  double alpha;    // step of the last update
+  double beta;
+  double tol2;     // rtol^2
+  double rr_true;  // ||f - K u||^2 after the loop
+  double c;        // compliance f^T u
+  int iter;
+  int maxit;
+  int status;      // 0 ok, TOSOLVE_EBREAKDOWN on breakdown
+  int converged;
+  int coarse_status;  // non-zero if the coarse Cholesky met a bad pivot
+  int pad[3];
+};
+
+struct Level {
+  int ex, ey, ez;   // elements per axis
+  int Lx, Ly, Lz;   // node lattice
+  int nn, ndof;
+  int nsub;         // density cells per element edge at this level
+  double h;         // element edge length
+  bool op64;        // operator stored in FP64 for the V-cycle
+  uint8_t* mask = nullptr;
+  double* S64 = nullptr;   // FP64 stencil (level 0 always; others when op64)
+  float* S32 = nullptr;    // FP32 stencil (FP32 preconditioner levels)
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  void* b = nullptr;  // V-cycle vectors in the preconditioner precision
+  void* v = nullptr;
+  void* r = nullptr;
+  void* z = nullptr;
+};
+
+// Read-only view of a level's operator for the kernels.
+template <typename T>
+struct LevelView {
+  int Lx, Ly, Lz, nn;
+  const T* S;
+  const T* dinv;
+  const uint8_t* mask;
+};
+
+// ---- launchers (k_setup.cu) ----------------------------------------------
+void launch_subcell_table(int n, double nu, double h, double* tab, cudaStream_t st);
+void launch_symmetrize(int m, const double* tab, double* tabsym, cudaStream_t st);
+void launch_moment_basis(double nu, double* cmom, cudaStream_t st);
+void launch_filter_init(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,
+                        double* invom, cudaStream_t st);
+void launch_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,
+                       const double* invom, const double* x, double Emin, double dE,
+                       double penal, double* rho, double* w, cudaStream_t st);
+void launch_elem_direct(bool fp64, const Level& L, int n, const double* w, int Dx, int Dy,
+                        const double* tabsym, void* Ke, cudaStream_t st);
+void launch_elem_moments(bool fp64, const Level& L, const double* w, int Dx, int Dy,
+                         const double* cmom, void* Ke, cudaStream_t st);
+void launch_assemble(bool fp64, const Level& L, const void* Ke, void* S, void* dinv,
+                     cudaStream_t st);
+void launch_to_fp32(size_t n, const double* a, float* b, cudaStream_t st);
+void launch_coarse_dense(const Level& L, double* A, cudaStream_t st);
+cudaError_t launch_coarse_factor(int n, double* A, double* W, double* Dblk, double* X,
+                                 double* Ainv, int* status, int grid, cudaStream_t st);
+int coarse_factor_grid();
+
+// ---- launchers (k_solve.cu) ----------------------------------------------
+template <typename T>
+LevelView<T> view(const Level& L);
+void launch_vcycle(bool fp64, Level* lv, int L, double omega, int gamma, const double* Ainv,
+                   cudaStream_t st);
+void launch_cg_prep(const Level& L0, const double* fin, const double* uin, double* f,
+                    double* u, double* part, int np, cudaStream_t st);
+void launch_cg_residual(bool fp64, const Level& L0, const double* f, const double* u,
+                        double* r, void* b0, double* part, int np, cudaStream_t st);
+void launch_cg_check_init(double* part_ff, double* part_rr, int np, DevState* ds,
+                          cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st);
+void launch_cg_dots_rz(bool fp64, const Level& L0, const double* r, const void* z,
+                       const double* q, double* part_rz, double* part_zq, int np,
+                       cudaStream_t st);
+void launch_cg_dir(bool fp64, const Level& L0, const double* part_rz, const double* part_zq,
+                   int np, const void* z, double* p, DevState* ds, cudaStream_t st);
+void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np,
+                     cudaStream_t st);
+void launch_cg_update(bool fp64, const Level& L0, const double* part_pq, int np, double* u,
+                      double* r, const double* p, const double* q, void* b0, double* part_rr,
+                      DevState* ds, cudaStream_t st);
+void launch_cg_check(const double* part_rr, int np, DevState* ds,
+                     cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st);
+void launch_cg_final(const double* part_rr, int np, DevState* ds, cudaStream_t st);
+void launch_apply_diag(bool fp64, const Level& L, const double* x, double* y, cudaStream_t st);
+void launch_cast(bool to_fp64, size_t n, const void* a, void* b, bool src_fp64,
+                 cudaStream_t st);
+
+// ---- launchers (k_grad.cu) -----------------------------------------------
+void launch_energy_grad(const Level& L0, int n, const double* u, const double* tabsym,
+                        const double* rho, double penal, double dE, int Dx, int Dy,
+                        bool first, double* g_rho, cudaStream_t st);
+void launch_scale(size_t n, const double* a, const double* s, double* out, cudaStream_t st);
+void launch_filter_T(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,
+                     const double* gt, double* gx, cudaStream_t st);
+void launch_compliance(const Level& L0, const double* f, const double* u, double* part, int np,
+                       DevState* ds, cudaStream_t st);
+
+inline int parts_for(int nn) {
+  int g = (nn + kBS - 1) / kBS;
+  return g < kMaxPart ? (g < 1 ? 1 : g) : kMaxPart;
+}
+
+__host__ __device__ inline int sym_index(int r, int c) {
+  // r <= c < 24: row-major upper triangle
+  return r * kEdofQ1 - (r * (r - 1)) / 2 + (c - r);
+}
+
+}  // namespace tos
+
+// The opaque handle of the C ABI.
+struct tosolve_s {
+  tosolve_desc d;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int dev = 0;
+  int L = 1;
+  tos::Level lv[tos::kMaxLevels];
+  int Dx = 0, Dy = 0, Dz = 0, ncell = 0;
+  int m = 1;  // subcells per fine element
+  // density side
+  double* rho = nullptr;
+  double* w = nullptr;
+  double* invom = nullptr;
+  int noff = 0;
+  int4* foff = nullptr;
+  double* fwgt = nullptr;
+  double* gtmp = nullptr;
+  // element tables
+  double* tab64 = nullptr;     // m x 24 x 24
+  double* tabsym64 = nullptr;  // m x 300
+  double* cmom64 = nullptr;    // 27 x 300
+  void* Ke = nullptr;
+  // coarse level
+  int nc = 0;
+  double* Ad = nullptr;
+  double* Wp = nullptr;
+  double* Dblk = nullptr;
+  double* Xinv = nullptr;
+  double* Ainv = nullptr;
+  int cgrid = 1;
+  // PCG
+  double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *f = nullptr;
+  double *tmpa = nullptr, *tmpb = nullptr;
+  double* part = nullptr;  // 4 x kMaxPart
+  int np = 1;
+  tos::DevState* ds = nullptr;
+  tos::DevState* hs = nullptr;  // pinned mirror
+  bool graph_ready = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle hcond = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // host-step staging
+  double *hx = nullptr, *hf = nullptr, *hu = nullptr, *hg = nullptr;
+  int hrhs = 0;
+  bool have_u = false;
+  bool have_rho = false;
+  std::string err;
+  size_t bytes = 0;
+};

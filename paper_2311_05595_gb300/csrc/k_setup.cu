@@ -1,0 +1,511 @@
+// Setup kernels: the stacked subcell stiffness table (Sec. 3.3), the density
+// filter (Sec. 2.2 / 3.2), SIMP weights (Eq. matrixK), and the per-design
+// multigrid refresh of Sec. 7.2 (every level's operator and the coarsest
+// level's Cholesky factor are rebuilt for each new density field; the level
+// structure itself is built once).
+#include <cooperative_groups.h>
+
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace tos {
+namespace {
+
+// 1D trilinear factors on [-1, 1]: phi_0 = (1 - t)/2, phi_1 = (1 + t)/2.
+__device__ __forceinline__ double phi(int a, double t) { return a ? 0.5 * (1.0 + t) : 0.5 * (1.0 - t); }
+__device__ __forceinline__ double dphi(int a) { return a ? 0.5 : -0.5; }
+
+// K^(e_i) = int_{subcell i} lambda d_i N_a d_j N_b + mu d_j N_a d_i N_b
+//                          + mu delta_ij grad N_a . grad N_b   (E = 1),
+// the tensor form of int B^T D B, integrated with 2x2x2 Gauss points per
+// subcell (exact for the trilinear element).  One block per subcell.
+__global__ void k_subcell_table(int n, double nu, double h, double* __restrict__ tab) {
+  __shared__ double g[8][8][3];  // [gauss point][node][direction], physical
+  const int sub = blockIdx.x;
+  const int sa = sub % n, sb = (sub / n) % n, sc = sub / (n * n);
+  const double half = 1.0 / n;
+  const double gp = 1.0 / sqrt(3.0);
+  const int tid = threadIdx.x;
+  if (tid < 64) {
+    const int q = tid >> 3, node = tid & 7;
+    const double xi = -1.0 + (2 * sa + 1) * half + half * ((q & 1) ? gp : -gp);
+    const double eta = -1.0 + (2 * sb + 1) * half + half * ((q & 2) ? gp : -gp);
+    const double zeta = -1.0 + (2 * sc + 1) * half + half * ((q & 4) ? gp : -gp);
+    const int ix = node & 1, iy = (node >> 1) & 1, iz = node >> 2;
+    const double s = 2.0 / h;
+    g[q][node][0] = s * dphi(ix) * phi(iy, eta) * phi(iz, zeta);
+    g[q][node][1] = s * phi(ix, xi) * dphi(iy) * phi(iz, zeta);
+    g[q][node][2] = s * phi(ix, xi) * phi(iy, eta) * dphi(iz);
+  }
+  __syncthreads();
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = 1.0 / (2.0 * (1.0 + nu));
+  const double wq = half * half * half * (0.125 * h * h * h);  // GL weights are 1
+  for (int t = tid; t < kEdofQ1 * kEdofQ1; t += blockDim.x) {
+    const int R = t / kEdofQ1, C = t % kEdofQ1;
+    const int a = R / 3, i = R % 3, b = C / 3, j = C % 3;
+    double acc = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      const double* ga = g[q][a];
+      const double* gb = g[q][b];
+      double v = lam * ga[i] * gb[j] + mu * ga[j] * gb[i];
+      if (i == j) v += mu * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
+      acc += v;
+    }
+    tab[(size_t)sub * kEdofQ1 * kEdofQ1 + t] = wq * acc;
+  }
+}
+
+__global__ void k_symmetrize(int m, const double* __restrict__ tab, double* __restrict__ tabsym) {
+  const int s = blockIdx.x;
+  for (int t = threadIdx.x; t < kEdofQ1 * kEdofQ1; t += blockDim.x) {
+    const int R = t / kEdofQ1, C = t % kEdofQ1;
+    if (R <= C) tabsym[(size_t)s * kSym + sym_index(R, C)] = tab[(size_t)s * kEdofQ1 * kEdofQ1 + t];
+  }
+}
+
+// Polynomial coefficients of one 1D factor: value (deriv = 0) or derivative.
+__device__ __forceinline__ void poly1(int a, int deriv, double c[2]) {
+  if (deriv) { c[0] = a ? 0.5 : -0.5; c[1] = 0.0; }
+  else { c[0] = 0.5; c[1] = a ? 0.5 : -0.5; }
+}
+
+// Coefficient of xi^k (k = 0..2) of the product of two degree-1 factors.
+__device__ __forceinline__ double prod_coef(const double u[2], const double v[2], int k) {
+  if (k == 0) return u[0] * v[0];
+  if (k == 1) return u[0] * v[1] + u[1] * v[0];
+  return u[1] * v[1];
+}
+
+// Moment basis of the trilinear element: the integrand of the element
+// matrix, in reference coordinates, is sum_alpha C_alpha xi^alpha with
+// alpha in {0,1,2}^3, so K^(e) = (h/2) sum_alpha M_alpha C_alpha with
+// M_alpha = int_e w(xi) xi^alpha dxi.  Thread per (alpha, upper entry).
+__global__ void k_moment_basis(double nu, double* __restrict__ cmom) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 27 * kSym) return;
+  const int alpha = t / kSym, e = t % kSym;
+  int R = 0;
+  while (sym_index(R, kEdofQ1 - 1) < e) ++R;
+  const int C = R + (e - sym_index(R, R));
+  const int al[3] = {alpha % 3, (alpha / 3) % 3, alpha / 9};
+  const int a = R / 3, i = R % 3, b = C / 3, j = C % 3;
+  const int na[3] = {a & 1, (a >> 1) & 1, a >> 2};
+  const int nb[3] = {b & 1, (b >> 1) & 1, b >> 2};
+  // T(p, s) = coefficient of xi^alpha in d_p N_a * d_s N_b
+  auto T = [&](int p, int s) {
+    double v = 1.0;
+    for (int ax = 0; ax < 3; ++ax) {
+      double u[2], w[2];
+      poly1(na[ax], p == ax, u);
+      poly1(nb[ax], s == ax, w);
+      v *= prod_coef(u, w, al[ax]);
+    }
+    return v;
+  };
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = 1.0 / (2.0 * (1.0 + nu));
+  double v = lam * T(i, j) + mu * T(j, i);
+  if (i == j) v += mu * (T(0, 0) + T(1, 1) + T(2, 2));
+  cmom[t] = v;
+}
+
+__global__ void k_filter_init(int Dx, int Dy, int Dz, int noff, const int4* __restrict__ off,
+                              const double* __restrict__ wgt, double* __restrict__ invom) {
+  const long N = (long)Dx * Dy * Dz;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
+    const int cx = c % Dx, cy = (c / Dx) % Dy, cz = c / ((long)Dx * Dy);
+    double s = 0.0;
+    for (int o = 0; o < noff; ++o) {
+      const int4 d = off[o];
+      const int x = cx + d.x, y = cy + d.y, z = cz + d.z;
+      if (x >= 0 && x < Dx && y >= 0 && y < Dy && z >= 0 && z < Dz) s += wgt[o];
+    }
+    invom[c] = 1.0 / s;
+  }
+}
+
+// rho_i = sum_j (w_ij / w_i) x_j (Eq. filter_weights / projdsgn) and the
+// SIMP weight w_i = Emin + rho_i^p (E0 - Emin) (Eq. matrixK), fused.
+__global__ void k_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* __restrict__ off,
+                             const double* __restrict__ wgt, const double* __restrict__ invom,
+                             const double* __restrict__ x, double Emin, double dE, double penal,
+                             double* __restrict__ rho, double* __restrict__ w) {
+  const long N = (long)Dx * Dy * Dz;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
+    const int cx = c % Dx, cy = (c / Dx) % Dy, cz = c / ((long)Dx * Dy);
+    double s = 0.0;
+    for (int o = 0; o < noff; ++o) {
+      const int4 d = off[o];
+      const int X = cx + d.x, Y = cy + d.y, Z = cz + d.z;
+      if (X >= 0 && X < Dx && Y >= 0 && Y < Dy && Z >= 0 && Z < Dz)
+        s += wgt[o] * x[X + (long)Dx * (Y + (long)Dy * Z)];
+    }
+    const double r = s * invom[c];
+    rho[c] = r;
+    w[c] = Emin + pow(r, penal) * dE;
+  }
+}
+
+// Fine-level element matrices, Eq. matrixK_mr: K^(e) = sum_i w_{e,i} K^(e_i),
+// upper triangle.  One block per element; FP64 accumulation.
+template <typename T>
+__global__ void k_elem_direct(int ex, int ey, int ez, int n, const double* __restrict__ w, int Dx,
+                              int Dy, const double* __restrict__ tabsym, T* __restrict__ Ke) {
+  __shared__ double ws[512];
+  const int m = n * n * n;
+  const long e = blockIdx.x;
+  const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+  for (int s = threadIdx.x; s < m; s += blockDim.x) {
+    const int a = s % n, b = (s / n) % n, c = s / (n * n);
+    ws[s] = w[(n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c))];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kSym; t += blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < m; ++s) acc += ws[s] * tabsym[(size_t)s * kSym + t];
+    Ke[e * kSym + t] = (T)acc;
+  }
+}
+
+// Coarse-level element matrices from the density field: a level-l element
+// covers N^3 density cells; K^(e) = (h/2) sum_alpha M_alpha C_alpha with the
+// 27 polynomial moments M_alpha of the cellwise-constant weights.  This is
+// Eq. matrixK_mr with N^3 subcells evaluated exactly through the moments.
+// One block per element.
+template <typename T, typename Acc>
+__global__ void k_elem_moments(int ex, int ey, int ez, int N, double h, const double* __restrict__ w,
+                               int Dx, int Dy, const double* __restrict__ cmom, T* __restrict__ Ke) {
+  __shared__ Acc mu[3][1024];
+  __shared__ Acc red[32][27];
+  __shared__ Acc M[27];
+  const long e = blockIdx.x;
+  const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+  const int tid = threadIdx.x;
+  for (int a = tid; a < N; a += blockDim.x) {
+    const double t0 = -1.0 + 2.0 * a / N, t1 = -1.0 + 2.0 * (a + 1) / N;
+    mu[0][a] = (Acc)(t1 - t0);
+    mu[1][a] = (Acc)(0.5 * (t1 * t1 - t0 * t0));
+    mu[2][a] = (Acc)((t1 * t1 * t1 - t0 * t0 * t0) / 3.0);
+  }
+  __syncthreads();
+  Acc acc[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) acc[q] = 0;
+  const long ncell = (long)N * N * N;
+  for (long s = tid; s < ncell; s += blockDim.x) {
+    const int a = s % N, b = (s / N) % N, c = s / ((long)N * N);
+    const Acc wv = (Acc)w[(N * exi + a) + (long)Dx * ((N * eyi + b) + (long)Dy * (N * ezi + c))];
+#pragma unroll
+    for (int gz = 0; gz < 3; ++gz)
+#pragma unroll
+      for (int gy = 0; gy < 3; ++gy) {
+        const Acc wyz = wv * mu[gy][b] * mu[gz][c];
+#pragma unroll
+        for (int gx = 0; gx < 3; ++gx) acc[gx + 3 * (gy + 3 * gz)] += wyz * mu[gx][a];
+      }
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    Acc v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (tid < 27) {
+    Acc s = 0;
+    for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) s += red[wi][tid];
+    M[tid] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < kSym; t += blockDim.x) {
+    Acc s = 0;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) s += M[q] * (Acc)cmom[q * kSym + t];
+    Ke[e * kSym + t] = (T)((Acc)(0.5 * h) * s);
+  }
+}
+
+// Node-centred assembly of the 27-point block stencil from the element
+// matrices around each node (gather, fixed order: deterministic).  Fixed DOFs
+// get identity rows and zero columns.  Also writes the inverse diagonal.
+template <typename T>
+__global__ void k_assemble(int ex, int ey, int ez, int Lx, int Ly, int Lz, const T* __restrict__ Ke,
+                           const uint8_t* __restrict__ mask, T* __restrict__ S, T* __restrict__ dinv) {
+  const long nn = (long)Lx * Ly * Lz;
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
+       node += (long)gridDim.x * blockDim.x) {
+    const int i = node % Lx, j = (node / Lx) % Ly, l = node / ((long)Lx * Ly);
+    for (int o = 0; o < 27; ++o) {
+      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+      const int ii = i + dx, jj = j + dy, ll = l + dz;
+      const bool valid = ii >= 0 && ii < Lx && jj >= 0 && jj < Ly && ll >= 0 && ll < Lz;
+      double acc[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+      if (valid) {
+        const int x0 = max(dx == 1 ? i : i - 1, 0), x1 = min(dx == -1 ? i - 1 : i, ex - 1);
+        const int y0 = max(dy == 1 ? j : j - 1, 0), y1 = min(dy == -1 ? j - 1 : j, ey - 1);
+        const int z0 = max(dz == 1 ? l : l - 1, 0), z1 = min(dz == -1 ? l - 1 : l, ez - 1);
+        for (int ez_ = z0; ez_ <= z1; ++ez_)
+          for (int ey_ = y0; ey_ <= y1; ++ey_)
+            for (int ex_ = x0; ex_ <= x1; ++ex_) {
+              const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
+              const int a = (i - ex_) + 2 * ((j - ey_) + 2 * (l - ez_));
+              const int b = (ii - ex_) + 2 * ((jj - ey_) + 2 * (ll - ez_));
+              const T* base = Ke + e * kSym;
+#pragma unroll
+              for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  const int R = 3 * a + r, C = 3 * b + c;
+                  acc[3 * r + c] += (double)base[R <= C ? sym_index(R, C) : sym_index(C, R)];
+                }
+            }
+      }
+      const long nb = valid ? node + dx + (long)Lx * (dy + (long)Ly * dz) : node;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const bool fr = mask[3 * node + r] != 0;
+          const bool fc = valid ? (mask[3 * nb + c] != 0) : true;
+          double v = acc[3 * r + c];
+          if (fr || fc) v = (o == 13 && r == c) ? 1.0 : 0.0;
+          S[(size_t)(o * 9 + 3 * r + c) * nn + node] = (T)v;
+          if (o == 13 && r == c) dinv[3 * node + r] = (T)(1.0 / v);
+        }
+    }
+  }
+}
+
+__global__ void k_to_fp32(size_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    b[t] = (float)a[t];
+}
+
+__global__ void k_coarse_dense(int Lx, int Ly, int Lz, const double* __restrict__ S, double* __restrict__ A) {
+  const long nn = (long)Lx * Ly * Lz;
+  const long n = 3 * nn;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nn * 27; t += (long)gridDim.x * blockDim.x) {
+    const long node = t % nn;
+    const int o = t / nn;
+    const int i = node % Lx, j = (node / Lx) % Ly, l = node / ((long)Lx * Ly);
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int ii = i + dx, jj = j + dy, ll = l + dz;
+    if (ii < 0 || ii >= Lx || jj < 0 || jj >= Ly || ll < 0 || ll >= Lz) continue;
+    const long nb = node + dx + (long)Lx * (dy + (long)Ly * dz);
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c)
+        A[(3 * node + r) * n + 3 * nb + c] = S[(size_t)(o * 9 + 3 * r + c) * nn + node];
+  }
+}
+
+// Dense FP64 Cholesky A = L L^T (blocked, right-looking), then
+// X = L^{-1} (block rows) and A^{-1} = X^T X, in one cooperative launch.
+// The V-cycle's coarse solve is then one dense matrix-vector product spread
+// over many SMs (FP64 issue is 4 flop/clk/SM on this part, so a sequential
+// triangular solve on one SM would dominate the cycle).
+__global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restrict__ W,
+                                double* __restrict__ Dblk, double* __restrict__ X,
+                                double* __restrict__ Ainv, int* __restrict__ status) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double a[kNB][kNB + 1];
+  __shared__ double li[kNB][kNB + 1];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const long gtid = blockIdx.x * (long)bd + tid, gstride = (long)gridDim.x * bd;
+  const int nblk = (n + kNB - 1) / kNB;
+  for (int kb = 0; kb < nblk; ++kb) {
+    const int k0 = kb * kNB, nb = min(kNB, n - k0);
+    // (A) every block factors the diagonal block in shared memory
+    for (int t = tid; t < kNB * kNB; t += bd) {
+      const int i = t / kNB, j = t % kNB;
+      a[i][j] = (i < nb && j < nb && j <= i) ? A[(size_t)(k0 + i) * n + k0 + j] : 0.0;
+    }
+    __syncthreads();
+    for (int jj = 0; jj < nb; ++jj) {
+      if (tid == 0) {
+        double d = a[jj][jj];
+        if (!(d > 0.0)) {
+          if (blockIdx.x == 0) atomicExch(status, 1);
+          d = 1.0;
+        }
+        a[jj][jj] = sqrt(d);
+      }
+      __syncthreads();
+      for (int i = jj + 1 + tid; i < nb; i += bd) a[i][jj] /= a[jj][jj];
+      __syncthreads();
+      const int m = nb - jj - 1;
+      for (int t = tid; t < m * m; t += bd) {
+        const int i = jj + 1 + t / m, j = jj + 1 + t % m;
+        if (j <= i) a[i][j] -= a[i][jj] * a[j][jj];
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < kNB * kNB; t += bd) li[t / kNB][t % kNB] = 0.0;
+    __syncthreads();
+    if (tid < nb) {
+      const int j = tid;
+      for (int i = j; i < nb; ++i) {
+        double s = (i == j) ? 1.0 : 0.0;
+        for (int t = j; t < i; ++t) s -= a[i][t] * li[t][j];
+        li[i][j] = s / a[i][i];
+      }
+    }
+    __syncthreads();
+    // (B) panel below the diagonal block: W = A_panel L_kk^{-T}
+    const int rows = n - k0 - nb;
+    for (long t = gtid; t < (long)rows * nb; t += gstride) {
+      const int i = k0 + nb + (int)(t / nb), jj = (int)(t % nb);
+      double s = 0.0;
+      for (int q = 0; q <= jj; ++q) s += A[(size_t)i * n + k0 + q] * li[jj][q];
+      W[(size_t)i * kNB + jj] = s;
+    }
+    grid.sync();
+    // (C) write L_kk, its inverse and the panel; update the trailing matrix
+    if (blockIdx.x == 0) {
+      for (int t = tid; t < kNB * kNB; t += bd) {
+        const int i = t / kNB, j = t % kNB;
+        if (i < nb && j < nb && j <= i) A[(size_t)(k0 + i) * n + k0 + j] = a[i][j];
+        Dblk[(size_t)kb * kNB * kNB + t] = li[i][j];
+      }
+    }
+    for (long t = gtid; t < (long)rows * nb; t += gstride) {
+      const int i = k0 + nb + (int)(t / nb), jj = (int)(t % nb);
+      A[(size_t)i * n + k0 + jj] = W[(size_t)i * kNB + jj];
+    }
+    for (long t = gtid; t < (long)rows * rows; t += gstride) {
+      int i = (int)(t / rows), j = (int)(t % rows);
+      if (j > i) continue;
+      i += k0 + nb;
+      j += k0 + nb;
+      double s = 0.0;
+      for (int q = 0; q < nb; ++q) s += W[(size_t)i * kNB + q] * W[(size_t)j * kNB + q];
+      A[(size_t)i * n + j] -= s;
+    }
+    grid.sync();
+  }
+  // X = L^{-1}, one block row at a time: X_ib,jb = -Linv_ib * sum_q L_ib,q X_q,jb
+  for (int ib = 0; ib < nblk; ++ib) {
+    const int i0 = ib * kNB, nbi = min(kNB, n - i0);
+    for (long t = gtid; t < (long)nbi * i0; t += gstride) {  // T = L[i0:, :i0] X[:i0, :i0]
+      const int r = (int)(t / i0), j = (int)(t % i0);
+      double s = 0.0;
+      for (int q = j; q < i0; ++q) s += A[(size_t)(i0 + r) * n + q] * X[(size_t)q * n + j];
+      Ainv[(size_t)r * n + j] = s;  // Ainv used as scratch for T (rows 0..nbi-1)
+    }
+    grid.sync();
+    const double* Li = Dblk + (size_t)ib * kNB * kNB;
+    for (long t = gtid; t < (long)nbi * (i0 + nbi); t += gstride) {
+      const int r = (int)(t / (i0 + nbi)), j = (int)(t % (i0 + nbi));
+      double v;
+      if (j >= i0) {
+        v = (j - i0 <= r) ? Li[r * kNB + (j - i0)] : 0.0;
+      } else {
+        v = 0.0;
+        for (int s2 = 0; s2 <= r; ++s2) v -= Li[r * kNB + s2] * Ainv[(size_t)s2 * n + j];
+      }
+      X[(size_t)(i0 + r) * n + j] = v;
+    }
+    grid.sync();
+  }
+  // A^{-1} = X^T X (lower triangle computed, mirrored)
+  for (long t = gtid; t < (long)n * n; t += gstride) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (j > i) continue;
+    double s = 0.0;
+    for (int q = i; q < n; ++q) s += X[(size_t)q * n + i] * X[(size_t)q * n + j];
+    Ainv[(size_t)i * n + j] = s;
+    Ainv[(size_t)j * n + i] = s;
+  }
+}
+
+inline int grid_for(long n, int bs = kBS, int cap = 4096) {
+  long g = (n + bs - 1) / bs;
+  if (g < 1) g = 1;
+  return (int)(g < cap ? g : cap);
+}
+
+}  // namespace
+
+void launch_subcell_table(int n, double nu, double h, double* tab, cudaStream_t st) {
+  k_subcell_table<<<n * n * n, 256, 0, st>>>(n, nu, h, tab);
+}
+
+void launch_symmetrize(int m, const double* tab, double* tabsym, cudaStream_t st) {
+  k_symmetrize<<<m, 256, 0, st>>>(m, tab, tabsym);
+}
+
+void launch_moment_basis(double nu, double* cmom, cudaStream_t st) {
+  k_moment_basis<<<(27 * kSym + 255) / 256, 256, 0, st>>>(nu, cmom);
+}
+
+void launch_filter_init(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,
+                        double* invom, cudaStream_t st) {
+  k_filter_init<<<grid_for((long)Dx * Dy * Dz), kBS, 0, st>>>(Dx, Dy, Dz, noff, off, wgt, invom);
+}
+
+void launch_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,
+                       const double* invom, const double* x, double Emin, double dE,
+                       double penal, double* rho, double* w, cudaStream_t st) {
+  k_filter_fwd<<<grid_for((long)Dx * Dy * Dz), kBS, 0, st>>>(Dx, Dy, Dz, noff, off, wgt, invom, x,
+                                                             Emin, dE, penal, rho, w);
+}
+
+void launch_elem_direct(bool fp64, const Level& L, int n, const double* w, int Dx, int Dy,
+                        const double* tabsym, void* Ke, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * L.ez;
+  if (fp64)
+    k_elem_direct<double><<<E, 320, 0, st>>>(L.ex, L.ey, L.ez, n, w, Dx, Dy, tabsym, (double*)Ke);
+  else
+    k_elem_direct<float><<<E, 320, 0, st>>>(L.ex, L.ey, L.ez, n, w, Dx, Dy, tabsym, (float*)Ke);
+}
+
+void launch_elem_moments(bool fp64, const Level& L, const double* w, int Dx, int Dy,
+                         const double* cmom, void* Ke, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * L.ez;
+  if (fp64)
+    k_elem_moments<double, double><<<E, 320, 0, st>>>(L.ex, L.ey, L.ez, L.nsub, L.h, w, Dx, Dy,
+                                                      cmom, (double*)Ke);
+  else
+    k_elem_moments<float, float><<<E, 320, 0, st>>>(L.ex, L.ey, L.ez, L.nsub, L.h, w, Dx, Dy, cmom,
+                                                    (float*)Ke);
+}
+
+void launch_assemble(bool fp64, const Level& L, const void* Ke, void* S, void* dinv,
+                     cudaStream_t st) {
+  const int g = grid_for(L.nn, 128);
+  if (fp64)
+    k_assemble<double><<<g, 128, 0, st>>>(L.ex, L.ey, L.ez, L.Lx, L.Ly, L.Lz, (const double*)Ke,
+                                          L.mask, (double*)S, (double*)dinv);
+  else
+    k_assemble<float><<<g, 128, 0, st>>>(L.ex, L.ey, L.ez, L.Lx, L.Ly, L.Lz, (const float*)Ke,
+                                         L.mask, (float*)S, (float*)dinv);
+}
+
+void launch_to_fp32(size_t n, const double* a, float* b, cudaStream_t st) {
+  k_to_fp32<<<grid_for((long)n), kBS, 0, st>>>(n, a, b);
+}
+
+void launch_coarse_dense(const Level& L, double* A, cudaStream_t st) {
+  k_coarse_dense<<<grid_for((long)L.nn * 27), kBS, 0, st>>>(L.Lx, L.Ly, L.Lz, L.S64, A);
+}
+
+int coarse_factor_grid() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_factor, 256, 0);
+  // one block per SM: co-resident as long as one block fits (checked here)
+  return per >= 1 ? sms : 0;
+}
+
+cudaError_t launch_coarse_factor(int n, double* A, double* W, double* Dblk, double* X,
+                                 double* Ainv, int* status, int grid, cudaStream_t st) {
+  void* args[] = {&n, &A, &W, &Dblk, &X, &Ainv, &status};
+  return cudaLaunchCooperativeKernel((void*)k_coarse_factor, dim3(grid), dim3(256), args, 0, st);
+}
+
+}  // namespace tos

@@ -1,0 +1,715 @@
+// C ABI of the solver (declared in include/tosolve.h): validation, memory
+// plan, the per-design refresh, the graph-captured PCG loop and the
+// gradient.  Every device step is one of the kernels in k_*.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace tos;
+
+namespace {
+
+thread_local std::string g_err;
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      h->err = std::string(#call) + " failed: " + cudaGetErrorString(e_);            \
+      return TOSOLVE_ECUDA;                                                           \
+    }                                                                                 \
+  } while (0)
+
+struct Plan {
+  int L = 1;
+  int n = 1, m = 1;
+  int Dx = 0, Dy = 0, Dz = 0;
+  long ncell = 0;
+  struct Lv {
+    int ex, ey, ez, Lx, Ly, Lz;
+    long nn, ndof;
+    int nsub;
+    bool s64, s32;
+  } lv[kMaxLevels];
+  long nc = 0;
+  int noff = 0;
+  size_t bytes = 0;
+};
+
+bool divisible(const tosolve_desc& d, int levels) {
+  const int s = 1 << (levels - 1);
+  return d.nx % s == 0 && d.ny % s == 0 && d.nz % s == 0;
+}
+
+long coarse_dofs(const tosolve_desc& d, int levels) {
+  const int s = 1 << (levels - 1);
+  return 3L * (d.nx / s + 1) * (d.ny / s + 1) * (d.nz / s + 1);
+}
+
+int count_offsets(int n, double rmin) {
+  if (rmin <= 0.0) return 1;
+  const double rc2 = (rmin * n) * (rmin * n);
+  const int R = (int)std::floor(rmin * n + 1e-9);
+  int cnt = 0;
+  for (int k = -R; k <= R; ++k)
+    for (int j = -R; j <= R; ++j)
+      for (int i = -R; i <= R; ++i)
+        if (i * i + j * j + k * k <= rc2 * (1.0 + 1e-12)) ++cnt;
+  return cnt;
+}
+
+// Validates the descriptor and computes the level structure and the bytes
+// tosolve_create allocates.  No CUDA calls.
+tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
+  if (dp == nullptr) { *why = "descriptor is NULL"; return TOSOLVE_EINVAL; }
+  tosolve_desc d = *dp;
+  if (d.nx < 1 || d.ny < 1 || d.nz < 1) { *why = "nx, ny, nz must be >= 1"; return TOSOLVE_EINVAL; }
+  if ((long)d.nx * d.ny * d.nz > (1L << 28)) { *why = "mesh too large"; return TOSOLVE_EINVAL; }
+  if (d.degree != 1) { *why = "only Lagrange degree 1 is built"; return TOSOLVE_EINVAL; }
+  if (d.n_mr < 1 || d.n_mr > 8) { *why = "n_mr must be in 1..8"; return TOSOLVE_EINVAL; }
+  if (d.d_mr != 0 && d.d_mr != d.n_mr) { *why = "d_mr must equal n_mr"; return TOSOLVE_EINVAL; }
+  if (!(d.E0 > 0.0) || !(d.Emin > 0.0) || d.Emin > d.E0) { *why = "need 0 < Emin <= E0"; return TOSOLVE_EINVAL; }
+  if (!(d.nu > -1.0 && d.nu < 0.5)) { *why = "nu must be in (-1, 0.5)"; return TOSOLVE_EINVAL; }
+  if (!(d.penal >= 1.0)) { *why = "penal must be >= 1"; return TOSOLVE_EINVAL; }
+  if (!(d.rmin >= 0.0) || d.rmin * d.n_mr > 16.0) { *why = "rmin*n_mr must be in [0, 16]"; return TOSOLVE_EINVAL; }
+  if (d.precision != TOSOLVE_PREC_FP64 && d.precision != TOSOLVE_PREC_FP32) { *why = "unknown precision"; return TOSOLVE_EINVAL; }
+  if (d.omega != 0.0 && !(d.omega > 0.0 && d.omega < 2.0)) { *why = "omega must be in (0, 2)"; return TOSOLVE_EINVAL; }
+  if (d.cycle_gamma != 0 && d.cycle_gamma != 1) { *why = "only the V-cycle (gamma = 1) is built"; return TOSOLVE_EINVAL; }
+  if (d.max_rhs < 0 || d.max_rhs > 64) { *why = "max_rhs must be in 0..64"; return TOSOLVE_EINVAL; }
+  int L = d.mg_levels;
+  if (L == 0) {
+    L = 1;
+    while (L < kMaxLevels && divisible(d, L + 1) && coarse_dofs(d, L) > 3000) ++L;
+  }
+  if (L < 1 || L > kMaxLevels) { *why = "mg_levels must be in 1..8"; return TOSOLVE_EINVAL; }
+  if (!divisible(d, L)) { *why = "nx, ny, nz must be divisible by 2^(mg_levels-1)"; return TOSOLVE_EINVAL; }
+  if (d.n_mr * (1 << (L - 1)) > 1024) { *why = "too many levels for n_mr"; return TOSOLVE_EINVAL; }
+  P->L = L;
+  P->n = d.n_mr;
+  P->m = d.n_mr * d.n_mr * d.n_mr;
+  P->Dx = d.n_mr * d.nx;
+  P->Dy = d.n_mr * d.ny;
+  P->Dz = d.n_mr * d.nz;
+  P->ncell = (long)P->Dx * P->Dy * P->Dz;
+  P->noff = count_offsets(d.n_mr, d.rmin);
+  const bool fp32 = d.precision == TOSOLVE_PREC_FP32;
+  const int maxrhs = d.max_rhs > 0 ? d.max_rhs : 1;
+  size_t B = 0;
+  size_t keB = 0;
+  for (int l = 0; l < L; ++l) {
+    Plan::Lv& v = P->lv[l];
+    v.ex = d.nx >> l; v.ey = d.ny >> l; v.ez = d.nz >> l;
+    v.Lx = v.ex + 1; v.Ly = v.ey + 1; v.Lz = v.ez + 1;
+    v.nn = (long)v.Lx * v.Ly * v.Lz;
+    v.ndof = 3 * v.nn;
+    v.nsub = d.n_mr << l;
+    const bool coarsest = l == L - 1;
+    v.s64 = (l == 0) || !fp32 || coarsest;
+    v.s32 = fp32 && !coarsest;
+    const size_t tsz = fp32 ? 4 : 8;
+    B += v.ndof;  // mask
+    if (v.s64) B += 243 * v.nn * 8 + v.ndof * 8;
+    if (v.s32) B += 243 * v.nn * 4 + v.ndof * 4;
+    B += 4 * v.ndof * tsz;  // b, v, r, z
+    const size_t ke = (size_t)v.ex * v.ey * v.ez * kSym * 8;
+    if (ke > keB) keB = ke;
+  }
+  P->nc = P->lv[L - 1].ndof;
+  if (P->nc > kMaxCoarse) { *why = "coarsest level too large for the dense solve: add levels"; return TOSOLVE_EINVAL; }
+  const long ndof0 = P->lv[0].ndof;
+  B += keB;
+  B += (size_t)P->ncell * 8 * 5;                      // rho, w, invom, gtmp, staging x
+  B += (size_t)P->noff * (sizeof(int4) + 8);
+  B += (size_t)P->m * (576 + kSym) * 8 + 27 * kSym * 8;  // tables
+  const long nc = P->nc;
+  const long nblk = (nc + kNB - 1) / kNB;
+  B += (size_t)(3 * nc * nc + nc * kNB + nblk * kNB * kNB) * 8;
+  B += (size_t)ndof0 * 8 * 7;                         // u r p q f tmpa tmpb
+  B += (size_t)ndof0 * 8 * 2 * maxrhs;                // host-step staging f, u
+  B += 4 * kMaxPart * 8 + sizeof(DevState) + (size_t)P->ncell * 8;
+  P->bytes = B;
+  return TOSOLVE_OK;
+}
+
+template <typename T>
+cudaError_t dalloc(tosolve_s* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) h->bytes += count * sizeof(T);
+  return e;
+}
+
+void free_all(tosolve_s* h) {
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  for (int l = 0; l < kMaxLevels; ++l) {
+    Level& L = h->lv[l];
+    F(L.mask); F(L.S64); F(L.S32); F(L.dinv64); F(L.dinv32); F(L.b); F(L.v); F(L.r); F(L.z);
+  }
+  F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
+  F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->Ke);
+  F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv);
+  F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
+  F(h->hx); F(h->hf); F(h->hu); F(h->hg);
+  if (h->hs) cudaFreeHost(h->hs);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+}
+
+bool prec_fp64(const tosolve_s* h) { return h->d.precision == TOSOLVE_PREC_FP64; }
+
+// Records the PCG loop of one right-hand side as a CUDA graph with a
+// device-side while node: prep, r0 = f - K u0, convergence test; while
+// (not converged): z = B r (multigrid cycle), direction, q = K p, update,
+// test; then the FP64 true residual.  The loop runs without host round trips.
+tosolve_status build_graph(tosolve_s* h) {
+  const bool fp64 = prec_fp64(h);
+  Level& L0 = h->lv[0];
+  const int np = h->np;
+  double* part0 = h->part;
+  double* part1 = h->part + kMaxPart;
+  double* part2 = h->part + 2 * kMaxPart;
+  double* part3 = h->part + 3 * kMaxPart;
+  cudaStream_t cs = h->st;
+  cudaStream_t bs = nullptr;
+  CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(bs);
+    h->err = std::string("begin capture: ") + cudaGetErrorString(e);
+    return TOSOLVE_ECUDA;
+  }
+  launch_cg_prep(L0, h->f, h->u, h->f, h->u, part0, np, cs);
+  launch_cg_residual(fp64, L0, h->f, h->u, h->r, L0.b, part1, np, cs);
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cgraph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cgraph, &deps, nullptr, &ndeps);
+  cudaGraphConditionalHandle hc = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, cgraph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    launch_cg_check_init(part0, part1, np, h->ds, hc, 1, cs);
+    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cgraph, &deps, nullptr, &ndeps);
+  }
+  cudaGraphNode_t cnode = nullptr;
+  cudaGraph_t body = nullptr;
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&cnode, cgraph, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+  }
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, bs);
+    launch_cg_dots_rz(fp64, L0, h->r, L0.z, h->q, part2, part3, np, bs);
+    launch_cg_dir(fp64, L0, part2, part3, np, L0.z, h->p, h->ds, bs);
+    launch_cg_apply(L0, h->p, h->q, part0, np, bs);
+    launch_cg_update(fp64, L0, part0, np, h->u, h->r, h->p, h->q, L0.b, part1, h->ds, bs);
+    launch_cg_check(part1, np, h->ds, hc, 1, bs);
+    cudaGraph_t bo = nullptr;
+    e = cudaStreamEndCapture(bs, &bo);
+  }
+  if (e == cudaSuccess) {
+    launch_cg_residual(fp64, L0, h->f, h->u, h->tmpa, nullptr, part1, np, cs);
+    launch_cg_final(part1, np, h->ds, cs);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(bs);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    h->err = std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+    cudaGetLastError();
+    return TOSOLVE_ECUDA;
+  }
+  h->graph = g;
+  h->hcond = hc;
+  CK(cudaGraphInstantiate(&h->gexec, g, 0));
+  h->graph_ready = true;
+  return TOSOLVE_OK;
+}
+
+tosolve_status set_err(tosolve_t h, tosolve_status s, const char* msg) {
+  if (h) h->err = msg;
+  g_err = msg;
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+tosolve_status tosolve_footprint(const tosolve_desc* desc, size_t* bytes) {
+  Plan P;
+  std::string why;
+  const tosolve_status s = plan_for(desc, &P, &why);
+  if (s != TOSOLVE_OK) { g_err = why; return s; }
+  if (bytes == nullptr) { g_err = "bytes is NULL"; return TOSOLVE_EINVAL; }
+  *bytes = P.bytes;
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host, void* cuda_stream,
+                              tosolve_t* out) {
+  if (out == nullptr) { g_err = "out is NULL"; return TOSOLVE_EINVAL; }
+  *out = nullptr;
+  Plan P;
+  std::string why;
+  tosolve_status s = plan_for(desc, &P, &why);
+  if (s != TOSOLVE_OK) { g_err = why; return s; }
+  if (mask_host == nullptr) { g_err = "mask is NULL"; return TOSOLVE_EINVAL; }
+  tosolve_s* h = new (std::nothrow) tosolve_s();
+  if (h == nullptr) { g_err = "host allocation failed"; return TOSOLVE_ENOMEM; }
+  h->d = *desc;
+  if (h->d.omega == 0.0) h->d.omega = 0.5;
+  if (h->d.cycle_gamma == 0) h->d.cycle_gamma = 1;
+  if (h->d.max_rhs == 0) h->d.max_rhs = 1;
+  h->d.d_mr = h->d.n_mr;
+  h->d.mg_levels = P.L;
+  h->L = P.L;
+  h->m = P.m;
+  h->Dx = P.Dx; h->Dy = P.Dy; h->Dz = P.Dz;
+  h->ncell = (int)P.ncell;
+  h->noff = P.noff;
+  h->nc = (int)P.nc;
+  const bool fp32 = h->d.precision == TOSOLVE_PREC_FP32;
+  auto fail = [&](tosolve_status st) {
+    free_all(h);
+    g_err = h->err;
+    delete h;
+    return st;
+  };
+#define CKC(call)                                                                     \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      h->err = std::string(#call) + " failed: " + cudaGetErrorString(e_);             \
+      cudaGetLastError();                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? TOSOLVE_ENOMEM : TOSOLVE_ECUDA);  \
+    }                                                                                 \
+  } while (0)
+  CKC(cudaGetDevice(&h->dev));
+  if (cuda_stream == nullptr) {
+    // a blocking stream: ordered with the legacy default stream
+    CKC(cudaStreamCreate(&h->st));
+    h->own_stream = true;
+  } else {
+    h->st = (cudaStream_t)cuda_stream;
+  }
+  cudaStream_t st = h->st;
+  // levels and masks
+  std::vector<uint8_t> mask(mask_host, mask_host + P.lv[0].ndof);
+  for (int l = 0; l < P.L; ++l) {
+    const Plan::Lv& v = P.lv[l];
+    Level& L = h->lv[l];
+    L.ex = v.ex; L.ey = v.ey; L.ez = v.ez;
+    L.Lx = v.Lx; L.Ly = v.Ly; L.Lz = v.Lz;
+    L.nn = (int)v.nn; L.ndof = (int)v.ndof;
+    L.nsub = v.nsub;
+    L.h = (double)(1 << l);
+    L.op64 = !fp32 || l == P.L - 1;
+    CKC(dalloc(h, &L.mask, v.ndof));
+    CKC(cudaMemcpy(L.mask, mask.data(), v.ndof, cudaMemcpyHostToDevice));
+    if (v.s64) { CKC(dalloc(h, &L.S64, 243 * v.nn)); CKC(dalloc(h, &L.dinv64, v.ndof)); }
+    if (v.s32) { CKC(dalloc(h, &L.S32, 243 * v.nn)); CKC(dalloc(h, &L.dinv32, v.ndof)); }
+    const size_t tsz = fp32 ? 4 : 8;
+    void** vecs[4] = {&L.b, &L.v, &L.r, &L.z};
+    for (void** pv : vecs) {
+      char* p = nullptr;
+      CKC(dalloc(h, &p, v.ndof * tsz));
+      CKC(cudaMemset(p, 0, v.ndof * tsz));
+      *pv = p;
+    }
+    if (l + 1 < P.L) {  // coarse DOF fixed iff the coincident fine DOF is fixed
+      const Plan::Lv& c = P.lv[l + 1];
+      std::vector<uint8_t> cm(c.ndof);
+      for (int K = 0; K < c.Lz; ++K)
+        for (int J = 0; J < c.Ly; ++J)
+          for (int I = 0; I < c.Lx; ++I) {
+            const long cn = I + (long)c.Lx * (J + (long)c.Ly * K);
+            const long fn = 2 * I + (long)v.Lx * (2 * J + (long)v.Ly * 2 * K);
+            for (int q = 0; q < 3; ++q) cm[3 * cn + q] = mask[3 * fn + q];
+          }
+      mask.swap(cm);
+    }
+  }
+  // tables (Sec. 3.3: the subcell matrices are computed once)
+  CKC(dalloc(h, &h->tab64, (size_t)P.m * 576));
+  CKC(dalloc(h, &h->tabsym64, (size_t)P.m * kSym));
+  CKC(dalloc(h, &h->cmom64, 27 * kSym));
+  launch_subcell_table(P.n, h->d.nu, 1.0, h->tab64, st);
+  launch_symmetrize(P.m, h->tab64, h->tabsym64, st);
+  launch_moment_basis(h->d.nu, h->cmom64, st);
+  // filter stencil: integer offsets with di^2+dj^2+dk^2 <= (r n)^2 (ties in)
+  {
+    std::vector<int4> off;
+    std::vector<double> wgt;
+    if (h->d.rmin <= 0.0) {
+      off.push_back(make_int4(0, 0, 0, 0));
+      wgt.push_back(1.0);
+    } else {
+      const int n = P.n;
+      const double r = h->d.rmin, rc2 = (r * n) * (r * n), sig = r / 3.0;
+      const int R = (int)std::floor(r * n + 1e-9);
+      for (int k = -R; k <= R; ++k)
+        for (int j = -R; j <= R; ++j)
+          for (int i = -R; i <= R; ++i) {
+            const int q = i * i + j * j + k * k;
+            if (q <= rc2 * (1.0 + 1e-12)) {
+              off.push_back(make_int4(i, j, k, 0));
+              wgt.push_back(std::exp(-(q / (double)(n * n)) / (2.0 * sig * sig)));
+            }
+          }
+    }
+    h->noff = (int)off.size();
+    CKC(dalloc(h, &h->foff, off.size()));
+    CKC(dalloc(h, &h->fwgt, wgt.size()));
+    CKC(cudaMemcpy(h->foff, off.data(), off.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpy(h->fwgt, wgt.data(), wgt.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  CKC(dalloc(h, &h->rho, P.ncell));
+  CKC(dalloc(h, &h->w, P.ncell));
+  CKC(dalloc(h, &h->invom, P.ncell));
+  CKC(dalloc(h, &h->gtmp, 2 * P.ncell));
+  launch_filter_init(P.Dx, P.Dy, P.Dz, h->noff, h->foff, h->fwgt, h->invom, st);
+  size_t keB = 0;
+  for (int l = 0; l < P.L; ++l) {
+    const size_t ke = (size_t)P.lv[l].ex * P.lv[l].ey * P.lv[l].ez * kSym;
+    if (ke > keB) keB = ke;
+  }
+  CKC(dalloc(h, (double**)&h->Ke, keB));
+  // coarse dense solve
+  {
+    const long nc = P.nc, nblk = (nc + kNB - 1) / kNB;
+    CKC(dalloc(h, &h->Ad, nc * nc));
+    CKC(dalloc(h, &h->Wp, nc * kNB));
+    CKC(dalloc(h, &h->Dblk, nblk * kNB * kNB));
+    CKC(dalloc(h, &h->Xinv, nc * nc));
+    CKC(dalloc(h, &h->Ainv, nc * nc));
+    h->cgrid = coarse_factor_grid();
+    if (h->cgrid < 1) { h->err = "coarse factor kernel cannot be made co-resident"; return fail(TOSOLVE_ECUDA); }
+  }
+  // PCG
+  const long nd = P.lv[0].ndof;
+  double** vec64[7] = {&h->u, &h->r, &h->p, &h->q, &h->f, &h->tmpa, &h->tmpb};
+  for (double** pv : vec64) {
+    CKC(dalloc(h, pv, nd));
+    CKC(cudaMemset(*pv, 0, nd * 8));
+  }
+  CKC(dalloc(h, &h->part, 4 * kMaxPart));
+  CKC(cudaMemset(h->part, 0, 4 * kMaxPart * 8));
+  CKC(dalloc(h, &h->ds, 1));
+  CKC(cudaMemset(h->ds, 0, sizeof(DevState)));
+  CKC(cudaMallocHost((void**)&h->hs, sizeof(DevState)));
+  std::memset(h->hs, 0, sizeof(DevState));
+  h->np = parts_for(h->lv[0].nn);
+  // host-step staging
+  h->hrhs = h->d.max_rhs;
+  CKC(dalloc(h, &h->hx, P.ncell));
+  CKC(dalloc(h, &h->hf, nd * h->hrhs));
+  CKC(dalloc(h, &h->hu, nd * h->hrhs));
+  CKC(dalloc(h, &h->hg, P.ncell));
+  CKC(cudaEventCreate(&h->ev0));
+  CKC(cudaEventCreate(&h->ev1));
+  CKC(cudaStreamSynchronize(st));
+  CKC(cudaGetLastError());
+  if (std::getenv("TOSOLVE_NO_GRAPH") == nullptr) {
+    s = build_graph(h);
+    if (s != TOSOLVE_OK) return fail(s);
+  }
+  *out = h;
+  return TOSOLVE_OK;
+#undef CKC
+}
+
+void tosolve_destroy(tosolve_t h) {
+  if (h == nullptr) return;
+  cudaStreamSynchronize(h->st);
+  free_all(h);
+  delete h;
+}
+
+const char* tosolve_last_error(tosolve_t h) {
+  if (h == nullptr) return g_err.c_str();
+  return h->err.c_str();
+}
+
+tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
+  if (h == nullptr) return set_err(h, TOSOLVE_EINVAL, "handle is NULL");
+  if (x_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "x is NULL");
+  cudaStream_t st = h->st;
+  const tosolve_desc& d = h->d;
+  const int n = d.n_mr;
+  launch_filter_fwd(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, h->invom, x_dev, d.Emin,
+                    d.E0 - d.Emin, d.penal, h->rho, h->w, st);
+  const bool fp32 = d.precision == TOSOLVE_PREC_FP32;
+  for (int l = 0; l < h->L; ++l) {
+    Level& L = h->lv[l];
+    if (l == 0) {
+      launch_elem_direct(true, L, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, st);
+      launch_assemble(true, L, h->Ke, L.S64, L.dinv64, st);
+      if (L.S32) {
+        launch_to_fp32((size_t)243 * L.nn, L.S64, L.S32, st);
+        launch_to_fp32((size_t)L.ndof, L.dinv64, L.dinv32, st);
+      }
+    } else {
+      const bool op64 = !fp32 || l == h->L - 1;
+      launch_elem_moments(op64, L, h->w, h->Dx, h->Dy, h->cmom64, h->Ke, st);
+      if (op64)
+        launch_assemble(true, L, h->Ke, L.S64, L.dinv64, st);
+      else
+        launch_assemble(false, L, h->Ke, L.S32, L.dinv32, st);
+    }
+  }
+  Level& C = h->lv[h->L - 1];
+  CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), st));
+  launch_coarse_dense(C, h->Ad, st);
+  CK(cudaMemsetAsync(&h->ds->coarse_status, 0, sizeof(int), st));
+  CK(launch_coarse_factor(h->nc, h->Ad, h->Wp, h->Dblk, h->Xinv, h->Ainv, &h->ds->coarse_status,
+                          h->cgrid, st));
+  CK(cudaGetLastError());
+  h->have_rho = true;
+  return TOSOLVE_OK;
+}
+
+static tosolve_status run_loop_nograph(tosolve_t h) {
+  // Same kernels as the graph, driven from the host (debug path).
+  const bool fp64 = prec_fp64(h);
+  Level& L0 = h->lv[0];
+  const int np = h->np;
+  double *part0 = h->part, *part1 = h->part + kMaxPart, *part2 = h->part + 2 * kMaxPart,
+         *part3 = h->part + 3 * kMaxPart;
+  cudaStream_t st = h->st;
+  launch_cg_prep(L0, h->f, h->u, h->f, h->u, part0, np, st);
+  launch_cg_residual(fp64, L0, h->f, h->u, h->r, L0.b, part1, np, st);
+  launch_cg_check_init(part0, part1, np, h->ds, 0, 0, st);
+  CK(cudaMemcpyAsync(h->hs, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  while (!h->hs->converged && h->hs->status == 0 && h->hs->iter < h->hs->maxit) {
+    launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, st);
+    launch_cg_dots_rz(fp64, L0, h->r, L0.z, h->q, part2, part3, np, st);
+    launch_cg_dir(fp64, L0, part2, part3, np, L0.z, h->p, h->ds, st);
+    launch_cg_apply(L0, h->p, h->q, part0, np, st);
+    launch_cg_update(fp64, L0, part0, np, h->u, h->r, h->p, h->q, L0.b, part1, h->ds, st);
+    launch_cg_check(part1, np, h->ds, 0, 0, st);
+    CK(cudaMemcpyAsync(h->hs, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  launch_cg_residual(fp64, L0, h->f, h->u, h->tmpa, nullptr, part1, np, st);
+  launch_cg_final(part1, np, h->ds, st);
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_solve(tosolve_t h, const double* f_dev, int nrhs, double* u_dev, double rtol,
+                             int maxit, tosolve_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  auto finish = [&](tosolve_status s) {
+    if (info) info->status = (int)s;
+    return s;
+  };
+  if (h == nullptr) return finish(set_err(h, TOSOLVE_EINVAL, "handle is NULL"));
+  if (f_dev == nullptr || u_dev == nullptr) return finish(set_err(h, TOSOLVE_EINVAL, "f or u is NULL"));
+  if (nrhs < 1 || nrhs > h->d.max_rhs) return finish(set_err(h, TOSOLVE_EINVAL, "nrhs must be in 1..max_rhs"));
+  if (!(rtol > 0.0) || maxit < 1 || maxit > 100000)
+    return finish(set_err(h, TOSOLVE_EINVAL, "need rtol > 0 and 1 <= maxit <= 100000"));
+  if (!h->have_rho) return finish(set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first"));
+  cudaStream_t st = h->st;
+  const size_t nd = h->lv[0].ndof;
+  tosolve_status result = TOSOLVE_OK;
+  int total = 0, last = 0;
+  double worst = 0.0;
+  if (cudaEventRecord(h->ev0, st) != cudaSuccess) return finish(set_err(h, TOSOLVE_ECUDA, "event record failed"));
+  for (int r = 0; r < nrhs && result == TOSOLVE_OK; ++r) {
+    const double* fr = f_dev + r * nd;
+    double* ur = u_dev + r * nd;
+    int used = 0;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      h->hs->tol2 = rtol * rtol;
+      h->hs->maxit = maxit - used;
+      if (cudaMemcpyAsync(&h->ds->tol2, &h->hs->tol2, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(&h->ds->maxit, &h->hs->maxit, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(h->f, fr, nd * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(h->u, ur, nd * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return finish(set_err(h, TOSOLVE_ECUDA, "copy into the solver failed"));
+      if (h->graph_ready) {
+        if (cudaGraphLaunch(h->gexec, st) != cudaSuccess)
+          return finish(set_err(h, TOSOLVE_ECUDA, "graph launch failed"));
+      } else {
+        const tosolve_status s2 = run_loop_nograph(h);
+        if (s2 != TOSOLVE_OK) return finish(s2);
+      }
+      CK(cudaMemcpyAsync(ur, h->u, nd * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(h->hs, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+      const cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        h->err = std::string("solve: ") + cudaGetErrorString(e);
+        return finish(TOSOLVE_ECUDA);
+      }
+      const DevState& S = *h->hs;
+      used += S.iter;
+      if (S.ff == 0.0) {  // f = 0: the solution is u = 0
+        CK(cudaMemsetAsync(ur, 0, nd * 8, st));
+        last = 0;
+        break;
+      }
+      const double rel = std::sqrt(S.rr_true / S.ff);
+      last = used;
+      if (S.status != 0) {
+        result = TOSOLVE_EBREAKDOWN;
+        h->err = S.coarse_status ? "coarse Cholesky met a non-positive pivot" : "PCG breakdown (p^T K p <= 0 or NaN)";
+        worst = std::fmax(worst, rel);
+        break;
+      }
+      if (rel <= rtol) { worst = std::fmax(worst, rel); break; }
+      if (used >= maxit || attempt == 3) {
+        worst = std::fmax(worst, rel);
+        result = TOSOLVE_ENOTCONV;
+        h->err = "maxit reached before the tolerance";
+        break;
+      }
+      // recursive residual met the tolerance but the true one did not:
+      // restart from the current iterate with a freshly computed residual
+    }
+    total += used;
+  }
+  CK(cudaEventRecord(h->ev1, st));
+  CK(cudaEventSynchronize(h->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  if (info) {
+    info->iterations = last;
+    info->total_iterations = total;
+    info->rel_residual = worst;
+    info->ms = ms;
+  }
+  return finish(result);
+}
+
+tosolve_status tosolve_compliance_grad(tosolve_t h, const double* u_dev, const double* f_dev, int nrhs,
+                                       double* c_host, double* dcdx_dev, double* dcdrho_dev) {
+  if (h == nullptr) return set_err(h, TOSOLVE_EINVAL, "handle is NULL");
+  if (u_dev == nullptr || f_dev == nullptr || c_host == nullptr) return set_err(h, TOSOLVE_EINVAL, "u, f or c is NULL");
+  if (nrhs < 1 || nrhs > h->d.max_rhs) return set_err(h, TOSOLVE_EINVAL, "nrhs must be in 1..max_rhs");
+  if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");
+  cudaStream_t st = h->st;
+  const tosolve_desc& d = h->d;
+  const size_t nd = h->lv[0].ndof;
+  double* g = h->gtmp;
+  double* gt = h->gtmp + h->ncell;
+  const bool want_grad = dcdx_dev != nullptr || dcdrho_dev != nullptr;
+  for (int r = 0; r < nrhs; ++r) {
+    launch_compliance(h->lv[0], f_dev + r * nd, u_dev + r * nd, h->part, h->np, h->ds, st);
+    CK(cudaMemcpyAsync(&h->hs->c, &h->ds->c, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c_host[r] = h->hs->c;
+    if (want_grad)
+      launch_energy_grad(h->lv[0], d.n_mr, u_dev + r * nd, h->tabsym64, h->rho, d.penal,
+                         d.E0 - d.Emin, h->Dx, h->Dy, r == 0, g, st);
+  }
+  if (dcdrho_dev) CK(cudaMemcpyAsync(dcdrho_dev, g, (size_t)h->ncell * 8, cudaMemcpyDeviceToDevice, st));
+  if (dcdx_dev) {
+    launch_scale((size_t)h->ncell, g, h->invom, gt, st);
+    launch_filter_T(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, gt, dcdx_dev, st);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_step_host(tosolve_t h, const double* x_host, const double* f_host, int nrhs,
+                                 double rtol, int maxit, int warm, double* u_host, double* c_host,
+                                 double* dcdx_host, tosolve_info* info) {
+  if (h == nullptr) return set_err(h, TOSOLVE_EINVAL, "handle is NULL");
+  if (x_host == nullptr || f_host == nullptr || c_host == nullptr) return set_err(h, TOSOLVE_EINVAL, "x, f or c is NULL");
+  if (nrhs < 1 || nrhs > h->hrhs) return set_err(h, TOSOLVE_EINVAL, "nrhs must be in 1..max_rhs");
+  cudaStream_t st = h->st;
+  const size_t nd = h->lv[0].ndof;
+  CK(cudaMemcpyAsync(h->hx, x_host, (size_t)h->ncell * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->hf, f_host, nd * nrhs * 8, cudaMemcpyHostToDevice, st));
+  if (!h->have_u || !warm) {
+    CK(cudaMemsetAsync(h->hu, 0, nd * h->hrhs * 8, st));
+    h->have_u = true;
+  }
+  tosolve_status s = tosolve_set_densities(h, h->hx);
+  if (s != TOSOLVE_OK) return s;
+  s = tosolve_solve(h, h->hf, nrhs, h->hu, rtol, maxit, info);
+  if (s != TOSOLVE_OK && s != TOSOLVE_ENOTCONV) return s;
+  const tosolve_status s2 = tosolve_compliance_grad(h, h->hu, h->hf, nrhs, c_host,
+                                                    dcdx_host ? h->hg : nullptr, nullptr);
+  if (s2 != TOSOLVE_OK) return s2;
+  if (u_host) CK(cudaMemcpyAsync(u_host, h->hu, nd * nrhs * 8, cudaMemcpyDeviceToHost, st));
+  if (dcdx_host) CK(cudaMemcpyAsync(dcdx_host, h->hg, (size_t)h->ncell * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return s;
+}
+
+tosolve_status tosolve_level_dims(tosolve_t h, int level, int* dims) {
+  if (h == nullptr || dims == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
+  if (level < 0 || level >= h->L) return set_err(h, TOSOLVE_EINVAL, "level out of range");
+  dims[0] = h->lv[level].Lx;
+  dims[1] = h->lv[level].Ly;
+  dims[2] = h->lv[level].Lz;
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_subcell_table(tosolve_t h, double* table_dev) {
+  if (h == nullptr || table_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
+  CK(cudaMemcpyAsync(table_dev, h->tab64, (size_t)h->m * 576 * 8, cudaMemcpyDeviceToDevice, h->st));
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_densities(tosolve_t h, double* rho_dev, double* w_dev) {
+  if (h == nullptr) return set_err(h, TOSOLVE_EINVAL, "handle is NULL");
+  if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");
+  if (rho_dev) CK(cudaMemcpyAsync(rho_dev, h->rho, (size_t)h->ncell * 8, cudaMemcpyDeviceToDevice, h->st));
+  if (w_dev) CK(cudaMemcpyAsync(w_dev, h->w, (size_t)h->ncell * 8, cudaMemcpyDeviceToDevice, h->st));
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double* x_dev, double* y_dev) {
+  if (h == nullptr || x_dev == nullptr || y_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
+  if (level < 0 || level >= h->L) return set_err(h, TOSOLVE_EINVAL, "level out of range");
+  if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");
+  const Level& L = h->lv[level];
+  if (precision == 0) {
+    if (!L.S64) return set_err(h, TOSOLVE_EINVAL, "this level has no FP64 operator");
+    launch_apply_diag(true, L, x_dev, y_dev, h->st);
+  } else if (precision == 1) {
+    if (!L.S32) return set_err(h, TOSOLVE_EINVAL, "this level has no FP32 operator");
+    launch_apply_diag(false, L, x_dev, y_dev, h->st);
+  } else {
+    return set_err(h, TOSOLVE_EINVAL, "precision must be 0 or 1");
+  }
+  CK(cudaGetLastError());
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_precondition(tosolve_t h, const double* b_dev, double* z_dev) {
+  if (h == nullptr || b_dev == nullptr || z_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
+  if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");
+  const bool fp64 = prec_fp64(h);
+  Level& L0 = h->lv[0];
+  if (fp64)
+    CK(cudaMemcpyAsync(L0.b, b_dev, (size_t)L0.ndof * 8, cudaMemcpyDeviceToDevice, h->st));
+  else
+    launch_cast(false, (size_t)L0.ndof, b_dev, L0.b, true, h->st);
+  launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, h->st);
+  launch_cast(true, (size_t)L0.ndof, L0.z, z_dev, fp64, h->st);
+  CK(cudaGetLastError());
+  return TOSOLVE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+"""Python binding of the tosolve C ABI (include/tosolve.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels
+of libtosolve.so.  Functions keep the C names; device buffers are passed as
+torch CUDA tensors (or raw integer addresses) and streams as torch streams.
+There is no CPU fallback: if the library is missing, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libtosolve.so")
+
+OK, EINVAL, ENOMEM, ENOTCONV, EBREAKDOWN, ECUDA = range(6)
+PREC_FP64, PREC_FP32 = 0, 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "EBREAKDOWN", 5: "ECUDA"}
+
+
+class tosolve_desc(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("degree", C.c_int), ("n_mr", C.c_int), ("d_mr", C.c_int),
+        ("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double),
+        ("penal", C.c_double), ("rmin", C.c_double),
+        ("mg_levels", C.c_int), ("precision", C.c_int),
+        ("omega", C.c_double), ("cycle_gamma", C.c_int), ("max_rhs", C.c_int),
+    ]
+
+
+class tosolve_info(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int), ("total_iterations", C.c_int),
+        ("rel_residual", C.c_double), ("ms", C.c_double), ("status", C.c_int),
+    ]
+
+
+class TosolveError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(
+            f"{_LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+            "(the solver has no CPU fallback)")
+    lib = C.CDLL(_LIB_PATH)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    P = C.POINTER
+    sigs = {
+        "tosolve_create": ([P(tosolve_desc), vp, vp, P(vp)], i),
+        "tosolve_footprint": ([P(tosolve_desc), P(sz)], i),
+        "tosolve_set_densities": ([vp, vp], i),
+        "tosolve_solve": ([vp, vp, i, vp, d, i, P(tosolve_info)], i),
+        "tosolve_compliance_grad": ([vp, vp, vp, i, P(d), vp, vp], i),
+        "tosolve_step_host": ([vp, vp, vp, i, d, i, i, vp, P(d), vp, P(tosolve_info)], i),
+        "tosolve_level_dims": ([vp, i, P(i)], i),
+        "tosolve_subcell_table": ([vp, vp], i),
+        "tosolve_densities": ([vp, vp, vp], i),
+        "tosolve_apply": ([vp, i, i, vp, vp], i),
+        "tosolve_precondition": ([vp, vp, vp], i),
+        "tosolve_last_error": ([vp], C.c_char_p),
+        "tosolve_destroy": ([vp], None),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _check(h, status: int, what: str):
+    if status != OK:
+        msg = _lib.tosolve_last_error(h)
+        raise TosolveError(status, f"{what}: {msg.decode() if msg else ''}")
+
+
+def make_desc(nx, ny, nz, *, degree=1, n_mr=1, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0, rmin=0.0,
+              mg_levels=0, precision=PREC_FP64, omega=0.5, cycle_gamma=1, max_rhs=1) -> tosolve_desc:
+    return tosolve_desc(nx, ny, nz, degree, n_mr, n_mr, E0, Emin, nu, penal, rmin, mg_levels,
+                        precision, omega, cycle_gamma, max_rhs)
+
+
+# ---- the C ABI, same names ----------------------------------------------------
+
+def tosolve_footprint(desc: tosolve_desc) -> int:
+    out = C.c_size_t(0)
+    _check(None, _lib.tosolve_footprint(C.byref(desc), C.byref(out)), "tosolve_footprint")
+    return out.value
+
+
+def tosolve_create(desc: tosolve_desc, mask: np.ndarray, stream=None) -> int:
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    h = C.c_void_p(0)
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    _check(None, _lib.tosolve_create(C.byref(desc), mask.ctypes.data, st, C.byref(h)),
+           "tosolve_create")
+    return h.value
+
+
+def tosolve_destroy(h) -> None:
+    _lib.tosolve_destroy(h)
+
+
+def tosolve_set_densities(h, x_dev) -> None:
+    _check(h, _lib.tosolve_set_densities(h, _ptr(x_dev)), "tosolve_set_densities")
+
+
+def tosolve_solve(h, f_dev, nrhs: int, u_dev, rtol: float, maxit: int, raise_on_error=True):
+    info = tosolve_info()
+    s = _lib.tosolve_solve(h, _ptr(f_dev), nrhs, _ptr(u_dev), rtol, maxit, C.byref(info))
+    if raise_on_error:
+        _check(h, s, "tosolve_solve")
+    return info
+
+
+def tosolve_compliance_grad(h, u_dev, f_dev, nrhs: int, dcdx_dev=None, dcdrho_dev=None):
+    c = (C.c_double * nrhs)()
+    _check(h, _lib.tosolve_compliance_grad(h, _ptr(u_dev), _ptr(f_dev), nrhs, c, _ptr(dcdx_dev),
+                                           _ptr(dcdrho_dev)), "tosolve_compliance_grad")
+    return np.array(c[:])
+
+
+def tosolve_step_host(h, x_host: np.ndarray, f_host: np.ndarray, nrhs: int, rtol: float, maxit: int,
+                      warm: int = 0, u_host: np.ndarray | None = None,
+                      dcdx_host: np.ndarray | None = None):
+    c = (C.c_double * nrhs)()
+    info = tosolve_info()
+    s = _lib.tosolve_step_host(h, _ptr(x_host), _ptr(f_host), nrhs, rtol, maxit, warm, _ptr(u_host),
+                               c, _ptr(dcdx_host), C.byref(info))
+    _check(h, s, "tosolve_step_host")
+    return np.array(c[:]), info
+
+
+def tosolve_level_dims(h, level: int):
+    dims = (C.c_int * 3)()
+    _check(h, _lib.tosolve_level_dims(h, level, dims), "tosolve_level_dims")
+    return tuple(dims[:])
+
+
+def tosolve_subcell_table(h, table_dev) -> None:
+    _check(h, _lib.tosolve_subcell_table(h, _ptr(table_dev)), "tosolve_subcell_table")
+
+
+def tosolve_densities(h, rho_dev=None, w_dev=None) -> None:
+    _check(h, _lib.tosolve_densities(h, _ptr(rho_dev), _ptr(w_dev)), "tosolve_densities")
+
+
+def tosolve_apply(h, level: int, precision: int, x_dev, y_dev) -> None:
+    _check(h, _lib.tosolve_apply(h, level, precision, _ptr(x_dev), _ptr(y_dev)), "tosolve_apply")
+
+
+def tosolve_precondition(h, b_dev, z_dev) -> None:
+    _check(h, _lib.tosolve_precondition(h, _ptr(b_dev), _ptr(z_dev)), "tosolve_precondition")
+
+
+def tosolve_last_error(h) -> str:
+    msg = _lib.tosolve_last_error(h)
+    return msg.decode() if msg else ""
+
+
+class Solver:
+    """Owns one handle; a convenience wrapper used by the tests and the
+    benchmark (each method is one ABI call)."""
+
+    def __init__(self, desc: tosolve_desc, mask: np.ndarray, stream=None):
+        self.desc = desc
+        self.h = tosolve_create(desc, mask, stream)
+
+    def close(self):
+        if self.h:
+            tosolve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
