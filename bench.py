@@ -73,7 +73,7 @@ class ClockSampler:
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -109,48 +109,47 @@ class ClockSampler:
 
 # ---- CPU oracle (reference arm and cpu_baseline) ------------------------------
 
-def oracle_step_seconds() -> tuple[float, int, int]:
-    """One full oracle step on the workload, in a fresh single-threaded
-    process (spawned: never forked from a CUDA process)."""
+def oracle_steps(steps: int, warmup: int) -> tuple[list, int, int]:
+    """Times `steps` full oracle steps (after `warmup` untimed ones) on the
+    workload, in one fresh single-threaded process (spawned: never forked
+    from a CUDA process).  Returns per-step seconds, free DOFs, load cases."""
     code = (
         "import os,sys,time; sys.path.insert(0, %r)\n"
-        "import bench, numpy as np\n"
+        "import bench\n"
         "from oracle import fe\n"
         "p = bench.problem()\n"
-        "t = time.perf_counter()\n"
-        "m = fe.Model(p)\n"
-        "out = m.run(method='mg', rtol=%r, levels=%d)\n"
-        "dt = time.perf_counter() - t\n"
-        "print(dt, p.nfree, p.nrhs)\n" % (ROOT, WORKLOAD["rtol"], WORKLOAD["levels"]))
+        "def one():\n"
+        "    t = time.perf_counter()\n"
+        "    m = fe.Model(p)\n"
+        "    m.run(method='mg', rtol=%r, levels=%d)\n"
+        "    return time.perf_counter() - t\n"
+        "for _ in range(%d): one()\n"
+        "ts = [one() for _ in range(%d)]\n"
+        "print(' '.join(map(repr, ts)), p.nfree, p.nrhs)\n"
+        % (ROOT, WORKLOAD["rtol"], WORKLOAD["levels"], warmup, steps))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       cwd=ROOT, timeout=900)
+                       cwd=ROOT, timeout=3600)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
-    dt, nfree, nrhs = r.stdout.split()[-3:]
-    return float(dt), int(nfree), int(nrhs)
+    parts = r.stdout.split()
+    return [float(v) for v in parts[:-2]], int(parts[-2]), int(parts[-1])
 
 
 def cpu_baseline_entry():
-    dt, nfree, nrhs = oracle_step_seconds()
-    return {"value": nfree * nrhs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one full oracle step (filter, assembly, MG hierarchy, MG-PCG to 1e-8, "
-                      "gradient) on the exact benchmark input, single-threaded, "
-                      f"{dt:.1f} s"}
+    ts, nfree, nrhs = oracle_steps(1, 1)
+    return {"value": nfree * nrhs / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one full oracle step (filter, assembly, every MG level's operator, "
+                      "dense Cholesky, MG-PCG to 1e-8, compliance, gradient) on the exact "
+                      f"benchmark input after one warm-up step, single-threaded: {ts[0]:.2f} s"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_step_seconds()
-    times = []
-    nfree = nrhs = 1
-    for _ in range(args.steps):
-        dt, nfree, nrhs = oracle_step_seconds()
-        times.append(dt)
+    times, nfree, nrhs = oracle_steps(args.steps, args.warmup)
     T = sum(times)
     value = nfree * nrhs * len(times) / T
     line = {
@@ -160,7 +159,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "precision": "fp64 (CPU oracle, scipy sparse)"},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
-                         "sample": "full oracle step on the benchmark input per step"},
+                         "sample": "each step: one full oracle step on the exact benchmark input"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -247,13 +246,11 @@ def run_gpu(args):
 
     sampler = ClockSampler(local)
     out = {}
-    for label, prec in (("mixed", T.PREC_FP32), ("fp64", T.PREC_FP64)):
-        s = make(prec)
-        if label == "mixed":
-            sampler.start()
+    solvers = {"mixed": make(T.PREC_FP32), "fp64": make(T.PREC_FP64)}
+    sampler.start()
+    for label in ("mixed", "fp64"):
+        s = solvers[label]
         ms, infos, wall = timed(s, args.steps, args.warmup)
-        if label == "mixed":
-            clocks = sampler.stop()
         tot = sum(ms)
         if world > 1:
             t = torch.tensor([tot], device=dev, dtype=torch.float64)
@@ -261,6 +258,31 @@ def run_gpu(args):
             tot = float(t.item())
         solve_ms = sorted(i[3] for i in infos)
         out[label] = dict(ms=ms, tot=tot, infos=infos, wall=wall, solve_ms=solve_ms, solver=s)
+    clocks = sampler.stop()
+
+    # per-phase device time (separate untimed pass, same step)
+    phases = {}
+    for label in ("mixed", "fp64"):
+        s = solvers[label]
+        acc = {"set_densities": 0.0, "solve": 0.0, "gradient": 0.0}
+        nph = 5
+        with torch.cuda.stream(stream):
+            for _ in range(nph):
+                flush.zero_()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                ev[0].record(stream)
+                T.tosolve_set_densities(s.h, x)
+                u.zero_()
+                ev[1].record(stream)
+                T.tosolve_solve(s.h, f, 1, u, rtol, maxit)
+                ev[2].record(stream)
+                T.tosolve_compliance_grad(s.h, u, f, 1, gx)
+                ev[3].record(stream)
+                stream.synchronize()
+                acc["set_densities"] += ev[0].elapsed_time(ev[1]) / nph
+                acc["solve"] += ev[1].elapsed_time(ev[2]) / nph
+                acc["gradient"] += ev[2].elapsed_time(ev[3]) / nph
+        phases[label] = {k: round(v, 4) for k, v in acc.items()}
     free_dofs = p.nfree * p.nrhs
     mixed = out["mixed"]
     fp64 = out["fp64"]
@@ -339,6 +361,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}"},
         "fp64_value": fp64_value, "speedup_vs_fp64": value / fp64_value,
         "fp64_ms_per_step": fp64["tot"] / args.steps,
+        "phase_ms": phases,
         "pcg_iterations": {"mixed": statistics.median(its), "fp64": statistics.median(its64)},
         "true_rel_residual_max": res,
         "solve_latency_ms": {"p50": pct(mixed["solve_ms"], 0.5), "p99": pct(mixed["solve_ms"], 0.99),
@@ -372,11 +395,16 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the PCG loop from the host (same kernels, no CUDA graph): "
+                         "ncu cannot profile kernels inside a graph with a conditional node")
     args = ap.parse_args()
+    if args.host_loop:
+        os.environ["TOSOLVE_NO_GRAPH"] = "1"
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -18,6 +18,8 @@ Conventions (shared with the C ABI by documentation only, not by code):
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 from numpy.polynomial import polynomial as npoly
 from numpy.polynomial import legendre as nleg
@@ -102,6 +104,13 @@ def strain_displacement(dNdx: np.ndarray) -> np.ndarray:
 
 
 def subcell_stiffness(k: int, n: int, nu: float, h: float = 1.0) -> np.ndarray:
+    """The stacked subcell stiffness table of Eq. matrixK_mr (a fresh copy of
+    the memoised table: Section 3.3 computes it once for a regular mesh)."""
+    return _subcell_stiffness(int(k), int(n), float(nu), float(h)).copy()
+
+
+@functools.lru_cache(maxsize=32)
+def _subcell_stiffness(k: int, n: int, nu: float, h: float) -> np.ndarray:
     """The stacked subcell stiffness table of Eq. matrixK_mr.
 
     K[i] = int over subcell i of B^T D B dx (E = 1), for the n^3 subcells of a

@@ -25,7 +25,8 @@ constexpr int kMaxPart = 608;  // partial sums per reduction (4 blocks per SM)
 constexpr int kMaxLevels = 8;
 constexpr int kEdofQ1 = 24;    // DOFs of a trilinear hexahedron
 constexpr int kSym = 300;      // entries of a 24x24 symmetric upper triangle
-constexpr int kNB = 32;        // block size of the coarse Cholesky
+constexpr int kNB = 16;        // block size of the coarse Cholesky
+constexpr int kTile = 32;      // output tile of the coarse inverse product
 constexpr int kMaxCoarse = 4096;  // largest coarse system (DOFs)
 
 // Scalars of the PCG loop, kept on the device so the loop runs as a CUDA
@@ -87,7 +88,7 @@ void launch_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* off, const 
 void launch_elem_direct(bool fp64, const Level& L, int n, const double* w, int Dx, int Dy,
                         const double* tabsym, void* Ke, cudaStream_t st);
 void launch_elem_moments(bool fp64, const Level& L, const double* w, int Dx, int Dy,
-                         const double* cmom, void* Ke, cudaStream_t st);
+                         const double* cmom, void* Mscr, void* Ke, cudaStream_t st);
 void launch_assemble(bool fp64, const Level& L, const void* Ke, void* S, void* dinv,
                      cudaStream_t st);
 void launch_to_fp32(size_t n, const double* a, float* b, cudaStream_t st);
@@ -101,25 +102,21 @@ template <typename T>
 LevelView<T> view(const Level& L);
 void launch_vcycle(bool fp64, Level* lv, int L, double omega, int gamma, const double* Ainv,
                    cudaStream_t st);
-void launch_cg_prep(const Level& L0, const double* fin, const double* uin, double* f,
-                    double* u, double* part, int np, cudaStream_t st);
-void launch_cg_residual(bool fp64, const Level& L0, const double* f, const double* u,
-                        double* r, void* b0, double* part, int np, cudaStream_t st);
-void launch_cg_check_init(double* part_ff, double* part_rr, int np, DevState* ds,
-                          cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st);
-void launch_cg_dots_rz(bool fp64, const Level& L0, const double* r, const void* z,
-                       const double* q, double* part_rz, double* part_zq, int np,
-                       cudaStream_t st);
-void launch_cg_dir(bool fp64, const Level& L0, const double* part_rz, const double* part_zq,
-                   int np, const void* z, double* p, DevState* ds, cudaStream_t st);
-void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np,
-                     cudaStream_t st);
-void launch_cg_update(bool fp64, const Level& L0, const double* part_pq, int np, double* u,
-                      double* r, const double* p, const double* q, void* b0, double* part_rr,
-                      DevState* ds, cudaStream_t st);
-void launch_cg_check(const double* part_rr, int np, DevState* ds,
-                     cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st);
-void launch_cg_final(const double* part_rr, int np, DevState* ds, cudaStream_t st);
+void launch_smooth0(bool fp64, const Level& L0, double omega, cudaStream_t st);
+void launch_cg_prep(const Level& L0, double* f, double* u, double* part, int np, cudaStream_t st);
+void launch_cg_residual(bool fp64, const Level& L0, double omega, const double* f, const double* u,
+                        double* r, int mode, double* part, const double* part_ff, int np,
+                        DevState* ds, unsigned* cnt, cudaGraphConditionalHandle hc, int use_cond,
+                        cudaStream_t st);
+void launch_cg_dots_rz(bool fp64, const Level& L0, const double* r, const double* q, double* part_rz,
+                       double* part_zq, int np, DevState* ds, unsigned* cnt, cudaStream_t st);
+void launch_cg_dir(bool fp64, const Level& L0, double* p, int np, const DevState* ds,
+                   cudaStream_t st);
+void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np, DevState* ds,
+                     unsigned* cnt, cudaStream_t st);
+void launch_cg_update(bool fp64, const Level& L0, double omega, double* u, double* r, const double* p,
+                      const double* q, double* part_rr, int np, DevState* ds, unsigned* cnt,
+                      cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st);
 void launch_apply_diag(bool fp64, const Level& L, const double* x, double* y, cudaStream_t st);
 void launch_cast(bool to_fp64, size_t n, const void* a, void* b, bool src_fp64,
                  cudaStream_t st);
@@ -134,9 +131,11 @@ void launch_filter_T(int Dx, int Dy, int Dz, int noff, const int4* off, const do
 void launch_compliance(const Level& L0, const double* f, const double* u, double* part, int np,
                        DevState* ds, cudaStream_t st);
 
-inline int parts_for(int nn) {
-  int g = (nn + kBS - 1) / kBS;
-  return g < kMaxPart ? (g < 1 ? 1 : g) : kMaxPart;
+// Blocks of the node-parallel solve kernels (64 nodes per block); also the
+// number of partial sums their reductions produce.
+inline int parts_for(long nn) {
+  long g = (nn + 63) / 64;
+  return (int)(g < kMaxPart ? (g < 1 ? 1 : g) : kMaxPart);
 }
 
 __host__ __device__ inline int sym_index(int r, int c) {
@@ -150,6 +149,8 @@ __host__ __device__ inline int sym_index(int r, int c) {
 struct tosolve_s {
   tosolve_desc d;
   cudaStream_t st = nullptr;
+  cudaStream_t st2 = nullptr;  // coarse-level chain of the refresh
+  cudaEvent_t evf = nullptr, evj = nullptr;
   bool own_stream = false;
   int dev = 0;
   int L = 1;
@@ -169,6 +170,9 @@ struct tosolve_s {
   double* tabsym64 = nullptr;  // m x 300
   double* cmom64 = nullptr;    // 27 x 300
   void* Ke = nullptr;
+  double* Kec = nullptr;  // element matrices of the coarsest level (second stream)
+  double* Mom = nullptr;   // 27 moments per element, finer coarse levels
+  double* Momc = nullptr;  // 27 moments per element, coarsest level
   // coarse level
   int nc = 0;
   double* Ad = nullptr;
@@ -181,6 +185,7 @@ struct tosolve_s {
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *f = nullptr;
   double *tmpa = nullptr, *tmpb = nullptr;
   double* part = nullptr;  // 4 x kMaxPart
+  unsigned* cnt = nullptr; // last-block counters of the fused reductions (4)
   int np = 1;
   tos::DevState* ds = nullptr;
   tos::DevState* hs = nullptr;  // pinned mirror

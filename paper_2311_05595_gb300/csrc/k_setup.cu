@@ -149,23 +149,36 @@ __global__ void k_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* __res
 }
 
 // Fine-level element matrices, Eq. matrixK_mr: K^(e) = sum_i w_{e,i} K^(e_i),
-// upper triangle.  One block per element; FP64 accumulation.
+// upper triangle.  A block handles epb consecutive elements (their weights
+// staged in shared memory); consecutive threads write consecutive entries.
+// FP64 accumulation.
 template <typename T>
-__global__ void k_elem_direct(int ex, int ey, int ez, int n, const double* __restrict__ w, int Dx,
-                              int Dy, const double* __restrict__ tabsym, T* __restrict__ Ke) {
-  __shared__ double ws[512];
+__global__ void k_elem_direct(int ex, int ey, int ez, int n, int epb, const double* __restrict__ w,
+                              int Dx, int Dy, const double* __restrict__ tabsym, T* __restrict__ Ke) {
+  extern __shared__ double ws[];  // epb * m
   const int m = n * n * n;
-  const long e = blockIdx.x;
-  const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
-  for (int s = threadIdx.x; s < m; s += blockDim.x) {
-    const int a = s % n, b = (s / n) % n, c = s / (n * n);
-    ws[s] = w[(n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c))];
+  const long E = (long)ex * ey * ez;
+  const long e0 = (long)blockIdx.x * epb;
+  for (int t = threadIdx.x; t < epb * m; t += blockDim.x) {
+    const int q = t / m, s = t % m;
+    const long e = e0 + q;
+    double v = 0.0;
+    if (e < E) {
+      const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+      const int a = s % n, b = (s / n) % n, c = s / (n * n);
+      v = w[(n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c))];
+    }
+    ws[t] = v;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < kSym; t += blockDim.x) {
+  for (int t = threadIdx.x; t < epb * kSym; t += blockDim.x) {
+    const int q = t / kSym, k = t % kSym;
+    const long e = e0 + q;
+    if (e >= E) continue;
+    const double* wq = ws + q * m;
     double acc = 0.0;
-    for (int s = 0; s < m; ++s) acc += ws[s] * tabsym[(size_t)s * kSym + t];
-    Ke[e * kSym + t] = (T)acc;
+    for (int s = 0; s < m; ++s) acc += wq[s] * tabsym[(size_t)s * kSym + k];
+    Ke[e * kSym + k] = (T)acc;
   }
 }
 
@@ -173,38 +186,84 @@ __global__ void k_elem_direct(int ex, int ey, int ez, int n, const double* __res
 // covers N^3 density cells; K^(e) = (h/2) sum_alpha M_alpha C_alpha with the
 // 27 polynomial moments M_alpha of the cellwise-constant weights.  This is
 // Eq. matrixK_mr with N^3 subcells evaluated exactly through the moments.
-// One block per element.
-template <typename T, typename Acc>
-__global__ void k_elem_moments(int ex, int ey, int ez, int N, double h, const double* __restrict__ w,
-                               int Dx, int Dy, const double* __restrict__ cmom, T* __restrict__ Ke) {
+//
+// Moments are separable: for each row of cells along x, three sums
+// sum_a w mu_k(a) (3 FMAs per cell), then 27 products with mu_l(b) mu_m(c)
+// per row.  mu_k(a) = int over the a-th of N intervals of xi^k.
+template <typename Acc>
+__device__ __forceinline__ void row_moments(const double* __restrict__ w, long rowbase, int N,
+                                            int b, int c, const Acc* mu0, const Acc* mu1,
+                                            const Acc* mu2, Acc acc[27]) {
+  Acc s0 = 0, s1 = 0, s2 = 0;
+  for (int a = 0; a < N; ++a) {
+    const Acc wv = (Acc)w[rowbase + a];
+    s0 += wv * mu0[a];
+    s1 += wv * mu1[a];
+    s2 += wv * mu2[a];
+  }
+  const Acc sx[3] = {s0, s1, s2};
+  const Acc my[3] = {mu0[b], mu1[b], mu2[b]};
+  const Acc mz[3] = {mu0[c], mu1[c], mu2[c]};
+#pragma unroll
+  for (int gz = 0; gz < 3; ++gz)
+#pragma unroll
+    for (int gy = 0; gy < 3; ++gy)
+#pragma unroll
+      for (int gx = 0; gx < 3; ++gx) acc[gx + 3 * (gy + 3 * gz)] += sx[gx] * my[gy] * mz[gz];
+}
+
+template <typename Acc>
+__device__ __forceinline__ void fill_mu(int N, Acc* mu0, Acc* mu1, Acc* mu2) {
+  for (int a = threadIdx.x; a < N; a += blockDim.x) {
+    const double t0 = -1.0 + 2.0 * a / N, t1 = -1.0 + 2.0 * (a + 1) / N;
+    mu0[a] = (Acc)(t1 - t0);
+    mu1[a] = (Acc)(0.5 * (t1 * t1 - t0 * t0));
+    mu2[a] = (Acc)((t1 * t1 * t1 - t0 * t0 * t0) / 3.0);
+  }
+}
+
+// Moments of small elements (N <= 4): one thread per element.
+template <typename Acc>
+__global__ void k_moments_thread(int ex, int ey, int ez, int N, const double* __restrict__ w, int Dx,
+                                 int Dy, Acc* __restrict__ M) {
+  __shared__ Acc mu[3][4];
+  fill_mu<Acc>(N, mu[0], mu[1], mu[2]);
+  __syncthreads();
+  const long E = (long)ex * ey * ez;
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+  Acc acc[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) acc[q] = 0;
+  for (int c = 0; c < N; ++c)
+    for (int b = 0; b < N; ++b) {
+      const long rowbase = (N * exi) + (long)Dx * ((N * eyi + b) + (long)Dy * (N * ezi + c));
+      row_moments<Acc>(w, rowbase, N, b, c, mu[0], mu[1], mu[2], acc);
+    }
+#pragma unroll
+  for (int q = 0; q < 27; ++q) M[e * 27 + q] = acc[q];
+}
+
+// Moments of larger elements: one block per element, one thread per row of
+// cells, warp-shuffle then shared-memory reduction (fixed order).
+template <typename Acc>
+__global__ void k_moments_block(int ex, int ey, int ez, int N, const double* __restrict__ w, int Dx,
+                                int Dy, Acc* __restrict__ M) {
   __shared__ Acc mu[3][1024];
   __shared__ Acc red[32][27];
-  __shared__ Acc M[27];
   const long e = blockIdx.x;
   const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
   const int tid = threadIdx.x;
-  for (int a = tid; a < N; a += blockDim.x) {
-    const double t0 = -1.0 + 2.0 * a / N, t1 = -1.0 + 2.0 * (a + 1) / N;
-    mu[0][a] = (Acc)(t1 - t0);
-    mu[1][a] = (Acc)(0.5 * (t1 * t1 - t0 * t0));
-    mu[2][a] = (Acc)((t1 * t1 * t1 - t0 * t0 * t0) / 3.0);
-  }
+  fill_mu<Acc>(N, mu[0], mu[1], mu[2]);
   __syncthreads();
   Acc acc[27];
 #pragma unroll
   for (int q = 0; q < 27; ++q) acc[q] = 0;
-  const long ncell = (long)N * N * N;
-  for (long s = tid; s < ncell; s += blockDim.x) {
-    const int a = s % N, b = (s / N) % N, c = s / ((long)N * N);
-    const Acc wv = (Acc)w[(N * exi + a) + (long)Dx * ((N * eyi + b) + (long)Dy * (N * ezi + c))];
-#pragma unroll
-    for (int gz = 0; gz < 3; ++gz)
-#pragma unroll
-      for (int gy = 0; gy < 3; ++gy) {
-        const Acc wyz = wv * mu[gy][b] * mu[gz][c];
-#pragma unroll
-        for (int gx = 0; gx < 3; ++gx) acc[gx + 3 * (gy + 3 * gz)] += wyz * mu[gx][a];
-      }
+  for (long rr = tid; rr < (long)N * N; rr += blockDim.x) {
+    const int b = rr % N, c = rr / N;
+    const long rowbase = (N * exi) + (long)Dx * ((N * eyi + b) + (long)Dy * (N * ezi + c));
+    row_moments<Acc>(w, rowbase, N, b, c, mu[0], mu[1], mu[2], acc);
   }
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
@@ -217,67 +276,90 @@ __global__ void k_elem_moments(int ex, int ey, int ez, int N, double h, const do
   if (tid < 27) {
     Acc s = 0;
     for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) s += red[wi][tid];
-    M[tid] = s;
+    M[e * 27 + tid] = s;
   }
+}
+
+// K^(e) = (h/2) M_e C for 32 elements per block: C (27 x 300) staged once in
+// shared memory, consecutive threads write consecutive entries.
+template <typename T, typename Acc>
+__global__ void k_moments_to_ke(long E, double h, const Acc* __restrict__ M,
+                                const double* __restrict__ cmom, T* __restrict__ Ke) {
+  extern __shared__ unsigned char smraw[];
+  Acc* cm = (Acc*)smraw;       // 27 * kSym
+  Acc* Ms = cm + 27 * kSym;    // 32 * 27
+  const long e0 = blockIdx.x * 32L;
+  const int ne = (int)min(32L, E - e0);
+  for (int t = threadIdx.x; t < 27 * kSym; t += blockDim.x) cm[t] = (Acc)cmom[t];
+  for (int t = threadIdx.x; t < ne * 27; t += blockDim.x) Ms[t] = M[e0 * 27 + t];
   __syncthreads();
-  for (int t = tid; t < kSym; t += blockDim.x) {
-    Acc s = 0;
+  const Acc half = (Acc)(0.5 * h);
+  for (int o = threadIdx.x; o < ne * kSym; o += blockDim.x) {
+    const int q = o / kSym, k = o % kSym;
+    const Acc* Mq = Ms + q * 27;
+    Acc s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
-    for (int q = 0; q < 27; ++q) s += M[q] * (Acc)cmom[q * kSym + t];
-    Ke[e * kSym + t] = (T)((Acc)(0.5 * h) * s);
+    for (int a = 0; a < 27; a += 3) {
+      s0 += Mq[a] * cm[a * kSym + k];
+      s1 += Mq[a + 1] * cm[(a + 1) * kSym + k];
+      s2 += Mq[a + 2] * cm[(a + 2) * kSym + k];
+    }
+    Ke[(e0 + q) * kSym + k] = (T)(half * ((s0 + s1) + s2));
   }
 }
 
 // Node-centred assembly of the 27-point block stencil from the element
-// matrices around each node (gather, fixed order: deterministic).  Fixed DOFs
-// get identity rows and zero columns.  Also writes the inverse diagonal.
+// matrices around each node (gather, fixed order: deterministic).  One
+// thread per (neighbour block o, node), node fastest, so each of its 9
+// stores is coalesced.  Fixed DOFs get identity rows and zero columns; the
+// centre block also writes the inverse diagonal.
 template <typename T>
 __global__ void k_assemble(int ex, int ey, int ez, int Lx, int Ly, int Lz, const T* __restrict__ Ke,
                            const uint8_t* __restrict__ mask, T* __restrict__ S, T* __restrict__ dinv) {
   const long nn = (long)Lx * Ly * Lz;
-  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
-       node += (long)gridDim.x * blockDim.x) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < 27 * nn;
+       t += (long)gridDim.x * blockDim.x) {
+    const int o = (int)(t / nn);
+    const long node = t % nn;
     const int i = node % Lx, j = (node / Lx) % Ly, l = node / ((long)Lx * Ly);
-    for (int o = 0; o < 27; ++o) {
-      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-      const int ii = i + dx, jj = j + dy, ll = l + dz;
-      const bool valid = ii >= 0 && ii < Lx && jj >= 0 && jj < Ly && ll >= 0 && ll < Lz;
-      double acc[9];
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int ii = i + dx, jj = j + dy, ll = l + dz;
+    const bool valid = ii >= 0 && ii < Lx && jj >= 0 && jj < Ly && ll >= 0 && ll < Lz;
+    double acc[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-      if (valid) {
-        const int x0 = max(dx == 1 ? i : i - 1, 0), x1 = min(dx == -1 ? i - 1 : i, ex - 1);
-        const int y0 = max(dy == 1 ? j : j - 1, 0), y1 = min(dy == -1 ? j - 1 : j, ey - 1);
-        const int z0 = max(dz == 1 ? l : l - 1, 0), z1 = min(dz == -1 ? l - 1 : l, ez - 1);
-        for (int ez_ = z0; ez_ <= z1; ++ez_)
-          for (int ey_ = y0; ey_ <= y1; ++ey_)
-            for (int ex_ = x0; ex_ <= x1; ++ex_) {
-              const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
-              const int a = (i - ex_) + 2 * ((j - ey_) + 2 * (l - ez_));
-              const int b = (ii - ex_) + 2 * ((jj - ey_) + 2 * (ll - ez_));
-              const T* base = Ke + e * kSym;
+    for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+    if (valid) {
+      const int x0 = max(dx == 1 ? i : i - 1, 0), x1 = min(dx == -1 ? i - 1 : i, ex - 1);
+      const int y0 = max(dy == 1 ? j : j - 1, 0), y1 = min(dy == -1 ? j - 1 : j, ey - 1);
+      const int z0 = max(dz == 1 ? l : l - 1, 0), z1 = min(dz == -1 ? l - 1 : l, ez - 1);
+      for (int ez_ = z0; ez_ <= z1; ++ez_)
+        for (int ey_ = y0; ey_ <= y1; ++ey_)
+          for (int ex_ = x0; ex_ <= x1; ++ex_) {
+            const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
+            const int a = (i - ex_) + 2 * ((j - ey_) + 2 * (l - ez_));
+            const int b = (ii - ex_) + 2 * ((jj - ey_) + 2 * (ll - ez_));
+            const T* base = Ke + e * kSym;
 #pragma unroll
-              for (int r = 0; r < 3; ++r)
+            for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                  const int R = 3 * a + r, C = 3 * b + c;
-                  acc[3 * r + c] += (double)base[R <= C ? sym_index(R, C) : sym_index(C, R)];
-                }
-            }
-      }
-      const long nb = valid ? node + dx + (long)Lx * (dy + (long)Ly * dz) : node;
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const bool fr = mask[3 * node + r] != 0;
-          const bool fc = valid ? (mask[3 * nb + c] != 0) : true;
-          double v = acc[3 * r + c];
-          if (fr || fc) v = (o == 13 && r == c) ? 1.0 : 0.0;
-          S[(size_t)(o * 9 + 3 * r + c) * nn + node] = (T)v;
-          if (o == 13 && r == c) dinv[3 * node + r] = (T)(1.0 / v);
-        }
+              for (int c = 0; c < 3; ++c) {
+                const int R = 3 * a + r, C = 3 * b + c;
+                acc[3 * r + c] += (double)base[R <= C ? sym_index(R, C) : sym_index(C, R)];
+              }
+          }
     }
+    const long nb = valid ? node + dx + (long)Lx * (dy + (long)Ly * dz) : node;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const bool fr = mask[3 * node + r] != 0;
+        const bool fc = valid ? (mask[3 * nb + c] != 0) : true;
+        double v = acc[3 * r + c];
+        if (fr || fc) v = (o == 13 && r == c) ? 1.0 : 0.0;
+        S[(size_t)(o * 9 + 3 * r + c) * nn + node] = (T)v;
+        if (o == 13 && r == c) dinv[3 * node + r] = (T)(1.0 / v);
+      }
   }
 }
 
@@ -306,16 +388,37 @@ __global__ void k_coarse_dense(int Lx, int Ly, int Lz, const double* __restrict_
 // Dense FP64 Cholesky A = L L^T (blocked, right-looking), then
 // X = L^{-1} (block rows) and A^{-1} = X^T X, in one cooperative launch.
 // The V-cycle's coarse solve is then one dense matrix-vector product spread
-// over many SMs (FP64 issue is 4 flop/clk/SM on this part, so a sequential
-// triangular solve on one SM would dominate the cycle).
+// over many SMs (FP64 issues 4 flop/clk/SM on this part, so a sequential
+// triangular solve on one SM would dominate the cycle).  FP64 latency is
+// long here, so no thread runs a long dependent chain: pivots use one
+// reciprocal each, inner products use four independent accumulators or a
+// whole warp, and the final product is a shared-memory tiled product.
+__device__ __forceinline__ double dot4(const double* a, int sa, const double* b, int sb, int len) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int q = 0;
+  for (; q + 3 < len; q += 4) {
+    s0 += a[q * sa] * b[q * sb];
+    s1 += a[(q + 1) * sa] * b[(q + 1) * sb];
+    s2 += a[(q + 2) * sa] * b[(q + 2) * sb];
+    s3 += a[(q + 3) * sa] * b[(q + 3) * sb];
+  }
+  for (; q < len; ++q) s0 += a[q * sa] * b[q * sb];
+  return (s0 + s1) + (s2 + s3);
+}
+
 __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restrict__ W,
                                 double* __restrict__ Dblk, double* __restrict__ X,
                                 double* __restrict__ Ainv, int* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double a[kNB][kNB + 1];
   __shared__ double li[kNB][kNB + 1];
+  __shared__ double dinv[kNB];
+  __shared__ double ta[kTile][kTile + 1];
+  __shared__ double tb[kTile][kTile + 1];
   const int tid = threadIdx.x, bd = blockDim.x;
   const long gtid = blockIdx.x * (long)bd + tid, gstride = (long)gridDim.x * bd;
+  const int lane = tid & 31;
+  const long gwarp = gtid >> 5, nwarps = gstride >> 5;
   const int nblk = (n + kNB - 1) / kNB;
   for (int kb = 0; kb < nblk; ++kb) {
     const int k0 = kb * kNB, nb = min(kNB, n - k0);
@@ -323,6 +426,7 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
     for (int t = tid; t < kNB * kNB; t += bd) {
       const int i = t / kNB, j = t % kNB;
       a[i][j] = (i < nb && j < nb && j <= i) ? A[(size_t)(k0 + i) * n + k0 + j] : 0.0;
+      li[i][j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int jj = 0; jj < nb; ++jj) {
@@ -332,10 +436,12 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
           if (blockIdx.x == 0) atomicExch(status, 1);
           d = 1.0;
         }
-        a[jj][jj] = sqrt(d);
+        const double sq = sqrt(d);
+        a[jj][jj] = sq;
+        dinv[jj] = 1.0 / sq;
       }
       __syncthreads();
-      for (int i = jj + 1 + tid; i < nb; i += bd) a[i][jj] /= a[jj][jj];
+      for (int i = jj + 1 + tid; i < nb; i += bd) a[i][jj] *= dinv[jj];
       __syncthreads();
       const int m = nb - jj - 1;
       for (int t = tid; t < m * m; t += bd) {
@@ -344,24 +450,22 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
       }
       __syncthreads();
     }
-    for (int t = tid; t < kNB * kNB; t += bd) li[t / kNB][t % kNB] = 0.0;
-    __syncthreads();
-    if (tid < nb) {
-      const int j = tid;
-      for (int i = j; i < nb; ++i) {
-        double s = (i == j) ? 1.0 : 0.0;
-        for (int t = j; t < i; ++t) s -= a[i][t] * li[t][j];
-        li[i][j] = s / a[i][i];
+    // inverse of the unit... of L_kk, column-parallel forward substitution
+    for (int k = 0; k < nb; ++k) {
+      for (int j = tid; j <= k; j += bd) li[k][j] *= dinv[k];
+      __syncthreads();
+      const int rows = nb - k - 1, cols = k + 1;
+      for (int t = tid; t < rows * cols; t += bd) {
+        const int i = k + 1 + t / cols, j = t % cols;
+        li[i][j] -= a[i][k] * li[k][j];
       }
+      __syncthreads();
     }
-    __syncthreads();
     // (B) panel below the diagonal block: W = A_panel L_kk^{-T}
     const int rows = n - k0 - nb;
     for (long t = gtid; t < (long)rows * nb; t += gstride) {
       const int i = k0 + nb + (int)(t / nb), jj = (int)(t % nb);
-      double s = 0.0;
-      for (int q = 0; q <= jj; ++q) s += A[(size_t)i * n + k0 + q] * li[jj][q];
-      W[(size_t)i * kNB + jj] = s;
+      W[(size_t)i * kNB + jj] = dot4(A + (size_t)i * n + k0, 1, &li[jj][0], 1, jj + 1);
     }
     grid.sync();
     // (C) write L_kk, its inverse and the panel; update the trailing matrix
@@ -369,7 +473,7 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
       for (int t = tid; t < kNB * kNB; t += bd) {
         const int i = t / kNB, j = t % kNB;
         if (i < nb && j < nb && j <= i) A[(size_t)(k0 + i) * n + k0 + j] = a[i][j];
-        Dblk[(size_t)kb * kNB * kNB + t] = li[i][j];
+        Dblk[(size_t)kb * kNB * kNB + t] = (i < nb && j < nb && j <= i) ? li[i][j] : 0.0;
       }
     }
     for (long t = gtid; t < (long)rows * nb; t += gstride) {
@@ -381,20 +485,20 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
       if (j > i) continue;
       i += k0 + nb;
       j += k0 + nb;
-      double s = 0.0;
-      for (int q = 0; q < nb; ++q) s += W[(size_t)i * kNB + q] * W[(size_t)j * kNB + q];
-      A[(size_t)i * n + j] -= s;
+      A[(size_t)i * n + j] -= dot4(W + (size_t)i * kNB, 1, W + (size_t)j * kNB, 1, nb);
     }
     grid.sync();
   }
   // X = L^{-1}, one block row at a time: X_ib,jb = -Linv_ib * sum_q L_ib,q X_q,jb
   for (int ib = 0; ib < nblk; ++ib) {
     const int i0 = ib * kNB, nbi = min(kNB, n - i0);
-    for (long t = gtid; t < (long)nbi * i0; t += gstride) {  // T = L[i0:, :i0] X[:i0, :i0]
-      const int r = (int)(t / i0), j = (int)(t % i0);
+    // T[r][j] = sum_{q=j}^{i0-1} L[i0+r][q] X[q][j]: one warp per (r, j)
+    for (long w = gwarp; w < (long)nbi * i0; w += nwarps) {
+      const int r = (int)(w / i0), j = (int)(w % i0);
       double s = 0.0;
-      for (int q = j; q < i0; ++q) s += A[(size_t)(i0 + r) * n + q] * X[(size_t)q * n + j];
-      Ainv[(size_t)r * n + j] = s;  // Ainv used as scratch for T (rows 0..nbi-1)
+      for (int q = j + lane; q < i0; q += 32) s += A[(size_t)(i0 + r) * n + q] * X[(size_t)q * n + j];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) Ainv[(size_t)r * n + j] = s;  // Ainv rows 0..nbi-1 hold T
     }
     grid.sync();
     const double* Li = Dblk + (size_t)ib * kNB * kNB;
@@ -404,21 +508,46 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
       if (j >= i0) {
         v = (j - i0 <= r) ? Li[r * kNB + (j - i0)] : 0.0;
       } else {
-        v = 0.0;
-        for (int s2 = 0; s2 <= r; ++s2) v -= Li[r * kNB + s2] * Ainv[(size_t)s2 * n + j];
+        v = -dot4(Li + r * kNB, 1, Ainv + j, n, r + 1);
       }
       X[(size_t)(i0 + r) * n + j] = v;
     }
     grid.sync();
   }
-  // A^{-1} = X^T X (lower triangle computed, mirrored)
-  for (long t = gtid; t < (long)n * n; t += gstride) {
-    const int i = (int)(t / n), j = (int)(t % n);
-    if (j > i) continue;
-    double s = 0.0;
-    for (int q = i; q < n; ++q) s += X[(size_t)q * n + i] * X[(size_t)q * n + j];
-    Ainv[(size_t)i * n + j] = s;
-    Ainv[(size_t)j * n + i] = s;
+  // A^{-1} = X^T X: 32x32 output tiles (lower triangle), shared-memory staged
+  const int nt = (n + kTile - 1) / kTile;
+  const int ntiles = nt * (nt + 1) / 2;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    const int tj = tile - ti * (ti + 1) / 2;
+    const int i0 = ti * kTile, j0 = tj * kTile;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int ly = tid / kTile, lx = tid % kTile;  // 8 x 32 threads, 4 rows each
+    for (int q0 = i0; q0 < n; q0 += kTile) {
+      __syncthreads();
+      for (int t = tid; t < kTile * kTile; t += bd) {
+        const int qq = t / kTile, c = t % kTile;
+        const int q = q0 + qq;
+        ta[qq][c] = (q < n && i0 + c < n) ? X[(size_t)q * n + i0 + c] : 0.0;
+        tb[qq][c] = (q < n && j0 + c < n) ? X[(size_t)q * n + j0 + c] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int qq = 0; qq < kTile; ++qq) {
+        const double bx = tb[qq][lx];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += ta[qq][ly + 8 * u] * bx;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + ly + 8 * u, j = j0 + lx;
+      if (i < n && j < n && j <= i) {
+        Ainv[(size_t)i * n + j] = acc[u];
+        Ainv[(size_t)j * n + i] = acc[u];
+      }
+    }
   }
 }
 
@@ -457,26 +586,57 @@ void launch_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* off, const 
 void launch_elem_direct(bool fp64, const Level& L, int n, const double* w, int Dx, int Dy,
                         const double* tabsym, void* Ke, cudaStream_t st) {
   const long E = (long)L.ex * L.ey * L.ez;
+  const int m = n * n * n;
+  int epb = 4096 / m;
+  if (epb > 32) epb = 32;
+  if (epb < 1) epb = 1;
+  const long g = (E + epb - 1) / epb;
+  const size_t sm = (size_t)epb * m * sizeof(double);
   if (fp64)
-    k_elem_direct<double><<<E, 320, 0, st>>>(L.ex, L.ey, L.ez, n, w, Dx, Dy, tabsym, (double*)Ke);
+    k_elem_direct<double><<<g, 256, sm, st>>>(L.ex, L.ey, L.ez, n, epb, w, Dx, Dy, tabsym, (double*)Ke);
   else
-    k_elem_direct<float><<<E, 320, 0, st>>>(L.ex, L.ey, L.ez, n, w, Dx, Dy, tabsym, (float*)Ke);
+    k_elem_direct<float><<<g, 256, sm, st>>>(L.ex, L.ey, L.ez, n, epb, w, Dx, Dy, tabsym, (float*)Ke);
 }
 
 void launch_elem_moments(bool fp64, const Level& L, const double* w, int Dx, int Dy,
-                         const double* cmom, void* Ke, cudaStream_t st) {
+                         const double* cmom, void* Mscr, void* Ke, cudaStream_t st) {
   const long E = (long)L.ex * L.ey * L.ez;
-  if (fp64)
-    k_elem_moments<double, double><<<E, 320, 0, st>>>(L.ex, L.ey, L.ez, L.nsub, L.h, w, Dx, Dy,
-                                                      cmom, (double*)Ke);
-  else
-    k_elem_moments<float, float><<<E, 320, 0, st>>>(L.ex, L.ey, L.ez, L.nsub, L.h, w, Dx, Dy, cmom,
-                                                    (float*)Ke);
+  const int N = L.nsub;
+  const long gk = (E + 31) / 32;
+  if (fp64) {
+    double* M = (double*)Mscr;
+    if (N <= 4)
+      k_moments_thread<double><<<(E + 127) / 128, 128, 0, st>>>(L.ex, L.ey, L.ez, N, w, Dx, Dy, M);
+    else
+      k_moments_block<double><<<E, N * N >= 256 ? 256 : 64, 0, st>>>(L.ex, L.ey, L.ez, N, w, Dx, Dy, M);
+    const size_t sm = (size_t)(27 * kSym + 32 * 27) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_moments_to_ke<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+      attr = true;
+    }
+    k_moments_to_ke<double, double><<<gk, 256, sm, st>>>(E, L.h, M, cmom, (double*)Ke);
+  } else {
+    float* M = (float*)Mscr;
+    if (N <= 4)
+      k_moments_thread<float><<<(E + 127) / 128, 128, 0, st>>>(L.ex, L.ey, L.ez, N, w, Dx, Dy, M);
+    else
+      k_moments_block<float><<<E, N * N >= 256 ? 256 : 64, 0, st>>>(L.ex, L.ey, L.ez, N, w, Dx, Dy, M);
+    const size_t sm = (size_t)(27 * kSym + 32 * 27) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_moments_to_ke<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+      attr = true;
+    }
+    k_moments_to_ke<float, float><<<gk, 256, sm, st>>>(E, L.h, M, cmom, (float*)Ke);
+  }
 }
 
 void launch_assemble(bool fp64, const Level& L, const void* Ke, void* S, void* dinv,
                      cudaStream_t st) {
-  const int g = grid_for(L.nn, 128);
+  const int g = grid_for((long)L.nn * 27, 128, 65536);
   if (fp64)
     k_assemble<double><<<g, 128, 0, st>>>(L.ex, L.ey, L.ez, L.Lx, L.Ly, L.Lz, (const double*)Ke,
                                           L.mask, (double*)S, (double*)dinv);
@@ -498,8 +658,11 @@ int coarse_factor_grid() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_factor, 256, 0);
-  // one block per SM: co-resident as long as one block fits (checked here)
-  return per >= 1 ? sms : 0;
+  // at most 64 blocks (one per SM): the factorisation is latency-bound, a
+  // smaller grid makes its barriers cheaper and leaves SMs to the
+  // concurrent fine-level assembly
+  if (per < 1) return 0;
+  return sms < 64 ? sms : 64;
 }
 
 cudaError_t launch_coarse_factor(int n, double* A, double* W, double* Dblk, double* X,

@@ -2,8 +2,8 @@
 // Eq. matrixK_mr assembled per node), the multigrid cycle of Algorithm 1
 // (damped Jacobi smoothing, linear-interpolation transfer, dense coarse
 // solve), and the FP64 preconditioned CG of Sec. 7.2 with fused vector
-// updates and deterministic two-stage reductions (warp shuffles, then a
-// fixed-order sum of per-block partials).
+// updates and deterministic reductions (warp shuffles, then a fixed-order
+// sum of per-block partials done by the last block to finish).
 #include "internal.cuh"
 
 namespace tos {
@@ -21,27 +21,54 @@ LevelView<float> view<float>(const Level& L) {
 
 namespace {
 
-// y = (A x)_node for the three DOFs of one node; ld(nb, x0, x1, x2) loads
-// the operand at neighbour node nb.
+// Row-parallel mapping of the stencil kernels: a block of kRowThreads = 192
+// threads covers 64 nodes; warp w handles output row r = w % 3 of 32
+// consecutive nodes, so each coefficient load S[(o*9 + 3r + c)*nn + node]
+// is one contiguous 32-wide access and the work of a level spreads over 3x
+// more warps (FP64 issue is 4 flop/clk/SM, so every SM must take a share).
+constexpr int kRowThreads = 192;
+constexpr int kRowNodes = 64;
+
+// (A x)_{node, r}: ld(nb, c) loads component c of the operand at node nb.
+// Neighbours outside the lattice are clamped onto it: their stencil
+// coefficients are zero (assembly writes 0 there), so the load is harmless
+// and the loop has no branch -- every load of the 27 neighbours can be in
+// flight at once instead of one memory round trip per neighbour.
 template <typename T, typename LD>
-__device__ __forceinline__ void stencil_node(const LevelView<T>& V, long node, int i, int j, int l,
-                                             LD ld, T& y0, T& y1, T& y2) {
-  y0 = y1 = y2 = T(0);
+__device__ __forceinline__ T stencil_row(const LevelView<T>& V, long node, int i, int j, int l, int r,
+                                         LD ld) {
   const size_t nn = V.nn;
+  const long sx[3] = {i > 0 ? -1L : 0L, 0L, i + 1 < V.Lx ? 1L : 0L};
+  const long sy[3] = {j > 0 ? -(long)V.Lx : 0L, 0L, j + 1 < V.Ly ? (long)V.Lx : 0L};
+  const long sz[3] = {l > 0 ? -(long)V.Lx * V.Ly : 0L, 0L, l + 1 < V.Lz ? (long)V.Lx * V.Ly : 0L};
+  T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int o = 0; o < 27; ++o) {
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-    const int ii = i + dx, jj = j + dy, ll = l + dz;
-    if (ii < 0 || ii >= V.Lx || jj < 0 || jj >= V.Ly || ll < 0 || ll >= V.Lz) continue;
-    const long nb = node + dx + (long)V.Lx * (dy + (long)V.Ly * dz);
-    T x0, x1, x2;
-    ld(nb, x0, x1, x2);
-    const T* s = V.S + (size_t)o * 9 * nn + node;
-    y0 += s[0] * x0 + s[nn] * x1 + s[2 * nn] * x2;
-    y1 += s[3 * nn] * x0 + s[4 * nn] * x1 + s[5 * nn] * x2;
-    y2 += s[6 * nn] * x0 + s[7 * nn] * x1 + s[8 * nn] * x2;
+    const long nb = node + sx[o % 3] + sy[(o / 3) % 3] + sz[o / 9];
+    const T* s = V.S + (size_t)(o * 9 + 3 * r) * nn + node;
+    acc[o % 3] += s[0] * ld(nb, 0) + s[nn] * ld(nb, 1) + s[2 * nn] * ld(nb, 2);
   }
+  return (acc[0] + acc[1]) + acc[2];
 }
+
+#define ROW_LOOP(nn)                                                                  \
+  const int lane_ = threadIdx.x & 31, r = (threadIdx.x >> 5) % 3,                     \
+            grp_ = threadIdx.x / 96;                                                  \
+  for (long base_ = (long)blockIdx.x * kRowNodes; base_ < (nn);                       \
+       base_ += (long)gridDim.x * kRowNodes)                                          \
+    for (long node = base_ + grp_ * 32 + lane_, once_ = 0; once_ == 0 && node < (nn); ++once_)
+
+#define DOF_LOOP(ndof)                                                             \
+  for (long d = blockIdx.x * (long)blockDim.x + threadIdx.x; d < (ndof);           \
+       d += (long)gridDim.x * blockDim.x)
+
+#define NODE_LOOP(nn)                                                              \
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < (nn);       \
+       node += (long)gridDim.x * blockDim.x)
+
+#define NODE_IJL(V)                                                                \
+  const int i = node % (V).Lx, j = (node / (V).Lx) % (V).Ly,                       \
+            l = node / ((long)(V).Lx * (V).Ly)
 
 // Deterministic block sum of one double (result valid in thread 0).
 __device__ __forceinline__ double block_sum(double v) {
@@ -57,12 +84,12 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
-// Sum of np partials, computed identically by every block (fixed order);
-// the result is broadcast to all threads of the block.
-__device__ __forceinline__ double reduce_parts(const double* __restrict__ part, int np) {
+// Sum of np partials in a fixed order (L2 reads: the partials were written
+// by other SMs during this launch); broadcast to the whole block.
+__device__ __forceinline__ double reduce_parts(const double* part, int np) {
   __shared__ double bc;
   double v = 0.0;
-  for (int t = threadIdx.x; t < np; t += blockDim.x) v += part[t];
+  for (int t = threadIdx.x; t < np; t += blockDim.x) v += __ldcg(part + t);
   v = block_sum(v);
   if (threadIdx.x == 0) bc = v;
   __syncthreads();
@@ -71,51 +98,52 @@ __device__ __forceinline__ double reduce_parts(const double* __restrict__ part, 
   return r;
 }
 
-#define NODE_LOOP(nn)                                                              \
-  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < (nn);       \
-       node += (long)gridDim.x * blockDim.x)
+// Thread 0 of every block has written the block's partial(s); returns true
+// in the single block that finishes last (threadfence + counter: no block
+// ever waits on another).  That block then owns the final reduction and
+// resets the counter for the next launch.
+__device__ __forceinline__ bool last_block(unsigned* cnt) {
+  __shared__ unsigned flag;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    flag = (atomicAdd(cnt, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (flag) __threadfence();
+  return flag != 0;
+}
 
-#define NODE_IJL(V)                                                                \
-  const int i = node % (V).Lx, j = (node / (V).Lx) % (V).Ly,                       \
-            l = node / ((long)(V).Lx * (V).Ly)
+__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle hc, int use_cond, unsigned v) {
+  if (use_cond) cudaGraphSetConditional(hc, v);
+}
 
 // ---- multigrid cycle ------------------------------------------------------
 
-// Pre-smoothing from a zero guess and the residual, fused:
-// v = omega D^-1 b, r = b - A v.
+// Residual after the pre-smoothing step from a zero guess: the producer of
+// b already wrote v = omega D^-1 b; here r = b - A v.
 template <typename T>
-__global__ void k_vc_pre(LevelView<T> V, T omega, const T* __restrict__ b, T* __restrict__ v,
-                         T* __restrict__ r) {
-  NODE_LOOP(V.nn) {
+__global__ void k_vc_pre(LevelView<T> V, const T* __restrict__ b, const T* __restrict__ v,
+                         T* __restrict__ r_out) {
+  ROW_LOOP(V.nn) {
     NODE_IJL(V);
-    T y0, y1, y2;
-    stencil_node(V, node, i, j, l,
-                 [&](long nb, T& x0, T& x1, T& x2) {
-                   x0 = omega * V.dinv[3 * nb] * b[3 * nb];
-                   x1 = omega * V.dinv[3 * nb + 1] * b[3 * nb + 1];
-                   x2 = omega * V.dinv[3 * nb + 2] * b[3 * nb + 2];
-                 },
-                 y0, y1, y2);
-    const T b0 = b[3 * node], b1 = b[3 * node + 1], b2 = b[3 * node + 2];
-    v[3 * node] = omega * V.dinv[3 * node] * b0;
-    v[3 * node + 1] = omega * V.dinv[3 * node + 1] * b1;
-    v[3 * node + 2] = omega * V.dinv[3 * node + 2] * b2;
-    r[3 * node] = b0 - y0;
-    r[3 * node + 1] = b1 - y1;
-    r[3 * node + 2] = b2 - y2;
+    const T y = stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return v[3 * nb + c]; });
+    const long d = 3 * node + r;
+    r_out[d] = b[d] - y;
   }
 }
 
-// r_H = M_H P^T r_h: each coarse node gathers the 3x3x3 fine nodes around its
-// coincident fine node with weights (1, 1/2) per axis.
+// b_H = M_H P^T r_h: each coarse node gathers the 3x3x3 fine nodes around its
+// coincident fine node with weights (1, 1/2) per axis; also v_H = omega
+// D_H^-1 b_H (the next level's first smoothing step) unless H is coarsest.
 template <typename T>
 __global__ void k_vc_restrict(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int Lzc,
                               const uint8_t* __restrict__ maskc, const T* __restrict__ rf,
-                              T* __restrict__ bc) {
+                              T* __restrict__ bc, const T* __restrict__ dinvc, T omega,
+                              T* __restrict__ vc) {
   const long nnc = (long)Lxc * Lyc * Lzc;
   NODE_LOOP(nnc) {
     const int I = node % Lxc, J = (node / Lxc) % Lyc, K = node / ((long)Lxc * Lyc);
-    T a0 = 0, a1 = 0, a2 = 0;
+    T a[3] = {0, 0, 0};
     for (int dz = -1; dz <= 1; ++dz) {
       const int l = 2 * K + dz;
       if (l < 0 || l >= Lzf) continue;
@@ -129,15 +157,19 @@ __global__ void k_vc_restrict(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int L
           if (i < 0 || i >= Lxf) continue;
           const T wgt = wyz * (dx ? T(0.5) : T(1));
           const long f = i + (long)Lxf * (j + (long)Lyf * l);
-          a0 += wgt * rf[3 * f];
-          a1 += wgt * rf[3 * f + 1];
-          a2 += wgt * rf[3 * f + 2];
+          a[0] += wgt * rf[3 * f];
+          a[1] += wgt * rf[3 * f + 1];
+          a[2] += wgt * rf[3 * f + 2];
         }
       }
     }
-    bc[3 * node] = maskc[3 * node] ? T(0) : a0;
-    bc[3 * node + 1] = maskc[3 * node + 1] ? T(0) : a1;
-    bc[3 * node + 2] = maskc[3 * node + 2] ? T(0) : a2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long d = 3 * node + c;
+      const T bv = maskc[d] ? T(0) : a[c];
+      bc[d] = bv;
+      if (vc != nullptr) vc[d] = omega * dinvc[d] * bv;
+    }
   }
 }
 
@@ -175,19 +207,11 @@ __global__ void k_vc_prolong(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc,
 template <typename T>
 __global__ void k_vc_post(LevelView<T> V, T omega, const T* __restrict__ b, const T* __restrict__ v,
                           T* __restrict__ z) {
-  NODE_LOOP(V.nn) {
+  ROW_LOOP(V.nn) {
     NODE_IJL(V);
-    T y0, y1, y2;
-    stencil_node(V, node, i, j, l,
-                 [&](long nb, T& x0, T& x1, T& x2) {
-                   x0 = v[3 * nb];
-                   x1 = v[3 * nb + 1];
-                   x2 = v[3 * nb + 2];
-                 },
-                 y0, y1, y2);
-    z[3 * node] = v[3 * node] + omega * V.dinv[3 * node] * (b[3 * node] - y0);
-    z[3 * node + 1] = v[3 * node + 1] + omega * V.dinv[3 * node + 1] * (b[3 * node + 1] - y1);
-    z[3 * node + 2] = v[3 * node + 2] + omega * V.dinv[3 * node + 2] * (b[3 * node + 2] - y2);
+    const T y = stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return v[3 * nb + c]; });
+    const long d = 3 * node + r;
+    z[d] = v[d] + omega * V.dinv[d] * (b[d] - y);
   }
 }
 
@@ -207,90 +231,87 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const T* 
   }
 }
 
+template <typename T>
+__global__ void k_smooth0(long n, T omega, const T* __restrict__ dinv, const T* __restrict__ b,
+                          T* __restrict__ v) {
+  DOF_LOOP(n) v[d] = omega * dinv[d] * b[d];
+}
+
 // ---- FP64 preconditioned CG -------------------------------------------------
 
-__global__ void k_cg_prep(int nn, const uint8_t* __restrict__ mask, const double* __restrict__ fin,
-                          const double* __restrict__ uin, double* __restrict__ f,
+__global__ void k_cg_prep(int nn, const uint8_t* __restrict__ mask, double* __restrict__ f,
                           double* __restrict__ u, double* __restrict__ part) {
   double s = 0.0;
-  NODE_LOOP(nn) {
-    for (int c = 0; c < 3; ++c) {
-      const long d = 3 * node + c;
-      const bool fx = mask[d] != 0;
-      const double fv = fx ? 0.0 : fin[d];
-      f[d] = fv;
-      u[d] = fx ? 0.0 : uin[d];
-      s += fv * fv;
-    }
+  DOF_LOOP(3L * nn) {
+    const bool fx = mask[d] != 0;
+    const double fv = fx ? 0.0 : f[d];
+    f[d] = fv;
+    if (fx) u[d] = 0.0;
+    s += fv * fv;
   }
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// r = f - K u (FP64), optional cast of r into the preconditioner input b0,
-// partial ||r||^2.
+// r = f - K u (FP64) with partial ||r||^2.  mode 1 (before the loop): also
+// b0 = (T) r, v0 = omega D0^-1 b0, and the last block runs the initial
+// convergence test (||f||^2 from part_ff) and sets the loop condition;
+// mode 2 (after the loop): the last block stores the true residual.
 template <typename T>
 __global__ void k_cg_residual(LevelView<double> V, const double* __restrict__ f,
-                              const double* __restrict__ u, double* __restrict__ r,
-                              T* __restrict__ b0, double* __restrict__ part) {
+                              const double* __restrict__ u, double* __restrict__ rv,
+                              T* __restrict__ b0, const T* __restrict__ dinv0, T omega,
+                              T* __restrict__ v0, double* part, const double* part_ff, int mode,
+                              DevState* __restrict__ ds, unsigned* cnt,
+                              cudaGraphConditionalHandle hc, int use_cond) {
   double s = 0.0;
-  NODE_LOOP(V.nn) {
+  ROW_LOOP(V.nn) {
     NODE_IJL(V);
-    double y0, y1, y2;
-    stencil_node(V, node, i, j, l,
-                 [&](long nb, double& x0, double& x1, double& x2) {
-                   x0 = u[3 * nb];
-                   x1 = u[3 * nb + 1];
-                   x2 = u[3 * nb + 2];
-                 },
-                 y0, y1, y2);
-    const double r0 = f[3 * node] - y0, r1 = f[3 * node + 1] - y1, r2 = f[3 * node + 2] - y2;
-    r[3 * node] = r0;
-    r[3 * node + 1] = r1;
-    r[3 * node + 2] = r2;
-    if (b0 != nullptr) {
-      b0[3 * node] = (T)r0;
-      b0[3 * node + 1] = (T)r1;
-      b0[3 * node + 2] = (T)r2;
+    const double y = stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return u[3 * nb + c]; });
+    const long d = 3 * node + r;
+    const double rd = f[d] - y;
+    rv[d] = rd;
+    if (mode == 1) {
+      const T bt = (T)rd;
+      b0[d] = bt;
+      if (dinv0 != nullptr) v0[d] = omega * dinv0[d] * bt;  // no smoothing level when L = 1
     }
-    s += r0 * r0 + r1 * r1 + r2 * r2;
+    s += rd * rd;
   }
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle hc, int use_cond, unsigned v) {
-  if (use_cond) cudaGraphSetConditional(hc, v);
-}
-
-__global__ void k_cg_check_init(const double* __restrict__ part_ff, const double* __restrict__ part_rr,
-                                int np, DevState* __restrict__ ds, cudaGraphConditionalHandle hc,
-                                int use_cond) {
-  const double ff = reduce_parts(part_ff, np);
-  const double rr = reduce_parts(part_rr, np);
-  if (threadIdx.x == 0) {
-    ds->ff = ff;
-    ds->rr = rr;
-    ds->iter = 0;
-    ds->status = ds->coarse_status ? (int)TOSOLVE_EBREAKDOWN : 0;
-    const bool conv = (rr <= ds->tol2 * ff) || ff == 0.0;
-    ds->converged = conv;
-    if (!(rr == rr)) ds->status = TOSOLVE_EBREAKDOWN;
-    set_cond(hc, use_cond, (conv || ds->status || ds->maxit <= 0) ? 0u : 1u);
+  if (!last_block(cnt)) return;
+  const double rr = reduce_parts(part, gridDim.x);
+  if (mode == 1) {
+    const double ff = reduce_parts(part_ff, gridDim.x);
+    if (threadIdx.x == 0) {
+      ds->ff = ff;
+      ds->rr = rr;
+      ds->iter = 0;
+      ds->status = ds->coarse_status ? (int)TOSOLVE_EBREAKDOWN : 0;
+      if (!(rr == rr)) ds->status = TOSOLVE_EBREAKDOWN;
+      const bool conv = (rr <= ds->tol2 * ff) || ff == 0.0;
+      ds->converged = conv;
+      set_cond(hc, use_cond, (conv || ds->status || ds->maxit <= 0) ? 0u : 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    ds->rr_true = rr;
   }
+  if (threadIdx.x == 0) *cnt = 0u;
 }
 
+// Partial r^T z and z^T q; the last block forms the flexible (Polak-Ribiere)
+// coefficient, valid for a preconditioner evaluated in lower precision:
+//   beta = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k) = -alpha_k z_{k+1}^T q_k / rz_k.
 template <typename T>
 __global__ void k_cg_dots_rz(int nn, const double* __restrict__ r, const T* __restrict__ z,
-                             const double* __restrict__ q, double* __restrict__ part_rz,
-                             double* __restrict__ part_zq) {
+                             const double* __restrict__ q, double* part_rz, double* part_zq,
+                             DevState* __restrict__ ds, unsigned* cnt) {
   double a = 0.0, b = 0.0;
-  NODE_LOOP(nn) {
-    for (int c = 0; c < 3; ++c) {
-      const double zv = (double)z[3 * node + c];
-      a += r[3 * node + c] * zv;
-      b += zv * q[3 * node + c];
-    }
+  DOF_LOOP(3L * nn) {
+    const double zv = (double)z[d];
+    a += r[d] * zv;
+    b += zv * q[d];
   }
   a = block_sum(a);
   b = block_sum(b);
@@ -298,87 +319,78 @@ __global__ void k_cg_dots_rz(int nn, const double* __restrict__ r, const T* __re
     part_rz[blockIdx.x] = a;
     part_zq[blockIdx.x] = b;
   }
-}
-
-// Flexible (Polak-Ribiere) direction update, which stays valid for a
-// preconditioner evaluated in lower precision:
-//   beta = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k) = -alpha_k z_{k+1}^T q_k / rz_k.
-template <typename T>
-__global__ void k_cg_dir(int nn, const double* __restrict__ part_rz, const double* __restrict__ part_zq,
-                         int np, const T* __restrict__ z, double* __restrict__ p,
-                         DevState* __restrict__ ds) {
-  const double rz_new = reduce_parts(part_rz, np);
-  const double zq = reduce_parts(part_zq, np);
-  const bool first = ds->iter == 0;
-  const double beta = first ? 0.0 : -ds->alpha * zq / ds->rz;
-  NODE_LOOP(nn) {
-    for (int c = 0; c < 3; ++c) {
-      const double zv = (double)z[3 * node + c];
-      p[3 * node + c] = first ? zv : zv + beta * p[3 * node + c];
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (!last_block(cnt)) return;
+  const double rz_new = reduce_parts(part_rz, gridDim.x);
+  const double zq = reduce_parts(part_zq, gridDim.x);
+  if (threadIdx.x == 0) {
+    ds->beta = (ds->iter == 0) ? 0.0 : -ds->alpha * zq / ds->rz;
     ds->rz_next = rz_new;
-    ds->beta = beta;
+    *cnt = 0u;
   }
 }
 
+template <typename T>
+__global__ void k_cg_dir(int nn, const T* __restrict__ z, double* __restrict__ p,
+                         const DevState* __restrict__ ds) {
+  const bool first = ds->iter == 0;
+  const double beta = ds->beta;
+  DOF_LOOP(3L * nn) {
+    const double zv = (double)z[d];
+    p[d] = first ? zv : zv + beta * p[d];
+  }
+}
+
+// q = K p (FP64) and partial p^T q; the last block forms alpha = rz / p^T q
+// (a non-positive or non-finite value is a breakdown).
 __global__ void k_cg_apply(LevelView<double> V, const double* __restrict__ p, double* __restrict__ q,
-                           double* __restrict__ part) {
+                           double* part, DevState* __restrict__ ds, unsigned* cnt) {
   double s = 0.0;
-  NODE_LOOP(V.nn) {
+  ROW_LOOP(V.nn) {
     NODE_IJL(V);
-    double y0, y1, y2;
-    stencil_node(V, node, i, j, l,
-                 [&](long nb, double& x0, double& x1, double& x2) {
-                   x0 = p[3 * nb];
-                   x1 = p[3 * nb + 1];
-                   x2 = p[3 * nb + 2];
-                 },
-                 y0, y1, y2);
-    q[3 * node] = y0;
-    q[3 * node + 1] = y1;
-    q[3 * node + 2] = y2;
-    s += p[3 * node] * y0 + p[3 * node + 1] * y1 + p[3 * node + 2] * y2;
+    const double y = stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return p[3 * nb + c]; });
+    const long d = 3 * node + r;
+    q[d] = y;
+    s += p[d] * y;
   }
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!last_block(cnt)) return;
+  const double pq = reduce_parts(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    const double rz = ds->rz_next;
+    const double alpha = rz / pq;
+    const bool ok = (pq > 0.0) && (alpha == alpha) && (fabs(alpha) < 1e300);
+    ds->alpha = ok ? alpha : 0.0;
+    ds->rz = rz;
+    if (!ok) ds->status = TOSOLVE_EBREAKDOWN;
+    *cnt = 0u;
+  }
 }
 
+// u += alpha p, r -= alpha q, b0 = (T) r, v0 = omega D0^-1 b0, partial
+// ||r||^2; the last block runs the convergence test and sets the loop
+// condition (stop on convergence, breakdown or maxit).
 template <typename T>
-__global__ void k_cg_update(int nn, const double* __restrict__ part_pq, int np, double* __restrict__ u,
-                            double* __restrict__ r, const double* __restrict__ p,
-                            const double* __restrict__ q, T* __restrict__ b0,
-                            double* __restrict__ part_rr, DevState* __restrict__ ds) {
-  const double pq = reduce_parts(part_pq, np);
-  const double rz = ds->rz_next;
-  const double alpha = rz / pq;
-  const bool ok = (pq > 0.0) && (alpha == alpha) && (fabs(alpha) < 1e300);
+__global__ void k_cg_update(int nn, double* __restrict__ u, double* __restrict__ r,
+                            const double* __restrict__ p, const double* __restrict__ q,
+                            T* __restrict__ b0, const T* __restrict__ dinv0, T omega,
+                            T* __restrict__ v0, double* part_rr, DevState* __restrict__ ds,
+                            unsigned* cnt, cudaGraphConditionalHandle hc, int use_cond) {
+  const double alpha = ds->alpha;
   double s = 0.0;
-  if (ok) {
-    NODE_LOOP(nn) {
-      for (int c = 0; c < 3; ++c) {
-        const long d = 3 * node + c;
-        u[d] += alpha * p[d];
-        const double rv = r[d] - alpha * q[d];
-        r[d] = rv;
-        b0[d] = (T)rv;
-        s += rv * rv;
-      }
-    }
+  DOF_LOOP(3L * nn) {
+    u[d] += alpha * p[d];
+    const double rv = r[d] - alpha * q[d];
+    r[d] = rv;
+    const T bt = (T)rv;
+    b0[d] = bt;
+    if (dinv0 != nullptr) v0[d] = omega * dinv0[d] * bt;  // no smoothing level when L = 1
+    s += rv * rv;
   }
   s = block_sum(s);
   if (threadIdx.x == 0) part_rr[blockIdx.x] = s;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ds->alpha = alpha;
-    ds->rz = rz;
-    if (!ok) ds->status = TOSOLVE_EBREAKDOWN;
-  }
-}
-
-__global__ void k_cg_check(const double* __restrict__ part_rr, int np, DevState* __restrict__ ds,
-                           cudaGraphConditionalHandle hc, int use_cond) {
-  const double rr = reduce_parts(part_rr, np);
+  if (!last_block(cnt)) return;
+  const double rr = reduce_parts(part_rr, gridDim.x);
   if (threadIdx.x == 0) {
     ds->rr = rr;
     ds->iter += 1;
@@ -386,30 +398,16 @@ __global__ void k_cg_check(const double* __restrict__ part_rr, int np, DevState*
     const bool conv = rr <= ds->tol2 * ds->ff;
     ds->converged = conv;
     set_cond(hc, use_cond, (conv || ds->status || ds->iter >= ds->maxit) ? 0u : 1u);
+    *cnt = 0u;
   }
-}
-
-__global__ void k_cg_final(const double* __restrict__ part_rr, int np, DevState* __restrict__ ds) {
-  const double rr = reduce_parts(part_rr, np);
-  if (threadIdx.x == 0) ds->rr_true = rr;
 }
 
 // Diagnostic: y = A x in the level's stored precision, FP64 in and out.
 template <typename T>
 __global__ void k_apply_diag(LevelView<T> V, const double* __restrict__ x, double* __restrict__ y) {
-  NODE_LOOP(V.nn) {
+  ROW_LOOP(V.nn) {
     NODE_IJL(V);
-    T y0, y1, y2;
-    stencil_node(V, node, i, j, l,
-                 [&](long nb, T& x0, T& x1, T& x2) {
-                   x0 = (T)x[3 * nb];
-                   x1 = (T)x[3 * nb + 1];
-                   x2 = (T)x[3 * nb + 2];
-                 },
-                 y0, y1, y2);
-    y[3 * node] = y0;
-    y[3 * node + 1] = y1;
-    y[3 * node + 2] = y2;
+    y[3 * node + r] = (double)stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return (T)x[3 * nb + c]; });
   }
 }
 
@@ -419,11 +417,14 @@ __global__ void k_cast(size_t n, const A* __restrict__ a, B* __restrict__ b) {
     b[t] = (B)a[t];
 }
 
-inline int grid_nodes(long nn) {
-  long g = (nn + kBS - 1) / kBS;
-  if (g < 1) g = 1;
-  return (int)(g < kMaxPart ? g : kMaxPart);
-}
+inline int grid_nodes(long nn) { return parts_for(nn); }
+
+template <typename T>
+const T* dinv_of(const Level& L);
+template <>
+const double* dinv_of<double>(const Level& L) { return L.dinv64; }
+template <>
+const float* dinv_of<float>(const Level& L) { return L.dinv32; }
 
 template <typename T>
 void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, cudaStream_t st) {
@@ -437,13 +438,16 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, cudaStream
   }
   Level& C = lv[l + 1];
   const LevelView<T> V = view<T>(F);
-  k_vc_pre<T><<<grid_nodes(F.nn), kBS, 0, st>>>(V, omega, (const T*)F.b, (T*)F.v, (T*)F.r);
-  k_vc_restrict<T><<<grid_nodes(C.nn), kBS, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, C.mask,
-                                                     (const T*)F.r, (T*)C.b);
+  const bool c_coarsest = (l + 1 == L - 1);
+  k_vc_pre<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(V, (const T*)F.b, (const T*)F.v, (T*)F.r);
+  k_vc_restrict<T><<<grid_nodes(C.nn), kRowThreads, 0, st>>>(
+      F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, C.mask, (const T*)F.r, (T*)C.b,
+      c_coarsest ? nullptr : dinv_of<T>(C), omega, c_coarsest ? nullptr : (T*)C.v);
   vcycle_rec<T>(lv, l + 1, L, omega, Ainv, st);
-  k_vc_prolong<T><<<grid_nodes(F.nn), kBS, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, F.mask,
-                                                    (const T*)C.z, (T*)F.v);
-  k_vc_post<T><<<grid_nodes(F.nn), kBS, 0, st>>>(V, omega, (const T*)F.b, (const T*)F.v, (T*)F.z);
+  k_vc_prolong<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, F.mask,
+                                                            (const T*)C.z, (T*)F.v);
+  k_vc_post<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(V, omega, (const T*)F.b, (const T*)F.v,
+                                                         (T*)F.z);
 }
 
 }  // namespace
@@ -457,68 +461,74 @@ void launch_vcycle(bool fp64, Level* lv, int L, double omega, int gamma, const d
     vcycle_rec<float>(lv, 0, L, (float)omega, Ainv, st);
 }
 
-void launch_cg_prep(const Level& L0, const double* fin, const double* uin, double* f, double* u,
-                    double* part, int np, cudaStream_t st) {
-  k_cg_prep<<<np, kBS, 0, st>>>(L0.nn, L0.mask, fin, uin, f, u, part);
-}
-
-void launch_cg_residual(bool fp64, const Level& L0, const double* f, const double* u, double* r,
-                        void* b0, double* part, int np, cudaStream_t st) {
+void launch_smooth0(bool fp64, const Level& L0, double omega, cudaStream_t st) {
+  const int g = parts_for(L0.nn);
   if (fp64)
-    k_cg_residual<double><<<np, kBS, 0, st>>>(view<double>(L0), f, u, r, (double*)b0, part);
+    k_smooth0<double><<<g, kRowThreads, 0, st>>>(L0.ndof, omega, L0.dinv64, (const double*)L0.b,
+                                                 (double*)L0.v);
   else
-    k_cg_residual<float><<<np, kBS, 0, st>>>(view<double>(L0), f, u, r, (float*)b0, part);
+    k_smooth0<float><<<g, kRowThreads, 0, st>>>(L0.ndof, (float)omega, L0.dinv32,
+                                                (const float*)L0.b, (float*)L0.v);
 }
 
-void launch_cg_check_init(double* part_ff, double* part_rr, int np, DevState* ds,
-                          cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st) {
-  k_cg_check_init<<<1, kBS, 0, st>>>(part_ff, part_rr, np, ds, hc, use_cond);
+void launch_cg_prep(const Level& L0, double* f, double* u, double* part, int np, cudaStream_t st) {
+  k_cg_prep<<<np, kRowThreads, 0, st>>>(L0.nn, L0.mask, f, u, part);
 }
 
-void launch_cg_dots_rz(bool fp64, const Level& L0, const double* r, const void* z, const double* q,
-                       double* part_rz, double* part_zq, int np, cudaStream_t st) {
+void launch_cg_residual(bool fp64, const Level& L0, double omega, const double* f, const double* u,
+                        double* r, int mode, double* part, const double* part_ff, int np,
+                        DevState* ds, unsigned* cnt, cudaGraphConditionalHandle hc, int use_cond,
+                        cudaStream_t st) {
   if (fp64)
-    k_cg_dots_rz<double><<<np, kBS, 0, st>>>(L0.nn, r, (const double*)z, q, part_rz, part_zq);
+    k_cg_residual<double><<<np, kRowThreads, 0, st>>>(view<double>(L0), f, u, r, (double*)L0.b,
+                                                      L0.dinv64, omega, (double*)L0.v, part, part_ff,
+                                                      mode, ds, cnt, hc, use_cond);
   else
-    k_cg_dots_rz<float><<<np, kBS, 0, st>>>(L0.nn, r, (const float*)z, q, part_rz, part_zq);
+    k_cg_residual<float><<<np, kRowThreads, 0, st>>>(view<double>(L0), f, u, r, (float*)L0.b,
+                                                     L0.dinv32, (float)omega, (float*)L0.v, part,
+                                                     part_ff, mode, ds, cnt, hc, use_cond);
 }
 
-void launch_cg_dir(bool fp64, const Level& L0, const double* part_rz, const double* part_zq, int np,
-                   const void* z, double* p, DevState* ds, cudaStream_t st) {
+void launch_cg_dots_rz(bool fp64, const Level& L0, const double* r, const double* q, double* part_rz,
+                       double* part_zq, int np, DevState* ds, unsigned* cnt, cudaStream_t st) {
   if (fp64)
-    k_cg_dir<double><<<np, kBS, 0, st>>>(L0.nn, part_rz, part_zq, np, (const double*)z, p, ds);
+    k_cg_dots_rz<double><<<np, kRowThreads, 0, st>>>(L0.nn, r, (const double*)L0.z, q, part_rz,
+                                                     part_zq, ds, cnt);
   else
-    k_cg_dir<float><<<np, kBS, 0, st>>>(L0.nn, part_rz, part_zq, np, (const float*)z, p, ds);
+    k_cg_dots_rz<float><<<np, kRowThreads, 0, st>>>(L0.nn, r, (const float*)L0.z, q, part_rz,
+                                                    part_zq, ds, cnt);
 }
 
-void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np,
-                     cudaStream_t st) {
-  k_cg_apply<<<np, kBS, 0, st>>>(view<double>(L0), p, q, part);
-}
-
-void launch_cg_update(bool fp64, const Level& L0, const double* part_pq, int np, double* u,
-                      double* r, const double* p, const double* q, void* b0, double* part_rr,
-                      DevState* ds, cudaStream_t st) {
+void launch_cg_dir(bool fp64, const Level& L0, double* p, int np, const DevState* ds,
+                   cudaStream_t st) {
   if (fp64)
-    k_cg_update<double><<<np, kBS, 0, st>>>(L0.nn, part_pq, np, u, r, p, q, (double*)b0, part_rr, ds);
+    k_cg_dir<double><<<np, kRowThreads, 0, st>>>(L0.nn, (const double*)L0.z, p, ds);
   else
-    k_cg_update<float><<<np, kBS, 0, st>>>(L0.nn, part_pq, np, u, r, p, q, (float*)b0, part_rr, ds);
+    k_cg_dir<float><<<np, kRowThreads, 0, st>>>(L0.nn, (const float*)L0.z, p, ds);
 }
 
-void launch_cg_check(const double* part_rr, int np, DevState* ds, cudaGraphConditionalHandle hc,
-                     int use_cond, cudaStream_t st) {
-  k_cg_check<<<1, kBS, 0, st>>>(part_rr, np, ds, hc, use_cond);
+void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np, DevState* ds,
+                     unsigned* cnt, cudaStream_t st) {
+  k_cg_apply<<<np, kRowThreads, 0, st>>>(view<double>(L0), p, q, part, ds, cnt);
 }
 
-void launch_cg_final(const double* part_rr, int np, DevState* ds, cudaStream_t st) {
-  k_cg_final<<<1, kBS, 0, st>>>(part_rr, np, ds);
+void launch_cg_update(bool fp64, const Level& L0, double omega, double* u, double* r, const double* p,
+                      const double* q, double* part_rr, int np, DevState* ds, unsigned* cnt,
+                      cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st) {
+  if (fp64)
+    k_cg_update<double><<<np, kRowThreads, 0, st>>>(L0.nn, u, r, p, q, (double*)L0.b, L0.dinv64, omega,
+                                                     (double*)L0.v, part_rr, ds, cnt, hc, use_cond);
+  else
+    k_cg_update<float><<<np, kRowThreads, 0, st>>>(L0.nn, u, r, p, q, (float*)L0.b, L0.dinv32,
+                                                    (float)omega, (float*)L0.v, part_rr, ds, cnt, hc,
+                                                    use_cond);
 }
 
 void launch_apply_diag(bool fp64, const Level& L, const double* x, double* y, cudaStream_t st) {
   if (fp64)
-    k_apply_diag<double><<<grid_nodes(L.nn), kBS, 0, st>>>(view<double>(L), x, y);
+    k_apply_diag<double><<<grid_nodes(L.nn), kRowThreads, 0, st>>>(view<double>(L), x, y);
   else
-    k_apply_diag<float><<<grid_nodes(L.nn), kBS, 0, st>>>(view<float>(L), x, y);
+    k_apply_diag<float><<<grid_nodes(L.nn), kRowThreads, 0, st>>>(view<float>(L), x, y);
 }
 
 void launch_cast(bool to_fp64, size_t n, const void* a, void* b, bool src_fp64, cudaStream_t st) {

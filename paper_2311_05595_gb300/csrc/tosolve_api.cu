@@ -152,15 +152,19 @@ void free_all(tosolve_s* h) {
     F(L.mask); F(L.S64); F(L.S32); F(L.dinv64); F(L.dinv32); F(L.b); F(L.v); F(L.r); F(L.z);
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
-  F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->Ke);
+  F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
+  F(h->cnt);
   F(h->hx); F(h->hf); F(h->hu); F(h->hg);
   if (h->hs) cudaFreeHost(h->hs);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->evf) cudaEventDestroy(h->evf);
+  if (h->evj) cudaEventDestroy(h->evj);
+  if (h->st2) cudaStreamDestroy(h->st2);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
 }
 
@@ -188,8 +192,7 @@ tosolve_status build_graph(tosolve_s* h) {
     h->err = std::string("begin capture: ") + cudaGetErrorString(e);
     return TOSOLVE_ECUDA;
   }
-  launch_cg_prep(L0, h->f, h->u, h->f, h->u, part0, np, cs);
-  launch_cg_residual(fp64, L0, h->f, h->u, h->r, L0.b, part1, np, cs);
+  launch_cg_prep(L0, h->f, h->u, part0, np, cs);
   cudaStreamCaptureStatus cst;
   cudaGraph_t cgraph = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -198,7 +201,8 @@ tosolve_status build_graph(tosolve_s* h) {
   cudaGraphConditionalHandle hc = 0;
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, cgraph, 1, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) {
-    launch_cg_check_init(part0, part1, np, h->ds, hc, 1, cs);
+    launch_cg_residual(fp64, L0, h->d.omega, h->f, h->u, h->r, 1, part1, part0, np, h->ds, h->cnt, hc,
+                       1, cs);
     e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cgraph, &deps, nullptr, &ndeps);
   }
   cudaGraphNode_t cnode = nullptr;
@@ -215,18 +219,17 @@ tosolve_status build_graph(tosolve_s* h) {
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, bs);
-    launch_cg_dots_rz(fp64, L0, h->r, L0.z, h->q, part2, part3, np, bs);
-    launch_cg_dir(fp64, L0, part2, part3, np, L0.z, h->p, h->ds, bs);
-    launch_cg_apply(L0, h->p, h->q, part0, np, bs);
-    launch_cg_update(fp64, L0, part0, np, h->u, h->r, h->p, h->q, L0.b, part1, h->ds, bs);
-    launch_cg_check(part1, np, h->ds, hc, 1, bs);
+    launch_cg_dots_rz(fp64, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, bs);
+    launch_cg_dir(fp64, L0, h->p, np, h->ds, bs);
+    launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, bs);
+    launch_cg_update(fp64, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, hc, 1,
+                     bs);
     cudaGraph_t bo = nullptr;
     e = cudaStreamEndCapture(bs, &bo);
   }
-  if (e == cudaSuccess) {
-    launch_cg_residual(fp64, L0, h->f, h->u, h->tmpa, nullptr, part1, np, cs);
-    launch_cg_final(part1, np, h->ds, cs);
-  }
+  if (e == cudaSuccess)
+    launch_cg_residual(fp64, L0, h->d.omega, h->f, h->u, h->tmpa, 2, part1, part0, np, h->ds, h->cnt,
+                       hc, 0, cs);
   cudaError_t e2 = cudaStreamEndCapture(cs, &g);
   cudaStreamDestroy(bs);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -391,6 +394,20 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
     if (ke > keB) keB = ke;
   }
   CKC(dalloc(h, (double**)&h->Ke, keB));
+  {
+    const Plan::Lv& c = P.lv[P.L - 1];
+    CKC(dalloc(h, &h->Kec, (size_t)c.ex * c.ey * c.ez * kSym));
+    CKC(dalloc(h, &h->Momc, (size_t)c.ex * c.ey * c.ez * 27));
+    size_t em = 1;
+    for (int l = 1; l < P.L; ++l) {
+      const size_t e = (size_t)P.lv[l].ex * P.lv[l].ey * P.lv[l].ez;
+      if (e > em) em = e;
+    }
+    CKC(dalloc(h, &h->Mom, em * 27));
+  }
+  CKC(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
+  CKC(cudaEventCreateWithFlags(&h->evf, cudaEventDisableTiming));
+  CKC(cudaEventCreateWithFlags(&h->evj, cudaEventDisableTiming));
   // coarse dense solve
   {
     const long nc = P.nc, nblk = (nc + kNB - 1) / kNB;
@@ -398,6 +415,7 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
     CKC(dalloc(h, &h->Wp, nc * kNB));
     CKC(dalloc(h, &h->Dblk, nblk * kNB * kNB));
     CKC(dalloc(h, &h->Xinv, nc * nc));
+    CKC(cudaMemset(h->Xinv, 0, nc * nc * sizeof(double)));
     CKC(dalloc(h, &h->Ainv, nc * nc));
     h->cgrid = coarse_factor_grid();
     if (h->cgrid < 1) { h->err = "coarse factor kernel cannot be made co-resident"; return fail(TOSOLVE_ECUDA); }
@@ -411,6 +429,8 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
   }
   CKC(dalloc(h, &h->part, 4 * kMaxPart));
   CKC(cudaMemset(h->part, 0, 4 * kMaxPart * 8));
+  CKC(dalloc(h, &h->cnt, 4));
+  CKC(cudaMemset(h->cnt, 0, 4 * sizeof(unsigned)));
   CKC(dalloc(h, &h->ds, 1));
   CKC(cudaMemset(h->ds, 0, sizeof(DevState)));
   CKC(cudaMallocHost((void**)&h->hs, sizeof(DevState)));
@@ -453,63 +473,89 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
   cudaStream_t st = h->st;
   const tosolve_desc& d = h->d;
   const int n = d.n_mr;
+  const int L = h->L;
+  const bool fp32 = d.precision == TOSOLVE_PREC_FP32;
   launch_filter_fwd(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, h->invom, x_dev, d.Emin,
                     d.E0 - d.Emin, d.penal, h->rho, h->w, st);
-  const bool fp32 = d.precision == TOSOLVE_PREC_FP32;
-  for (int l = 0; l < h->L; ++l) {
-    Level& L = h->lv[l];
-    if (l == 0) {
-      launch_elem_direct(true, L, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, st);
-      launch_assemble(true, L, h->Ke, L.S64, L.dinv64, st);
-      if (L.S32) {
-        launch_to_fp32((size_t)243 * L.nn, L.S64, L.S32, st);
-        launch_to_fp32((size_t)L.ndof, L.dinv64, L.dinv32, st);
-      }
-    } else {
-      const bool op64 = !fp32 || l == h->L - 1;
-      launch_elem_moments(op64, L, h->w, h->Dx, h->Dy, h->cmom64, h->Ke, st);
-      if (op64)
-        launch_assemble(true, L, h->Ke, L.S64, L.dinv64, st);
-      else
-        launch_assemble(false, L, h->Ke, L.S32, L.dinv32, st);
+  // The coarsest level (FP64 operator, dense matrix, Cholesky and inverse)
+  // only needs the weights: with more than one level it runs on a second
+  // stream, overlapped with the FP64-bound assembly of the finer levels.
+  cudaStream_t cst = st;
+  if (L > 1) {
+    CK(cudaEventRecord(h->evf, st));
+    CK(cudaStreamWaitEvent(h->st2, h->evf, 0));
+    cst = h->st2;
+  }
+  Level& C = h->lv[L - 1];
+  if (L > 1) {
+    launch_elem_moments(true, C, h->w, h->Dx, h->Dy, h->cmom64, h->Momc, h->Kec, cst);
+    launch_assemble(true, C, h->Kec, C.S64, C.dinv64, cst);
+  } else {
+    launch_elem_direct(true, C, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, cst);
+    launch_assemble(true, C, h->Ke, C.S64, C.dinv64, cst);
+    if (C.S32) {
+      launch_to_fp32((size_t)243 * C.nn, C.S64, C.S32, cst);
+      launch_to_fp32((size_t)C.ndof, C.dinv64, C.dinv32, cst);
     }
   }
-  Level& C = h->lv[h->L - 1];
-  CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), st));
-  launch_coarse_dense(C, h->Ad, st);
-  CK(cudaMemsetAsync(&h->ds->coarse_status, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), cst));
+  launch_coarse_dense(C, h->Ad, cst);
+  CK(cudaMemsetAsync(&h->ds->coarse_status, 0, sizeof(int), cst));
   CK(launch_coarse_factor(h->nc, h->Ad, h->Wp, h->Dblk, h->Xinv, h->Ainv, &h->ds->coarse_status,
-                          h->cgrid, st));
+                          h->cgrid, cst));
+  for (int l = 0; l + 1 < L; ++l) {
+    Level& Lv = h->lv[l];
+    if (l == 0) {
+      launch_elem_direct(true, Lv, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, st);
+      launch_assemble(true, Lv, h->Ke, Lv.S64, Lv.dinv64, st);
+      if (Lv.S32) {
+        launch_to_fp32((size_t)243 * Lv.nn, Lv.S64, Lv.S32, st);
+        launch_to_fp32((size_t)Lv.ndof, Lv.dinv64, Lv.dinv32, st);
+      }
+    } else {
+      const bool op64 = !fp32;
+      launch_elem_moments(op64, Lv, h->w, h->Dx, h->Dy, h->cmom64, h->Mom, h->Ke, st);
+      if (op64)
+        launch_assemble(true, Lv, h->Ke, Lv.S64, Lv.dinv64, st);
+      else
+        launch_assemble(false, Lv, h->Ke, Lv.S32, Lv.dinv32, st);
+    }
+  }
+  if (L > 1) {
+    CK(cudaEventRecord(h->evj, h->st2));
+    CK(cudaStreamWaitEvent(st, h->evj, 0));
+  }
   CK(cudaGetLastError());
   h->have_rho = true;
   return TOSOLVE_OK;
 }
 
 static tosolve_status run_loop_nograph(tosolve_t h) {
-  // Same kernels as the graph, driven from the host (debug path).
+  // Same kernels as the graph, driven from the host (profiling path: ncu
+  // cannot profile kernels of a graph that holds a conditional node).
   const bool fp64 = prec_fp64(h);
   Level& L0 = h->lv[0];
   const int np = h->np;
   double *part0 = h->part, *part1 = h->part + kMaxPart, *part2 = h->part + 2 * kMaxPart,
          *part3 = h->part + 3 * kMaxPart;
   cudaStream_t st = h->st;
-  launch_cg_prep(L0, h->f, h->u, h->f, h->u, part0, np, st);
-  launch_cg_residual(fp64, L0, h->f, h->u, h->r, L0.b, part1, np, st);
-  launch_cg_check_init(part0, part1, np, h->ds, 0, 0, st);
+  launch_cg_prep(L0, h->f, h->u, part0, np, st);
+  launch_cg_residual(fp64, L0, h->d.omega, h->f, h->u, h->r, 1, part1, part0, np, h->ds, h->cnt, 0, 0,
+                     st);
   CK(cudaMemcpyAsync(h->hs, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   while (!h->hs->converged && h->hs->status == 0 && h->hs->iter < h->hs->maxit) {
     launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, st);
-    launch_cg_dots_rz(fp64, L0, h->r, L0.z, h->q, part2, part3, np, st);
-    launch_cg_dir(fp64, L0, part2, part3, np, L0.z, h->p, h->ds, st);
-    launch_cg_apply(L0, h->p, h->q, part0, np, st);
-    launch_cg_update(fp64, L0, part0, np, h->u, h->r, h->p, h->q, L0.b, part1, h->ds, st);
-    launch_cg_check(part1, np, h->ds, 0, 0, st);
+    launch_cg_dots_rz(fp64, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, st);
+    launch_cg_dir(fp64, L0, h->p, np, h->ds, st);
+    launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, st);
+    launch_cg_update(fp64, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, 0, 0,
+                     st);
     CK(cudaMemcpyAsync(h->hs, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
-  launch_cg_residual(fp64, L0, h->f, h->u, h->tmpa, nullptr, part1, np, st);
-  launch_cg_final(part1, np, h->ds, st);
+  launch_cg_residual(fp64, L0, h->d.omega, h->f, h->u, h->tmpa, 2, part1, part0, np, h->ds, h->cnt, 0,
+                     0, st);
   return TOSOLVE_OK;
 }
 
@@ -706,6 +752,7 @@ tosolve_status tosolve_precondition(tosolve_t h, const double* b_dev, double* z_
     CK(cudaMemcpyAsync(L0.b, b_dev, (size_t)L0.ndof * 8, cudaMemcpyDeviceToDevice, h->st));
   else
     launch_cast(false, (size_t)L0.ndof, b_dev, L0.b, true, h->st);
+  if (h->L > 1) launch_smooth0(fp64, L0, h->d.omega, h->st);
   launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, h->st);
   launch_cast(true, (size_t)L0.ndof, L0.z, z_dev, fp64, h->st);
   CK(cudaGetLastError());
