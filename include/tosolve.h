@@ -61,7 +61,11 @@ typedef enum {
  * and the gradient are always FP64). */
 typedef enum {
   TOSOLVE_PREC_FP64 = 0, /* plain FP64 MG-PCG                                */
-  TOSOLVE_PREC_FP32 = 1  /* FP32 V-cycle operators and vectors, FP32 accum.  */
+  TOSOLVE_PREC_FP32 = 1, /* FP32 V-cycle operators and vectors, FP32 accum.  */
+  TOSOLVE_PREC_TF32 = 2  /* as FP32, but the finest level's operator is the  */
+                         /* stacked subcell contraction of Eq. matrixK_mr on */
+                         /* the tcgen05 tensor cores (TF32 operands, FP32    */
+                         /* accumulation in TMEM); needs n_mr <= 2           */
 } tosolve_precision;
 
 /* Problem and solver description (Sec. 2, 3.1, 7 intro). */
@@ -167,8 +171,10 @@ tosolve_status tosolve_subcell_table(tosolve_t h, double* table_dev);
 tosolve_status tosolve_densities(tosolve_t h, double* rho_dev, double* w_dev);
 
 /* y = A_l x for the level-l operator (fixed rows/columns replaced by
- * identity), computed in FP64 (precision 0) or in the preconditioner's FP32
- * form (precision 1; inputs/outputs still FP64).  x_dev, y_dev: 3*nodes(l).
+ * identity), computed in FP64 (precision 0), in the preconditioner's FP32
+ * stencil form (precision 1) or, on level 0 of a TF32 handle, as the
+ * tensor-core stacked contraction plus node gather (precision 2); inputs and
+ * outputs are FP64.  x_dev, y_dev: 3*nodes(l).
  * Level 0 FP64 is K(rho) of Eq. matrixK_mr; coarser levels are re-discretised
  * from the density field (Sec. 7.2: system matrices of each mesh level). */
 tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double* x_dev,

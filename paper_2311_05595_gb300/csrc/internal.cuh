@@ -25,7 +25,7 @@ constexpr int kMaxPart = 608;  // partial sums per reduction (4 blocks per SM)
 constexpr int kMaxLevels = 8;
 constexpr int kEdofQ1 = 24;    // DOFs of a trilinear hexahedron
 constexpr int kSym = 300;      // entries of a 24x24 symmetric upper triangle
-constexpr int kNB = 16;        // block size of the coarse Cholesky
+constexpr int kNB = 32;        // block size of the coarse Cholesky
 constexpr int kTile = 32;      // output tile of the coarse inverse product
 constexpr int kMaxCoarse = 4096;  // largest coarse system (DOFs)
 
@@ -46,7 +46,8 @@ struct DevState {
   int status;      // 0 ok, TOSOLVE_EBREAKDOWN on breakdown
   int converged;
   int coarse_status;  // non-zero if the coarse Cholesky met a bad pivot
-  int pad[3];
+  int tc_status;      // non-zero if a tensor-core tile wait timed out
+  int pad[2];
 };
 
 struct Level {
@@ -94,14 +95,34 @@ void launch_assemble(bool fp64, const Level& L, const void* Ke, void* S, void* d
 void launch_to_fp32(size_t n, const double* a, float* b, cudaStream_t st);
 void launch_coarse_dense(const Level& L, double* A, cudaStream_t st);
 cudaError_t launch_coarse_factor(int n, double* A, double* W, double* Dblk, double* X,
-                                 double* Ainv, int* status, int grid, cudaStream_t st);
+                                 double* Ainv, double* Pq, int* status, int grid, cudaStream_t st);
 int coarse_factor_grid();
+
+// ---- launchers (k_tc.cu) -------------------------------------------------
+// Finest-level operator of the TF32 preconditioner on tcgen05.
+struct TcOp {
+  bool on = false;
+  int m = 1;                // subcells per element
+  const float* w32 = nullptr;  // E x m element-major weights
+  const float* KT = nullptr;   // m x 24 x 24 FP32 table
+  float* Ye = nullptr;         // E x 24 element results
+  int* err = nullptr;
+  int sms = 1;
+};
+bool tc_supported(int n);
+cudaError_t launch_tc_apply(const Level& L0, int m, const float* v, const float* w32, const float* KT,
+                            float* Ye, int* err, int sms, cudaStream_t st);
+void launch_tc_gather(const Level& L0, const float* Ye, const float* b, const float* v, const float* dinv,
+                      float omega, int mode, float* out, cudaStream_t st);
+void launch_weights_elem(const Level& L0, int n, const double* w, int Dx, int Dy, float* w32,
+                         cudaStream_t st);
+void launch_mask_fp32(const Level& L, float* x, cudaStream_t st);
 
 // ---- launchers (k_solve.cu) ----------------------------------------------
 template <typename T>
 LevelView<T> view(const Level& L);
 void launch_vcycle(bool fp64, Level* lv, int L, double omega, int gamma, const double* Ainv,
-                   cudaStream_t st);
+                   const TcOp& tc, cudaStream_t st);
 void launch_smooth0(bool fp64, const Level& L0, double omega, cudaStream_t st);
 void launch_cg_prep(const Level& L0, double* f, double* u, double* part, int np, cudaStream_t st);
 void launch_cg_residual(bool fp64, const Level& L0, double omega, const double* f, const double* u,
@@ -138,6 +159,13 @@ inline int parts_for(long nn) {
   return (int)(g < kMaxPart ? (g < 1 ? 1 : g) : kMaxPart);
 }
 
+// Number of q-chunks the coarse inverse product is split into (partial
+// sums scratch of coarse_qchunks(n) * n^2 doubles).
+__host__ __device__ inline int coarse_qchunks(int n) {
+  const int q = (n + 63) / 64;
+  return q < 4 ? (q < 1 ? 1 : q) : 4;
+}
+
 __host__ __device__ inline int sym_index(int r, int c) {
   // r <= c < 24: row-major upper triangle
   return r * kEdofQ1 - (r * (r - 1)) / 2 + (c - r);
@@ -169,6 +197,10 @@ struct tosolve_s {
   double* tab64 = nullptr;     // m x 24 x 24
   double* tabsym64 = nullptr;  // m x 300
   double* cmom64 = nullptr;    // 27 x 300
+  float* KT32 = nullptr;       // m x 24 x 24 FP32 (tensor-core operand)
+  float* w32 = nullptr;        // E x m element-major FP32 weights
+  float* Ye = nullptr;         // E x 24 element results of the tensor-core apply
+  tos::TcOp tc;
   void* Ke = nullptr;
   double* Kec = nullptr;  // element matrices of the coarsest level (second stream)
   double* Mom = nullptr;   // 27 moments per element, finer coarse levels
@@ -180,6 +212,7 @@ struct tosolve_s {
   double* Dblk = nullptr;
   double* Xinv = nullptr;
   double* Ainv = nullptr;
+  double* Pq = nullptr;  // partial sums of the coarse inverse product
   int cgrid = 1;
   // PCG
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *f = nullptr;

@@ -389,10 +389,15 @@ __global__ void k_coarse_dense(int Lx, int Ly, int Lz, const double* __restrict_
 // X = L^{-1} (block rows) and A^{-1} = X^T X, in one cooperative launch.
 // The V-cycle's coarse solve is then one dense matrix-vector product spread
 // over many SMs (FP64 issues 4 flop/clk/SM on this part, so a sequential
-// triangular solve on one SM would dominate the cycle).  FP64 latency is
-// long here, so no thread runs a long dependent chain: pivots use one
-// reciprocal each, inner products use four independent accumulators or a
-// whole warp, and the final product is a shared-memory tiled product.
+// triangular solve on one SM would dominate the cycle).
+//
+// FP64 latency is long here, so the work is shaped for it: one reciprocal
+// square root per pivot; the trailing update, the inverse and the final
+// product are tiled 16x16 with operands staged in shared memory (short,
+// independent FMA chains, coalesced loads); the final product is split
+// into (tile, q-chunk) items whose partial sums are added in a fixed order.
+constexpr int kCT = 16;   // output tile of the parallel phases
+
 __device__ __forceinline__ double dot4(const double* a, int sa, const double* b, int sb, int len) {
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int q = 0;
@@ -406,19 +411,30 @@ __device__ __forceinline__ double dot4(const double* a, int sa, const double* b,
   return (s0 + s1) + (s2 + s3);
 }
 
-__global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restrict__ W,
-                                double* __restrict__ Dblk, double* __restrict__ X,
-                                double* __restrict__ Ainv, int* __restrict__ status) {
+// Lower-triangle tile index -> (ti, tj) with tj <= ti.
+__device__ __forceinline__ void tri_tile(int tile, int& ti, int& tj) {
+  int t = 0;
+  while ((t + 1) * (t + 2) / 2 <= tile) ++t;
+  ti = t;
+  tj = tile - t * (t + 1) / 2;
+}
+
+__global__ void __launch_bounds__(256) k_coarse_factor(int n, double* __restrict__ A,
+                                                       double* __restrict__ W,
+                                                       double* __restrict__ Dblk,
+                                                       double* __restrict__ X,
+                                                       double* __restrict__ Ainv,
+                                                       double* __restrict__ Pq,
+                                                       int* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double a[kNB][kNB + 1];
   __shared__ double li[kNB][kNB + 1];
   __shared__ double dinv[kNB];
-  __shared__ double ta[kTile][kTile + 1];
-  __shared__ double tb[kTile][kTile + 1];
+  __shared__ double sa[kCT][kNB + 1];  // staged rows (tile i side)
+  __shared__ double sb[kCT][kNB + 1];  // staged rows (tile j side)
   const int tid = threadIdx.x, bd = blockDim.x;
   const long gtid = blockIdx.x * (long)bd + tid, gstride = (long)gridDim.x * bd;
-  const int lane = tid & 31;
-  const long gwarp = gtid >> 5, nwarps = gstride >> 5;
+  const int ty = tid / kCT, tx = tid % kCT;  // 16 x 16 threads
   const int nblk = (n + kNB - 1) / kNB;
   for (int kb = 0; kb < nblk; ++kb) {
     const int k0 = kb * kNB, nb = min(kNB, n - k0);
@@ -436,21 +452,27 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
           if (blockIdx.x == 0) atomicExch(status, 1);
           d = 1.0;
         }
-        const double sq = sqrt(d);
-        a[jj][jj] = sq;
-        dinv[jj] = 1.0 / sq;
+        const double ri = rsqrt(d);
+        a[jj][jj] = d * ri;
+        dinv[jj] = ri;
       }
       __syncthreads();
+      const int m = nb - jj - 1;
       for (int i = jj + 1 + tid; i < nb; i += bd) a[i][jj] *= dinv[jj];
       __syncthreads();
-      const int m = nb - jj - 1;
-      for (int t = tid; t < m * m; t += bd) {
-        const int i = jj + 1 + t / m, j = jj + 1 + t % m;
-        if (j <= i) a[i][j] -= a[i][jj] * a[j][jj];
+      // rank-1 update of the lower triangle only (compact indexing: every
+      // lane of a warp has an entry, one FMA each)
+      for (int t = tid; t < m * (m + 1) / 2; t += bd) {
+        int ii = (int)((sqrt(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+        while (ii * (ii + 1) / 2 > t) --ii;
+        const int jx = t - ii * (ii + 1) / 2;
+        const int i = jj + 1 + ii, j = jj + 1 + jx;
+        a[i][j] -= a[i][jj] * a[j][jj];
       }
       __syncthreads();
     }
-    // inverse of the unit... of L_kk, column-parallel forward substitution
+    // inverse of L_kk, column-parallel forward substitution
     for (int k = 0; k < nb; ++k) {
       for (int j = tid; j <= k; j += bd) li[k][j] *= dinv[k];
       __syncthreads();
@@ -468,7 +490,7 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
       W[(size_t)i * kNB + jj] = dot4(A + (size_t)i * n + k0, 1, &li[jj][0], 1, jj + 1);
     }
     grid.sync();
-    // (C) write L_kk, its inverse and the panel; update the trailing matrix
+    // (C) write L_kk, its inverse and the panel; trailing update in 16x16 tiles
     if (blockIdx.x == 0) {
       for (int t = tid; t < kNB * kNB; t += bd) {
         const int i = t / kNB, j = t % kNB;
@@ -480,25 +502,42 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
       const int i = k0 + nb + (int)(t / nb), jj = (int)(t % nb);
       A[(size_t)i * n + k0 + jj] = W[(size_t)i * kNB + jj];
     }
-    for (long t = gtid; t < (long)rows * rows; t += gstride) {
-      int i = (int)(t / rows), j = (int)(t % rows);
-      if (j > i) continue;
-      i += k0 + nb;
-      j += k0 + nb;
-      A[(size_t)i * n + j] -= dot4(W + (size_t)i * kNB, 1, W + (size_t)j * kNB, 1, nb);
+    const int tr = (rows + kCT - 1) / kCT;
+    for (int tile = blockIdx.x; tile < tr * (tr + 1) / 2; tile += gridDim.x) {
+      int ti, tj;
+      tri_tile(tile, ti, tj);
+      const int i0 = k0 + nb + ti * kCT, j0 = k0 + nb + tj * kCT;
+      __syncthreads();
+      for (int t = tid; t < kCT * kNB; t += bd) {
+        const int r = t / kNB, q = t % kNB;
+        sa[r][q] = (i0 + r < n && q < nb) ? W[(size_t)(i0 + r) * kNB + q] : 0.0;
+        sb[r][q] = (j0 + r < n && q < nb) ? W[(size_t)(j0 + r) * kNB + q] : 0.0;
+      }
+      __syncthreads();
+      const int i = i0 + ty, j = j0 + tx;
+      if (i < n && j < n && j <= i) {
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int q = 0; q < kNB; q += 2) {
+          s0 += sa[ty][q] * sb[tx][q];
+          s1 += sa[ty][q + 1] * sb[tx][q + 1];
+        }
+        A[(size_t)i * n + j] -= s0 + s1;
+      }
     }
     grid.sync();
   }
   // X = L^{-1}, one block row at a time: X_ib,jb = -Linv_ib * sum_q L_ib,q X_q,jb
   for (int ib = 0; ib < nblk; ++ib) {
     const int i0 = ib * kNB, nbi = min(kNB, n - i0);
-    // T[r][j] = sum_{q=j}^{i0-1} L[i0+r][q] X[q][j]: one warp per (r, j)
-    for (long w = gwarp; w < (long)nbi * i0; w += nwarps) {
-      const int r = (int)(w / i0), j = (int)(w % i0);
-      double s = 0.0;
-      for (int q = j + lane; q < i0; q += 32) s += A[(size_t)(i0 + r) * n + q] * X[(size_t)q * n + j];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) Ainv[(size_t)r * n + j] = s;  // Ainv rows 0..nbi-1 hold T
+    // T[r][j] = sum_{q=j}^{i0-1} L[i0+r][q] X[q][j]; consecutive threads take
+    // consecutive j and walk the same absolute q (X[q][j] = 0 for q < j, so
+    // starting at the warp's first j is exact): coalesced X rows, L broadcast,
+    // four independent accumulators
+    for (long t = gtid; t < (long)nbi * i0; t += gstride) {
+      const int r = (int)(t / i0), j = (int)(t % i0);
+      const int q0 = j & ~31;
+      Ainv[(size_t)r * n + j] = dot4(A + (size_t)(i0 + r) * n + q0, 1, X + (size_t)q0 * n + j, n, i0 - q0);
     }
     grid.sync();
     const double* Li = Dblk + (size_t)ib * kNB * kNB;
@@ -514,40 +553,46 @@ __global__ void k_coarse_factor(int n, double* __restrict__ A, double* __restric
     }
     grid.sync();
   }
-  // A^{-1} = X^T X: 32x32 output tiles (lower triangle), shared-memory staged
-  const int nt = (n + kTile - 1) / kTile;
+  // A^{-1} = X^T X: items (16x16 lower tile, 64-wide q chunk) -> partials in
+  // Pq[chunk], then every entry adds its chunks in order.
+  const int nt = (n + kCT - 1) / kCT;
+  const int nq = coarse_qchunks(n);
+  const int kQC = ((n + nq - 1) / nq + kNB - 1) / kNB * kNB;  // q-chunk length
   const int ntiles = nt * (nt + 1) / 2;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int ti = 0;
-    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
-    const int tj = tile - ti * (ti + 1) / 2;
-    const int i0 = ti * kTile, j0 = tj * kTile;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const int ly = tid / kTile, lx = tid % kTile;  // 8 x 32 threads, 4 rows each
-    for (int q0 = i0; q0 < n; q0 += kTile) {
+  for (int item = blockIdx.x; item < ntiles * nq; item += gridDim.x) {
+    const int tile = item / nq, qc = item % nq;
+    int ti, tj;
+    tri_tile(tile, ti, tj);
+    const int i0 = ti * kCT, j0 = tj * kCT;
+    const int qlo = max(qc * kQC, i0), qhi = min((qc + 1) * kQC, n);
+    const int i = i0 + ty, j = j0 + tx;
+    double s0 = 0.0, s1 = 0.0;
+    for (int q0 = qlo; q0 < qhi; q0 += kNB) {
       __syncthreads();
-      for (int t = tid; t < kTile * kTile; t += bd) {
-        const int qq = t / kTile, c = t % kTile;
+      for (int t = tid; t < kCT * kNB; t += bd) {
+        const int c = t / kNB, qq = t % kNB;
         const int q = q0 + qq;
-        ta[qq][c] = (q < n && i0 + c < n) ? X[(size_t)q * n + i0 + c] : 0.0;
-        tb[qq][c] = (q < n && j0 + c < n) ? X[(size_t)q * n + j0 + c] : 0.0;
+        sa[c][qq] = (q < qhi && i0 + c < n) ? X[(size_t)q * n + i0 + c] : 0.0;
+        sb[c][qq] = (q < qhi && j0 + c < n) ? X[(size_t)q * n + j0 + c] : 0.0;
       }
       __syncthreads();
-#pragma unroll 4
-      for (int qq = 0; qq < kTile; ++qq) {
-        const double bx = tb[qq][lx];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] += ta[qq][ly + 8 * u] * bx;
+      for (int qq = 0; qq < kNB; qq += 2) {
+        s0 += sa[ty][qq] * sb[tx][qq];
+        s1 += sa[ty][qq + 1] * sb[tx][qq + 1];
       }
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + ly + 8 * u, j = j0 + lx;
-      if (i < n && j < n && j <= i) {
-        Ainv[(size_t)i * n + j] = acc[u];
-        Ainv[(size_t)j * n + i] = acc[u];
-      }
-    }
+    if (i < n && j < n && j <= i) Pq[((size_t)qc * n + i) * n + j] = s0 + s1;
+  }
+  grid.sync();
+  for (long t = gtid; t < (long)n * n; t += gstride) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (j > i) continue;
+    double s = 0.0;
+    for (int qc = 0; qc < nq; ++qc)
+      if ((qc + 1) * kQC > ((i / kCT) * kCT)) s += Pq[((size_t)qc * n + i) * n + j];
+    Ainv[(size_t)i * n + j] = s;
+    Ainv[(size_t)j * n + i] = s;
   }
 }
 
@@ -658,16 +703,14 @@ int coarse_factor_grid() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_factor, 256, 0);
-  // at most 64 blocks (one per SM): the factorisation is latency-bound, a
-  // smaller grid makes its barriers cheaper and leaves SMs to the
-  // concurrent fine-level assembly
+  // one block per SM (co-resident as long as one block fits, checked here)
   if (per < 1) return 0;
-  return sms < 64 ? sms : 64;
+  return sms;
 }
 
 cudaError_t launch_coarse_factor(int n, double* A, double* W, double* Dblk, double* X,
-                                 double* Ainv, int* status, int grid, cudaStream_t st) {
-  void* args[] = {&n, &A, &W, &Dblk, &X, &Ainv, &status};
+                                 double* Ainv, double* Pq, int* status, int grid, cudaStream_t st) {
+  void* args[] = {&n, &A, &W, &Dblk, &X, &Ainv, &Pq, &status};
   return cudaLaunchCooperativeKernel((void*)k_coarse_factor, dim3(grid), dim3(256), args, 0, st);
 }
 

@@ -427,7 +427,8 @@ template <>
 const float* dinv_of<float>(const Level& L) { return L.dinv32; }
 
 template <typename T>
-void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, cudaStream_t st) {
+void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp& tc,
+                cudaStream_t st) {
   Level& F = lv[l];
   if (l == L - 1) {
     const int n = F.ndof;
@@ -439,13 +440,30 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, cudaStream
   Level& C = lv[l + 1];
   const LevelView<T> V = view<T>(F);
   const bool c_coarsest = (l + 1 == L - 1);
-  k_vc_pre<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(V, (const T*)F.b, (const T*)F.v, (T*)F.r);
+  const bool use_tc = tc.on && l == 0;
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc) {  // r = b - A v with A v from the tensor-core stacked contraction
+      launch_tc_apply(F, tc.m, (const float*)F.v, tc.w32, tc.KT, tc.Ye, tc.err, tc.sms, st);
+      launch_tc_gather(F, tc.Ye, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 0,
+                       (float*)F.r, st);
+    }
+  }
+  if (!use_tc)
+    k_vc_pre<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(V, (const T*)F.b, (const T*)F.v, (T*)F.r);
   k_vc_restrict<T><<<grid_nodes(C.nn), kRowThreads, 0, st>>>(
       F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, C.mask, (const T*)F.r, (T*)C.b,
       c_coarsest ? nullptr : dinv_of<T>(C), omega, c_coarsest ? nullptr : (T*)C.v);
-  vcycle_rec<T>(lv, l + 1, L, omega, Ainv, st);
+  vcycle_rec<T>(lv, l + 1, L, omega, Ainv, tc, st);
   k_vc_prolong<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, F.mask,
                                                             (const T*)C.z, (T*)F.v);
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc) {  // z = v + omega D^-1 (b - A v)
+      launch_tc_apply(F, tc.m, (const float*)F.v, tc.w32, tc.KT, tc.Ye, tc.err, tc.sms, st);
+      launch_tc_gather(F, tc.Ye, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 1,
+                       (float*)F.z, st);
+      return;
+    }
+  }
   k_vc_post<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(V, omega, (const T*)F.b, (const T*)F.v,
                                                          (T*)F.z);
 }
@@ -453,12 +471,12 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, cudaStream
 }  // namespace
 
 void launch_vcycle(bool fp64, Level* lv, int L, double omega, int gamma, const double* Ainv,
-                   cudaStream_t st) {
+                   const TcOp& tc, cudaStream_t st) {
   (void)gamma;
   if (fp64)
-    vcycle_rec<double>(lv, 0, L, omega, Ainv, st);
+    vcycle_rec<double>(lv, 0, L, omega, Ainv, tc, st);
   else
-    vcycle_rec<float>(lv, 0, L, (float)omega, Ainv, st);
+    vcycle_rec<float>(lv, 0, L, (float)omega, Ainv, tc, st);
 }
 
 void launch_smooth0(bool fp64, const Level& L0, double omega, cudaStream_t st) {

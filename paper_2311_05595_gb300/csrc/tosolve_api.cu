@@ -77,14 +77,19 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (!(d.nu > -1.0 && d.nu < 0.5)) { *why = "nu must be in (-1, 0.5)"; return TOSOLVE_EINVAL; }
   if (!(d.penal >= 1.0)) { *why = "penal must be >= 1"; return TOSOLVE_EINVAL; }
   if (!(d.rmin >= 0.0) || d.rmin * d.n_mr > 16.0) { *why = "rmin*n_mr must be in [0, 16]"; return TOSOLVE_EINVAL; }
-  if (d.precision != TOSOLVE_PREC_FP64 && d.precision != TOSOLVE_PREC_FP32) { *why = "unknown precision"; return TOSOLVE_EINVAL; }
+  if (d.precision != TOSOLVE_PREC_FP64 && d.precision != TOSOLVE_PREC_FP32 &&
+      d.precision != TOSOLVE_PREC_TF32) { *why = "unknown precision"; return TOSOLVE_EINVAL; }
+  if (d.precision == TOSOLVE_PREC_TF32 && !tc_supported(d.n_mr)) {
+    *why = "TF32 tensor-core preconditioner needs n_mr <= 2 (24 n^3 stacked rows <= 256)";
+    return TOSOLVE_EINVAL;
+  }
   if (d.omega != 0.0 && !(d.omega > 0.0 && d.omega < 2.0)) { *why = "omega must be in (0, 2)"; return TOSOLVE_EINVAL; }
   if (d.cycle_gamma != 0 && d.cycle_gamma != 1) { *why = "only the V-cycle (gamma = 1) is built"; return TOSOLVE_EINVAL; }
   if (d.max_rhs < 0 || d.max_rhs > 64) { *why = "max_rhs must be in 0..64"; return TOSOLVE_EINVAL; }
   int L = d.mg_levels;
   if (L == 0) {
     L = 1;
-    while (L < kMaxLevels && divisible(d, L + 1) && coarse_dofs(d, L) > 3000) ++L;
+    while (L < kMaxLevels && divisible(d, L + 1) && coarse_dofs(d, L) > 1500) ++L;
   }
   if (L < 1 || L > kMaxLevels) { *why = "mg_levels must be in 1..8"; return TOSOLVE_EINVAL; }
   if (!divisible(d, L)) { *why = "nx, ny, nz must be divisible by 2^(mg_levels-1)"; return TOSOLVE_EINVAL; }
@@ -97,7 +102,8 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   P->Dz = d.n_mr * d.nz;
   P->ncell = (long)P->Dx * P->Dy * P->Dz;
   P->noff = count_offsets(d.n_mr, d.rmin);
-  const bool fp32 = d.precision == TOSOLVE_PREC_FP32;
+  const bool fp32 = d.precision != TOSOLVE_PREC_FP64;
+  const bool tf32 = d.precision == TOSOLVE_PREC_TF32 && L > 1;
   const int maxrhs = d.max_rhs > 0 ? d.max_rhs : 1;
   size_t B = 0;
   size_t keB = 0;
@@ -110,7 +116,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     v.nsub = d.n_mr << l;
     const bool coarsest = l == L - 1;
     v.s64 = (l == 0) || !fp32 || coarsest;
-    v.s32 = fp32 && !coarsest;
+    v.s32 = fp32 && !coarsest && !(tf32 && l == 0);  // TF32: level 0 runs on tensor cores
     const size_t tsz = fp32 ? 4 : 8;
     B += v.ndof;  // mask
     if (v.s64) B += 243 * v.nn * 8 + v.ndof * 8;
@@ -128,10 +134,14 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   B += (size_t)P->m * (576 + kSym) * 8 + 27 * kSym * 8;  // tables
   const long nc = P->nc;
   const long nblk = (nc + kNB - 1) / kNB;
-  B += (size_t)(3 * nc * nc + nc * kNB + nblk * kNB * kNB) * 8;
+  B += (size_t)(3 * nc * nc + nc * kNB + nblk * kNB * kNB + (size_t)coarse_qchunks((int)nc) * nc * nc) * 8;
   B += (size_t)ndof0 * 8 * 7;                         // u r p q f tmpa tmpb
   B += (size_t)ndof0 * 8 * 2 * maxrhs;                // host-step staging f, u
   B += 4 * kMaxPart * 8 + sizeof(DevState) + (size_t)P->ncell * 8;
+  if (tf32) {
+    const size_t E0 = (size_t)d.nx * d.ny * d.nz;
+    B += E0 * (P->m + 24) * 4 + (size_t)P->m * 576 * 4 + P->lv[0].ndof * 4;
+  }
   P->bytes = B;
   return TOSOLVE_OK;
 }
@@ -152,8 +162,8 @@ void free_all(tosolve_s* h) {
     F(L.mask); F(L.S64); F(L.S32); F(L.dinv64); F(L.dinv32); F(L.b); F(L.v); F(L.r); F(L.z);
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
-  F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
-  F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv);
+  F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
+  F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv); F(h->Pq);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
   F(h->cnt);
   F(h->hx); F(h->hf); F(h->hu); F(h->hg);
@@ -218,7 +228,7 @@ tosolve_status build_graph(tosolve_s* h) {
   if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, bs);
+    launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, bs);
     launch_cg_dots_rz(fp64, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, bs);
     launch_cg_dir(fp64, L0, h->p, np, h->ds, bs);
     launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, bs);
@@ -288,7 +298,8 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
   h->ncell = (int)P.ncell;
   h->noff = P.noff;
   h->nc = (int)P.nc;
-  const bool fp32 = h->d.precision == TOSOLVE_PREC_FP32;
+  const bool fp32 = h->d.precision != TOSOLVE_PREC_FP64;
+  const bool tf32 = h->d.precision == TOSOLVE_PREC_TF32 && P.L > 1;
   auto fail = [&](tosolve_status st) {
     free_all(h);
     g_err = h->err;
@@ -328,6 +339,7 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
     CKC(cudaMemcpy(L.mask, mask.data(), v.ndof, cudaMemcpyHostToDevice));
     if (v.s64) { CKC(dalloc(h, &L.S64, 243 * v.nn)); CKC(dalloc(h, &L.dinv64, v.ndof)); }
     if (v.s32) { CKC(dalloc(h, &L.S32, 243 * v.nn)); CKC(dalloc(h, &L.dinv32, v.ndof)); }
+    if (tf32 && l == 0) CKC(dalloc(h, &L.dinv32, v.ndof));
     const size_t tsz = fp32 ? 4 : 8;
     void** vecs[4] = {&L.b, &L.v, &L.r, &L.z};
     for (void** pv : vecs) {
@@ -356,6 +368,21 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
   launch_subcell_table(P.n, h->d.nu, 1.0, h->tab64, st);
   launch_symmetrize(P.m, h->tab64, h->tabsym64, st);
   launch_moment_basis(h->d.nu, h->cmom64, st);
+  if (tf32) {  // tensor-core operands of the finest level
+    const size_t E0 = (size_t)P.lv[0].ex * P.lv[0].ey * P.lv[0].ez;
+    CKC(dalloc(h, &h->KT32, (size_t)P.m * 576));
+    CKC(dalloc(h, &h->w32, E0 * P.m));
+    CKC(dalloc(h, &h->Ye, E0 * 24));
+    launch_to_fp32((size_t)P.m * 576, h->tab64, h->KT32, st);
+    int sms = 1;
+    CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+    h->tc.on = true;
+    h->tc.m = P.m;
+    h->tc.w32 = h->w32;
+    h->tc.KT = h->KT32;
+    h->tc.Ye = h->Ye;
+    h->tc.sms = sms;
+  }
   // filter stencil: integer offsets with di^2+dj^2+dk^2 <= (r n)^2 (ties in)
   {
     std::vector<int4> off;
@@ -417,6 +444,7 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
     CKC(dalloc(h, &h->Xinv, nc * nc));
     CKC(cudaMemset(h->Xinv, 0, nc * nc * sizeof(double)));
     CKC(dalloc(h, &h->Ainv, nc * nc));
+    CKC(dalloc(h, &h->Pq, (size_t)coarse_qchunks((int)nc) * nc * nc));
     h->cgrid = coarse_factor_grid();
     if (h->cgrid < 1) { h->err = "coarse factor kernel cannot be made co-resident"; return fail(TOSOLVE_ECUDA); }
   }
@@ -433,6 +461,7 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
   CKC(cudaMemset(h->cnt, 0, 4 * sizeof(unsigned)));
   CKC(dalloc(h, &h->ds, 1));
   CKC(cudaMemset(h->ds, 0, sizeof(DevState)));
+  if (h->tc.on) h->tc.err = &h->ds->tc_status;
   CKC(cudaMallocHost((void**)&h->hs, sizeof(DevState)));
   std::memset(h->hs, 0, sizeof(DevState));
   h->np = parts_for(h->lv[0].nn);
@@ -474,7 +503,7 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
   const tosolve_desc& d = h->d;
   const int n = d.n_mr;
   const int L = h->L;
-  const bool fp32 = d.precision == TOSOLVE_PREC_FP32;
+  const bool fp32 = d.precision != TOSOLVE_PREC_FP64;
   launch_filter_fwd(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, h->invom, x_dev, d.Emin,
                     d.E0 - d.Emin, d.penal, h->rho, h->w, st);
   // The coarsest level (FP64 operator, dense matrix, Cholesky and inverse)
@@ -501,17 +530,16 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
   CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), cst));
   launch_coarse_dense(C, h->Ad, cst);
   CK(cudaMemsetAsync(&h->ds->coarse_status, 0, sizeof(int), cst));
-  CK(launch_coarse_factor(h->nc, h->Ad, h->Wp, h->Dblk, h->Xinv, h->Ainv, &h->ds->coarse_status,
-                          h->cgrid, cst));
+  CK(launch_coarse_factor(h->nc, h->Ad, h->Wp, h->Dblk, h->Xinv, h->Ainv, h->Pq,
+                          &h->ds->coarse_status, h->cgrid, cst));
   for (int l = 0; l + 1 < L; ++l) {
     Level& Lv = h->lv[l];
     if (l == 0) {
       launch_elem_direct(true, Lv, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, st);
       launch_assemble(true, Lv, h->Ke, Lv.S64, Lv.dinv64, st);
-      if (Lv.S32) {
-        launch_to_fp32((size_t)243 * Lv.nn, Lv.S64, Lv.S32, st);
-        launch_to_fp32((size_t)Lv.ndof, Lv.dinv64, Lv.dinv32, st);
-      }
+      if (Lv.S32) launch_to_fp32((size_t)243 * Lv.nn, Lv.S64, Lv.S32, st);
+      if (Lv.dinv32) launch_to_fp32((size_t)Lv.ndof, Lv.dinv64, Lv.dinv32, st);
+      if (h->tc.on) launch_weights_elem(Lv, n, h->w, h->Dx, h->Dy, h->w32, st);
     } else {
       const bool op64 = !fp32;
       launch_elem_moments(op64, Lv, h->w, h->Dx, h->Dy, h->cmom64, h->Mom, h->Ke, st);
@@ -545,7 +573,7 @@ static tosolve_status run_loop_nograph(tosolve_t h) {
   CK(cudaMemcpyAsync(h->hs, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   while (!h->hs->converged && h->hs->status == 0 && h->hs->iter < h->hs->maxit) {
-    launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, st);
+    launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, st);
     launch_cg_dots_rz(fp64, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, st);
     launch_cg_dir(fp64, L0, h->p, np, h->ds, st);
     launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, st);
@@ -606,6 +634,10 @@ tosolve_status tosolve_solve(tosolve_t h, const double* f_dev, int nrhs, double*
       }
       const DevState& S = *h->hs;
       used += S.iter;
+      if (S.tc_status) {
+        h->err = "a tensor-core tile did not complete within its bounded wait";
+        return finish(TOSOLVE_ECUDA);
+      }
       if (S.ff == 0.0) {  // f = 0: the solution is u = 0
         CK(cudaMemsetAsync(ur, 0, nd * 8, st));
         last = 0;
@@ -736,8 +768,18 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
   } else if (precision == 1) {
     if (!L.S32) return set_err(h, TOSOLVE_EINVAL, "this level has no FP32 operator");
     launch_apply_diag(false, L, x_dev, y_dev, h->st);
+  } else if (precision == 2) {
+    if (level != 0 || !h->tc.on) return set_err(h, TOSOLVE_EINVAL, "no tensor-core operator on this level");
+    // masked copy feeds the elements; the unmasked copy gives the identity rows
+    Level& L0 = h->lv[0];
+    launch_cast(false, (size_t)L0.ndof, x_dev, L0.b, true, h->st);
+    launch_cast(false, (size_t)L0.ndof, x_dev, L0.v, true, h->st);
+    launch_mask_fp32(L0, (float*)L0.v, h->st);
+    CK(launch_tc_apply(L0, h->tc.m, (const float*)L0.v, h->w32, h->KT32, h->Ye, h->tc.err, h->tc.sms, h->st));
+    launch_tc_gather(L0, h->Ye, (const float*)L0.b, (const float*)L0.b, L0.dinv32, 0.f, 2, (float*)L0.r, h->st);
+    launch_cast(true, (size_t)L0.ndof, L0.r, y_dev, false, h->st);
   } else {
-    return set_err(h, TOSOLVE_EINVAL, "precision must be 0 or 1");
+    return set_err(h, TOSOLVE_EINVAL, "precision must be 0, 1 or 2");
   }
   CK(cudaGetLastError());
   return TOSOLVE_OK;
@@ -753,7 +795,7 @@ tosolve_status tosolve_precondition(tosolve_t h, const double* b_dev, double* z_
   else
     launch_cast(false, (size_t)L0.ndof, b_dev, L0.b, true, h->st);
   if (h->L > 1) launch_smooth0(fp64, L0, h->d.omega, h->st);
-  launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, h->st);
+  launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, h->st);
   launch_cast(true, (size_t)L0.ndof, L0.z, z_dev, fp64, h->st);
   CK(cudaGetLastError());
   return TOSOLVE_OK;

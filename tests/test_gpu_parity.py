@@ -23,7 +23,16 @@ from tests.gpu_helpers import Run, rel
 
 pytestmark = pytest.mark.gpu
 
-FP64, FP32 = 0, 1
+FP64, FP32, TF32 = 0, 1, 2
+
+
+_C1_REF = {}
+
+
+def _c1_reference(m):
+    if "ref" not in _C1_REF:
+        _C1_REF["ref"] = m.run(method="mg", rtol=1e-13)
+    return _C1_REF["ref"]
 
 
 def oracle_residual(m, w_e, f, u, mask):
@@ -85,6 +94,26 @@ def test_fine_operator_matches_assembled_K(n, rmin):
     R.close()
 
 
+@pytest.mark.parametrize("n,rmin", [(1, 0.0), (2, 1.5)])
+def test_tensor_core_stacked_apply_matches_assembled_K(n, rmin):
+    """Finest level of the TF32 preconditioner: the stacked subcell
+    contraction on tcgen05 (TF32 operands, FP32 accumulation) plus the node
+    gather.  TF32 keeps 10 mantissa bits of each operand: relative error of
+    the product about 2^-11 per term, 5e-3 in the 2-norm as the bar."""
+    p = workloads.cantilever(16, 8, 8, n_mr=n, rmin=rmin, seed=2, mg_levels=3)
+    R = Run(p, TF32)
+    R.set_densities()
+    m = fe.Model(p)
+    w_e = m.weights(m.densities(p.x))
+    x = np.random.default_rng(0).normal(size=p.ndof)
+    y_ref = m.apply(w_e, x)
+    y = R.apply(0, TF32, x)
+    assert rel(y, y_ref) <= 5e-3
+    fixed = p.mask == 1
+    np.testing.assert_allclose(y[fixed], x[fixed], rtol=1e-6)  # identity rows
+    R.close()
+
+
 @pytest.mark.parametrize("n", [1, 2])
 def test_coarse_operators_match_oracle_hierarchy(n):
     # ragged: 12 x 4 x 8 with 3 levels -> 3 x 1 x 2 elements on the coarsest
@@ -126,7 +155,7 @@ def test_one_cycle_matches_algorithm_1():
 
 # ---- whole path ----------------------------------------------------------------
 
-@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("precision", [FP64, FP32, TF32])
 @pytest.mark.parametrize("seed", [0, 1])
 def test_cantilever_24x12x12_matches_direct_solve(precision, seed):
     """Config: Q1 24x12x12, n = 1, clamped face, line load, rho ~ U[0.01, 1]."""
@@ -149,13 +178,14 @@ def test_cantilever_24x12x12_matches_direct_solve(precision, seed):
     R.close()
 
 
-def test_multiresolution_48x24x24_full_size():
+@pytest.mark.parametrize("precision", [FP32, TF32])
+def test_multiresolution_48x24x24_full_size(precision):
     """Config: density 96x48x48, Q1 48x24x24 (n = 2), smooth field, r = 1.5,
-    4 levels, FP32 preconditioner -- the benchmark workload."""
+    4 levels, FP32 / TF32 preconditioner -- the benchmark workload."""
     p = workloads.cantilever(48, 24, 24, n_mr=2, rmin=1.5, density="smooth", seed=0, mg_levels=4)
     m = fe.Model(p)
-    ref = m.run(method="mg", rtol=1e-13)
-    R = Run(p, FP32)
+    ref = _c1_reference(m)
+    R = Run(p, precision)
     R.set_densities()
     u, info = R.solve(rtol=1e-8)
     assert info.rel_residual <= 1e-8
@@ -174,7 +204,9 @@ def test_ragged_and_single_level_meshes(shape, n, levels, rmin):
     p = workloads.cantilever(*shape, n_mr=n, rmin=rmin, seed=9, mg_levels=levels)
     m = fe.Model(p)
     ref = m.run(method="dense")
-    for prec in (FP64, FP32):
+    for prec in (FP64, FP32, TF32):
+        if prec == TF32 and n > 2:
+            continue
         R = Run(p, prec)
         R.set_densities()
         u, info = R.solve(rtol=1e-11)
@@ -229,9 +261,10 @@ def test_zero_load_maxit_and_order():
     R.close()
 
 
-def test_bitwise_deterministic():
+@pytest.mark.parametrize("precision", [FP32, TF32])
+def test_bitwise_deterministic(precision):
     p = workloads.cantilever(16, 8, 8, n_mr=2, rmin=1.0, seed=6, mg_levels=3)
-    R = Run(p, FP32)
+    R = Run(p, precision)
     R.set_densities()
     u1, i1 = R.solve(rtol=1e-9)
     R.set_densities()
