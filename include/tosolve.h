@@ -156,6 +156,43 @@ tosolve_status tosolve_step_host(tosolve_t h, const double* x_host, const double
                                  int nrhs, double rtol, int maxit, int warm, double* u_host,
                                  double* c_host, double* dcdx_host, tosolve_info* info);
 
+/* ---- Batches: many independent instances in one graph launch ---------- */
+
+typedef struct tosolve_batch_s* tosolve_batch_t;
+
+/* Records one CUDA graph that solves every load case of every instance.
+ * Each instance is one parallel branch of the graph; its load cases follow
+ * one another inside that branch (they share the handle's workspace), each
+ * a device-side while loop like tosolve_solve's.  Instances of uneven size
+ * therefore run concurrently and the whole batch is a single launch.
+ *   handles: count distinct handles (1 <= count <= 4096; each has its own
+ *            workspace, so a handle appears at most once).  The operators
+ *            used are whatever the last tosolve_set_densities on each handle
+ *            produced.  Handles outlive the batch.
+ *   nrhs:    load cases per instance (1 .. that handle's max_rhs).
+ *   f_dev, u_dev: per instance, nrhs x ndof FP64 device buffers (layout as
+ *            in tosolve_solve).  The graph is bound to these addresses: the
+ *            caller keeps them alive until tosolve_batch_destroy.
+ * Errors: EINVAL (NULL, duplicate handle, nrhs out of range, a handle
+ * created with graphs disabled), ENOMEM, ECUDA. */
+tosolve_status tosolve_batch_create(const tosolve_t* handles, int count, const int* nrhs,
+                                    const double* const* f_dev, double* const* u_dev,
+                                    tosolve_batch_t* out);
+
+/* Runs the batch once from the current contents of u_dev (warm start) to
+ * ||f - K u|| / ||f|| <= rtol for every load case (1 <= maxit <= 100000),
+ * ordered after all work issued so far on the instances' streams; work
+ * issued on them later waits for the batch.  A load case whose recursive
+ * residual met rtol but whose true residual did not is finished by
+ * tosolve_solve on its own handle.  infos: count entries (one per instance,
+ * as tosolve_solve's info; ms is the whole batch's graph time), may be NULL.
+ * Synchronises.  Errors: ENOTCONV if a load case reached maxit first,
+ * EBREAKDOWN, EINVAL (rtol, maxit, densities not set), ECUDA. */
+tosolve_status tosolve_batch_solve(tosolve_batch_t b, double rtol, int maxit, tosolve_info* infos);
+
+/* Frees the batch (not the handles).  NULL is accepted. */
+void tosolve_batch_destroy(tosolve_batch_t b);
+
 /* ---- Single steps of the path, for verification ------------------------ */
 
 /* Number of multigrid levels and, for level l, its node lattice (Lx, Ly, Lz)

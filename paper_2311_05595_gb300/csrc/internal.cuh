@@ -124,6 +124,7 @@ LevelView<T> view(const Level& L);
 void launch_vcycle(bool fp64, Level* lv, int L, double omega, int gamma, const double* Ainv,
                    const TcOp& tc, cudaStream_t st);
 void launch_smooth0(bool fp64, const Level& L0, double omega, cudaStream_t st);
+void launch_set_params(DevState* ds, const double* params, cudaStream_t st);
 void launch_cg_prep(const Level& L0, double* f, double* u, double* part, int np, cudaStream_t st);
 void launch_cg_residual(bool fp64, const Level& L0, double omega, const double* f, const double* u,
                         double* r, int mode, double* part, const double* part_ff, int np,

@@ -231,6 +231,15 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const T* 
   }
 }
 
+// Solve parameters from device memory (so a recorded graph keeps the
+// latest rtol / maxit): params = {rtol^2, maxit}.
+__global__ void k_set_params(DevState* __restrict__ ds, const double* __restrict__ params) {
+  if (threadIdx.x == 0) {
+    ds->tol2 = params[0];
+    ds->maxit = (int)params[1];
+  }
+}
+
 template <typename T>
 __global__ void k_smooth0(long n, T omega, const T* __restrict__ dinv, const T* __restrict__ b,
                           T* __restrict__ v) {
@@ -477,6 +486,10 @@ void launch_vcycle(bool fp64, Level* lv, int L, double omega, int gamma, const d
     vcycle_rec<double>(lv, 0, L, omega, Ainv, tc, st);
   else
     vcycle_rec<float>(lv, 0, L, (float)omega, Ainv, tc, st);
+}
+
+void launch_set_params(DevState* ds, const double* params, cudaStream_t st) {
+  k_set_params<<<1, 32, 0, st>>>(ds, params);
 }
 
 void launch_smooth0(bool fp64, const Level& L0, double omega, cudaStream_t st) {

@@ -12,6 +12,25 @@
 
 using namespace tos;
 
+struct tosolve_batch_s {
+  std::vector<tosolve_t> hs;
+  std::vector<int> nrhs;
+  std::vector<const double*> f;
+  std::vector<double*> u;
+  cudaStream_t st = nullptr;
+  cudaStream_t bs = nullptr;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> ev;  // per instance: ordering with the handle's stream
+  cudaEvent_t evf = nullptr, evd = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  double* hparams = nullptr;  // pinned {rtol^2, maxit}
+  double* dparams = nullptr;
+  tos::DevState* hst = nullptr;  // pinned, one per (instance, load case)
+  int total = 0;
+  std::string err;
+};
+
 namespace {
 
 thread_local std::string g_err;
@@ -180,11 +199,12 @@ void free_all(tosolve_s* h) {
 
 bool prec_fp64(const tosolve_s* h) { return h->d.precision == TOSOLVE_PREC_FP64; }
 
-// Records the PCG loop of one right-hand side as a CUDA graph with a
-// device-side while node: prep, r0 = f - K u0, convergence test; while
-// (not converged): z = B r (multigrid cycle), direction, q = K p, update,
-// test; then the FP64 true residual.  The loop runs without host round trips.
-tosolve_status build_graph(tosolve_s* h) {
+// Appends the PCG loop of one right-hand side to the stream capture active
+// on cs: prep, r0 = f - K u0 and the convergence test; a device-side while
+// node whose body (captured on bs) is z = B r (multigrid cycle), direction,
+// q = K p, update and test; then the FP64 true residual.  The loop runs
+// without host round trips.
+cudaError_t append_solve(tosolve_s* h, cudaStream_t cs, cudaStream_t bs) {
   const bool fp64 = prec_fp64(h);
   Level& L0 = h->lv[0];
   const int np = h->np;
@@ -192,22 +212,12 @@ tosolve_status build_graph(tosolve_s* h) {
   double* part1 = h->part + kMaxPart;
   double* part2 = h->part + 2 * kMaxPart;
   double* part3 = h->part + 3 * kMaxPart;
-  cudaStream_t cs = h->st;
-  cudaStream_t bs = nullptr;
-  CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    cudaStreamDestroy(bs);
-    h->err = std::string("begin capture: ") + cudaGetErrorString(e);
-    return TOSOLVE_ECUDA;
-  }
   launch_cg_prep(L0, h->f, h->u, part0, np, cs);
   cudaStreamCaptureStatus cst;
   cudaGraph_t cgraph = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cgraph, &deps, nullptr, &ndeps);
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cgraph, &deps, nullptr, &ndeps);
   cudaGraphConditionalHandle hc = 0;
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, cgraph, 1, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) {
@@ -240,6 +250,22 @@ tosolve_status build_graph(tosolve_s* h) {
   if (e == cudaSuccess)
     launch_cg_residual(fp64, L0, h->d.omega, h->f, h->u, h->tmpa, 2, part1, part0, np, h->ds, h->cnt,
                        hc, 0, cs);
+  return e;
+}
+
+// The handle's own graph: one right-hand side, launched by tosolve_solve.
+tosolve_status build_graph(tosolve_s* h) {
+  cudaStream_t cs = h->st;
+  cudaStream_t bs = nullptr;
+  CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(bs);
+    h->err = std::string("begin capture: ") + cudaGetErrorString(e);
+    return TOSOLVE_ECUDA;
+  }
+  e = append_solve(h, cs, bs);
   cudaError_t e2 = cudaStreamEndCapture(cs, &g);
   cudaStreamDestroy(bs);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -249,7 +275,6 @@ tosolve_status build_graph(tosolve_s* h) {
     return TOSOLVE_ECUDA;
   }
   h->graph = g;
-  h->hcond = hc;
   CK(cudaGraphInstantiate(&h->gexec, g, 0));
   h->graph_ready = true;
   return TOSOLVE_OK;
@@ -799,6 +824,188 @@ tosolve_status tosolve_precondition(tosolve_t h, const double* b_dev, double* z_
   launch_cast(true, (size_t)L0.ndof, L0.z, z_dev, fp64, h->st);
   CK(cudaGetLastError());
   return TOSOLVE_OK;
+}
+
+static void batch_free(tosolve_batch_t b) {
+  if (b->ge) cudaGraphExecDestroy(b->ge);
+  if (b->g) cudaGraphDestroy(b->g);
+  for (cudaStream_t x : b->branch) if (x) cudaStreamDestroy(x);
+  for (cudaEvent_t x : b->ev) if (x) cudaEventDestroy(x);
+  if (b->evf) cudaEventDestroy(b->evf);
+  if (b->evd) cudaEventDestroy(b->evd);
+  if (b->t0) cudaEventDestroy(b->t0);
+  if (b->t1) cudaEventDestroy(b->t1);
+  if (b->bs) cudaStreamDestroy(b->bs);
+  if (b->st) cudaStreamDestroy(b->st);
+  if (b->hparams) cudaFreeHost(b->hparams);
+  if (b->hst) cudaFreeHost(b->hst);
+  if (b->dparams) cudaFree(b->dparams);
+}
+
+tosolve_status tosolve_batch_create(const tosolve_t* handles, int count, const int* nrhs,
+                                    const double* const* f_dev, double* const* u_dev,
+                                    tosolve_batch_t* out) {
+  if (out == nullptr) { g_err = "out is NULL"; return TOSOLVE_EINVAL; }
+  *out = nullptr;
+  if (handles == nullptr || nrhs == nullptr || f_dev == nullptr || u_dev == nullptr || count < 1 ||
+      count > 4096) {
+    g_err = "need 1 <= count <= 4096 and non-NULL arrays";
+    return TOSOLVE_EINVAL;
+  }
+  for (int i = 0; i < count; ++i) {
+    if (handles[i] == nullptr || f_dev[i] == nullptr || u_dev[i] == nullptr) { g_err = "NULL handle or buffer"; return TOSOLVE_EINVAL; }
+    if (nrhs[i] < 1 || nrhs[i] > handles[i]->d.max_rhs) { g_err = "nrhs out of range for a handle"; return TOSOLVE_EINVAL; }
+    if (!handles[i]->graph_ready) { g_err = "handle built without graphs"; return TOSOLVE_EINVAL; }
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) { g_err = "a handle appears twice in the batch"; return TOSOLVE_EINVAL; }
+  }
+  tosolve_batch_s* b = new (std::nothrow) tosolve_batch_s();
+  if (b == nullptr) { g_err = "host allocation failed"; return TOSOLVE_ENOMEM; }
+  b->hs.assign(handles, handles + count);
+  b->nrhs.assign(nrhs, nrhs + count);
+  b->f.assign(f_dev, f_dev + count);
+  b->u.assign(u_dev, u_dev + count);
+  for (int i = 0; i < count; ++i) b->total += nrhs[i];
+  auto fail = [&](cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    batch_free(b);
+    delete b;
+    return e == cudaErrorMemoryAllocation ? TOSOLVE_ENOMEM : TOSOLVE_ECUDA;
+  };
+#define CKB(call)                                  \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return fail(e_, #call); \
+  } while (0)
+  CKB(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+  CKB(cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking));
+  CKB(cudaEventCreateWithFlags(&b->evf, cudaEventDisableTiming));
+  CKB(cudaEventCreateWithFlags(&b->evd, cudaEventDisableTiming));
+  CKB(cudaEventCreate(&b->t0));
+  CKB(cudaEventCreate(&b->t1));
+  CKB(cudaMallocHost((void**)&b->hparams, 2 * sizeof(double)));
+  CKB(cudaMallocHost((void**)&b->hst, (size_t)b->total * sizeof(DevState)));
+  CKB(cudaMalloc((void**)&b->dparams, 2 * sizeof(double)));
+  b->branch.resize(count, nullptr);
+  b->ev.resize(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    CKB(cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking));
+    CKB(cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming));
+  }
+  // record: fork one branch per instance, its load cases in sequence
+  CKB(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaEventRecord(b->evf, b->st);
+  int k = 0;
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    tosolve_s* h = b->hs[i];
+    cudaStream_t si = b->branch[i];
+    const size_t nd = h->lv[0].ndof;
+    e = cudaStreamWaitEvent(si, b->evf, 0);
+    if (e == cudaSuccess) launch_set_params(h->ds, b->dparams, si);
+    for (int r = 0; r < b->nrhs[i] && e == cudaSuccess; ++r, ++k) {
+      e = cudaMemcpyAsync(h->f, b->f[i] + r * nd, nd * 8, cudaMemcpyDeviceToDevice, si);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->u, b->u[i] + r * nd, nd * 8, cudaMemcpyDeviceToDevice, si);
+      if (e == cudaSuccess) e = append_solve(h, si, b->bs);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b->u[i] + r * nd, h->u, nd * 8, cudaMemcpyDeviceToDevice, si);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&b->hst[k], h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, si);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev[i], si);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->ev[i], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->st, &b->g);
+  if (e != cudaSuccess) return fail(e, "batch capture");
+  if (e2 != cudaSuccess) return fail(e2, "batch capture end");
+  CKB(cudaGraphInstantiate(&b->ge, b->g, 0));
+#undef CKB
+  *out = b;
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_batch_solve(tosolve_batch_t b, double rtol, int maxit, tosolve_info* infos) {
+  if (b == nullptr) { g_err = "batch is NULL"; return TOSOLVE_EINVAL; }
+  const int count = (int)b->hs.size();
+  if (infos) std::memset(infos, 0, count * sizeof(tosolve_info));
+  if (!(rtol > 0.0) || maxit < 1 || maxit > 100000) { g_err = "need rtol > 0 and 1 <= maxit <= 100000"; return TOSOLVE_EINVAL; }
+  for (int i = 0; i < count; ++i)
+    if (!b->hs[i]->have_rho) { g_err = "call tosolve_set_densities on every handle first"; return TOSOLVE_EINVAL; }
+  auto cuda_fail = [&](cudaError_t e) {
+    g_err = std::string("batch solve: ") + cudaGetErrorString(e);
+    return TOSOLVE_ECUDA;
+  };
+  b->hparams[0] = rtol * rtol;
+  b->hparams[1] = (double)maxit;
+  cudaError_t e = cudaMemcpyAsync(b->dparams, b->hparams, 2 * sizeof(double), cudaMemcpyHostToDevice, b->st);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {  // after everything issued on the handles
+    e = cudaEventRecord(b->ev[i], b->hs[i]->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->ev[i], 0);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->t0, b->st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->ge, b->st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->evd, b->st);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->hs[i]->st, b->evd, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, b->t0, b->t1);
+  tosolve_status result = TOSOLVE_OK;
+  int k = 0;
+  for (int i = 0; i < count; ++i) {
+    tosolve_s* h = b->hs[i];
+    tosolve_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    inf.ms = ms;
+    const size_t nd = h->lv[0].ndof;
+    for (int r = 0; r < b->nrhs[i]; ++r, ++k) {
+      const DevState& S = b->hst[k];
+      double* ur = b->u[i] + r * nd;
+      int used = S.iter;
+      double rel = 0.0;
+      tosolve_status st = TOSOLVE_OK;
+      if (S.tc_status) {
+        st = TOSOLVE_ECUDA;
+        h->err = "a tensor-core tile did not complete within its bounded wait";
+      } else if (S.ff == 0.0) {  // f = 0: the solution is u = 0
+        e = cudaMemsetAsync(ur, 0, nd * 8, b->st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        used = 0;
+      } else {
+        rel = std::sqrt(S.rr_true / S.ff);
+        if (S.status != 0) {
+          st = TOSOLVE_EBREAKDOWN;
+        } else if (rel > rtol && used < maxit) {
+          // the recursive residual met the tolerance, the true one did not:
+          // finish this load case alone, warm-started from the batch result
+          tosolve_info more;
+          st = tosolve_solve(h, b->f[i] + r * nd, 1, ur, rtol, maxit - used, &more);
+          used += more.total_iterations;
+          rel = more.rel_residual;
+        } else if (rel > rtol) {
+          st = TOSOLVE_ENOTCONV;
+        }
+      }
+      inf.iterations = used;
+      inf.total_iterations += used;
+      inf.rel_residual = std::fmax(inf.rel_residual, rel);
+      if (st != TOSOLVE_OK && inf.status == TOSOLVE_OK) inf.status = st;
+      if (st != TOSOLVE_OK && (result == TOSOLVE_OK || result == TOSOLVE_ENOTCONV)) result = st;
+    }
+    if (infos) infos[i] = inf;
+  }
+  e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (result == TOSOLVE_ENOTCONV) g_err = "a load case reached maxit before the tolerance";
+  else if (result == TOSOLVE_EBREAKDOWN) g_err = "breakdown in a load case (PCG or coarse Cholesky)";
+  else if (result == TOSOLVE_ECUDA) g_err = "a tensor-core tile did not complete within its bounded wait";
+  return result;
+}
+
+void tosolve_batch_destroy(tosolve_batch_t b) {
+  if (b == nullptr) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  batch_free(b);
+  delete b;
 }
 
 }  // extern "C"

@@ -65,6 +65,9 @@ def _load():
         "tosolve_densities": ([vp, vp, vp], i),
         "tosolve_apply": ([vp, i, i, vp, vp], i),
         "tosolve_precondition": ([vp, vp, vp], i),
+        "tosolve_batch_create": ([P(vp), i, P(i), P(vp), P(vp), P(vp)], i),
+        "tosolve_batch_solve": ([vp, d, i, vp], i),
+        "tosolve_batch_destroy": ([vp], None),
         "tosolve_last_error": ([vp], C.c_char_p),
         "tosolve_destroy": ([vp], None),
     }
@@ -153,6 +156,31 @@ def tosolve_step_host(h, x_host: np.ndarray, f_host: np.ndarray, nrhs: int, rtol
                                c, _ptr(dcdx_host), C.byref(info))
     _check(h, s, "tosolve_step_host")
     return np.array(c[:]), info
+
+
+def tosolve_batch_create(handles, nrhs, f_devs, u_devs) -> int:
+    n = len(handles)
+    if not (len(nrhs) == len(f_devs) == len(u_devs) == n):
+        raise ValueError("handles, nrhs, f_devs and u_devs must have the same length")
+    hv = (C.c_void_p * n)(*handles)
+    rv = (C.c_int * n)(*nrhs)
+    fv = (C.c_void_p * n)(*[_ptr(t) for t in f_devs])
+    uv = (C.c_void_p * n)(*[_ptr(t) for t in u_devs])
+    b = C.c_void_p(0)
+    _check(None, _lib.tosolve_batch_create(hv, n, rv, fv, uv, C.byref(b)), "tosolve_batch_create")
+    return b.value
+
+
+def tosolve_batch_solve(b, rtol: float, maxit: int, count: int, raise_on_error=True):
+    infos = (tosolve_info * count)()
+    s = _lib.tosolve_batch_solve(b, rtol, maxit, infos)
+    if raise_on_error:
+        _check(None, s, "tosolve_batch_solve")
+    return list(infos)
+
+
+def tosolve_batch_destroy(b) -> None:
+    _lib.tosolve_batch_destroy(b)
 
 
 def tosolve_level_dims(h, level: int):
