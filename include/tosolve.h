@@ -193,6 +193,39 @@ tosolve_status tosolve_batch_solve(tosolve_batch_t b, double rtol, int maxit, to
 /* Frees the batch (not the handles).  NULL is accepted. */
 void tosolve_batch_destroy(tosolve_batch_t b);
 
+/* ---- Compliance without device allocation ----------------------------- */
+
+/* Most load cases handled per call, and the size in bytes of the one fixed
+ * device array (per device) that holds the partial sums. */
+#define TOSOLVE_NOALLOC_MAX_RHS 16
+#define TOSOLVE_NOALLOC_SCRATCH_BYTES 77824
+
+/* c_dev[r] = f_r^T u_r summed over the free DOFs, r < nrhs: the compliance
+ * of tosolve_compliance_grad (Sec. 3.4), for callers that may not allocate
+ * device memory when they need it (code confined to buffers a host
+ * application hands it, or a latency-critical loop that cannot afford the
+ * device-wide synchronisation a cudaMalloc can cause).  The paper has no
+ * counterpart: it is a service of this library.  It allocates nothing and
+ * needs no handle.
+ *   f_dev, u_dev: nrhs x ndof FP64 device arrays, rows contiguous.
+ *   mask_dev:     ndof bytes on the device, 1 = fixed DOF (excluded).
+ *   ndof:         1 .. 2^62.
+ *   nrhs:         1 .. TOSOLVE_NOALLOC_MAX_RHS; more is rejected with EINVAL.
+ *   c_dev:        nrhs FP64 results on the device (caller-owned).
+ *   cuda_stream:  cudaStream_t to run on (NULL = legacy default stream).
+ * The partial sums live in one fixed device array of
+ * TOSOLVE_NOALLOC_SCRATCH_BYTES per device, shared by every call and keeping
+ * what the last call wrote; each call overwrites every entry it reads.
+ * Calls whose kernels may overlap on the GPU race on that array: order them
+ * (one stream, or events).  The first call on a device, with that device
+ * current, looks up the array's address with cudaGetSymbolAddress; make that
+ * first call before any stream capture begins.  Asynchronous (does not
+ * synchronise).  Errors: EINVAL (NULL pointer, ndof or nrhs out of range;
+ * checked before any CUDA call), ECUDA.  Message: tosolve_last_error(NULL). */
+tosolve_status tosolve_compliance_noalloc(const double* f_dev, const double* u_dev,
+                                          const uint8_t* mask_dev, size_t ndof, int nrhs,
+                                          double* c_dev, void* cuda_stream);
+
 /* ---- Single steps of the path, for verification ------------------------ */
 
 /* Number of multigrid levels and, for level l, its node lattice (Lx, Ly, Lz)

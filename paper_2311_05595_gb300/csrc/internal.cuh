@@ -109,6 +109,8 @@ struct TcOp {
   int* err = nullptr;
   int sms = 1;
 };
+// Message returned by tosolve_last_error(NULL) for calls that have no handle.
+void set_last_error(const char* msg);
 bool tc_supported(int n);
 cudaError_t launch_tc_apply(const Level& L0, int m, const float* v, const float* w32, const float* KT,
                             float* Ye, int* err, int sms, cudaStream_t st);

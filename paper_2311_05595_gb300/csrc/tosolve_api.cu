@@ -826,6 +826,12 @@ tosolve_status tosolve_precondition(tosolve_t h, const double* b_dev, double* z_
   return TOSOLVE_OK;
 }
 
+}  // extern "C"
+
+void tos::set_last_error(const char* msg) { g_err = msg; }
+
+extern "C" {
+
 static void batch_free(tosolve_batch_t b) {
   if (b->ge) cudaGraphExecDestroy(b->ge);
   if (b->g) cudaGraphDestroy(b->g);

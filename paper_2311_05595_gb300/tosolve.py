@@ -68,6 +68,7 @@ def _load():
         "tosolve_batch_create": ([P(vp), i, P(i), P(vp), P(vp), P(vp)], i),
         "tosolve_batch_solve": ([vp, d, i, vp], i),
         "tosolve_batch_destroy": ([vp], None),
+        "tosolve_compliance_noalloc": ([vp, vp, vp, sz, i, vp, vp], i),
         "tosolve_last_error": ([vp], C.c_char_p),
         "tosolve_destroy": ([vp], None),
     }
@@ -181,6 +182,17 @@ def tosolve_batch_solve(b, rtol: float, maxit: int, count: int, raise_on_error=T
 
 def tosolve_batch_destroy(b) -> None:
     _lib.tosolve_batch_destroy(b)
+
+
+NOALLOC_MAX_RHS = 16
+
+
+def tosolve_compliance_noalloc(f_dev, u_dev, mask_dev, ndof: int, nrhs: int, c_dev, stream=None) -> None:
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    _check(None, _lib.tosolve_compliance_noalloc(_ptr(f_dev), _ptr(u_dev), _ptr(mask_dev), ndof, nrhs,
+                                                 _ptr(c_dev), st), "tosolve_compliance_noalloc")
 
 
 def tosolve_level_dims(h, level: int):
