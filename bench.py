@@ -248,9 +248,11 @@ def run_gpu(args):
 
     sampler = ClockSampler(local)
     out = {}
-    solvers = {"fp32": make(T.PREC_FP32), "tf32": make(T.PREC_TF32), "fp64": make(T.PREC_FP64)}
+    mixed_labels = ("fp32", "tf32", "fp32x2")
+    solvers = {"fp32": make(T.PREC_FP32), "tf32": make(T.PREC_TF32),
+               "fp32x2": make(T.PREC_FP32X2), "fp64": make(T.PREC_FP64)}
     sampler.start()
-    for label in ("fp32", "tf32", "fp64"):
+    for label in mixed_labels + ("fp64",):
         s = solvers[label]
         ms, infos, wall = timed(s, args.steps, args.warmup)
         tot = sum(ms)
@@ -264,7 +266,7 @@ def run_gpu(args):
 
     # per-phase device time (separate untimed pass, same step)
     phases = {}
-    for label in ("fp32", "tf32", "fp64"):
+    for label in mixed_labels + ("fp64",):
         s = solvers[label]
         acc = {"set_densities": 0.0, "solve": 0.0, "gradient": 0.0}
         nph = 5
@@ -286,7 +288,7 @@ def run_gpu(args):
                 acc["gradient"] += ev[2].elapsed_time(ev[3]) / nph
         phases[label] = {k: round(v, 4) for k, v in acc.items()}
     free_dofs = p.nfree * p.nrhs
-    best = "tf32" if out["tf32"]["tot"] < out["fp32"]["tot"] else "fp32"
+    best = min(mixed_labels, key=lambda lab: out[lab]["tot"])
     mixed = out[best]
     fp64 = out["fp64"]
     value = world * free_dofs * args.steps / (mixed["tot"] * 1e-3)
@@ -298,7 +300,6 @@ def run_gpu(args):
 
     # ---- end to end through the host-buffer entry point ----
     s = mixed["solver"]
-    other = out["fp32" if best == "tf32" else "tf32"]
     xh = torch.tensor(p.x).pin_memory()
     fh = torch.tensor(p.f).pin_memory()
     uh = torch.zeros(p.f.shape, dtype=torch.float64).pin_memory()
@@ -350,8 +351,6 @@ def run_gpu(args):
     traffic = NCU_TRAFFIC.get(("k_apply_diag<double>", source_hash("k_solve.cu")))
 
     its = [i[0] for i in mixed["infos"]]
-    its_other = [i[0] for i in other["infos"]]
-    its64 = [i[0] for i in fp64["infos"]]
     res = max(i[2] for i in mixed["infos"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -361,17 +360,18 @@ def run_gpu(args):
                    "density_cells": int(p.x.size), "mg_levels": WORKLOAD["levels"],
                    "smoother": "damped Jacobi omega=0.5, 1+1, V-cycle",
                    "precision": f"FP64 CG + {best.upper()} V-cycle (value; TF32 = finest level "
-                                f"on tcgen05); FP64 MG-PCG (fp64_value)",
+                                f"on tcgen05, FP32X2 = FP32 operators with float-pair vectors); "
+                                f"FP64 MG-PCG (fp64_value)",
                    "rtol": rtol, "start": "u0 = 0 every step",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"replicas x{world}"},
         "fp64_value": fp64_value, "speedup_vs_fp64": value / fp64_value,
         "mixed_variants": {lab: world * free_dofs * args.steps / (out[lab]["tot"] * 1e-3)
-                           for lab in ("fp32", "tf32")},
+                           for lab in mixed_labels},
         "fp64_ms_per_step": fp64["tot"] / args.steps,
         "phase_ms": phases,
-        "pcg_iterations": {best: statistics.median(its), ("fp32" if best == "tf32" else "tf32"):
-                           statistics.median(its_other), "fp64": statistics.median(its64)},
+        "pcg_iterations": {lab: statistics.median(i[0] for i in out[lab]["infos"])
+                           for lab in mixed_labels + ("fp64",)},
         "true_rel_residual_max": res,
         "solve_latency_ms": {"p50": pct(mixed["solve_ms"], 0.5), "p99": pct(mixed["solve_ms"], 0.99),
                              "fp64_p50": pct(fp64["solve_ms"], 0.5),
@@ -393,12 +393,134 @@ def run_gpu(args):
             line["cpu_baseline"] = cpu_baseline_entry()
         except Exception as e:  # reported, never silently dropped
             line["cpu_baseline"] = {"error": str(e)[-300:]}
-    for lab in ("fp32", "tf32", "fp64"):
+    for lab in mixed_labels + ("fp64",):
         out[lab]["solver"].close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# nx is rounded to a multiple of 16 (not 8) so that every instance coarsens
+# far enough for the dense coarsest solve (nx = 8 * odd >= 88 would leave a
+# coarsest level of about 10^4 DOFs).
+BATCH = dict(name="batch64_q1_32x16x16_to_128x64x64_1to3rhs", count=64, seed=2024, mult=16,
+             rtol=1e-8)
+
+
+def run_batch(args):
+    """64 uneven Q1 instances (nx = 32 * 2^U(0,2) rounded to 16, ny = nz =
+    nx/2, 1-3 edge load cases each, x ~ U[0.01, 1]) solved from u0 = 0 by
+    one batched graph launch; also the same instances solved one handle at
+    a time, and the batch in FP64.  Prints one JSON line."""
+    import torch
+
+    import workloads
+    from paper_2311_05595_gb300 import tosolve as T
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    probs = workloads.batched_instances(BATCH["count"], BATCH["seed"], mult=BATCH["mult"])
+    rtol, maxit = BATCH["rtol"], 2000
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    dofs = sum(p.nfree * p.nrhs for p in probs)
+    xs = [torch.tensor(p.x, device=dev) for p in probs]
+    fs = [torch.tensor(p.f, device=dev) for p in probs]
+    us = [torch.zeros_like(f) for f in fs]
+
+    def build(precision):
+        sol = []
+        for p, x in zip(probs, xs):
+            d = T.make_desc(p.nx, p.ny, p.nz, Emin=p.Emin, nu=p.nu, penal=p.penal,
+                            precision=precision, max_rhs=p.nrhs)
+            s = T.Solver(d, p.mask, stream)
+            T.tosolve_set_densities(s.h, x)
+            sol.append(s)
+        stream.synchronize()
+        b = T.tosolve_batch_create([s.h for s in sol], [p.nrhs for p in probs], fs, us)
+        return sol, b
+
+    def zero():
+        for u in us:
+            u.zero_()
+
+    def time_batch(b):
+        for _ in range(args.warmup):
+            zero()
+            T.tosolve_batch_solve(b, rtol, maxit, len(probs))
+        ms, its = [], []
+        for _ in range(args.steps):
+            zero()
+            flush.zero_()
+            torch.cuda.synchronize()
+            infos = T.tosolve_batch_solve(b, rtol, maxit, len(probs))
+            ms.append(infos[0].ms)
+            its.append(sum(i.total_iterations for i in infos))
+        return ms, its
+
+    def time_sequential(sol):
+        ms = []
+        with torch.cuda.stream(stream):
+            for rep in range(args.warmup + args.steps):
+                zero()
+                flush.zero_()
+                stream.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for s, p, f, u in zip(sol, probs, fs, us):
+                    T.tosolve_solve(s.h, f, p.nrhs, u, rtol, maxit)
+                e1.record(stream)
+                stream.synchronize()
+                if rep >= args.warmup:
+                    ms.append(e0.elapsed_time(e1))
+        return ms
+
+    sampler = ClockSampler(0)
+    res = {}
+    mem = {}
+    sampler.start()
+    for label, prec in (("fp32x2", T.PREC_FP32X2), ("fp32", T.PREC_FP32), ("fp64", T.PREC_FP64)):
+        torch.cuda.synchronize()
+        m0 = torch.cuda.mem_get_info(dev)[0]
+        sol, b = build(prec)
+        mem[label] = (m0 - torch.cuda.mem_get_info(dev)[0]) / 2**30
+        ms, its = time_batch(b)
+        res[label] = dict(ms=ms, its=its)
+        if label == "fp32x2":
+            res["fp32x2_sequential"] = dict(ms=time_sequential(sol))
+        T.tosolve_batch_destroy(b)
+        for s in sol:
+            s.close()
+    clocks = sampler.stop()
+    med = {k: statistics.median(v["ms"]) for k, v in res.items()}
+    best = min(("fp32x2", "fp32"), key=lambda k: med[k])
+    value = dofs / (med[best] * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": med[best], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": BATCH["name"], "instances": len(probs),
+                   "load_cases": sum(p.nrhs for p in probs),
+                   "free_dofs_x_load_cases": dofs,
+                   "largest_free_dofs": max(p.nfree for p in probs),
+                   "precision": f"FP64 CG + {best.upper()} V-cycle (value; FP32X2 = FP32 "
+                                f"operators with float-pair vectors); FP64 MG-PCG (fp64_value)",
+                   "rtol": rtol, "start": "u0 = 0 every step",
+                   "timed": "one tosolve_batch_solve graph launch (CUDA events), median of steps",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+        "fp64_value": dofs / (med["fp64"] * 1e-3),
+        "mixed_variants": {k: dofs / (med[k] * 1e-3) for k in ("fp32x2", "fp32")},
+        "sequential_value_fp32x2": dofs / (med["fp32x2_sequential"] * 1e-3),
+        "batch_speedup_vs_sequential": med["fp32x2_sequential"] / med["fp32x2"],
+        "speedup_vs_fp64": med["fp64"] / med[best],
+        "pcg_iterations_total": {k: statistics.median(res[k]["its"])
+                                 for k in ("fp32x2", "fp32", "fp64")},
+        "device_gib": mem,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -408,6 +530,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cantilever", choices=["cantilever", "batch64"],
+                    help="batch64: the 64-instance batched solve (its own JSON line)")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the PCG loop from the host (same kernels, no CUDA graph): "
                          "ncu cannot profile kernels inside a graph with a conditional node")
@@ -418,6 +542,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_gpu(args)
 

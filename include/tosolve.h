@@ -62,10 +62,15 @@ typedef enum {
 typedef enum {
   TOSOLVE_PREC_FP64 = 0, /* plain FP64 MG-PCG                                */
   TOSOLVE_PREC_FP32 = 1, /* FP32 V-cycle operators and vectors, FP32 accum.  */
-  TOSOLVE_PREC_TF32 = 2  /* as FP32, but the finest level's operator is the  */
+  TOSOLVE_PREC_TF32 = 2, /* as FP32, but the finest level's operator is the  */
                          /* stacked subcell contraction of Eq. matrixK_mr on */
                          /* the tcgen05 tensor cores (TF32 operands, FP32    */
                          /* accumulation in TMEM); needs n_mr <= 2           */
+  TOSOLVE_PREC_FP32X2 = 3 /* FP32 V-cycle operators (formed in FP64, then    */
+                         /* rounded) and vectors held as float pairs: about */
+                         /* 48-bit arithmetic on the FP32 pipes, for        */
+                         /* high-contrast densities where FP32 vectors slow */
+                         /* convergence                                     */
 } tosolve_precision;
 
 /* Problem and solver description (Sec. 2, 3.1, 7 intro). */
@@ -242,9 +247,10 @@ tosolve_status tosolve_densities(tosolve_t h, double* rho_dev, double* w_dev);
 
 /* y = A_l x for the level-l operator (fixed rows/columns replaced by
  * identity), computed in FP64 (precision 0), in the preconditioner's FP32
- * stencil form (precision 1) or, on level 0 of a TF32 handle, as the
- * tensor-core stacked contraction plus node gather (precision 2); inputs and
- * outputs are FP64.  x_dev, y_dev: 3*nodes(l).
+ * stencil form (precision 1), on level 0 of a TF32 handle as the
+ * tensor-core stacked contraction plus node gather (precision 2), or with
+ * the FP32 stencil and float-pair arithmetic of FP32X2 (precision 3); inputs
+ * and outputs are FP64.  x_dev, y_dev: 3*nodes(l).
  * Level 0 FP64 is K(rho) of Eq. matrixK_mr; coarser levels are re-discretised
  * from the density field (Sec. 7.2: system matrices of each mesh level). */
 tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double* x_dev,

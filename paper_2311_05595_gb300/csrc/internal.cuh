@@ -17,6 +17,7 @@
 #include <string>
 
 #include "../../include/tosolve.h"
+#include "dfloat.cuh"
 
 namespace tos {
 
@@ -68,12 +69,24 @@ struct Level {
   void* z = nullptr;
 };
 
+// Arithmetic of the multigrid vectors: FP64, FP32, or float pairs (FP32X2,
+// on FP32 operators).
+enum Vt : int { kVtF64 = 0, kVtF32 = 1, kVtDF = 2 };
+
+// Storage type of the operator and Jacobi diagonal used with vectors of T.
+template <typename T>
+struct OpOf { using type = T; };
+template <>
+struct OpOf<dfloat> { using type = float; };
+template <typename T>
+using op_t = typename OpOf<T>::type;
+
 // Read-only view of a level's operator for the kernels.
 template <typename T>
 struct LevelView {
   int Lx, Ly, Lz, nn;
-  const T* S;
-  const T* dinv;
+  const op_t<T>* S;
+  const op_t<T>* dinv;
   const uint8_t* mask;
 };
 
@@ -123,25 +136,28 @@ void launch_mask_fp32(const Level& L, float* x, cudaStream_t st);
 // ---- launchers (k_solve.cu) ----------------------------------------------
 template <typename T>
 LevelView<T> view(const Level& L);
-void launch_vcycle(bool fp64, Level* lv, int L, double omega, int gamma, const double* Ainv,
+void launch_vcycle(int vt, Level* lv, int L, double omega, int gamma, const double* Ainv,
                    const TcOp& tc, cudaStream_t st);
-void launch_smooth0(bool fp64, const Level& L0, double omega, cudaStream_t st);
+void launch_smooth0(int vt, const Level& L0, double omega, cudaStream_t st);
 void launch_set_params(DevState* ds, const double* params, cudaStream_t st);
 void launch_cg_prep(const Level& L0, double* f, double* u, double* part, int np, cudaStream_t st);
-void launch_cg_residual(bool fp64, const Level& L0, double omega, const double* f, const double* u,
+void launch_cg_residual(int vt, const Level& L0, double omega, const double* f, const double* u,
                         double* r, int mode, double* part, const double* part_ff, int np,
                         DevState* ds, unsigned* cnt, cudaGraphConditionalHandle hc, int use_cond,
                         cudaStream_t st);
-void launch_cg_dots_rz(bool fp64, const Level& L0, const double* r, const double* q, double* part_rz,
+void launch_cg_dots_rz(int vt, const Level& L0, const double* r, const double* q, double* part_rz,
                        double* part_zq, int np, DevState* ds, unsigned* cnt, cudaStream_t st);
-void launch_cg_dir(bool fp64, const Level& L0, double* p, int np, const DevState* ds,
+void launch_cg_dir(int vt, const Level& L0, double* p, int np, const DevState* ds,
                    cudaStream_t st);
 void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np, DevState* ds,
                      unsigned* cnt, cudaStream_t st);
-void launch_cg_update(bool fp64, const Level& L0, double omega, double* u, double* r, const double* p,
+void launch_cg_update(int vt, const Level& L0, double omega, double* u, double* r, const double* p,
                       const double* q, double* part_rr, int np, DevState* ds, unsigned* cnt,
                       cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st);
-void launch_apply_diag(bool fp64, const Level& L, const double* x, double* y, cudaStream_t st);
+void launch_apply_diag(int vt, const Level& L, const double* x, double* y, cudaStream_t st);
+// FP64 vector <-> multigrid vector of arithmetic vt.
+void launch_vec_in(int vt, size_t n, const double* a, void* b, cudaStream_t st);
+void launch_vec_out(int vt, size_t n, const void* a, double* b, cudaStream_t st);
 void launch_cast(bool to_fp64, size_t n, const void* a, void* b, bool src_fp64,
                  cudaStream_t st);
 

@@ -4,6 +4,8 @@
 // solve), and the FP64 preconditioned CG of Sec. 7.2 with fused vector
 // updates and deterministic reductions (warp shuffles, then a fixed-order
 // sum of per-block partials done by the last block to finish).
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace tos {
@@ -17,6 +19,10 @@ LevelView<double> view<double>(const Level& L) {
 template <>
 LevelView<float> view<float>(const Level& L) {
   return LevelView<float>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask};
+}
+template <>
+LevelView<dfloat> view<dfloat>(const Level& L) {
+  return LevelView<dfloat>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask};
 }
 
 namespace {
@@ -49,6 +55,30 @@ __device__ __forceinline__ T stencil_row(const LevelView<T>& V, long node, int i
     acc[o % 3] += s[0] * ld(nb, 0) + s[nn] * ld(nb, 1) + s[2 * nn] * ld(nb, 2);
   }
   return (acc[0] + acc[1]) + acc[2];
+}
+
+// The same row with FP32 coefficients and float-pair operands, summed by
+// Dot2 (every product and addition error kept): the result carries about
+// twice FP32's precision at a few FP32 operations per coefficient.
+template <typename LD>
+__device__ __forceinline__ dfloat stencil_row(const LevelView<dfloat>& V, long node, int i, int j,
+                                              int l, int r, LD ld) {
+  const size_t nn = V.nn;
+  const long sx[3] = {i > 0 ? -1L : 0L, 0L, i + 1 < V.Lx ? 1L : 0L};
+  const long sy[3] = {j > 0 ? -(long)V.Lx : 0L, 0L, j + 1 < V.Ly ? (long)V.Lx : 0L};
+  const long sz[3] = {l > 0 ? -(long)V.Lx * V.Ly : 0L, 0L, l + 1 < V.Lz ? (long)V.Lx * V.Ly : 0L};
+  Dot2 acc[3];
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    const long nb = node + sx[o % 3] + sy[(o / 3) % 3] + sz[o / 9];
+    const float* s = V.S + (size_t)(o * 9 + 3 * r) * nn + node;
+    acc[o % 3].add(s[0], ld(nb, 0));
+    acc[o % 3].add(s[nn], ld(nb, 1));
+    acc[o % 3].add(s[2 * nn], ld(nb, 2));
+  }
+  acc[0].add(acc[1]);
+  acc[0].add(acc[2]);
+  return acc[0].value();
 }
 
 #define ROW_LOOP(nn)                                                                  \
@@ -138,7 +168,7 @@ __global__ void k_vc_pre(LevelView<T> V, const T* __restrict__ b, const T* __res
 template <typename T>
 __global__ void k_vc_restrict(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int Lzc,
                               const uint8_t* __restrict__ maskc, const T* __restrict__ rf,
-                              T* __restrict__ bc, const T* __restrict__ dinvc, T omega,
+                              T* __restrict__ bc, const op_t<T>* __restrict__ dinvc, T omega,
                               T* __restrict__ vc) {
   const long nnc = (long)Lxc * Lyc * Lzc;
   NODE_LOOP(nnc) {
@@ -241,7 +271,7 @@ __global__ void k_set_params(DevState* __restrict__ ds, const double* __restrict
 }
 
 template <typename T>
-__global__ void k_smooth0(long n, T omega, const T* __restrict__ dinv, const T* __restrict__ b,
+__global__ void k_smooth0(long n, T omega, const op_t<T>* __restrict__ dinv, const T* __restrict__ b,
                           T* __restrict__ v) {
   DOF_LOOP(n) v[d] = omega * dinv[d] * b[d];
 }
@@ -269,7 +299,7 @@ __global__ void k_cg_prep(int nn, const uint8_t* __restrict__ mask, double* __re
 template <typename T>
 __global__ void k_cg_residual(LevelView<double> V, const double* __restrict__ f,
                               const double* __restrict__ u, double* __restrict__ rv,
-                              T* __restrict__ b0, const T* __restrict__ dinv0, T omega,
+                              T* __restrict__ b0, const op_t<T>* __restrict__ dinv0, T omega,
                               T* __restrict__ v0, double* part, const double* part_ff, int mode,
                               DevState* __restrict__ ds, unsigned* cnt,
                               cudaGraphConditionalHandle hc, int use_cond) {
@@ -382,7 +412,7 @@ __global__ void k_cg_apply(LevelView<double> V, const double* __restrict__ p, do
 template <typename T>
 __global__ void k_cg_update(int nn, double* __restrict__ u, double* __restrict__ r,
                             const double* __restrict__ p, const double* __restrict__ q,
-                            T* __restrict__ b0, const T* __restrict__ dinv0, T omega,
+                            T* __restrict__ b0, const op_t<T>* __restrict__ dinv0, T omega,
                             T* __restrict__ v0, double* part_rr, DevState* __restrict__ ds,
                             unsigned* cnt, cudaGraphConditionalHandle hc, int use_cond) {
   const double alpha = ds->alpha;
@@ -429,11 +459,13 @@ __global__ void k_cast(size_t n, const A* __restrict__ a, B* __restrict__ b) {
 inline int grid_nodes(long nn) { return parts_for(nn); }
 
 template <typename T>
-const T* dinv_of(const Level& L);
+const op_t<T>* dinv_of(const Level& L);
 template <>
 const double* dinv_of<double>(const Level& L) { return L.dinv64; }
 template <>
 const float* dinv_of<float>(const Level& L) { return L.dinv32; }
+template <>
+const float* dinv_of<dfloat>(const Level& L) { return L.dinv32; }
 
 template <typename T>
 void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp& tc,
@@ -450,7 +482,7 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
   const LevelView<T> V = view<T>(F);
   const bool c_coarsest = (l + 1 == L - 1);
   const bool use_tc = tc.on && l == 0;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (std::is_same<T, float>::value) {
     if (use_tc) {  // r = b - A v with A v from the tensor-core stacked contraction
       launch_tc_apply(F, tc.m, (const float*)F.v, tc.w32, tc.KT, tc.Ye, tc.err, tc.sms, st);
       launch_tc_gather(F, tc.Ye, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 0,
@@ -465,7 +497,7 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
   vcycle_rec<T>(lv, l + 1, L, omega, Ainv, tc, st);
   k_vc_prolong<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, F.mask,
                                                             (const T*)C.z, (T*)F.v);
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (std::is_same<T, float>::value) {
     if (use_tc) {  // z = v + omega D^-1 (b - A v)
       launch_tc_apply(F, tc.m, (const float*)F.v, tc.w32, tc.KT, tc.Ye, tc.err, tc.sms, st);
       launch_tc_gather(F, tc.Ye, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 1,
@@ -479,63 +511,59 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
 
 }  // namespace
 
-void launch_vcycle(bool fp64, Level* lv, int L, double omega, int gamma, const double* Ainv,
+// Runs BODY with T bound to the vector type of vt.
+#define VT_DISPATCH(vt, BODY)                 \
+  do {                                        \
+    if ((vt) == kVtF64) {                     \
+      using T = double;                       \
+      BODY;                                   \
+    } else if ((vt) == kVtF32) {              \
+      using T = float;                        \
+      BODY;                                   \
+    } else {                                  \
+      using T = dfloat;                       \
+      BODY;                                   \
+    }                                         \
+  } while (0)
+
+void launch_vcycle(int vt, Level* lv, int L, double omega, int gamma, const double* Ainv,
                    const TcOp& tc, cudaStream_t st) {
   (void)gamma;
-  if (fp64)
-    vcycle_rec<double>(lv, 0, L, omega, Ainv, tc, st);
-  else
-    vcycle_rec<float>(lv, 0, L, (float)omega, Ainv, tc, st);
+  VT_DISPATCH(vt, vcycle_rec<T>(lv, 0, L, (T)omega, Ainv, tc, st));
 }
 
 void launch_set_params(DevState* ds, const double* params, cudaStream_t st) {
   k_set_params<<<1, 32, 0, st>>>(ds, params);
 }
 
-void launch_smooth0(bool fp64, const Level& L0, double omega, cudaStream_t st) {
+void launch_smooth0(int vt, const Level& L0, double omega, cudaStream_t st) {
   const int g = parts_for(L0.nn);
-  if (fp64)
-    k_smooth0<double><<<g, kRowThreads, 0, st>>>(L0.ndof, omega, L0.dinv64, (const double*)L0.b,
-                                                 (double*)L0.v);
-  else
-    k_smooth0<float><<<g, kRowThreads, 0, st>>>(L0.ndof, (float)omega, L0.dinv32,
-                                                (const float*)L0.b, (float*)L0.v);
+  VT_DISPATCH(vt, (k_smooth0<T><<<g, kRowThreads, 0, st>>>(L0.ndof, (T)omega, dinv_of<T>(L0),
+                                                           (const T*)L0.b, (T*)L0.v)));
 }
 
 void launch_cg_prep(const Level& L0, double* f, double* u, double* part, int np, cudaStream_t st) {
   k_cg_prep<<<np, kRowThreads, 0, st>>>(L0.nn, L0.mask, f, u, part);
 }
 
-void launch_cg_residual(bool fp64, const Level& L0, double omega, const double* f, const double* u,
+void launch_cg_residual(int vt, const Level& L0, double omega, const double* f, const double* u,
                         double* r, int mode, double* part, const double* part_ff, int np,
                         DevState* ds, unsigned* cnt, cudaGraphConditionalHandle hc, int use_cond,
                         cudaStream_t st) {
-  if (fp64)
-    k_cg_residual<double><<<np, kRowThreads, 0, st>>>(view<double>(L0), f, u, r, (double*)L0.b,
-                                                      L0.dinv64, omega, (double*)L0.v, part, part_ff,
-                                                      mode, ds, cnt, hc, use_cond);
-  else
-    k_cg_residual<float><<<np, kRowThreads, 0, st>>>(view<double>(L0), f, u, r, (float*)L0.b,
-                                                     L0.dinv32, (float)omega, (float*)L0.v, part,
-                                                     part_ff, mode, ds, cnt, hc, use_cond);
+  VT_DISPATCH(vt, (k_cg_residual<T><<<np, kRowThreads, 0, st>>>(
+                      view<double>(L0), f, u, r, (T*)L0.b, dinv_of<T>(L0), (T)omega, (T*)L0.v,
+                      part, part_ff, mode, ds, cnt, hc, use_cond)));
 }
 
-void launch_cg_dots_rz(bool fp64, const Level& L0, const double* r, const double* q, double* part_rz,
+void launch_cg_dots_rz(int vt, const Level& L0, const double* r, const double* q, double* part_rz,
                        double* part_zq, int np, DevState* ds, unsigned* cnt, cudaStream_t st) {
-  if (fp64)
-    k_cg_dots_rz<double><<<np, kRowThreads, 0, st>>>(L0.nn, r, (const double*)L0.z, q, part_rz,
-                                                     part_zq, ds, cnt);
-  else
-    k_cg_dots_rz<float><<<np, kRowThreads, 0, st>>>(L0.nn, r, (const float*)L0.z, q, part_rz,
-                                                    part_zq, ds, cnt);
+  VT_DISPATCH(vt, (k_cg_dots_rz<T><<<np, kRowThreads, 0, st>>>(L0.nn, r, (const T*)L0.z, q, part_rz,
+                                                               part_zq, ds, cnt)));
 }
 
-void launch_cg_dir(bool fp64, const Level& L0, double* p, int np, const DevState* ds,
+void launch_cg_dir(int vt, const Level& L0, double* p, int np, const DevState* ds,
                    cudaStream_t st) {
-  if (fp64)
-    k_cg_dir<double><<<np, kRowThreads, 0, st>>>(L0.nn, (const double*)L0.z, p, ds);
-  else
-    k_cg_dir<float><<<np, kRowThreads, 0, st>>>(L0.nn, (const float*)L0.z, p, ds);
+  VT_DISPATCH(vt, (k_cg_dir<T><<<np, kRowThreads, 0, st>>>(L0.nn, (const T*)L0.z, p, ds)));
 }
 
 void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np, DevState* ds,
@@ -543,23 +571,16 @@ void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, 
   k_cg_apply<<<np, kRowThreads, 0, st>>>(view<double>(L0), p, q, part, ds, cnt);
 }
 
-void launch_cg_update(bool fp64, const Level& L0, double omega, double* u, double* r, const double* p,
+void launch_cg_update(int vt, const Level& L0, double omega, double* u, double* r, const double* p,
                       const double* q, double* part_rr, int np, DevState* ds, unsigned* cnt,
                       cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st) {
-  if (fp64)
-    k_cg_update<double><<<np, kRowThreads, 0, st>>>(L0.nn, u, r, p, q, (double*)L0.b, L0.dinv64, omega,
-                                                     (double*)L0.v, part_rr, ds, cnt, hc, use_cond);
-  else
-    k_cg_update<float><<<np, kRowThreads, 0, st>>>(L0.nn, u, r, p, q, (float*)L0.b, L0.dinv32,
-                                                    (float)omega, (float*)L0.v, part_rr, ds, cnt, hc,
-                                                    use_cond);
+  VT_DISPATCH(vt, (k_cg_update<T><<<np, kRowThreads, 0, st>>>(
+                      L0.nn, u, r, p, q, (T*)L0.b, dinv_of<T>(L0), (T)omega, (T*)L0.v, part_rr,
+                      ds, cnt, hc, use_cond)));
 }
 
-void launch_apply_diag(bool fp64, const Level& L, const double* x, double* y, cudaStream_t st) {
-  if (fp64)
-    k_apply_diag<double><<<grid_nodes(L.nn), kRowThreads, 0, st>>>(view<double>(L), x, y);
-  else
-    k_apply_diag<float><<<grid_nodes(L.nn), kRowThreads, 0, st>>>(view<float>(L), x, y);
+void launch_apply_diag(int vt, const Level& L, const double* x, double* y, cudaStream_t st) {
+  VT_DISPATCH(vt, (k_apply_diag<T><<<grid_nodes(L.nn), kRowThreads, 0, st>>>(view<T>(L), x, y)));
 }
 
 void launch_cast(bool to_fp64, size_t n, const void* a, void* b, bool src_fp64, cudaStream_t st) {
@@ -575,6 +596,16 @@ void launch_cast(bool to_fp64, size_t n, const void* a, void* b, bool src_fp64, 
     else
       k_cast<float, float><<<g, kBS, 0, st>>>(n, (const float*)a, (float*)b);
   }
+}
+
+void launch_vec_in(int vt, size_t n, const double* a, void* b, cudaStream_t st) {
+  const int g = (int)((n + kBS - 1) / kBS < 4096 ? (n + kBS - 1) / kBS : 4096);
+  VT_DISPATCH(vt, (k_cast<double, T><<<g, kBS, 0, st>>>(n, a, (T*)b)));
+}
+
+void launch_vec_out(int vt, size_t n, const void* a, double* b, cudaStream_t st) {
+  const int g = (int)((n + kBS - 1) / kBS < 4096 ? (n + kBS - 1) / kBS : 4096);
+  VT_DISPATCH(vt, (k_cast<T, double><<<g, kBS, 0, st>>>(n, (const T*)a, b)));
 }
 
 }  // namespace tos

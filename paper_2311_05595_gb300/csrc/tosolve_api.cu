@@ -97,7 +97,10 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (!(d.penal >= 1.0)) { *why = "penal must be >= 1"; return TOSOLVE_EINVAL; }
   if (!(d.rmin >= 0.0) || d.rmin * d.n_mr > 16.0) { *why = "rmin*n_mr must be in [0, 16]"; return TOSOLVE_EINVAL; }
   if (d.precision != TOSOLVE_PREC_FP64 && d.precision != TOSOLVE_PREC_FP32 &&
-      d.precision != TOSOLVE_PREC_TF32) { *why = "unknown precision"; return TOSOLVE_EINVAL; }
+      d.precision != TOSOLVE_PREC_TF32 && d.precision != TOSOLVE_PREC_FP32X2) {
+    *why = "unknown precision";
+    return TOSOLVE_EINVAL;
+  }
   if (d.precision == TOSOLVE_PREC_TF32 && !tc_supported(d.n_mr)) {
     *why = "TF32 tensor-core preconditioner needs n_mr <= 2 (24 n^3 stacked rows <= 256)";
     return TOSOLVE_EINVAL;
@@ -123,6 +126,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   P->noff = count_offsets(d.n_mr, d.rmin);
   const bool fp32 = d.precision != TOSOLVE_PREC_FP64;
   const bool tf32 = d.precision == TOSOLVE_PREC_TF32 && L > 1;
+  const bool x2 = d.precision == TOSOLVE_PREC_FP32X2;
   const int maxrhs = d.max_rhs > 0 ? d.max_rhs : 1;
   size_t B = 0;
   size_t keB = 0;
@@ -134,9 +138,9 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     v.ndof = 3 * v.nn;
     v.nsub = d.n_mr << l;
     const bool coarsest = l == L - 1;
-    v.s64 = (l == 0) || !fp32 || coarsest;
+    v.s64 = (l == 0) || !fp32 || coarsest || x2;  // FP32X2: every level formed in FP64
     v.s32 = fp32 && !coarsest && !(tf32 && l == 0);  // TF32: level 0 runs on tensor cores
-    const size_t tsz = fp32 ? 4 : 8;
+    const size_t tsz = (fp32 && !x2) ? 4 : 8;
     B += v.ndof;  // mask
     if (v.s64) B += 243 * v.nn * 8 + v.ndof * 8;
     if (v.s32) B += 243 * v.nn * 4 + v.ndof * 4;
@@ -197,7 +201,14 @@ void free_all(tosolve_s* h) {
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
 }
 
-bool prec_fp64(const tosolve_s* h) { return h->d.precision == TOSOLVE_PREC_FP64; }
+// Arithmetic of the multigrid vectors for the handle's precision.
+int vt_of(const tosolve_s* h) {
+  switch (h->d.precision) {
+    case TOSOLVE_PREC_FP64: return kVtF64;
+    case TOSOLVE_PREC_FP32X2: return kVtDF;
+    default: return kVtF32;
+  }
+}
 
 // Appends the PCG loop of one right-hand side to the stream capture active
 // on cs: prep, r0 = f - K u0 and the convergence test; a device-side while
@@ -205,7 +216,7 @@ bool prec_fp64(const tosolve_s* h) { return h->d.precision == TOSOLVE_PREC_FP64;
 // q = K p, update and test; then the FP64 true residual.  The loop runs
 // without host round trips.
 cudaError_t append_solve(tosolve_s* h, cudaStream_t cs, cudaStream_t bs) {
-  const bool fp64 = prec_fp64(h);
+  const int vt = vt_of(h);
   Level& L0 = h->lv[0];
   const int np = h->np;
   double* part0 = h->part;
@@ -221,7 +232,7 @@ cudaError_t append_solve(tosolve_s* h, cudaStream_t cs, cudaStream_t bs) {
   cudaGraphConditionalHandle hc = 0;
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, cgraph, 1, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) {
-    launch_cg_residual(fp64, L0, h->d.omega, h->f, h->u, h->r, 1, part1, part0, np, h->ds, h->cnt, hc,
+    launch_cg_residual(vt, L0, h->d.omega, h->f, h->u, h->r, 1, part1, part0, np, h->ds, h->cnt, hc,
                        1, cs);
     e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cgraph, &deps, nullptr, &ndeps);
   }
@@ -238,17 +249,17 @@ cudaError_t append_solve(tosolve_s* h, cudaStream_t cs, cudaStream_t bs) {
   if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, bs);
-    launch_cg_dots_rz(fp64, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, bs);
-    launch_cg_dir(fp64, L0, h->p, np, h->ds, bs);
+    launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, bs);
+    launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, bs);
+    launch_cg_dir(vt, L0, h->p, np, h->ds, bs);
     launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, bs);
-    launch_cg_update(fp64, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, hc, 1,
+    launch_cg_update(vt, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, hc, 1,
                      bs);
     cudaGraph_t bo = nullptr;
     e = cudaStreamEndCapture(bs, &bo);
   }
   if (e == cudaSuccess)
-    launch_cg_residual(fp64, L0, h->d.omega, h->f, h->u, h->tmpa, 2, part1, part0, np, h->ds, h->cnt,
+    launch_cg_residual(vt, L0, h->d.omega, h->f, h->u, h->tmpa, 2, part1, part0, np, h->ds, h->cnt,
                        hc, 0, cs);
   return e;
 }
@@ -365,7 +376,7 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
     if (v.s64) { CKC(dalloc(h, &L.S64, 243 * v.nn)); CKC(dalloc(h, &L.dinv64, v.ndof)); }
     if (v.s32) { CKC(dalloc(h, &L.S32, 243 * v.nn)); CKC(dalloc(h, &L.dinv32, v.ndof)); }
     if (tf32 && l == 0) CKC(dalloc(h, &L.dinv32, v.ndof));
-    const size_t tsz = fp32 ? 4 : 8;
+    const size_t tsz = vt_of(h) == kVtF32 ? 4 : 8;
     void** vecs[4] = {&L.b, &L.v, &L.r, &L.z};
     for (void** pv : vecs) {
       char* p = nullptr;
@@ -566,12 +577,16 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
       if (Lv.dinv32) launch_to_fp32((size_t)Lv.ndof, Lv.dinv64, Lv.dinv32, st);
       if (h->tc.on) launch_weights_elem(Lv, n, h->w, h->Dx, h->Dy, h->w32, st);
     } else {
-      const bool op64 = !fp32;
+      const bool op64 = !fp32 || d.precision == TOSOLVE_PREC_FP32X2;
       launch_elem_moments(op64, Lv, h->w, h->Dx, h->Dy, h->cmom64, h->Mom, h->Ke, st);
       if (op64)
         launch_assemble(true, Lv, h->Ke, Lv.S64, Lv.dinv64, st);
       else
         launch_assemble(false, Lv, h->Ke, Lv.S32, Lv.dinv32, st);
+      if (op64 && Lv.S32) {  // FP32X2: FP32 copy of the FP64-formed operator
+        launch_to_fp32((size_t)243 * Lv.nn, Lv.S64, Lv.S32, st);
+        launch_to_fp32((size_t)Lv.ndof, Lv.dinv64, Lv.dinv32, st);
+      }
     }
   }
   if (L > 1) {
@@ -586,28 +601,28 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
 static tosolve_status run_loop_nograph(tosolve_t h) {
   // Same kernels as the graph, driven from the host (profiling path: ncu
   // cannot profile kernels of a graph that holds a conditional node).
-  const bool fp64 = prec_fp64(h);
+  const int vt = vt_of(h);
   Level& L0 = h->lv[0];
   const int np = h->np;
   double *part0 = h->part, *part1 = h->part + kMaxPart, *part2 = h->part + 2 * kMaxPart,
          *part3 = h->part + 3 * kMaxPart;
   cudaStream_t st = h->st;
   launch_cg_prep(L0, h->f, h->u, part0, np, st);
-  launch_cg_residual(fp64, L0, h->d.omega, h->f, h->u, h->r, 1, part1, part0, np, h->ds, h->cnt, 0, 0,
+  launch_cg_residual(vt, L0, h->d.omega, h->f, h->u, h->r, 1, part1, part0, np, h->ds, h->cnt, 0, 0,
                      st);
   CK(cudaMemcpyAsync(h->hs, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   while (!h->hs->converged && h->hs->status == 0 && h->hs->iter < h->hs->maxit) {
-    launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, st);
-    launch_cg_dots_rz(fp64, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, st);
-    launch_cg_dir(fp64, L0, h->p, np, h->ds, st);
+    launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, st);
+    launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, st);
+    launch_cg_dir(vt, L0, h->p, np, h->ds, st);
     launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, st);
-    launch_cg_update(fp64, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, 0, 0,
+    launch_cg_update(vt, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, 0, 0,
                      st);
     CK(cudaMemcpyAsync(h->hs, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
-  launch_cg_residual(fp64, L0, h->d.omega, h->f, h->u, h->tmpa, 2, part1, part0, np, h->ds, h->cnt, 0,
+  launch_cg_residual(vt, L0, h->d.omega, h->f, h->u, h->tmpa, 2, part1, part0, np, h->ds, h->cnt, 0,
                      0, st);
   return TOSOLVE_OK;
 }
@@ -789,10 +804,10 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
   const Level& L = h->lv[level];
   if (precision == 0) {
     if (!L.S64) return set_err(h, TOSOLVE_EINVAL, "this level has no FP64 operator");
-    launch_apply_diag(true, L, x_dev, y_dev, h->st);
-  } else if (precision == 1) {
+    launch_apply_diag(kVtF64, L, x_dev, y_dev, h->st);
+  } else if (precision == 1 || precision == 3) {
     if (!L.S32) return set_err(h, TOSOLVE_EINVAL, "this level has no FP32 operator");
-    launch_apply_diag(false, L, x_dev, y_dev, h->st);
+    launch_apply_diag(precision == 1 ? kVtF32 : kVtDF, L, x_dev, y_dev, h->st);
   } else if (precision == 2) {
     if (level != 0 || !h->tc.on) return set_err(h, TOSOLVE_EINVAL, "no tensor-core operator on this level");
     // masked copy feeds the elements; the unmasked copy gives the identity rows
@@ -804,7 +819,7 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
     launch_tc_gather(L0, h->Ye, (const float*)L0.b, (const float*)L0.b, L0.dinv32, 0.f, 2, (float*)L0.r, h->st);
     launch_cast(true, (size_t)L0.ndof, L0.r, y_dev, false, h->st);
   } else {
-    return set_err(h, TOSOLVE_EINVAL, "precision must be 0, 1 or 2");
+    return set_err(h, TOSOLVE_EINVAL, "precision must be 0, 1, 2 or 3");
   }
   CK(cudaGetLastError());
   return TOSOLVE_OK;
@@ -813,15 +828,12 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
 tosolve_status tosolve_precondition(tosolve_t h, const double* b_dev, double* z_dev) {
   if (h == nullptr || b_dev == nullptr || z_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
   if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");
-  const bool fp64 = prec_fp64(h);
+  const int vt = vt_of(h);
   Level& L0 = h->lv[0];
-  if (fp64)
-    CK(cudaMemcpyAsync(L0.b, b_dev, (size_t)L0.ndof * 8, cudaMemcpyDeviceToDevice, h->st));
-  else
-    launch_cast(false, (size_t)L0.ndof, b_dev, L0.b, true, h->st);
-  if (h->L > 1) launch_smooth0(fp64, L0, h->d.omega, h->st);
-  launch_vcycle(fp64, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, h->st);
-  launch_cast(true, (size_t)L0.ndof, L0.z, z_dev, fp64, h->st);
+  launch_vec_in(vt, (size_t)L0.ndof, b_dev, L0.b, h->st);
+  if (h->L > 1) launch_smooth0(vt, L0, h->d.omega, h->st);
+  launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, h->st);
+  launch_vec_out(vt, (size_t)L0.ndof, L0.z, z_dev, h->st);
   CK(cudaGetLastError());
   return TOSOLVE_OK;
 }

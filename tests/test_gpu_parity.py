@@ -5,6 +5,11 @@ Tolerances (the bar of the task, stated per check):
     relative 1e-13 (different summation orders / formulas on each side);
   * FP32 preconditioner operators: relative 1e-6 (single rounding of FP64
     values plus FP32 accumulation of 27 blocks);
+  * FP32X2 operator apply (FP32 coefficients, float-pair arithmetic) against
+    the FP64 product with the FP32-rounded oracle operator: relative 1e-9
+    (the float-pair sum carries about 48 bits; the GPU's and the oracle's
+    FP64 operators agree to 1e-13, so their FP32 roundings differ in at most
+    a few entries by one FP32 ulp);
   * one multigrid cycle in FP64: relative 1e-9 (the coarse solve applies an
     explicit inverse formed from the Cholesky factor instead of two
     triangular solves; its error is about cond(A_c) * 1e-16);
@@ -23,7 +28,7 @@ from tests.gpu_helpers import Run, rel
 
 pytestmark = pytest.mark.gpu
 
-FP64, FP32, TF32 = 0, 1, 2
+FP64, FP32, TF32, FP32X2 = 0, 1, 2, 3
 
 
 _C1_REF = {}
@@ -153,9 +158,48 @@ def test_one_cycle_matches_algorithm_1():
     R.close()
 
 
+@pytest.mark.parametrize("n", [1, 2])
+def test_fp32x2_operators_and_cycle(n):
+    p = workloads.cantilever(12, 4, 8, n_mr=n, rmin=0.9 if n == 2 else 0.0, seed=8, mg_levels=3)
+    m = fe.Model(p)
+    rho = m.densities(p.x)
+    h = mg.Hierarchy(p, rho, 3)
+    rng = np.random.default_rng(1)
+    R = Run(p, FP32X2)
+    R.set_densities()
+    for l, L in enumerate(h.levels[:-1]):
+        x = rng.normal(size=L.ndof)
+        A32 = L.A.astype(np.float32).astype(np.float64)
+        y = R.apply(l, FP32X2, x)
+        assert rel(y, A32 @ x) <= 1e-9, l
+        assert rel(y, L.A @ x) <= 1e-6, l
+        assert rel(R.apply(l, FP32, x), A32 @ x) > 1e-9 or l > 0  # FP32 sums are coarser
+    b = np.where(p.mask == 0, rng.normal(size=p.ndof), 0.0)
+    assert rel(R.precondition(b), mg.vcycle(h, b)) <= 1e-5
+    R.close()
+
+
+def test_fp32x2_keeps_fp64_convergence_on_high_contrast_densities():
+    """rho ~ U[0.01, 1] (w from 1e-6 to 1): FP32 vector arithmetic in the
+    V-cycle raises the PCG iteration count (about +45% here); float pairs on
+    the same FP32 operators stay within 10% of the FP64 count (at this
+    conditioning the count moves by a few with any change of rounding)."""
+    p = workloads.batched_instances(1, 7, min_nx=64, max_nx=64, mult=8)[0]
+    its = {}
+    for prec in (FP64, FP32, FP32X2):
+        R = Run(p, prec)
+        R.set_densities()
+        u, info = R.solve(rtol=1e-8)
+        assert info.rel_residual <= 1e-8
+        its[prec] = info.iterations
+        R.close()
+    assert its[FP32X2] <= 1.1 * its[FP64], its
+    assert its[FP32X2] < its[FP32], its
+
+
 # ---- whole path ----------------------------------------------------------------
 
-@pytest.mark.parametrize("precision", [FP64, FP32, TF32])
+@pytest.mark.parametrize("precision", [FP64, FP32, TF32, FP32X2])
 @pytest.mark.parametrize("seed", [0, 1])
 def test_cantilever_24x12x12_matches_direct_solve(precision, seed):
     """Config: Q1 24x12x12, n = 1, clamped face, line load, rho ~ U[0.01, 1]."""
@@ -178,7 +222,7 @@ def test_cantilever_24x12x12_matches_direct_solve(precision, seed):
     R.close()
 
 
-@pytest.mark.parametrize("precision", [FP32, TF32])
+@pytest.mark.parametrize("precision", [FP32, TF32, FP32X2])
 def test_multiresolution_48x24x24_full_size(precision):
     """Config: density 96x48x48, Q1 48x24x24 (n = 2), smooth field, r = 1.5,
     4 levels, FP32 / TF32 preconditioner -- the benchmark workload."""
@@ -204,7 +248,7 @@ def test_ragged_and_single_level_meshes(shape, n, levels, rmin):
     p = workloads.cantilever(*shape, n_mr=n, rmin=rmin, seed=9, mg_levels=levels)
     m = fe.Model(p)
     ref = m.run(method="dense")
-    for prec in (FP64, FP32, TF32):
+    for prec in (FP64, FP32, TF32, FP32X2):
         if prec == TF32 and n > 2:
             continue
         R = Run(p, prec)
@@ -261,7 +305,7 @@ def test_zero_load_maxit_and_order():
     R.close()
 
 
-@pytest.mark.parametrize("precision", [FP32, TF32])
+@pytest.mark.parametrize("precision", [FP32, TF32, FP32X2])
 def test_bitwise_deterministic(precision):
     p = workloads.cantilever(16, 8, 8, n_mr=2, rmin=1.0, seed=6, mg_levels=3)
     R = Run(p, precision)
