@@ -29,7 +29,7 @@ def _nvcc() -> str:
 
 def _sources():
     srcs = [os.path.join(CSRC, u) for u in UNITS]
-    deps = srcs + [os.path.join(CSRC, "internal.cuh"),
+    deps = srcs + [os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "dfloat.cuh"),
                    os.path.join(os.path.dirname(HERE), "include", "tosolve.h")]
     return srcs, deps
 

@@ -3,10 +3,13 @@
 // Data layout in HBM (all arrays owned by the handle, allocated once in
 // tosolve_create):
 //   * DOF vectors: 3 values per lattice node, node id i + Lx*(j + Ly*l);
-//   * level operators: a 27-point stencil of 3x3 blocks per node, stored
-//     structure-of-arrays S[(o*9 + r*3 + c)*nn + node] with neighbour offset
-//     o = (dx+1) + 3*((dy+1) + 3*(dz+1)), so one warp reads 32 consecutive
-//     nodes' coefficient of the same (o, r, c) in one transaction;
+//   * level operators: a 27-point stencil of 3x3 blocks per node, in tiles
+//     of 32 consecutive nodes: S[((node/32)*243 + e)*32 + node%32] with
+//     e = o*9 + 3r + c and neighbour offset o = (dx+1) + 3*((dy+1) +
+//     3*(dz+1)).  A tile (243 x 32 coefficients) is one contiguous block
+//     that a single bulk copy moves into shared memory, and within it one
+//     warp reads the 32 nodes' coefficient e in one transaction.  The node
+//     count is padded to whole tiles (padding coefficients are zero);
 //   * element matrices: upper triangle (300 of 24x24) per element;
 //   * density / design grid: one FP64 per cell, x fastest.
 #pragma once
@@ -29,6 +32,14 @@ constexpr int kSym = 300;      // entries of a 24x24 symmetric upper triangle
 constexpr int kNB = 32;        // block size of the coarse Cholesky
 constexpr int kTile = 32;      // output tile of the coarse inverse product
 constexpr int kMaxCoarse = 4096;  // largest coarse system (DOFs)
+constexpr int kTN = 32;        // nodes per operator tile
+
+// Position of coefficient e (= o*9 + 3r + c) of node in a level operator.
+__host__ __device__ inline size_t op_idx(long node, int e) {
+  return ((size_t)(node / kTN) * 243 + e) * kTN + (size_t)(node % kTN);
+}
+// Coefficients stored for a level of nn nodes (whole tiles).
+inline size_t op_len(long nn) { return (size_t)((nn + kTN - 1) / kTN) * 243 * kTN; }
 
 // Scalars of the PCG loop, kept on the device so the loop runs as a CUDA
 // graph with a device-side while condition.
@@ -48,7 +59,8 @@ struct DevState {
   int converged;
   int coarse_status;  // non-zero if the coarse Cholesky met a bad pivot
   int tc_status;      // non-zero if a tensor-core tile wait timed out
-  int pad[2];
+  int tile_status;    // non-zero if an operator tile copy wait timed out
+  int pad;
 };
 
 struct Level {
@@ -58,6 +70,8 @@ struct Level {
   int nsub;         // density cells per element edge at this level
   double h;         // element edge length
   bool op64;        // operator stored in FP64 for the V-cycle
+  int sms = 1;      // SMs of the device (grid of the tile kernels)
+  int* err = nullptr;  // set when an operator tile copy times out
   uint8_t* mask = nullptr;
   double* S64 = nullptr;   // FP64 stencil (level 0 always; others when op64)
   float* S32 = nullptr;    // FP32 stencil (FP32 preconditioner levels)
@@ -88,6 +102,8 @@ struct LevelView {
   const op_t<T>* S;
   const op_t<T>* dinv;
   const uint8_t* mask;
+  int* err;
+  int sms;
 };
 
 // ---- launchers (k_setup.cu) ----------------------------------------------
@@ -155,6 +171,9 @@ void launch_cg_update(int vt, const Level& L0, double omega, double* u, double* 
                       const double* q, double* part_rr, int np, DevState* ds, unsigned* cnt,
                       cudaGraphConditionalHandle hc, int use_cond, cudaStream_t st);
 void launch_apply_diag(int vt, const Level& L, const double* x, double* y, cudaStream_t st);
+// Lets the stencil tile kernels use their shared-memory ring (once per
+// process and device, before the first launch).
+cudaError_t configure_tile_kernels();
 // FP64 vector <-> multigrid vector of arithmetic vt.
 void launch_vec_in(int vt, size_t n, const double* a, void* b, cudaStream_t st);
 void launch_vec_out(int vt, size_t n, const void* a, double* b, cudaStream_t st);

@@ -357,7 +357,7 @@ __global__ void k_assemble(int ex, int ey, int ez, int Lx, int Ly, int Lz, const
         const bool fc = valid ? (mask[3 * nb + c] != 0) : true;
         double v = acc[3 * r + c];
         if (fr || fc) v = (o == 13 && r == c) ? 1.0 : 0.0;
-        S[(size_t)(o * 9 + 3 * r + c) * nn + node] = (T)v;
+        S[op_idx(node, o * 9 + 3 * r + c)] = (T)v;
         if (o == 13 && r == c) dinv[3 * node + r] = (T)(1.0 / v);
       }
   }
@@ -381,7 +381,7 @@ __global__ void k_coarse_dense(int Lx, int Ly, int Lz, const double* __restrict_
     const long nb = node + dx + (long)Lx * (dy + (long)Ly * dz);
     for (int r = 0; r < 3; ++r)
       for (int c = 0; c < 3; ++c)
-        A[(3 * node + r) * n + 3 * nb + c] = S[(size_t)(o * 9 + 3 * r + c) * nn + node];
+        A[(3 * node + r) * n + 3 * nb + c] = S[op_idx(node, o * 9 + 3 * r + c)];
   }
 }
 

@@ -14,79 +14,205 @@ template <typename T>
 LevelView<T> view(const Level& L);
 template <>
 LevelView<double> view<double>(const Level& L) {
-  return LevelView<double>{L.Lx, L.Ly, L.Lz, L.nn, L.S64, L.dinv64, L.mask};
+  return LevelView<double>{L.Lx, L.Ly, L.Lz, L.nn, L.S64, L.dinv64, L.mask, L.err, L.sms};
 }
 template <>
 LevelView<float> view<float>(const Level& L) {
-  return LevelView<float>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask};
+  return LevelView<float>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask, L.err, L.sms};
 }
 template <>
 LevelView<dfloat> view<dfloat>(const Level& L) {
-  return LevelView<dfloat>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask};
+  return LevelView<dfloat>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask, L.err, L.sms};
 }
 
 namespace {
 
-// Row-parallel mapping of the stencil kernels: a block of kRowThreads = 192
-// threads covers 64 nodes; warp w handles output row r = w % 3 of 32
-// consecutive nodes, so each coefficient load S[(o*9 + 3r + c)*nn + node]
-// is one contiguous 32-wide access and the work of a level spreads over 3x
-// more warps (FP64 issue is 4 flop/clk/SM, so every SM must take a share).
-constexpr int kRowThreads = 192;
-constexpr int kRowNodes = 64;
+// Stencil kernels.  The operator is streamed tile by tile (32 nodes x 243
+// coefficients, one contiguous block, see internal.cuh) into a ring of
+// kStages shared-memory buffers by 1D bulk copies (TMA) that complete on an
+// mbarrier, so the coefficient stream -- nearly all of the kernel's DRAM
+// traffic -- runs ahead of the arithmetic instead of stalling each thread on
+// its own loads.  A block of 288 threads (9 warps) is persistent over its
+// tiles.  The operand vector is read from global memory (L1/L2: each value
+// is used by 27 neighbours and 3 rows).
+constexpr int kTileThreads = 9 * kTN;  // 3 rows x 3 neighbour planes
+constexpr int kStages = 3;
+constexpr long kTileSpin = 1L << 22;  // bound of every mbarrier wait
 
-// (A x)_{node, r}: ld(nb, c) loads component c of the operand at node nb.
-// Neighbours outside the lattice are clamped onto it: their stencil
-// coefficients are zero (assembly writes 0 there), so the load is harmless
-// and the loop has no branch -- every load of the 27 neighbours can be in
-// flight at once instead of one memory round trip per neighbour.
+template <typename T>
+constexpr uint32_t tile_bytes() { return 243u * kTN * (uint32_t)sizeof(op_t<T>); }
+template <typename T>
+constexpr size_t tile_smem() { return (size_t)kStages * tile_bytes<T>() + kStages * sizeof(uint64_t); }
+// Blocks of the tile kernels resident per SM (shared-memory bound).
+template <typename T>
+constexpr int tile_blocks_per_sm() { return sizeof(op_t<T>) == 4 ? 2 : 1; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tile_issue(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool tile_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < kTileSpin && !done; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+
+// Operand loads through the read-only path.  They are volatile asm so that
+// the compiler issues all of a row's loads, in order, before the products
+// that consume them: left to itself it schedules each load next to its use
+// and the row then waits on one load at a time.
+__device__ __forceinline__ float ld_nc(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_nc(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ dfloat ld_nc(const dfloat* p) {
+  float h, l;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(h), "=f"(l) : "l"(p));
+  return dfloat(h, l);
+}
+
+// Partial of row r of (A x) at node over the 9 neighbours in z-plane g
+// (o = 9g .. 9g+8), from the tile's coefficients sb (shared memory);
+// ld(nb, c) loads component c of the operand at node nb.  Neighbours outside
+// the lattice are clamped onto it (their coefficients are zero), so there is
+// no branch.
+template <typename T>
+struct Partial { using type = T; };
+template <>
+struct Partial<dfloat> { using type = Dot2; };
+template <typename T>
+using partial_t = typename Partial<T>::type;
+
 template <typename T, typename LD>
-__device__ __forceinline__ T stencil_row(const LevelView<T>& V, long node, int i, int j, int l, int r,
-                                         LD ld) {
-  const size_t nn = V.nn;
+__device__ __forceinline__ T plane_row(const LevelView<T>& V, const op_t<T>* __restrict__ sb, long node,
+                                       int i, int j, int l, int r, int g, LD ld) {
   const long sx[3] = {i > 0 ? -1L : 0L, 0L, i + 1 < V.Lx ? 1L : 0L};
   const long sy[3] = {j > 0 ? -(long)V.Lx : 0L, 0L, j + 1 < V.Ly ? (long)V.Lx : 0L};
-  const long sz[3] = {l > 0 ? -(long)V.Lx * V.Ly : 0L, 0L, l + 1 < V.Lz ? (long)V.Lx * V.Ly : 0L};
+  const long zoff = g == 0 ? (l > 0 ? -(long)V.Lx * V.Ly : 0L) : g == 1 ? 0L
+                                                                   : (l + 1 < V.Lz ? (long)V.Lx * V.Ly : 0L);
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
-  for (int o = 0; o < 27; ++o) {
-    const long nb = node + sx[o % 3] + sy[(o / 3) % 3] + sz[o / 9];
-    const T* s = V.S + (size_t)(o * 9 + 3 * r) * nn + node;
-    acc[o % 3] += s[0] * ld(nb, 0) + s[nn] * ld(nb, 1) + s[2 * nn] * ld(nb, 2);
+  for (int q = 0; q < 9; ++q) {
+    const long nb = node + sx[q % 3] + sy[q / 3] + zoff;
+    const op_t<T>* s = sb + ((9 * g + q) * 9 + 3 * r) * kTN;
+    acc[q % 3] += s[0] * ld(nb, 0) + s[kTN] * ld(nb, 1) + s[2 * kTN] * ld(nb, 2);
   }
   return (acc[0] + acc[1]) + acc[2];
 }
 
-// The same row with FP32 coefficients and float-pair operands, summed by
-// Dot2 (every product and addition error kept): the result carries about
-// twice FP32's precision at a few FP32 operations per coefficient.
+// The same with FP32 coefficients and float-pair operands, summed by Dot2
+// (every product and addition error kept): the result carries about twice
+// FP32's precision at a few FP32 operations per coefficient.
 template <typename LD>
-__device__ __forceinline__ dfloat stencil_row(const LevelView<dfloat>& V, long node, int i, int j,
-                                              int l, int r, LD ld) {
-  const size_t nn = V.nn;
+__device__ __forceinline__ Dot2 plane_row(const LevelView<dfloat>& V, const float* __restrict__ sb,
+                                          long node, int i, int j, int l, int r, int g, LD ld) {
   const long sx[3] = {i > 0 ? -1L : 0L, 0L, i + 1 < V.Lx ? 1L : 0L};
   const long sy[3] = {j > 0 ? -(long)V.Lx : 0L, 0L, j + 1 < V.Ly ? (long)V.Lx : 0L};
-  const long sz[3] = {l > 0 ? -(long)V.Lx * V.Ly : 0L, 0L, l + 1 < V.Lz ? (long)V.Lx * V.Ly : 0L};
+  const long zoff = g == 0 ? (l > 0 ? -(long)V.Lx * V.Ly : 0L) : g == 1 ? 0L
+                                                                   : (l + 1 < V.Lz ? (long)V.Lx * V.Ly : 0L);
   Dot2 acc[3];
 #pragma unroll
-  for (int o = 0; o < 27; ++o) {
-    const long nb = node + sx[o % 3] + sy[(o / 3) % 3] + sz[o / 9];
-    const float* s = V.S + (size_t)(o * 9 + 3 * r) * nn + node;
-    acc[o % 3].add(s[0], ld(nb, 0));
-    acc[o % 3].add(s[nn], ld(nb, 1));
-    acc[o % 3].add(s[2 * nn], ld(nb, 2));
+  for (int q = 0; q < 9; ++q) {
+    const long nb = node + sx[q % 3] + sy[q / 3] + zoff;
+    const float* s = sb + ((9 * g + q) * 9 + 3 * r) * kTN;
+    acc[q % 3].add(s[0], ld(nb, 0));
+    acc[q % 3].add(s[kTN], ld(nb, 1));
+    acc[q % 3].add(s[2 * kTN], ld(nb, 2));
   }
   acc[0].add(acc[1]);
   acc[0].add(acc[2]);
-  return acc[0].value();
+  return acc[0];
 }
 
-#define ROW_LOOP(nn)                                                                  \
-  const int lane_ = threadIdx.x & 31, r = (threadIdx.x >> 5) % 3,                     \
-            grp_ = threadIdx.x / 96;                                                  \
-  for (long base_ = (long)blockIdx.x * kRowNodes; base_ < (nn);                       \
-       base_ += (long)gridDim.x * kRowNodes)                                          \
-    for (long node = base_ + grp_ * 32 + lane_, once_ = 0; once_ == 0 && node < (nn); ++once_)
+template <typename P>
+__device__ __forceinline__ P sum3(P a, P b, P c) { return (a + b) + c; }
+__device__ __forceinline__ dfloat sum3(Dot2 a, const Dot2& b, const Dot2& c) {
+  a.add(b);
+  a.add(c);
+  return a.value();
+}
+
+// Runs row(node, r, y) with y = (A x)_{node, r} for every node of the tiles
+// this block owns (tiles blockIdx.x, +gridDim.x, ...).  Thread 0 keeps
+// kStages tile copies in flight; a stage is refilled once every warp is done
+// with it.  Warp w = 3g + r computes, for the tile's 32 nodes, the part of
+// row r that comes from the neighbours in z-plane g; the three parts meet in
+// shared memory and the g = 0 warps finish the rows.  Every wait is bounded:
+// if a copy does not land in time the block sets *V.err, waits (bounded) for
+// its other copies and stops; the result is then invalid and the host
+// reports the error.
+template <typename T, typename LD, typename ROW>
+__device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW row) {
+  extern __shared__ __align__(128) unsigned char tsm[];
+  using O = op_t<T>;
+  using PT = partial_t<T>;
+  constexpr uint32_t kBytes = tile_bytes<T>();
+  __shared__ PT parts[3][kTileThreads / 3];
+  O* sbuf = reinterpret_cast<O*>(tsm);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + (size_t)kStages * kBytes);
+  const int tid = threadIdx.x, g = tid / 96, rl = tid % 96, r = rl >> 5, lane = tid & 31;
+  const long ntiles = ((long)V.nn + kTN - 1) / kTN;
+  const long nk = (long)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const char* gsrc = reinterpret_cast<const char*>(V.S);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (long k = 0; k < kStages && k < nk; ++k)
+      tile_issue(tsm + k * kBytes, gsrc + (size_t)(blockIdx.x + k * gridDim.x) * kBytes, kBytes,
+                 &bars[k]);
+  long k = 0;
+  for (; k < nk; ++k) {
+    const int s = (int)(k % kStages);
+    const bool got = tile_wait(&bars[s], (uint32_t)((k / kStages) & 1));
+    if (__syncthreads_or(!got)) break;
+    const long node = (blockIdx.x + k * gridDim.x) * kTN + lane;
+    const bool live = node < V.nn;
+    const int i = node % V.Lx, j = (node / V.Lx) % V.Ly, l = node / ((long)V.Lx * V.Ly);
+    if (live) parts[g][rl] = plane_row(V, sbuf + (size_t)s * 243 * kTN + lane, node, i, j, l, r, g, ld);
+    __syncthreads();  // stage s is free; the three parts are in
+    if (tid == 0 && k + kStages < nk) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tile_issue(tsm + (size_t)s * kBytes,
+                 gsrc + (size_t)(blockIdx.x + (k + kStages) * gridDim.x) * kBytes, kBytes, &bars[s]);
+    }
+    if (g == 0 && live) row(node, r, sum3(parts[0][rl], parts[1][rl], parts[2][rl]));
+    __syncthreads();  // parts are free
+  }
+  if (k < nk && tid == 0) {  // timed out: flag, then let the copies in flight land
+    atomicExch(V.err, 1);
+    for (long q = k; q < nk && q < k + kStages; ++q)
+      tile_wait(&bars[q % kStages], (uint32_t)((q / kStages) & 1));
+  }
+}
+
+// Threads per block of the vector kernels (one DOF or node per thread).
+constexpr int kRowThreads = 192;
 
 #define DOF_LOOP(ndof)                                                             \
   for (long d = blockIdx.x * (long)blockDim.x + threadIdx.x; d < (ndof);           \
@@ -95,10 +221,6 @@ __device__ __forceinline__ dfloat stencil_row(const LevelView<dfloat>& V, long n
 #define NODE_LOOP(nn)                                                              \
   for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < (nn);       \
        node += (long)gridDim.x * blockDim.x)
-
-#define NODE_IJL(V)                                                                \
-  const int i = node % (V).Lx, j = (node / (V).Lx) % (V).Ly,                       \
-            l = node / ((long)(V).Lx * (V).Ly)
 
 // Deterministic block sum of one double (result valid in thread 0).
 __device__ __forceinline__ double block_sum(double v) {
@@ -149,18 +271,29 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle hc, int use_
 
 // ---- multigrid cycle ------------------------------------------------------
 
-// Residual after the pre-smoothing step from a zero guess: the producer of
-// b already wrote v = omega D^-1 b; here r = b - A v.
 template <typename T>
-__global__ void k_vc_pre(LevelView<T> V, const T* __restrict__ b, const T* __restrict__ v,
-                         T* __restrict__ r_out) {
-  ROW_LOOP(V.nn) {
-    NODE_IJL(V);
-    const T y = stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return v[3 * nb + c]; });
+__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_vc_pre(LevelView<T> V, const T* __restrict__ b,
+                                                        const T* __restrict__ v, T* __restrict__ r_out) {
+  for_each_row(V, [&](long nb, int c) { return ld_nc(v + 3 * nb + c); }, [&](long node, int r, T y) {
     const long d = 3 * node + r;
     r_out[d] = b[d] - y;
-  }
+  });
 }
+
+// Weighted sum with FP32 weights (the transfer weights are powers of 1/2,
+// exact in FP32): plain for FP64 / FP32, compensated (Dot2) for float pairs.
+template <typename T>
+struct Acc {
+  T s = T(0);
+  __device__ __forceinline__ void add(float w, T x) { s += (T)w * x; }
+  __device__ __forceinline__ T value() const { return s; }
+};
+template <>
+struct Acc<dfloat> {
+  Dot2 d;
+  __device__ __forceinline__ void add(float w, dfloat x) { d.add(w, x); }
+  __device__ __forceinline__ dfloat value() const { return d.value(); }
+};
 
 // b_H = M_H P^T r_h: each coarse node gathers the 3x3x3 fine nodes around its
 // coincident fine node with weights (1, 1/2) per axis; also v_H = omega
@@ -173,30 +306,30 @@ __global__ void k_vc_restrict(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int L
   const long nnc = (long)Lxc * Lyc * Lzc;
   NODE_LOOP(nnc) {
     const int I = node % Lxc, J = (node / Lxc) % Lyc, K = node / ((long)Lxc * Lyc);
-    T a[3] = {0, 0, 0};
+    Acc<T> a[3];
     for (int dz = -1; dz <= 1; ++dz) {
       const int l = 2 * K + dz;
       if (l < 0 || l >= Lzf) continue;
-      const T wz = dz ? T(0.5) : T(1);
+      const float wz = dz ? 0.5f : 1.f;
       for (int dy = -1; dy <= 1; ++dy) {
         const int j = 2 * J + dy;
         if (j < 0 || j >= Lyf) continue;
-        const T wyz = wz * (dy ? T(0.5) : T(1));
+        const float wyz = wz * (dy ? 0.5f : 1.f);
         for (int dx = -1; dx <= 1; ++dx) {
           const int i = 2 * I + dx;
           if (i < 0 || i >= Lxf) continue;
-          const T wgt = wyz * (dx ? T(0.5) : T(1));
+          const float wgt = wyz * (dx ? 0.5f : 1.f);
           const long f = i + (long)Lxf * (j + (long)Lyf * l);
-          a[0] += wgt * rf[3 * f];
-          a[1] += wgt * rf[3 * f + 1];
-          a[2] += wgt * rf[3 * f + 2];
+          a[0].add(wgt, rf[3 * f]);
+          a[1].add(wgt, rf[3 * f + 1]);
+          a[2].add(wgt, rf[3 * f + 2]);
         }
       }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long d = 3 * node + c;
-      const T bv = maskc[d] ? T(0) : a[c];
+      const T bv = maskc[d] ? T(0) : a[c].value();
       bc[d] = bv;
       if (vc != nullptr) vc[d] = omega * dinvc[d] * bv;
     }
@@ -213,36 +346,34 @@ __global__ void k_vc_prolong(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc,
     const int i = node % Lxf, j = (node / Lxf) % Lyf, l = node / ((long)Lxf * Lyf);
     const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1, K0 = l >> 1,
               K1 = (l + 1) >> 1;
-    T a0 = 0, a1 = 0, a2 = 0;
+    Acc<T> a0, a1, a2;
     for (int K = K0; K <= K1; ++K) {
-      const T wz = (K0 == K1) ? T(1) : T(0.5);
+      const float wz = (K0 == K1) ? 1.f : 0.5f;
       for (int J = J0; J <= J1; ++J) {
-        const T wyz = wz * ((J0 == J1) ? T(1) : T(0.5));
+        const float wyz = wz * ((J0 == J1) ? 1.f : 0.5f);
         for (int I = I0; I <= I1; ++I) {
-          const T wgt = wyz * ((I0 == I1) ? T(1) : T(0.5));
+          const float wgt = wyz * ((I0 == I1) ? 1.f : 0.5f);
           const long c = I + (long)Lxc * (J + (long)Lyc * K);
-          a0 += wgt * zc[3 * c];
-          a1 += wgt * zc[3 * c + 1];
-          a2 += wgt * zc[3 * c + 2];
+          a0.add(wgt, zc[3 * c]);
+          a1.add(wgt, zc[3 * c + 1]);
+          a2.add(wgt, zc[3 * c + 2]);
         }
       }
     }
-    if (!maskf[3 * node]) v[3 * node] += a0;
-    if (!maskf[3 * node + 1]) v[3 * node + 1] += a1;
-    if (!maskf[3 * node + 2]) v[3 * node + 2] += a2;
+    if (!maskf[3 * node]) v[3 * node] += a0.value();
+    if (!maskf[3 * node + 1]) v[3 * node + 1] += a1.value();
+    if (!maskf[3 * node + 2]) v[3 * node + 2] += a2.value();
   }
 }
 
 // Post-smoothing: z = v + omega D^-1 (b - A v).
 template <typename T>
-__global__ void k_vc_post(LevelView<T> V, T omega, const T* __restrict__ b, const T* __restrict__ v,
-                          T* __restrict__ z) {
-  ROW_LOOP(V.nn) {
-    NODE_IJL(V);
-    const T y = stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return v[3 * nb + c]; });
+__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_vc_post(LevelView<T> V, T omega, const T* __restrict__ b,
+                                                         const T* __restrict__ v, T* __restrict__ z) {
+  for_each_row(V, [&](long nb, int c) { return ld_nc(v + 3 * nb + c); }, [&](long node, int r, T y) {
     const long d = 3 * node + r;
     z[d] = v[d] + omega * V.dinv[d] * (b[d] - y);
-  }
+  });
 }
 
 // Coarsest level: z = A_c^{-1} b in FP64, one warp per row.
@@ -297,16 +428,14 @@ __global__ void k_cg_prep(int nn, const uint8_t* __restrict__ mask, double* __re
 // convergence test (||f||^2 from part_ff) and sets the loop condition;
 // mode 2 (after the loop): the last block stores the true residual.
 template <typename T>
-__global__ void k_cg_residual(LevelView<double> V, const double* __restrict__ f,
-                              const double* __restrict__ u, double* __restrict__ rv,
-                              T* __restrict__ b0, const op_t<T>* __restrict__ dinv0, T omega,
-                              T* __restrict__ v0, double* part, const double* part_ff, int mode,
-                              DevState* __restrict__ ds, unsigned* cnt,
-                              cudaGraphConditionalHandle hc, int use_cond) {
+__global__ void __launch_bounds__(kTileThreads)
+    k_cg_residual(LevelView<double> V, const double* __restrict__ f, const double* __restrict__ u,
+                  double* __restrict__ rv, T* __restrict__ b0, const op_t<T>* __restrict__ dinv0,
+                  T omega, T* __restrict__ v0, double* part, const double* part_ff, int np_ff,
+                  int mode, DevState* __restrict__ ds, unsigned* cnt, cudaGraphConditionalHandle hc,
+                  int use_cond) {
   double s = 0.0;
-  ROW_LOOP(V.nn) {
-    NODE_IJL(V);
-    const double y = stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return u[3 * nb + c]; });
+  for_each_row(V, [&](long nb, int c) { return ld_nc(u + 3 * nb + c); }, [&](long node, int r, double y) {
     const long d = 3 * node + r;
     const double rd = f[d] - y;
     rv[d] = rd;
@@ -316,13 +445,13 @@ __global__ void k_cg_residual(LevelView<double> V, const double* __restrict__ f,
       if (dinv0 != nullptr) v0[d] = omega * dinv0[d] * bt;  // no smoothing level when L = 1
     }
     s += rd * rd;
-  }
+  });
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   if (!last_block(cnt)) return;
   const double rr = reduce_parts(part, gridDim.x);
   if (mode == 1) {
-    const double ff = reduce_parts(part_ff, gridDim.x);
+    const double ff = reduce_parts(part_ff, np_ff);
     if (threadIdx.x == 0) {
       ds->ff = ff;
       ds->rr = rr;
@@ -331,7 +460,7 @@ __global__ void k_cg_residual(LevelView<double> V, const double* __restrict__ f,
       if (!(rr == rr)) ds->status = TOSOLVE_EBREAKDOWN;
       const bool conv = (rr <= ds->tol2 * ff) || ff == 0.0;
       ds->converged = conv;
-      set_cond(hc, use_cond, (conv || ds->status || ds->maxit <= 0) ? 0u : 1u);
+      set_cond(hc, use_cond, (conv || ds->status || ds->tile_status || ds->maxit <= 0) ? 0u : 1u);
     }
   } else if (threadIdx.x == 0) {
     ds->rr_true = rr;
@@ -381,16 +510,15 @@ __global__ void k_cg_dir(int nn, const T* __restrict__ z, double* __restrict__ p
 
 // q = K p (FP64) and partial p^T q; the last block forms alpha = rz / p^T q
 // (a non-positive or non-finite value is a breakdown).
-__global__ void k_cg_apply(LevelView<double> V, const double* __restrict__ p, double* __restrict__ q,
-                           double* part, DevState* __restrict__ ds, unsigned* cnt) {
+__global__ void __launch_bounds__(kTileThreads)
+    k_cg_apply(LevelView<double> V, const double* __restrict__ p, double* __restrict__ q, double* part,
+               DevState* __restrict__ ds, unsigned* cnt) {
   double s = 0.0;
-  ROW_LOOP(V.nn) {
-    NODE_IJL(V);
-    const double y = stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return p[3 * nb + c]; });
+  for_each_row(V, [&](long nb, int c) { return ld_nc(p + 3 * nb + c); }, [&](long node, int r, double y) {
     const long d = 3 * node + r;
     q[d] = y;
     s += p[d] * y;
-  }
+  });
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   if (!last_block(cnt)) return;
@@ -436,18 +564,17 @@ __global__ void k_cg_update(int nn, double* __restrict__ u, double* __restrict__
     if (!(rr == rr)) ds->status = TOSOLVE_EBREAKDOWN;
     const bool conv = rr <= ds->tol2 * ds->ff;
     ds->converged = conv;
-    set_cond(hc, use_cond, (conv || ds->status || ds->iter >= ds->maxit) ? 0u : 1u);
+    set_cond(hc, use_cond, (conv || ds->status || ds->tile_status || ds->iter >= ds->maxit) ? 0u : 1u);
     *cnt = 0u;
   }
 }
 
 // Diagnostic: y = A x in the level's stored precision, FP64 in and out.
 template <typename T>
-__global__ void k_apply_diag(LevelView<T> V, const double* __restrict__ x, double* __restrict__ y) {
-  ROW_LOOP(V.nn) {
-    NODE_IJL(V);
-    y[3 * node + r] = (double)stencil_row(V, node, i, j, l, r, [&](long nb, int c) { return (T)x[3 * nb + c]; });
-  }
+__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_apply_diag(LevelView<T> V, const double* __restrict__ x,
+                                                            double* __restrict__ y) {
+  for_each_row(V, [&](long nb, int c) { return (T)ld_nc(x + 3 * nb + c); },
+               [&](long node, int r, T v) { y[3 * node + r] = (double)v; });
 }
 
 template <typename A, typename B>
@@ -457,6 +584,17 @@ __global__ void k_cast(size_t n, const A* __restrict__ a, B* __restrict__ b) {
 }
 
 inline int grid_nodes(long nn) { return parts_for(nn); }
+
+// Grid of a tile kernel over level L: persistent blocks, at most as many as
+// are resident at once (and at most kMaxPart, the partial-sum capacity).
+template <typename T>
+int tile_grid(const Level& L) {
+  const long nt = ((long)L.nn + kTN - 1) / kTN;
+  long g = (long)tile_blocks_per_sm<T>() * L.sms;
+  if (g > nt) g = nt;
+  if (g > kMaxPart) g = kMaxPart;
+  return g < 1 ? 1 : (int)g;
+}
 
 template <typename T>
 const op_t<T>* dinv_of(const Level& L);
@@ -490,7 +628,8 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
     }
   }
   if (!use_tc)
-    k_vc_pre<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(V, (const T*)F.b, (const T*)F.v, (T*)F.r);
+    k_vc_pre<T><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(V, (const T*)F.b, (const T*)F.v,
+                                                                       (T*)F.r);
   k_vc_restrict<T><<<grid_nodes(C.nn), kRowThreads, 0, st>>>(
       F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, C.mask, (const T*)F.r, (T*)C.b,
       c_coarsest ? nullptr : dinv_of<T>(C), omega, c_coarsest ? nullptr : (T*)C.v);
@@ -505,8 +644,8 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
       return;
     }
   }
-  k_vc_post<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(V, omega, (const T*)F.b, (const T*)F.v,
-                                                         (T*)F.z);
+  k_vc_post<T><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(V, omega, (const T*)F.b,
+                                                                        (const T*)F.v, (T*)F.z);
 }
 
 }  // namespace
@@ -550,9 +689,9 @@ void launch_cg_residual(int vt, const Level& L0, double omega, const double* f, 
                         double* r, int mode, double* part, const double* part_ff, int np,
                         DevState* ds, unsigned* cnt, cudaGraphConditionalHandle hc, int use_cond,
                         cudaStream_t st) {
-  VT_DISPATCH(vt, (k_cg_residual<T><<<np, kRowThreads, 0, st>>>(
+  VT_DISPATCH(vt, (k_cg_residual<T><<<tile_grid<double>(L0), kTileThreads, tile_smem<double>(), st>>>(
                       view<double>(L0), f, u, r, (T*)L0.b, dinv_of<T>(L0), (T)omega, (T*)L0.v,
-                      part, part_ff, mode, ds, cnt, hc, use_cond)));
+                      part, part_ff, np, mode, ds, cnt, hc, use_cond)));
 }
 
 void launch_cg_dots_rz(int vt, const Level& L0, const double* r, const double* q, double* part_rz,
@@ -568,7 +707,9 @@ void launch_cg_dir(int vt, const Level& L0, double* p, int np, const DevState* d
 
 void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np, DevState* ds,
                      unsigned* cnt, cudaStream_t st) {
-  k_cg_apply<<<np, kRowThreads, 0, st>>>(view<double>(L0), p, q, part, ds, cnt);
+  (void)np;
+  k_cg_apply<<<tile_grid<double>(L0), kTileThreads, tile_smem<double>(), st>>>(view<double>(L0), p, q,
+                                                                              part, ds, cnt);
 }
 
 void launch_cg_update(int vt, const Level& L0, double omega, double* u, double* r, const double* p,
@@ -580,7 +721,30 @@ void launch_cg_update(int vt, const Level& L0, double omega, double* u, double* 
 }
 
 void launch_apply_diag(int vt, const Level& L, const double* x, double* y, cudaStream_t st) {
-  VT_DISPATCH(vt, (k_apply_diag<T><<<grid_nodes(L.nn), kRowThreads, 0, st>>>(view<T>(L), x, y)));
+  VT_DISPATCH(vt, (k_apply_diag<T><<<tile_grid<T>(L), kTileThreads, tile_smem<T>(), st>>>(view<T>(L), x,
+                                                                                          y)));
+}
+
+template <typename T>
+cudaError_t allow_tile_smem() {
+  const int b = (int)tile_smem<T>();
+  const int b64 = (int)tile_smem<double>();
+  cudaError_t e = cudaFuncSetAttribute(k_vc_pre<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_vc_post<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_residual<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b64);
+  return e;
+}
+
+cudaError_t configure_tile_kernels() {
+  cudaError_t e = allow_tile_smem<double>();
+  if (e == cudaSuccess) e = allow_tile_smem<float>();
+  if (e == cudaSuccess) e = allow_tile_smem<dfloat>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tile_smem<double>());
+  return e;
 }
 
 void launch_cast(bool to_fp64, size_t n, const void* a, void* b, bool src_fp64, cudaStream_t st) {

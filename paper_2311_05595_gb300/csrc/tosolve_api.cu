@@ -142,8 +142,8 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     v.s32 = fp32 && !coarsest && !(tf32 && l == 0);  // TF32: level 0 runs on tensor cores
     const size_t tsz = (fp32 && !x2) ? 4 : 8;
     B += v.ndof;  // mask
-    if (v.s64) B += 243 * v.nn * 8 + v.ndof * 8;
-    if (v.s32) B += 243 * v.nn * 4 + v.ndof * 4;
+    if (v.s64) B += op_len(v.nn) * 8 + v.ndof * 8;
+    if (v.s32) B += op_len(v.nn) * 4 + v.ndof * 4;
     B += 4 * v.ndof * tsz;  // b, v, r, z
     const size_t ke = (size_t)v.ex * v.ey * v.ez * kSym * 8;
     if (ke > keB) keB = ke;
@@ -373,8 +373,16 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
     L.op64 = !fp32 || l == P.L - 1;
     CKC(dalloc(h, &L.mask, v.ndof));
     CKC(cudaMemcpy(L.mask, mask.data(), v.ndof, cudaMemcpyHostToDevice));
-    if (v.s64) { CKC(dalloc(h, &L.S64, 243 * v.nn)); CKC(dalloc(h, &L.dinv64, v.ndof)); }
-    if (v.s32) { CKC(dalloc(h, &L.S32, 243 * v.nn)); CKC(dalloc(h, &L.dinv32, v.ndof)); }
+    if (v.s64) {  // padding coefficients of the last tile stay zero
+      CKC(dalloc(h, &L.S64, op_len(v.nn)));
+      CKC(cudaMemset(L.S64, 0, op_len(v.nn) * sizeof(double)));
+      CKC(dalloc(h, &L.dinv64, v.ndof));
+    }
+    if (v.s32) {
+      CKC(dalloc(h, &L.S32, op_len(v.nn)));
+      CKC(cudaMemset(L.S32, 0, op_len(v.nn) * sizeof(float)));
+      CKC(dalloc(h, &L.dinv32, v.ndof));
+    }
     if (tf32 && l == 0) CKC(dalloc(h, &L.dinv32, v.ndof));
     const size_t tsz = vt_of(h) == kVtF32 ? 4 : 8;
     void** vecs[4] = {&L.b, &L.v, &L.r, &L.z};
@@ -498,6 +506,15 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
   CKC(dalloc(h, &h->ds, 1));
   CKC(cudaMemset(h->ds, 0, sizeof(DevState)));
   if (h->tc.on) h->tc.err = &h->ds->tc_status;
+  {
+    int sms = 1;
+    CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+    for (int l = 0; l < P.L; ++l) {
+      h->lv[l].err = &h->ds->tile_status;
+      h->lv[l].sms = sms;
+    }
+    CKC(configure_tile_kernels());
+  }
   CKC(cudaMallocHost((void**)&h->hs, sizeof(DevState)));
   std::memset(h->hs, 0, sizeof(DevState));
   h->np = parts_for(h->lv[0].nn);
@@ -559,7 +576,7 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
     launch_elem_direct(true, C, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, cst);
     launch_assemble(true, C, h->Ke, C.S64, C.dinv64, cst);
     if (C.S32) {
-      launch_to_fp32((size_t)243 * C.nn, C.S64, C.S32, cst);
+      launch_to_fp32(op_len(C.nn), C.S64, C.S32, cst);
       launch_to_fp32((size_t)C.ndof, C.dinv64, C.dinv32, cst);
     }
   }
@@ -573,7 +590,7 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
     if (l == 0) {
       launch_elem_direct(true, Lv, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, st);
       launch_assemble(true, Lv, h->Ke, Lv.S64, Lv.dinv64, st);
-      if (Lv.S32) launch_to_fp32((size_t)243 * Lv.nn, Lv.S64, Lv.S32, st);
+      if (Lv.S32) launch_to_fp32(op_len(Lv.nn), Lv.S64, Lv.S32, st);
       if (Lv.dinv32) launch_to_fp32((size_t)Lv.ndof, Lv.dinv64, Lv.dinv32, st);
       if (h->tc.on) launch_weights_elem(Lv, n, h->w, h->Dx, h->Dy, h->w32, st);
     } else {
@@ -584,7 +601,7 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
       else
         launch_assemble(false, Lv, h->Ke, Lv.S32, Lv.dinv32, st);
       if (op64 && Lv.S32) {  // FP32X2: FP32 copy of the FP64-formed operator
-        launch_to_fp32((size_t)243 * Lv.nn, Lv.S64, Lv.S32, st);
+        launch_to_fp32(op_len(Lv.nn), Lv.S64, Lv.S32, st);
         launch_to_fp32((size_t)Lv.ndof, Lv.dinv64, Lv.dinv32, st);
       }
     }
@@ -674,8 +691,9 @@ tosolve_status tosolve_solve(tosolve_t h, const double* f_dev, int nrhs, double*
       }
       const DevState& S = *h->hs;
       used += S.iter;
-      if (S.tc_status) {
-        h->err = "a tensor-core tile did not complete within its bounded wait";
+      if (S.tc_status || S.tile_status) {  // sticky: the handle stays unusable
+        h->err = S.tc_status ? "a tensor-core tile did not complete within its bounded wait"
+                             : "an operator tile copy did not complete within its bounded wait";
         return finish(TOSOLVE_ECUDA);
       }
       if (S.ff == 0.0) {  // f = 0: the solution is u = 0
@@ -981,9 +999,9 @@ tosolve_status tosolve_batch_solve(tosolve_batch_t b, double rtol, int maxit, to
       int used = S.iter;
       double rel = 0.0;
       tosolve_status st = TOSOLVE_OK;
-      if (S.tc_status) {
+      if (S.tc_status || S.tile_status) {
         st = TOSOLVE_ECUDA;
-        h->err = "a tensor-core tile did not complete within its bounded wait";
+        h->err = "a tensor-core or operator tile copy did not complete within its bounded wait";
       } else if (S.ff == 0.0) {  // f = 0: the solution is u = 0
         e = cudaMemsetAsync(ur, 0, nd * 8, b->st);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -1015,7 +1033,7 @@ tosolve_status tosolve_batch_solve(tosolve_batch_t b, double rtol, int maxit, to
   if (e != cudaSuccess) return cuda_fail(e);
   if (result == TOSOLVE_ENOTCONV) g_err = "a load case reached maxit before the tolerance";
   else if (result == TOSOLVE_EBREAKDOWN) g_err = "breakdown in a load case (PCG or coarse Cholesky)";
-  else if (result == TOSOLVE_ECUDA) g_err = "a tensor-core tile did not complete within its bounded wait";
+  else if (result == TOSOLVE_ECUDA) g_err = "a tensor-core or operator tile copy did not complete within its bounded wait";
   return result;
 }
 
