@@ -39,10 +39,10 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DFMA rate at ~1.96 GHz) x 2 flop x 152 SMs x 2070 MHz max SM clock.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # DRAM traffic per launch of the dominant kernel from an ncu capture of the
-# same workload (profiles/k_cg_apply_*.md: the FP64 stencil apply of the CG,
-# the same stencil code as the diagnostic apply timed below), valid while the
-# kernel source is unchanged (keyed by the source hash).
-NCU_TRAFFIC = {("k_apply_diag<double>", "610c2dd64d8c"): 60.308224e6 + 0.126976e6}
+# same workload (ncu --set full of the diagnostic FP64 apply timed below, the
+# same tile kernel body as the CG's q = K p), valid while the kernel source
+# is unchanged (keyed by the source hash).
+NCU_TRAFFIC = {("k_apply_diag<double>", "d09ac84b551d"): 60.347904e6 + 0.040704e6}
 
 
 def problem():
@@ -248,9 +248,11 @@ def run_gpu(args):
 
     sampler = ClockSampler(local)
     out = {}
-    mixed_labels = ("fp32", "tf32", "fp32x2")
-    solvers = {"fp32": make(T.PREC_FP32), "tf32": make(T.PREC_TF32),
-               "fp32x2": make(T.PREC_FP32X2), "fp64": make(T.PREC_FP64)}
+    precs = {"fp32": T.PREC_FP32, "tf32": T.PREC_TF32, "fp32x2": T.PREC_FP32X2, "fp64": T.PREC_FP64}
+    mixed_labels = tuple(v for v in args.variants.split(",") if v != "fp64")
+    if not mixed_labels or any(v not in precs for v in mixed_labels):
+        raise SystemExit("--variants: a comma list of fp32, tf32, fp32x2 (fp64 always runs)")
+    solvers = {lab: make(precs[lab]) for lab in mixed_labels + ("fp64",)}
     sampler.start()
     for label in mixed_labels + ("fp64",):
         s = solvers[label]
@@ -530,6 +532,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="fp32,tf32,fp32x2",
+                    help="mixed-precision variants timed beside FP64 (comma list)")
     ap.add_argument("--workload", default="cantilever", choices=["cantilever", "batch64"],
                     help="batch64: the 64-instance batched solve (its own JSON line)")
     ap.add_argument("--host-loop", action="store_true",
