@@ -525,6 +525,116 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+SERVE = dict(name="serve256_q1_density_64x32x32_to_384x192x192_poisson200", designs=256,
+             rate=200.0, requests=2000, seed=77, rtol=1e-8, budget_gib=200)
+
+
+def serve_designs(count: int, seed: int):
+    """Live designs of the serving workload: density size s * (64, 32, 32)
+    with ln s ~ N(ln 2, 0.5) truncated to [1, 6]; n in {1, 2, 3} uniform;
+    displacement mesh = density / n rounded to a multiple of 16, 32 or 64
+    (x; half that in y, z) so that it coarsens to a small dense coarsest
+    level; Q1 (degree 2
+    is not built yet); cantilever supports and line load; a smooth initial
+    design field."""
+    import numpy as np
+
+    import workloads
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        while True:
+            sc = float(np.exp(rng.normal(np.log(2.0), 0.5)))
+            if 1.0 <= sc <= 6.0:
+                break
+        n = int(rng.integers(1, 4))
+        raw = 64 * sc / n
+        mult = 16 if raw <= 128 else (32 if raw <= 256 else 64)  # coarsest level stays small
+        nx = max(16, int(round(raw / mult)) * mult)
+        p = workloads.cantilever(nx, nx // 2, nx // 2, n_mr=n, rmin=0.0, density="smooth",
+                                 seed=int(rng.integers(1 << 31)))
+        p.name = f"design{k}_{nx}x{nx // 2}x{nx // 2}_n{n}"
+        out.append(p)
+    return out
+
+
+def run_serve(args):
+    """Serving: Poisson arrivals (mean 200/s) of SLP-iteration requests over
+    256 live designs.  Each request drifts its design's x by U(-0.05, 0.05)
+    (clipped to [0.001, 1]) and is solved warm-started from the design's
+    previous displacements, with compliance and gradient.  The same arrival
+    sequence runs with the FP32X2 preconditioner and with FP64."""
+    import numpy as np
+
+    from paper_2311_05595_gb300 import tosolve as T
+
+    probs = serve_designs(args.designs, SERVE["seed"])
+    nreq = args.requests
+    rng = np.random.default_rng(SERVE["seed"] + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / SERVE["rate"], size=nreq))
+    which = rng.integers(0, len(probs), size=nreq)
+    drift_seed = SERVE["seed"] + 2
+    budget = SERVE["budget_gib"] << 30
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": SERVE["name"], "designs": len(probs), "requests": nreq,
+                       "offered_rate_per_s": SERVE["rate"], "slots": args.slots,
+                       "hbm_budget_gib": SERVE["budget_gib"], "rtol": SERVE["rtol"],
+                       "degree": "Q1 only (degree 2 not built)",
+                       "free_dofs_range": [min(p.nfree for p in probs),
+                                           max(p.nfree for p in probs)]}}
+    sampler = ClockSampler(0)
+    sampler.start()
+    for label, prec in (("fp32x2", T.PREC_FP32X2), ("fp64", T.PREC_FP64)):
+        srv = T.tosolve_server_create(args.slots, budget, SERVE["rtol"], 2000)
+        try:
+            for k, p in enumerate(probs):
+                d = T.make_desc(p.nx, p.ny, p.nz, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin, nu=p.nu,
+                                penal=p.penal, precision=prec, max_rhs=p.nrhs)
+                T.tosolve_server_add_design(srv, k, d, p.mask, np.asarray(p.f), p.nrhs)
+            xs = [np.array(p.x) for p in probs]
+            drng = np.random.default_rng(drift_seed)
+            dofs = {}
+            results = []
+            t0 = time.perf_counter()
+            nxt = 0
+            while len(results) < nreq:
+                now = time.perf_counter() - t0
+                while nxt < nreq and arrivals[nxt] <= now:
+                    k = int(which[nxt])
+                    xs[k] = np.clip(xs[k] + drng.uniform(-0.05, 0.05, size=xs[k].shape), 0.001, 1.0)
+                    rid = T.tosolve_server_submit(srv, k, xs[k])
+                    dofs[rid] = probs[k].nfree * probs[k].nrhs
+                    nxt += 1
+                wait = 50 if nxt >= nreq else max(0, int(1000 * (arrivals[nxt] - now)))
+                results += T.tosolve_server_poll(srv, 256, min(wait, 50))
+            info = T.tosolve_server_stats(srv)
+        finally:
+            T.tosolve_server_destroy(srv)
+        bad = [r for r in results if r.status != T.OK]
+        t_first = min(r.t_submit for r in results)
+        t_last = max(r.t_end for r in results)
+        lat = np.array([r.t_end - r.t_submit for r in results]) * 1e3
+        svc = np.array([r.t_end - r.t_start for r in results]) * 1e3
+        warm = np.array([r.iterations for r in results if not r.cold])
+        total_dofs = sum(dofs[r.request] for r in results)
+        line[label] = {
+            "solved_dofs_per_s": total_dofs / (t_last - t_first),
+            "achieved_rate_per_s": len(results) / (t_last - t_first),
+            "offered_rate_per_s": nreq / float(arrivals[-1]),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "service_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
+            "warm_iterations_median": float(np.median(warm)) if warm.size else None,
+            "failed": len(bad), "builds": info.builds, "evictions": info.evictions,
+        }
+    line["clocks"] = sampler.stop()
+    line["value"] = line["fp32x2"]["solved_dofs_per_s"]
+    line["fp64_value"] = line["fp64"]["solved_dofs_per_s"]
+    line["speedup_vs_fp64"] = line["value"] / line["fp64_value"]
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -534,8 +644,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="fp32,tf32,fp32x2",
                     help="mixed-precision variants timed beside FP64 (comma list)")
-    ap.add_argument("--workload", default="cantilever", choices=["cantilever", "batch64"],
-                    help="batch64: the 64-instance batched solve (its own JSON line)")
+    ap.add_argument("--workload", default="cantilever", choices=["cantilever", "batch64", "serve"],
+                    help="batch64: the 64-instance batched solve; serve: the serving loop "
+                         "(each its own JSON line)")
+    ap.add_argument("--designs", type=int, default=SERVE["designs"])
+    ap.add_argument("--requests", type=int, default=SERVE["requests"])
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the PCG loop from the host (same kernels, no CUDA graph): "
                          "ncu cannot profile kernels inside a graph with a conditional node")
@@ -548,6 +662,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

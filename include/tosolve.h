@@ -198,6 +198,80 @@ tosolve_status tosolve_batch_solve(tosolve_batch_t b, double rtol, int maxit, to
 /* Frees the batch (not the handles).  NULL is accepted. */
 void tosolve_batch_destroy(tosolve_batch_t b);
 
+/* ---- Serving: SLP-iteration requests of many designs ------------------- */
+
+/* The serving runtime keeps many independent designs (mesh, supports, load
+ * cases) and runs their SLP iterations as requests arrive.  One request =
+ * new design variables x -> tosolve_set_densities, a solve warm-started
+ * from the design's previous displacements (Sec. 7.2.1), compliance and
+ * gradient.  Requests of one design run in submission order, one at a time;
+ * requests of different designs run concurrently on `slots` worker threads,
+ * each on its design's own CUDA stream, so their kernels overlap on the
+ * GPU.  A design's handle, buffers and warm start stay on the device while
+ * the budget allows; when a request needs room, idle designs are evicted
+ * least recently used first (their displacements move to the host and come
+ * back as the warm start).  Results carry timestamps for latency figures. */
+typedef struct tosolve_server_s* tosolve_server_t;
+
+typedef struct {
+  int slots;          /* requests running at once, 1..64                     */
+  size_t hbm_budget;  /* device bytes for resident designs (handle + x, f,   */
+                      /* u, gradient buffers; tosolve_footprint + those)     */
+  double rtol;        /* per request, as tosolve_solve                      */
+  int maxit;          /* per request, 1..100000                             */
+} tosolve_server_desc;
+
+typedef struct {
+  long long request;   /* id from tosolve_server_submit                      */
+  int design;
+  int status;          /* tosolve_status of the request; ENOMEM if the       */
+                       /* design alone exceeds hbm_budget                    */
+  int iterations;      /* PCG iterations over all load cases                 */
+  int cold;            /* 1 if the design was (re)built for this request     */
+  double compliance;   /* sum over load cases of f^T u                       */
+  double rel_residual; /* worst true relative residual                       */
+  double t_submit, t_start, t_end;  /* seconds on the server's clock          */
+} tosolve_request_result;
+
+typedef struct {
+  int designs, resident_designs, pending, running;
+  size_t resident_bytes;
+  long long builds, evictions;
+  double now;          /* the server's clock, seconds                        */
+} tosolve_server_info;
+
+/* Starts the worker threads on the current device.  Errors: EINVAL, ENOMEM. */
+tosolve_status tosolve_server_create(const tosolve_server_desc* desc, tosolve_server_t* out);
+
+/* Registers design `design` (any int, unique): its descriptor, DOF mask
+ * (host, as tosolve_create) and nrhs load cases f_host (nrhs x ndof, host),
+ * all copied.  No device memory is used until its first request.
+ * Errors: EINVAL (invalid descriptor, duplicate id). */
+tosolve_status tosolve_server_add_design(tosolve_server_t s, int design, const tosolve_desc* desc,
+                                         const uint8_t* mask_host, const double* f_host, int nrhs);
+
+/* Queues one SLP iteration of `design` with design variables x_host (host,
+ * copied now).  If dcdx_host is not NULL, dc/dx (summed over load cases) is
+ * written there when the request completes; the caller keeps it valid until
+ * the request's result has been polled.  request may be NULL.
+ * Errors: EINVAL (unknown design, NULL x, server stopping). */
+tosolve_status tosolve_server_submit(tosolve_server_t s, int design, const double* x_host,
+                                     double* dcdx_host, long long* request);
+
+/* Moves up to max finished results to out (completion order), waiting up
+ * to timeout_ms for the first one.  Returns how many were written. */
+int tosolve_server_poll(tosolve_server_t s, tosolve_request_result* out, int max, int timeout_ms);
+
+/* Occupancy and counters.  Errors: EINVAL. */
+tosolve_status tosolve_server_stats(tosolve_server_t s, tosolve_server_info* info);
+
+/* Message of the last failed server call on this thread. */
+const char* tosolve_server_last_error(void);
+
+/* Drops queued requests, waits for the running ones, frees every design.
+ * NULL is accepted. */
+void tosolve_server_destroy(tosolve_server_t s);
+
 /* ---- Compliance without device allocation ----------------------------- */
 
 /* Most load cases handled per call, and the size in bytes of the one fixed

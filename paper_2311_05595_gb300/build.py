@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtosolve.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["k_setup.cu", "k_solve.cu", "k_grad.cu", "k_tc.cu", "k_noalloc.cu", "tosolve_api.cu"]
+UNITS = ["k_setup.cu", "k_solve.cu", "k_grad.cu", "k_tc.cu", "k_noalloc.cu", "tosolve_api.cu", "tosolve_server.cpp"]
 
 
 def _nvcc() -> str:

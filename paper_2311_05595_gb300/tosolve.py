@@ -39,6 +39,24 @@ class tosolve_info(C.Structure):
     ]
 
 
+class tosolve_server_desc(C.Structure):
+    _fields_ = [("slots", C.c_int), ("hbm_budget", C.c_size_t), ("rtol", C.c_double),
+                ("maxit", C.c_int)]
+
+
+class tosolve_request_result(C.Structure):
+    _fields_ = [("request", C.c_longlong), ("design", C.c_int), ("status", C.c_int),
+                ("iterations", C.c_int), ("cold", C.c_int), ("compliance", C.c_double),
+                ("rel_residual", C.c_double), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_end", C.c_double)]
+
+
+class tosolve_server_info(C.Structure):
+    _fields_ = [("designs", C.c_int), ("resident_designs", C.c_int), ("pending", C.c_int),
+                ("running", C.c_int), ("resident_bytes", C.c_size_t), ("builds", C.c_longlong),
+                ("evictions", C.c_longlong), ("now", C.c_double)]
+
+
 class TosolveError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -69,6 +87,13 @@ def _load():
         "tosolve_batch_solve": ([vp, d, i, vp], i),
         "tosolve_batch_destroy": ([vp], None),
         "tosolve_compliance_noalloc": ([vp, vp, vp, sz, i, vp, vp], i),
+        "tosolve_server_create": ([P(tosolve_server_desc), P(vp)], i),
+        "tosolve_server_add_design": ([vp, i, P(tosolve_desc), vp, vp, i], i),
+        "tosolve_server_submit": ([vp, i, vp, vp, P(C.c_longlong)], i),
+        "tosolve_server_poll": ([vp, P(tosolve_request_result), i, i], i),
+        "tosolve_server_stats": ([vp, P(tosolve_server_info)], i),
+        "tosolve_server_last_error": ([], C.c_char_p),
+        "tosolve_server_destroy": ([vp], None),
         "tosolve_last_error": ([vp], C.c_char_p),
         "tosolve_destroy": ([vp], None),
     }
@@ -182,6 +207,53 @@ def tosolve_batch_solve(b, rtol: float, maxit: int, count: int, raise_on_error=T
 
 def tosolve_batch_destroy(b) -> None:
     _lib.tosolve_batch_destroy(b)
+
+
+def _check_server(status: int, what: str):
+    if status != OK:
+        msg = _lib.tosolve_server_last_error()
+        raise TosolveError(status, f"{what}: {msg.decode() if msg else ''}")
+
+
+def tosolve_server_create(slots: int, hbm_budget: int, rtol: float, maxit: int) -> int:
+    d = tosolve_server_desc(slots, hbm_budget, rtol, maxit)
+    s = C.c_void_p(0)
+    _check_server(_lib.tosolve_server_create(C.byref(d), C.byref(s)), "tosolve_server_create")
+    return s.value
+
+
+def tosolve_server_add_design(s, design: int, desc: tosolve_desc, mask: np.ndarray, f: np.ndarray,
+                              nrhs: int) -> None:
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check_server(_lib.tosolve_server_add_design(s, design, C.byref(desc), mask.ctypes.data,
+                                                 f.ctypes.data, nrhs), "tosolve_server_add_design")
+
+
+def tosolve_server_submit(s, design: int, x: np.ndarray, dcdx: np.ndarray | None = None) -> int:
+    """x is copied at once; dcdx (if given) is written when the request
+    completes and must stay alive until its result has been polled."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    rid = C.c_longlong(0)
+    _check_server(_lib.tosolve_server_submit(s, design, x.ctypes.data, _ptr(dcdx), C.byref(rid)),
+                  "tosolve_server_submit")
+    return rid.value
+
+
+def tosolve_server_poll(s, max_results: int = 64, timeout_ms: int = 100) -> list:
+    buf = (tosolve_request_result * max_results)()
+    n = _lib.tosolve_server_poll(s, buf, max_results, timeout_ms)
+    return [buf[k] for k in range(n)]
+
+
+def tosolve_server_stats(s) -> tosolve_server_info:
+    info = tosolve_server_info()
+    _check_server(_lib.tosolve_server_stats(s, C.byref(info)), "tosolve_server_stats")
+    return info
+
+
+def tosolve_server_destroy(s) -> None:
+    _lib.tosolve_server_destroy(s)
 
 
 NOALLOC_MAX_RHS = 16
