@@ -198,6 +198,13 @@ tosolve_status tosolve_batch_solve(tosolve_batch_t b, double rtol, int maxit, to
 /* Frees the batch (not the handles).  NULL is accepted. */
 void tosolve_batch_destroy(tosolve_batch_t b);
 
+/* Device memory of handles and servers comes from one stream-ordered pool
+ * per device.  Memory freed by tosolve_destroy (or a server eviction) stays
+ * reserved in that pool for the next build; this returns the unused part
+ * above keep_bytes to the driver (current device; synchronises it).
+ * Errors: ECUDA. */
+tosolve_status tosolve_trim_pool(size_t keep_bytes);
+
 /* ---- Serving: SLP-iteration requests of many designs ------------------- */
 
 /* The serving runtime keeps many independent designs (mesh, supports, load

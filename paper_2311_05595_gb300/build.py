@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtosolve.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["k_setup.cu", "k_solve.cu", "k_grad.cu", "k_tc.cu", "k_noalloc.cu", "tosolve_api.cu", "tosolve_server.cpp"]
+UNITS = ["k_setup.cu", "k_solve.cu", "k_grad.cu", "k_tc.cu", "k_noalloc.cu", "k_q2.cu", "tosolve_api.cu", "tosolve_server.cpp", "pool.cpp"]
 
 
 def _nvcc() -> str:
@@ -30,6 +30,7 @@ def _nvcc() -> str:
 def _sources():
     srcs = [os.path.join(CSRC, u) for u in UNITS]
     deps = srcs + [os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "dfloat.cuh"),
+                   os.path.join(CSRC, "pool.h"),
                    os.path.join(os.path.dirname(HERE), "include", "tosolve.h")]
     return srcs, deps
 
@@ -60,7 +61,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(err)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

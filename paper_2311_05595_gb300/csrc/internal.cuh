@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <string>
 
 #include "../../include/tosolve.h"
@@ -33,6 +34,22 @@ constexpr int kNB = 32;        // block size of the coarse Cholesky
 constexpr int kTile = 32;      // output tile of the coarse inverse product
 constexpr int kMaxCoarse = 4096;  // largest coarse system (DOFs)
 constexpr int kTN = 32;        // nodes per operator tile
+constexpr size_t kSlabBytes = size_t(1) << 30;  // element-matrix scratch of the refresh
+
+// Scratch for the element matrices of the levels refreshed slab by slab
+// (ex x ey x ez elements per level, up to kSym doubles each): whole levels
+// when they fit in kSlabBytes, else slabs of at least two element layers.
+inline size_t slab_scratch_bytes(const int* ex, const int* ey, const int* ez, int nlev) {
+  size_t b = 0;
+  for (int l = 0; l < nlev; ++l) {
+    const size_t layer = (size_t)ex[l] * ey[l] * kSym * 8;
+    const size_t full = layer * ez[l];
+    size_t need = kSlabBytes > 2 * layer ? kSlabBytes : 2 * layer;
+    if (need > full) need = full;
+    if (need > b) b = need;
+  }
+  return b;
+}
 
 // Position of coefficient e (= o*9 + 3r + c) of node in a level operator.
 __host__ __device__ inline size_t op_idx(long node, int e) {
@@ -72,6 +89,11 @@ struct Level {
   bool op64;        // operator stored in FP64 for the V-cycle
   int sms = 1;      // SMs of the device (grid of the tile kernels)
   int* err = nullptr;  // set when an operator tile copy times out
+  int k = 1;        // Lagrange degree of the level's elements
+  // degree 2: the operator as element matrices (81 x 81 each, full)
+  double* K64 = nullptr;
+  float* K32 = nullptr;
+  void* Y = nullptr;  // per-element results of an apply (shared scratch)
   uint8_t* mask = nullptr;
   double* S64 = nullptr;   // FP64 stencil (level 0 always; others when op64)
   float* S32 = nullptr;    // FP32 stencil (FP32 preconditioner levels)
@@ -115,12 +137,21 @@ void launch_filter_init(int Dx, int Dy, int Dz, int noff, const int4* off, const
 void launch_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,
                        const double* invom, const double* x, double Emin, double dE,
                        double penal, double* rho, double* w, cudaStream_t st);
-void launch_elem_direct(bool fp64, const Level& L, int n, const double* w, int Dx, int Dy,
-                        const double* tabsym, void* Ke, cudaStream_t st);
-void launch_elem_moments(bool fp64, const Level& L, const double* w, int Dx, int Dy,
+// Element matrices of the element z-layers [ze0, ze1), written from the
+// start of Ke (a slab of the level).
+void launch_elem_direct(bool fp64, const Level& L, int ze0, int ze1, int n, const double* w, int Dx,
+                        int Dy, const double* tabsym, void* Ke, cudaStream_t st);
+void launch_elem_moments(bool fp64, const Level& L, int ze0, int ze1, const double* w, int Dx, int Dy,
                          const double* cmom, void* Mscr, void* Ke, cudaStream_t st);
-void launch_assemble(bool fp64, const Level& L, const void* Ke, void* S, void* dinv,
-                     cudaStream_t st);
+// Stencil rows of the node z-layers [l0, l1) from a slab of element matrices
+// that starts at element layer ze0.
+void launch_assemble(bool fp64, const Level& L, int l0, int l1, int ze0, const void* Ke, void* S,
+                     void* dinv, cudaStream_t st);
+// Splits a level into z-slabs whose element matrices (elem_bytes each) fit
+// in scratch_bytes: fn(l0, l1, ze0, ze1) for node layers [l0, l1) and the
+// element layers [ze0, ze1) they touch (consecutive slabs share one layer).
+void for_each_slab(const Level& L, size_t scratch_bytes, size_t elem_bytes,
+                   const std::function<void(int, int, int, int)>& fn);
 void launch_to_fp32(size_t n, const double* a, float* b, cudaStream_t st);
 void launch_coarse_dense(const Level& L, double* A, cudaStream_t st);
 cudaError_t launch_coarse_factor(int n, double* A, double* W, double* Dblk, double* X,
@@ -174,6 +205,26 @@ void launch_apply_diag(int vt, const Level& L, const double* x, double* y, cudaS
 // Lets the stencil tile kernels use their shared-memory ring (once per
 // process and device, before the first launch).
 cudaError_t configure_tile_kernels();
+
+// ---- launchers (k_q2.cu): Lagrange degree 2 in element form ---------------
+constexpr int kD2 = 81;       // DOFs of a triquadratic element
+constexpr int kDD2 = 81 * 81;
+constexpr int kNM2 = 125;     // moments of a degree-2 element matrix
+void launch_q2_subcell_table(int n, double nu, double h, double* tab, cudaStream_t st);
+void launch_q2_moment_basis(double nu, double* cmom, cudaStream_t st);
+void launch_q2_elem(const Level& L, int n, const double* w, int Dx, int Dy, const double* tab,
+                    double* Ke, cudaStream_t st);
+void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, const double* cmom,
+                           double* Mscr, double* Ke, cudaStream_t st);
+void launch_q2_dinv(bool fp64, const Level& L, const double* Ke, void* dinv, cudaStream_t st);
+void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t st);
+// out = f(A_l v) in vector type vt: mode 0 b - Av, 1 v + omega D^-1 (b - Av),
+// 2 Av (identity rows at fixed DOFs).  Ke is FP64 for kVtF64, else FP32.
+void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b, const void* v,
+                  const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st);
+void launch_q2_energy_grad(const Level& L0, int n, const double* u, const double* tab,
+                           const double* rho, double penal, double dE, int Dx, int Dy, bool first,
+                           double* g, int sms, cudaStream_t st);
 // FP64 vector <-> multigrid vector of arithmetic vt.
 void launch_vec_in(int vt, size_t n, const double* a, void* b, cudaStream_t st);
 void launch_vec_out(int vt, size_t n, const void* a, double* b, cudaStream_t st);
@@ -232,14 +283,18 @@ struct tosolve_s {
   double* fwgt = nullptr;
   double* gtmp = nullptr;
   // element tables
-  double* tab64 = nullptr;     // m x 24 x 24
+  double* tab64 = nullptr;     // m x 24 x 24 (degree 2: m x 81 x 81)
   double* tabsym64 = nullptr;  // m x 300
-  double* cmom64 = nullptr;    // 27 x 300
+  double* cmom64 = nullptr;    // 27 x 300 (degree 2: 125 x 81 x 81)
+  double* Yq = nullptr;        // degree 2: per-element apply results (E0 x 81)
+  double* Mq = nullptr;        // degree 2: moments of the finer coarse levels
+  double* Mqc = nullptr;       // degree 2: moments of the coarsest level
   float* KT32 = nullptr;       // m x 24 x 24 FP32 (tensor-core operand)
   float* w32 = nullptr;        // E x m element-major FP32 weights
   float* Ye = nullptr;         // E x 24 element results of the tensor-core apply
   tos::TcOp tc;
   void* Ke = nullptr;
+  size_t ke_bytes = 0;     // size of Ke (slab_scratch_bytes)
   double* Kec = nullptr;  // element matrices of the coarsest level (second stream)
   double* Mom = nullptr;   // 27 moments per element, finer coarse levels
   double* Momc = nullptr;  // 27 moments per element, coarsest level

@@ -1,0 +1,495 @@
+// Triquadratic (Lagrange degree 2) elements: every step of the path for
+// k = 2, in element form.
+//
+// The level operators of a degree-2 hierarchy are kept as element matrices
+// K^(e) (81 x 81, full, FP64 and optionally an FP32 copy) instead of node
+// stencils: a degree-2 node couples to up to 125 lattice nodes, and on this
+// GPU the element form reads fewer bytes per apply than that stencil would.
+// An apply is two kernels: Y_e = K^(e) u_e for every element (u gathered
+// with the fixed DOFs zeroed), then a node gather y_n = sum of the Y_e of the
+// elements containing n (fixed order: deterministic), with identity rows at
+// fixed DOFs.  The gather also finishes the multigrid smoothing steps.
+//
+// Element conventions: reference [-1,1]^3, K = 3 equispaced nodes per axis,
+// local node a = ax + 3 (ay + 3 az) at lattice node (2 ex + ax, 2 ey + ay,
+// 2 ez + az), DOF 3a + c.  Sec. 2.1 (Lagrange elements), Sec. 3.3
+// (Eq. matrixK_mr: K^(e) = sum_i w_i K^(e_i) over the element's n^3
+// subcells), Sec. 2.3 (linear interpolation between node lattices).
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace tos {
+namespace {
+
+constexpr int kK = 3;               // nodes per axis
+constexpr int kNE = kK * kK * kK;   // 27 nodes
+constexpr int kD = 3 * kNE;         // 81 DOFs
+constexpr int kDD = kD * kD;        // 6561
+constexpr int kP = 2 * kK - 1;      // 5 monomial powers per axis
+constexpr int kNM = kP * kP * kP;   // 125 moments
+
+// 1D Lagrange basis on the nodes -1, 0, 1: value and derivative of basis j.
+__host__ __device__ __forceinline__ double lag(int j, double x) {
+  return j == 0 ? 0.5 * x * (x - 1.0) : (j == 1 ? 1.0 - x * x : 0.5 * x * (x + 1.0));
+}
+__host__ __device__ __forceinline__ double dlag(int j, double x) {
+  return j == 0 ? x - 0.5 : (j == 1 ? -2.0 * x : x + 0.5);
+}
+// Monomial coefficients (degree <= 2) of the basis (deriv = 0) or its
+// derivative (deriv = 1).
+__device__ __forceinline__ void lag_coef(int j, int deriv, double c[3]) {
+  if (!deriv) {
+    if (j == 0) { c[0] = 0.0; c[1] = -0.5; c[2] = 0.5; }
+    else if (j == 1) { c[0] = 1.0; c[1] = 0.0; c[2] = -1.0; }
+    else { c[0] = 0.0; c[1] = 0.5; c[2] = 0.5; }
+  } else {
+    if (j == 0) { c[0] = -0.5; c[1] = 1.0; c[2] = 0.0; }
+    else if (j == 1) { c[0] = 0.0; c[1] = -2.0; c[2] = 0.0; }
+    else { c[0] = 0.5; c[1] = 1.0; c[2] = 0.0; }
+  }
+}
+
+// K^(e_i) for the n^3 subcells of an element of edge h (E = 1), full 81 x 81:
+// 3-point Gauss-Legendre per axis in each subcell (exact: the integrand has
+// degree <= 4 per axis).  One block per subcell.
+__global__ void k_q2_subcell_table(int n, double nu, double h, double* __restrict__ tab) {
+  __shared__ double gr[27][kNE][3];  // physical gradients at the 27 points
+  const int sub = blockIdx.x;
+  const int sa = sub % n, sb = (sub / n) % n, sc = sub / (n * n);
+  const double half = 1.0 / n;
+  const double gp[3] = {-sqrt(0.6), 0.0, sqrt(0.6)};
+  const double gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+  const double s = 2.0 / h;
+  for (int t = threadIdx.x; t < 27 * kNE; t += blockDim.x) {
+    const int q = t / kNE, a = t % kNE;
+    const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
+    const double xi = -1.0 + (2 * sa + 1) * half + half * gp[qx];
+    const double eta = -1.0 + (2 * sb + 1) * half + half * gp[qy];
+    const double zeta = -1.0 + (2 * sc + 1) * half + half * gp[qz];
+    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+    gr[q][a][0] = s * dlag(ax, xi) * lag(ay, eta) * lag(az, zeta);
+    gr[q][a][1] = s * lag(ax, xi) * dlag(ay, eta) * lag(az, zeta);
+    gr[q][a][2] = s * lag(ax, xi) * lag(ay, eta) * dlag(az, zeta);
+  }
+  __syncthreads();
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = 1.0 / (2.0 * (1.0 + nu));
+  // dx = (h/2)^3 dxi, and the subcell maps onto xi with factor 1/n per axis
+  const double jac = half * half * half * (0.125 * h * h * h);
+  for (int t = threadIdx.x; t < kDD; t += blockDim.x) {
+    const int R = t / kD, C = t % kD;
+    const int a = R / 3, i = R % 3, b = C / 3, j = C % 3;
+    double acc = 0.0;
+    for (int q = 0; q < 27; ++q) {
+      const double wq = gw[q % 3] * gw[(q / 3) % 3] * gw[q / 9];
+      const double* ga = gr[q][a];
+      const double* gb = gr[q][b];
+      double v = lam * ga[i] * gb[j] + mu * ga[j] * gb[i];
+      if (i == j) v += mu * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
+      acc += wq * v;
+    }
+    tab[(size_t)sub * kDD + t] = jac * acc;
+  }
+}
+
+// Moment basis: the element-matrix integrand in reference coordinates is
+// sum_alpha C_alpha xi^alpha (alpha in {0..4}^3), so an element of edge h
+// with cellwise-constant weights w has K^(e) = (h/2) sum_alpha M_alpha
+// C_alpha, M_alpha = int_ref w(xi) xi^alpha dxi.  Thread per (alpha, entry).
+__global__ void k_q2_moment_basis(double nu, double* __restrict__ cmom) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)kNM * kDD) return;
+  const int alpha = (int)(t / kDD), e = (int)(t % kDD);
+  const int R = e / kD, C = e % kD;
+  const int al[3] = {alpha % kP, (alpha / kP) % kP, alpha / (kP * kP)};
+  const int a = R / 3, i = R % 3, b = C / 3, j = C % 3;
+  const int na[3] = {a % 3, (a / 3) % 3, a / 9};
+  const int nb[3] = {b % 3, (b / 3) % 3, b / 9};
+  auto T = [&](int p, int q) {  // coefficient of xi^alpha in d_p N_a * d_q N_b
+    double v = 1.0;
+    for (int ax = 0; ax < 3; ++ax) {
+      double u[3], w[3];
+      lag_coef(na[ax], p == ax, u);
+      lag_coef(nb[ax], q == ax, w);
+      double c = 0.0;
+      for (int r = 0; r < 3; ++r) {
+        const int s = al[ax] - r;
+        if (s >= 0 && s < 3) c += u[r] * w[s];
+      }
+      v *= c;
+    }
+    return v;
+  };
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = 1.0 / (2.0 * (1.0 + nu));
+  double v = lam * T(i, j) + mu * T(j, i);
+  if (i == j) v += mu * (T(0, 0) + T(1, 1) + T(2, 2));
+  cmom[t] = v;
+}
+
+// mu_p(a) = integral of xi^p over the a-th of N equal intervals of [-1, 1].
+__device__ __forceinline__ double mono_int(int p, int a, int N) {
+  const double t0 = -1.0 + 2.0 * a / N, t1 = -1.0 + 2.0 * (a + 1) / N;
+  double p0 = t0, p1 = t1;
+  for (int k = 0; k < p; ++k) { p0 *= t0; p1 *= t1; }
+  return (p1 - p0) / (p + 1);
+}
+
+// Moments M_alpha (125) of the weights over each element of a coarse
+// degree-2 level (N^3 density cells per element), separably: for each row of
+// cells along x the five sums sum_a w mu_p(a), then products with mu_q(b)
+// mu_r(c).  One block per element, threads over rows, fixed-order
+// reduction.
+__global__ void k_q2_moments(int ex, int ey, int N, const double* __restrict__ w, int Dx, int Dy,
+                             double* __restrict__ M) {
+  __shared__ double red[kNM];
+  const long e = blockIdx.x;
+  const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+  for (int q = threadIdx.x; q < kNM; q += blockDim.x) red[q] = 0.0;
+  __syncthreads();
+  // rows handled in a fixed order by a fixed thread; partial sums per thread
+  double acc[kNM];
+  for (int q = 0; q < kNM; ++q) acc[q] = 0.0;
+  for (long rr = threadIdx.x; rr < (long)N * N; rr += blockDim.x) {
+    const int b = rr % N, c = rr / N;
+    const long base = (N * exi) + (long)Dx * ((N * eyi + b) + (long)Dy * (N * ezi + c));
+    double sx[kP] = {0, 0, 0, 0, 0};
+    for (int a = 0; a < N; ++a) {
+      const double wv = w[base + a];
+      for (int p = 0; p < kP; ++p) sx[p] += wv * mono_int(p, a, N);
+    }
+    double my[kP], mz[kP];
+    for (int p = 0; p < kP; ++p) { my[p] = mono_int(p, b, N); mz[p] = mono_int(p, c, N); }
+    for (int q = 0; q < kNM; ++q) acc[q] += sx[q % kP] * my[(q / kP) % kP] * mz[q / (kP * kP)];
+  }
+  // fixed-order combination: thread t adds its partials in turn
+  for (int t = 0; t < (int)blockDim.x; ++t) {
+    if ((int)threadIdx.x == t)
+      for (int q = 0; q < kNM; ++q) red[q] += acc[q];
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < kNM; q += blockDim.x) M[e * kNM + q] = red[q];
+}
+
+// K^(e) = (h/2) sum_alpha M_alpha C_alpha, full 81 x 81, for kEB elements per
+// block (each C_alpha entry read once per block).
+constexpr int kEB = 8;
+template <typename T>
+__global__ void k_q2_moments_to_ke(long E, double h, const double* __restrict__ M,
+                                   const double* __restrict__ cmom, T* __restrict__ Ke) {
+  __shared__ double Ms[kEB][kNM];
+  const long e0 = blockIdx.x * (long)kEB;
+  const int ne = (int)min((long)kEB, E - e0);
+  for (int t = threadIdx.x; t < ne * kNM; t += blockDim.x) Ms[t / kNM][t % kNM] = M[e0 * kNM + t];
+  __syncthreads();
+  for (int ent = threadIdx.x; ent < kDD; ent += blockDim.x) {
+    double acc[kEB];
+#pragma unroll
+    for (int q = 0; q < kEB; ++q) acc[q] = 0.0;
+    for (int al = 0; al < kNM; ++al) {
+      const double c = cmom[(size_t)al * kDD + ent];
+#pragma unroll
+      for (int q = 0; q < kEB; ++q) acc[q] += Ms[q][al] * c;
+    }
+    for (int q = 0; q < ne; ++q) Ke[(e0 + q) * (size_t)kDD + ent] = (T)(0.5 * h * acc[q]);
+  }
+}
+
+// Level-0 element matrices: K^(e) = sum_i w_{e,i} K^(e_i) over the n^3
+// subcells (Eq. matrixK_mr), FP64.  Block per kEB elements.
+__global__ void k_q2_elem(int ex, int ey, long E, int n, const double* __restrict__ w, int Dx, int Dy,
+                          const double* __restrict__ tab, double* __restrict__ Ke) {
+  extern __shared__ double ws[];  // kEB * m
+  const int m = n * n * n;
+  const long e0 = blockIdx.x * (long)kEB;
+  const int ne = (int)min((long)kEB, E - e0);
+  for (int t = threadIdx.x; t < kEB * m; t += blockDim.x) {
+    const int q = t / m, s = t % m;
+    double v = 0.0;
+    if (q < ne) {
+      const long e = e0 + q;
+      const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+      const int a = s % n, b = (s / n) % n, c = s / (n * n);
+      v = w[(n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c))];
+    }
+    ws[t] = v;
+  }
+  __syncthreads();
+  for (int ent = threadIdx.x; ent < kDD; ent += blockDim.x) {
+    double acc[kEB];
+#pragma unroll
+    for (int q = 0; q < kEB; ++q) acc[q] = 0.0;
+    for (int s = 0; s < m; ++s) {
+      const double t = tab[(size_t)s * kDD + ent];
+#pragma unroll
+      for (int q = 0; q < kEB; ++q) acc[q] += ws[q * m + s] * t;
+    }
+    for (int q = 0; q < ne; ++q) Ke[(e0 + q) * (size_t)kDD + ent] = acc[q];
+  }
+}
+
+__device__ __forceinline__ long elem_node(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
+  return (2 * exi + a % 3) + (long)Lx * ((2 * eyi + (a / 3) % 3) + (long)Ly * (2 * ezi + a / 9));
+}
+
+template <typename T>
+struct Sum {
+  T s = T(0);
+  __device__ __forceinline__ void add(op_t<T> a, T x) { s += a * x; }
+  __device__ __forceinline__ T value() const { return s; }
+};
+template <>
+struct Sum<dfloat> {
+  Dot2 d;
+  __device__ __forceinline__ void add(float a, dfloat x) { d.add(a, x); }
+  __device__ __forceinline__ dfloat value() const { return d.value(); }
+};
+
+// Y_e = K^(e) u_e for every element; u_e gathered with the fixed DOFs set to
+// zero.  One block of 96 threads per element at a time (persistent), thread
+// a < 81 computes entry a; K^(e) is symmetric, so its column a (read
+// coalesced across the threads) is its row a.
+template <typename T>
+__global__ void __launch_bounds__(96) k_q2_apply(int ex, int ey, long E, int Lx, int Ly,
+                                                 const op_t<T>* __restrict__ Ke,
+                                                 const uint8_t* __restrict__ mask,
+                                                 const T* __restrict__ u, T* __restrict__ Y) {
+  __shared__ T ue[kD];
+  for (long e = blockIdx.x; e < E; e += gridDim.x) {
+    const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+    if (threadIdx.x < kD) {
+      const int a = threadIdx.x / 3, c = threadIdx.x % 3;
+      const long d = 3 * elem_node(exi, eyi, ezi, a, Lx, Ly) + c;
+      ue[threadIdx.x] = mask[d] ? T(0) : u[d];
+    }
+    __syncthreads();
+    if (threadIdx.x < kD) {
+      const op_t<T>* K = Ke + e * (size_t)kDD + threadIdx.x;
+      Sum<T> acc;
+#pragma unroll 9
+      for (int b = 0; b < kD; ++b) acc.add(K[(size_t)b * kD], ue[b]);
+      Y[e * kD + threadIdx.x] = acc.value();
+    }
+    __syncthreads();
+  }
+}
+
+// y_n = sum of Y_e over the elements containing node n (fixed order), then
+//   mode 0: out = b - y            (residual after the first smoothing)
+//   mode 1: out = v + omega D^-1 (b - y)   (post-smoothing)
+//   mode 2: out = y                (plain apply)
+// Fixed DOFs are identity rows: y = v there.
+template <typename T>
+__global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, const T* __restrict__ Y,
+                            const T* __restrict__ b, const T* __restrict__ v,
+                            const op_t<T>* __restrict__ dinv, const uint8_t* __restrict__ mask,
+                            T omega, int mode, T* __restrict__ out) {
+  const long nn = (long)Lx * Ly * Lz;
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
+       node += (long)gridDim.x * blockDim.x) {
+    const int i = node % Lx, j = (node / Lx) % Ly, l = node / ((long)Lx * Ly);
+    // elements along each axis containing this lattice coordinate
+    int e0[3], e1[3];
+    const int co[3] = {i, j, l}, ext[3] = {ex, ey, ez};
+    for (int ax = 0; ax < 3; ++ax) {
+      if (co[ax] & 1) { e0[ax] = e1[ax] = co[ax] >> 1; }
+      else { e0[ax] = max((co[ax] >> 1) - 1, 0); e1[ax] = min(co[ax] >> 1, ext[ax] - 1); }
+    }
+    T y[3] = {T(0), T(0), T(0)};
+    for (int ez_ = e0[2]; ez_ <= e1[2]; ++ez_)
+      for (int ey_ = e0[1]; ey_ <= e1[1]; ++ey_)
+        for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
+          const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
+          const int a = (i - 2 * ex_) + 3 * ((j - 2 * ey_) + 3 * (l - 2 * ez_));
+          const T* Ye = Y + e * kD + 3 * a;
+          y[0] += Ye[0];
+          y[1] += Ye[1];
+          y[2] += Ye[2];
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long d = 3 * node + c;
+      const T yc = mask[d] ? v[d] : y[c];
+      if (mode == 0) out[d] = b[d] - yc;
+      else if (mode == 1) out[d] = v[d] + omega * dinv[d] * (b[d] - yc);
+      else out[d] = yc;
+    }
+  }
+}
+
+// Inverse Jacobi diagonal: 1 / sum_e K^(e)_{3a+c, 3a+c}; fixed DOFs 1.
+template <typename T>
+__global__ void k_q2_dinv(int Lx, int Ly, int Lz, int ex, int ey, int ez, const double* __restrict__ Ke,
+                          const uint8_t* __restrict__ mask, T* __restrict__ dinv) {
+  const long nn = (long)Lx * Ly * Lz;
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
+       node += (long)gridDim.x * blockDim.x) {
+    const int i = node % Lx, j = (node / Lx) % Ly, l = node / ((long)Lx * Ly);
+    int e0[3], e1[3];
+    const int co[3] = {i, j, l}, ext[3] = {ex, ey, ez};
+    for (int ax = 0; ax < 3; ++ax) {
+      if (co[ax] & 1) { e0[ax] = e1[ax] = co[ax] >> 1; }
+      else { e0[ax] = max((co[ax] >> 1) - 1, 0); e1[ax] = min(co[ax] >> 1, ext[ax] - 1); }
+    }
+    double dg[3] = {0.0, 0.0, 0.0};
+    for (int ez_ = e0[2]; ez_ <= e1[2]; ++ez_)
+      for (int ey_ = e0[1]; ey_ <= e1[1]; ++ey_)
+        for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
+          const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
+          const int a = (i - 2 * ex_) + 3 * ((j - 2 * ey_) + 3 * (l - 2 * ez_));
+          for (int c = 0; c < 3; ++c) dg[c] += Ke[e * (size_t)kDD + (size_t)(3 * a + c) * kD + 3 * a + c];
+        }
+    for (int c = 0; c < 3; ++c) {
+      const long d = 3 * node + c;
+      dinv[d] = mask[d] ? T(1.0) : T(1.0 / dg[c]);
+    }
+  }
+}
+
+// Dense matrix of the coarsest level: elements of one parity class (no two
+// share a node) add their matrices; fixed rows and columns are identity.
+__global__ void k_q2_dense(int ex, int ey, int ez, int Lx, int Ly, int par, const double* __restrict__ Ke,
+                           const uint8_t* __restrict__ mask, long n, double* __restrict__ A) {
+  const int px = par & 1, py = (par >> 1) & 1, pz = par >> 2;
+  const int cx = (ex - px + 1) / 2, cy = (ey - py + 1) / 2, cz = (ez - pz + 1) / 2;
+  const long Ec = (long)cx * cy * cz;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < Ec * kDD;
+       t += (long)gridDim.x * blockDim.x) {
+    const long q = t / kDD;
+    const int ent = (int)(t % kDD);
+    const int exi = 2 * (int)(q % cx) + px, eyi = 2 * (int)((q / cx) % cy) + py,
+              ezi = 2 * (int)(q / ((long)cx * cy)) + pz;
+    const long e = exi + (long)ex * (eyi + (long)ey * ezi);
+    const int R = ent / kD, C = ent % kD;
+    const long dr = 3 * elem_node(exi, eyi, ezi, R / 3, Lx, Ly) + R % 3;
+    const long dc = 3 * elem_node(exi, eyi, ezi, C / 3, Lx, Ly) + C % 3;
+    if (mask[dr] || mask[dc]) continue;
+    A[dr * n + dc] += Ke[e * (size_t)kDD + ent];
+  }
+}
+
+__global__ void k_q2_dense_fixed(long n, const uint8_t* __restrict__ mask, double* __restrict__ A) {
+  for (long d = blockIdx.x * (long)blockDim.x + threadIdx.x; d < n; d += (long)gridDim.x * blockDim.x)
+    if (mask[d]) A[d * n + d] = 1.0;
+}
+
+// Sensitivities, Sec. 3.4: s_{e,i} = u_e^T K^(e_i) u_e for every (element,
+// subcell), dc/drho_i = -p rho_i^(p-1) (E0 - Emin) s (accumulated over load
+// cases unless first).  Block per element: u_e staged, warps over subcells,
+// lanes over rows.
+__global__ void k_q2_energy_grad(int ex, int ey, long E, int n, int Lx, int Ly,
+                                 const double* __restrict__ u, const double* __restrict__ tab,
+                                 const double* __restrict__ rho, double penal, double dE, int Dx,
+                                 int Dy, int first, double* __restrict__ g) {
+  __shared__ double ue[kD];
+  const int m = n * n * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (long e = blockIdx.x; e < E; e += gridDim.x) {
+    const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+    for (int t = threadIdx.x; t < kD; t += blockDim.x)
+      ue[t] = u[3 * elem_node(exi, eyi, ezi, t / 3, Lx, Ly) + t % 3];
+    __syncthreads();
+    for (int s = warp; s < m; s += nw) {
+      const double* K = tab + (size_t)s * kDD;
+      double acc = 0.0;
+      for (int R = lane; R < kD; R += 32) {
+        double y = 0.0;
+        for (int C = 0; C < kD; ++C) y += K[(size_t)R * kD + C] * ue[C];
+        acc += ue[R] * y;
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        const int a = s % n, b = (s / n) % n, c = s / (n * n);
+        const long cell = (n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c));
+        const double r = rho[cell];
+        const double gv = -penal * pow(r, penal - 1.0) * dE * acc;
+        g[cell] = first ? gv : g[cell] + gv;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+inline int grid_for2(long work, int cap = 65536) {
+  long g = (work + 255) / 256;
+  if (g < 1) g = 1;
+  return (int)(g < cap ? g : cap);
+}
+
+}  // namespace
+
+// ---- launchers -------------------------------------------------------------
+
+void launch_q2_subcell_table(int n, double nu, double h, double* tab, cudaStream_t st) {
+  k_q2_subcell_table<<<n * n * n, 256, 0, st>>>(n, nu, h, tab);
+}
+
+void launch_q2_moment_basis(double nu, double* cmom, cudaStream_t st) {
+  k_q2_moment_basis<<<(int)(((long)kNM * kDD + 255) / 256), 256, 0, st>>>(nu, cmom);
+}
+
+void launch_q2_elem(const Level& L, int n, const double* w, int Dx, int Dy, const double* tab,
+                    double* Ke, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * L.ez;
+  const size_t sm = (size_t)kEB * n * n * n * sizeof(double);
+  k_q2_elem<<<(int)((E + kEB - 1) / kEB), 256, sm, st>>>(L.ex, L.ey, E, n, w, Dx, Dy, tab, Ke);
+}
+
+void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, const double* cmom,
+                           double* Mscr, double* Ke, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * L.ez;
+  const int N = L.nsub;
+  k_q2_moments<<<(int)E, N * N >= 128 ? 128 : 32, 0, st>>>(L.ex, L.ey, N, w, Dx, Dy, Mscr);
+  k_q2_moments_to_ke<double><<<(int)((E + kEB - 1) / kEB), 256, 0, st>>>(E, L.h, Mscr, cmom, Ke);
+}
+
+void launch_q2_dinv(bool fp64, const Level& L, const double* Ke, void* dinv, cudaStream_t st) {
+  const int g = grid_for2(L.nn);
+  if (fp64)
+    k_q2_dinv<double><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (double*)dinv);
+  else
+    k_q2_dinv<float><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (float*)dinv);
+}
+
+void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t st) {
+  const long n = L.ndof;
+  for (int par = 0; par < 8; ++par)
+    k_q2_dense<<<grid_for2((long)L.ex * L.ey * L.ez * kDD / 8 + 1), 256, 0, st>>>(
+        L.ex, L.ey, L.ez, L.Lx, L.Ly, par, Ke, L.mask, n, A);
+  k_q2_dense_fixed<<<grid_for2(n), 256, 0, st>>>(n, L.mask, A);
+}
+
+// y = A_l v (element apply + gather) with the given mode; T is the vector
+// type (double, float, dfloat), the element matrices are op_t<T>.
+void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b, const void* v,
+                  const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * L.ez;
+  long ga = (long)sms * 16;
+  if (ga > E) ga = E;
+  if (ga < 1) ga = 1;
+  const int gg = grid_for2(L.nn);
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    k_q2_apply<T><<<(int)ga, 96, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
+                                          (const T*)v, (T*)Y);
+    k_q2_gather<T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
+                                       (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
+                                       (T*)out);
+  };
+  if (vt == kVtF64) run(double());
+  else if (vt == kVtF32) run(float());
+  else run(dfloat(0.f, 0.f));
+}
+
+void launch_q2_energy_grad(const Level& L0, int n, const double* u, const double* tab,
+                           const double* rho, double penal, double dE, int Dx, int Dy, bool first,
+                           double* g, int sms, cudaStream_t st) {
+  const long E = (long)L0.ex * L0.ey * L0.ez;
+  long gr = (long)sms * 8;
+  if (gr > E) gr = E;
+  k_q2_energy_grad<<<(int)gr, 256, 0, st>>>(L0.ex, L0.ey, E, n, L0.Lx, L0.Ly, u, tab, rho, penal, dE,
+                                            Dx, Dy, first ? 1 : 0, g);
+}
+
+}  // namespace tos

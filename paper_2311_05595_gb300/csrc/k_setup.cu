@@ -5,6 +5,9 @@
 // structure itself is built once).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <functional>
+
 #include "internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -152,19 +155,22 @@ __global__ void k_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* __res
 // upper triangle.  A block handles epb consecutive elements (their weights
 // staged in shared memory); consecutive threads write consecutive entries.
 // FP64 accumulation.
+// Elements of z-layers [ze0, ze0 + nlayers) (a slab); Ke is indexed from the
+// slab's first element.
 template <typename T>
-__global__ void k_elem_direct(int ex, int ey, int ez, int n, int epb, const double* __restrict__ w,
-                              int Dx, int Dy, const double* __restrict__ tabsym, T* __restrict__ Ke) {
+__global__ void k_elem_direct(int ex, int ey, int ze0, int nlayers, int n, int epb,
+                              const double* __restrict__ w, int Dx, int Dy,
+                              const double* __restrict__ tabsym, T* __restrict__ Ke) {
   extern __shared__ double ws[];  // epb * m
   const int m = n * n * n;
-  const long E = (long)ex * ey * ez;
+  const long E = (long)ex * ey * nlayers;
   const long e0 = (long)blockIdx.x * epb;
   for (int t = threadIdx.x; t < epb * m; t += blockDim.x) {
     const int q = t / m, s = t % m;
     const long e = e0 + q;
     double v = 0.0;
     if (e < E) {
-      const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+      const int exi = e % ex, eyi = (e / ex) % ey, ezi = ze0 + (int)(e / ((long)ex * ey));
       const int a = s % n, b = (s / n) % n, c = s / (n * n);
       v = w[(n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c))];
     }
@@ -224,15 +230,15 @@ __device__ __forceinline__ void fill_mu(int N, Acc* mu0, Acc* mu1, Acc* mu2) {
 
 // Moments of small elements (N <= 4): one thread per element.
 template <typename Acc>
-__global__ void k_moments_thread(int ex, int ey, int ez, int N, const double* __restrict__ w, int Dx,
-                                 int Dy, Acc* __restrict__ M) {
+__global__ void k_moments_thread(int ex, int ey, int ze0, int nlayers, int N,
+                                 const double* __restrict__ w, int Dx, int Dy, Acc* __restrict__ M) {
   __shared__ Acc mu[3][4];
   fill_mu<Acc>(N, mu[0], mu[1], mu[2]);
   __syncthreads();
-  const long E = (long)ex * ey * ez;
+  const long E = (long)ex * ey * nlayers;
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= E) return;
-  const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+  const int exi = e % ex, eyi = (e / ex) % ey, ezi = ze0 + (int)(e / ((long)ex * ey));
   Acc acc[27];
 #pragma unroll
   for (int q = 0; q < 27; ++q) acc[q] = 0;
@@ -248,12 +254,12 @@ __global__ void k_moments_thread(int ex, int ey, int ez, int N, const double* __
 // Moments of larger elements: one block per element, one thread per row of
 // cells, warp-shuffle then shared-memory reduction (fixed order).
 template <typename Acc>
-__global__ void k_moments_block(int ex, int ey, int ez, int N, const double* __restrict__ w, int Dx,
+__global__ void k_moments_block(int ex, int ey, int ze0, int N, const double* __restrict__ w, int Dx,
                                 int Dy, Acc* __restrict__ M) {
   __shared__ Acc mu[3][1024];
   __shared__ Acc red[32][27];
   const long e = blockIdx.x;
-  const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+  const int exi = e % ex, eyi = (e / ex) % ey, ezi = ze0 + (int)(e / ((long)ex * ey));
   const int tid = threadIdx.x;
   fill_mu<Acc>(N, mu[0], mu[1], mu[2]);
   __syncthreads();
@@ -313,14 +319,17 @@ __global__ void k_moments_to_ke(long E, double h, const Acc* __restrict__ M,
 // thread per (neighbour block o, node), node fastest, so each of its 9
 // stores is coalesced.  Fixed DOFs get identity rows and zero columns; the
 // centre block also writes the inverse diagonal.
+// Nodes of z-layers [l0, l1); Ke holds the elements of layers from ze0 on
+// (every element these nodes touch).
 template <typename T>
-__global__ void k_assemble(int ex, int ey, int ez, int Lx, int Ly, int Lz, const T* __restrict__ Ke,
-                           const uint8_t* __restrict__ mask, T* __restrict__ S, T* __restrict__ dinv) {
-  const long nn = (long)Lx * Ly * Lz;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < 27 * nn;
+__global__ void k_assemble(int ex, int ey, int ez, int Lx, int Ly, int Lz, int l0, int l1, int ze0,
+                           const T* __restrict__ Ke, const uint8_t* __restrict__ mask,
+                           T* __restrict__ S, T* __restrict__ dinv) {
+  const long nsl = (long)Lx * Ly * (l1 - l0);
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < 27 * nsl;
        t += (long)gridDim.x * blockDim.x) {
-    const int o = (int)(t / nn);
-    const long node = t % nn;
+    const int o = (int)(t / nsl);
+    const long node = t % nsl + (long)Lx * Ly * l0;
     const int i = node % Lx, j = (node / Lx) % Ly, l = node / ((long)Lx * Ly);
     const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
     const int ii = i + dx, jj = j + dy, ll = l + dz;
@@ -335,7 +344,7 @@ __global__ void k_assemble(int ex, int ey, int ez, int Lx, int Ly, int Lz, const
       for (int ez_ = z0; ez_ <= z1; ++ez_)
         for (int ey_ = y0; ey_ <= y1; ++ey_)
           for (int ex_ = x0; ex_ <= x1; ++ex_) {
-            const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
+            const long e = ex_ + (long)ex * (ey_ + (long)ey * (ez_ - ze0));
             const int a = (i - ex_) + 2 * ((j - ey_) + 2 * (l - ez_));
             const int b = (ii - ex_) + 2 * ((jj - ey_) + 2 * (ll - ez_));
             const T* base = Ke + e * kSym;
@@ -628,9 +637,9 @@ void launch_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* off, const 
                                                              Emin, dE, penal, rho, w);
 }
 
-void launch_elem_direct(bool fp64, const Level& L, int n, const double* w, int Dx, int Dy,
-                        const double* tabsym, void* Ke, cudaStream_t st) {
-  const long E = (long)L.ex * L.ey * L.ez;
+void launch_elem_direct(bool fp64, const Level& L, int ze0, int ze1, int n, const double* w, int Dx,
+                        int Dy, const double* tabsym, void* Ke, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * (ze1 - ze0);
   const int m = n * n * n;
   int epb = 4096 / m;
   if (epb > 32) epb = 32;
@@ -638,22 +647,25 @@ void launch_elem_direct(bool fp64, const Level& L, int n, const double* w, int D
   const long g = (E + epb - 1) / epb;
   const size_t sm = (size_t)epb * m * sizeof(double);
   if (fp64)
-    k_elem_direct<double><<<g, 256, sm, st>>>(L.ex, L.ey, L.ez, n, epb, w, Dx, Dy, tabsym, (double*)Ke);
+    k_elem_direct<double><<<g, 256, sm, st>>>(L.ex, L.ey, ze0, ze1 - ze0, n, epb, w, Dx, Dy, tabsym,
+                                              (double*)Ke);
   else
-    k_elem_direct<float><<<g, 256, sm, st>>>(L.ex, L.ey, L.ez, n, epb, w, Dx, Dy, tabsym, (float*)Ke);
+    k_elem_direct<float><<<g, 256, sm, st>>>(L.ex, L.ey, ze0, ze1 - ze0, n, epb, w, Dx, Dy, tabsym,
+                                             (float*)Ke);
 }
 
-void launch_elem_moments(bool fp64, const Level& L, const double* w, int Dx, int Dy,
+void launch_elem_moments(bool fp64, const Level& L, int ze0, int ze1, const double* w, int Dx, int Dy,
                          const double* cmom, void* Mscr, void* Ke, cudaStream_t st) {
-  const long E = (long)L.ex * L.ey * L.ez;
+  const long E = (long)L.ex * L.ey * (ze1 - ze0);
   const int N = L.nsub;
   const long gk = (E + 31) / 32;
   if (fp64) {
     double* M = (double*)Mscr;
     if (N <= 4)
-      k_moments_thread<double><<<(E + 127) / 128, 128, 0, st>>>(L.ex, L.ey, L.ez, N, w, Dx, Dy, M);
+      k_moments_thread<double><<<(E + 127) / 128, 128, 0, st>>>(L.ex, L.ey, ze0, ze1 - ze0, N, w, Dx,
+                                                                Dy, M);
     else
-      k_moments_block<double><<<E, N * N >= 256 ? 256 : 64, 0, st>>>(L.ex, L.ey, L.ez, N, w, Dx, Dy, M);
+      k_moments_block<double><<<E, N * N >= 256 ? 256 : 64, 0, st>>>(L.ex, L.ey, ze0, N, w, Dx, Dy, M);
     const size_t sm = (size_t)(27 * kSym + 32 * 27) * sizeof(double);
     static bool attr = false;
     if (!attr) {
@@ -665,9 +677,10 @@ void launch_elem_moments(bool fp64, const Level& L, const double* w, int Dx, int
   } else {
     float* M = (float*)Mscr;
     if (N <= 4)
-      k_moments_thread<float><<<(E + 127) / 128, 128, 0, st>>>(L.ex, L.ey, L.ez, N, w, Dx, Dy, M);
+      k_moments_thread<float><<<(E + 127) / 128, 128, 0, st>>>(L.ex, L.ey, ze0, ze1 - ze0, N, w, Dx,
+                                                               Dy, M);
     else
-      k_moments_block<float><<<E, N * N >= 256 ? 256 : 64, 0, st>>>(L.ex, L.ey, L.ez, N, w, Dx, Dy, M);
+      k_moments_block<float><<<E, N * N >= 256 ? 256 : 64, 0, st>>>(L.ex, L.ey, ze0, N, w, Dx, Dy, M);
     const size_t sm = (size_t)(27 * kSym + 32 * 27) * sizeof(float);
     static bool attr = false;
     if (!attr) {
@@ -679,15 +692,30 @@ void launch_elem_moments(bool fp64, const Level& L, const double* w, int Dx, int
   }
 }
 
-void launch_assemble(bool fp64, const Level& L, const void* Ke, void* S, void* dinv,
-                     cudaStream_t st) {
-  const int g = grid_for((long)L.nn * 27, 128, 65536);
+void launch_assemble(bool fp64, const Level& L, int l0, int l1, int ze0, const void* Ke, void* S,
+                     void* dinv, cudaStream_t st) {
+  const int g = grid_for((long)L.Lx * L.Ly * (l1 - l0) * 27, 128, 65536);
   if (fp64)
-    k_assemble<double><<<g, 128, 0, st>>>(L.ex, L.ey, L.ez, L.Lx, L.Ly, L.Lz, (const double*)Ke,
-                                          L.mask, (double*)S, (double*)dinv);
+    k_assemble<double><<<g, 128, 0, st>>>(L.ex, L.ey, L.ez, L.Lx, L.Ly, L.Lz, l0, l1, ze0,
+                                          (const double*)Ke, L.mask, (double*)S, (double*)dinv);
   else
-    k_assemble<float><<<g, 128, 0, st>>>(L.ex, L.ey, L.ez, L.Lx, L.Ly, L.Lz, (const float*)Ke,
-                                         L.mask, (float*)S, (float*)dinv);
+    k_assemble<float><<<g, 128, 0, st>>>(L.ex, L.ey, L.ez, L.Lx, L.Ly, L.Lz, l0, l1, ze0,
+                                         (const float*)Ke, L.mask, (float*)S, (float*)dinv);
+}
+
+void for_each_slab(const Level& L, size_t scratch_bytes, size_t elem_bytes,
+                   const std::function<void(int, int, int, int)>& fn) {
+  const size_t layer = (size_t)L.ex * L.ey * elem_bytes;
+  int C = L.Lz;  // node layers per slab
+  if ((size_t)L.ez * layer > scratch_bytes) {
+    const size_t fit = scratch_bytes / layer;  // element layers that fit
+    C = fit >= 2 ? (int)(fit - 1) : 1;
+  }
+  for (int l0 = 0; l0 < L.Lz; l0 += C) {
+    const int l1 = std::min(l0 + C, L.Lz);
+    const int ze0 = std::max(l0 - 1, 0), ze1 = std::min(l1, L.ez);
+    fn(l0, l1, ze0, ze1);
+  }
 }
 
 void launch_to_fp32(size_t n, const double* a, float* b, cudaStream_t st) {

@@ -534,6 +534,66 @@ __global__ void __launch_bounds__(kTileThreads)
   }
 }
 
+// The same two CG steps when the operator was applied by another kernel
+// (element-form levels): y holds K u (residual) or K p (= q, apply).
+template <typename T>
+__global__ void k_cg_residual_y(int nn, const double* __restrict__ f, double* __restrict__ yr,
+                                T* __restrict__ b0, const op_t<T>* __restrict__ dinv0, T omega,
+                                T* __restrict__ v0, double* part, const double* part_ff, int np_ff,
+                                int mode, DevState* __restrict__ ds, unsigned* cnt,
+                                cudaGraphConditionalHandle hc, int use_cond) {
+  double s = 0.0;
+  DOF_LOOP(3L * nn) {
+    const double rd = f[d] - yr[d];
+    yr[d] = rd;
+    if (mode == 1) {
+      const T bt = (T)rd;
+      b0[d] = bt;
+      if (dinv0 != nullptr) v0[d] = omega * dinv0[d] * bt;
+    }
+    s += rd * rd;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!last_block(cnt)) return;
+  const double rr = reduce_parts(part, gridDim.x);
+  if (mode == 1) {
+    const double ff = reduce_parts(part_ff, np_ff);
+    if (threadIdx.x == 0) {
+      ds->ff = ff;
+      ds->rr = rr;
+      ds->iter = 0;
+      ds->status = ds->coarse_status ? (int)TOSOLVE_EBREAKDOWN : 0;
+      if (!(rr == rr)) ds->status = TOSOLVE_EBREAKDOWN;
+      const bool conv = (rr <= ds->tol2 * ff) || ff == 0.0;
+      ds->converged = conv;
+      set_cond(hc, use_cond, (conv || ds->status || ds->tile_status || ds->maxit <= 0) ? 0u : 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    ds->rr_true = rr;
+  }
+  if (threadIdx.x == 0) *cnt = 0u;
+}
+
+__global__ void k_cg_apply_y(int nn, const double* __restrict__ p, const double* __restrict__ q,
+                             double* part, DevState* __restrict__ ds, unsigned* cnt) {
+  double s = 0.0;
+  DOF_LOOP(3L * nn) s += p[d] * q[d];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!last_block(cnt)) return;
+  const double pq = reduce_parts(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    const double rz = ds->rz_next;
+    const double alpha = rz / pq;
+    const bool ok = (pq > 0.0) && (alpha == alpha) && (fabs(alpha) < 1e300);
+    ds->alpha = ok ? alpha : 0.0;
+    ds->rz = rz;
+    if (!ok) ds->status = TOSOLVE_EBREAKDOWN;
+    *cnt = 0u;
+  }
+}
+
 // u += alpha p, r -= alpha q, b0 = (T) r, v0 = omega D0^-1 b0, partial
 // ||r||^2; the last block runs the convergence test and sets the loop
 // condition (stop on convergence, breakdown or maxit).
@@ -606,6 +666,15 @@ template <>
 const float* dinv_of<dfloat>(const Level& L) { return L.dinv32; }
 
 template <typename T>
+constexpr int vt_code() {
+  return std::is_same<T, double>::value ? kVtF64 : (std::is_same<T, float>::value ? kVtF32 : kVtDF);
+}
+template <typename T>
+const void* elem_op(const Level& L) {
+  return std::is_same<T, double>::value ? (const void*)L.K64 : (const void*)L.K32;
+}
+
+template <typename T>
 void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp& tc,
                 cudaStream_t st) {
   Level& F = lv[l];
@@ -627,7 +696,10 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
                        (float*)F.r, st);
     }
   }
-  if (!use_tc)
+  if (F.k == 2)
+    launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, 0, F.r,
+                 F.sms, st);
+  else if (!use_tc)
     k_vc_pre<T><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(V, (const T*)F.b, (const T*)F.v,
                                                                        (T*)F.r);
   k_vc_restrict<T><<<grid_nodes(C.nn), kRowThreads, 0, st>>>(
@@ -643,6 +715,11 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
                        (float*)F.z, st);
       return;
     }
+  }
+  if (F.k == 2) {
+    launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, 1, F.z,
+                 F.sms, st);
+    return;
   }
   k_vc_post<T><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(V, omega, (const T*)F.b,
                                                                         (const T*)F.v, (T*)F.z);
@@ -689,6 +766,13 @@ void launch_cg_residual(int vt, const Level& L0, double omega, const double* f, 
                         double* r, int mode, double* part, const double* part_ff, int np,
                         DevState* ds, unsigned* cnt, cudaGraphConditionalHandle hc, int use_cond,
                         cudaStream_t st) {
+  if (L0.k == 2) {  // r = K u by elements, then the residual step
+    launch_q2_op(kVtF64, L0, L0.K64, L0.Y, nullptr, u, nullptr, 0.0, 2, r, L0.sms, st);
+    VT_DISPATCH(vt, (k_cg_residual_y<T><<<np, kRowThreads, 0, st>>>(
+                        L0.nn, f, r, (T*)L0.b, dinv_of<T>(L0), (T)omega, (T*)L0.v, part, part_ff, np,
+                        mode, ds, cnt, hc, use_cond)));
+    return;
+  }
   VT_DISPATCH(vt, (k_cg_residual<T><<<tile_grid<double>(L0), kTileThreads, tile_smem<double>(), st>>>(
                       view<double>(L0), f, u, r, (T*)L0.b, dinv_of<T>(L0), (T)omega, (T*)L0.v,
                       part, part_ff, np, mode, ds, cnt, hc, use_cond)));
@@ -707,7 +791,11 @@ void launch_cg_dir(int vt, const Level& L0, double* p, int np, const DevState* d
 
 void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np, DevState* ds,
                      unsigned* cnt, cudaStream_t st) {
-  (void)np;
+  if (L0.k == 2) {
+    launch_q2_op(kVtF64, L0, L0.K64, L0.Y, nullptr, p, nullptr, 0.0, 2, q, L0.sms, st);
+    k_cg_apply_y<<<np, kRowThreads, 0, st>>>(L0.nn, p, q, part, ds, cnt);
+    return;
+  }
   k_cg_apply<<<tile_grid<double>(L0), kTileThreads, tile_smem<double>(), st>>>(view<double>(L0), p, q,
                                                                               part, ds, cnt);
 }
@@ -721,6 +809,19 @@ void launch_cg_update(int vt, const Level& L0, double omega, double* u, double* 
 }
 
 void launch_apply_diag(int vt, const Level& L, const double* x, double* y, cudaStream_t st) {
+  if (L.k == 2) {
+    if (vt == kVtF64) {  // FP64 in and out: no staging
+      launch_q2_op(kVtF64, L, L.K64, L.Y, nullptr, x, nullptr, 0.0, 2, y, L.sms, st);
+      return;
+    }
+    // through the level's preconditioner vectors, whose type is vt (the
+    // caller checks that vt is the handle's preconditioner arithmetic)
+    const size_t nd = L.ndof;
+    launch_vec_in(vt, nd, x, L.v, st);
+    launch_q2_op(vt, L, L.K32, L.Y, nullptr, L.v, nullptr, 0.0, 2, L.r, L.sms, st);
+    launch_vec_out(vt, nd, L.r, y, st);
+    return;
+  }
   VT_DISPATCH(vt, (k_apply_diag<T><<<tile_grid<T>(L), kTileThreads, tile_smem<T>(), st>>>(view<T>(L), x,
                                                                                           y)));
 }

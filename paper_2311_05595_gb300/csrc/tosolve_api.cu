@@ -1,6 +1,7 @@
 // C ABI of the solver (declared in include/tosolve.h): validation, memory
 // plan, the per-design refresh, the graph-captured PCG loop and the
 // gradient.  Every device step is one of the kernels in k_*.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -9,6 +10,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "pool.h"
 
 using namespace tos;
 
@@ -67,7 +69,8 @@ bool divisible(const tosolve_desc& d, int levels) {
 
 long coarse_dofs(const tosolve_desc& d, int levels) {
   const int s = 1 << (levels - 1);
-  return 3L * (d.nx / s + 1) * (d.ny / s + 1) * (d.nz / s + 1);
+  const long k = d.degree;
+  return 3L * (k * (d.nx / s) + 1) * (k * (d.ny / s) + 1) * (k * (d.nz / s) + 1);
 }
 
 int count_offsets(int n, double rmin) {
@@ -89,7 +92,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   tosolve_desc d = *dp;
   if (d.nx < 1 || d.ny < 1 || d.nz < 1) { *why = "nx, ny, nz must be >= 1"; return TOSOLVE_EINVAL; }
   if ((long)d.nx * d.ny * d.nz > (1L << 28)) { *why = "mesh too large"; return TOSOLVE_EINVAL; }
-  if (d.degree != 1) { *why = "only Lagrange degree 1 is built"; return TOSOLVE_EINVAL; }
+  if (d.degree != 1 && d.degree != 2) { *why = "Lagrange degree must be 1 or 2"; return TOSOLVE_EINVAL; }
   if (d.n_mr < 1 || d.n_mr > 8) { *why = "n_mr must be in 1..8"; return TOSOLVE_EINVAL; }
   if (d.d_mr != 0 && d.d_mr != d.n_mr) { *why = "d_mr must equal n_mr"; return TOSOLVE_EINVAL; }
   if (!(d.E0 > 0.0) || !(d.Emin > 0.0) || d.Emin > d.E0) { *why = "need 0 < Emin <= E0"; return TOSOLVE_EINVAL; }
@@ -99,6 +102,10 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (d.precision != TOSOLVE_PREC_FP64 && d.precision != TOSOLVE_PREC_FP32 &&
       d.precision != TOSOLVE_PREC_TF32 && d.precision != TOSOLVE_PREC_FP32X2) {
     *why = "unknown precision";
+    return TOSOLVE_EINVAL;
+  }
+  if (d.precision == TOSOLVE_PREC_TF32 && d.degree != 1) {
+    *why = "the TF32 tensor-core preconditioner is built for degree 1";
     return TOSOLVE_EINVAL;
   }
   if (d.precision == TOSOLVE_PREC_TF32 && !tc_supported(d.n_mr)) {
@@ -133,11 +140,21 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   for (int l = 0; l < L; ++l) {
     Plan::Lv& v = P->lv[l];
     v.ex = d.nx >> l; v.ey = d.ny >> l; v.ez = d.nz >> l;
-    v.Lx = v.ex + 1; v.Ly = v.ey + 1; v.Lz = v.ez + 1;
+    v.Lx = d.degree * v.ex + 1; v.Ly = d.degree * v.ey + 1; v.Lz = d.degree * v.ez + 1;
     v.nn = (long)v.Lx * v.Ly * v.Lz;
     v.ndof = 3 * v.nn;
     v.nsub = d.n_mr << l;
     const bool coarsest = l == L - 1;
+    if (d.degree == 2) {  // element matrices instead of stencils
+      const size_t E = (size_t)v.ex * v.ey * v.ez;
+      const size_t tsz = (fp32 && !x2) ? 4 : 8;
+      v.s64 = v.s32 = false;
+      B += v.ndof + v.ndof * 8 + 4 * v.ndof * tsz;  // mask, dinv64, b v r z
+      if (fp32) B += v.ndof * 4;
+      B += coarsest ? E * kDD2 * 8 : E * kDD2 * (8 + (fp32 ? 4 : 0));
+      if (l > 0) B += E * kNM2 * 8;
+      continue;
+    }
     v.s64 = (l == 0) || !fp32 || coarsest || x2;  // FP32X2: every level formed in FP64
     v.s32 = fp32 && !coarsest && !(tf32 && l == 0);  // TF32: level 0 runs on tensor cores
     const size_t tsz = (fp32 && !x2) ? 4 : 8;
@@ -145,8 +162,16 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     if (v.s64) B += op_len(v.nn) * 8 + v.ndof * 8;
     if (v.s32) B += op_len(v.nn) * 4 + v.ndof * 4;
     B += 4 * v.ndof * tsz;  // b, v, r, z
-    const size_t ke = (size_t)v.ex * v.ey * v.ez * kSym * 8;
-    if (ke > keB) keB = ke;
+  }
+  {
+    int ex[kMaxLevels], ey[kMaxLevels], ez[kMaxLevels];
+    for (int l = 0; l < L; ++l) { ex[l] = P->lv[l].ex; ey[l] = P->lv[l].ey; ez[l] = P->lv[l].ez; }
+    keB = slab_scratch_bytes(ex, ey, ez, L - 1 > 0 ? L - 1 : 1);
+    keB += keB / (kSym * 8) * 27 * 8;  // moments of a slab
+    const Plan::Lv& c = P->lv[L - 1];
+    keB += (size_t)c.ex * c.ey * c.ez * (kSym + 27) * 8;  // coarsest level's own
+    if (d.degree == 2)  // apply results + tables instead of the slab scratch
+      keB = (size_t)ex[0] * ey[0] * ez[0] * kD2 * 8 + ((size_t)P->m + kNM2) * kDD2 * 8;
   }
   P->nc = P->lv[L - 1].ndof;
   if (P->nc > kMaxCoarse) { *why = "coarsest level too large for the dense solve: add levels"; return TOSOLVE_EINVAL; }
@@ -169,27 +194,38 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   return TOSOLVE_OK;
 }
 
+// Device memory from the library's pool, ordered on the handle's stream and
+// complete before it is returned (so any stream may use it).
 template <typename T>
 cudaError_t dalloc(tosolve_s* h, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e == cudaSuccess) h->bytes += count * sizeof(T);
+  void* q = nullptr;
+  cudaError_t e = pool_alloc(&q, count * sizeof(T), h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e == cudaSuccess) {
+    *p = static_cast<T*>(q);
+    h->bytes += count * sizeof(T);
+  }
   return e;
 }
 
 void free_all(tosolve_s* h) {
-  auto F = [](void* p) { if (p) cudaFree(p); };
+  cudaStream_t fs = h->st;
+  auto F = [fs](void* p) { if (p) pool_free(p, fs); };
   for (int l = 0; l < kMaxLevels; ++l) {
     Level& L = h->lv[l];
     F(L.mask); F(L.S64); F(L.S32); F(L.dinv64); F(L.dinv32); F(L.b); F(L.v); F(L.r); F(L.z);
+    F(L.K64); F(L.K32);
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
+  F(h->Yq); F(h->Mq); F(h->Mqc);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv); F(h->Pq);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
   F(h->cnt);
   F(h->hx); F(h->hf); F(h->hu); F(h->hg);
+  if (fs) cudaStreamSynchronize(fs);
   if (h->hs) cudaFreeHost(h->hs);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
@@ -384,6 +420,14 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
       CKC(dalloc(h, &L.dinv32, v.ndof));
     }
     if (tf32 && l == 0) CKC(dalloc(h, &L.dinv32, v.ndof));
+    L.k = h->d.degree;
+    if (L.k == 2) {  // element matrices; the coarsest level's go to Kec
+      const size_t E = (size_t)v.ex * v.ey * v.ez;
+      CKC(dalloc(h, &L.dinv64, v.ndof));
+      if (fp32) CKC(dalloc(h, &L.dinv32, v.ndof));
+      if (l + 1 < P.L || l == 0) CKC(dalloc(h, &L.K64, E * kDD2));  // level 0: the CG's K
+      if (l + 1 < P.L && fp32) CKC(dalloc(h, &L.K32, E * kDD2));
+    }
     const size_t tsz = vt_of(h) == kVtF32 ? 4 : 8;
     void** vecs[4] = {&L.b, &L.v, &L.r, &L.z};
     for (void** pv : vecs) {
@@ -406,12 +450,22 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
     }
   }
   // tables (Sec. 3.3: the subcell matrices are computed once)
-  CKC(dalloc(h, &h->tab64, (size_t)P.m * 576));
-  CKC(dalloc(h, &h->tabsym64, (size_t)P.m * kSym));
-  CKC(dalloc(h, &h->cmom64, 27 * kSym));
-  launch_subcell_table(P.n, h->d.nu, 1.0, h->tab64, st);
-  launch_symmetrize(P.m, h->tab64, h->tabsym64, st);
-  launch_moment_basis(h->d.nu, h->cmom64, st);
+  if (h->d.degree == 2) {
+    CKC(dalloc(h, &h->tab64, (size_t)P.m * kDD2));
+    CKC(dalloc(h, &h->cmom64, (size_t)kNM2 * kDD2));
+    launch_q2_subcell_table(P.n, h->d.nu, 1.0, h->tab64, st);
+    launch_q2_moment_basis(h->d.nu, h->cmom64, st);
+    const Plan::Lv& v0 = P.lv[0];
+    CKC(dalloc(h, &h->Yq, (size_t)v0.ex * v0.ey * v0.ez * kD2));
+    for (int l = 0; l < P.L; ++l) h->lv[l].Y = h->Yq;
+  } else {
+    CKC(dalloc(h, &h->tab64, (size_t)P.m * 576));
+    CKC(dalloc(h, &h->tabsym64, (size_t)P.m * kSym));
+    CKC(dalloc(h, &h->cmom64, 27 * kSym));
+    launch_subcell_table(P.n, h->d.nu, 1.0, h->tab64, st);
+    launch_symmetrize(P.m, h->tab64, h->tabsym64, st);
+    launch_moment_basis(h->d.nu, h->cmom64, st);
+  }
   if (tf32) {  // tensor-core operands of the finest level
     const size_t E0 = (size_t)P.lv[0].ex * P.lv[0].ey * P.lv[0].ez;
     CKC(dalloc(h, &h->KT32, (size_t)P.m * 576));
@@ -459,22 +513,26 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
   CKC(dalloc(h, &h->invom, P.ncell));
   CKC(dalloc(h, &h->gtmp, 2 * P.ncell));
   launch_filter_init(P.Dx, P.Dy, P.Dz, h->noff, h->foff, h->fwgt, h->invom, st);
-  size_t keB = 0;
-  for (int l = 0; l < P.L; ++l) {
-    const size_t ke = (size_t)P.lv[l].ex * P.lv[l].ey * P.lv[l].ez * kSym;
-    if (ke > keB) keB = ke;
-  }
-  CKC(dalloc(h, (double**)&h->Ke, keB));
   {
+    // levels refreshed on the main stream (all but the coarsest, or the one
+    // level) share one slab scratch; the coarsest level has its own
+    int ex[kMaxLevels], ey[kMaxLevels], ez[kMaxLevels];
+    for (int l = 0; l < P.L; ++l) { ex[l] = P.lv[l].ex; ey[l] = P.lv[l].ey; ez[l] = P.lv[l].ez; }
     const Plan::Lv& c = P.lv[P.L - 1];
-    CKC(dalloc(h, &h->Kec, (size_t)c.ex * c.ey * c.ez * kSym));
-    CKC(dalloc(h, &h->Momc, (size_t)c.ex * c.ey * c.ez * 27));
-    size_t em = 1;
-    for (int l = 1; l < P.L; ++l) {
-      const size_t e = (size_t)P.lv[l].ex * P.lv[l].ey * P.lv[l].ez;
-      if (e > em) em = e;
+    const size_t Ec = (size_t)c.ex * c.ey * c.ez;
+    if (h->d.degree == 2) {
+      size_t em = 1;
+      for (int l = 1; l + 1 < P.L; ++l) em = std::max(em, (size_t)ex[l] * ey[l] * ez[l]);
+      CKC(dalloc(h, &h->Mq, em * kNM2));
+      CKC(dalloc(h, &h->Mqc, Ec * kNM2));
+      CKC(dalloc(h, &h->Kec, Ec * kDD2));
+    } else {
+      h->ke_bytes = slab_scratch_bytes(ex, ey, ez, P.L > 1 ? P.L - 1 : 1);
+      CKC(dalloc(h, (char**)&h->Ke, h->ke_bytes));
+      CKC(dalloc(h, &h->Mom, h->ke_bytes / (kSym * 8) * 27));
+      CKC(dalloc(h, &h->Kec, Ec * kSym));
+      CKC(dalloc(h, &h->Momc, Ec * 27));
     }
-    CKC(dalloc(h, &h->Mom, em * 27));
   }
   CKC(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
   CKC(cudaEventCreateWithFlags(&h->evf, cudaEventDisableTiming));
@@ -569,12 +627,47 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
     cst = h->st2;
   }
   Level& C = h->lv[L - 1];
+  if (d.degree == 2) {
+    const double* Kc = h->Kec;
+    if (L > 1) {
+      launch_q2_coarse_elem(C, h->w, h->Dx, h->Dy, h->cmom64, h->Mqc, h->Kec, cst);
+    } else {
+      launch_q2_elem(C, n, h->w, h->Dx, h->Dy, h->tab64, C.K64, cst);
+      Kc = C.K64;
+    }
+    CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), cst));
+    launch_q2_dense(C, Kc, h->Ad, cst);
+    CK(cudaMemsetAsync(&h->ds->coarse_status, 0, sizeof(int), cst));
+    CK(launch_coarse_factor(h->nc, h->Ad, h->Wp, h->Dblk, h->Xinv, h->Ainv, h->Pq,
+                            &h->ds->coarse_status, h->cgrid, cst));
+    for (int l = 0; l + 1 < L; ++l) {
+      Level& Lv = h->lv[l];
+      if (l == 0)
+        launch_q2_elem(Lv, n, h->w, h->Dx, h->Dy, h->tab64, Lv.K64, st);
+      else
+        launch_q2_coarse_elem(Lv, h->w, h->Dx, h->Dy, h->cmom64, h->Mq, Lv.K64, st);
+      launch_q2_dinv(true, Lv, Lv.K64, Lv.dinv64, st);
+      if (Lv.K32) {
+        launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * kDD2, Lv.K64, Lv.K32, st);
+        launch_q2_dinv(false, Lv, Lv.K64, Lv.dinv32, st);
+      }
+    }
+    if (L > 1) {
+      CK(cudaEventRecord(h->evj, h->st2));
+      CK(cudaStreamWaitEvent(st, h->evj, 0));
+    }
+    CK(cudaGetLastError());
+    h->have_rho = true;
+    return TOSOLVE_OK;
+  }
   if (L > 1) {
-    launch_elem_moments(true, C, h->w, h->Dx, h->Dy, h->cmom64, h->Momc, h->Kec, cst);
-    launch_assemble(true, C, h->Kec, C.S64, C.dinv64, cst);
+    launch_elem_moments(true, C, 0, C.ez, h->w, h->Dx, h->Dy, h->cmom64, h->Momc, h->Kec, cst);
+    launch_assemble(true, C, 0, C.Lz, 0, h->Kec, C.S64, C.dinv64, cst);
   } else {
-    launch_elem_direct(true, C, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, cst);
-    launch_assemble(true, C, h->Ke, C.S64, C.dinv64, cst);
+    for_each_slab(C, h->ke_bytes, kSym * 8, [&](int l0, int l1, int ze0, int ze1) {
+      launch_elem_direct(true, C, ze0, ze1, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, cst);
+      launch_assemble(true, C, l0, l1, ze0, h->Ke, C.S64, C.dinv64, cst);
+    });
     if (C.S32) {
       launch_to_fp32(op_len(C.nn), C.S64, C.S32, cst);
       launch_to_fp32((size_t)C.ndof, C.dinv64, C.dinv32, cst);
@@ -588,18 +681,22 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
   for (int l = 0; l + 1 < L; ++l) {
     Level& Lv = h->lv[l];
     if (l == 0) {
-      launch_elem_direct(true, Lv, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, st);
-      launch_assemble(true, Lv, h->Ke, Lv.S64, Lv.dinv64, st);
+      for_each_slab(Lv, h->ke_bytes, kSym * 8, [&](int l0, int l1, int ze0, int ze1) {
+        launch_elem_direct(true, Lv, ze0, ze1, n, h->w, h->Dx, h->Dy, h->tabsym64, h->Ke, st);
+        launch_assemble(true, Lv, l0, l1, ze0, h->Ke, Lv.S64, Lv.dinv64, st);
+      });
       if (Lv.S32) launch_to_fp32(op_len(Lv.nn), Lv.S64, Lv.S32, st);
       if (Lv.dinv32) launch_to_fp32((size_t)Lv.ndof, Lv.dinv64, Lv.dinv32, st);
       if (h->tc.on) launch_weights_elem(Lv, n, h->w, h->Dx, h->Dy, h->w32, st);
     } else {
       const bool op64 = !fp32 || d.precision == TOSOLVE_PREC_FP32X2;
-      launch_elem_moments(op64, Lv, h->w, h->Dx, h->Dy, h->cmom64, h->Mom, h->Ke, st);
-      if (op64)
-        launch_assemble(true, Lv, h->Ke, Lv.S64, Lv.dinv64, st);
-      else
-        launch_assemble(false, Lv, h->Ke, Lv.S32, Lv.dinv32, st);
+      for_each_slab(Lv, h->ke_bytes, kSym * (op64 ? 8 : 4), [&](int l0, int l1, int ze0, int ze1) {
+        launch_elem_moments(op64, Lv, ze0, ze1, h->w, h->Dx, h->Dy, h->cmom64, h->Mom, h->Ke, st);
+        if (op64)
+          launch_assemble(true, Lv, l0, l1, ze0, h->Ke, Lv.S64, Lv.dinv64, st);
+        else
+          launch_assemble(false, Lv, l0, l1, ze0, h->Ke, Lv.S32, Lv.dinv32, st);
+      });
       if (op64 && Lv.S32) {  // FP32X2: FP32 copy of the FP64-formed operator
         launch_to_fp32(op_len(Lv.nn), Lv.S64, Lv.S32, st);
         launch_to_fp32((size_t)Lv.ndof, Lv.dinv64, Lv.dinv32, st);
@@ -751,7 +848,10 @@ tosolve_status tosolve_compliance_grad(tosolve_t h, const double* u_dev, const d
     CK(cudaMemcpyAsync(&h->hs->c, &h->ds->c, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c_host[r] = h->hs->c;
-    if (want_grad)
+    if (want_grad && d.degree == 2)
+      launch_q2_energy_grad(h->lv[0], d.n_mr, u_dev + r * nd, h->tab64, h->rho, d.penal, d.E0 - d.Emin,
+                            h->Dx, h->Dy, r == 0, g, h->lv[0].sms, st);
+    else if (want_grad)
       launch_energy_grad(h->lv[0], d.n_mr, u_dev + r * nd, h->tabsym64, h->rho, d.penal,
                          d.E0 - d.Emin, h->Dx, h->Dy, r == 0, g, st);
   }
@@ -803,7 +903,8 @@ tosolve_status tosolve_level_dims(tosolve_t h, int level, int* dims) {
 
 tosolve_status tosolve_subcell_table(tosolve_t h, double* table_dev) {
   if (h == nullptr || table_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
-  CK(cudaMemcpyAsync(table_dev, h->tab64, (size_t)h->m * 576 * 8, cudaMemcpyDeviceToDevice, h->st));
+  const size_t dd = h->d.degree == 2 ? (size_t)kDD2 : 576;
+  CK(cudaMemcpyAsync(table_dev, h->tab64, (size_t)h->m * dd * 8, cudaMemcpyDeviceToDevice, h->st));
   return TOSOLVE_OK;
 }
 
@@ -820,7 +921,12 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
   if (level < 0 || level >= h->L) return set_err(h, TOSOLVE_EINVAL, "level out of range");
   if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");
   const Level& L = h->lv[level];
-  if (precision == 0) {
+  if (L.k == 2 && (precision == 0 || precision == 1 || precision == 3)) {
+    const bool ok = precision == 0 ? L.K64 != nullptr : L.K32 != nullptr;
+    const bool vt_ok = precision == 0 || (precision == 1) == (vt_of(h) == kVtF32);
+    if (!ok || !vt_ok) return set_err(h, TOSOLVE_EINVAL, "this level has no operator in that precision");
+    launch_apply_diag(precision == 0 ? kVtF64 : (precision == 1 ? kVtF32 : kVtDF), L, x_dev, y_dev, h->st);
+  } else if (precision == 0) {
     if (!L.S64) return set_err(h, TOSOLVE_EINVAL, "this level has no FP64 operator");
     launch_apply_diag(kVtF64, L, x_dev, y_dev, h->st);
   } else if (precision == 1 || precision == 3) {

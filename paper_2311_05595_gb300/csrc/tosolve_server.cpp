@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "../../include/tosolve.h"
+#include "pool.h"
 
 namespace {
 
@@ -92,6 +93,25 @@ size_t design_cells(const tosolve_desc& d) {
   return n * n * n * (size_t)d.nx * d.ny * d.nz;
 }
 
+void free_buffers(Design& D) {
+  tos::pool_free(D.xd, D.st);
+  tos::pool_free(D.gd, D.st);
+  tos::pool_free(D.fd, D.st);
+  tos::pool_free(D.ud, D.st);
+  cudaStreamSynchronize(D.st);
+  cudaStreamDestroy(D.st);
+  D.h = nullptr;
+  D.st = nullptr;
+  D.xd = D.gd = D.fd = D.ud = nullptr;
+}
+
+cudaError_t alloc_doubles(double** p, size_t n, cudaStream_t st) {
+  void* q = nullptr;
+  cudaError_t e = tos::pool_alloc(&q, n * sizeof(double), st);
+  *p = static_cast<double*>(q);
+  return e;
+}
+
 // Frees a resident design's device state (its displacements go to the host
 // first, as the next warm start).  Called with the lock held on an idle
 // design.
@@ -102,14 +122,7 @@ void evict(tosolve_server_s* s, Design& D) {
   D.has_u = cudaMemcpy(D.u_host.data(), D.ud, D.f.size() * sizeof(double), cudaMemcpyDeviceToHost) ==
             cudaSuccess;
   tosolve_destroy(D.h);
-  cudaFree(D.xd);
-  cudaFree(D.fd);
-  cudaFree(D.ud);
-  cudaFree(D.gd);
-  cudaStreamDestroy(D.st);
-  D.h = nullptr;
-  D.st = nullptr;
-  D.xd = D.fd = D.ud = D.gd = nullptr;
+  free_buffers(D);
   s->resident -= D.bytes;
   s->evictions++;
 }
@@ -128,10 +141,10 @@ tosolve_status build(Design& D, std::string* why) {
     return st;
   }
   const size_t nf = D.f.size();
-  e = cudaMalloc((void**)&D.xd, D.ncell * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&D.gd, D.ncell * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&D.fd, nf * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&D.ud, nf * sizeof(double));
+  e = alloc_doubles(&D.xd, D.ncell, D.st);
+  if (e == cudaSuccess) e = alloc_doubles(&D.gd, D.ncell, D.st);
+  if (e == cudaSuccess) e = alloc_doubles(&D.fd, nf, D.st);
+  if (e == cudaSuccess) e = alloc_doubles(&D.ud, nf, D.st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(D.fd, D.f.data(), nf * sizeof(double), cudaMemcpyHostToDevice, D.st);
   if (e == cudaSuccess) {
@@ -145,14 +158,7 @@ tosolve_status build(Design& D, std::string* why) {
     *why = std::string("device buffers: ") + cudaGetErrorString(e);
     cudaGetLastError();
     tosolve_destroy(D.h);
-    cudaFree(D.xd);
-    cudaFree(D.gd);
-    cudaFree(D.fd);
-    cudaFree(D.ud);
-    cudaStreamDestroy(D.st);
-    D.h = nullptr;
-    D.st = nullptr;
-    D.xd = D.gd = D.fd = D.ud = nullptr;
+    free_buffers(D);
     return e == cudaErrorMemoryAllocation ? TOSOLVE_ENOMEM : TOSOLVE_ECUDA;
   }
   return TOSOLVE_OK;

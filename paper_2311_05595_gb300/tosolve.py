@@ -94,6 +94,7 @@ def _load():
         "tosolve_server_stats": ([vp, P(tosolve_server_info)], i),
         "tosolve_server_last_error": ([], C.c_char_p),
         "tosolve_server_destroy": ([vp], None),
+        "tosolve_trim_pool": ([sz], i),
         "tosolve_last_error": ([vp], C.c_char_p),
         "tosolve_destroy": ([vp], None),
     }
@@ -265,6 +266,10 @@ def tosolve_compliance_noalloc(f_dev, u_dev, mask_dev, ndof: int, nrhs: int, c_d
         st = stream if isinstance(stream, int) else stream.cuda_stream
     _check(None, _lib.tosolve_compliance_noalloc(_ptr(f_dev), _ptr(u_dev), _ptr(mask_dev), ndof, nrhs,
                                                  _ptr(c_dev), st), "tosolve_compliance_noalloc")
+
+
+def tosolve_trim_pool(keep_bytes: int = 0) -> None:
+    _check(None, _lib.tosolve_trim_pool(keep_bytes), "tosolve_trim_pool")
 
 
 def tosolve_level_dims(h, level: int):

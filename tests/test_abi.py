@@ -76,7 +76,7 @@ def test_footprint_and_validation_without_gpu(lib):
     bad = [
         T.make_desc(24, 12, 12, mg_levels=5),      # 12 not divisible by 16
         T.make_desc(0, 12, 12),                    # empty mesh
-        T.make_desc(24, 12, 12, degree=2),         # degree not built
+        T.make_desc(24, 12, 12, degree=3),         # degree not built
         T.make_desc(24, 12, 12, nu=0.5),           # incompressible
         T.make_desc(24, 12, 12, Emin=0.0),         # singular void
         T.make_desc(24, 12, 12, cycle_gamma=2),    # W-cycle not built
