@@ -45,10 +45,25 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 NCU_TRAFFIC = {("k_apply_diag<double>", "d09ac84b551d"): 60.347904e6 + 0.040704e6}
 
 
-def problem():
+# Adaptive-degree bridge, all elements triquadratic: displacement 64x32x32
+# Q2 (n = 3, 27 subcells of a 192x96x96 density grid), four bottom corners
+# pinned, uniform downward top pressure, x iid U[0.01, 1].  The oracle's
+# bounded CPU sample is the same recipe at 16x8x8.
+BRIDGE = dict(name="bridge_q2_64x32x32_n3_density_192x96x96", kind="bridge", nx=64, ny=32, nz=32,
+              degree=2, n_mr=3, rmin=0.0, seed=0, levels=0, rtol=1e-8,
+              sample=dict(nx=16, ny=8, nz=8, levels=3))
+SPECS = {"cantilever": dict(WORKLOAD, kind="cantilever", degree=1), "bridge_q2": BRIDGE}
+
+
+def problem(spec=None, sample=False):
     import workloads
 
-    w = WORKLOAD
+    w = spec or SPECS["cantilever"]
+    dims = w["sample"] if sample else w
+    if w["kind"] == "bridge":
+        return workloads.bridge(dims["nx"], dims["ny"], dims["nz"], degree=w["degree"],
+                                n_mr=w["n_mr"], rmin=w["rmin"], seed=w["seed"],
+                                mg_levels=dims["levels"])
     return workloads.cantilever(w["nx"], w["ny"], w["nz"], n_mr=w["n_mr"], rmin=w["rmin"],
                                 density=w["density"], seed=w["seed"], mg_levels=w["levels"])
 
@@ -111,15 +126,19 @@ class ClockSampler:
 
 # ---- CPU oracle (reference arm and cpu_baseline) ------------------------------
 
-def oracle_steps(steps: int, warmup: int) -> tuple[list, int, int]:
+def oracle_steps(steps: int, warmup: int, spec_name: str = "cantilever") -> tuple[list, int, int]:
     """Times `steps` full oracle steps (after `warmup` untimed ones) on the
-    workload, in one fresh single-threaded process (spawned: never forked
-    from a CUDA process).  Returns per-step seconds, free DOFs, load cases."""
+    workload (its bounded sample where the spec has one), in one fresh
+    single-threaded process (spawned: never forked from a CUDA process).
+    Returns per-step seconds, free DOFs, load cases."""
+    spec = SPECS[spec_name]
+    levels = spec["sample"]["levels"] if "sample" in spec else spec["levels"]
     code = (
         "import os,sys,time; sys.path.insert(0, %r)\n"
         "import bench\n"
         "from oracle import fe\n"
-        "p = bench.problem()\n"
+        "spec = bench.SPECS[%r]\n"
+        "p = bench.problem(spec, sample='sample' in spec)\n"
         "def one():\n"
         "    t = time.perf_counter()\n"
         "    m = fe.Model(p)\n"
@@ -128,7 +147,7 @@ def oracle_steps(steps: int, warmup: int) -> tuple[list, int, int]:
         "for _ in range(%d): one()\n"
         "ts = [one() for _ in range(%d)]\n"
         "print(' '.join(map(repr, ts)), p.nfree, p.nrhs)\n"
-        % (ROOT, WORKLOAD["rtol"], WORKLOAD["levels"], warmup, steps))
+        % (ROOT, spec_name, spec["rtol"], levels, warmup, steps))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
@@ -139,12 +158,14 @@ def oracle_steps(steps: int, warmup: int) -> tuple[list, int, int]:
     return [float(v) for v in parts[:-2]], int(parts[-2]), int(parts[-1])
 
 
-def cpu_baseline_entry():
-    ts, nfree, nrhs = oracle_steps(1, 1)
+def cpu_baseline_entry(spec_name: str = "cantilever"):
+    ts, nfree, nrhs = oracle_steps(1, 1, spec_name)
+    where = ("the exact benchmark input" if "sample" not in SPECS[spec_name] else
+             "the same recipe at %(nx)dx%(ny)dx%(nz)d (%(levels)d levels)" % SPECS[spec_name]["sample"])
     return {"value": nfree * nrhs / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "one full oracle step (filter, assembly, every MG level's operator, "
-                      "dense Cholesky, MG-PCG to 1e-8, compliance, gradient) on the exact "
-                      f"benchmark input after one warm-up step, single-threaded: {ts[0]:.2f} s"}
+                      f"dense Cholesky, MG-PCG to 1e-8, compliance, gradient) on {where} "
+                      f"after one warm-up step, single-threaded: {ts[0]:.2f} s, {nfree} free DOFs"}
 
 
 def run_reference(args):
@@ -169,7 +190,7 @@ def run_reference(args):
 
 # ---- GPU arm -------------------------------------------------------------------
 
-def kernel_launches(levels: int, iterations: int, attempts: int = 1) -> int:
+def kernel_launches(levels: int, iterations: int, attempts: int = 1, degree: int = 1) -> int:
     """Our kernels per step: set_densities (filter; fine element matrices,
     assembly, two FP32 casts; 2 per coarse level; coarse dense + factor),
     solve (prep, residual, check; per PCG iteration: 4 per non-coarsest
@@ -177,6 +198,9 @@ def kernel_launches(levels: int, iterations: int, attempts: int = 1) -> int:
     (masked dot + sum, energies, scale, filter transpose)."""
     setd = 1 + 4 + 2 * (levels - 1) + 2
     per_it = 4 * (levels - 1) + 1 + 5
+    if degree == 2:  # element form: two kernels per operator apply, 8 dense passes
+        setd = 1 + 3 * (levels - 1) + 2 + 9 + 2
+        per_it = 6 * (levels - 1) + 1 + 6
     solve = attempts * 5 + per_it * iterations
     return setd + solve + 5
 
@@ -195,8 +219,9 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    p = problem()
-    rtol = WORKLOAD["rtol"]
+    spec = SPECS[args.workload]
+    p = problem(spec)
+    rtol = spec["rtol"]
     maxit = 2000
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -210,8 +235,8 @@ def run_gpu(args):
             dist.barrier()
 
     def make(precision):
-        d = T.make_desc(p.nx, p.ny, p.nz, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin, nu=p.nu,
-                        penal=p.penal, mg_levels=WORKLOAD["levels"], precision=precision)
+        d = T.make_desc(p.nx, p.ny, p.nz, degree=p.degree, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin,
+                        nu=p.nu, penal=p.penal, mg_levels=spec["levels"], precision=precision)
         return T.Solver(d, p.mask, stream)
 
     def step(s):
@@ -249,7 +274,8 @@ def run_gpu(args):
     sampler = ClockSampler(local)
     out = {}
     precs = {"fp32": T.PREC_FP32, "tf32": T.PREC_TF32, "fp32x2": T.PREC_FP32X2, "fp64": T.PREC_FP64}
-    mixed_labels = tuple(v for v in args.variants.split(",") if v != "fp64")
+    mixed_labels = tuple(v for v in args.variants.split(",") if v != "fp64"
+                         and not (v == "tf32" and p.degree != 1))
     if not mixed_labels or any(v not in precs for v in mixed_labels):
         raise SystemExit("--variants: a comma list of fp32, tf32, fp32x2 (fp64 always runs)")
     solvers = {lab: make(precs[lab]) for lab in mixed_labels + ("fp64",)}
@@ -345,12 +371,20 @@ def run_gpu(args):
         stream.synchronize()
     us = a0.elapsed_time(a1) * 1e3 / nrep
     Lx, Ly, Lz = p.lattice
-    pairs = (3 * Lx - 2) * (3 * Ly - 2) * (3 * Lz - 2)  # (node, neighbour) couplings
-    flops = 18.0 * pairs
     nn = Lx * Ly * Lz
-    bytes_alg = nn * (243 * 8 + 3 * 8 * 2)
+    if p.degree == 1:
+        pairs = (3 * Lx - 2) * (3 * Ly - 2) * (3 * Lz - 2)  # (node, neighbour) couplings
+        flops = 18.0 * pairs
+        bytes_alg = nn * (243 * 8 + 3 * 8 * 2)
+        kernel = "k_apply_diag<double> (FP64 27-point block stencil, K u)"
+        traffic = NCU_TRAFFIC.get(("k_apply_diag<double>", source_hash("k_solve.cu")))
+    else:  # element form: 81x81 FP64 product per element, then the node gather
+        E = p.nx * p.ny * p.nz
+        flops = 2.0 * 81 * 81 * E
+        bytes_alg = E * (81 * 81 * 8 + 81 * 8 * 2) + nn * 3 * 8 * 2
+        kernel = "k_q2_apply<double> + k_q2_gather<double> (FP64 element matrices, K u)"
+        traffic = NCU_TRAFFIC.get(("k_q2_apply<double>", source_hash("k_q2.cu")))
     achieved = flops / (us * 1e-6) / 1e12
-    traffic = NCU_TRAFFIC.get(("k_apply_diag<double>", source_hash("k_solve.cu")))
 
     its = [i[0] for i in mixed["infos"]]
     res = max(i[2] for i in mixed["infos"])
@@ -358,8 +392,9 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mixed["tot"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "free_dofs": p.nfree, "load_cases": p.nrhs,
-                   "density_cells": int(p.x.size), "mg_levels": WORKLOAD["levels"],
+        "config": {"workload": spec["name"], "free_dofs": p.nfree, "load_cases": p.nrhs,
+                   "degree": p.degree, "density_cells": int(p.x.size),
+                   "mg_levels": spec["levels"] or "auto",
                    "smoother": "damped Jacobi omega=0.5, 1+1, V-cycle",
                    "precision": f"FP64 CG + {best.upper()} V-cycle (value; TF32 = finest level "
                                 f"on tcgen05, FP32X2 = FP32 operators with float-pair vectors); "
@@ -380,8 +415,9 @@ def run_gpu(args):
                              "fp64_p99": pct(fp64["solve_ms"], 0.99)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": kernel_launches(WORKLOAD["levels"], int(statistics.median(its))) * args.steps,
-        "roofline": {"kernel": "k_apply_diag<double> (FP64 27-point block stencil, K u)",
+        "gpu_launches": kernel_launches(T.tosolve_level_count(s.h), int(statistics.median(its)),
+                                        degree=p.degree) * args.steps,
+        "roofline": {"kernel": kernel,
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                      "us_per_launch": us, "alg_bytes_per_launch": bytes_alg,
@@ -392,7 +428,7 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline_entry()
+            line["cpu_baseline"] = cpu_baseline_entry(args.workload)
         except Exception as e:  # reported, never silently dropped
             line["cpu_baseline"] = {"error": str(e)[-300:]}
     for lab in mixed_labels + ("fp64",):
@@ -660,9 +696,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="fp32,tf32,fp32x2",
                     help="mixed-precision variants timed beside FP64 (comma list)")
-    ap.add_argument("--workload", default="cantilever", choices=["cantilever", "batch64", "serve"],
-                    help="batch64: the 64-instance batched solve; serve: the serving loop "
-                         "(each its own JSON line)")
+    ap.add_argument("--workload", default="cantilever",
+                    choices=["cantilever", "bridge_q2", "batch64", "serve"],
+                    help="bridge_q2: the degree-2 bridge; batch64: the 64-instance batched "
+                         "solve; serve: the serving loop (each its own JSON line)")
     ap.add_argument("--designs", type=int, default=SERVE["designs"])
     ap.add_argument("--requests", type=int, default=SERVE["requests"])
     ap.add_argument("--slots", type=int, default=8)

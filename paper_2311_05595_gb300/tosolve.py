@@ -272,6 +272,15 @@ def tosolve_trim_pool(keep_bytes: int = 0) -> None:
     _check(None, _lib.tosolve_trim_pool(keep_bytes), "tosolve_trim_pool")
 
 
+def tosolve_level_count(h) -> int:
+    """Multigrid levels of a handle (the levels tosolve_level_dims accepts)."""
+    dims = (C.c_int * 3)()
+    n = 0
+    while n < 8 and _lib.tosolve_level_dims(h, n, dims) == OK:
+        n += 1
+    return n
+
+
 def tosolve_level_dims(h, level: int):
     dims = (C.c_int * 3)()
     _check(h, _lib.tosolve_level_dims(h, level, dims), "tosolve_level_dims")
