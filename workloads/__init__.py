@@ -68,6 +68,8 @@ class Problem:
     x: np.ndarray  # float64 (n_mr^3 * nx*ny*nz,), design variables
     mg_levels: int
     meta: dict = field(default_factory=dict)
+    # mixed degree (degree-2 lattice): uint8 per element, 1 = trilinear
+    elem_q1: np.ndarray | None = None
 
     @property
     def lattice(self) -> tuple[int, int, int]:
@@ -257,3 +259,17 @@ def batched_instances(count: int, seed: int, *, min_nx: int = 32, max_nx: int = 
         p.name = f"batch{b}_{nx}x{ny}x{nz}_rhs{nrhs}"
         out.append(p)
     return out
+
+
+def with_mixed_degree(p: Problem, q1_fraction: float, seed: int) -> Problem:
+    """The same problem on its degree-2 lattice with a random q1_fraction of
+    the elements trilinear (iid per element, seeded)."""
+    if p.degree != 2:
+        raise ValueError("mixed degree needs the degree-2 lattice")
+    rng = np.random.default_rng(seed)
+    E = p.nx * p.ny * p.nz
+    q = p.__class__(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    q.elem_q1 = (rng.random(E) < q1_fraction).astype(np.uint8)
+    q.name = p.name + f"_mixed{q1_fraction:g}"
+    q.meta = dict(p.meta, q1_fraction=q1_fraction, degree_seed=seed)
+    return q
