@@ -52,7 +52,13 @@ NCU_TRAFFIC = {("k_apply_diag<double>", "d09ac84b551d"): 60.347904e6 + 0.040704e
 BRIDGE = dict(name="bridge_q2_64x32x32_n3_density_192x96x96", kind="bridge", nx=64, ny=32, nz=32,
               degree=2, n_mr=3, rmin=0.0, seed=0, levels=0, rtol=1e-8,
               sample=dict(nx=16, ny=8, nz=8, levels=3))
-SPECS = {"cantilever": dict(WORKLOAD, kind="cantilever", degree=1), "bridge_q2": BRIDGE}
+# The adaptive-degree bridge as specified: a seeded half of the elements
+# trilinear, the rest triquadratic, on the degree-2 lattice (mixed coupling:
+# slaved midside nodes).
+BRIDGE_MIXED = dict(BRIDGE, name="bridge_mixed_q1q2_64x32x32_n3_density_192x96x96",
+                    q1_fraction=0.5, degree_seed=11)
+SPECS = {"cantilever": dict(WORKLOAD, kind="cantilever", degree=1), "bridge_q2": BRIDGE,
+         "bridge_mixed": BRIDGE_MIXED}
 
 
 def problem(spec=None, sample=False):
@@ -61,9 +67,12 @@ def problem(spec=None, sample=False):
     w = spec or SPECS["cantilever"]
     dims = w["sample"] if sample else w
     if w["kind"] == "bridge":
-        return workloads.bridge(dims["nx"], dims["ny"], dims["nz"], degree=w["degree"],
-                                n_mr=w["n_mr"], rmin=w["rmin"], seed=w["seed"],
-                                mg_levels=dims["levels"])
+        p = workloads.bridge(dims["nx"], dims["ny"], dims["nz"], degree=w["degree"],
+                             n_mr=w["n_mr"], rmin=w["rmin"], seed=w["seed"],
+                             mg_levels=dims["levels"])
+        if "q1_fraction" in w:
+            p = workloads.with_mixed_degree(p, w["q1_fraction"], w["degree_seed"])
+        return p
     return workloads.cantilever(w["nx"], w["ny"], w["nz"], n_mr=w["n_mr"], rmin=w["rmin"],
                                 density=w["density"], seed=w["seed"], mg_levels=w["levels"])
 
@@ -139,14 +148,18 @@ def oracle_steps(steps: int, warmup: int, spec_name: str = "cantilever") -> tupl
         "from oracle import fe\n"
         "spec = bench.SPECS[%r]\n"
         "p = bench.problem(spec, sample='sample' in spec)\n"
+        "from oracle import mixed\n"
         "def one():\n"
         "    t = time.perf_counter()\n"
-        "    m = fe.Model(p)\n"
-        "    m.run(method='mg', rtol=%r, levels=%d)\n"
+        "    if p.elem_q1 is not None:\n"
+        "        mixed.MixedModel(p).run(method='splu')\n"
+        "    else:\n"
+        "        fe.Model(p).run(method='mg', rtol=%r, levels=%d)\n"
         "    return time.perf_counter() - t\n"
         "for _ in range(%d): one()\n"
         "ts = [one() for _ in range(%d)]\n"
-        "print(' '.join(map(repr, ts)), p.nfree, p.nrhs)\n"
+        "nfree = mixed.MixedModel(p).free.size if p.elem_q1 is not None else p.nfree\n"
+        "print(' '.join(map(repr, ts)), nfree, p.nrhs)\n"
         % (ROOT, spec_name, spec["rtol"], levels, warmup, steps))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -162,10 +175,12 @@ def cpu_baseline_entry(spec_name: str = "cantilever"):
     ts, nfree, nrhs = oracle_steps(1, 1, spec_name)
     where = ("the exact benchmark input" if "sample" not in SPECS[spec_name] else
              "the same recipe at %(nx)dx%(ny)dx%(nz)d (%(levels)d levels)" % SPECS[spec_name]["sample"])
+    solve = ("sparse direct solve of T^T K T (the mixed oracle)" if "q1_fraction" in SPECS[spec_name]
+             else "every MG level's operator, dense Cholesky, MG-PCG to 1e-8")
     return {"value": nfree * nrhs / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one full oracle step (filter, assembly, every MG level's operator, "
-                      f"dense Cholesky, MG-PCG to 1e-8, compliance, gradient) on {where} "
-                      f"after one warm-up step, single-threaded: {ts[0]:.2f} s, {nfree} free DOFs"}
+            "sample": f"one full oracle step (filter, assembly, {solve}, compliance, gradient) on "
+                      f"{where} after one warm-up step, single-threaded: {ts[0]:.2f} s, "
+                      f"{nfree} free DOFs"}
 
 
 def run_reference(args):
@@ -237,7 +252,7 @@ def run_gpu(args):
     def make(precision):
         d = T.make_desc(p.nx, p.ny, p.nz, degree=p.degree, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin,
                         nu=p.nu, penal=p.penal, mg_levels=spec["levels"], precision=precision)
-        return T.Solver(d, p.mask, stream)
+        return T.Solver(d, p.mask, stream, elem_q1=p.elem_q1)
 
     def step(s):
         T.tosolve_set_densities(s.h, x)
@@ -315,7 +330,7 @@ def run_gpu(args):
                 acc["solve"] += ev[1].elapsed_time(ev[2]) / nph
                 acc["gradient"] += ev[2].elapsed_time(ev[3]) / nph
         phases[label] = {k: round(v, 4) for k, v in acc.items()}
-    free_dofs = p.nfree * p.nrhs
+    free_dofs = T.tosolve_free_dofs(solvers["fp64"].h) * p.nrhs
     best = min(mixed_labels, key=lambda lab: out[lab]["tot"])
     mixed = out[best]
     fp64 = out["fp64"]
@@ -392,7 +407,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mixed["tot"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": spec["name"], "free_dofs": p.nfree, "load_cases": p.nrhs,
+        "config": {"workload": spec["name"], "free_dofs": free_dofs // p.nrhs, "load_cases": p.nrhs,
                    "degree": p.degree, "density_cells": int(p.x.size),
                    "mg_levels": spec["levels"] or "auto",
                    "smoother": "damped Jacobi omega=0.5, 1+1, V-cycle",
@@ -697,7 +712,7 @@ def main():
     ap.add_argument("--variants", default="fp32,tf32,fp32x2",
                     help="mixed-precision variants timed beside FP64 (comma list)")
     ap.add_argument("--workload", default="cantilever",
-                    choices=["cantilever", "bridge_q2", "batch64", "serve"],
+                    choices=["cantilever", "bridge_q2", "bridge_mixed", "batch64", "serve"],
                     help="bridge_q2: the degree-2 bridge; batch64: the 64-instance batched "
                          "solve; serve: the serving loop (each its own JSON line)")
     ap.add_argument("--designs", type=int, default=SERVE["designs"])

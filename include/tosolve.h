@@ -76,7 +76,7 @@ typedef enum {
 /* Problem and solver description (Sec. 2, 3.1, 7 intro). */
 typedef struct {
   int nx, ny, nz;         /* displacement elements per axis, >= 1           */
-  int degree;             /* Lagrange degree k (this build: 1)              */
+  int degree;             /* Lagrange degree k: 1 or 2                      */
   int n_mr;               /* density cells per element edge, 1..8           */
   int d_mr;               /* design cells per element edge; must equal n_mr */
   double E0, Emin;        /* SIMP: E(rho) = Emin + rho^p (E0 - Emin), Eq.   */
@@ -115,6 +115,25 @@ typedef struct {
  * Errors: EINVAL (checked before any CUDA call), ENOMEM, ECUDA. */
 tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host,
                               void* cuda_stream, tosolve_t* out);
+
+/* A mesh that mixes trilinear and triquadratic elements on the degree-2
+ * lattice (desc->degree = 2).  elem_q1_host: nx*ny*nz bytes (x fastest),
+ * 1 = trilinear element.  Every element carries the triquadratic matrix of
+ * Eq. matrixK_mr; a lattice node that is not an element vertex and touches
+ * a trilinear element is slaved to the linear interpolation of the vertices
+ * of its edge, face or cell (the coupling is conforming and a trilinear
+ * element keeps exactly its trilinear matrix; the paper raises the degree
+ * of the whole mesh, Sec. 7.4, and does not spell a mixed coupling out).
+ * The solve is on u = T u_r with T^T K T u_r = T^T f; u_dev returns the
+ * expanded field, loads f_dev are the degree-2 consistent loads on the whole
+ * lattice, compliance and gradient use the expanded u.  Otherwise as
+ * tosolve_create (TF32 is not available).  Errors: EINVAL, ENOMEM, ECUDA. */
+tosolve_status tosolve_create_mixed(const tosolve_desc* desc, const uint8_t* mask_host,
+                                    const uint8_t* elem_q1_host, void* cuda_stream, tosolve_t* out);
+
+/* Number of unknowns of the handle's system: lattice DOFs that are neither
+ * supported nor (mixed meshes) slaved.  Errors: EINVAL. */
+tosolve_status tosolve_free_dofs(tosolve_t h, long long* n);
 
 /* Device memory tosolve_create would allocate for desc, in bytes (host
  * only; used for HBM admission).  Errors: EINVAL. */

@@ -222,6 +222,11 @@ void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t s
 // 2 Av (identity rows at fixed DOFs).  Ke is FP64 for kVtF64, else FP32.
 void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b, const void* v,
                   const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st);
+// Mixed degree: K^(e) <- T_e^T K^(e) T_e; f <- T^T f; u <- T u (slv: per
+// lattice node, 1 = slaved).
+void launch_q2_constrain(const Level& L, const uint8_t* slv, double* Ke, int sms, cudaStream_t st);
+void launch_q2_fold(const Level& L, const uint8_t* slv, double* f, cudaStream_t st);
+void launch_q2_expand(const Level& L, const uint8_t* slv, double* u, cudaStream_t st);
 void launch_q2_energy_grad(const Level& L0, int n, const double* u, const double* tab,
                            const double* rho, double penal, double dE, int Dx, int Dy, bool first,
                            double* g, int sms, cudaStream_t st);
@@ -238,8 +243,10 @@ void launch_energy_grad(const Level& L0, int n, const double* u, const double* t
 void launch_scale(size_t n, const double* a, const double* s, double* out, cudaStream_t st);
 void launch_filter_T(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,
                      const double* gt, double* gx, cudaStream_t st);
-void launch_compliance(const Level& L0, const double* f, const double* u, double* part, int np,
-                       DevState* ds, cudaStream_t st);
+// c = f^T u over the DOFs that fixed marks 0 (the supports only: slaved DOFs
+// of a mixed mesh carry load and displacement).
+void launch_compliance(const Level& L0, const uint8_t* fixed, const double* f, const double* u,
+                       double* part, int np, DevState* ds, cudaStream_t st);
 
 // Blocks of the node-parallel solve kernels (64 nodes per block); also the
 // number of partial sums their reductions produce.
@@ -289,6 +296,11 @@ struct tosolve_s {
   double* Yq = nullptr;        // degree 2: per-element apply results (E0 x 81)
   double* Mq = nullptr;        // degree 2: moments of the finer coarse levels
   double* Mqc = nullptr;       // degree 2: moments of the coarsest level
+  // mixed trilinear / triquadratic mesh (degree-2 lattice)
+  bool mixed = false;
+  long long free_dofs = 0;     // unknowns: DOFs neither supported nor slaved
+  uint8_t* slv0 = nullptr;     // per lattice node: 1 = slaved to its vertices
+  uint8_t* fix0 = nullptr;     // per DOF: the supports alone (level 0 mask adds slaved)
   float* KT32 = nullptr;       // m x 24 x 24 FP32 (tensor-core operand)
   float* w32 = nullptr;        // E x m element-major FP32 weights
   float* Ye = nullptr;         // E x 24 element results of the tensor-core apply

@@ -128,9 +128,9 @@ void launch_filter_T(int Dx, int Dy, int Dz, int noff, const int4* off, const do
   k_filter_T<<<grid_for((long)Dx * Dy * Dz), kBS, 0, st>>>(Dx, Dy, Dz, noff, off, wgt, gt, gx);
 }
 
-void launch_compliance(const Level& L0, const double* f, const double* u, double* part, int np,
-                       DevState* ds, cudaStream_t st) {
-  k_dot_masked<<<np, kBS, 0, st>>>((long)L0.ndof, L0.mask, f, u, part);
+void launch_compliance(const Level& L0, const uint8_t* fixed, const double* f, const double* u,
+                       double* part, int np, DevState* ds, cudaStream_t st) {
+  k_dot_masked<<<np, kBS, 0, st>>>((long)L0.ndof, fixed, f, u, part);
   k_sum_to<<<1, kBS, 0, st>>>(part, np, &ds->c);
 }
 

@@ -411,6 +411,123 @@ __global__ void k_q2_energy_grad(int ex, int ey, long E, int n, int Lx, int Ly,
   }
 }
 
+// Mixed trilinear / triquadratic meshes (the coupling rule of the mixed
+// reading): a non-vertex lattice node touching a trilinear element is slaved
+// to the linear interpolation of the 2^q vertices of its edge, face or cell
+// (q = number of its odd lattice coordinates, weight 2^-q each).  The slaved
+// values of an element come from its own corners, so the constraint is local:
+// K^(e) <- T_e^T K^(e) T_e.  Block per element, the matrix staged in shared
+// memory; elements without slaved nodes are left as they are.
+__device__ __forceinline__ int local_parents(int a, int par[8]) {
+  const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+  const int xs[2] = {ax == 1 ? 0 : ax, ax == 1 ? 2 : ax};
+  const int ys[2] = {ay == 1 ? 0 : ay, ay == 1 ? 2 : ay};
+  const int zs[2] = {az == 1 ? 0 : az, az == 1 ? 2 : az};
+  const int nx = ax == 1 ? 2 : 1, ny = ay == 1 ? 2 : 1, nz = az == 1 ? 2 : 1;
+  int k = 0;
+  for (int c = 0; c < nz; ++c)
+    for (int b = 0; b < ny; ++b)
+      for (int q = 0; q < nx; ++q) par[k++] = xs[q] + 3 * (ys[b] + 3 * zs[c]);
+  return k;
+}
+
+__global__ void k_q2_constrain(int ex, int ey, long E, int Lx, int Ly, const uint8_t* __restrict__ slv,
+                               double* __restrict__ Ke) {
+  extern __shared__ double Ks[];  // 81 x 81
+  __shared__ int sl[kNE];
+  for (long e = blockIdx.x; e < E; e += gridDim.x) {
+    const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+    if (threadIdx.x < kNE) sl[threadIdx.x] = slv[elem_node(exi, eyi, ezi, threadIdx.x, Lx, Ly)];
+    __syncthreads();
+    int any = 0;
+    for (int a = 0; a < kNE; ++a) any |= sl[a];
+    if (any) {
+      double* K = Ke + e * (size_t)kDD;
+      for (int t = threadIdx.x; t < kDD; t += blockDim.x) Ks[t] = K[t];
+      __syncthreads();
+      // K T: column groups; thread per row, slaved columns folded into their
+      // parents, in a fixed order
+      for (int R = threadIdx.x; R < kD; R += blockDim.x)
+        for (int a = 0; a < kNE; ++a) {
+          if (!sl[a]) continue;
+          int par[8];
+          const int np = local_parents(a, par);
+          const double w = 1.0 / np;
+          for (int c = 0; c < 3; ++c) {
+            const double v = Ks[R * kD + 3 * a + c];
+            for (int q = 0; q < np; ++q) Ks[R * kD + 3 * par[q] + c] += w * v;
+            Ks[R * kD + 3 * a + c] = 0.0;
+          }
+        }
+      __syncthreads();
+      // T^T (K T): the same on rows, thread per column
+      for (int Cc = threadIdx.x; Cc < kD; Cc += blockDim.x)
+        for (int a = 0; a < kNE; ++a) {
+          if (!sl[a]) continue;
+          int par[8];
+          const int np = local_parents(a, par);
+          const double w = 1.0 / np;
+          for (int c = 0; c < 3; ++c) {
+            const double v = Ks[(3 * a + c) * kD + Cc];
+            for (int q = 0; q < np; ++q) Ks[(3 * par[q] + c) * kD + Cc] += w * v;
+            Ks[(3 * a + c) * kD + Cc] = 0.0;
+          }
+        }
+      __syncthreads();
+      for (int t = threadIdx.x; t < kDD; t += blockDim.x) K[t] = Ks[t];
+    }
+    __syncthreads();
+  }
+}
+
+// f <- T^T f: every vertex node collects 2^-q of the value of each slaved
+// neighbour (q = number of nonzero offsets); fixed order.
+__global__ void k_q2_fold(int Lx, int Ly, int Lz, const uint8_t* __restrict__ slv, double* __restrict__ f) {
+  const long nn = (long)Lx * Ly * Lz;
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
+       node += (long)gridDim.x * blockDim.x) {
+    const int i = node % Lx, j = (node / Lx) % Ly, l = node / ((long)Lx * Ly);
+    if ((i | j | l) & 1) continue;  // vertices only
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int q = (dx != 0) + (dy != 0) + (dz != 0);
+          if (q == 0) continue;
+          const int ii = i + dx, jj = j + dy, ll = l + dz;
+          if (ii < 0 || ii >= Lx || jj < 0 || jj >= Ly || ll < 0 || ll >= Lz) continue;
+          const long s = ii + (long)Lx * (jj + (long)Ly * ll);
+          if (!slv[s]) continue;
+          const double w = 1.0 / (1 << q);
+          for (int c = 0; c < 3; ++c) acc[c] += w * f[3 * s + c];
+        }
+    for (int c = 0; c < 3; ++c) f[3 * node + c] += acc[c];
+  }
+}
+
+// u <- T u on the slaved nodes (their parents are vertices, never slaved).
+__global__ void k_q2_expand(int Lx, int Ly, int Lz, const uint8_t* __restrict__ slv, double* __restrict__ u) {
+  const long nn = (long)Lx * Ly * Lz;
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
+       node += (long)gridDim.x * blockDim.x) {
+    if (!slv[node]) continue;
+    const int i = node % Lx, j = (node / Lx) % Ly, l = node / ((long)Lx * Ly);
+    const int xs[2] = {i & 1 ? i - 1 : i, i & 1 ? i + 1 : i};
+    const int ys[2] = {j & 1 ? j - 1 : j, j & 1 ? j + 1 : j};
+    const int zs[2] = {l & 1 ? l - 1 : l, l & 1 ? l + 1 : l};
+    const int nx = (i & 1) + 1, ny = (j & 1) + 1, nz = (l & 1) + 1;
+    const double w = 1.0 / (nx * ny * nz);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int c2 = 0; c2 < nz; ++c2)
+      for (int b = 0; b < ny; ++b)
+        for (int a = 0; a < nx; ++a) {
+          const long p = xs[a] + (long)Lx * (ys[b] + (long)Ly * zs[c2]);
+          for (int c = 0; c < 3; ++c) acc[c] += w * u[3 * p + c];
+        }
+    for (int c = 0; c < 3; ++c) u[3 * node + c] = acc[c];
+  }
+}
+
 inline int grid_for2(long work, int cap = 65536) {
   long g = (work + 255) / 256;
   if (g < 1) g = 1;
@@ -480,6 +597,26 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
   if (vt == kVtF64) run(double());
   else if (vt == kVtF32) run(float());
   else run(dfloat(0.f, 0.f));
+}
+
+void launch_q2_constrain(const Level& L, const uint8_t* slv, double* Ke, int sms, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * L.ez;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_q2_constrain, cudaFuncAttributeMaxDynamicSharedMemorySize, kDD * 8);
+    attr = true;
+  }
+  long g = (long)sms * 4;
+  if (g > E) g = E;
+  k_q2_constrain<<<(int)g, 256, kDD * 8, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, slv, Ke);
+}
+
+void launch_q2_fold(const Level& L, const uint8_t* slv, double* f, cudaStream_t st) {
+  k_q2_fold<<<grid_for2(L.nn), 256, 0, st>>>(L.Lx, L.Ly, L.Lz, slv, f);
+}
+
+void launch_q2_expand(const Level& L, const uint8_t* slv, double* u, cudaStream_t st) {
+  k_q2_expand<<<grid_for2(L.nn), 256, 0, st>>>(L.Lx, L.Ly, L.Lz, slv, u);
 }
 
 void launch_q2_energy_grad(const Level& L0, int n, const double* u, const double* tab,

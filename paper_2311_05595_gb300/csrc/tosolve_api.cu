@@ -219,7 +219,7 @@ void free_all(tosolve_s* h) {
     F(L.K64); F(L.K32);
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
-  F(h->Yq); F(h->Mq); F(h->Mqc);
+  F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv); F(h->Pq);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
@@ -259,6 +259,7 @@ cudaError_t append_solve(tosolve_s* h, cudaStream_t cs, cudaStream_t bs) {
   double* part1 = h->part + kMaxPart;
   double* part2 = h->part + 2 * kMaxPart;
   double* part3 = h->part + 3 * kMaxPart;
+  if (h->mixed) launch_q2_fold(L0, h->slv0, h->f, cs);  // f <- T^T f
   launch_cg_prep(L0, h->f, h->u, part0, np, cs);
   cudaStreamCaptureStatus cst;
   cudaGraph_t cgraph = nullptr;
@@ -294,9 +295,11 @@ cudaError_t append_solve(tosolve_s* h, cudaStream_t cs, cudaStream_t bs) {
     cudaGraph_t bo = nullptr;
     e = cudaStreamEndCapture(bs, &bo);
   }
-  if (e == cudaSuccess)
+  if (e == cudaSuccess) {
     launch_cg_residual(vt, L0, h->d.omega, h->f, h->u, h->tmpa, 2, part1, part0, np, h->ds, h->cnt,
                        hc, 0, cs);
+    if (h->mixed) launch_q2_expand(L0, h->slv0, h->u, cs);  // u <- T u
+  }
   return e;
 }
 
@@ -347,8 +350,8 @@ tosolve_status tosolve_footprint(const tosolve_desc* desc, size_t* bytes) {
   return TOSOLVE_OK;
 }
 
-tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host, void* cuda_stream,
-                              tosolve_t* out) {
+static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_host,
+                                  const uint8_t* elem_q1, void* cuda_stream, tosolve_t* out) {
   if (out == nullptr) { g_err = "out is NULL"; return TOSOLVE_EINVAL; }
   *out = nullptr;
   Plan P;
@@ -398,6 +401,30 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
   cudaStream_t st = h->st;
   // levels and masks
   std::vector<uint8_t> mask(mask_host, mask_host + P.lv[0].ndof);
+  std::vector<uint8_t> slv;
+  if (elem_q1 != nullptr) {  // nodes slaved to their vertices; level 0 treats them as fixed
+    const Plan::Lv& v = P.lv[0];
+    slv.assign(v.nn, 0);
+    for (int ez = 0; ez < v.ez; ++ez)
+      for (int ey = 0; ey < v.ey; ++ey)
+        for (int ex = 0; ex < v.ex; ++ex) {
+          if (!elem_q1[ex + (long)v.ex * (ey + (long)v.ey * ez)]) continue;
+          for (int c = 0; c < 3; ++c)
+            for (int b = 0; b < 3; ++b)
+              for (int a = 0; a < 3; ++a)
+                if ((a | b | c) & 1)
+                  slv[(2 * ex + a) + (long)v.Lx * ((2 * ey + b) + (long)v.Ly * (2 * ez + c))] = 1;
+        }
+    h->mixed = true;
+    CKC(dalloc(h, &h->slv0, v.nn));
+    CKC(cudaMemcpy(h->slv0, slv.data(), v.nn, cudaMemcpyHostToDevice));
+    CKC(dalloc(h, &h->fix0, v.ndof));
+    CKC(cudaMemcpy(h->fix0, mask.data(), v.ndof, cudaMemcpyHostToDevice));
+    for (long nd = 0; nd < v.nn; ++nd)
+      if (slv[nd]) mask[3 * nd] = mask[3 * nd + 1] = mask[3 * nd + 2] = 1;
+  }
+  h->free_dofs = 0;
+  for (uint8_t m : mask) h->free_dofs += m == 0;
   for (int l = 0; l < P.L; ++l) {
     const Plan::Lv& v = P.lv[l];
     Level& L = h->lv[l];
@@ -595,6 +622,24 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
 #undef CKC
 }
 
+tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host, void* cuda_stream,
+                              tosolve_t* out) {
+  return create_impl(desc, mask_host, nullptr, cuda_stream, out);
+}
+
+tosolve_status tosolve_create_mixed(const tosolve_desc* desc, const uint8_t* mask_host,
+                                    const uint8_t* elem_q1_host, void* cuda_stream, tosolve_t* out) {
+  if (desc == nullptr || elem_q1_host == nullptr) { g_err = "NULL argument"; return TOSOLVE_EINVAL; }
+  if (desc->degree != 2) { g_err = "a mixed mesh lives on the degree-2 lattice (degree = 2)"; return TOSOLVE_EINVAL; }
+  return create_impl(desc, mask_host, elem_q1_host, cuda_stream, out);
+}
+
+tosolve_status tosolve_free_dofs(tosolve_t h, long long* n) {
+  if (h == nullptr || n == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
+  *n = h->free_dofs;
+  return TOSOLVE_OK;
+}
+
 void tosolve_destroy(tosolve_t h) {
   if (h == nullptr) return;
   cudaStreamSynchronize(h->st);
@@ -633,6 +678,7 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
       launch_q2_coarse_elem(C, h->w, h->Dx, h->Dy, h->cmom64, h->Mqc, h->Kec, cst);
     } else {
       launch_q2_elem(C, n, h->w, h->Dx, h->Dy, h->tab64, C.K64, cst);
+      if (h->mixed) launch_q2_constrain(C, h->slv0, C.K64, C.sms, cst);
       Kc = C.K64;
     }
     CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), cst));
@@ -642,9 +688,10 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
                             &h->ds->coarse_status, h->cgrid, cst));
     for (int l = 0; l + 1 < L; ++l) {
       Level& Lv = h->lv[l];
-      if (l == 0)
+      if (l == 0) {
         launch_q2_elem(Lv, n, h->w, h->Dx, h->Dy, h->tab64, Lv.K64, st);
-      else
+        if (h->mixed) launch_q2_constrain(Lv, h->slv0, Lv.K64, Lv.sms, st);
+      } else
         launch_q2_coarse_elem(Lv, h->w, h->Dx, h->Dy, h->cmom64, h->Mq, Lv.K64, st);
       launch_q2_dinv(true, Lv, Lv.K64, Lv.dinv64, st);
       if (Lv.K32) {
@@ -721,6 +768,7 @@ static tosolve_status run_loop_nograph(tosolve_t h) {
   double *part0 = h->part, *part1 = h->part + kMaxPart, *part2 = h->part + 2 * kMaxPart,
          *part3 = h->part + 3 * kMaxPart;
   cudaStream_t st = h->st;
+  if (h->mixed) launch_q2_fold(L0, h->slv0, h->f, st);
   launch_cg_prep(L0, h->f, h->u, part0, np, st);
   launch_cg_residual(vt, L0, h->d.omega, h->f, h->u, h->r, 1, part1, part0, np, h->ds, h->cnt, 0, 0,
                      st);
@@ -738,6 +786,7 @@ static tosolve_status run_loop_nograph(tosolve_t h) {
   }
   launch_cg_residual(vt, L0, h->d.omega, h->f, h->u, h->tmpa, 2, part1, part0, np, h->ds, h->cnt, 0,
                      0, st);
+  if (h->mixed) launch_q2_expand(L0, h->slv0, h->u, st);
   return TOSOLVE_OK;
 }
 
@@ -844,7 +893,8 @@ tosolve_status tosolve_compliance_grad(tosolve_t h, const double* u_dev, const d
   double* gt = h->gtmp + h->ncell;
   const bool want_grad = dcdx_dev != nullptr || dcdrho_dev != nullptr;
   for (int r = 0; r < nrhs; ++r) {
-    launch_compliance(h->lv[0], f_dev + r * nd, u_dev + r * nd, h->part, h->np, h->ds, st);
+    launch_compliance(h->lv[0], h->mixed ? h->fix0 : h->lv[0].mask, f_dev + r * nd, u_dev + r * nd,
+                      h->part, h->np, h->ds, st);
     CK(cudaMemcpyAsync(&h->hs->c, &h->ds->c, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c_host[r] = h->hs->c;

@@ -74,6 +74,8 @@ def _load():
     sigs = {
         "tosolve_create": ([P(tosolve_desc), vp, vp, P(vp)], i),
         "tosolve_footprint": ([P(tosolve_desc), P(sz)], i),
+        "tosolve_create_mixed": ([P(tosolve_desc), vp, vp, vp, P(vp)], i),
+        "tosolve_free_dofs": ([vp, P(C.c_longlong)], i),
         "tosolve_set_densities": ([vp, vp], i),
         "tosolve_solve": ([vp, vp, i, vp, d, i, P(tosolve_info)], i),
         "tosolve_compliance_grad": ([vp, vp, vp, i, P(d), vp, vp], i),
@@ -149,6 +151,24 @@ def tosolve_create(desc: tosolve_desc, mask: np.ndarray, stream=None) -> int:
     _check(None, _lib.tosolve_create(C.byref(desc), mask.ctypes.data, st, C.byref(h)),
            "tosolve_create")
     return h.value
+
+
+def tosolve_create_mixed(desc: tosolve_desc, mask: np.ndarray, elem_q1: np.ndarray, stream=None) -> int:
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    q1 = np.ascontiguousarray(elem_q1, dtype=np.uint8)
+    h = C.c_void_p(0)
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    _check(None, _lib.tosolve_create_mixed(C.byref(desc), mask.ctypes.data, q1.ctypes.data, st,
+                                           C.byref(h)), "tosolve_create_mixed")
+    return h.value
+
+
+def tosolve_free_dofs(h) -> int:
+    n = C.c_longlong(0)
+    _check(h, _lib.tosolve_free_dofs(h, C.byref(n)), "tosolve_free_dofs")
+    return n.value
 
 
 def tosolve_destroy(h) -> None:
@@ -312,9 +332,10 @@ class Solver:
     """Owns one handle; a convenience wrapper used by the tests and the
     benchmark (each method is one ABI call)."""
 
-    def __init__(self, desc: tosolve_desc, mask: np.ndarray, stream=None):
+    def __init__(self, desc: tosolve_desc, mask: np.ndarray, stream=None, elem_q1=None):
         self.desc = desc
-        self.h = tosolve_create(desc, mask, stream)
+        self.h = (tosolve_create(desc, mask, stream) if elem_q1 is None
+                  else tosolve_create_mixed(desc, mask, elem_q1, stream))
 
     def close(self):
         if self.h:

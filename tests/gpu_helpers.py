@@ -31,7 +31,8 @@ class Run:
         self.p = p
         self.dev = torch.device("cuda:0")
         self.stream = torch.cuda.Stream()
-        self.solver = T.Solver(desc_for(T, p, precision, levels, max_rhs), p.mask, self.stream)
+        self.solver = T.Solver(desc_for(T, p, precision, levels, max_rhs), p.mask, self.stream,
+                               elem_q1=getattr(p, "elem_q1", None))
         self.h = self.solver.h
         self.x = torch.tensor(p.x, device=self.dev)
         f = np.array(p.f, dtype=np.float64)
