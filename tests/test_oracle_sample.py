@@ -1,0 +1,44 @@
+"""The sampled oracle (oracle/sample.py) against the whole-mesh oracle on
+meshes small enough for both: every sampled row or cell must equal the
+corresponding entry of the assembled computation to FP64 rounding."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads
+from oracle import fe, mixed, sample
+
+
+@pytest.mark.parametrize("k,n,rmin", [(1, 2, 1.0), (2, 3, 0.7), (1, 1, 0.0)])
+def test_sampled_rows_and_cells_equal_the_whole_mesh(k, n, rmin):
+    p = workloads.cantilever(4, 3, 2, degree=k, n_mr=n, rmin=rmin, seed=3)
+    m = fe.Model(p)
+    S = sample.Sampler(p)
+    rng = np.random.default_rng(0)
+    u = rng.normal(size=p.ndof)
+    rho = m.densities(p.x)
+    y = m.apply(m.weights(rho), u).reshape(-1, 3)
+    nodes = list(range(p.nnodes))
+    ys = S.apply_rows(p.x, u, nodes)
+    assert np.abs(ys - y).max() <= 1e-13 * np.abs(y).max()
+    cells = rng.choice(p.x.size, size=12, replace=False)
+    np.testing.assert_allclose([S.rho(p.x, c) for c in cells], rho[cells], rtol=1e-14)
+    g = m.density_gradient(rho, m.subcell_energies(u))
+    gx = m.design_gradient(g)
+    np.testing.assert_allclose([S.drho(p.x, u, c) for c in cells], g[cells], rtol=1e-12)
+    np.testing.assert_allclose([S.dx(p.x, u, c) for c in cells], gx[cells], rtol=1e-12)
+
+
+def test_sampled_rows_of_a_mixed_mesh():
+    q = workloads.with_mixed_degree(workloads.bridge(4, 2, 2, degree=2, n_mr=2, seed=1), 0.5, 5)
+    m = mixed.MixedModel(q)
+    S = sample.Sampler(q)
+    u = np.random.default_rng(1).normal(size=q.ndof)
+    w = m.weights(m.densities(q.x))
+    A = (m.T.T @ m.assemble(w) @ m.T).tocsr()
+    held = (q.mask != 0) | m.slaved
+    keep = sp.diags((~held).astype(float))
+    A = keep @ A @ keep + sp.diags(held.astype(float))
+    y = (A @ u).reshape(-1, 3)
+    ys = S.apply_rows(q.x, u, list(range(q.nnodes)))
+    assert np.abs(ys - y).max() <= 1e-13 * np.abs(y).max()
