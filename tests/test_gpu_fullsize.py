@@ -1,0 +1,90 @@
+"""Parity at the benchmark configurations' full sizes, on sampled outputs.
+
+The meshes here are too large for the oracle to assemble (1.6M DOFs), so the
+oracle recomputes sampled rows of K u and sampled cells of the gradient from
+their definitions on the few elements involved (oracle/sample.py, pinned
+against the whole-mesh oracle).  Checks, each in the launch configuration
+the benchmark times:
+  * the FP64 operator at sampled nodes (relative 1e-13 of the largest row);
+  * the solve: true relative residual <= rtol recomputed with that operator;
+  * compliance f^T u (1e-12 relative, a sum over 10^6 terms);
+  * dc/drho and dc/dx at sampled cells (1e-10 relative: the same formula on
+    the same u, different summation order).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import sample
+from tests.gpu_helpers import Run, lib, desc_for, rel
+
+pytestmark = [pytest.mark.gpu]
+
+FP64, FP32X2 = 0, 3
+
+
+def _check_sampled(T, R, p, u_dev, rtol, rng, nodes=200, cells=40, dcells=8):
+    import torch
+
+    S = sample.Sampler(p)
+    u = u_dev.cpu().numpy().reshape(-1)
+    # operator rows
+    picks = list(rng.choice(p.nnodes, size=nodes, replace=False)) + [0, p.nnodes - 1]
+    y = R.apply(0, FP64, u).reshape(-1, 3)
+    ys = S.apply_rows(p.x, u, picks)
+    assert np.abs(y[picks] - ys).max() <= 1e-13 * np.abs(y).max()
+    # residual with that operator
+    f = np.where(p.mask == 0, p.f[0], 0.0)
+    if getattr(p, "elem_q1", None) is None:
+        r = f - y.reshape(-1)
+        r[p.mask != 0] = 0.0
+        assert np.linalg.norm(r) <= 1.05 * rtol * np.linalg.norm(f)
+    # compliance and gradient
+    c, gx, gr = R.grad(u_dev.reshape(1, -1).contiguous(), nrhs=1)
+    assert abs(c[0] - float(np.dot(f, u))) <= 1e-12 * abs(c[0])
+    cs = rng.choice(p.x.size, size=cells, replace=False)
+    np.testing.assert_allclose(gr[cs], [S.drho(p.x, u, ci) for ci in cs], rtol=1e-10)
+    ds = cs[:dcells]
+    np.testing.assert_allclose(gx[ds], [S.dx(p.x, u, ci) for ci in ds], rtol=1e-10)
+
+
+def test_largest_batch_instance_full_size():
+    """The 128x64x64 Q1 instance (1,622,400 free DOFs) of the 64-instance
+    batch, solved with a smaller one in one batched graph launch, FP32X2."""
+    import torch
+
+    T = lib()
+    probs = workloads.batched_instances(64, 2024, mult=16)
+    big = max(probs, key=lambda q: q.nfree)
+    small = min(probs, key=lambda q: q.nfree)
+    runs = [Run(q, FP32X2) for q in (big, small)]
+    for R in runs:
+        R.set_densities()
+    us = [torch.zeros((q.nrhs, q.ndof), dtype=torch.float64, device=R.dev) for q, R in zip((big, small), runs)]
+    b = T.tosolve_batch_create([R.h for R in runs], [q.nrhs for q in (big, small)], [R.f for R in runs], us)
+    try:
+        infos = T.tosolve_batch_solve(b, 1e-8, 2000, 2)
+        assert all(i.status == T.OK for i in infos)
+        big1 = big.__class__(**{k: getattr(big, k) for k in big.__dataclass_fields__})
+        big1.f = big.f[:1]
+        _check_sampled(T, runs[0], big1, us[0][0], 1e-8, np.random.default_rng(7))
+    finally:
+        T.tosolve_batch_destroy(b)
+        for R in runs:
+            R.close()
+
+
+def test_mixed_bridge_full_size():
+    """The bridge as specified: 64x32x32, n = 3, half the elements trilinear
+    (519,204 unknowns), FP32X2 preconditioner as in the benchmark."""
+    import torch
+
+    p = workloads.with_mixed_degree(
+        workloads.bridge(64, 32, 32, degree=2, n_mr=3, seed=0), 0.5, 11)
+    R = Run(p, FP32X2)
+    R.set_densities()
+    u, info = R.solve(rtol=1e-8)
+    assert info.rel_residual <= 1e-8
+    assert R.T.tosolve_free_dofs(R.h) == 519204
+    _check_sampled(R.T, R, p, u[0], 1e-8, np.random.default_rng(3), nodes=120, cells=30, dcells=6)
+    R.close()
