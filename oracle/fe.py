@@ -36,7 +36,8 @@ class Model:
         self.Ktab = fem.subcell_stiffness(k, n, prob.nu)  # (m, d, d)
         self.edofs = mesh.element_dofs(prob.nx, prob.ny, prob.nz, k)
         self.sub2cell = mesh.subcell_density_index(prob.nx, prob.ny, prob.nz, n)
-        self.H = filt.filter_matrix(prob.density_shape, n, prob.rmin)
+        d = getattr(prob, "d_mr", None) or n
+        self.H = filt.projection_matrix(prob.nx, prob.ny, prob.nz, n, d, prob.rmin)
         self.ndof = prob.ndof
         self.free = np.nonzero(prob.mask == 0)[0]
 

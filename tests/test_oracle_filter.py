@@ -12,6 +12,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 from oracle import filt
 
@@ -49,3 +50,55 @@ def test_rows_sum_to_one_and_transpose_preserves_sums():
 def test_zero_radius_is_identity():
     H = filt.filter_matrix((2, 3, 4), 1, 0.0)
     assert np.array_equal(H.toarray(), np.identity(24))
+
+
+def test_projection_equals_filter_on_the_density_grid():
+    from oracle import filt
+
+    P = filt.projection_matrix(3, 2, 2, 2, 2, 1.5)
+    F = filt.filter_matrix((4, 4, 6), 2, 1.5)
+    assert abs(P - F).max() == 0.0
+
+
+@pytest.mark.parametrize("n,d,r", [(3, 2, 0.6), (2, 1, 0.9), (4, 2, 0.6)])
+def test_projection_rows_are_weighted_averages(n, d, r):
+    from oracle import filt
+
+    P = filt.projection_matrix(3, 2, 2, n, d, r)
+    assert P.shape == (n ** 3 * 12, d ** 3 * 12)
+    np.testing.assert_allclose(np.asarray(P.sum(axis=1)).ravel(), 1.0, rtol=0, atol=1e-15)
+    assert P.min() >= 0.0
+
+
+def test_projection_with_a_small_radius_takes_the_containing_design_cell():
+    """d = 1, n = 2, r = 0.5: a density cell's own element centre is
+    sqrt(3)/4 = 0.433 away, every other element centre at least 0.83."""
+    from oracle import filt
+
+    nx, ny, nz = 3, 2, 2
+    P = filt.projection_matrix(nx, ny, nz, 2, 1, 0.5).toarray()
+    for c in range(P.shape[0]):
+        cx, cy, cz = c % 6, (c // 6) % 4, c // 24
+        e = cx // 2 + nx * (cy // 2 + ny * (cz // 2))
+        row = np.zeros(P.shape[1])
+        row[e] = 1.0
+        np.testing.assert_array_equal(P[c], row)
+
+
+def test_gradient_through_a_coarser_design_grid_matches_finite_differences():
+    import workloads
+    from oracle import fe
+
+    p = workloads.with_design_grid(workloads.cantilever(3, 2, 2, n_mr=2, rmin=0.8, seed=1), 1, 4,
+                                   lo=0.3, hi=0.9)
+    m = fe.Model(p)
+    out = m.run(method="dense")
+    g = out["g_x"]
+    assert g.size == p.x.size == 12
+    h = 1e-6
+    for j in range(0, 12, 3):
+        xp, xm = p.x.copy(), p.x.copy()
+        xp[j] += h * p.x[j]
+        xm[j] -= h * p.x[j]
+        fd = (m.run(x=xp, method="dense")["c"][0] - m.run(x=xm, method="dense")["c"][0]) / (2 * h * p.x[j])
+        assert abs(fd - g[j]) <= 1e-6 * abs(g[j])

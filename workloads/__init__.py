@@ -70,6 +70,8 @@ class Problem:
     meta: dict = field(default_factory=dict)
     # mixed degree (degree-2 lattice): uint8 per element, 1 = trilinear
     elem_q1: np.ndarray | None = None
+    # design cells per element edge (None: the density grid, d_mr = n_mr)
+    d_mr: int | None = None
 
     @property
     def lattice(self) -> tuple[int, int, int]:
@@ -272,4 +274,17 @@ def with_mixed_degree(p: Problem, q1_fraction: float, seed: int) -> Problem:
     q.elem_q1 = (rng.random(E) < q1_fraction).astype(np.uint8)
     q.name = p.name + f"_mixed{q1_fraction:g}"
     q.meta = dict(p.meta, q1_fraction=q1_fraction, degree_seed=seed)
+    return q
+
+
+def with_design_grid(p: Problem, d_mr: int, seed: int, lo: float = 0.01, hi: float = 1.0) -> Problem:
+    """The same problem with a coarser design grid (d_mr design cells per
+    element edge) and new design variables iid U[lo, hi] on it."""
+    if not 1 <= d_mr <= p.n_mr:
+        raise ValueError("need 1 <= d_mr <= n_mr")
+    rng = np.random.default_rng(seed)
+    q = p.__class__(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    q.d_mr = d_mr
+    q.x = uniform_field((d_mr * p.nz, d_mr * p.ny, d_mr * p.nx), lo, hi, rng)
+    q.name = p.name + f"_d{d_mr}"
     return q
