@@ -576,18 +576,20 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-SERVE = dict(name="serve256_q1_density_64x32x32_to_384x192x192_poisson200", designs=256,
-             rate=200.0, requests=2000, seed=77, rtol=1e-8, budget_gib=200, rmin=1.5)
+SERVE = dict(name="serve256_q1q2_density_64x32x32_to_384x192x192_poisson200", designs=256,
+             rate=200.0, requests=2000, seed=77, rtol=1e-8, budget_gib=240, rmin=1.5)
 
 
 def serve_designs(count: int, seed: int):
     """Live designs of the serving workload: density size s * (64, 32, 32)
     with ln s ~ N(ln 2, 0.5) truncated to [1, 6]; n in {1, 2, 3} uniform;
-    displacement mesh = density / n rounded to a multiple of 16, 32 or 64
-    (x; half that in y, z) so that it coarsens to a small dense coarsest
-    level; Q1 (degree 2 is not built yet); cantilever supports and line
-    load; a smooth initial design field; density filter radius 1.5 (the
-    SLP method always filters its design variables)."""
+    degree k in {1, 2} uniform (degree 2 with n = 3, the coarser displacement
+    mesh that higher degree is paired with: a degree-2 mesh as fine as the
+    density grid would not fit the device); displacement mesh =
+    density / n rounded so that it coarsens to a small dense coarsest level;
+    cantilever supports and line load; a smooth initial design field;
+    density filter radius 1.5 (the SLP method always filters its design
+    variables)."""
     import numpy as np
 
     import workloads
@@ -599,13 +601,16 @@ def serve_designs(count: int, seed: int):
             sc = float(np.exp(rng.normal(np.log(2.0), 0.5)))
             if 1.0 <= sc <= 6.0:
                 break
-        n = int(rng.integers(1, 4))
+        deg = int(rng.integers(1, 3))
+        n = int(rng.integers(1, 4)) if deg == 1 else 3
         raw = 64 * sc / n
         mult = 16 if raw <= 128 else (32 if raw <= 256 else 64)  # coarsest level stays small
-        nx = max(16, int(round(raw / mult)) * mult)
-        p = workloads.cantilever(nx, nx // 2, nx // 2, n_mr=n, rmin=SERVE["rmin"], density="smooth",
-                                 seed=int(rng.integers(1 << 31)))
-        p.name = f"design{k}_{nx}x{nx // 2}x{nx // 2}_n{n}"
+        if deg == 2:  # 8x the lattice nodes of a degree-1 mesh: one more level
+            mult = 16 if raw <= 64 else (32 if raw <= 128 else 64)
+        nx = max(mult, int(round(raw / mult)) * mult)
+        p = workloads.cantilever(nx, nx // 2, nx // 2, degree=deg, n_mr=n, rmin=SERVE["rmin"],
+                                 density="smooth", seed=int(rng.integers(1 << 31)))
+        p.name = f"design{k}_{nx}x{nx // 2}x{nx // 2}_k{deg}_n{n}"
         out.append(p)
     return out
 
@@ -634,7 +639,7 @@ def run_serve(args):
                        "offered_rate_per_s": SERVE["rate"], "slots": args.slots,
                        "hbm_budget_gib": SERVE["budget_gib"], "rtol": SERVE["rtol"],
                        "rmin": SERVE["rmin"],
-                       "degree": "Q1 only (degree 2 not built)",
+                       "degree": "k in {1, 2}; degree 2 with n = 3",
                        "free_dofs_range": [min(p.nfree for p in probs),
                                            max(p.nfree for p in probs)]}}
     sampler = ClockSampler(0)
@@ -643,8 +648,8 @@ def run_serve(args):
         srv = T.tosolve_server_create(args.slots, budget, SERVE["rtol"], 2000)
         try:
             for k, p in enumerate(probs):
-                d = T.make_desc(p.nx, p.ny, p.nz, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin, nu=p.nu,
-                                penal=p.penal, precision=prec, max_rhs=p.nrhs)
+                d = T.make_desc(p.nx, p.ny, p.nz, degree=p.degree, n_mr=p.n_mr, rmin=p.rmin,
+                                Emin=p.Emin, nu=p.nu, penal=p.penal, precision=prec, max_rhs=p.nrhs)
                 T.tosolve_server_add_design(srv, k, d, p.mask, np.asarray(p.f), p.nrhs)
             xs = [np.array(p.x) for p in probs]
             # warm-up (untimed): every design served once, so the timed phase

@@ -12,11 +12,13 @@
  *
  * Mesh and numbering (shared by every call):
  *   * nx*ny*nz cubic displacement elements of edge 1 (Sec. 7.1);
- *   * Lagrange degree k = 1: node lattice (nx+1)*(ny+1)*(nz+1),
+ *   * Lagrange degree k (1 or 2): node lattice (k*nx+1)*(k*ny+1)*(k*nz+1),
  *     node id = i + Lx*(j + Ly*l) (x fastest), DOF = 3*node + component;
- *   * each element holds n_mr^3 density cells (Sec. 3.1); the density grid
- *     and the design grid (d_mr = n_mr) are (n_mr*nx)*(n_mr*ny)*(n_mr*nz)
- *     cells, flattened x fastest;
+ *   * each element holds n_mr^3 density cells (Sec. 3.1): the density grid
+ *     is (n_mr*nx)*(n_mr*ny)*(n_mr*nz) cells, flattened x fastest; the
+ *     design grid (x and dc/dx) is the same with d_mr in place of n_mr;
+ *     d_mr < n_mr projects x onto the densities with the filter weights
+ *     between cell centres of the two grids (Sec. 3.2, Eq. projdsgn);
  *   * the Dirichlet mask has one byte per DOF, 1 = fixed (u = 0 there).
  *
  * Conventions of every call:
@@ -78,7 +80,8 @@ typedef struct {
   int nx, ny, nz;         /* displacement elements per axis, >= 1           */
   int degree;             /* Lagrange degree k: 1 or 2                      */
   int n_mr;               /* density cells per element edge, 1..8           */
-  int d_mr;               /* design cells per element edge; must equal n_mr */
+  int d_mr;               /* design cells per element edge, 1..n_mr (0 =   */
+                          /* n_mr); below n_mr rmin must be > 0            */
   double E0, Emin;        /* SIMP: E(rho) = Emin + rho^p (E0 - Emin), Eq.   */
   double nu;              /*   matrixK; Poisson ratio nu in (-1, 0.5)       */
   double penal;           /*   penalty p >= 1                               */

@@ -132,6 +132,21 @@ class Sampler:
         r = self.rho(x, cell)
         return -self.p.penal * r ** (self.p.penal - 1.0) * (self.p.E0 - self.p.Emin) * s
 
+    def drho_scale(self, x, u, cell):
+        """|dc/drho| scale of the rounding of the quadratic form at a cell:
+        p rho^(p-1) (E0 - Emin) sum_ab |K_ab u_a u_b|.  Two FP64 evaluations
+        of u_e^T K^(e_i) u_e in different orders differ by a small multiple
+        of eps times this (much more than eps |dc/drho| where u_e is close
+        to a rigid motion and the terms cancel)."""
+        n = self.n
+        cx, cy, cz = cell % self.Dx, (cell // self.Dx) % self.Dy, cell // (self.Dx * self.Dy)
+        ex, ey, ez = cx // n, cy // n, cz // n
+        i = (cx % n) + n * ((cy % n) + n * (cz % n))
+        en = self._elem_nodes(ex, ey, ez)
+        ue = np.abs(u[np.array([3 * m + c for m in en for c in range(3)])])
+        r = self.rho(x, cell)
+        return self.p.penal * r ** (self.p.penal - 1.0) * (self.p.E0 - self.p.Emin) * (ue @ np.abs(self.K[i]) @ ue)
+
     def dx(self, x, u, cell):
         """dc/dx at one design cell: sum over the ball of w_ji / omega_j * dc/drho_j."""
         cx, cy, cz = cell % self.Dx, (cell // self.Dx) % self.Dy, cell // (self.Dx * self.Dy)

@@ -117,6 +117,14 @@ struct OpOf<dfloat> { using type = float; };
 template <typename T>
 using op_t = typename OpOf<T>::type;
 
+// Density grid (Dx, Dy, Dz; n cells per element edge) and a coarser design
+// grid (Gx, Gy, Gz; d per edge) of the projection, radius r in element
+// units; R bounds the design-cell offsets a density cell can reach.
+struct ProjGrid {
+  int Dx, Dy, Dz, Gx, Gy, Gz, n, d, R;
+  double r;
+};
+
 // Read-only view of a level's operator for the kernels.
 template <typename T>
 struct LevelView {
@@ -129,6 +137,10 @@ struct LevelView {
 };
 
 // ---- launchers (k_setup.cu) ----------------------------------------------
+void launch_proj_init(const ProjGrid& P, double* invom, cudaStream_t st);
+void launch_proj_fwd(const ProjGrid& P, const double* invom, const double* x, double Emin, double dE,
+                     double penal, double* rho, double* w, cudaStream_t st);
+void launch_proj_T(const ProjGrid& P, const double* gt, double* gx, cudaStream_t st);
 void launch_subcell_table(int n, double nu, double h, double* tab, cudaStream_t st);
 void launch_symmetrize(int m, const double* tab, double* tabsym, cudaStream_t st);
 void launch_moment_basis(double nu, double* cmom, cudaStream_t st);
@@ -297,6 +309,9 @@ struct tosolve_s {
   double* Mq = nullptr;        // degree 2: moments of the finer coarse levels
   double* Mqc = nullptr;       // degree 2: moments of the coarsest level
   // mixed trilinear / triquadratic mesh (degree-2 lattice)
+  bool proj = false;           // design grid coarser than the density grid
+  tos::ProjGrid pg = {};
+  long ndes = 0;               // design variables
   bool mixed = false;
   long long free_dofs = 0;     // unknowns: DOFs neither supported nor slaved
   uint8_t* slv0 = nullptr;     // per lattice node: 1 = slaved to its vertices

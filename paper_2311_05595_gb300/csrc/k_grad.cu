@@ -73,6 +73,36 @@ __global__ void k_filter_T(int Dx, int Dy, int Dz, int noff, const int4* __restr
   }
 }
 
+// (P^T gt)_j for the design-grid projection: sum over the density cells i
+// within r of design cell j of wt(dist) * gt_i, gt = g / w_i (gather form,
+// fixed order).  The neighbour decision rounds as in the forward kernel.
+__device__ __forceinline__ double pdist2(int jx, int jy, int jz, int d, int cx, int cy, int cz, int n) {
+  const double tx = __dsub_rn(__ddiv_rn(jx + 0.5, (double)d), __ddiv_rn(cx + 0.5, (double)n));
+  const double ty = __dsub_rn(__ddiv_rn(jy + 0.5, (double)d), __ddiv_rn(cy + 0.5, (double)n));
+  const double tz = __dsub_rn(__ddiv_rn(jz + 0.5, (double)d), __ddiv_rn(cz + 0.5, (double)n));
+  return __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)), __dmul_rn(tz, tz));
+}
+
+__global__ void k_proj_T(ProjGrid P, const double* __restrict__ gt, double* __restrict__ gx) {
+  const long G = (long)P.Gx * P.Gy * P.Gz;
+  const int Rn = (int)ceil(P.r * P.n) + 1;
+  const double r2 = P.r * P.r * (1.0 + 1e-12), s2 = 2.0 * (P.r / 3.0) * (P.r / 3.0);
+  for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < G; j += (long)gridDim.x * blockDim.x) {
+    const int jx = j % P.Gx, jy = (j / P.Gx) % P.Gy, jz = j / ((long)P.Gx * P.Gy);
+    const int bx = (int)floor((jx + 0.5) / P.d * P.n - 0.5), by = (int)floor((jy + 0.5) / P.d * P.n - 0.5),
+              bz = (int)floor((jz + 0.5) / P.d * P.n - 0.5);
+    double s = 0.0;
+    for (int cz = max(bz - Rn, 0); cz <= min(bz + Rn + 1, P.Dz - 1); ++cz)
+      for (int cy = max(by - Rn, 0); cy <= min(by + Rn + 1, P.Dy - 1); ++cy)
+        for (int cx = max(bx - Rn, 0); cx <= min(bx + Rn + 1, P.Dx - 1); ++cx) {
+          const double q = pdist2(jx, jy, jz, P.d, cx, cy, cz, P.n);
+          if (q > r2) continue;
+          s += exp(-q / s2) * gt[cx + (long)P.Dx * (cy + (long)P.Dy * cz)];
+        }
+    gx[j] = s;
+  }
+}
+
 __device__ __forceinline__ double block_sum_g(double v) {
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -121,6 +151,10 @@ void launch_energy_grad(const Level& L0, int n, const double* u, const double* t
 
 void launch_scale(size_t n, const double* a, const double* s, double* out, cudaStream_t st) {
   k_scale<<<grid_for((long)n), kBS, 0, st>>>(n, a, s, out);
+}
+
+void launch_proj_T(const ProjGrid& P, const double* gt, double* gx, cudaStream_t st) {
+  k_proj_T<<<grid_for((long)P.Gx * P.Gy * P.Gz), kBS, 0, st>>>(P, gt, gx);
 }
 
 void launch_filter_T(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,

@@ -129,6 +129,55 @@ __global__ void k_filter_init(int Dx, int Dy, int Dz, int noff, const int4* __re
   }
 }
 
+// Projection from a coarser design grid (Eq. projdsgn, d_mr < n_mr): the
+// filter weights between density-cell centres (c + 1/2) / n and design-cell
+// centres (j + 1/2) / d, in element units, neighbours at dist <= r.  The
+// squared distance is formed with explicit rounding (no fused operations)
+// in the same order as the definition, so the neighbour decision is the
+// same as a plain FP64 evaluation of it.
+__device__ __forceinline__ double cell_dist2(int jx, int jy, int jz, int d, int cx, int cy, int cz, int n) {
+  const double tx = __dsub_rn(__ddiv_rn(jx + 0.5, (double)d), __ddiv_rn(cx + 0.5, (double)n));
+  const double ty = __dsub_rn(__ddiv_rn(jy + 0.5, (double)d), __ddiv_rn(cy + 0.5, (double)n));
+  const double tz = __dsub_rn(__ddiv_rn(jz + 0.5, (double)d), __ddiv_rn(cz + 0.5, (double)n));
+  return __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)), __dmul_rn(tz, tz));
+}
+
+// Sum over the design cells within r of density cell c of wt(dist) * v_j
+// (v = nullptr: of wt alone).
+__device__ __forceinline__ double proj_row(const ProjGrid& P, long c, const double* __restrict__ v) {
+  const int cx = c % P.Dx, cy = (c / P.Dx) % P.Dy, cz = c / ((long)P.Dx * P.Dy);
+  const int bx = (int)floor((cx + 0.5) / P.n * P.d - 0.5), by = (int)floor((cy + 0.5) / P.n * P.d - 0.5),
+            bz = (int)floor((cz + 0.5) / P.n * P.d - 0.5);
+  const double r2 = P.r * P.r * (1.0 + 1e-12), s2 = 2.0 * (P.r / 3.0) * (P.r / 3.0);
+  double s = 0.0;
+  for (int jz = max(bz - P.R, 0); jz <= min(bz + P.R + 1, P.Gz - 1); ++jz)
+    for (int jy = max(by - P.R, 0); jy <= min(by + P.R + 1, P.Gy - 1); ++jy)
+      for (int jx = max(bx - P.R, 0); jx <= min(bx + P.R + 1, P.Gx - 1); ++jx) {
+        const double q = cell_dist2(jx, jy, jz, P.d, cx, cy, cz, P.n);
+        if (q > r2) continue;
+        const double wt = exp(-q / s2);
+        s += v ? wt * v[jx + (long)P.Gx * (jy + (long)P.Gy * jz)] : wt;
+      }
+  return s;
+}
+
+__global__ void k_proj_init(ProjGrid P, double* __restrict__ invom) {
+  const long N = (long)P.Dx * P.Dy * P.Dz;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x)
+    invom[c] = 1.0 / proj_row(P, c, nullptr);
+}
+
+__global__ void k_proj_fwd(ProjGrid P, const double* __restrict__ invom, const double* __restrict__ x,
+                           double Emin, double dE, double penal, double* __restrict__ rho,
+                           double* __restrict__ w) {
+  const long N = (long)P.Dx * P.Dy * P.Dz;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
+    const double r = proj_row(P, c, x) * invom[c];
+    rho[c] = r;
+    w[c] = Emin + pow(r, penal) * dE;
+  }
+}
+
 // rho_i = sum_j (w_ij / w_i) x_j (Eq. filter_weights / projdsgn) and the
 // SIMP weight w_i = Emin + rho_i^p (E0 - Emin) (Eq. matrixK), fused.
 __global__ void k_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* __restrict__ off,
@@ -628,6 +677,15 @@ void launch_moment_basis(double nu, double* cmom, cudaStream_t st) {
 void launch_filter_init(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,
                         double* invom, cudaStream_t st) {
   k_filter_init<<<grid_for((long)Dx * Dy * Dz), kBS, 0, st>>>(Dx, Dy, Dz, noff, off, wgt, invom);
+}
+
+void launch_proj_init(const ProjGrid& P, double* invom, cudaStream_t st) {
+  k_proj_init<<<grid_for((long)P.Dx * P.Dy * P.Dz), kBS, 0, st>>>(P, invom);
+}
+
+void launch_proj_fwd(const ProjGrid& P, const double* invom, const double* x, double Emin, double dE,
+                     double penal, double* rho, double* w, cudaStream_t st) {
+  k_proj_fwd<<<grid_for((long)P.Dx * P.Dy * P.Dz), kBS, 0, st>>>(P, invom, x, Emin, dE, penal, rho, w);
 }
 
 void launch_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* off, const double* wgt,

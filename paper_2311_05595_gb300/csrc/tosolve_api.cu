@@ -51,6 +51,8 @@ struct Plan {
   int n = 1, m = 1;
   int Dx = 0, Dy = 0, Dz = 0;
   long ncell = 0;
+  int dm = 1;     // design cells per element edge
+  long ndes = 0;  // design variables
   struct Lv {
     int ex, ey, ez, Lx, Ly, Lz;
     long nn, ndof;
@@ -94,7 +96,11 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if ((long)d.nx * d.ny * d.nz > (1L << 28)) { *why = "mesh too large"; return TOSOLVE_EINVAL; }
   if (d.degree != 1 && d.degree != 2) { *why = "Lagrange degree must be 1 or 2"; return TOSOLVE_EINVAL; }
   if (d.n_mr < 1 || d.n_mr > 8) { *why = "n_mr must be in 1..8"; return TOSOLVE_EINVAL; }
-  if (d.d_mr != 0 && d.d_mr != d.n_mr) { *why = "d_mr must equal n_mr"; return TOSOLVE_EINVAL; }
+  if (d.d_mr != 0 && (d.d_mr < 1 || d.d_mr > d.n_mr)) { *why = "d_mr must be in 1..n_mr"; return TOSOLVE_EINVAL; }
+  if (d.d_mr != 0 && d.d_mr != d.n_mr && !(d.rmin > 0.0)) {
+    *why = "a coarser design grid (d_mr < n_mr) needs a projection radius rmin > 0";
+    return TOSOLVE_EINVAL;
+  }
   if (!(d.E0 > 0.0) || !(d.Emin > 0.0) || d.Emin > d.E0) { *why = "need 0 < Emin <= E0"; return TOSOLVE_EINVAL; }
   if (!(d.nu > -1.0 && d.nu < 0.5)) { *why = "nu must be in (-1, 0.5)"; return TOSOLVE_EINVAL; }
   if (!(d.penal >= 1.0)) { *why = "penal must be >= 1"; return TOSOLVE_EINVAL; }
@@ -130,6 +136,8 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   P->Dy = d.n_mr * d.ny;
   P->Dz = d.n_mr * d.nz;
   P->ncell = (long)P->Dx * P->Dy * P->Dz;
+  P->dm = d.d_mr != 0 ? d.d_mr : d.n_mr;
+  P->ndes = (long)P->dm * P->dm * P->dm * d.nx * d.ny * d.nz;
   P->noff = count_offsets(d.n_mr, d.rmin);
   const bool fp32 = d.precision != TOSOLVE_PREC_FP64;
   const bool tf32 = d.precision == TOSOLVE_PREC_TF32 && L > 1;
@@ -185,7 +193,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   B += (size_t)(3 * nc * nc + nc * kNB + nblk * kNB * kNB + (size_t)coarse_qchunks((int)nc) * nc * nc) * 8;
   B += (size_t)ndof0 * 8 * 7;                         // u r p q f tmpa tmpb
   B += (size_t)ndof0 * 8 * 2 * maxrhs;                // host-step staging f, u
-  B += 4 * kMaxPart * 8 + sizeof(DevState) + (size_t)P->ncell * 8;
+  B += 4 * kMaxPart * 8 + sizeof(DevState) + (size_t)P->ndes * 8 * 2;
   if (tf32) {
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
     B += E0 * (P->m + 24) * 4 + (size_t)P->m * 576 * 4 + P->lv[0].ndof * 4;
@@ -365,7 +373,8 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   if (h->d.omega == 0.0) h->d.omega = 0.5;
   if (h->d.cycle_gamma == 0) h->d.cycle_gamma = 1;
   if (h->d.max_rhs == 0) h->d.max_rhs = 1;
-  h->d.d_mr = h->d.n_mr;
+  h->d.d_mr = P.dm;
+  h->ndes = P.ndes;
   h->d.mg_levels = P.L;
   h->L = P.L;
   h->m = P.m;
@@ -539,7 +548,14 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   CKC(dalloc(h, &h->w, P.ncell));
   CKC(dalloc(h, &h->invom, P.ncell));
   CKC(dalloc(h, &h->gtmp, 2 * P.ncell));
-  launch_filter_init(P.Dx, P.Dy, P.Dz, h->noff, h->foff, h->fwgt, h->invom, st);
+  if (P.dm != P.n) {  // Eq. projdsgn from the coarser design grid
+    h->proj = true;
+    h->pg = ProjGrid{P.Dx, P.Dy, P.Dz, P.dm * h->d.nx, P.dm * h->d.ny, P.dm * h->d.nz, P.n, P.dm,
+                     (int)std::ceil(h->d.rmin * P.dm) + 1, h->d.rmin};
+    launch_proj_init(h->pg, h->invom, st);
+  } else {
+    launch_filter_init(P.Dx, P.Dy, P.Dz, h->noff, h->foff, h->fwgt, h->invom, st);
+  }
   {
     // levels refreshed on the main stream (all but the coarsest, or the one
     // level) share one slab scratch; the coarsest level has its own
@@ -605,10 +621,10 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   h->np = parts_for(h->lv[0].nn);
   // host-step staging
   h->hrhs = h->d.max_rhs;
-  CKC(dalloc(h, &h->hx, P.ncell));
+  CKC(dalloc(h, &h->hx, P.ndes));
   CKC(dalloc(h, &h->hf, nd * h->hrhs));
   CKC(dalloc(h, &h->hu, nd * h->hrhs));
-  CKC(dalloc(h, &h->hg, P.ncell));
+  CKC(dalloc(h, &h->hg, P.ndes));
   CKC(cudaEventCreate(&h->ev0));
   CKC(cudaEventCreate(&h->ev1));
   CKC(cudaStreamSynchronize(st));
@@ -660,8 +676,11 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
   const int n = d.n_mr;
   const int L = h->L;
   const bool fp32 = d.precision != TOSOLVE_PREC_FP64;
-  launch_filter_fwd(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, h->invom, x_dev, d.Emin,
-                    d.E0 - d.Emin, d.penal, h->rho, h->w, st);
+  if (h->proj)
+    launch_proj_fwd(h->pg, h->invom, x_dev, d.Emin, d.E0 - d.Emin, d.penal, h->rho, h->w, st);
+  else
+    launch_filter_fwd(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, h->invom, x_dev, d.Emin,
+                      d.E0 - d.Emin, d.penal, h->rho, h->w, st);
   // The coarsest level (FP64 operator, dense matrix, Cholesky and inverse)
   // only needs the weights: with more than one level it runs on a second
   // stream, overlapped with the FP64-bound assembly of the finer levels.
@@ -908,7 +927,10 @@ tosolve_status tosolve_compliance_grad(tosolve_t h, const double* u_dev, const d
   if (dcdrho_dev) CK(cudaMemcpyAsync(dcdrho_dev, g, (size_t)h->ncell * 8, cudaMemcpyDeviceToDevice, st));
   if (dcdx_dev) {
     launch_scale((size_t)h->ncell, g, h->invom, gt, st);
-    launch_filter_T(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, gt, dcdx_dev, st);
+    if (h->proj)
+      launch_proj_T(h->pg, gt, dcdx_dev, st);
+    else
+      launch_filter_T(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, gt, dcdx_dev, st);
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
@@ -923,7 +945,7 @@ tosolve_status tosolve_step_host(tosolve_t h, const double* x_host, const double
   if (nrhs < 1 || nrhs > h->hrhs) return set_err(h, TOSOLVE_EINVAL, "nrhs must be in 1..max_rhs");
   cudaStream_t st = h->st;
   const size_t nd = h->lv[0].ndof;
-  CK(cudaMemcpyAsync(h->hx, x_host, (size_t)h->ncell * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->hx, x_host, (size_t)h->ndes * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->hf, f_host, nd * nrhs * 8, cudaMemcpyHostToDevice, st));
   if (!h->have_u || !warm) {
     CK(cudaMemsetAsync(h->hu, 0, nd * h->hrhs * 8, st));
@@ -937,7 +959,7 @@ tosolve_status tosolve_step_host(tosolve_t h, const double* x_host, const double
                                                     dcdx_host ? h->hg : nullptr, nullptr);
   if (s2 != TOSOLVE_OK) return s2;
   if (u_host) CK(cudaMemcpyAsync(u_host, h->hu, nd * nrhs * 8, cudaMemcpyDeviceToHost, st));
-  if (dcdx_host) CK(cudaMemcpyAsync(dcdx_host, h->hg, (size_t)h->ncell * 8, cudaMemcpyDeviceToHost, st));
+  if (dcdx_host) CK(cudaMemcpyAsync(dcdx_host, h->hg, (size_t)h->ndes * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return s;
 }

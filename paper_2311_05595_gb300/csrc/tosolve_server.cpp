@@ -88,8 +88,9 @@ size_t design_dofs(const tosolve_desc& d) {
   return 3 * (k * d.nx + 1) * (k * d.ny + 1) * (k * d.nz + 1);
 }
 
+// Design variables (= what x and dc/dx hold): d_mr per element edge.
 size_t design_cells(const tosolve_desc& d) {
-  const size_t n = (size_t)d.n_mr;
+  const size_t n = (size_t)(d.d_mr != 0 ? d.d_mr : d.n_mr);
   return n * n * n * (size_t)d.nx * d.ny * d.nz;
 }
 

@@ -128,9 +128,10 @@ def _check(h, status: int, what: str):
         raise TosolveError(status, f"{what}: {msg.decode() if msg else ''}")
 
 
-def make_desc(nx, ny, nz, *, degree=1, n_mr=1, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0, rmin=0.0,
-              mg_levels=0, precision=PREC_FP64, omega=0.5, cycle_gamma=1, max_rhs=1) -> tosolve_desc:
-    return tosolve_desc(nx, ny, nz, degree, n_mr, n_mr, E0, Emin, nu, penal, rmin, mg_levels,
+def make_desc(nx, ny, nz, *, degree=1, n_mr=1, d_mr=None, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0,
+              rmin=0.0, mg_levels=0, precision=PREC_FP64, omega=0.5, cycle_gamma=1,
+              max_rhs=1) -> tosolve_desc:
+    return tosolve_desc(nx, ny, nz, degree, n_mr, d_mr or n_mr, E0, Emin, nu, penal, rmin, mg_levels,
                         precision, omega, cycle_gamma, max_rhs)
 
 

@@ -8,8 +8,10 @@ the benchmark times:
   * the FP64 operator at sampled nodes (relative 1e-13 of the largest row);
   * the solve: true relative residual <= rtol recomputed with that operator;
   * compliance f^T u (1e-12 relative, a sum over 10^6 terms);
-  * dc/drho and dc/dx at sampled cells (1e-10 relative: the same formula on
-    the same u, different summation order).
+  * dc/drho at sampled cells, to within 1e-12 of the rounding scale of the
+    quadratic form u_e^T K^(e_i) u_e (sum of |K_ab u_a u_b|): the same
+    formula on the same u in another order, whose terms cancel strongly in
+    elements that move almost rigidly; dc/dx (identity filter here) equal.
 """
 import numpy as np
 import pytest
@@ -43,9 +45,13 @@ def _check_sampled(T, R, p, u_dev, rtol, rng, nodes=200, cells=40, dcells=8):
     c, gx, gr = R.grad(u_dev.reshape(1, -1).contiguous(), nrhs=1)
     assert abs(c[0] - float(np.dot(f, u))) <= 1e-12 * abs(c[0])
     cs = rng.choice(p.x.size, size=cells, replace=False)
-    np.testing.assert_allclose(gr[cs], [S.drho(p.x, u, ci) for ci in cs], rtol=1e-10)
-    ds = cs[:dcells]
-    np.testing.assert_allclose(gx[ds], [S.dx(p.x, u, ci) for ci in ds], rtol=1e-10)
+    ref = np.array([S.drho(p.x, u, ci) for ci in cs])
+    scale = np.array([S.drho_scale(p.x, u, ci) for ci in cs])
+    err = np.abs(gr[cs] - ref) / (1e-12 * scale + 1e-14 * np.abs(ref))
+    assert err.max() <= 1.0, (err.max(), (np.abs(gr[cs] - ref) / np.abs(ref)).max())
+    # the filter is the identity in these configurations: dc/dx = dc/drho
+    np.testing.assert_array_equal(gx[cs], gr[cs])
+    assert dcells >= 0
 
 
 def test_largest_batch_instance_full_size():

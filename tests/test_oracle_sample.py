@@ -42,3 +42,29 @@ def test_sampled_rows_of_a_mixed_mesh():
     y = (A @ u).reshape(-1, 3)
     ys = S.apply_rows(q.x, u, list(range(q.nnodes)))
     assert np.abs(ys - y).max() <= 1e-13 * np.abs(y).max()
+
+
+def test_gradient_rounding_scale_bounds_the_error():
+    """drho_scale bounds |dc/drho| (triangle inequality) and, for a
+    displacement that is a large rigid translation plus a small strain, the
+    FP64 error of drho against the exact rational value of the same
+    quadratic form stays below 1e-12 of it (while the relative error may not)."""
+    from fractions import Fraction
+
+    p = workloads.cantilever(3, 2, 2, degree=1, n_mr=2, seed=5)
+    S = sample.Sampler(p)
+    rng = np.random.default_rng(2)
+    u = np.tile([3e5, -2e5, 1e5], p.nnodes) + 1e-3 * rng.normal(size=p.ndof)
+    for c in range(p.x.size):
+        d, s = S.drho(p.x, u, c), S.drho_scale(p.x, u, c)
+        assert abs(d) <= s * (1 + 1e-12)
+        n = S.n
+        cx, cy, cz = c % S.Dx, (c // S.Dx) % S.Dy, c // (S.Dx * S.Dy)
+        en = S._elem_nodes(cx // n, cy // n, cz // n)
+        i = (cx % n) + n * ((cy % n) + n * (cz % n))
+        ue = [Fraction(float(u[3 * m + q])) for m in en for q in range(3)]
+        K = S.K[i]
+        quad = sum(ue[a] * Fraction(float(K[a, b])) * ue[b] for a in range(24) for b in range(24))
+        r = S.rho(p.x, c)
+        exact = -p.penal * r ** (p.penal - 1.0) * (p.E0 - p.Emin) * float(quad)
+        assert abs(d - exact) <= 1e-12 * s
