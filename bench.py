@@ -576,6 +576,87 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+FIX = dict(name="ibeam_fix_96x48x48_n2_density_192x96x96", nx=96, ny=48, nz=48, n_mr=2, rmin=1.5,
+           rtol=1e-8, rho_lo=1e-6, rho_hi=0.9, eps_grad=1e-6)
+
+
+def run_fix(args):
+    """Sec. 6.1 on a design with large void regions: the I-beam cantilever
+    (flanges and web solid, x = 0 elsewhere, filter radius 1.5) at degree 1
+    (96x48x48 elements) and degree 2 (48x24x24 elements, the same lattice).
+    Each solve starts from u0 = 0; it is timed on the whole system, then
+    after tosolve_fix_variables has suppressed the DOFs of the fixed void
+    elements (no gradient: the density conditions alone).  Prints one JSON
+    line with both times per configuration."""
+    import torch
+
+    import workloads
+    from paper_2311_05595_gb300 import tosolve as T
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    for k in (1, 2):
+        nx, ny, nz = FIX["nx"] // k, FIX["ny"] // k, FIX["nz"] // k
+        p = workloads.cantilever(nx, ny, nz, degree=k, n_mr=FIX["n_mr"] * k, rmin=FIX["rmin"],
+                                 density="ibeam")
+        x = torch.tensor(p.x, device=dev)
+        f = torch.tensor(p.f, device=dev)
+        u = torch.zeros_like(f)
+        for label, prec in (("fp32x2", T.PREC_FP32X2), ("fp64", T.PREC_FP64)):
+            d = T.make_desc(p.nx, p.ny, p.nz, degree=k, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin,
+                            nu=p.nu, penal=p.penal, precision=prec, max_rhs=1)
+            s = T.Solver(d, p.mask, stream)
+            row = {}
+            with torch.cuda.stream(stream):
+                T.tosolve_set_densities(s.h, x)
+                for phase in ("whole", "suppressed"):
+                    if phase == "suppressed":
+                        row["suppressed_dofs"] = T.tosolve_fix_variables(
+                            s.h, None, FIX["rho_lo"], FIX["rho_hi"], FIX["eps_grad"])
+                    ms, its = [], []
+                    for rep in range(args.warmup + args.steps):
+                        u.zero_()
+                        flush.zero_()
+                        stream.synchronize()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        info = T.tosolve_solve(s.h, f, 1, u, FIX["rtol"], 5000)
+                        e1.record(stream)
+                        stream.synchronize()
+                        if rep >= args.warmup:
+                            ms.append(e0.elapsed_time(e1))
+                            its.append(info.total_iterations)
+                    c = T.tosolve_compliance_grad(s.h, u, f, 1)
+                    row[phase] = {"ms": statistics.median(ms), "iterations": statistics.median(its),
+                                  "compliance": float(c[0]),
+                                  "free_dofs": T.tosolve_free_dofs(s.h)}
+            row["speedup"] = row["whole"]["ms"] / row["suppressed"]["ms"]
+            row["compliance_rel_change"] = abs(row["suppressed"]["compliance"] - row["whole"]["compliance"]) \
+                / row["whole"]["compliance"]
+            rows[f"k{k}_{label}"] = row
+            s.close()
+    clocks = sampler.stop()
+    head = rows["k1_fp32x2"]
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": FIX["name"], "design": "I-beam, flanges and web solid (volume 0.34)",
+                       "rtol": FIX["rtol"], "rho_fix_lo": FIX["rho_lo"], "rho_fix_hi": FIX["rho_hi"],
+                       "start": "u0 = 0 every solve", "l2": f"flushed between solves ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "degree_2": "48x24x24 elements, n = 4 (same lattice and density grid)"},
+            "value": head["whole"]["free_dofs"] / (head["suppressed"]["ms"] * 1e-3),
+            "ms_per_step": head["suppressed"]["ms"],
+            "value_note": "whole-system unknowns / time of the suppressed solve (the same problem, Sec. 6.1)",
+            "rows": rows, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 SERVE = dict(name="serve256_q1q2_density_64x32x32_to_384x192x192_poisson200", designs=256,
              rate=200.0, requests=2000, seed=77, rtol=1e-8, budget_gib=240, rmin=1.5)
 
@@ -677,6 +758,7 @@ def run_serve(args):
                 wait = 50 if nxt >= nreq else max(0, int(1000 * (arrivals[nxt] - now)))
                 results += T.tosolve_server_poll(srv, 256, min(wait, 50))
             info = T.tosolve_server_stats(srv)
+            failures = T.tosolve_server_failures(srv)
         finally:
             T.tosolve_server_destroy(srv)
         bad = [r for r in results if r.status != T.OK]
@@ -696,6 +778,7 @@ def run_serve(args):
             "warm_iterations_median": float(np.median(warm)) if warm.size else None,
             "iterations_p99": float(np.percentile(its_all, 99)),
             "failed": len(bad), "failed_status": sorted({int(r.status) for r in bad}),
+            "failures": failures[:8],
             "builds": info.builds - info0.builds,
             "evictions": info.evictions - info0.evictions,
             "cold_requests": int(sum(1 for r in results if r.cold)),
@@ -717,7 +800,7 @@ def main():
     ap.add_argument("--variants", default="fp32,tf32,fp32x2",
                     help="mixed-precision variants timed beside FP64 (comma list)")
     ap.add_argument("--workload", default="cantilever",
-                    choices=["cantilever", "bridge_q2", "bridge_mixed", "batch64", "serve"],
+                    choices=["cantilever", "bridge_q2", "bridge_mixed", "batch64", "serve", "ibeam_fix"],
                     help="bridge_q2: the degree-2 bridge; batch64: the 64-instance batched "
                          "solve; serve: the serving loop (each its own JSON line)")
     ap.add_argument("--designs", type=int, default=SERVE["designs"])
@@ -737,6 +820,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "ibeam_fix":
+        run_fix(args)
     else:
         run_gpu(args)
 

@@ -53,7 +53,7 @@ typedef enum {
   TOSOLVE_OK = 0,
   TOSOLVE_EINVAL = 1,      /* bad descriptor, size, pointer or argument      */
   TOSOLVE_ENOMEM = 2,      /* device allocation failed in tosolve_create     */
-  TOSOLVE_ENOTCONV = 3,    /* maxit reached before the tolerance; info valid */
+  TOSOLVE_ENOTCONV = 3,    /* tolerance not reached (maxit or restarts); info valid */
   TOSOLVE_EBREAKDOWN = 4,  /* NaN/Inf, p^T K p <= 0 or a non-positive pivot  */
   TOSOLVE_ECUDA = 5        /* a CUDA runtime call failed                     */
 } tosolve_status;
@@ -135,8 +135,39 @@ tosolve_status tosolve_create_mixed(const tosolve_desc* desc, const uint8_t* mas
                                     const uint8_t* elem_q1_host, void* cuda_stream, tosolve_t* out);
 
 /* Number of unknowns of the handle's system: lattice DOFs that are neither
- * supported nor (mixed meshes) slaved.  Errors: EINVAL. */
+ * supported, (mixed meshes) slaved, nor suppressed by
+ * tosolve_fix_variables.  Errors: EINVAL. */
 tosolve_status tosolve_free_dofs(tosolve_t h, long long* n);
+
+/* Fixing variables and suppressing DOFs of void regions (Sec. 6.1).  From the
+ * densities of the last tosolve_set_densities and an optional design
+ * gradient:
+ *   an element is void when all its densities are <= rho_lo and all its
+ *   design-gradient components are >= -eps_grad, solid when all densities
+ *   are >= rho_hi and all components are <= eps_grad (the paper uses
+ *   rho_lo = 1e-6, rho_hi = 0.9, eps_grad = 1e-6); an element is fixed when
+ *   every element sharing a node with it (inside the domain) is of its kind;
+ *   a lattice node is suppressed when every element containing it is a fixed
+ *   void element: its DOFs join the supports (u = 0, rows and columns out of
+ *   K, loads ignored) and the multigrid setup is redone at once.
+ *   dcdx_dev:  design grid FP64 (e.g. from tosolve_compliance_grad), or NULL
+ *              to use the density conditions alone.
+ *   fixed_dev: NULL, or one byte per design variable (device) receiving the
+ *              class of its fixed element: 0 free, 1 void, 2 solid (an SLP
+ *              loop gives these variables zero step bounds).
+ *   suppressed_dofs: NULL or (host) the DOFs suppressed.
+ * The selection replaces any earlier one and stays in force through later
+ * tosolve_set_densities calls until tosolve_release_variables; while it is in
+ * force tosolve_compliance_grad returns dc/dx = 0 for the variables of fixed
+ * void elements.  Synchronises.  Errors: EINVAL (no densities set, bad
+ * thresholds), ECUDA. */
+tosolve_status tosolve_fix_variables(tosolve_t h, const double* dcdx_dev, double rho_lo, double rho_hi,
+                                     double eps_grad, uint8_t* fixed_dev, long long* suppressed_dofs);
+
+/* Drops the selection of tosolve_fix_variables: the supports alone again,
+ * multigrid setup redone if densities are set.  Synchronises.  Errors:
+ * EINVAL, ECUDA. */
+tosolve_status tosolve_release_variables(tosolve_t h);
 
 /* Device memory tosolve_create would allocate for desc, in bytes (host
  * only; used for HBM admission).  Errors: EINVAL. */
@@ -157,8 +188,11 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev);
  *          out: solution, 0 at fixed DOFs.
  *   info:  may be NULL; always written when non-NULL.
  * maxit is in 1..100000 (bounds the device-side loop).
- * Synchronises the stream.  Errors: EINVAL, ENOTCONV (maxit reached),
- * EBREAKDOWN, ECUDA. */
+ * When the recursive residual meets rtol but the true one does not, the
+ * loop restarts from the current iterate, at most three times.
+ * Synchronises the stream.  Errors: EINVAL, ENOTCONV (maxit reached, or the
+ * true residual still above rtol after the three restarts), EBREAKDOWN,
+ * ECUDA. */
 tosolve_status tosolve_solve(tosolve_t h, const double* f_dev, int nrhs, double* u_dev,
                              double rtol, int maxit, tosolve_info* info);
 
@@ -296,6 +330,12 @@ tosolve_status tosolve_server_stats(tosolve_server_t s, tosolve_server_info* inf
 
 /* Message of the last failed server call on this thread. */
 const char* tosolve_server_last_error(void);
+
+/* The k-th most recent failed request (k = 0: the newest; the server keeps
+ * the last 64): request id, design, whether it was cold, status, iterations,
+ * relative residual and the handle's error message.  NULL if k is out of
+ * range.  The string stays valid until the next call on this server. */
+const char* tosolve_server_failure(tosolve_server_t s, int k);
 
 /* Drops queued requests, waits for the running ones, frees every design.
  * NULL is accepted. */

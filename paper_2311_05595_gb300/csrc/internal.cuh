@@ -95,6 +95,8 @@ struct Level {
   float* K32 = nullptr;
   void* Y = nullptr;  // per-element results of an apply (shared scratch)
   uint8_t* mask = nullptr;
+  int* tl = nullptr;    // tile order: tiles with a free DOF first (LevelView::tl)
+  int* tcnt = nullptr;  // number of those tiles (device)
   double* S64 = nullptr;   // FP64 stencil (level 0 always; others when op64)
   float* S32 = nullptr;    // FP32 stencil (FP32 preconditioner levels)
   double* dinv64 = nullptr;
@@ -134,6 +136,11 @@ struct LevelView {
   const uint8_t* mask;
   int* err;
   int sms;
+  // Operator tiles in processing order: the tcnt[0] tiles that hold a free
+  // DOF first, then the tiles whose 32 nodes are all fixed (identity rows:
+  // y = x there, no coefficients read).
+  const int* tl;
+  const int* tcnt;
 };
 
 // ---- launchers (k_setup.cu) ----------------------------------------------
@@ -248,6 +255,14 @@ void launch_vec_out(int vt, size_t n, const void* a, double* b, cudaStream_t st)
 void launch_cast(bool to_fp64, size_t n, const void* a, void* b, bool src_fp64,
                  cudaStream_t st);
 
+// ---- launchers (k_fix.cu): fixing variables, Sec. 6.1 ----------------------
+void launch_fix_classify(const Level& L0, int n, int d, const double* rho, const double* g, double lo,
+                         double hi, double eps, int8_t* cls, cudaStream_t st);
+void launch_fix_surround(const Level& L0, const int8_t* cls, int8_t* fixed, cudaStream_t st);
+void launch_fix_design(const Level& L0, int d, const int8_t* fixed, uint8_t* out, cudaStream_t st);
+void launch_fix_mask(const Level& L0, const int8_t* fixed, const uint8_t* base, cudaStream_t st);
+void launch_zero_fixed_void(long n, const uint8_t* xfix, double* g, cudaStream_t st);
+
 // ---- launchers (k_grad.cu) -----------------------------------------------
 void launch_energy_grad(const Level& L0, int n, const double* u, const double* tabsym,
                         const double* rho, double penal, double dE, int Dx, int Dy,
@@ -316,6 +331,13 @@ struct tosolve_s {
   long long free_dofs = 0;     // unknowns: DOFs neither supported nor slaved
   uint8_t* slv0 = nullptr;     // per lattice node: 1 = slaved to its vertices
   uint8_t* fix0 = nullptr;     // per DOF: the supports alone (level 0 mask adds slaved)
+  // fixing variables (Sec. 6.1)
+  uint8_t* base0 = nullptr;    // level-0 mask before suppression (supports, slaved)
+  int8_t* ecls = nullptr;      // per element: 1 void, 2 solid, 0 neither
+  int8_t* efix = nullptr;      // per element: the class if fixed, else 0
+  uint8_t* xfix = nullptr;     // per design variable: the class of its fixed element
+  bool fixing = false;
+  long long free_base = 0;     // unknowns without suppression
   float* KT32 = nullptr;       // m x 24 x 24 FP32 (tensor-core operand)
   float* w32 = nullptr;        // E x m element-major FP32 weights
   float* Ye = nullptr;         // E x 24 element results of the tensor-core apply

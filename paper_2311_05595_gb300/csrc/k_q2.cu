@@ -249,7 +249,10 @@ struct Sum<dfloat> {
 // Y_e = K^(e) u_e for every element; u_e gathered with the fixed DOFs set to
 // zero.  One block of 96 threads per element at a time (persistent), thread
 // a < 81 computes entry a; K^(e) is symmetric, so its column a (read
-// coalesced across the threads) is its row a.
+// coalesced across the threads) is its row a.  An element whose 81 DOFs are
+// all fixed is skipped (no row of it is ever read: the gather passes fixed
+// DOFs through as identity rows), so suppressed void regions cost no
+// element-matrix traffic.
 template <typename T>
 __global__ void __launch_bounds__(96) k_q2_apply(int ex, int ey, long E, int Lx, int Ly,
                                                  const op_t<T>* __restrict__ Ke,
@@ -258,12 +261,14 @@ __global__ void __launch_bounds__(96) k_q2_apply(int ex, int ey, long E, int Lx,
   __shared__ T ue[kD];
   for (long e = blockIdx.x; e < E; e += gridDim.x) {
     const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+    bool free_dof = false;
     if (threadIdx.x < kD) {
       const int a = threadIdx.x / 3, c = threadIdx.x % 3;
       const long d = 3 * elem_node(exi, eyi, ezi, a, Lx, Ly) + c;
-      ue[threadIdx.x] = mask[d] ? T(0) : u[d];
+      free_dof = mask[d] == 0;
+      ue[threadIdx.x] = free_dof ? u[d] : T(0);
     }
-    __syncthreads();
+    if (!__syncthreads_or(free_dof)) continue;  // block-uniform
     if (threadIdx.x < kD) {
       const op_t<T>* K = Ke + e * (size_t)kDD + threadIdx.x;
       Sum<T> acc;
@@ -297,7 +302,9 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
       else { e0[ax] = max((co[ax] >> 1) - 1, 0); e1[ax] = min(co[ax] >> 1, ext[ax] - 1); }
     }
     T y[3] = {T(0), T(0), T(0)};
-    for (int ez_ = e0[2]; ez_ <= e1[2]; ++ez_)
+    // a node with all DOFs fixed does not use y (its elements may be skipped)
+    const bool all_fixed = mask[3 * node] && mask[3 * node + 1] && mask[3 * node + 2];
+    for (int ez_ = e0[2]; !all_fixed && ez_ <= e1[2]; ++ez_)
       for (int ey_ = e0[1]; ey_ <= e1[1]; ++ey_)
         for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
           const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);

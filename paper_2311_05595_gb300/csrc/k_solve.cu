@@ -14,15 +14,15 @@ template <typename T>
 LevelView<T> view(const Level& L);
 template <>
 LevelView<double> view<double>(const Level& L) {
-  return LevelView<double>{L.Lx, L.Ly, L.Lz, L.nn, L.S64, L.dinv64, L.mask, L.err, L.sms};
+  return LevelView<double>{L.Lx, L.Ly, L.Lz, L.nn, L.S64, L.dinv64, L.mask, L.err, L.sms, L.tl, L.tcnt};
 }
 template <>
 LevelView<float> view<float>(const Level& L) {
-  return LevelView<float>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask, L.err, L.sms};
+  return LevelView<float>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask, L.err, L.sms, L.tl, L.tcnt};
 }
 template <>
 LevelView<dfloat> view<dfloat>(const Level& L) {
-  return LevelView<dfloat>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask, L.err, L.sms};
+  return LevelView<dfloat>{L.Lx, L.Ly, L.Lz, L.nn, L.S32, L.dinv32, L.mask, L.err, L.sms, L.tl, L.tcnt};
 }
 
 namespace {
@@ -155,14 +155,16 @@ __device__ __forceinline__ dfloat sum3(Dot2 a, const Dot2& b, const Dot2& c) {
 }
 
 // Runs row(node, r, y) with y = (A x)_{node, r} for every node of the tiles
-// this block owns (tiles blockIdx.x, +gridDim.x, ...).  Thread 0 keeps
-// kStages tile copies in flight; a stage is refilled once every warp is done
-// with it.  Warp w = 3g + r computes, for the tile's 32 nodes, the part of
-// row r that comes from the neighbours in z-plane g; the three parts meet in
-// shared memory and the g = 0 warps finish the rows.  Every wait is bounded:
-// if a copy does not land in time the block sets *V.err, waits (bounded) for
-// its other copies and stops; the result is then invalid and the host
-// reports the error.
+// this block owns (entries blockIdx.x, +gridDim.x, ... of the tile order
+// V.tl).  Thread 0 keeps kStages tile copies in flight; a stage is refilled
+// once every warp is done with it.  Warp w = 3g + r computes, for the tile's
+// 32 nodes, the part of row r that comes from the neighbours in z-plane g;
+// the three parts meet in shared memory and the g = 0 warps finish the rows.
+// Tiles past the first *V.tcnt of the order hold fixed DOFs only, whose rows
+// are identity rows: the g = 0 warps pass y = x without reading the tile.
+// Every wait is bounded: if a copy does not land in time the block sets
+// *V.err, waits (bounded) for its other copies and stops; the result is then
+// invalid and the host reports the error.
 template <typename T, typename LD, typename ROW>
 __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW row) {
   extern __shared__ __align__(128) unsigned char tsm[];
@@ -174,7 +176,8 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
   uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + (size_t)kStages * kBytes);
   const int tid = threadIdx.x, g = tid / 96, rl = tid % 96, r = rl >> 5, lane = tid & 31;
   const long ntiles = ((long)V.nn + kTN - 1) / kTN;
-  const long nk = (long)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long nact = *V.tcnt;
+  const long nk = (long)blockIdx.x < nact ? (nact - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const char* gsrc = reinterpret_cast<const char*>(V.S);
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s)
@@ -184,14 +187,14 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
   __syncthreads();
   if (tid == 0)
     for (long k = 0; k < kStages && k < nk; ++k)
-      tile_issue(tsm + k * kBytes, gsrc + (size_t)(blockIdx.x + k * gridDim.x) * kBytes, kBytes,
+      tile_issue(tsm + k * kBytes, gsrc + (size_t)V.tl[blockIdx.x + k * gridDim.x] * kBytes, kBytes,
                  &bars[k]);
   long k = 0;
   for (; k < nk; ++k) {
     const int s = (int)(k % kStages);
     const bool got = tile_wait(&bars[s], (uint32_t)((k / kStages) & 1));
     if (__syncthreads_or(!got)) break;
-    const long node = (blockIdx.x + k * gridDim.x) * kTN + lane;
+    const long node = (long)V.tl[blockIdx.x + k * gridDim.x] * kTN + lane;
     const bool live = node < V.nn;
     const int i = node % V.Lx, j = (node / V.Lx) % V.Ly, l = node / ((long)V.Lx * V.Ly);
     if (live) parts[g][rl] = plane_row(V, sbuf + (size_t)s * 243 * kTN + lane, node, i, j, l, r, g, ld);
@@ -199,7 +202,7 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
     if (tid == 0 && k + kStages < nk) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tile_issue(tsm + (size_t)s * kBytes,
-                 gsrc + (size_t)(blockIdx.x + (k + kStages) * gridDim.x) * kBytes, kBytes, &bars[s]);
+                 gsrc + (size_t)V.tl[blockIdx.x + (k + kStages) * gridDim.x] * kBytes, kBytes, &bars[s]);
     }
     if (g == 0 && live) row(node, r, sum3(parts[0][rl], parts[1][rl], parts[2][rl]));
     __syncthreads();  // parts are free
@@ -209,6 +212,12 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
     for (long q = k; q < nk && q < k + kStages; ++q)
       tile_wait(&bars[q % kStages], (uint32_t)((q / kStages) & 1));
   }
+  if (k < nk) return;
+  if (g == 0)  // tiles of fixed DOFs only: identity rows
+    for (long q = nact + blockIdx.x; q < ntiles; q += gridDim.x) {
+      const long node = (long)V.tl[q] * kTN + lane;
+      if (node < V.nn) row(node, r, (T)ld(node, r));
+    }
 }
 
 // Threads per block of the vector kernels (one DOF or node per thread).

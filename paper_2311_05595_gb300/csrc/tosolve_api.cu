@@ -194,6 +194,8 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   B += (size_t)ndof0 * 8 * 7;                         // u r p q f tmpa tmpb
   B += (size_t)ndof0 * 8 * 2 * maxrhs;                // host-step staging f, u
   B += 4 * kMaxPart * 8 + sizeof(DevState) + (size_t)P->ndes * 8 * 2;
+  B += (size_t)ndof0 + 2 * (size_t)d.nx * d.ny * d.nz + (size_t)P->ndes;  // fixing (Sec. 6.1)
+  for (int l = 0; l < L; ++l) B += ((size_t)(P->lv[l].nn + kTN - 1) / kTN + 1) * sizeof(int);  // tile order
   if (tf32) {
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
     B += E0 * (P->m + 24) * 4 + (size_t)P->m * 576 * 4 + P->lv[0].ndof * 4;
@@ -224,10 +226,11 @@ void free_all(tosolve_s* h) {
   for (int l = 0; l < kMaxLevels; ++l) {
     Level& L = h->lv[l];
     F(L.mask); F(L.S64); F(L.S32); F(L.dinv64); F(L.dinv32); F(L.b); F(L.v); F(L.r); F(L.z);
-    F(L.K64); F(L.K32);
+    F(L.K64); F(L.K32); F(L.tl); F(L.tcnt);
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
+  F(h->base0); F(h->ecls); F(h->efix); F(h->xfix);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv); F(h->Pq);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
@@ -426,14 +429,24 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
         }
     h->mixed = true;
     CKC(dalloc(h, &h->slv0, v.nn));
-    CKC(cudaMemcpy(h->slv0, slv.data(), v.nn, cudaMemcpyHostToDevice));
+    CKC(cudaMemcpyAsync(h->slv0, slv.data(), v.nn, cudaMemcpyHostToDevice, st));
     CKC(dalloc(h, &h->fix0, v.ndof));
-    CKC(cudaMemcpy(h->fix0, mask.data(), v.ndof, cudaMemcpyHostToDevice));
+    CKC(cudaMemcpyAsync(h->fix0, mask.data(), v.ndof, cudaMemcpyHostToDevice, st));
     for (long nd = 0; nd < v.nn; ++nd)
       if (slv[nd]) mask[3 * nd] = mask[3 * nd + 1] = mask[3 * nd + 2] = 1;
   }
   h->free_dofs = 0;
   for (uint8_t m : mask) h->free_dofs += m == 0;
+  h->free_base = h->free_dofs;
+  {  // level-0 mask before any suppression, and the fixing workspace
+    const size_t E0 = (size_t)P.lv[0].ex * P.lv[0].ey * P.lv[0].ez;
+    CKC(dalloc(h, &h->base0, P.lv[0].ndof));
+    CKC(cudaMemcpyAsync(h->base0, mask.data(), P.lv[0].ndof, cudaMemcpyHostToDevice, st));
+    CKC(dalloc(h, &h->ecls, E0));
+    CKC(dalloc(h, &h->efix, E0));
+    CKC(dalloc(h, &h->xfix, P.ndes));
+    CKC(cudaMemsetAsync(h->xfix, 0, P.ndes, st));
+  }
   for (int l = 0; l < P.L; ++l) {
     const Plan::Lv& v = P.lv[l];
     Level& L = h->lv[l];
@@ -444,15 +457,24 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     L.h = (double)(1 << l);
     L.op64 = !fp32 || l == P.L - 1;
     CKC(dalloc(h, &L.mask, v.ndof));
-    CKC(cudaMemcpy(L.mask, mask.data(), v.ndof, cudaMemcpyHostToDevice));
+    CKC(cudaMemcpyAsync(L.mask, mask.data(), v.ndof, cudaMemcpyHostToDevice, st));
+    {  // tile order: every tile, in index order, until DOFs are suppressed
+      const int nt = (int)((v.nn + kTN - 1) / kTN);
+      std::vector<int> order(nt);
+      for (int t = 0; t < nt; ++t) order[t] = t;
+      CKC(dalloc(h, &L.tl, nt));
+      CKC(cudaMemcpyAsync(L.tl, order.data(), nt * sizeof(int), cudaMemcpyHostToDevice, st));
+      CKC(dalloc(h, &L.tcnt, 1));
+      CKC(cudaMemcpyAsync(L.tcnt, &nt, sizeof(int), cudaMemcpyHostToDevice, st));
+    }
     if (v.s64) {  // padding coefficients of the last tile stay zero
       CKC(dalloc(h, &L.S64, op_len(v.nn)));
-      CKC(cudaMemset(L.S64, 0, op_len(v.nn) * sizeof(double)));
+      CKC(cudaMemsetAsync(L.S64, 0, op_len(v.nn) * sizeof(double), st));
       CKC(dalloc(h, &L.dinv64, v.ndof));
     }
     if (v.s32) {
       CKC(dalloc(h, &L.S32, op_len(v.nn)));
-      CKC(cudaMemset(L.S32, 0, op_len(v.nn) * sizeof(float)));
+      CKC(cudaMemsetAsync(L.S32, 0, op_len(v.nn) * sizeof(float), st));
       CKC(dalloc(h, &L.dinv32, v.ndof));
     }
     if (tf32 && l == 0) CKC(dalloc(h, &L.dinv32, v.ndof));
@@ -469,7 +491,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     for (void** pv : vecs) {
       char* p = nullptr;
       CKC(dalloc(h, &p, v.ndof * tsz));
-      CKC(cudaMemset(p, 0, v.ndof * tsz));
+      CKC(cudaMemsetAsync(p, 0, v.ndof * tsz, st));
       *pv = p;
     }
     if (l + 1 < P.L) {  // coarse DOF fixed iff the coincident fine DOF is fixed
@@ -541,8 +563,8 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     h->noff = (int)off.size();
     CKC(dalloc(h, &h->foff, off.size()));
     CKC(dalloc(h, &h->fwgt, wgt.size()));
-    CKC(cudaMemcpy(h->foff, off.data(), off.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CKC(cudaMemcpy(h->fwgt, wgt.data(), wgt.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpyAsync(h->foff, off.data(), off.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    CKC(cudaMemcpyAsync(h->fwgt, wgt.data(), wgt.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   }
   CKC(dalloc(h, &h->rho, P.ncell));
   CKC(dalloc(h, &h->w, P.ncell));
@@ -587,7 +609,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     CKC(dalloc(h, &h->Wp, nc * kNB));
     CKC(dalloc(h, &h->Dblk, nblk * kNB * kNB));
     CKC(dalloc(h, &h->Xinv, nc * nc));
-    CKC(cudaMemset(h->Xinv, 0, nc * nc * sizeof(double)));
+    CKC(cudaMemsetAsync(h->Xinv, 0, nc * nc * sizeof(double), st));
     CKC(dalloc(h, &h->Ainv, nc * nc));
     CKC(dalloc(h, &h->Pq, (size_t)coarse_qchunks((int)nc) * nc * nc));
     h->cgrid = coarse_factor_grid();
@@ -598,14 +620,14 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   double** vec64[7] = {&h->u, &h->r, &h->p, &h->q, &h->f, &h->tmpa, &h->tmpb};
   for (double** pv : vec64) {
     CKC(dalloc(h, pv, nd));
-    CKC(cudaMemset(*pv, 0, nd * 8));
+    CKC(cudaMemsetAsync(*pv, 0, nd * 8, st));
   }
   CKC(dalloc(h, &h->part, 4 * kMaxPart));
-  CKC(cudaMemset(h->part, 0, 4 * kMaxPart * 8));
+  CKC(cudaMemsetAsync(h->part, 0, 4 * kMaxPart * 8, st));
   CKC(dalloc(h, &h->cnt, 4));
-  CKC(cudaMemset(h->cnt, 0, 4 * sizeof(unsigned)));
+  CKC(cudaMemsetAsync(h->cnt, 0, 4 * sizeof(unsigned), st));
   CKC(dalloc(h, &h->ds, 1));
-  CKC(cudaMemset(h->ds, 0, sizeof(DevState)));
+  CKC(cudaMemsetAsync(h->ds, 0, sizeof(DevState), st));
   if (h->tc.on) h->tc.err = &h->ds->tc_status;
   {
     int sms = 1;
@@ -668,19 +690,14 @@ const char* tosolve_last_error(tosolve_t h) {
   return h->err.c_str();
 }
 
-tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
-  if (h == nullptr) return set_err(h, TOSOLVE_EINVAL, "handle is NULL");
-  if (x_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "x is NULL");
+// The multigrid setup for the current weights w and level masks (Sec. 7.2:
+// every level's operator, Jacobi diagonal and the coarse factorisation).
+static tosolve_status refresh(tosolve_t h) {
   cudaStream_t st = h->st;
   const tosolve_desc& d = h->d;
   const int n = d.n_mr;
   const int L = h->L;
   const bool fp32 = d.precision != TOSOLVE_PREC_FP64;
-  if (h->proj)
-    launch_proj_fwd(h->pg, h->invom, x_dev, d.Emin, d.E0 - d.Emin, d.penal, h->rho, h->w, st);
-  else
-    launch_filter_fwd(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, h->invom, x_dev, d.Emin,
-                      d.E0 - d.Emin, d.penal, h->rho, h->w, st);
   // The coarsest level (FP64 operator, dense matrix, Cholesky and inverse)
   // only needs the weights: with more than one level it runs on a second
   // stream, overlapped with the FP64-bound assembly of the finer levels.
@@ -723,7 +740,6 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
       CK(cudaStreamWaitEvent(st, h->evj, 0));
     }
     CK(cudaGetLastError());
-    h->have_rho = true;
     return TOSOLVE_OK;
   }
   if (L > 1) {
@@ -774,7 +790,97 @@ tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
     CK(cudaStreamWaitEvent(st, h->evj, 0));
   }
   CK(cudaGetLastError());
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev) {
+  if (h == nullptr) return set_err(h, TOSOLVE_EINVAL, "handle is NULL");
+  if (x_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "x is NULL");
+  cudaStream_t st = h->st;
+  const tosolve_desc& d = h->d;
+  if (h->proj)
+    launch_proj_fwd(h->pg, h->invom, x_dev, d.Emin, d.E0 - d.Emin, d.penal, h->rho, h->w, st);
+  else
+    launch_filter_fwd(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, h->invom, x_dev, d.Emin,
+                      d.E0 - d.Emin, d.penal, h->rho, h->w, st);
+  const tosolve_status s = refresh(h);
+  if (s != TOSOLVE_OK) return s;
   h->have_rho = true;
+  return TOSOLVE_OK;
+}
+
+// After the level-0 mask changed: the free count of level 0 is read back and
+// its tile order puts the tiles with a free DOF first (the stencil kernels
+// pass the others through as identity rows).  The coarse levels keep the
+// supports alone: a coarse node that coincides with a suppressed node can
+// still carry a correction for the free nodes near it (the transfers mask
+// the fine side), whereas fixing it would clamp the coarse elements that
+// reach from the void into the structure.
+static tosolve_status remask(tosolve_t h) {
+  cudaStream_t st = h->st;
+  Level& L0 = h->lv[0];
+  const int nt = (L0.nn + kTN - 1) / kTN;
+  std::vector<uint8_t> m(L0.ndof);
+  CK(cudaMemcpyAsync(m.data(), L0.mask, L0.ndof, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<int> order;
+  order.reserve(nt);
+  int nact = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int t = 0; t < nt; ++t) {
+      const long d0 = 3L * kTN * t, d1 = std::min<long>(d0 + 3L * kTN, L0.ndof);
+      bool all = true;
+      for (long q = d0; q < d1 && all; ++q) all = m[q] != 0;
+      if (all == (pass == 1)) order.push_back(t);
+    }
+    if (pass == 0) nact = (int)order.size();
+  }
+  long long nfree = 0;
+  for (uint8_t v : m) nfree += v == 0;
+  CK(cudaMemcpyAsync(L0.tcnt, &nact, sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(L0.tl, order.data(), nt * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  h->free_dofs = nfree;
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_fix_variables(tosolve_t h, const double* dcdx_dev, double rho_lo, double rho_hi,
+                                     double eps_grad, uint8_t* fixed_dev, long long* suppressed_dofs) {
+  if (h == nullptr) return set_err(h, TOSOLVE_EINVAL, "handle is NULL");
+  if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");
+  if (!(rho_lo >= 0.0) || !(rho_hi <= 1.0) || !(rho_lo < rho_hi) || !(eps_grad >= 0.0))
+    return set_err(h, TOSOLVE_EINVAL, "need 0 <= rho_lo < rho_hi <= 1 and eps_grad >= 0");
+  cudaStream_t st = h->st;
+  const Level& L0 = h->lv[0];
+  const int dm = h->proj ? h->pg.d : h->d.n_mr;
+  launch_fix_classify(L0, h->d.n_mr, dm, h->rho, dcdx_dev, rho_lo, rho_hi, eps_grad, h->ecls, st);
+  launch_fix_surround(L0, h->ecls, h->efix, st);
+  launch_fix_design(L0, dm, h->efix, h->xfix, st);
+  launch_fix_mask(L0, h->efix, h->base0, st);
+  if (fixed_dev) CK(cudaMemcpyAsync(fixed_dev, h->xfix, (size_t)h->ndes, cudaMemcpyDeviceToDevice, st));
+  tosolve_status s = remask(h);
+  if (s != TOSOLVE_OK) return s;
+  h->fixing = true;
+  if (suppressed_dofs) *suppressed_dofs = h->free_base - h->free_dofs;
+  s = refresh(h);
+  if (s != TOSOLVE_OK) return s;
+  CK(cudaStreamSynchronize(st));
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_release_variables(tosolve_t h) {
+  if (h == nullptr) return set_err(h, TOSOLVE_EINVAL, "handle is NULL");
+  cudaStream_t st = h->st;
+  CK(cudaMemcpyAsync(h->lv[0].mask, h->base0, (size_t)h->lv[0].ndof, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(h->xfix, 0, (size_t)h->ndes, st));
+  tosolve_status s = remask(h);
+  if (s != TOSOLVE_OK) return s;
+  h->fixing = false;
+  if (h->have_rho) {
+    s = refresh(h);
+    if (s != TOSOLVE_OK) return s;
+  }
+  CK(cudaStreamSynchronize(st));
   return TOSOLVE_OK;
 }
 
@@ -878,7 +984,8 @@ tosolve_status tosolve_solve(tosolve_t h, const double* f_dev, int nrhs, double*
       if (used >= maxit || attempt == 3) {
         worst = std::fmax(worst, rel);
         result = TOSOLVE_ENOTCONV;
-        h->err = "maxit reached before the tolerance";
+        h->err = used >= maxit ? "maxit reached before the tolerance"
+                               : "the true residual stayed above the tolerance after 3 restarts";
         break;
       }
       // recursive residual met the tolerance but the true one did not:
@@ -931,6 +1038,7 @@ tosolve_status tosolve_compliance_grad(tosolve_t h, const double* u_dev, const d
       launch_proj_T(h->pg, gt, dcdx_dev, st);
     else
       launch_filter_T(h->Dx, h->Dy, h->Dz, h->noff, h->foff, h->fwgt, gt, dcdx_dev, st);
+    if (h->fixing) launch_zero_fixed_void(h->ndes, h->xfix, dcdx_dev, st);
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));

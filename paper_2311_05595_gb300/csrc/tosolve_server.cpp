@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -73,6 +74,8 @@ struct tosolve_server_s {
   size_t resident = 0;
   long long next_id = 1;
   long long builds = 0, evictions = 0;
+  std::deque<std::string> failures;  // newest last, at most kFailLog
+  std::string failure_copy;          // what tosolve_server_failure last returned
   int running = 0;
   bool stop = false;
 
@@ -82,6 +85,8 @@ struct tosolve_server_s {
 };
 
 namespace {
+
+constexpr size_t kFailLog = 64;
 
 size_t design_dofs(const tosolve_desc& d) {
   const size_t k = (size_t)d.degree;
@@ -120,8 +125,9 @@ void evict(tosolve_server_s* s, Design& D) {
   if (D.h == nullptr) return;
   cudaStreamSynchronize(D.st);
   D.u_host.resize(D.f.size());
-  D.has_u = cudaMemcpy(D.u_host.data(), D.ud, D.f.size() * sizeof(double), cudaMemcpyDeviceToHost) ==
-            cudaSuccess;
+  D.has_u = cudaMemcpyAsync(D.u_host.data(), D.ud, D.f.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                            D.st) == cudaSuccess &&
+            cudaStreamSynchronize(D.st) == cudaSuccess;
   tosolve_destroy(D.h);
   free_buffers(D);
   s->resident -= D.bytes;
@@ -229,6 +235,9 @@ void worker(tosolve_server_s* s) {
     if (!fits) {
       res.status = TOSOLVE_ENOMEM;
       res.t_end = res.t_start;
+      s->failures.push_back("request " + std::to_string(R.id) + " design " + std::to_string(R.design) +
+                            " status 2: the design is larger than the whole HBM budget");
+      if (s->failures.size() > kFailLog) s->failures.pop_front();
       s->results.push_back(res);
       s->cv_done.notify_all();
       continue;
@@ -256,10 +265,20 @@ void worker(tosolve_server_s* s) {
     std::string why;
     if (need_build) st = build(D, &why);
     res.cold = need_build ? 1 : 0;
-    if (st == TOSOLVE_OK) st = run(D, R, rtol, maxit, &res);
+    if (st == TOSOLVE_OK) {
+      st = run(D, R, rtol, maxit, &res);
+      if (st != TOSOLVE_OK) why = tosolve_last_error(D.h);
+    }
     res.status = st;
     res.t_end = s->now();
     lk.lock();
+    if (st != TOSOLVE_OK) {
+      char head[160];
+      std::snprintf(head, sizeof(head), "request %lld design %d%s status %d its %d rel %.3e: ", R.id,
+                    R.design, need_build ? " (cold)" : "", (int)st, res.iterations, res.rel_residual);
+      s->failures.push_back(head + why);
+      if (s->failures.size() > kFailLog) s->failures.pop_front();
+    }
     if (need_build && D.h == nullptr) s->resident -= D.bytes;  // the build failed
     D.busy = false;
     D.last_used = res.t_end;
@@ -388,6 +407,14 @@ tosolve_status tosolve_server_stats(tosolve_server_t s, tosolve_server_info* inf
 }
 
 const char* tosolve_server_last_error(void) { return s_err.c_str(); }
+
+const char* tosolve_server_failure(tosolve_server_t s, int k) {
+  if (s == nullptr || k < 0) return nullptr;
+  std::lock_guard<std::mutex> g(s->mu);
+  if ((size_t)k >= s->failures.size()) return nullptr;
+  s->failure_copy = s->failures[s->failures.size() - 1 - (size_t)k];
+  return s->failure_copy.c_str();
+}
 
 void tosolve_server_destroy(tosolve_server_t s) {
   if (s == nullptr) return;

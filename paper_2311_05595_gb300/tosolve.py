@@ -95,8 +95,11 @@ def _load():
         "tosolve_server_poll": ([vp, P(tosolve_request_result), i, i], i),
         "tosolve_server_stats": ([vp, P(tosolve_server_info)], i),
         "tosolve_server_last_error": ([], C.c_char_p),
+        "tosolve_server_failure": ([vp, i], C.c_char_p),
         "tosolve_server_destroy": ([vp], None),
         "tosolve_trim_pool": ([sz], i),
+        "tosolve_fix_variables": ([vp, vp, C.c_double, C.c_double, C.c_double, vp, P(C.c_longlong)], i),
+        "tosolve_release_variables": ([vp], i),
         "tosolve_last_error": ([vp], C.c_char_p),
         "tosolve_destroy": ([vp], None),
     }
@@ -274,6 +277,16 @@ def tosolve_server_stats(s) -> tosolve_server_info:
     return info
 
 
+def tosolve_server_failures(s) -> list:
+    """Messages of the most recent failed requests, newest first."""
+    out = []
+    while True:
+        m = _lib.tosolve_server_failure(s, len(out))
+        if not m:
+            return out
+        out.append(m.decode())
+
+
 def tosolve_server_destroy(s) -> None:
     _lib.tosolve_server_destroy(s)
 
@@ -287,6 +300,19 @@ def tosolve_compliance_noalloc(f_dev, u_dev, mask_dev, ndof: int, nrhs: int, c_d
         st = stream if isinstance(stream, int) else stream.cuda_stream
     _check(None, _lib.tosolve_compliance_noalloc(_ptr(f_dev), _ptr(u_dev), _ptr(mask_dev), ndof, nrhs,
                                                  _ptr(c_dev), st), "tosolve_compliance_noalloc")
+
+
+def tosolve_fix_variables(h, dcdx_dev=None, rho_lo: float = 1e-6, rho_hi: float = 0.9,
+                          eps_grad: float = 1e-6, fixed_dev=None) -> int:
+    """Sec. 6.1 fixing; returns the number of suppressed DOFs."""
+    n = C.c_longlong(0)
+    _check(h, _lib.tosolve_fix_variables(h, _ptr(dcdx_dev), rho_lo, rho_hi, eps_grad, _ptr(fixed_dev),
+                                         C.byref(n)), "tosolve_fix_variables")
+    return n.value
+
+
+def tosolve_release_variables(h) -> None:
+    _check(h, _lib.tosolve_release_variables(h), "tosolve_release_variables")
 
 
 def tosolve_trim_pool(keep_bytes: int = 0) -> None:

@@ -134,6 +134,29 @@ def test_admission_evicts_idle_designs_and_restores_warm_starts():
         T.tosolve_server_submit(s, 0, p.x)
         got = T.tosolve_server_poll(s, 4, 5000)
         assert len(got) == 1 and got[0].status == T.ENOMEM
+        msgs = T.tosolve_server_failures(s)
+        assert len(msgs) == 1 and "status 2" in msgs[0] and "design 0" in msgs[0]
+    finally:
+        T.tosolve_server_destroy(s)
+
+
+def test_failed_requests_are_logged_with_their_reason():
+    """maxit = 1: every request ends ENOTCONV; the failure log holds the
+    newest 64, newest first, each with its status, iterations and residual."""
+    T = lib()
+    p = workloads.cantilever(8, 4, 4, seed=2, mg_levels=2)
+    s = T.tosolve_server_create(2, 4 * GiB, 1e-10, 1)
+    try:
+        T.tosolve_server_add_design(s, 7, desc_for(T, p, FP32X2), p.mask, np.asarray(p.f), p.nrhs)
+        ids = [T.tosolve_server_submit(s, 7, p.x) for _ in range(70)]
+        done = []
+        while len(done) < len(ids):
+            done += T.tosolve_server_poll(s, 64, 5000)
+        assert all(r.status == T.ENOTCONV and r.iterations == 1 for r in done)
+        msgs = T.tosolve_server_failures(s)
+        assert len(msgs) == 64
+        assert msgs[0].startswith(f"request {ids[-1]} design 7 status 3 its 1")
+        assert all("status 3" in m and "maxit" in m for m in msgs)
     finally:
         T.tosolve_server_destroy(s)
 

@@ -150,6 +150,20 @@ def _line_weights(n_elems: int, k: int) -> np.ndarray:
     return w
 
 
+def ibeam_field(shape) -> np.ndarray:
+    """(Dz, Dy, Dx) cells, flattened x fastest: 1 in the bottom and top
+    flanges (Dz/8 cells thick each, rounded up) and in the web (Dy/8 cells
+    wide, centred), 0 elsewhere."""
+    Dz, Dy, Dx = shape
+    t = max(1, -(-Dz // 8))
+    wy = max(1, -(-Dy // 8))
+    y0 = (Dy - wy) // 2
+    z = np.arange(Dz)[:, None, None]
+    y = np.arange(Dy)[None, :, None]
+    solid = (z < t) | (z >= Dz - t) | ((y >= y0) & (y < y0 + wy))
+    return np.broadcast_to(solid, (Dz, Dy, Dx)).astype(np.float64).reshape(-1)
+
+
 def cantilever(nx: int, ny: int, nz: int, *, degree: int = 1, n_mr: int = 1,
                rmin: float = 0.0, density: str = "uniform", seed: int = 0,
                E0: float = 1.0, Emin: float = 1e-9, nu: float = 0.3,
@@ -161,7 +175,12 @@ def cantilever(nx: int, ny: int, nz: int, *, degree: int = 1, n_mr: int = 1,
 
     density='uniform': design variables iid U[lo, hi];
     density='smooth' : smooth_field (coarse 12x6x6 iid U[0,1], trilinear
-                       resampling, clipped to [0.001, 1]).
+                       resampling, clipped to [0.001, 1]);
+    density='ibeam'  : a 0/1 design with large void regions, the kind an
+                       optimisation ends with (Sec. 6.1 fixes variables in
+                       such regions): an I-beam along x, flanges of an
+                       eighth of the height at the bottom and top, a web of
+                       an eighth of the width in the middle, x = 0 elsewhere.
     """
     lat = lattice_shape(nx, ny, nz, degree)
     Lx, Ly, Lz = lat
@@ -184,6 +203,8 @@ def cantilever(nx: int, ny: int, nz: int, *, degree: int = 1, n_mr: int = 1,
         x = smooth_field(shape, rng)
     elif density == "solid":
         x = np.ones(int(np.prod(shape)))
+    elif density == "ibeam":
+        x = ibeam_field(shape)
     else:
         raise ValueError(density)
     return Problem(f"cantilever{nx}x{ny}x{nz}_k{degree}_n{n_mr}", nx, ny, nz, degree,
