@@ -164,6 +164,49 @@ tosolve_status tosolve_free_dofs(tosolve_t h, long long* n);
 tosolve_status tosolve_fix_variables(tosolve_t h, const double* dcdx_dev, double rho_lo, double rho_hi,
                                      double eps_grad, uint8_t* fixed_dev, long long* suppressed_dofs);
 
+/* ---- Thresholding and the Heaviside projection (Sec. 5) -------------------
+ * Device-side steps of the density projection strategy, on a density vector
+ * of n equal-volume cells (rho_dev, n FP64 on the device, values in [0, 1]).
+ * They are independent of any handle: each takes a caller-owned device
+ * scratch buffer of at least tosolve_threshold_scratch_bytes(n) bytes and
+ * runs on cuda_stream (NULL: the legacy default stream), synchronising it.
+ * With n = 0 nothing is read or written and pointers may be NULL.
+ * Errors (tosolve_last_error(NULL)): EINVAL (NULL pointer, n outside
+ * 0..2^31-1, a parameter out of range, scratch too small), ECUDA. */
+size_t tosolve_threshold_scratch_bytes(long long n);
+
+/* Heaviside projection: out = h(rho, beta, eta) with h(rho, beta, eta) =
+ * (tanh(beta eta) + tanh(beta (rho - eta))) / (tanh(beta eta) +
+ * tanh(beta (1 - eta))) and eta the zero of sum h(rho_i, beta, eta) -
+ * sum rho_i (the volume is kept), by Newton's method from eta = 1/2 (a step
+ * that would leave (0, 1) is halved; stop when |f| <= 1e-12 n or the step
+ * is below 1e-14).  beta > 0.  eta, newton_its: host, may be NULL. */
+tosolve_status tosolve_heaviside(const double* rho_dev, long long n, double beta, double* out_dev, double* eta,
+                                 int* newton_its, void* scratch_dev, size_t scratch_bytes, void* cuda_stream);
+
+/* Strategy based on the density values: densities >= round_hi become 1 and
+ * <= round_lo become 0 (the paper: 0.95, 0.05); then the floor(vfrac n)
+ * largest become 1 and the others 0 (among equal densities the lower index
+ * first).  accepted (host, may be NULL) = 1 when d = out - rho_rounded and
+ * -gradL make an angle below theta_max_deg (Eq. angle; the paper: 89.9).
+ * gradL_dev: n FP64, the gradient of the Lagrangian w.r.t. the densities. */
+tosolve_status tosolve_threshold_density(const double* rho_dev, long long n, double vfrac, double round_lo,
+                                         double round_hi, const double* gradL_dev, double theta_max_deg,
+                                         double* out_dev, int* accepted, void* scratch_dev, size_t scratch_bytes,
+                                         void* cuda_stream);
+
+/* Strategy based on the gradient of the Lagrangian: the same rounding, then
+ * out = clip(rho - alpha gradL, 0, 1) with alpha the largest of the steps at
+ * which a component reaches its bound (0 where gradL > 0, 1 where < 0; ties
+ * ordered by index) such that out satisfies the angle condition and no
+ * component reached 1 from a density below vu_min or 0 from one above
+ * vl_max (the paper: 0.3, 0.7); alpha = 0 if none qualifies.  alpha: host,
+ * may be NULL. */
+tosolve_status tosolve_threshold_gradient(const double* rho_dev, const double* gradL_dev, long long n,
+                                          double round_lo, double round_hi, double vu_min, double vl_max,
+                                          double theta_max_deg, double* out_dev, double* alpha, void* scratch_dev,
+                                          size_t scratch_bytes, void* cuda_stream);
+
 /* Drops the selection of tosolve_fix_variables: the supports alone again,
  * multigrid setup redone if densities are set.  Synchronises.  Errors:
  * EINVAL, ECUDA. */

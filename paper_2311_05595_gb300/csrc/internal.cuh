@@ -95,8 +95,10 @@ struct Level {
   float* K32 = nullptr;
   void* Y = nullptr;  // per-element results of an apply (shared scratch)
   uint8_t* mask = nullptr;
-  int* tl = nullptr;    // tile order: tiles with a free DOF first (LevelView::tl)
-  int* tcnt = nullptr;  // number of those tiles (device)
+  int* tl = nullptr;    // tile order in force (LevelView::tl), or null: index order
+  int* tcnt = nullptr;  // number of tiles with a free DOF (device), with tl
+  int* tl_buf = nullptr;    // level 0: storage of the order used after a suppression
+  int* tcnt_buf = nullptr;
   double* S64 = nullptr;   // FP64 stencil (level 0 always; others when op64)
   float* S32 = nullptr;    // FP32 stencil (FP32 preconditioner levels)
   double* dinv64 = nullptr;
@@ -136,9 +138,9 @@ struct LevelView {
   const uint8_t* mask;
   int* err;
   int sms;
-  // Operator tiles in processing order: the tcnt[0] tiles that hold a free
-  // DOF first, then the tiles whose 32 nodes are all fixed (identity rows:
-  // y = x there, no coefficients read).
+  // Operator tiles in processing order, or null for index order: the
+  // tcnt[0] tiles that hold a free DOF first, then the tiles whose 32 nodes
+  // are all fixed (identity rows: y = x there, no coefficients read).
   const int* tl;
   const int* tcnt;
 };
@@ -262,6 +264,17 @@ void launch_fix_surround(const Level& L0, const int8_t* cls, int8_t* fixed, cuda
 void launch_fix_design(const Level& L0, int d, const int8_t* fixed, uint8_t* out, cudaStream_t st);
 void launch_fix_mask(const Level& L0, const int8_t* fixed, const uint8_t* base, cudaStream_t st);
 void launch_zero_fixed_void(long n, const uint8_t* xfix, double* g, cudaStream_t st);
+
+// ---- thresholding and the Heaviside projection (k_thresh.cu), Sec. 5 -------
+size_t threshold_scratch_bytes(long n);
+tosolve_status heaviside(const double* rho, long n, double beta, double* out, double* eta_out, int* its_out,
+                         void* scratch, size_t bytes, cudaStream_t st, std::string* why);
+tosolve_status threshold_density(const double* rho, long n, double vfrac, double lo, double hi, const double* grad,
+                                 double theta_deg, double* out, int* accepted, void* scratch, size_t bytes,
+                                 cudaStream_t st, std::string* why);
+tosolve_status threshold_gradient(const double* rho, long n, double lo, double hi, const double* grad, double vu,
+                                  double vl, double theta_deg, double* out, double* alpha_out, void* scratch,
+                                  size_t bytes, cudaStream_t st, std::string* why);
 
 // ---- launchers (k_grad.cu) -----------------------------------------------
 void launch_energy_grad(const Level& L0, int n, const double* u, const double* tabsym,

@@ -176,7 +176,9 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
   uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + (size_t)kStages * kBytes);
   const int tid = threadIdx.x, g = tid / 96, rl = tid % 96, r = rl >> 5, lane = tid & 31;
   const long ntiles = ((long)V.nn + kTN - 1) / kTN;
-  const long nact = *V.tcnt;
+  const bool ordered = V.tl != nullptr;
+  const long nact = ordered ? *V.tcnt : ntiles;
+  auto tile_at = [&](long q) { return ordered ? (long)V.tl[q] : q; };
   const long nk = (long)blockIdx.x < nact ? (nact - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const char* gsrc = reinterpret_cast<const char*>(V.S);
   if (tid == 0) {
@@ -187,14 +189,14 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
   __syncthreads();
   if (tid == 0)
     for (long k = 0; k < kStages && k < nk; ++k)
-      tile_issue(tsm + k * kBytes, gsrc + (size_t)V.tl[blockIdx.x + k * gridDim.x] * kBytes, kBytes,
+      tile_issue(tsm + k * kBytes, gsrc + (size_t)tile_at(blockIdx.x + k * gridDim.x) * kBytes, kBytes,
                  &bars[k]);
   long k = 0;
   for (; k < nk; ++k) {
     const int s = (int)(k % kStages);
     const bool got = tile_wait(&bars[s], (uint32_t)((k / kStages) & 1));
     if (__syncthreads_or(!got)) break;
-    const long node = (long)V.tl[blockIdx.x + k * gridDim.x] * kTN + lane;
+    const long node = tile_at(blockIdx.x + k * gridDim.x) * kTN + lane;
     const bool live = node < V.nn;
     const int i = node % V.Lx, j = (node / V.Lx) % V.Ly, l = node / ((long)V.Lx * V.Ly);
     if (live) parts[g][rl] = plane_row(V, sbuf + (size_t)s * 243 * kTN + lane, node, i, j, l, r, g, ld);
@@ -202,7 +204,7 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
     if (tid == 0 && k + kStages < nk) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tile_issue(tsm + (size_t)s * kBytes,
-                 gsrc + (size_t)V.tl[blockIdx.x + (k + kStages) * gridDim.x] * kBytes, kBytes, &bars[s]);
+                 gsrc + (size_t)tile_at(blockIdx.x + (k + kStages) * gridDim.x) * kBytes, kBytes, &bars[s]);
     }
     if (g == 0 && live) row(node, r, sum3(parts[0][rl], parts[1][rl], parts[2][rl]));
     __syncthreads();  // parts are free
@@ -215,7 +217,7 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
   if (k < nk) return;
   if (g == 0)  // tiles of fixed DOFs only: identity rows
     for (long q = nact + blockIdx.x; q < ntiles; q += gridDim.x) {
-      const long node = (long)V.tl[q] * kTN + lane;
+      const long node = tile_at(q) * kTN + lane;
       if (node < V.nn) row(node, r, (T)ld(node, r));
     }
 }

@@ -2,6 +2,7 @@
 // plan, the per-design refresh, the graph-captured PCG loop and the
 // gradient.  Every device step is one of the kernels in k_*.cu.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -195,7 +196,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   B += (size_t)ndof0 * 8 * 2 * maxrhs;                // host-step staging f, u
   B += 4 * kMaxPart * 8 + sizeof(DevState) + (size_t)P->ndes * 8 * 2;
   B += (size_t)ndof0 + 2 * (size_t)d.nx * d.ny * d.nz + (size_t)P->ndes;  // fixing (Sec. 6.1)
-  for (int l = 0; l < L; ++l) B += ((size_t)(P->lv[l].nn + kTN - 1) / kTN + 1) * sizeof(int);  // tile order
+  B += ((size_t)(P->lv[0].nn + kTN - 1) / kTN + 1) * sizeof(int);  // level-0 tile order
   if (tf32) {
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
     B += E0 * (P->m + 24) * 4 + (size_t)P->m * 576 * 4 + P->lv[0].ndof * 4;
@@ -226,7 +227,7 @@ void free_all(tosolve_s* h) {
   for (int l = 0; l < kMaxLevels; ++l) {
     Level& L = h->lv[l];
     F(L.mask); F(L.S64); F(L.S32); F(L.dinv64); F(L.dinv32); F(L.b); F(L.v); F(L.r); F(L.z);
-    F(L.K64); F(L.K32); F(L.tl); F(L.tcnt);
+    F(L.K64); F(L.K32); F(L.tl_buf); F(L.tcnt_buf);
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
@@ -458,14 +459,9 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     L.op64 = !fp32 || l == P.L - 1;
     CKC(dalloc(h, &L.mask, v.ndof));
     CKC(cudaMemcpyAsync(L.mask, mask.data(), v.ndof, cudaMemcpyHostToDevice, st));
-    {  // tile order: every tile, in index order, until DOFs are suppressed
-      const int nt = (int)((v.nn + kTN - 1) / kTN);
-      std::vector<int> order(nt);
-      for (int t = 0; t < nt; ++t) order[t] = t;
-      CKC(dalloc(h, &L.tl, nt));
-      CKC(cudaMemcpyAsync(L.tl, order.data(), nt * sizeof(int), cudaMemcpyHostToDevice, st));
-      CKC(dalloc(h, &L.tcnt, 1));
-      CKC(cudaMemcpyAsync(L.tcnt, &nt, sizeof(int), cudaMemcpyHostToDevice, st));
+    if (l == 0) {  // storage of the tile order used after a suppression
+      CKC(dalloc(h, &L.tl_buf, (v.nn + kTN - 1) / kTN));
+      CKC(dalloc(h, &L.tcnt_buf, 1));
     }
     if (v.s64) {  // padding coefficients of the last tile stay zero
       CKC(dalloc(h, &L.S64, op_len(v.nn)));
@@ -837,10 +833,26 @@ static tosolve_status remask(tosolve_t h) {
   }
   long long nfree = 0;
   for (uint8_t v : m) nfree += v == 0;
-  CK(cudaMemcpyAsync(L0.tcnt, &nact, sizeof(int), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(L0.tl, order.data(), nt * sizeof(int), cudaMemcpyHostToDevice, st));
-  CK(cudaStreamSynchronize(st));
   h->free_dofs = nfree;
+  // The stored order always matches the current mask (a batch graph recorded
+  // while an order was in force keeps reading it); the kernels of the
+  // handle's own graph follow it only while some tile is all fixed.
+  CK(cudaMemcpyAsync(L0.tcnt_buf, &nact, sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(L0.tl_buf, order.data(), nt * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  int* want = nact < nt ? L0.tl_buf : nullptr;
+  if (want != L0.tl) {  // the kernel arguments change: record the graph again
+    L0.tl = want;
+    L0.tcnt = want ? L0.tcnt_buf : nullptr;
+    if (h->graph_ready) {
+      cudaGraphExecDestroy(h->gexec);
+      cudaGraphDestroy(h->graph);
+      h->gexec = nullptr;
+      h->graph = nullptr;
+      h->graph_ready = false;
+      return build_graph(h);
+    }
+  }
   return TOSOLVE_OK;
 }
 
@@ -866,6 +878,75 @@ tosolve_status tosolve_fix_variables(tosolve_t h, const double* dcdx_dev, double
   if (s != TOSOLVE_OK) return s;
   CK(cudaStreamSynchronize(st));
   return TOSOLVE_OK;
+}
+
+// ---- thresholding and the Heaviside projection (Sec. 5) ----------------------
+
+size_t tosolve_threshold_scratch_bytes(long long n) {
+  if (n < 0 || n > INT_MAX) return 0;
+  return threshold_scratch_bytes((long)n);
+}
+
+static tosolve_status thresh_args(const double* a, const double* b, long long n, const void* scratch,
+                                  double theta) {
+  if (n < 0 || n > INT_MAX) { g_err = "n must be in 0..2^31-1"; return TOSOLVE_EINVAL; }
+  if (n > 0 && (a == nullptr || b == nullptr)) { g_err = "NULL argument"; return TOSOLVE_EINVAL; }
+  if (n > 0 && scratch == nullptr) { g_err = "scratch is NULL"; return TOSOLVE_EINVAL; }
+  if (!(theta > 0.0 && theta < 180.0)) { g_err = "theta_max must be in (0, 180) degrees"; return TOSOLVE_EINVAL; }
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_heaviside(const double* rho_dev, long long n, double beta, double* out_dev, double* eta,
+                                 int* newton_its, void* scratch_dev, size_t scratch_bytes, void* cuda_stream) {
+  tosolve_status s = thresh_args(rho_dev, out_dev, n, scratch_dev, 90.0);
+  if (s != TOSOLVE_OK) return s;
+  if (!(beta > 0.0)) { g_err = "beta must be > 0"; return TOSOLVE_EINVAL; }
+  if (n == 0) {
+    if (eta) *eta = 0.5;
+    if (newton_its) *newton_its = 0;
+    return TOSOLVE_OK;
+  }
+  return heaviside(rho_dev, (long)n, beta, out_dev, eta, newton_its, scratch_dev, scratch_bytes,
+                   (cudaStream_t)cuda_stream, &g_err);
+}
+
+tosolve_status tosolve_threshold_density(const double* rho_dev, long long n, double vfrac, double round_lo,
+                                         double round_hi, const double* gradL_dev, double theta_max_deg,
+                                         double* out_dev, int* accepted, void* scratch_dev, size_t scratch_bytes,
+                                         void* cuda_stream) {
+  tosolve_status s = thresh_args(rho_dev, out_dev, n, scratch_dev, theta_max_deg);
+  if (s != TOSOLVE_OK) return s;
+  if (n > 0 && gradL_dev == nullptr) { g_err = "gradL is NULL"; return TOSOLVE_EINVAL; }
+  if (!(vfrac >= 0.0 && vfrac <= 1.0)) { g_err = "vfrac must be in [0, 1]"; return TOSOLVE_EINVAL; }
+  if (!(round_lo >= 0.0 && round_lo < round_hi && round_hi <= 1.0)) {
+    g_err = "need 0 <= round_lo < round_hi <= 1";
+    return TOSOLVE_EINVAL;
+  }
+  if (n == 0) {
+    if (accepted) *accepted = 0;
+    return TOSOLVE_OK;
+  }
+  return threshold_density(rho_dev, (long)n, vfrac, round_lo, round_hi, gradL_dev, theta_max_deg, out_dev, accepted,
+                           scratch_dev, scratch_bytes, (cudaStream_t)cuda_stream, &g_err);
+}
+
+tosolve_status tosolve_threshold_gradient(const double* rho_dev, const double* gradL_dev, long long n,
+                                          double round_lo, double round_hi, double vu_min, double vl_max,
+                                          double theta_max_deg, double* out_dev, double* alpha, void* scratch_dev,
+                                          size_t scratch_bytes, void* cuda_stream) {
+  tosolve_status s = thresh_args(rho_dev, out_dev, n, scratch_dev, theta_max_deg);
+  if (s != TOSOLVE_OK) return s;
+  if (n > 0 && gradL_dev == nullptr) { g_err = "gradL is NULL"; return TOSOLVE_EINVAL; }
+  if (!(round_lo >= 0.0 && round_lo < round_hi && round_hi <= 1.0)) {
+    g_err = "need 0 <= round_lo < round_hi <= 1";
+    return TOSOLVE_EINVAL;
+  }
+  if (n == 0) {
+    if (alpha) *alpha = 0.0;
+    return TOSOLVE_OK;
+  }
+  return threshold_gradient(rho_dev, (long)n, round_lo, round_hi, gradL_dev, vu_min, vl_max, theta_max_deg, out_dev,
+                            alpha, scratch_dev, scratch_bytes, (cudaStream_t)cuda_stream, &g_err);
 }
 
 tosolve_status tosolve_release_variables(tosolve_t h) {

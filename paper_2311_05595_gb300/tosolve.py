@@ -100,6 +100,12 @@ def _load():
         "tosolve_trim_pool": ([sz], i),
         "tosolve_fix_variables": ([vp, vp, C.c_double, C.c_double, C.c_double, vp, P(C.c_longlong)], i),
         "tosolve_release_variables": ([vp], i),
+        "tosolve_threshold_scratch_bytes": ([C.c_longlong], sz),
+        "tosolve_heaviside": ([vp, C.c_longlong, C.c_double, vp, P(C.c_double), P(i), vp, sz, vp], i),
+        "tosolve_threshold_density": ([vp, C.c_longlong, C.c_double, C.c_double, C.c_double, vp, C.c_double,
+                                       vp, P(i), vp, sz, vp], i),
+        "tosolve_threshold_gradient": ([vp, vp, C.c_longlong, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, vp, P(C.c_double), vp, sz, vp], i),
         "tosolve_last_error": ([vp], C.c_char_p),
         "tosolve_destroy": ([vp], None),
     }
@@ -309,6 +315,47 @@ def tosolve_fix_variables(h, dcdx_dev=None, rho_lo: float = 1e-6, rho_hi: float 
     _check(h, _lib.tosolve_fix_variables(h, _ptr(dcdx_dev), rho_lo, rho_hi, eps_grad, _ptr(fixed_dev),
                                          C.byref(n)), "tosolve_fix_variables")
     return n.value
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def tosolve_threshold_scratch_bytes(n: int) -> int:
+    return int(_lib.tosolve_threshold_scratch_bytes(n))
+
+
+def tosolve_heaviside(rho_dev, beta: float, out_dev, scratch_dev, stream=None) -> tuple[float, int]:
+    """Sec. 5 Heaviside projection; returns (eta, Newton iterations)."""
+    eta, its = C.c_double(0.0), C.c_int(0)
+    _check(None, _lib.tosolve_heaviside(_ptr(rho_dev), rho_dev.numel(), beta, _ptr(out_dev), C.byref(eta),
+                                        C.byref(its), _ptr(scratch_dev), scratch_dev.numel() * scratch_dev.element_size(),
+                                        _stream_ptr(stream)), "tosolve_heaviside")
+    return eta.value, its.value
+
+
+def tosolve_threshold_density(rho_dev, vfrac: float, gradL_dev, out_dev, scratch_dev, round_lo: float = 0.05,
+                              round_hi: float = 0.95, theta_max_deg: float = 89.9, stream=None) -> bool:
+    acc = C.c_int(0)
+    _check(None, _lib.tosolve_threshold_density(_ptr(rho_dev), rho_dev.numel(), vfrac, round_lo, round_hi,
+                                                _ptr(gradL_dev), theta_max_deg, _ptr(out_dev), C.byref(acc),
+                                                _ptr(scratch_dev), scratch_dev.numel() * scratch_dev.element_size(),
+                                                _stream_ptr(stream)), "tosolve_threshold_density")
+    return bool(acc.value)
+
+
+def tosolve_threshold_gradient(rho_dev, gradL_dev, out_dev, scratch_dev, round_lo: float = 0.05,
+                               round_hi: float = 0.95, vu_min: float = 0.3, vl_max: float = 0.7,
+                               theta_max_deg: float = 89.9, stream=None) -> float:
+    alpha = C.c_double(0.0)
+    _check(None, _lib.tosolve_threshold_gradient(_ptr(rho_dev), _ptr(gradL_dev), rho_dev.numel(), round_lo,
+                                                 round_hi, vu_min, vl_max, theta_max_deg, _ptr(out_dev),
+                                                 C.byref(alpha), _ptr(scratch_dev),
+                                                 scratch_dev.numel() * scratch_dev.element_size(),
+                                                 _stream_ptr(stream)), "tosolve_threshold_gradient")
+    return alpha.value
 
 
 def tosolve_release_variables(h) -> None:
