@@ -165,7 +165,7 @@ __device__ __forceinline__ dfloat sum3(Dot2 a, const Dot2& b, const Dot2& c) {
 // Every wait is bounded: if a copy does not land in time the block sets
 // *V.err, waits (bounded) for its other copies and stops; the result is then
 // invalid and the host reports the error.
-template <typename T, typename LD, typename ROW>
+template <bool kOrd, typename T, typename LD, typename ROW>
 __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW row) {
   extern __shared__ __align__(128) unsigned char tsm[];
   using O = op_t<T>;
@@ -176,9 +176,8 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
   uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + (size_t)kStages * kBytes);
   const int tid = threadIdx.x, g = tid / 96, rl = tid % 96, r = rl >> 5, lane = tid & 31;
   const long ntiles = ((long)V.nn + kTN - 1) / kTN;
-  const bool ordered = V.tl != nullptr;
-  const long nact = ordered ? *V.tcnt : ntiles;
-  auto tile_at = [&](long q) { return ordered ? (long)V.tl[q] : q; };
+  const long nact = kOrd ? *V.tcnt : ntiles;
+  auto tile_at = [&](long q) { return kOrd ? (long)V.tl[q] : q; };
   const long nk = (long)blockIdx.x < nact ? (nact - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const char* gsrc = reinterpret_cast<const char*>(V.S);
   if (tid == 0) {
@@ -214,7 +213,7 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
     for (long q = k; q < nk && q < k + kStages; ++q)
       tile_wait(&bars[q % kStages], (uint32_t)((q / kStages) & 1));
   }
-  if (k < nk) return;
+  if (!kOrd || k < nk) return;
   if (g == 0)  // tiles of fixed DOFs only: identity rows
     for (long q = nact + blockIdx.x; q < ntiles; q += gridDim.x) {
       const long node = tile_at(q) * kTN + lane;
@@ -282,10 +281,10 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle hc, int use_
 
 // ---- multigrid cycle ------------------------------------------------------
 
-template <typename T>
+template <typename T, bool kOrd>
 __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_vc_pre(LevelView<T> V, const T* __restrict__ b,
                                                         const T* __restrict__ v, T* __restrict__ r_out) {
-  for_each_row(V, [&](long nb, int c) { return ld_nc(v + 3 * nb + c); }, [&](long node, int r, T y) {
+  for_each_row<kOrd>(V, [&](long nb, int c) { return ld_nc(v + 3 * nb + c); }, [&](long node, int r, T y) {
     const long d = 3 * node + r;
     r_out[d] = b[d] - y;
   });
@@ -378,10 +377,10 @@ __global__ void k_vc_prolong(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc,
 }
 
 // Post-smoothing: z = v + omega D^-1 (b - A v).
-template <typename T>
+template <typename T, bool kOrd>
 __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_vc_post(LevelView<T> V, T omega, const T* __restrict__ b,
                                                          const T* __restrict__ v, T* __restrict__ z) {
-  for_each_row(V, [&](long nb, int c) { return ld_nc(v + 3 * nb + c); }, [&](long node, int r, T y) {
+  for_each_row<kOrd>(V, [&](long nb, int c) { return ld_nc(v + 3 * nb + c); }, [&](long node, int r, T y) {
     const long d = 3 * node + r;
     z[d] = v[d] + omega * V.dinv[d] * (b[d] - y);
   });
@@ -438,7 +437,7 @@ __global__ void k_cg_prep(int nn, const uint8_t* __restrict__ mask, double* __re
 // b0 = (T) r, v0 = omega D0^-1 b0, and the last block runs the initial
 // convergence test (||f||^2 from part_ff) and sets the loop condition;
 // mode 2 (after the loop): the last block stores the true residual.
-template <typename T>
+template <typename T, bool kOrd>
 __global__ void __launch_bounds__(kTileThreads)
     k_cg_residual(LevelView<double> V, const double* __restrict__ f, const double* __restrict__ u,
                   double* __restrict__ rv, T* __restrict__ b0, const op_t<T>* __restrict__ dinv0,
@@ -446,7 +445,7 @@ __global__ void __launch_bounds__(kTileThreads)
                   int mode, DevState* __restrict__ ds, unsigned* cnt, cudaGraphConditionalHandle hc,
                   int use_cond) {
   double s = 0.0;
-  for_each_row(V, [&](long nb, int c) { return ld_nc(u + 3 * nb + c); }, [&](long node, int r, double y) {
+  for_each_row<kOrd>(V, [&](long nb, int c) { return ld_nc(u + 3 * nb + c); }, [&](long node, int r, double y) {
     const long d = 3 * node + r;
     const double rd = f[d] - y;
     rv[d] = rd;
@@ -521,11 +520,12 @@ __global__ void k_cg_dir(int nn, const T* __restrict__ z, double* __restrict__ p
 
 // q = K p (FP64) and partial p^T q; the last block forms alpha = rz / p^T q
 // (a non-positive or non-finite value is a breakdown).
+template <bool kOrd>
 __global__ void __launch_bounds__(kTileThreads)
     k_cg_apply(LevelView<double> V, const double* __restrict__ p, double* __restrict__ q, double* part,
                DevState* __restrict__ ds, unsigned* cnt) {
   double s = 0.0;
-  for_each_row(V, [&](long nb, int c) { return ld_nc(p + 3 * nb + c); }, [&](long node, int r, double y) {
+  for_each_row<kOrd>(V, [&](long nb, int c) { return ld_nc(p + 3 * nb + c); }, [&](long node, int r, double y) {
     const long d = 3 * node + r;
     q[d] = y;
     s += p[d] * y;
@@ -641,10 +641,10 @@ __global__ void k_cg_update(int nn, double* __restrict__ u, double* __restrict__
 }
 
 // Diagnostic: y = A x in the level's stored precision, FP64 in and out.
-template <typename T>
+template <typename T, bool kOrd>
 __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_apply_diag(LevelView<T> V, const double* __restrict__ x,
                                                             double* __restrict__ y) {
-  for_each_row(V, [&](long nb, int c) { return (T)ld_nc(x + 3 * nb + c); },
+  for_each_row<kOrd>(V, [&](long nb, int c) { return (T)ld_nc(x + 3 * nb + c); },
                [&](long node, int r, T v) { y[3 * node + r] = (double)v; });
 }
 
@@ -658,6 +658,20 @@ inline int grid_nodes(long nn) { return parts_for(nn); }
 
 // Grid of a tile kernel over level L: persistent blocks, at most as many as
 // are resident at once (and at most kMaxPart, the partial-sum capacity).
+// Launches the stencil kernel variant that follows the level's tile order
+// (kOrd = true, only while a suppression leaves tiles of fixed DOFs) or the
+// plain index order.
+#define TILE_ORD(V, ...)                  \
+  do {                                    \
+    if ((V).tl != nullptr) {              \
+      constexpr bool kOrd = true;         \
+      __VA_ARGS__;                        \
+    } else {                              \
+      constexpr bool kOrd = false;        \
+      __VA_ARGS__;                        \
+    }                                     \
+  } while (0)
+
 template <typename T>
 int tile_grid(const Level& L) {
   const long nt = ((long)L.nn + kTN - 1) / kTN;
@@ -711,8 +725,8 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
     launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, 0, F.r,
                  F.sms, st);
   else if (!use_tc)
-    k_vc_pre<T><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(V, (const T*)F.b, (const T*)F.v,
-                                                                       (T*)F.r);
+    TILE_ORD(V, (k_vc_pre<T, kOrd><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(
+                    V, (const T*)F.b, (const T*)F.v, (T*)F.r)));
   k_vc_restrict<T><<<grid_nodes(C.nn), kRowThreads, 0, st>>>(
       F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, C.mask, (const T*)F.r, (T*)C.b,
       c_coarsest ? nullptr : dinv_of<T>(C), omega, c_coarsest ? nullptr : (T*)C.v);
@@ -732,8 +746,8 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
                  F.sms, st);
     return;
   }
-  k_vc_post<T><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(V, omega, (const T*)F.b,
-                                                                        (const T*)F.v, (T*)F.z);
+  TILE_ORD(V, (k_vc_post<T, kOrd><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(
+                  V, omega, (const T*)F.b, (const T*)F.v, (T*)F.z)));
 }
 
 }  // namespace
@@ -784,9 +798,11 @@ void launch_cg_residual(int vt, const Level& L0, double omega, const double* f, 
                         mode, ds, cnt, hc, use_cond)));
     return;
   }
-  VT_DISPATCH(vt, (k_cg_residual<T><<<tile_grid<double>(L0), kTileThreads, tile_smem<double>(), st>>>(
-                      view<double>(L0), f, u, r, (T*)L0.b, dinv_of<T>(L0), (T)omega, (T*)L0.v,
-                      part, part_ff, np, mode, ds, cnt, hc, use_cond)));
+  const LevelView<double> V0 = view<double>(L0);
+  VT_DISPATCH(vt, TILE_ORD(V0, (k_cg_residual<T, kOrd><<<tile_grid<double>(L0), kTileThreads,
+                                                         tile_smem<double>(), st>>>(
+                                   V0, f, u, r, (T*)L0.b, dinv_of<T>(L0), (T)omega, (T*)L0.v, part,
+                                   part_ff, np, mode, ds, cnt, hc, use_cond))));
 }
 
 void launch_cg_dots_rz(int vt, const Level& L0, const double* r, const double* q, double* part_rz,
@@ -807,8 +823,9 @@ void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, 
     k_cg_apply_y<<<np, kRowThreads, 0, st>>>(L0.nn, p, q, part, ds, cnt);
     return;
   }
-  k_cg_apply<<<tile_grid<double>(L0), kTileThreads, tile_smem<double>(), st>>>(view<double>(L0), p, q,
-                                                                              part, ds, cnt);
+  const LevelView<double> V0 = view<double>(L0);
+  TILE_ORD(V0, (k_cg_apply<kOrd><<<tile_grid<double>(L0), kTileThreads, tile_smem<double>(), st>>>(
+                   V0, p, q, part, ds, cnt)));
 }
 
 void launch_cg_update(int vt, const Level& L0, double omega, double* u, double* r, const double* p,
@@ -833,28 +850,36 @@ void launch_apply_diag(int vt, const Level& L, const double* x, double* y, cudaS
     launch_vec_out(vt, nd, L.r, y, st);
     return;
   }
-  VT_DISPATCH(vt, (k_apply_diag<T><<<tile_grid<T>(L), kTileThreads, tile_smem<T>(), st>>>(view<T>(L), x,
-                                                                                          y)));
+  VT_DISPATCH(vt, TILE_ORD(view<T>(L), (k_apply_diag<T, kOrd><<<tile_grid<T>(L), kTileThreads,
+                                                                   tile_smem<T>(), st>>>(view<T>(L), x, y))));
 }
 
-template <typename T>
+template <typename T, bool kOrd>
 cudaError_t allow_tile_smem() {
   const int b = (int)tile_smem<T>();
   const int b64 = (int)tile_smem<double>();
-  cudaError_t e = cudaFuncSetAttribute(k_vc_pre<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_vc_post<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaError_t e = cudaFuncSetAttribute(k_vc_pre<T, kOrd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cg_residual<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b64);
+    e = cudaFuncSetAttribute(k_vc_post<T, kOrd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_apply_diag<T, kOrd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_residual<T, kOrd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b64);
   return e;
 }
 
 cudaError_t configure_tile_kernels() {
-  cudaError_t e = allow_tile_smem<double>();
-  if (e == cudaSuccess) e = allow_tile_smem<float>();
-  if (e == cudaSuccess) e = allow_tile_smem<dfloat>();
+  cudaError_t e = allow_tile_smem<double, false>();
+  if (e == cudaSuccess) e = allow_tile_smem<float, false>();
+  if (e == cudaSuccess) e = allow_tile_smem<dfloat, false>();
+  if (e == cudaSuccess) e = allow_tile_smem<double, true>();
+  if (e == cudaSuccess) e = allow_tile_smem<float, true>();
+  if (e == cudaSuccess) e = allow_tile_smem<dfloat, true>();
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cg_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_cg_apply<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tile_smem<double>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cg_apply<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tile_smem<double>());
   return e;
 }
