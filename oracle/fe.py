@@ -33,7 +33,7 @@ class Model:
         self.p = prob
         k, n = prob.degree, prob.n_mr
         self.k, self.n = k, n
-        self.Ktab = fem.subcell_stiffness(k, n, prob.nu)  # (m, d, d)
+        self.Ktab = fem.subcell_stiffness(k, n, prob.nu, family=getattr(prob, "family", "lagrange"))  # (m, d, d)
         self.edofs = mesh.element_dofs(prob.nx, prob.ny, prob.nz, k)
         self.sub2cell = mesh.subcell_density_index(prob.nx, prob.ny, prob.nz, n)
         d = getattr(prob, "d_mr", None) or n

@@ -1,7 +1,13 @@
-"""Element library of the oracle: Lagrange hexahedra of degree k = 1..3.
+"""Element library of the oracle: Lagrange hexahedra of degree k = 1..3 and
+the 20-node serendipity hexahedron.
 
 Section 2.1 (finite element types): rectangular prismatic elements, three
-displacement DOFs per node, Lagrange elements with (k+1)^3 nodes.
+displacement DOFs per node, Lagrange elements with (k+1)^3 nodes, and the
+serendipity family, whose quadratic member has nodes at the 8 vertices and
+the 12 edge midpoints only.  The serendipity element is written on the
+27-node lattice of the quadratic Lagrange element (same local numbering),
+with identically zero shape functions at the 6 face centres and the centre:
+its matrices are 81 x 81 with zero rows and columns there.
 Section 3.3 (assembly, Eq. matrixK_mr): a displacement element split into
 n^3 density elements ("subcells"); the subcell matrices
     K^(e_i) = int_{Omega_{e_i}} B^T D B dOmega
@@ -72,6 +78,52 @@ def shape_3d(k: int, xi: float, eta: float, zeta: float, h: float = 1.0):
     return N, dN * (2.0 / h)
 
 
+def serendipity2_shape(xi: float, eta: float, zeta: float, h: float = 1.0):
+    """The 20-node serendipity shape functions on the 27-node lattice order.
+
+    A vertex (xi_a, eta_a, zeta_a in {-1, 1}) has
+        N = (1 + xi xi_a)(1 + eta eta_a)(1 + zeta zeta_a)(xi xi_a + eta eta_a + zeta zeta_a - 2) / 8,
+    an edge midpoint with xi_a = 0 has N = (1 - xi^2)(1 + eta eta_a)(1 + zeta zeta_a) / 4
+    (and the same with the roles of the coordinates exchanged); face centres
+    and the centre have N = 0.  Returns N (27,) and the physical gradient
+    dN (27, 3) for a cube of edge h."""
+    x = (xi, eta, zeta)
+    N = np.zeros(27)
+    dN = np.zeros((27, 3))
+    for iz in range(3):
+        for iy in range(3):
+            for ix in range(3):
+                a = ix + 3 * (iy + 3 * iz)
+                c = (ix - 1, iy - 1, iz - 1)
+                mids = [q for q in range(3) if c[q] == 0]
+                if len(mids) == 0:
+                    f = [1.0 + x[q] * c[q] for q in range(3)]
+                    s = x[0] * c[0] + x[1] * c[1] + x[2] * c[2] - 2.0
+                    N[a] = f[0] * f[1] * f[2] * s / 8.0
+                    for q in range(3):
+                        o = [f[r] for r in range(3) if r != q]
+                        dN[a, q] = (c[q] * o[0] * o[1] * s + f[0] * f[1] * f[2] * c[q]) / 8.0
+                elif len(mids) == 1:
+                    m = mids[0]
+                    f = [(1.0 - x[q] * x[q]) if q == m else (1.0 + x[q] * c[q]) for q in range(3)]
+                    df = [(-2.0 * x[q]) if q == m else c[q] for q in range(3)]
+                    N[a] = f[0] * f[1] * f[2] / 4.0
+                    dN[a, 0] = df[0] * f[1] * f[2] / 4.0
+                    dN[a, 1] = f[0] * df[1] * f[2] / 4.0
+                    dN[a, 2] = f[0] * f[1] * df[2] / 4.0
+    return N, dN * (2.0 / h)
+
+
+def serendipity2_present() -> np.ndarray:
+    """(27,) bool: the 20 lattice positions that carry a serendipity node."""
+    out = np.zeros(27, dtype=bool)
+    for iz in range(3):
+        for iy in range(3):
+            for ix in range(3):
+                out[ix + 3 * (iy + 3 * iz)] = (ix % 2) + (iy % 2) + (iz % 2) <= 1
+    return out
+
+
 def elasticity_D(nu: float, E: float = 1.0) -> np.ndarray:
     """Isotropic linear-elastic constitutive matrix (Voigt, engineering
     shear strains), the D of Eq. matrixK."""
@@ -103,10 +155,44 @@ def strain_displacement(dNdx: np.ndarray) -> np.ndarray:
     return B
 
 
-def subcell_stiffness(k: int, n: int, nu: float, h: float = 1.0) -> np.ndarray:
+def subcell_stiffness(k: int, n: int, nu: float, h: float = 1.0, family: str = "lagrange") -> np.ndarray:
     """The stacked subcell stiffness table of Eq. matrixK_mr (a fresh copy of
-    the memoised table: Section 3.3 computes it once for a regular mesh)."""
+    the memoised table: Section 3.3 computes it once for a regular mesh).
+    family 'serendipity' (k = 2): the 20-node element on the 27-node lattice."""
+    if family == "serendipity":
+        if k != 2:
+            raise ValueError("the serendipity element is built for degree 2")
+        return _subcell_stiffness_s2(int(n), float(nu), float(h)).copy()
     return _subcell_stiffness(int(k), int(n), float(nu), float(h)).copy()
+
+
+@functools.lru_cache(maxsize=8)
+def _subcell_stiffness_s2(n: int, nu: float, h: float) -> np.ndarray:
+    """As _subcell_stiffness for the 20-node serendipity element: its
+    integrand is also of degree at most 4 in each coordinate, so 3 Gauss
+    points per axis and subcell are exact."""
+    D = elasticity_D(nu)
+    gp, gw = nleg.leggauss(3)
+    jac = (h / 2.0) ** 3
+    half = 1.0 / n
+    out = np.zeros((n ** 3, 81, 81))
+    for c in range(n):
+        for b in range(n):
+            for a in range(n):
+                cx = -1.0 + (2 * a + 1) / n
+                cy = -1.0 + (2 * b + 1) / n
+                cz = -1.0 + (2 * c + 1) / n
+                Ki = np.zeros((81, 81))
+                for qz in range(3):
+                    for qy in range(3):
+                        for qx in range(3):
+                            wq = gw[qx] * gw[qy] * gw[qz] * half ** 3
+                            _, dN = serendipity2_shape(cx + half * gp[qx], cy + half * gp[qy],
+                                                       cz + half * gp[qz], h)
+                            B = strain_displacement(dN)
+                            Ki += wq * jac * (B.T @ D @ B)
+                out[a + n * (b + n * c)] = Ki
+    return out
 
 
 @functools.lru_cache(maxsize=32)

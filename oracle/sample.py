@@ -24,7 +24,7 @@ class Sampler:
     def __init__(self, prob):
         self.p = prob
         self.k, self.n = prob.degree, prob.n_mr
-        self.K = fem.subcell_stiffness(self.k, self.n, prob.nu)  # (m, d, d)
+        self.K = fem.subcell_stiffness(self.k, self.n, prob.nu, family=getattr(prob, "family", "lagrange"))
         self.Dx, self.Dy, self.Dz = self.n * prob.nx, self.n * prob.ny, self.n * prob.nz
         self.offs, self.wts = filt.filter_offsets(self.n, prob.rmin) if prob.rmin > 0 else ([(0, 0, 0)], [1.0])
         self.slv = None

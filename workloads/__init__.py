@@ -72,6 +72,9 @@ class Problem:
     elem_q1: np.ndarray | None = None
     # design cells per element edge (None: the density grid, d_mr = n_mr)
     d_mr: int | None = None
+    # element family: "lagrange", or "serendipity" (degree 2: the 20-node
+    # element on the degree-2 lattice, no nodes at face and cell centres)
+    family: str = "lagrange"
 
     @property
     def lattice(self) -> tuple[int, int, int]:
@@ -282,6 +285,33 @@ def batched_instances(count: int, seed: int, *, min_nx: int = 32, max_nx: int = 
         p.name = f"batch{b}_{nx}x{ny}x{nz}_rhs{nrhs}"
         out.append(p)
     return out
+
+
+def serendipity_absent_nodes(p: Problem) -> np.ndarray:
+    """(nnodes,) bool: the nodes of the degree-2 lattice that no 20-node
+    serendipity element has: face centres and element centres (two or three
+    odd lattice coordinates)."""
+    Lx, Ly, Lz = p.lattice
+    n = np.arange(Lx * Ly * Lz)
+    i, j, l = n % Lx, (n // Lx) % Ly, n // (Lx * Ly)
+    return (i % 2) + (j % 2) + (l % 2) >= 2
+
+
+def with_serendipity(p: Problem) -> Problem:
+    """The same problem with 20-node serendipity elements on its degree-2
+    lattice: the lattice nodes the element does not have are held at 0 with
+    the supports (they carry no unknown).  Loads there must be zero."""
+    if p.degree != 2:
+        raise ValueError("the serendipity element is built for degree 2")
+    q = Problem(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    absent = serendipity_absent_nodes(p)
+    if np.any(np.asarray(p.f)[:, np.repeat(absent, 3)] != 0.0):
+        raise ValueError("loads on nodes the serendipity element does not have")
+    q.mask = (np.asarray(p.mask) != 0) | np.repeat(absent, 3)
+    q.mask = q.mask.astype(np.uint8)
+    q.family = "serendipity"
+    q.name = p.name.replace("_k2", "_s2")
+    return q
 
 
 def with_mixed_degree(p: Problem, q1_fraction: float, seed: int) -> Problem:
