@@ -657,6 +657,74 @@ def run_fix(args):
     print(json.dumps(line), flush=True)
 
 
+SERENDIPITY = dict(name="cantilever_q2_vs_s2_48x24x24_n2_density_96x48x48", nx=48, ny=24, nz=24, n_mr=2,
+                   rmin=1.5, rtol=1e-8)
+
+
+def run_serendipity(args):
+    """Sec. 2.1 element families on one mesh: the degree-2 cantilever
+    (48x24x24 elements, n = 2, the C1 density grid and smooth design) with
+    27-node Lagrange and with 20-node serendipity elements.  Cold solves
+    (u0 = 0) to 1e-8, CUDA events, L2 flushed between solves; solved
+    unknowns per second for each family and preconditioner precision."""
+    import torch
+
+    import workloads
+    from paper_2311_05595_gb300 import tosolve as T
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    S = SERENDIPITY
+    base = workloads.cantilever(S["nx"], S["ny"], S["nz"], degree=2, n_mr=S["n_mr"], rmin=S["rmin"],
+                                density="smooth", seed=0)
+    rows = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    for fam, p in (("lagrange", base), ("serendipity", workloads.with_serendipity(base))):
+        x = torch.tensor(p.x, device=dev)
+        f = torch.tensor(p.f, device=dev)
+        u = torch.zeros_like(f)
+        for label, prec in (("fp32x2", T.PREC_FP32X2), ("fp64", T.PREC_FP64)):
+            d = T.make_desc(p.nx, p.ny, p.nz, degree=2, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin, nu=p.nu,
+                            penal=p.penal, precision=prec, max_rhs=1,
+                            family=T.FAMILY_SERENDIPITY if fam == "serendipity" else T.FAMILY_LAGRANGE)
+            s = T.Solver(d, p.mask, stream)
+            ms, its = [], []
+            with torch.cuda.stream(stream):
+                T.tosolve_set_densities(s.h, x)
+                for rep in range(args.warmup + args.steps):
+                    u.zero_()
+                    flush.zero_()
+                    stream.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    info = T.tosolve_solve(s.h, f, 1, u, S["rtol"], 5000)
+                    e1.record(stream)
+                    stream.synchronize()
+                    if rep >= args.warmup:
+                        ms.append(e0.elapsed_time(e1))
+                        its.append(info.total_iterations)
+                c = T.tosolve_compliance_grad(s.h, u, f, 1)
+            nfree = T.tosolve_free_dofs(s.h)
+            med = statistics.median(ms)
+            rows[f"{fam}_{label}"] = {"free_dofs": nfree, "ms": med, "iterations": statistics.median(its),
+                                      "dofs_per_s": nfree / (med * 1e-3), "compliance": float(c[0])}
+            s.close()
+    clocks = sampler.stop()
+    head = rows["serendipity_fp32x2"]
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "value": head["dofs_per_s"], "ms_per_step": head["ms"],
+            "config": {"workload": S["name"], "rtol": S["rtol"], "start": "u0 = 0 every solve",
+                       "l2": f"flushed between solves ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "coarse_levels": "degree-2 Lagrange for both families"},
+            "rows": rows, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 SERVE = dict(name="serve256_q1q2_density_64x32x32_to_384x192x192_poisson200", designs=256,
              rate=200.0, requests=2000, seed=77, rtol=1e-8, budget_gib=240, rmin=1.5)
 
@@ -800,7 +868,8 @@ def main():
     ap.add_argument("--variants", default="fp32,tf32,fp32x2",
                     help="mixed-precision variants timed beside FP64 (comma list)")
     ap.add_argument("--workload", default="cantilever",
-                    choices=["cantilever", "bridge_q2", "bridge_mixed", "batch64", "serve", "ibeam_fix"],
+                    choices=["cantilever", "bridge_q2", "bridge_mixed", "batch64", "serve", "ibeam_fix",
+                             "serendipity"],
                     help="bridge_q2: the degree-2 bridge; batch64: the 64-instance batched "
                          "solve; serve: the serving loop (each its own JSON line)")
     ap.add_argument("--designs", type=int, default=SERVE["designs"])
@@ -822,6 +891,8 @@ def main():
         run_serve(args)
     elif args.workload == "ibeam_fix":
         run_fix(args)
+    elif args.workload == "serendipity":
+        run_serendipity(args)
     else:
         run_gpu(args)
 

@@ -78,7 +78,7 @@ typedef enum {
 /* Problem and solver description (Sec. 2, 3.1, 7 intro). */
 typedef struct {
   int nx, ny, nz;         /* displacement elements per axis, >= 1           */
-  int degree;             /* Lagrange degree k: 1 or 2                      */
+  int degree;             /* degree k: 1 or 2 (see family)                  */
   int n_mr;               /* density cells per element edge, 1..8           */
   int d_mr;               /* design cells per element edge, 1..n_mr (0 =   */
                           /* n_mr); below n_mr rmin must be > 0            */
@@ -89,10 +89,17 @@ typedef struct {
   int mg_levels;          /* multigrid levels >= 1 (each halves the mesh;   */
                           /*   nx, ny, nz divisible by 2^(levels-1))        */
   int precision;          /* tosolve_precision of the preconditioner        */
-  double omega;           /* damped-Jacobi factor (0 => 0.5, Sec. 7 intro)  */
+  double omega;           /* damped-Jacobi factor (0 => 0.5, Sec. 7 intro;  */
+                          /*   0.3 for the serendipity element)             */
   int cycle_gamma;        /* cycles per level: 1 = V-cycle (0 => 1; the     */
                           /*   only value this build accepts)               */
   int max_rhs;            /* load cases per solve call, >= 1 (0 => 1)       */
+  int family;             /* element family (Sec. 2.1): 0 Lagrange; 1 the   */
+                          /*   20-node serendipity element (degree 2 only), */
+                          /*   on the degree-2 lattice without the face and */
+                          /*   element-centre nodes, which the library holds */
+                          /*   at 0 with the supports; its coarse levels are */
+                          /*   degree-2 Lagrange                            */
 } tosolve_desc;
 
 typedef struct {

@@ -50,10 +50,43 @@ __device__ __forceinline__ void lag_coef(int j, int deriv, double c[3]) {
   }
 }
 
+// Reference gradient of the 20-node serendipity shape function at lattice
+// position (ax, ay, az) in 0..2 (Sec. 2.1): a vertex has
+// N = (1 + x c_x)(1 + y c_y)(1 + z c_z)(x c_x + y c_y + z c_z - 2) / 8, an
+// edge midpoint (one coordinate c = 0) N = (1 - t^2)(1 + ...)(1 + ...) / 4;
+// face and element centres have no node (zero).
+__device__ __forceinline__ void s2_grad(int ax, int ay, int az, double x, double y, double z, double g[3]) {
+  const int c[3] = {ax - 1, ay - 1, az - 1};
+  const double p[3] = {x, y, z};
+  const int nmid = (c[0] == 0) + (c[1] == 0) + (c[2] == 0);
+  g[0] = g[1] = g[2] = 0.0;
+  if (nmid == 0) {
+    double f[3];
+    for (int q = 0; q < 3; ++q) f[q] = 1.0 + p[q] * c[q];
+    const double sv = p[0] * c[0] + p[1] * c[1] + p[2] * c[2] - 2.0;
+    const double prod = f[0] * f[1] * f[2];
+    for (int q = 0; q < 3; ++q) {
+      const double others = q == 0 ? f[1] * f[2] : (q == 1 ? f[0] * f[2] : f[0] * f[1]);
+      g[q] = (c[q] * others * sv + prod * c[q]) * 0.125;
+    }
+  } else if (nmid == 1) {
+    double f[3], df[3];
+    for (int q = 0; q < 3; ++q) {
+      if (c[q] == 0) { f[q] = 1.0 - p[q] * p[q]; df[q] = -2.0 * p[q]; }
+      else { f[q] = 1.0 + p[q] * c[q]; df[q] = c[q]; }
+    }
+    g[0] = df[0] * f[1] * f[2] * 0.25;
+    g[1] = f[0] * df[1] * f[2] * 0.25;
+    g[2] = f[0] * f[1] * df[2] * 0.25;
+  }
+}
+
 // K^(e_i) for the n^3 subcells of an element of edge h (E = 1), full 81 x 81:
 // 3-point Gauss-Legendre per axis in each subcell (exact: the integrand has
-// degree <= 4 per axis).  One block per subcell.
-__global__ void k_q2_subcell_table(int n, double nu, double h, double* __restrict__ tab) {
+// degree <= 4 per axis, for both element families).  One block per subcell.
+// family 1: the serendipity element (zero rows and columns at the face and
+// element centres).
+__global__ void k_q2_subcell_table(int n, double nu, double h, int family, double* __restrict__ tab) {
   __shared__ double gr[27][kNE][3];  // physical gradients at the 27 points
   const int sub = blockIdx.x;
   const int sa = sub % n, sb = (sub / n) % n, sc = sub / (n * n);
@@ -68,9 +101,17 @@ __global__ void k_q2_subcell_table(int n, double nu, double h, double* __restric
     const double eta = -1.0 + (2 * sb + 1) * half + half * gp[qy];
     const double zeta = -1.0 + (2 * sc + 1) * half + half * gp[qz];
     const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
-    gr[q][a][0] = s * dlag(ax, xi) * lag(ay, eta) * lag(az, zeta);
-    gr[q][a][1] = s * lag(ax, xi) * dlag(ay, eta) * lag(az, zeta);
-    gr[q][a][2] = s * lag(ax, xi) * lag(ay, eta) * dlag(az, zeta);
+    if (family == 1) {
+      double g[3];
+      s2_grad(ax, ay, az, xi, eta, zeta, g);
+      gr[q][a][0] = s * g[0];
+      gr[q][a][1] = s * g[1];
+      gr[q][a][2] = s * g[2];
+    } else {
+      gr[q][a][0] = s * dlag(ax, xi) * lag(ay, eta) * lag(az, zeta);
+      gr[q][a][1] = s * lag(ax, xi) * dlag(ay, eta) * lag(az, zeta);
+      gr[q][a][2] = s * lag(ax, xi) * lag(ay, eta) * dlag(az, zeta);
+    }
   }
   __syncthreads();
   const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
@@ -118,6 +159,89 @@ __global__ void k_q2_moment_basis(double nu, double* __restrict__ cmom) {
         if (s >= 0 && s < 3) c += u[r] * w[s];
       }
       v *= c;
+    }
+    return v;
+  };
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = 1.0 / (2.0 * (1.0 + nu));
+  double v = lam * T(i, j) + mu * T(j, i);
+  if (i == j) v += mu * (T(0, 0) + T(1, 1) + T(2, 2));
+  cmom[t] = v;
+}
+
+// Monomial coefficients of the 20-node serendipity shape function at lattice
+// position (ax, ay, az): c[e0 + 3 (e1 + 3 e2)] multiplies xi^e0 eta^e1
+// zeta^e2 (each exponent <= 2); zero for face and element centres.
+__device__ void s2_coef(int ax, int ay, int az, double c[27]) {
+  for (int q = 0; q < 27; ++q) c[q] = 0.0;
+  const int cc[3] = {ax - 1, ay - 1, az - 1};
+  const int nmid = (cc[0] == 0) + (cc[1] == 0) + (cc[2] == 0);
+  if (nmid >= 2) return;
+  // 1D factors: (1 + c t) for a vertex coordinate, (1 - t^2) for the
+  // midpoint coordinate of an edge node
+  double f[3][3];
+  for (int q = 0; q < 3; ++q) {
+    if (cc[q] == 0) { f[q][0] = 1.0; f[q][1] = 0.0; f[q][2] = -1.0; }
+    else { f[q][0] = 1.0; f[q][1] = (double)cc[q]; f[q][2] = 0.0; }
+  }
+  double prod[27];
+  for (int e2 = 0; e2 < 3; ++e2)
+    for (int e1 = 0; e1 < 3; ++e1)
+      for (int e0 = 0; e0 < 3; ++e0) prod[e0 + 3 * (e1 + 3 * e2)] = f[0][e0] * f[1][e1] * f[2][e2];
+  if (nmid == 1) {
+    for (int q = 0; q < 27; ++q) c[q] = 0.25 * prod[q];
+    return;
+  }
+  // vertex: times (c0 xi + c1 eta + c2 zeta - 2) / 8; (1 + c t) t = t + c t^2
+  // keeps every exponent <= 2
+  for (int e2 = 0; e2 < 3; ++e2)
+    for (int e1 = 0; e1 < 3; ++e1)
+      for (int e0 = 0; e0 < 3; ++e0) {
+        const double v = prod[e0 + 3 * (e1 + 3 * e2)];
+        if (v == 0.0) continue;
+        c[e0 + 3 * (e1 + 3 * e2)] += -2.0 * v / 8.0;
+        const int ee[3] = {e0, e1, e2};
+        for (int q = 0; q < 3; ++q) {
+          int up[3] = {ee[0], ee[1], ee[2]};
+          up[q] += 1;
+          if (up[q] <= 2) c[up[0] + 3 * (up[1] + 3 * up[2])] += cc[q] * v / 8.0;
+        }
+      }
+}
+
+// The moment basis of the serendipity element (as k_q2_moment_basis): the
+// coefficient of xi^alpha in d_p N_a d_q N_b is a 3D convolution of the
+// derivatives' coefficient arrays.  Thread per (alpha, entry).
+__global__ void k_s2_moment_basis(double nu, double* __restrict__ cmom) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)kNM * kDD) return;
+  const int alpha = (int)(t / kDD), e = (int)(t % kDD);
+  const int R = e / kD, C = e % kD;
+  const int al[3] = {alpha % kP, (alpha / kP) % kP, alpha / (kP * kP)};
+  const int a = R / 3, i = R % 3, b = C / 3, j = C % 3;
+  double ca[27], cb[27];
+  s2_coef(a % 3, (a / 3) % 3, a / 9, ca);
+  s2_coef(b % 3, (b / 3) % 3, b / 9, cb);
+  auto deriv = [](const double* c, int p, int e0, int e1, int e2) {  // coefficient of t^e in d_p N
+    int ee[3] = {e0, e1, e2};
+    ee[p] += 1;
+    if (ee[p] > 2) return 0.0;
+    return ee[p] * c[ee[0] + 3 * (ee[1] + 3 * ee[2])];
+  };
+  auto T = [&](int p, int q) {
+    double v = 0.0;
+    for (int x0 = 0; x0 <= 1 + (p != 0); ++x0) {
+      const int y0 = al[0] - x0;
+      if (y0 < 0 || y0 > 2) continue;
+      for (int x1 = 0; x1 <= 2; ++x1) {
+        const int y1 = al[1] - x1;
+        if (y1 < 0 || y1 > 2) continue;
+        for (int x2 = 0; x2 <= 2; ++x2) {
+          const int y2 = al[2] - x2;
+          if (y2 < 0 || y2 > 2) continue;
+          v += deriv(ca, p, x0, x1, x2) * deriv(cb, q, y0, y1, y2);
+        }
+      }
     }
     return v;
   };
@@ -245,6 +369,104 @@ struct Sum<dfloat> {
   __device__ __forceinline__ void add(float a, dfloat x) { d.add(a, x); }
   __device__ __forceinline__ dfloat value() const { return d.value(); }
 };
+
+// Transfers between serendipity levels by the coarse shape functions
+// (prolongation v_h(x) = sum_a phi_a(x) v_H(x_a)) and their transpose.  A
+// fine lattice node belongs to the coarse element min(i / 4, E - 1) along
+// each axis, at local fine position f = i - 4 e in 0..4; W[a][f] (27 x 125,
+// FP32: the values at the quarter points are dyadic and exact) is coarse
+// shape function a there.  The restriction gathers, for each coarse node,
+// the fine nodes of its elements that belong to those elements, so that it
+// is exactly the transpose of the prolongation.
+template <typename T>
+__global__ void k_s2_prolong(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int ecx, int ecy, int ecz,
+                             const float* __restrict__ W, const uint8_t* __restrict__ maskf,
+                             const T* __restrict__ zc, T* __restrict__ v) {
+  const long nnf = (long)Lxf * Lyf * Lzf;
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nnf;
+       node += (long)gridDim.x * blockDim.x) {
+    const int i = node % Lxf, j = (node / Lxf) % Lyf, l = node / ((long)Lxf * Lyf);
+    const int ex = min(i / 4, ecx - 1), ey = min(j / 4, ecy - 1), ez = min(l / 4, ecz - 1);
+    const int f = (i - 4 * ex) + 5 * ((j - 4 * ey) + 5 * (l - 4 * ez));
+    Sum<T> acc[3];
+    for (int a = 0; a < 27; ++a) {
+      const float wgt = W[a * 125 + f];
+      if (wgt == 0.f) continue;
+      const long cn = (2 * ex + a % 3) + (long)Lxc * ((2 * ey + (a / 3) % 3) + (long)Lyc * (2 * ez + a / 9));
+      acc[0].add(wgt, zc[3 * cn]);
+      acc[1].add(wgt, zc[3 * cn + 1]);
+      acc[2].add(wgt, zc[3 * cn + 2]);
+    }
+    for (int c = 0; c < 3; ++c)
+      if (!maskf[3 * node + c]) v[3 * node + c] += acc[c].value();
+  }
+}
+
+// Restriction, element by element: coarse element E owns the fine nodes
+// with min(i / 4, E - 1) = e along each axis (so each fine node counts
+// once); Y_E[a] = sum over its owned fine points f of W[a][f] r_f, then each
+// coarse node adds Y over the elements that contain it (fixed order).  One
+// block per coarse element at a time, 81 outputs.
+template <typename T>
+__global__ void __launch_bounds__(96) k_s2_restrict_elem(int Lxf, int Lyf, int ecx, int ecy, long Ec,
+                                                         const float* __restrict__ W, const T* __restrict__ rf,
+                                                         T* __restrict__ Y) {
+  __shared__ T rs[125][3];
+  __shared__ float ws[27 * 125];
+  for (int t = threadIdx.x; t < 27 * 125; t += blockDim.x) ws[t] = W[t];
+  const int ecz = (int)(Ec / ((long)ecx * ecy));
+  for (long e = blockIdx.x; e < Ec; e += gridDim.x) {
+    const int ex = e % ecx, ey = (e / ecx) % ecy, ez = e / ((long)ecx * ecy);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
+      const int fx = t % 5, fy = (t / 5) % 5, fz = t / 25;
+      const int i = 4 * ex + fx, j = 4 * ey + fy, l = 4 * ez + fz;
+      const bool own = min(i / 4, ecx - 1) == ex && min(j / 4, ecy - 1) == ey && min(l / 4, ecz - 1) == ez;
+      const long fn = i + (long)Lxf * (j + (long)Lyf * l);
+      for (int c = 0; c < 3; ++c) rs[t][c] = own ? rf[3 * fn + c] : T(0);
+    }
+    __syncthreads();
+    if (threadIdx.x < kD) {
+      const int a = threadIdx.x / 3, c = threadIdx.x % 3;
+      Sum<T> acc;
+      for (int f = 0; f < 125; ++f) {
+        const float wgt = ws[a * 125 + f];
+        if (wgt != 0.f) acc.add(wgt, rs[f][c]);
+      }
+      Y[e * kD + threadIdx.x] = acc.value();
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_s2_restrict_gather(int Lxc, int Lyc, int Lzc, int ecx, int ecy, int ecz,
+                                     const T* __restrict__ Y, const uint8_t* __restrict__ maskc,
+                                     T* __restrict__ bc, const op_t<T>* __restrict__ dinvc, T omega,
+                                     T* __restrict__ vc) {
+  const long nnc = (long)Lxc * Lyc * Lzc;
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nnc;
+       node += (long)gridDim.x * blockDim.x) {
+    const int I = node % Lxc, J = (node / Lxc) % Lyc, K = node / ((long)Lxc * Lyc);
+    const int x0 = (I & 1) ? I >> 1 : max((I >> 1) - 1, 0), x1 = min(I >> 1, ecx - 1);
+    const int y0 = (J & 1) ? J >> 1 : max((J >> 1) - 1, 0), y1 = min(J >> 1, ecy - 1);
+    const int z0 = (K & 1) ? K >> 1 : max((K >> 1) - 1, 0), z1 = min(K >> 1, ecz - 1);
+    T acc[3] = {T(0), T(0), T(0)};
+    for (int ez = z0; ez <= z1; ++ez)
+      for (int ey = y0; ey <= y1; ++ey)
+        for (int ex = x0; ex <= x1; ++ex) {
+          const long e = ex + (long)ecx * (ey + (long)ecy * ez);
+          const int a = (I - 2 * ex) + 3 * ((J - 2 * ey) + 3 * (K - 2 * ez));
+          for (int c = 0; c < 3; ++c) acc[c] += Y[e * kD + 3 * a + c];
+        }
+    for (int c = 0; c < 3; ++c) {
+      const long d = 3 * node + c;
+      const T bv = maskc[d] ? T(0) : acc[c];
+      bc[d] = bv;
+      if (vc != nullptr) vc[d] = omega * dinvc[d] * bv;
+    }
+  }
+}
+
 
 // Y_e = K^(e) u_e for every element; u_e gathered with the fixed DOFs set to
 // zero.  One block of 96 threads per element at a time (persistent), thread
@@ -545,12 +767,44 @@ inline int grid_for2(long work, int cap = 65536) {
 
 // ---- launchers -------------------------------------------------------------
 
-void launch_q2_subcell_table(int n, double nu, double h, double* tab, cudaStream_t st) {
-  k_q2_subcell_table<<<n * n * n, 256, 0, st>>>(n, nu, h, tab);
+void launch_q2_subcell_table(int n, double nu, double h, int family, double* tab, cudaStream_t st) {
+  k_q2_subcell_table<<<n * n * n, 256, 0, st>>>(n, nu, h, family, tab);
 }
 
-void launch_q2_moment_basis(double nu, double* cmom, cudaStream_t st) {
-  k_q2_moment_basis<<<(int)(((long)kNM * kDD + 255) / 256), 256, 0, st>>>(nu, cmom);
+void launch_q2_moment_basis(double nu, int family, double* cmom, cudaStream_t st) {
+  if (family == 1)
+    k_s2_moment_basis<<<(int)(((long)kNM * kDD + 255) / 256), 256, 0, st>>>(nu, cmom);
+  else
+    k_q2_moment_basis<<<(int)(((long)kNM * kDD + 255) / 256), 256, 0, st>>>(nu, cmom);
+}
+
+void launch_s2_restrict(int vt, const Level& F, const Level& C, const float* W, const void* dinvc, double omega,
+                        void* vc, cudaStream_t st) {
+  const long Ec = (long)C.ex * C.ey * C.ez;
+  long ge = (long)F.sms * 8;
+  if (ge > Ec) ge = Ec;
+  const int g = grid_for2(C.nn);
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    k_s2_restrict_elem<T><<<(int)ge, 96, 0, st>>>(F.Lx, F.Ly, C.ex, C.ey, Ec, W, (const T*)F.r, (T*)C.Y);
+    k_s2_restrict_gather<T><<<g, 256, 0, st>>>(C.Lx, C.Ly, C.Lz, C.ex, C.ey, C.ez, (const T*)C.Y, C.mask,
+                                               (T*)C.b, (const op_t<T>*)dinvc, (T)omega, (T*)vc);
+  };
+  if (vt == kVtF64) run(double());
+  else if (vt == kVtF32) run(float());
+  else run(dfloat(0.f, 0.f));
+}
+
+void launch_s2_prolong(int vt, const Level& F, const Level& C, const float* W, cudaStream_t st) {
+  const int g = grid_for2(F.nn);
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    k_s2_prolong<T><<<g, 256, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.ex, C.ey, C.ez, W, F.mask,
+                                       (const T*)C.z, (T*)F.v);
+  };
+  if (vt == kVtF64) run(double());
+  else if (vt == kVtF32) run(float());
+  else run(dfloat(0.f, 0.f));
 }
 
 void launch_q2_elem(const Level& L, int n, const double* w, int Dx, int Dy, const double* tab,

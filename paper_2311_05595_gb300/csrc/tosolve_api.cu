@@ -95,7 +95,9 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   tosolve_desc d = *dp;
   if (d.nx < 1 || d.ny < 1 || d.nz < 1) { *why = "nx, ny, nz must be >= 1"; return TOSOLVE_EINVAL; }
   if ((long)d.nx * d.ny * d.nz > (1L << 28)) { *why = "mesh too large"; return TOSOLVE_EINVAL; }
-  if (d.degree != 1 && d.degree != 2) { *why = "Lagrange degree must be 1 or 2"; return TOSOLVE_EINVAL; }
+  if (d.degree != 1 && d.degree != 2) { *why = "degree must be 1 or 2"; return TOSOLVE_EINVAL; }
+  if (d.family != 0 && d.family != 1) { *why = "family must be 0 (Lagrange) or 1 (serendipity)"; return TOSOLVE_EINVAL; }
+  if (d.family == 1 && d.degree != 2) { *why = "the serendipity element is built for degree 2"; return TOSOLVE_EINVAL; }
   if (d.n_mr < 1 || d.n_mr > 8) { *why = "n_mr must be in 1..8"; return TOSOLVE_EINVAL; }
   if (d.d_mr != 0 && (d.d_mr < 1 || d.d_mr > d.n_mr)) { *why = "d_mr must be in 1..n_mr"; return TOSOLVE_EINVAL; }
   if (d.d_mr != 0 && d.d_mr != d.n_mr && !(d.rmin > 0.0)) {
@@ -231,7 +233,7 @@ void free_all(tosolve_s* h) {
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
-  F(h->base0); F(h->ecls); F(h->efix); F(h->xfix);
+  F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->s2w);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv); F(h->Pq);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
@@ -374,7 +376,10 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   tosolve_s* h = new (std::nothrow) tosolve_s();
   if (h == nullptr) { g_err = "host allocation failed"; return TOSOLVE_ENOMEM; }
   h->d = *desc;
-  if (h->d.omega == 0.0) h->d.omega = 0.5;
+  // damped Jacobi: 0.5 (Sec. 7 intro); the serendipity element has
+  // lambda_max(D^-1 A) near 5.3 (Lagrange degree 2: 3.1), beyond 2 / 0.5, so
+  // its default is 0.3
+  if (h->d.omega == 0.0) h->d.omega = h->d.family == 1 ? 0.3 : 0.5;
   if (h->d.cycle_gamma == 0) h->d.cycle_gamma = 1;
   if (h->d.max_rhs == 0) h->d.max_rhs = 1;
   h->d.d_mr = P.dm;
@@ -436,6 +441,15 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     for (long nd = 0; nd < v.nn; ++nd)
       if (slv[nd]) mask[3 * nd] = mask[3 * nd + 1] = mask[3 * nd + 2] = 1;
   }
+  // serendipity: no node at face and element centres, held at 0 on every level
+  auto hold_absent = [&](const Plan::Lv& v, std::vector<uint8_t>& m) {
+    if (h->d.family != 1) return;
+    for (long nd = 0; nd < v.nn; ++nd) {
+      const long i = nd % v.Lx, j = (nd / v.Lx) % v.Ly, l = nd / ((long)v.Lx * v.Ly);
+      if ((i & 1) + (j & 1) + (l & 1) >= 2) m[3 * nd] = m[3 * nd + 1] = m[3 * nd + 2] = 1;
+    }
+  };
+  hold_absent(P.lv[0], mask);
   h->free_dofs = 0;
   for (uint8_t m : mask) h->free_dofs += m == 0;
   h->free_base = h->free_dofs;
@@ -500,6 +514,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
             const long fn = 2 * I + (long)v.Lx * (2 * J + (long)v.Ly * 2 * K);
             for (int q = 0; q < 3; ++q) cm[3 * cn + q] = mask[3 * fn + q];
           }
+      hold_absent(c, cm);
       mask.swap(cm);
     }
   }
@@ -507,8 +522,31 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   if (h->d.degree == 2) {
     CKC(dalloc(h, &h->tab64, (size_t)P.m * kDD2));
     CKC(dalloc(h, &h->cmom64, (size_t)kNM2 * kDD2));
-    launch_q2_subcell_table(P.n, h->d.nu, 1.0, h->tab64, st);
-    launch_q2_moment_basis(h->d.nu, h->cmom64, st);
+    launch_q2_subcell_table(P.n, h->d.nu, 1.0, h->d.family, h->tab64, st);
+    launch_q2_moment_basis(h->d.nu, h->d.family, h->cmom64, st);
+    if (h->d.family == 1) {  // serendipity transfer table: coarse shape values at the quarter points
+      std::vector<float> W(27 * 125, 0.f);
+      for (int a = 0; a < 27; ++a) {
+        const int c[3] = {a % 3 - 1, (a / 3) % 3 - 1, a / 9 - 1};
+        const int nmid = (c[0] == 0) + (c[1] == 0) + (c[2] == 0);
+        if (nmid >= 2) continue;
+        for (int f = 0; f < 125; ++f) {
+          const double x[3] = {-1.0 + 0.5 * (f % 5), -1.0 + 0.5 * ((f / 5) % 5), -1.0 + 0.5 * (f / 25)};
+          double v;
+          if (nmid == 0) {
+            v = (1.0 + x[0] * c[0]) * (1.0 + x[1] * c[1]) * (1.0 + x[2] * c[2]) *
+                (x[0] * c[0] + x[1] * c[1] + x[2] * c[2] - 2.0) / 8.0;
+          } else {
+            v = 0.25;
+            for (int q = 0; q < 3; ++q) v *= c[q] == 0 ? 1.0 - x[q] * x[q] : 1.0 + x[q] * c[q];
+          }
+          W[a * 125 + f] = (float)v;
+        }
+      }
+      CKC(dalloc(h, &h->s2w, W.size()));
+      CKC(cudaMemcpyAsync(h->s2w, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+      for (int l = 1; l < P.L; ++l) h->lv[l].s2w = h->s2w;
+    }
     const Plan::Lv& v0 = P.lv[0];
     CKC(dalloc(h, &h->Yq, (size_t)v0.ex * v0.ey * v0.ez * kD2));
     for (int l = 0; l < P.L; ++l) h->lv[l].Y = h->Yq;
@@ -665,6 +703,7 @@ tosolve_status tosolve_create_mixed(const tosolve_desc* desc, const uint8_t* mas
                                     const uint8_t* elem_q1_host, void* cuda_stream, tosolve_t* out) {
   if (desc == nullptr || elem_q1_host == nullptr) { g_err = "NULL argument"; return TOSOLVE_EINVAL; }
   if (desc->degree != 2) { g_err = "a mixed mesh lives on the degree-2 lattice (degree = 2)"; return TOSOLVE_EINVAL; }
+  if (desc->family != 0) { g_err = "a mixed mesh couples Lagrange elements (family = 0)"; return TOSOLVE_EINVAL; }
   return create_impl(desc, mask_host, elem_q1_host, cuda_stream, out);
 }
 

@@ -18,7 +18,8 @@ def desc_for(T, p, precision, levels=None, max_rhs=None):
     return T.make_desc(p.nx, p.ny, p.nz, degree=p.degree, n_mr=p.n_mr, d_mr=getattr(p, "d_mr", None),
                        E0=p.E0, Emin=p.Emin, nu=p.nu,
                        penal=p.penal, rmin=p.rmin, mg_levels=levels or p.mg_levels,
-                       precision=precision, max_rhs=max_rhs or p.nrhs)
+                       precision=precision, max_rhs=max_rhs or p.nrhs,
+                       family=1 if getattr(p, "family", "lagrange") == "serendipity" else 0)
 
 
 class Run:
