@@ -98,8 +98,17 @@ typedef struct {
                           /*   20-node serendipity element (degree 2 only), */
                           /*   on the degree-2 lattice without the face and */
                           /*   element-centre nodes, which the library holds */
-                          /*   at 0 with the supports; its coarse levels are */
-                          /*   degree-2 Lagrange                            */
+                          /*   at 0 with the supports; coarse levels are    */
+                          /*   serendipity meshes with shape-function       */
+                          /*   transfers (Sec. 2.3)                         */
+  int prolongation;       /* degree-2 transfers: 0 the coarse shape         */
+                          /*   functions (Sec. 2.3 for serendipity; nested  */
+                          /*   spaces, so the re-discretised coarse         */
+                          /*   operators are the Galerkin products), 1      */
+                          /*   linear interpolation on the node lattices    */
+                          /*   (the paper's choice for Lagrange elements;   */
+                          /*   not for serendipity); degree 1: the two are  */
+                          /*   the same trilinear interpolation             */
 } tosolve_desc;
 
 typedef struct {

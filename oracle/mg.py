@@ -18,8 +18,16 @@ Readings taken here (the paper does not say):
   * supports: a coarse DOF is fixed iff the coincident fine DOF is fixed;
     fixed rows/columns of every level operator are replaced by identity and
     P is masked on both sides, P = M_f P_lin M_c;
-  * the prolongation for every degree is trilinear interpolation on the node
-    lattices (the paper's choice for Lagrange elements).
+  * the prolongation is trilinear interpolation on the node lattices (the
+    paper's choice for Lagrange elements) for degree 1, where it is also the
+    shape-function interpolation, and on request for degree 2; by default a
+    degree-2 level is interpolated with the coarse shape functions, the
+    construction the paper proposes for serendipity elements: the quadratic
+    spaces are nested, so the re-discretised coarse operator is then the
+    Galerkin product P^T A P (tested);
+  * serendipity levels hold their face and element-centre nodes at 0 like
+    supports, and use omega = 0.3 (damped Jacobi with 0.5 diverges on this
+    element: lambda_max(D^-1 A) is about 5.3).
 """
 from __future__ import annotations
 
@@ -50,6 +58,58 @@ def prolongation(lat_fine) -> sp.csr_matrix:
     return sp.kron(Pn, sp.identity(3), format="csr")
 
 
+def _quad_1d(nf: int) -> sp.csr_matrix:
+    """Interpolation by the coarse quadratic Lagrange basis from a degree-2
+    lattice of (nf-1)/2+1 nodes to the degree-2 lattice of twice as many
+    elements (nf nodes): fine node i lies in coarse element min(i // 4, E - 1)
+    at xi = -1 + (i - 4 e) / 2."""
+    E = (nf - 1) // 4
+    nc = 2 * E + 1
+    rows, cols, vals = [], [], []
+    for i in range(nf):
+        e = min(i // 4, E - 1)
+        xi = -1.0 + 0.5 * (i - 4 * e)
+        N = (0.5 * xi * (xi - 1.0), 1.0 - xi * xi, 0.5 * xi * (xi + 1.0))
+        for j in range(3):
+            if N[j] != 0.0:
+                rows.append(i); cols.append(2 * e + j); vals.append(N[j])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(nf, nc))
+
+
+def prolongation_shape(lat_fine, family: str = "lagrange") -> sp.csr_matrix:
+    """Interpolation by the coarse degree-2 shape functions (Lagrange: the
+    tensor product of _quad_1d; serendipity: the 20-node shape functions of
+    oracle/fem.py in the coarse element owning each fine node)."""
+    Lx, Ly, Lz = lat_fine
+    if family == "lagrange":
+        Pn = sp.kron(sp.kron(_quad_1d(Lz), _quad_1d(Ly)), _quad_1d(Lx))
+        return sp.kron(Pn, sp.identity(3), format="csr")
+    Ex, Ey, Ez = (Lx - 1) // 4, (Ly - 1) // 4, (Lz - 1) // 4
+    Lxc, Lyc = 2 * Ex + 1, 2 * Ey + 1
+    nc = Lxc * Lyc * (2 * Ez + 1)
+    rows, cols, vals = [], [], []
+    for node in range(Lx * Ly * Lz):
+        i, j, l = node % Lx, (node // Lx) % Ly, node // (Lx * Ly)
+        ex, ey, ez = min(i // 4, Ex - 1), min(j // 4, Ey - 1), min(l // 4, Ez - 1)
+        N, _ = fem.serendipity2_shape(-1.0 + 0.5 * (i - 4 * ex), -1.0 + 0.5 * (j - 4 * ey),
+                                      -1.0 + 0.5 * (l - 4 * ez))
+        for a in range(27):
+            if N[a] != 0.0:
+                cn = (2 * ex + a % 3) + Lxc * ((2 * ey + (a // 3) % 3) + Lyc * (2 * ez + a // 9))
+                rows.append(node); cols.append(cn); vals.append(N[a])
+    Pn = sp.csr_matrix((vals, (rows, cols)), shape=(Lx * Ly * Lz, nc))
+    return sp.kron(Pn, sp.identity(3), format="csr")
+
+
+def serendipity_absent(lat) -> np.ndarray:
+    """(3 nnodes,) bool: DOFs of degree-2 lattice nodes with two or three odd
+    coordinates (no serendipity node there)."""
+    Lx, Ly, Lz = lat
+    n = np.arange(Lx * Ly * Lz)
+    i, j, l = n % Lx, (n // Lx) % Ly, n // (Lx * Ly)
+    return np.repeat((i % 2) + (j % 2) + (l % 2) >= 2, 3)
+
+
 def coarse_mask(mask_f: np.ndarray, lat_fine) -> np.ndarray:
     """Coarse DOF fixed iff the coincident fine DOF is fixed."""
     Lx, Ly, Lz = lat_fine
@@ -65,8 +125,14 @@ class Hierarchy:
     """Level operators A_l (supports -> identity), Jacobi diagonals, P_l and
     the dense Cholesky factor of the coarsest operator."""
 
-    def __init__(self, prob, rho: np.ndarray, levels: int):
+    def __init__(self, prob, rho: np.ndarray, levels: int, transfer: str | None = None):
         k, n = prob.degree, prob.n_mr
+        family = getattr(prob, "family", "lagrange")
+        if transfer is None:
+            transfer = "shape" if k == 2 else "linear"
+        if family == "serendipity" and transfer != "shape":
+            raise ValueError("serendipity levels take shape-function transfers")
+        self.omega = 0.3 if family == "serendipity" else 0.5
         nx, ny, nz = prob.nx, prob.ny, prob.nz
         w_cells = simp_weights(rho, prob.E0, prob.Emin, prob.penal)
         self.levels = []
@@ -81,7 +147,7 @@ class Hierarchy:
             L.lat = (k * L.nx + 1, k * L.ny + 1, k * L.nz + 1)
             L.ndof = 3 * L.lat[0] * L.lat[1] * L.lat[2]
             L.mask = mask
-            Ktab = fem.subcell_stiffness(k, L.nsub, prob.nu, h=float(s))
+            Ktab = fem.subcell_stiffness(k, L.nsub, prob.nu, h=float(s), family=family)
             m, d, _ = Ktab.shape
             w_e = w_cells[mesh.subcell_density_index(L.nx, L.ny, L.nz, L.nsub)]
             Ke = (w_e @ Ktab.reshape(m, d * d)).reshape(-1, d, d)
@@ -96,9 +162,12 @@ class Hierarchy:
             self.levels.append(L)
             if l + 1 < levels:
                 mask = coarse_mask(mask, L.lat)
+                if family == "serendipity":
+                    lat_c = (k * (nx // (2 * s)) + 1, k * (ny // (2 * s)) + 1, k * (nz // (2 * s)) + 1)
+                    mask = (mask.astype(bool) | serendipity_absent(lat_c)).astype(np.uint8)
         for l in range(levels - 1):
             F, C = self.levels[l], self.levels[l + 1]
-            P = prolongation(F.lat)
+            P = prolongation_shape(F.lat, family) if transfer == "shape" else prolongation(F.lat)
             Mf = sp.diags((F.mask == 0).astype(np.float64))
             Mc = sp.diags((C.mask == 0).astype(np.float64))
             F.P = (Mf @ P @ Mc).tocsr()
@@ -106,10 +175,11 @@ class Hierarchy:
         last.chol = sla.cho_factor(last.A.toarray(), lower=True)
 
 
-def vcycle(h: Hierarchy, b: np.ndarray, l: int = 0, omega: float = 0.5, eta1: int = 1,
+def vcycle(h: Hierarchy, b: np.ndarray, l: int = 0, omega: float | None = None, eta1: int = 1,
            eta2: int = 1, gamma: int = 1) -> np.ndarray:
     """Approximate A_l^{-1} b by one multigrid cycle from a zero initial guess
-    (Algorithm 1 applied recursively)."""
+    (Algorithm 1 applied recursively).  omega: the hierarchy's default."""
+    omega = h.omega if omega is None else omega
     L = h.levels[l]
     if l == len(h.levels) - 1:
         return sla.cho_solve(L.chol, b)

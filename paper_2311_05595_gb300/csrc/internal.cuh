@@ -90,7 +90,7 @@ struct Level {
   int sms = 1;      // SMs of the device (grid of the tile kernels)
   int* err = nullptr;  // set when an operator tile copy times out
   int k = 1;        // Lagrange degree of the level's elements
-  const float* s2w = nullptr;  // serendipity levels: the transfer table W (else null)
+  const float* ptab = nullptr;  // shape-function transfers into this level: the table W (else null)
   // degree 2: the operator as element matrices (81 x 81 each, full)
   double* K64 = nullptr;
   float* K32 = nullptr;
@@ -234,9 +234,9 @@ constexpr int kDD2 = 81 * 81;
 constexpr int kNM2 = 125;     // moments of a degree-2 element matrix
 void launch_q2_subcell_table(int n, double nu, double h, int family, double* tab, cudaStream_t st);
 void launch_q2_moment_basis(double nu, int family, double* cmom, cudaStream_t st);
-// Serendipity levels (family 1): transfers by the coarse shape functions,
-// W = the 27 x 125 table of coarse shape values at the fine lattice points
-// of a coarse element (device, FP32).
+// Degree-2 levels with shape-function transfers (always for the serendipity
+// element): W = the 27 x 125 table of coarse shape values at the fine
+// lattice points of a coarse element (device, FP32).
 void launch_s2_restrict(int vt, const Level& F, const Level& C, const float* W, const void* dinvc, double omega,
                         void* vc, cudaStream_t st);
 void launch_s2_prolong(int vt, const Level& F, const Level& C, const float* W, cudaStream_t st);
@@ -352,7 +352,7 @@ struct tosolve_s {
   uint8_t* slv0 = nullptr;     // per lattice node: 1 = slaved to its vertices
   uint8_t* fix0 = nullptr;     // per DOF: the supports alone (level 0 mask adds slaved)
   // fixing variables (Sec. 6.1)
-  float* s2w = nullptr;         // serendipity transfer table (27 x 125)
+  float* ptab = nullptr;         // shape-function transfer table (27 x 125)
   uint8_t* base0 = nullptr;    // level-0 mask before suppression (supports, slaved)
   int8_t* ecls = nullptr;      // per element: 1 void, 2 solid, 0 neither
   int8_t* efix = nullptr;      // per element: the class if fixed, else 0

@@ -727,16 +727,16 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
   else if (!use_tc)
     TILE_ORD(V, (k_vc_pre<T, kOrd><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(
                     V, (const T*)F.b, (const T*)F.v, (T*)F.r)));
-  if (C.s2w != nullptr)  // serendipity: the coarse shape functions and their transpose
-    launch_s2_restrict(vt_code<T>(), F, C, C.s2w, c_coarsest ? nullptr : dinv_of<T>(C), (double)omega,
+  if (C.ptab != nullptr)  // the coarse shape functions and their transpose
+    launch_s2_restrict(vt_code<T>(), F, C, C.ptab, c_coarsest ? nullptr : dinv_of<T>(C), (double)omega,
                        c_coarsest ? nullptr : C.v, st);
   else
     k_vc_restrict<T><<<grid_nodes(C.nn), kRowThreads, 0, st>>>(
         F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, C.mask, (const T*)F.r, (T*)C.b,
         c_coarsest ? nullptr : dinv_of<T>(C), omega, c_coarsest ? nullptr : (T*)C.v);
   vcycle_rec<T>(lv, l + 1, L, omega, Ainv, tc, st);
-  if (C.s2w != nullptr)
-    launch_s2_prolong(vt_code<T>(), F, C, C.s2w, st);
+  if (C.ptab != nullptr)
+    launch_s2_prolong(vt_code<T>(), F, C, C.ptab, st);
   else
     k_vc_prolong<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, F.mask,
                                                               (const T*)C.z, (T*)F.v);

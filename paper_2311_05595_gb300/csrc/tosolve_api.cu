@@ -98,6 +98,11 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (d.degree != 1 && d.degree != 2) { *why = "degree must be 1 or 2"; return TOSOLVE_EINVAL; }
   if (d.family != 0 && d.family != 1) { *why = "family must be 0 (Lagrange) or 1 (serendipity)"; return TOSOLVE_EINVAL; }
   if (d.family == 1 && d.degree != 2) { *why = "the serendipity element is built for degree 2"; return TOSOLVE_EINVAL; }
+  if (d.prolongation != 0 && d.prolongation != 1) { *why = "prolongation must be 0 or 1"; return TOSOLVE_EINVAL; }
+  if (d.prolongation == 1 && d.family == 1) {
+    *why = "the serendipity element takes shape-function transfers (prolongation = 0)";
+    return TOSOLVE_EINVAL;
+  }
   if (d.n_mr < 1 || d.n_mr > 8) { *why = "n_mr must be in 1..8"; return TOSOLVE_EINVAL; }
   if (d.d_mr != 0 && (d.d_mr < 1 || d.d_mr > d.n_mr)) { *why = "d_mr must be in 1..n_mr"; return TOSOLVE_EINVAL; }
   if (d.d_mr != 0 && d.d_mr != d.n_mr && !(d.rmin > 0.0)) {
@@ -233,7 +238,7 @@ void free_all(tosolve_s* h) {
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
-  F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->s2w);
+  F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv); F(h->Pq);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
@@ -524,16 +529,25 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     CKC(dalloc(h, &h->cmom64, (size_t)kNM2 * kDD2));
     launch_q2_subcell_table(P.n, h->d.nu, 1.0, h->d.family, h->tab64, st);
     launch_q2_moment_basis(h->d.nu, h->d.family, h->cmom64, st);
-    if (h->d.family == 1) {  // serendipity transfer table: coarse shape values at the quarter points
+    if (h->d.family == 1 || h->d.prolongation == 0) {
+      // shape-function transfers: the 27 coarse shape functions at the 125
+      // quarter points of a coarse element (always for the serendipity
+      // element; for degree-2 Lagrange unless linear lattice interpolation is
+      // asked for)
       std::vector<float> W(27 * 125, 0.f);
+      auto lag1 = [](int j, double x) {  // quadratic Lagrange basis on -1, 0, 1
+        return j == 0 ? 0.5 * x * (x - 1.0) : (j == 1 ? 1.0 - x * x : 0.5 * x * (x + 1.0));
+      };
       for (int a = 0; a < 27; ++a) {
         const int c[3] = {a % 3 - 1, (a / 3) % 3 - 1, a / 9 - 1};
         const int nmid = (c[0] == 0) + (c[1] == 0) + (c[2] == 0);
-        if (nmid >= 2) continue;
+        if (h->d.family == 1 && nmid >= 2) continue;
         for (int f = 0; f < 125; ++f) {
           const double x[3] = {-1.0 + 0.5 * (f % 5), -1.0 + 0.5 * ((f / 5) % 5), -1.0 + 0.5 * (f / 25)};
           double v;
-          if (nmid == 0) {
+          if (h->d.family == 0) {
+            v = lag1(a % 3, x[0]) * lag1((a / 3) % 3, x[1]) * lag1(a / 9, x[2]);
+          } else if (nmid == 0) {
             v = (1.0 + x[0] * c[0]) * (1.0 + x[1] * c[1]) * (1.0 + x[2] * c[2]) *
                 (x[0] * c[0] + x[1] * c[1] + x[2] * c[2] - 2.0) / 8.0;
           } else {
@@ -543,9 +557,9 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
           W[a * 125 + f] = (float)v;
         }
       }
-      CKC(dalloc(h, &h->s2w, W.size()));
-      CKC(cudaMemcpyAsync(h->s2w, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-      for (int l = 1; l < P.L; ++l) h->lv[l].s2w = h->s2w;
+      CKC(dalloc(h, &h->ptab, W.size()));
+      CKC(cudaMemcpyAsync(h->ptab, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+      for (int l = 1; l < P.L; ++l) h->lv[l].ptab = h->ptab;
     }
     const Plan::Lv& v0 = P.lv[0];
     CKC(dalloc(h, &h->Yq, (size_t)v0.ex * v0.ey * v0.ez * kD2));

@@ -55,12 +55,24 @@ def test_q2_operators_match_oracle(n, rmin):
     R.close()
 
 
-def test_q2_one_cycle_matches_algorithm_1():
+@pytest.mark.parametrize("prolongation,transfer", [(0, "shape"), (1, "linear")])
+def test_q2_one_cycle_matches_algorithm_1(prolongation, transfer):
+    """One V-cycle against the oracle's Algorithm 1, with the coarse shape
+    functions as transfers (the default) and with linear interpolation on
+    the node lattices (prolongation = 1)."""
+    from paper_2311_05595_gb300 import tosolve as T
+
     p = workloads.cantilever(8, 4, 4, degree=2, n_mr=2, rmin=1.0, seed=4, mg_levels=3, lo=0.3)
     m = fe.Model(p)
-    h = mg.Hierarchy(p, m.densities(p.x), 3)
+    h = mg.Hierarchy(p, m.densities(p.x), 3, transfer=transfer)
     b = np.where(p.mask == 0, np.random.default_rng(2).normal(size=p.ndof), 0.0)
     R = Run(p, FP64)
+    if prolongation:
+        R.close()
+        R.solver = T.Solver(T.make_desc(p.nx, p.ny, p.nz, degree=2, n_mr=p.n_mr, rmin=p.rmin, nu=p.nu,
+                                        penal=p.penal, Emin=p.Emin, mg_levels=3, prolongation=1),
+                            p.mask, R.stream)
+        R.h = R.solver.h
     R.set_densities()
     assert rel(R.precondition(b), mg.vcycle(h, b)) <= 1e-9
     R.close()

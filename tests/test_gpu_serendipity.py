@@ -79,6 +79,21 @@ def test_coarse_level_is_the_serendipity_mesh_of_the_coarse_elements():
     R.close()
 
 
+def test_one_cycle_matches_algorithm_1():
+    """One V-cycle (omega = 0.3, serendipity levels, shape-function
+    transfers) against the oracle's Algorithm 1 on the same hierarchy."""
+    from oracle import mg
+
+    q = _s2(shape=(8, 4, 4), n=2, levels=3, rmin=1.0)
+    m = fe.Model(q)
+    h = mg.Hierarchy(q, m.densities(q.x), 3)
+    b = np.where(q.mask == 0, np.random.default_rng(4).normal(size=q.ndof), 0.0)
+    R = Run(q, FP64)
+    R.set_densities()
+    assert rel(R.precondition(b), mg.vcycle(h, b)) <= 1e-9
+    R.close()
+
+
 @pytest.mark.parametrize("precision", [FP64, FP32, FP32X2])
 def test_solve_matches_oracle(precision):
     q = _s2(shape=(8, 4, 4), n=2, levels=3)

@@ -87,3 +87,49 @@ def test_run_with_mg_matches_direct_run():
     assert np.linalg.norm(a["u"] - b["u"]) <= 1e-9 * np.linalg.norm(b["u"])
     assert abs(a["c"][0] - b["c"][0]) <= 1e-11 * b["c"][0]
     assert np.linalg.norm(a["g_x"] - b["g_x"]) <= 1e-9 * np.linalg.norm(b["g_x"])
+
+
+@pytest.mark.parametrize("family,n", [("lagrange", 1), ("lagrange", 2), ("serendipity", 1), ("serendipity", 2)])
+def test_degree2_shape_transfers_give_galerkin_coarse_operators(family, n):
+    """Degree 2 with the coarse shape functions as P: the quadratic spaces
+    are nested (the serendipity monomials are closed under per-axis affine
+    maps), so the re-discretised coarse operator is P^T A P on the free
+    DOFs, for both families."""
+    p = workloads.cantilever(8, 4, 4, degree=2, n_mr=n, seed=4)
+    if family == "serendipity":
+        p = workloads.with_serendipity(p)
+    m = fe.Model(p)
+    h = mg.Hierarchy(p, m.densities(p.x), 3)
+    for l in range(2):
+        F, C = h.levels[l], h.levels[l + 1]
+        G = (F.P.T @ F.A @ F.P).toarray()
+        freec = C.mask == 0
+        A = C.A.toarray()
+        Gf = G[np.ix_(freec, freec)]
+        Af = A[np.ix_(freec, freec)]
+        assert np.abs(Gf - Af).max() <= 1e-12 * np.abs(Af).max()
+    # the paper's linear lattice interpolation is not Galerkin for degree 2
+    if family == "lagrange":
+        hl = mg.Hierarchy(p, m.densities(p.x), 2, transfer="linear")
+        F, C = hl.levels[0], hl.levels[1]
+        freec = C.mask == 0
+        G = (F.P.T @ F.A @ F.P).toarray()[np.ix_(freec, freec)]
+        assert np.abs(G - C.A.toarray()[np.ix_(freec, freec)]).max() > 1e-3 * np.abs(G).max()
+
+
+def test_degree2_shape_prolongation_reproduces_quadratics():
+    lat_f = (17, 9, 9)  # 8x4x4 degree-2 lattice; coarse 4x2x2
+    Xc = mesh.node_coords(4, 2, 2, 2) * 2.0
+    Xf = mesh.node_coords(8, 4, 4, 2)
+    q = lambda X: 1 + X[:, 0] - 2 * X[:, 1] + X[:, 0] ** 2 * X[:, 1] ** 2 * X[:, 2] ** 2 - X[:, 1] * X[:, 2]
+    P = mg.prolongation_shape(lat_f, "lagrange")
+    vc = np.zeros(3 * len(Xc)); vc[2::3] = q(Xc)
+    np.testing.assert_allclose((P @ vc)[2::3], q(Xf), atol=1e-12)
+    # serendipity: a field in its space (x^2 y z, not x^2 y^2), at the nodes it has
+    s = lambda X: 1 + X[:, 0] * X[:, 1] - X[:, 2] ** 2 + X[:, 0] ** 2 * X[:, 1] * X[:, 2]
+    Ps = mg.prolongation_shape(lat_f, "serendipity")
+    vc = np.zeros(3 * len(Xc)); vc[0::3] = s(Xc)
+    vc[mg.serendipity_absent((9, 5, 5))] = 0.0
+    vf = (Ps @ vc)[0::3]
+    present = ~mg.serendipity_absent(lat_f)[0::3]
+    np.testing.assert_allclose(vf[present], s(Xf)[present], atol=1e-12)
