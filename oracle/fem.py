@@ -124,6 +124,61 @@ def serendipity2_present() -> np.ndarray:
     return out
 
 
+def serendipity3_shape(xi: float, eta: float, zeta: float, h: float = 1.0):
+    """The 32-node cubic serendipity shape functions on the 64-node lattice
+    order of the cubic Lagrange element (lattice positions -1, -1/3, 1/3, 1
+    per axis; index ix + 4 (iy + 4 iz)).
+
+    A vertex (all coordinates +-1) has
+        N = (1 + xi xi_a)(1 + eta eta_a)(1 + zeta zeta_a)(9 (xi^2 + eta^2 + zeta^2) - 19) / 64,
+    an edge node with xi_a = +-1/3 (the others +-1)
+        N = 9 (1 - xi^2)(1 + 9 xi xi_a)(1 + eta eta_a)(1 + zeta zeta_a) / 64
+    (and the same with the coordinates exchanged); positions with two or
+    three interior coordinates carry no node (N = 0).  Returns N (64,) and the
+    physical gradient (64, 3) for a cube of edge h."""
+    x = np.array([xi, eta, zeta], dtype=np.float64)
+    pos = (-1.0, -1.0 / 3.0, 1.0 / 3.0, 1.0)
+    N = np.zeros(64)
+    dN = np.zeros((64, 3))
+    for iz in range(4):
+        for iy in range(4):
+            for ix in range(4):
+                a = ix + 4 * (iy + 4 * iz)
+                c = np.array([pos[ix], pos[iy], pos[iz]])
+                inner = [q for q in range(3) if abs(c[q]) < 1.0]
+                if len(inner) == 0:
+                    f = 1.0 + x * c
+                    s = 9.0 * float(x @ x) - 19.0
+                    N[a] = f[0] * f[1] * f[2] * s / 64.0
+                    for q in range(3):
+                        o = np.prod([f[r] for r in range(3) if r != q])
+                        dN[a, q] = (c[q] * o * s + f[0] * f[1] * f[2] * 18.0 * x[q]) / 64.0
+                elif len(inner) == 1:
+                    m = inner[0]
+                    f = np.array([(1.0 - x[q] * x[q]) * (1.0 + 9.0 * x[q] * c[q]) if q == m else 1.0 + x[q] * c[q]
+                                  for q in range(3)])
+                    df = np.array([(-2.0 * x[q]) * (1.0 + 9.0 * x[q] * c[q]) + (1.0 - x[q] * x[q]) * 9.0 * c[q]
+                                   if q == m else c[q] for q in range(3)])
+                    N[a] = 9.0 * f[0] * f[1] * f[2] / 64.0
+                    dN[a, 0] = 9.0 * df[0] * f[1] * f[2] / 64.0
+                    dN[a, 1] = 9.0 * f[0] * df[1] * f[2] / 64.0
+                    dN[a, 2] = 9.0 * f[0] * f[1] * df[2] / 64.0
+    return N, dN * (2.0 / h)
+
+
+def serendipity_present(k: int) -> np.ndarray:
+    """((k+1)^3,) bool: the lattice positions of the degree-k serendipity
+    element (at most one interior coordinate): 20 for k = 2, 32 for k = 3."""
+    na = k + 1
+    out = np.zeros(na ** 3, dtype=bool)
+    for iz in range(na):
+        for iy in range(na):
+            for ix in range(na):
+                inner = sum(1 for c in (ix, iy, iz) if 0 < c < k)
+                out[ix + na * (iy + na * iz)] = inner <= 1
+    return out
+
+
 def elasticity_D(nu: float, E: float = 1.0) -> np.ndarray:
     """Isotropic linear-elastic constitutive matrix (Voigt, engineering
     shear strains), the D of Eq. matrixK."""
@@ -160,9 +215,11 @@ def subcell_stiffness(k: int, n: int, nu: float, h: float = 1.0, family: str = "
     the memoised table: Section 3.3 computes it once for a regular mesh).
     family 'serendipity' (k = 2): the 20-node element on the 27-node lattice."""
     if family == "serendipity":
-        if k != 2:
-            raise ValueError("the serendipity element is built for degree 2")
-        return _subcell_stiffness_s2(int(n), float(nu), float(h)).copy()
+        if k == 2:
+            return _subcell_stiffness_s2(int(n), float(nu), float(h)).copy()
+        if k == 3:
+            return _subcell_stiffness_s3(int(n), float(nu), float(h)).copy()
+        raise ValueError("the serendipity element is built for degree 2 and 3")
     return _subcell_stiffness(int(k), int(n), float(nu), float(h)).copy()
 
 
@@ -188,6 +245,33 @@ def _subcell_stiffness_s2(n: int, nu: float, h: float) -> np.ndarray:
                         for qx in range(3):
                             wq = gw[qx] * gw[qy] * gw[qz] * half ** 3
                             _, dN = serendipity2_shape(cx + half * gp[qx], cy + half * gp[qy],
+                                                       cz + half * gp[qz], h)
+                            B = strain_displacement(dN)
+                            Ki += wq * jac * (B.T @ D @ B)
+                out[a + n * (b + n * c)] = Ki
+    return out
+
+
+@functools.lru_cache(maxsize=8)
+def _subcell_stiffness_s3(n: int, nu: float, h: float) -> np.ndarray:
+    """The 32-node cubic serendipity element: its shape functions have degree
+    at most 3 in each coordinate, so 4 Gauss points per axis and subcell are
+    exact for the integrand (degree <= 6 per axis)."""
+    D = elasticity_D(nu)
+    gp, gw = nleg.leggauss(4)
+    jac = (h / 2.0) ** 3
+    half = 1.0 / n
+    out = np.zeros((n ** 3, 192, 192))
+    for c in range(n):
+        for b in range(n):
+            for a in range(n):
+                cx, cy, cz = -1.0 + (2 * a + 1) / n, -1.0 + (2 * b + 1) / n, -1.0 + (2 * c + 1) / n
+                Ki = np.zeros((192, 192))
+                for qz in range(4):
+                    for qy in range(4):
+                        for qx in range(4):
+                            wq = gw[qx] * gw[qy] * gw[qz] * half ** 3
+                            _, dN = serendipity3_shape(cx + half * gp[qx], cy + half * gp[qy],
                                                        cz + half * gp[qz], h)
                             B = strain_displacement(dN)
                             Ki += wq * jac * (B.T @ D @ B)

@@ -94,3 +94,49 @@ def test_mixed_bridge_full_size():
     assert R.T.tosolve_free_dofs(R.h) == 519204
     _check_sampled(R.T, R, p, u[0], 1e-8, np.random.default_rng(3), nodes=120, cells=30, dcells=6)
     R.close()
+
+
+def test_serendipity_cantilever_full_size():
+    """The serendipity benchmark configuration: 48x24x24 elements, n = 2,
+    the smooth design with r = 1.5, 352,800 unknowns; FP32X2."""
+    p = workloads.with_serendipity(workloads.cantilever(48, 24, 24, degree=2, n_mr=2, rmin=1.5,
+                                                        density="smooth", seed=0))
+    R = Run(p, FP32X2)
+    R.set_densities()
+    u, info = R.solve(rtol=1e-8, maxit=3000)
+    assert info.rel_residual <= 1e-8
+    assert R.T.tosolve_free_dofs(R.h) == p.nfree == 352800
+    _check_sampled(R.T, R, p, u[0], 1e-8, np.random.default_rng(11), nodes=150, cells=30)
+    R.close()
+
+
+def test_suppression_on_the_ibeam_full_size():
+    """The I-beam of the suppression benchmark (96x48x48 Q1, n = 2, r = 1.5):
+    the selection bit for bit against the oracle's, then the suppressed
+    operator on sampled rows and the solve."""
+    import torch
+
+    from oracle import fe, fix
+
+    p = workloads.cantilever(96, 48, 48, n_mr=2, rmin=1.5, density="ibeam", seed=0)
+    S = sample.Sampler(p)
+    R = Run(p, FP32X2)
+    R.set_densities()
+    rho_dev = torch.zeros_like(R.x)
+    with torch.cuda.stream(R.stream):
+        R.T.tosolve_densities(R.h, rho_dev)
+    R.stream.synchronize()
+    rho = rho_dev.cpu().numpy()
+    # the densities themselves are pinned against the sampled oracle
+    cells = np.random.default_rng(5).choice(p.x.size, size=200, replace=False)
+    np.testing.assert_allclose(rho[cells], [S.rho(p.x, c) for c in cells], rtol=1e-14, atol=1e-300)
+    fixed = torch.zeros(p.x.size, dtype=torch.uint8, device=R.dev)
+    nsup = R.T.tosolve_fix_variables(R.h, None, 1e-6, 0.9, 1e-6, fixed)
+    fx = fix.fixed_elements(p, fix.element_class(p, rho, None, 1e-6, 0.9, 1e-6))
+    assert np.array_equal(fixed.cpu().numpy(), fix.fixed_design_variables(p, fx).astype(np.uint8))
+    q = fix.suppressed_problem(p, fix.suppressed_nodes(p, fx))
+    assert nsup == p.nfree - q.nfree and R.T.tosolve_free_dofs(R.h) == q.nfree
+    u, info = R.solve(rtol=1e-8)
+    assert info.rel_residual <= 1e-8
+    _check_sampled(R.T, R, q, u[0], 1e-8, np.random.default_rng(12), nodes=150, cells=20)
+    R.close()

@@ -1,5 +1,6 @@
-"""Pins of the 20-node serendipity element in the oracle (oracle/fem.py,
-Sec. 2.1) and of a serendipity mesh on the degree-2 lattice.
+"""Pins of the serendipity elements in the oracle (oracle/fem.py, Sec. 2.1):
+the 20-node element on the degree-2 lattice and the 32-node element on the
+degree-3 lattice (the same checks, the second set at the end).
 
 * The shape functions: Kronecker delta at the 20 nodes, zero at the face
   and cell centres, partition of unity, and exact reproduction of the 20
@@ -136,6 +137,77 @@ def test_patch_test_on_a_serendipity_mesh():
     u[0::3] = 0.01 * i + 0.02 * j
     u[1::3] = -0.03 * l
     u[2::3] = 0.005 * i - 0.01 * l
+    u[np.repeat(absent, 3)] = 0.0
+    r = K @ u
+    interior = (i > 0) & (i < Lx - 1) & (j > 0) & (j < Ly - 1) & (l > 0) & (l < Lz - 1) & ~absent
+    assert interior.any()
+    assert np.abs(r[np.repeat(interior, 3)]).max() < 1e-12
+
+
+# ---- the 32-node cubic serendipity element -----------------------------------
+
+POS3 = (-1.0, -1.0 / 3.0, 1.0 / 3.0, 1.0)
+NODES3 = [(POS3[i % 4], POS3[(i // 4) % 4], POS3[i // 16]) for i in range(64)]
+
+
+def test_s3_kronecker_and_completeness():
+    present = fem.serendipity_present(3)
+    assert present.sum() == 32
+    for b, xb in enumerate(NODES3):
+        N, _ = fem.serendipity3_shape(*xb)
+        if present[b]:
+            want = np.zeros(64)
+            want[b] = 1.0
+            assert np.allclose(N, want, atol=1e-14)
+        assert np.all(N[~present] == 0.0)
+    # the 32 monomials of superlinear degree <= 3 (the total degree less the
+    # number of variables that appear linearly): reproduced exactly
+    mons = [m for m in itertools.product(range(4), repeat=3) if sum(m) - sum(1 for e in m if e == 1) <= 3]
+    assert len(mons) == 32, len(mons)
+    rng = np.random.default_rng(3)
+    for _ in range(8):
+        x = rng.uniform(-1, 1, size=3)
+        N, _ = fem.serendipity3_shape(*x)
+        assert abs(N.sum() - 1.0) < 1e-13
+        for m in mons:
+            vals = np.array([np.prod([c ** e for c, e in zip(xb, m)]) for xb in NODES3])
+            vals[~present] = 0.0
+            assert abs(N @ vals - np.prod(x ** np.array(m))) < 1e-13, m
+    x = np.array([0.3, -0.4, 0.7])
+    N, _ = fem.serendipity3_shape(*x)
+    vals = np.array([xb[0] ** 2 * xb[1] ** 2 for xb in NODES3])  # superlinear degree 4
+    assert abs(N @ vals - x[0] ** 2 * x[1] ** 2) > 1e-3
+
+
+def test_s3_gradients_rank_and_subcells():
+    x = np.array([0.37, -0.52, 0.11])
+    _, dN = fem.serendipity3_shape(*x, h=2.0)
+    e = 1e-6
+    for q in range(3):
+        xp, xm = x.copy(), x.copy()
+        xp[q] += e
+        xm[q] -= e
+        fd = (fem.serendipity3_shape(*xp)[0] - fem.serendipity3_shape(*xm)[0]) / (2 * e)
+        assert np.allclose(dN[:, q], fd, atol=1e-8)
+    K = fem.subcell_stiffness(3, 1, NU, family="serendipity")[0]
+    assert np.linalg.matrix_rank(K, tol=1e-9) == 90
+    assert np.abs(K @ fem.rigid_body_modes(3).T).max() < 1e-13
+    K2 = fem.subcell_stiffness(3, 2, NU, family="serendipity")
+    assert np.abs(K2.sum(axis=0) - K).max() < 1e-12
+
+
+def test_s3_patch_test():
+    p = workloads.with_serendipity(workloads.cantilever(2, 2, 2, degree=3, n_mr=1, density="solid", seed=0))
+    m = fe.Model(p)
+    K = m.assemble(m.weights(m.densities(p.x))).toarray()
+    Lx, Ly, Lz = p.lattice
+    n = np.arange(Lx * Ly * Lz)
+    i, j, l = n % Lx, (n // Lx) % Ly, n // (Lx * Ly)
+    absent = workloads.serendipity_absent_nodes(p)
+    u = np.zeros(3 * len(n))
+    u[0::3] = 0.01 * i - 0.02 * l
+    u[1::3] = 0.03 * j
+    u[2::3] = -0.01 * i + 0.005 * j
     u[np.repeat(absent, 3)] = 0.0
     r = K @ u
     interior = (i > 0) & (i < Lx - 1) & (j > 0) & (j < Ly - 1) & (l > 0) & (l < Lz - 1) & ~absent

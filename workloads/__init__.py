@@ -288,21 +288,23 @@ def batched_instances(count: int, seed: int, *, min_nx: int = 32, max_nx: int = 
 
 
 def serendipity_absent_nodes(p: Problem) -> np.ndarray:
-    """(nnodes,) bool: the nodes of the degree-2 lattice that no 20-node
-    serendipity element has: face centres and element centres (two or three
-    odd lattice coordinates)."""
+    """(nnodes,) bool: the nodes of the degree-k lattice (k = 2, 3) that no
+    serendipity element has: those with two or three coordinates inside an
+    element edge (not a multiple of k) -- face and element interiors."""
+    k = p.degree
     Lx, Ly, Lz = p.lattice
     n = np.arange(Lx * Ly * Lz)
     i, j, l = n % Lx, (n // Lx) % Ly, n // (Lx * Ly)
-    return (i % 2) + (j % 2) + (l % 2) >= 2
+    return (i % k != 0).astype(int) + (j % k != 0) + (l % k != 0) >= 2
 
 
 def with_serendipity(p: Problem) -> Problem:
-    """The same problem with 20-node serendipity elements on its degree-2
-    lattice: the lattice nodes the element does not have are held at 0 with
-    the supports (they carry no unknown).  Loads there must be zero."""
-    if p.degree != 2:
-        raise ValueError("the serendipity element is built for degree 2")
+    """The same problem with serendipity elements (20 nodes for degree 2, 32
+    for degree 3) on its lattice: the lattice nodes the element does not
+    have are held at 0 with the supports (they carry no unknown).  Loads
+    there must be zero."""
+    if p.degree not in (2, 3):
+        raise ValueError("the serendipity element is built for degree 2 and 3")
     q = Problem(**{k: getattr(p, k) for k in p.__dataclass_fields__})
     absent = serendipity_absent_nodes(p)
     if np.any(np.asarray(p.f)[:, np.repeat(absent, 3)] != 0.0):
@@ -310,7 +312,7 @@ def with_serendipity(p: Problem) -> Problem:
     q.mask = (np.asarray(p.mask) != 0) | np.repeat(absent, 3)
     q.mask = q.mask.astype(np.uint8)
     q.family = "serendipity"
-    q.name = p.name.replace("_k2", "_s2")
+    q.name = p.name.replace(f"_k{p.degree}", f"_s{p.degree}")
     return q
 
 
