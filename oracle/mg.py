@@ -101,13 +101,61 @@ def prolongation_shape(lat_fine, family: str = "lagrange") -> sp.csr_matrix:
     return sp.kron(Pn, sp.identity(3), format="csr")
 
 
-def serendipity_absent(lat) -> np.ndarray:
-    """(3 nnodes,) bool: DOFs of degree-2 lattice nodes with two or three odd
-    coordinates (no serendipity node there)."""
+def serendipity_absent(lat, k: int = 2) -> np.ndarray:
+    """(3 nnodes,) bool: DOFs of degree-k lattice nodes with two or three
+    coordinates inside an element edge (no serendipity node there)."""
     Lx, Ly, Lz = lat
     n = np.arange(Lx * Ly * Lz)
     i, j, l = n % Lx, (n // Lx) % Ly, n // (Lx * Ly)
-    return np.repeat((i % 2) + (j % 2) + (l % 2) >= 2, 3)
+    return np.repeat((i % k != 0).astype(int) + (j % k != 0) + (l % k != 0) >= 2, 3)
+
+
+def prolongation_p(mesh_shape, family: str = "lagrange") -> sp.csr_matrix:
+    """Degree 2 -> degree 3 on the same mesh: the value at every node of the
+    degree-3 lattice of the degree-2 shape functions of the element owning
+    it (element min(i // 3, E - 1) along each axis, local xi = -1 + 2 f / 3).
+    The quadratic spaces are contained in the cubic ones of the same family,
+    so the degree-2 operator re-discretised on the same mesh is the Galerkin
+    product."""
+    nx, ny, nz = mesh_shape
+    L3 = (3 * nx + 1, 3 * ny + 1, 3 * nz + 1)
+    L2x, L2y = 2 * nx + 1, 2 * ny + 1
+    nc = L2x * L2y * (2 * nz + 1)
+    rows, cols, vals = [], [], []
+    lag = lambda j, x: (0.5 * x * (x - 1.0), 1.0 - x * x, 0.5 * x * (x + 1.0))[j]
+    for node in range(L3[0] * L3[1] * L3[2]):
+        i, j, l = node % L3[0], (node // L3[0]) % L3[1], node // (L3[0] * L3[1])
+        ex, ey, ez = min(i // 3, nx - 1), min(j // 3, ny - 1), min(l // 3, nz - 1)
+        x = (-1.0 + 2.0 * (i - 3 * ex) / 3.0, -1.0 + 2.0 * (j - 3 * ey) / 3.0, -1.0 + 2.0 * (l - 3 * ez) / 3.0)
+        if family == "lagrange":
+            N = np.array([lag(a % 3, x[0]) * lag((a // 3) % 3, x[1]) * lag(a // 9, x[2]) for a in range(27)])
+        else:
+            N, _ = fem.serendipity2_shape(*x)
+        for a in range(27):
+            if N[a] != 0.0:
+                cn = (2 * ex + a % 3) + L2x * ((2 * ey + (a // 3) % 3) + L2y * (2 * ez + a // 9))
+                rows.append(node); cols.append(cn); vals.append(N[a])
+    Pn = sp.csr_matrix((vals, (rows, cols)), shape=(L3[0] * L3[1] * L3[2], nc))
+    return sp.kron(Pn, sp.identity(3), format="csr")
+
+
+def p_coarse_mask(mask3: np.ndarray, mesh_shape) -> np.ndarray:
+    """Degree-2 mask from a degree-3 mask on the same mesh: a degree-2 DOF is
+    fixed iff every degree-3 DOF of the same component at its place is
+    fixed -- per axis, a vertex coordinate 2I meets the node 3I, a midpoint
+    2I + 1 the two nodes 3I + 1 and 3I + 2 inside the same edge."""
+    nx, ny, nz = mesh_shape
+    L3 = (3 * nx + 1, 3 * ny + 1, 3 * nz + 1)
+    m3 = mask3.reshape(L3[2], L3[1], L3[0], 3).astype(bool)
+    def idx(I):
+        return [3 * I // 2] if I % 2 == 0 else [3 * (I - 1) // 2 + 1, 3 * (I - 1) // 2 + 2]
+    out = np.zeros((2 * nz + 1, 2 * ny + 1, 2 * nx + 1, 3), dtype=np.uint8)
+    for K in range(2 * nz + 1):
+        for J in range(2 * ny + 1):
+            for I in range(2 * nx + 1):
+                sub = m3[np.ix_(idx(K), idx(J), idx(I))]
+                out[K, J, I] = sub.reshape(-1, 3).all(axis=0)
+    return out.reshape(-1)
 
 
 def coarse_mask(mask_f: np.ndarray, lat_fine) -> np.ndarray:
@@ -126,6 +174,9 @@ class Hierarchy:
     the dense Cholesky factor of the coarsest operator."""
 
     def __init__(self, prob, rho: np.ndarray, levels: int, transfer: str | None = None):
+        if prob.degree == 3:
+            self._init_cubic(prob, rho, levels)
+            return
         k, n = prob.degree, prob.n_mr
         family = getattr(prob, "family", "lagrange")
         if transfer is None:
@@ -173,6 +224,53 @@ class Hierarchy:
             F.P = (Mf @ P @ Mc).tocsr()
         last = self.levels[-1]
         last.chol = sla.cho_factor(last.A.toarray(), lower=True)
+
+
+def _cubic_levels(self, prob, rho, levels):
+    """Degree 3 (Lagrange or serendipity): level 0 is the degree-3 mesh,
+    level 1 the degree-2 mesh of the same family on the same elements (the
+    degree is coarsened first, Sec. 2.3's shape-function interpolation as
+    P), and the further levels the degree-2 hierarchy below it."""
+    family = getattr(prob, "family", "lagrange")
+    if levels < 2:
+        raise ValueError("degree 3 takes at least two levels")
+    # levels 1.. : the degree-2 hierarchy of the same mesh and densities
+    import copy
+
+    q = copy.copy(prob)
+    q.degree = 2
+    lat2 = (2 * prob.nx + 1, 2 * prob.ny + 1, 2 * prob.nz + 1)
+    m2 = p_coarse_mask(prob.mask, (prob.nx, prob.ny, prob.nz))
+    if family == "serendipity":
+        m2 = (m2.astype(bool) | serendipity_absent(lat2, 2)).astype(np.uint8)
+    q.mask = m2
+    sub = Hierarchy(q, rho, levels - 1)
+    self.omega = 0.3 if family == "serendipity" else 0.5
+    w_cells = simp_weights(rho, prob.E0, prob.Emin, prob.penal)
+    F = Level()
+    F.nx, F.ny, F.nz = prob.nx, prob.ny, prob.nz
+    F.nsub = prob.n_mr
+    F.lat = (3 * F.nx + 1, 3 * F.ny + 1, 3 * F.nz + 1)
+    F.ndof = 3 * F.lat[0] * F.lat[1] * F.lat[2]
+    F.mask = prob.mask.astype(np.uint8)
+    Ktab = fem.subcell_stiffness(3, F.nsub, prob.nu, family=family)
+    m, d, _ = Ktab.shape
+    w_e = w_cells[mesh.subcell_density_index(F.nx, F.ny, F.nz, F.nsub)]
+    Ke = (w_e @ Ktab.reshape(m, d * d)).reshape(-1, d, d)
+    ed = mesh.element_dofs(F.nx, F.ny, F.nz, 3)
+    K = sp.coo_matrix((Ke.reshape(-1), (np.repeat(ed, d, axis=1).reshape(-1), np.tile(ed, (1, d)).reshape(-1))),
+                      shape=(F.ndof, F.ndof)).tocsr()
+    free = (F.mask == 0).astype(np.float64)
+    Mf = sp.diags(free)
+    F.A = (Mf @ K @ Mf + sp.diags(1.0 - free)).tocsr()
+    F.Dinv = 1.0 / F.A.diagonal()
+    C = sub.levels[0]
+    Mc = sp.diags((C.mask == 0).astype(np.float64))
+    F.P = (Mf @ prolongation_p((F.nx, F.ny, F.nz), family) @ Mc).tocsr()
+    self.levels = [F] + sub.levels
+
+
+Hierarchy._init_cubic = _cubic_levels
 
 
 def vcycle(h: Hierarchy, b: np.ndarray, l: int = 0, omega: float | None = None, eta1: int = 1,

@@ -133,3 +133,27 @@ def test_degree2_shape_prolongation_reproduces_quadratics():
     vf = (Ps @ vc)[0::3]
     present = ~mg.serendipity_absent(lat_f)[0::3]
     np.testing.assert_allclose(vf[present], s(Xf)[present], atol=1e-12)
+
+
+@pytest.mark.parametrize("family", ["lagrange", "serendipity"])
+def test_degree3_p_coarsening_is_galerkin_and_converges(family):
+    """Degree 3: level 1 is the degree-2 mesh of the same family on the same
+    elements, P the degree-2 shape functions at the degree-3 nodes.  The
+    degree-2 space lies in the degree-3 one (serendipity: superlinear degree
+    2 within 3), so the re-discretised level-1 operator is P^T A P; MG-PCG
+    reaches the direct solution."""
+    p = workloads.cantilever(4, 2, 2, degree=3, n_mr=2, seed=3)
+    if family == "serendipity":
+        p = workloads.with_serendipity(p)
+    m = fe.Model(p)
+    h = mg.Hierarchy(p, m.densities(p.x), 3 if family == "lagrange" else 2)
+    F, C = h.levels[0], h.levels[1]
+    fc = C.mask == 0
+    G = (F.P.T @ F.A @ F.P).toarray()[np.ix_(fc, fc)]
+    A = C.A.toarray()[np.ix_(fc, fc)]
+    assert np.abs(G - A).max() <= 1e-12 * np.abs(A).max()
+    f = p.f[0].copy()
+    f[p.mask.astype(bool)] = 0.0
+    u, its, _ = mg.pcg(h, f, rtol=1e-11)
+    ref = m.run(method="splu")
+    assert np.linalg.norm(u - ref["u"][0]) <= 1e-8 * np.linalg.norm(ref["u"][0])
