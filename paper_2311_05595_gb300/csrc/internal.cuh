@@ -232,8 +232,14 @@ cudaError_t configure_tile_kernels();
 constexpr int kD2 = 81;       // DOFs of a triquadratic element
 constexpr int kDD2 = 81 * 81;
 constexpr int kNM2 = 125;     // moments of a degree-2 element matrix
+constexpr int kD3 = 192;      // DOFs of a tricubic element
+constexpr int kDD3 = 192 * 192;
 void launch_q2_subcell_table(int n, double nu, double h, int family, double* tab, cudaStream_t st);
 void launch_q2_moment_basis(double nu, int family, double* cmom, cudaStream_t st);
+// Degree-3 subcell tables (family 0 Lagrange, 1 the 32-node serendipity
+// element): grad_scratch holds n^3 * 64 * 64 * 3 doubles.
+void launch_q3_subcell_table(int n, double nu, double h, int family, double* grad_scratch, double* tab,
+                             cudaStream_t st);
 // Degree-2 levels with shape-function transfers (always for the serendipity
 // element): W = the 27 x 125 table of coarse shape values at the fine
 // lattice points of a coarse element (device, FP32).
@@ -353,6 +359,7 @@ struct tosolve_s {
   uint8_t* fix0 = nullptr;     // per DOF: the supports alone (level 0 mask adds slaved)
   // fixing variables (Sec. 6.1)
   float* ptab = nullptr;         // shape-function transfer table (27 x 125)
+  float* ptab3 = nullptr;        // degree 3 -> 2 transfer table (27 x 64)
   uint8_t* base0 = nullptr;    // level-0 mask before suppression (supports, slaved)
   int8_t* ecls = nullptr;      // per element: 1 void, 2 solid, 0 neither
   int8_t* efix = nullptr;      // per element: the class if fixed, else 0

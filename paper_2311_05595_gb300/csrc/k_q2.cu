@@ -29,6 +29,18 @@ constexpr int kDD = kD * kD;        // 6561
 constexpr int kP = 2 * kK - 1;      // 5 monomial powers per axis
 constexpr int kNM = kP * kP * kP;   // 125 moments
 
+// An element of degree K (2 or 3) on its node lattice: K + 1 nodes per axis.
+// The degree-3 element appears only on the finest level of a hierarchy,
+// whose next level is the degree-2 mesh of the same elements.
+template <int K>
+struct Deg {
+  static constexpr int NA = K + 1;
+  static constexpr int NE = NA * NA * NA;
+  static constexpr int D = 3 * NE;
+  static constexpr int DD = D * D;
+  static constexpr int TB = (D + 31) / 32 * 32;  // threads of the element apply
+};
+
 // 1D Lagrange basis on the nodes -1, 0, 1: value and derivative of basis j.
 __host__ __device__ __forceinline__ double lag(int j, double x) {
   return j == 0 ? 0.5 * x * (x - 1.0) : (j == 1 ? 1.0 - x * x : 0.5 * x * (x + 1.0));
@@ -131,6 +143,130 @@ __global__ void k_q2_subcell_table(int n, double nu, double h, int family, doubl
       acc += wq * v;
     }
     tab[(size_t)sub * kDD + t] = jac * acc;
+  }
+}
+
+// Degree 3 (the finest level only).  1D cubic Lagrange basis on the nodes
+// -1, -1/3, 1/3, 1 and its derivative (product form).
+__device__ __forceinline__ double lag3(int j, double x) {
+  double v = 1.0;
+  const double xj = -1.0 + 2.0 * j / 3.0;
+  for (int m = 0; m < 4; ++m)
+    if (m != j) {
+      const double xm = -1.0 + 2.0 * m / 3.0;
+      v *= (x - xm) / (xj - xm);
+    }
+  return v;
+}
+__device__ __forceinline__ double dlag3(int j, double x) {
+  const double xj = -1.0 + 2.0 * j / 3.0;
+  double s = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    if (q == j) continue;
+    double v = 1.0 / (xj - (-1.0 + 2.0 * q / 3.0));
+    for (int m = 0; m < 4; ++m)
+      if (m != j && m != q) {
+        const double xm = -1.0 + 2.0 * m / 3.0;
+        v *= (x - xm) / (xj - xm);
+      }
+    s += v;
+  }
+  return s;
+}
+
+// Reference gradient of the 32-node serendipity shape function at lattice
+// position (ax, ay, az) in 0..3 (positions -1, -1/3, 1/3, 1): a vertex has
+// N = (1 + x c_x)(1 + y c_y)(1 + z c_z)(9 (x^2 + y^2 + z^2) - 19) / 64, an
+// edge node with interior coordinate c = +-1/3 along axis m
+// N = 9 (1 - t^2)(1 + 9 t c)(1 + ...)(1 + ...) / 64; positions with two or
+// three interior coordinates have no node.
+__device__ void s3_grad(int ax, int ay, int az, double x, double y, double z, double g[3]) {
+  const int ix[3] = {ax, ay, az};
+  const double p[3] = {x, y, z};
+  double c[3];
+  int inner = 0, m = 0;
+  for (int q = 0; q < 3; ++q) {
+    c[q] = -1.0 + 2.0 * ix[q] / 3.0;
+    if (ix[q] == 1 || ix[q] == 2) { ++inner; m = q; }
+  }
+  g[0] = g[1] = g[2] = 0.0;
+  if (inner == 0) {
+    double f[3];
+    for (int q = 0; q < 3; ++q) f[q] = 1.0 + p[q] * c[q];
+    const double sv = 9.0 * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - 19.0;
+    const double prod = f[0] * f[1] * f[2];
+    for (int q = 0; q < 3; ++q) {
+      const double others = q == 0 ? f[1] * f[2] : (q == 1 ? f[0] * f[2] : f[0] * f[1]);
+      g[q] = (c[q] * others * sv + prod * 18.0 * p[q]) / 64.0;
+    }
+  } else if (inner == 1) {
+    double f[3], df[3];
+    for (int q = 0; q < 3; ++q) {
+      if (q == m) {
+        f[q] = (1.0 - p[q] * p[q]) * (1.0 + 9.0 * p[q] * c[q]);
+        df[q] = -2.0 * p[q] * (1.0 + 9.0 * p[q] * c[q]) + (1.0 - p[q] * p[q]) * 9.0 * c[q];
+      } else {
+        f[q] = 1.0 + p[q] * c[q];
+        df[q] = c[q];
+      }
+    }
+    g[0] = 9.0 * df[0] * f[1] * f[2] / 64.0;
+    g[1] = 9.0 * f[0] * df[1] * f[2] / 64.0;
+    g[2] = 9.0 * f[0] * f[1] * df[2] / 64.0;
+  }
+}
+
+// Physical gradients of the 64 degree-3 shape functions at the 4^3
+// Gauss-Legendre points of every subcell: gr[((sub * 64 + q) * 64 + a) * 3 + i].
+__global__ void k_q3_grads(int n, double h, int family, double* __restrict__ gr) {
+  const double gp[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
+  const long total = (long)n * n * n * 64 * 64;
+  const double half = 1.0 / n, s = 2.0 / h;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int a = t % 64, q = (t / 64) % 64;
+    const int sub = (int)(t / (64 * 64));
+    const int sa = sub % n, sb = (sub / n) % n, sc = sub / (n * n);
+    const double xi = -1.0 + (2 * sa + 1) * half + half * gp[q % 4];
+    const double eta = -1.0 + (2 * sb + 1) * half + half * gp[(q / 4) % 4];
+    const double zeta = -1.0 + (2 * sc + 1) * half + half * gp[q / 16];
+    const int ax = a % 4, ay = (a / 4) % 4, az = a / 16;
+    double g[3];
+    if (family == 1) {
+      s3_grad(ax, ay, az, xi, eta, zeta, g);
+    } else {
+      g[0] = dlag3(ax, xi) * lag3(ay, eta) * lag3(az, zeta);
+      g[1] = lag3(ax, xi) * dlag3(ay, eta) * lag3(az, zeta);
+      g[2] = lag3(ax, xi) * lag3(ay, eta) * dlag3(az, zeta);
+    }
+    for (int i = 0; i < 3; ++i) gr[t * 3 + i] = s * g[i];
+  }
+}
+
+// K^(e_i), 192 x 192, from the gradients: 4-point Gauss-Legendre per axis
+// and subcell (exact for the integrand's degree <= 6 per axis).
+__global__ void k_q3_subcell_table(int n, double nu, double h, const double* __restrict__ gr,
+                                   double* __restrict__ tab) {
+  constexpr int kD3 = Deg<3>::D, kDD3 = Deg<3>::DD;
+  const double gw[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461, 0.3478548451374538};
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = 1.0 / (2.0 * (1.0 + nu));
+  const double half = 1.0 / n;
+  const double jac = half * half * half * (0.125 * h * h * h);
+  const long total = (long)n * n * n * kDD3;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int sub = (int)(t / kDD3), ent = (int)(t % kDD3);
+    const int R = ent / kD3, C = ent % kD3;
+    const int a = R / 3, i = R % 3, b = C / 3, j = C % 3;
+    double acc = 0.0;
+    for (int q = 0; q < 64; ++q) {
+      const double wq = gw[q % 4] * gw[(q / 4) % 4] * gw[q / 16];
+      const double* ga = gr + ((size_t)(sub * 64 + q) * 64 + a) * 3;
+      const double* gb = gr + ((size_t)(sub * 64 + q) * 64 + b) * 3;
+      double v = lam * ga[i] * gb[j] + mu * ga[j] * gb[i];
+      if (i == j) v += mu * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
+      acc += wq * v;
+    }
+    tab[t] = jac * acc;
   }
 }
 
@@ -322,8 +458,10 @@ __global__ void k_q2_moments_to_ke(long E, double h, const double* __restrict__ 
 
 // Level-0 element matrices: K^(e) = sum_i w_{e,i} K^(e_i) over the n^3
 // subcells (Eq. matrixK_mr), FP64.  Block per kEB elements.
+template <int K>
 __global__ void k_q2_elem(int ex, int ey, long E, int n, const double* __restrict__ w, int Dx, int Dy,
                           const double* __restrict__ tab, double* __restrict__ Ke) {
+  constexpr int kDD = Deg<K>::DD;
   extern __shared__ double ws[];  // kEB * m
   const int m = n * n * n;
   const long e0 = blockIdx.x * (long)kEB;
@@ -353,8 +491,25 @@ __global__ void k_q2_elem(int ex, int ey, long E, int n, const double* __restric
   }
 }
 
+template <int K>
+__device__ __forceinline__ long elem_node_k(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
+  constexpr int NA = K + 1;
+  return (K * exi + a % NA) + (long)Lx * ((K * eyi + (a / NA) % NA) + (long)Ly * (K * ezi + a / (NA * NA)));
+}
 __device__ __forceinline__ long elem_node(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
-  return (2 * exi + a % 3) + (long)Lx * ((2 * eyi + (a / 3) % 3) + (long)Ly * (2 * ezi + a / 9));
+  return elem_node_k<2>(exi, eyi, ezi, a, Lx, Ly);
+}
+
+// Elements along one axis that contain lattice coordinate c (degree K, e
+// elements): [lo, hi].
+template <int K>
+__device__ __forceinline__ void elems_of(int c, int e, int& lo, int& hi) {
+  if (c % K) {
+    lo = hi = c / K;
+  } else {
+    lo = max(c / K - 1, 0);
+    hi = min(c / K, e - 1);
+  }
 }
 
 template <typename T>
@@ -378,19 +533,20 @@ struct Sum<dfloat> {
 // shape function a there.  The restriction gathers, for each coarse node,
 // the fine nodes of its elements that belong to those elements, so that it
 // is exactly the transpose of the prolongation.
-template <typename T>
+template <int S, typename T>
 __global__ void k_s2_prolong(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int ecx, int ecy, int ecz,
                              const float* __restrict__ W, const uint8_t* __restrict__ maskf,
                              const T* __restrict__ zc, T* __restrict__ v) {
+  constexpr int FP = S + 1, NF = FP * FP * FP;
   const long nnf = (long)Lxf * Lyf * Lzf;
   for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nnf;
        node += (long)gridDim.x * blockDim.x) {
     const int i = node % Lxf, j = (node / Lxf) % Lyf, l = node / ((long)Lxf * Lyf);
-    const int ex = min(i / 4, ecx - 1), ey = min(j / 4, ecy - 1), ez = min(l / 4, ecz - 1);
-    const int f = (i - 4 * ex) + 5 * ((j - 4 * ey) + 5 * (l - 4 * ez));
+    const int ex = min(i / S, ecx - 1), ey = min(j / S, ecy - 1), ez = min(l / S, ecz - 1);
+    const int f = (i - S * ex) + FP * ((j - S * ey) + FP * (l - S * ez));
     Sum<T> acc[3];
     for (int a = 0; a < 27; ++a) {
-      const float wgt = W[a * 125 + f];
+      const float wgt = W[a * NF + f];
       if (wgt == 0.f) continue;
       const long cn = (2 * ex + a % 3) + (long)Lxc * ((2 * ey + (a / 3) % 3) + (long)Lyc * (2 * ez + a / 9));
       acc[0].add(wgt, zc[3 * cn]);
@@ -407,21 +563,22 @@ __global__ void k_s2_prolong(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int ec
 // once); Y_E[a] = sum over its owned fine points f of W[a][f] r_f, then each
 // coarse node adds Y over the elements that contain it (fixed order).  One
 // block per coarse element at a time, 81 outputs.
-template <typename T>
+template <int S, typename T>
 __global__ void __launch_bounds__(96) k_s2_restrict_elem(int Lxf, int Lyf, int ecx, int ecy, long Ec,
                                                          const float* __restrict__ W, const T* __restrict__ rf,
                                                          T* __restrict__ Y) {
-  __shared__ T rs[125][3];
-  __shared__ float ws[27 * 125];
-  for (int t = threadIdx.x; t < 27 * 125; t += blockDim.x) ws[t] = W[t];
+  constexpr int FP = S + 1, NF = FP * FP * FP;
+  __shared__ T rs[NF][3];
+  __shared__ float ws[27 * NF];
+  for (int t = threadIdx.x; t < 27 * NF; t += blockDim.x) ws[t] = W[t];
   const int ecz = (int)(Ec / ((long)ecx * ecy));
   for (long e = blockIdx.x; e < Ec; e += gridDim.x) {
     const int ex = e % ecx, ey = (e / ecx) % ecy, ez = e / ((long)ecx * ecy);
     __syncthreads();
-    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
-      const int fx = t % 5, fy = (t / 5) % 5, fz = t / 25;
-      const int i = 4 * ex + fx, j = 4 * ey + fy, l = 4 * ez + fz;
-      const bool own = min(i / 4, ecx - 1) == ex && min(j / 4, ecy - 1) == ey && min(l / 4, ecz - 1) == ez;
+    for (int t = threadIdx.x; t < NF; t += blockDim.x) {
+      const int fx = t % FP, fy = (t / FP) % FP, fz = t / (FP * FP);
+      const int i = S * ex + fx, j = S * ey + fy, l = S * ez + fz;
+      const bool own = min(i / S, ecx - 1) == ex && min(j / S, ecy - 1) == ey && min(l / S, ecz - 1) == ez;
       const long fn = i + (long)Lxf * (j + (long)Lyf * l);
       for (int c = 0; c < 3; ++c) rs[t][c] = own ? rf[3 * fn + c] : T(0);
     }
@@ -429,8 +586,8 @@ __global__ void __launch_bounds__(96) k_s2_restrict_elem(int Lxf, int Lyf, int e
     if (threadIdx.x < kD) {
       const int a = threadIdx.x / 3, c = threadIdx.x % 3;
       Sum<T> acc;
-      for (int f = 0; f < 125; ++f) {
-        const float wgt = ws[a * 125 + f];
+      for (int f = 0; f < NF; ++f) {
+        const float wgt = ws[a * NF + f];
         if (wgt != 0.f) acc.add(wgt, rs[f][c]);
       }
       Y[e * kD + threadIdx.x] = acc.value();
@@ -475,27 +632,28 @@ __global__ void k_s2_restrict_gather(int Lxc, int Lyc, int Lzc, int ecx, int ecy
 // all fixed is skipped (no row of it is ever read: the gather passes fixed
 // DOFs through as identity rows), so suppressed void regions cost no
 // element-matrix traffic.
-template <typename T>
-__global__ void __launch_bounds__(96) k_q2_apply(int ex, int ey, long E, int Lx, int Ly,
-                                                 const op_t<T>* __restrict__ Ke,
-                                                 const uint8_t* __restrict__ mask,
-                                                 const T* __restrict__ u, T* __restrict__ Y) {
+template <int K, typename T>
+__global__ void __launch_bounds__(Deg<K>::TB) k_q2_apply(int ex, int ey, long E, int Lx, int Ly,
+                                                         const op_t<T>* __restrict__ Ke,
+                                                         const uint8_t* __restrict__ mask,
+                                                         const T* __restrict__ u, T* __restrict__ Y) {
+  constexpr int kD = Deg<K>::D, kDD = Deg<K>::DD;
   __shared__ T ue[kD];
   for (long e = blockIdx.x; e < E; e += gridDim.x) {
     const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
     bool free_dof = false;
     if (threadIdx.x < kD) {
       const int a = threadIdx.x / 3, c = threadIdx.x % 3;
-      const long d = 3 * elem_node(exi, eyi, ezi, a, Lx, Ly) + c;
+      const long d = 3 * elem_node_k<K>(exi, eyi, ezi, a, Lx, Ly) + c;
       free_dof = mask[d] == 0;
       ue[threadIdx.x] = free_dof ? u[d] : T(0);
     }
     if (!__syncthreads_or(free_dof)) continue;  // block-uniform
     if (threadIdx.x < kD) {
-      const op_t<T>* K = Ke + e * (size_t)kDD + threadIdx.x;
+      const op_t<T>* Kc = Ke + e * (size_t)kDD + threadIdx.x;
       Sum<T> acc;
 #pragma unroll 9
-      for (int b = 0; b < kD; ++b) acc.add(K[(size_t)b * kD], ue[b]);
+      for (int b = 0; b < kD; ++b) acc.add(Kc[(size_t)b * kD], ue[b]);
       Y[e * kD + threadIdx.x] = acc.value();
     }
     __syncthreads();
@@ -507,11 +665,12 @@ __global__ void __launch_bounds__(96) k_q2_apply(int ex, int ey, long E, int Lx,
 //   mode 1: out = v + omega D^-1 (b - y)   (post-smoothing)
 //   mode 2: out = y                (plain apply)
 // Fixed DOFs are identity rows: y = v there.
-template <typename T>
+template <int K, typename T>
 __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, const T* __restrict__ Y,
                             const T* __restrict__ b, const T* __restrict__ v,
                             const op_t<T>* __restrict__ dinv, const uint8_t* __restrict__ mask,
                             T omega, int mode, T* __restrict__ out) {
+  constexpr int kD = Deg<K>::D, NA = K + 1;
   const long nn = (long)Lx * Ly * Lz;
   for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
        node += (long)gridDim.x * blockDim.x) {
@@ -519,10 +678,7 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
     // elements along each axis containing this lattice coordinate
     int e0[3], e1[3];
     const int co[3] = {i, j, l}, ext[3] = {ex, ey, ez};
-    for (int ax = 0; ax < 3; ++ax) {
-      if (co[ax] & 1) { e0[ax] = e1[ax] = co[ax] >> 1; }
-      else { e0[ax] = max((co[ax] >> 1) - 1, 0); e1[ax] = min(co[ax] >> 1, ext[ax] - 1); }
-    }
+    for (int ax = 0; ax < 3; ++ax) elems_of<K>(co[ax], ext[ax], e0[ax], e1[ax]);
     T y[3] = {T(0), T(0), T(0)};
     // a node with all DOFs fixed does not use y (its elements may be skipped)
     const bool all_fixed = mask[3 * node] && mask[3 * node + 1] && mask[3 * node + 2];
@@ -530,7 +686,7 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
       for (int ey_ = e0[1]; ey_ <= e1[1]; ++ey_)
         for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
           const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
-          const int a = (i - 2 * ex_) + 3 * ((j - 2 * ey_) + 3 * (l - 2 * ez_));
+          const int a = (i - K * ex_) + NA * ((j - K * ey_) + NA * (l - K * ez_));
           const T* Ye = Y + e * kD + 3 * a;
           y[0] += Ye[0];
           y[1] += Ye[1];
@@ -548,25 +704,23 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
 }
 
 // Inverse Jacobi diagonal: 1 / sum_e K^(e)_{3a+c, 3a+c}; fixed DOFs 1.
-template <typename T>
+template <int K, typename T>
 __global__ void k_q2_dinv(int Lx, int Ly, int Lz, int ex, int ey, int ez, const double* __restrict__ Ke,
                           const uint8_t* __restrict__ mask, T* __restrict__ dinv) {
+  constexpr int kD = Deg<K>::D, kDD = Deg<K>::DD, NA = K + 1;
   const long nn = (long)Lx * Ly * Lz;
   for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
        node += (long)gridDim.x * blockDim.x) {
     const int i = node % Lx, j = (node / Lx) % Ly, l = node / ((long)Lx * Ly);
     int e0[3], e1[3];
     const int co[3] = {i, j, l}, ext[3] = {ex, ey, ez};
-    for (int ax = 0; ax < 3; ++ax) {
-      if (co[ax] & 1) { e0[ax] = e1[ax] = co[ax] >> 1; }
-      else { e0[ax] = max((co[ax] >> 1) - 1, 0); e1[ax] = min(co[ax] >> 1, ext[ax] - 1); }
-    }
+    for (int ax = 0; ax < 3; ++ax) elems_of<K>(co[ax], ext[ax], e0[ax], e1[ax]);
     double dg[3] = {0.0, 0.0, 0.0};
     for (int ez_ = e0[2]; ez_ <= e1[2]; ++ez_)
       for (int ey_ = e0[1]; ey_ <= e1[1]; ++ey_)
         for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
           const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
-          const int a = (i - 2 * ex_) + 3 * ((j - 2 * ey_) + 3 * (l - 2 * ez_));
+          const int a = (i - K * ex_) + NA * ((j - K * ey_) + NA * (l - K * ez_));
           for (int c = 0; c < 3; ++c) dg[c] += Ke[e * (size_t)kDD + (size_t)(3 * a + c) * kD + 3 * a + c];
         }
     for (int c = 0; c < 3; ++c) {
@@ -607,24 +761,26 @@ __global__ void k_q2_dense_fixed(long n, const uint8_t* __restrict__ mask, doubl
 // subcell), dc/drho_i = -p rho_i^(p-1) (E0 - Emin) s (accumulated over load
 // cases unless first).  Block per element: u_e staged, warps over subcells,
 // lanes over rows.
+template <int K>
 __global__ void k_q2_energy_grad(int ex, int ey, long E, int n, int Lx, int Ly,
                                  const double* __restrict__ u, const double* __restrict__ tab,
                                  const double* __restrict__ rho, double penal, double dE, int Dx,
                                  int Dy, int first, double* __restrict__ g) {
+  constexpr int kD = Deg<K>::D, kDD = Deg<K>::DD;
   __shared__ double ue[kD];
   const int m = n * n * n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (long e = blockIdx.x; e < E; e += gridDim.x) {
     const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
     for (int t = threadIdx.x; t < kD; t += blockDim.x)
-      ue[t] = u[3 * elem_node(exi, eyi, ezi, t / 3, Lx, Ly) + t % 3];
+      ue[t] = u[3 * elem_node_k<K>(exi, eyi, ezi, t / 3, Lx, Ly) + t % 3];
     __syncthreads();
     for (int s = warp; s < m; s += nw) {
-      const double* K = tab + (size_t)s * kDD;
+      const double* Ks = tab + (size_t)s * kDD;
       double acc = 0.0;
       for (int R = lane; R < kD; R += 32) {
         double y = 0.0;
-        for (int C = 0; C < kD; ++C) y += K[(size_t)R * kD + C] * ue[C];
+        for (int C = 0; C < kD; ++C) y += Ks[(size_t)R * kD + C] * ue[C];
         acc += ue[R] * y;
       }
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -784,9 +940,13 @@ void launch_s2_restrict(int vt, const Level& F, const Level& C, const float* W, 
   long ge = (long)F.sms * 8;
   if (ge > Ec) ge = Ec;
   const int g = grid_for2(C.nn);
+  const bool pdeg = F.k == 3;  // degree 3 -> 2 on the same elements
   auto run = [&](auto tag) {
     using T = decltype(tag);
-    k_s2_restrict_elem<T><<<(int)ge, 96, 0, st>>>(F.Lx, F.Ly, C.ex, C.ey, Ec, W, (const T*)F.r, (T*)C.Y);
+    if (pdeg)
+      k_s2_restrict_elem<3, T><<<(int)ge, 96, 0, st>>>(F.Lx, F.Ly, C.ex, C.ey, Ec, W, (const T*)F.r, (T*)C.Y);
+    else
+      k_s2_restrict_elem<4, T><<<(int)ge, 96, 0, st>>>(F.Lx, F.Ly, C.ex, C.ey, Ec, W, (const T*)F.r, (T*)C.Y);
     k_s2_restrict_gather<T><<<g, 256, 0, st>>>(C.Lx, C.Ly, C.Lz, C.ex, C.ey, C.ez, (const T*)C.Y, C.mask,
                                                (T*)C.b, (const op_t<T>*)dinvc, (T)omega, (T*)vc);
   };
@@ -799,8 +959,12 @@ void launch_s2_prolong(int vt, const Level& F, const Level& C, const float* W, c
   const int g = grid_for2(F.nn);
   auto run = [&](auto tag) {
     using T = decltype(tag);
-    k_s2_prolong<T><<<g, 256, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.ex, C.ey, C.ez, W, F.mask,
-                                       (const T*)C.z, (T*)F.v);
+    if (F.k == 3)
+      k_s2_prolong<3, T><<<g, 256, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.ex, C.ey, C.ez, W, F.mask,
+                                            (const T*)C.z, (T*)F.v);
+    else
+      k_s2_prolong<4, T><<<g, 256, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.ex, C.ey, C.ez, W, F.mask,
+                                            (const T*)C.z, (T*)F.v);
   };
   if (vt == kVtF64) run(double());
   else if (vt == kVtF32) run(float());
@@ -811,7 +975,18 @@ void launch_q2_elem(const Level& L, int n, const double* w, int Dx, int Dy, cons
                     double* Ke, cudaStream_t st) {
   const long E = (long)L.ex * L.ey * L.ez;
   const size_t sm = (size_t)kEB * n * n * n * sizeof(double);
-  k_q2_elem<<<(int)((E + kEB - 1) / kEB), 256, sm, st>>>(L.ex, L.ey, E, n, w, Dx, Dy, tab, Ke);
+  if (L.k == 3)
+    k_q2_elem<3><<<(int)((E + kEB - 1) / kEB), 256, sm, st>>>(L.ex, L.ey, E, n, w, Dx, Dy, tab, Ke);
+  else
+    k_q2_elem<2><<<(int)((E + kEB - 1) / kEB), 256, sm, st>>>(L.ex, L.ey, E, n, w, Dx, Dy, tab, Ke);
+}
+
+void launch_q3_subcell_table(int n, double nu, double h, int family, double* grad_scratch, double* tab,
+                             cudaStream_t st) {
+  const long ng = (long)n * n * n * 64 * 64;
+  k_q3_grads<<<grid_for2(ng), 256, 0, st>>>(n, h, family, grad_scratch);
+  const long nt = (long)n * n * n * Deg<3>::DD;
+  k_q3_subcell_table<<<grid_for2(nt), 256, 0, st>>>(n, nu, h, grad_scratch, tab);
 }
 
 void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, const double* cmom,
@@ -824,10 +999,17 @@ void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, cons
 
 void launch_q2_dinv(bool fp64, const Level& L, const double* Ke, void* dinv, cudaStream_t st) {
   const int g = grid_for2(L.nn);
-  if (fp64)
-    k_q2_dinv<double><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (double*)dinv);
-  else
-    k_q2_dinv<float><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (float*)dinv);
+  if (L.k == 3) {
+    if (fp64)
+      k_q2_dinv<3, double><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (double*)dinv);
+    else
+      k_q2_dinv<3, float><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (float*)dinv);
+  } else {
+    if (fp64)
+      k_q2_dinv<2, double><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (double*)dinv);
+    else
+      k_q2_dinv<2, float><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (float*)dinv);
+  }
 }
 
 void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t st) {
@@ -849,11 +1031,19 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
   const int gg = grid_for2(L.nn);
   auto run = [&](auto tag) {
     using T = decltype(tag);
-    k_q2_apply<T><<<(int)ga, 96, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
-                                          (const T*)v, (T*)Y);
-    k_q2_gather<T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
-                                       (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
-                                       (T*)out);
+    if (L.k == 3) {
+      k_q2_apply<3, T><<<(int)ga, Deg<3>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
+                                                        (const T*)v, (T*)Y);
+      k_q2_gather<3, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
+                                            (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
+                                            (T*)out);
+    } else {
+      k_q2_apply<2, T><<<(int)ga, Deg<2>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
+                                                        (const T*)v, (T*)Y);
+      k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
+                                            (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
+                                            (T*)out);
+    }
   };
   if (vt == kVtF64) run(double());
   else if (vt == kVtF32) run(float());
@@ -886,8 +1076,12 @@ void launch_q2_energy_grad(const Level& L0, int n, const double* u, const double
   const long E = (long)L0.ex * L0.ey * L0.ez;
   long gr = (long)sms * 8;
   if (gr > E) gr = E;
-  k_q2_energy_grad<<<(int)gr, 256, 0, st>>>(L0.ex, L0.ey, E, n, L0.Lx, L0.Ly, u, tab, rho, penal, dE,
-                                            Dx, Dy, first ? 1 : 0, g);
+  if (L0.k == 3)
+    k_q2_energy_grad<3><<<(int)gr, 256, 0, st>>>(L0.ex, L0.ey, E, n, L0.Lx, L0.Ly, u, tab, rho, penal, dE,
+                                                 Dx, Dy, first ? 1 : 0, g);
+  else
+    k_q2_energy_grad<2><<<(int)gr, 256, 0, st>>>(L0.ex, L0.ey, E, n, L0.Lx, L0.Ly, u, tab, rho, penal, dE,
+                                                 Dx, Dy, first ? 1 : 0, g);
 }
 
 }  // namespace tos

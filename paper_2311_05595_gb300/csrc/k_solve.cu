@@ -721,7 +721,7 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
                        (float*)F.r, st);
     }
   }
-  if (F.k == 2)
+  if (F.k >= 2)
     launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, 0, F.r,
                  F.sms, st);
   else if (!use_tc)
@@ -748,7 +748,7 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
       return;
     }
   }
-  if (F.k == 2) {
+  if (F.k >= 2) {
     launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, 1, F.z,
                  F.sms, st);
     return;
@@ -798,7 +798,7 @@ void launch_cg_residual(int vt, const Level& L0, double omega, const double* f, 
                         double* r, int mode, double* part, const double* part_ff, int np,
                         DevState* ds, unsigned* cnt, cudaGraphConditionalHandle hc, int use_cond,
                         cudaStream_t st) {
-  if (L0.k == 2) {  // r = K u by elements, then the residual step
+  if (L0.k >= 2) {  // r = K u by elements, then the residual step
     launch_q2_op(kVtF64, L0, L0.K64, L0.Y, nullptr, u, nullptr, 0.0, 2, r, L0.sms, st);
     VT_DISPATCH(vt, (k_cg_residual_y<T><<<np, kRowThreads, 0, st>>>(
                         L0.nn, f, r, (T*)L0.b, dinv_of<T>(L0), (T)omega, (T*)L0.v, part, part_ff, np,
@@ -825,7 +825,7 @@ void launch_cg_dir(int vt, const Level& L0, double* p, int np, const DevState* d
 
 void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, int np, DevState* ds,
                      unsigned* cnt, cudaStream_t st) {
-  if (L0.k == 2) {
+  if (L0.k >= 2) {
     launch_q2_op(kVtF64, L0, L0.K64, L0.Y, nullptr, p, nullptr, 0.0, 2, q, L0.sms, st);
     k_cg_apply_y<<<np, kRowThreads, 0, st>>>(L0.nn, p, q, part, ds, cnt);
     return;
@@ -844,7 +844,7 @@ void launch_cg_update(int vt, const Level& L0, double omega, double* u, double* 
 }
 
 void launch_apply_diag(int vt, const Level& L, const double* x, double* y, cudaStream_t st) {
-  if (L.k == 2) {
+  if (L.k >= 2) {
     if (vt == kVtF64) {  // FP64 in and out: no staging
       launch_q2_op(kVtF64, L, L.K64, L.Y, nullptr, x, nullptr, 0.0, 2, y, L.sms, st);
       return;

@@ -65,14 +65,20 @@ struct Plan {
   size_t bytes = 0;
 };
 
+// Degree 3: level 0 is the cubic mesh, level 1 the quadratic mesh of the
+// same elements (the degree is coarsened first), and each further level
+// halves the mesh.  Otherwise every level halves the mesh of the one above.
+int level_degree(const tosolve_desc& d, int l) { return d.degree == 3 ? (l == 0 ? 3 : 2) : d.degree; }
+int level_shift(const tosolve_desc& d, int l) { return d.degree == 3 ? (l == 0 ? 0 : l - 1) : l; }
+
 bool divisible(const tosolve_desc& d, int levels) {
-  const int s = 1 << (levels - 1);
+  const int s = 1 << level_shift(d, levels - 1);
   return d.nx % s == 0 && d.ny % s == 0 && d.nz % s == 0;
 }
 
 long coarse_dofs(const tosolve_desc& d, int levels) {
-  const int s = 1 << (levels - 1);
-  const long k = d.degree;
+  const int s = 1 << level_shift(d, levels - 1);
+  const long k = level_degree(d, levels - 1);
   return 3L * (k * (d.nx / s) + 1) * (k * (d.ny / s) + 1) * (k * (d.nz / s) + 1);
 }
 
@@ -95,9 +101,10 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   tosolve_desc d = *dp;
   if (d.nx < 1 || d.ny < 1 || d.nz < 1) { *why = "nx, ny, nz must be >= 1"; return TOSOLVE_EINVAL; }
   if ((long)d.nx * d.ny * d.nz > (1L << 28)) { *why = "mesh too large"; return TOSOLVE_EINVAL; }
-  if (d.degree != 1 && d.degree != 2) { *why = "degree must be 1 or 2"; return TOSOLVE_EINVAL; }
+  if (d.degree < 1 || d.degree > 3) { *why = "degree must be 1, 2 or 3"; return TOSOLVE_EINVAL; }
   if (d.family != 0 && d.family != 1) { *why = "family must be 0 (Lagrange) or 1 (serendipity)"; return TOSOLVE_EINVAL; }
-  if (d.family == 1 && d.degree != 2) { *why = "the serendipity element is built for degree 2"; return TOSOLVE_EINVAL; }
+  if (d.family == 1 && d.degree == 1) { *why = "the serendipity element is built for degree 2 and 3"; return TOSOLVE_EINVAL; }
+  if (d.degree == 3 && d.mg_levels == 1) { *why = "degree 3 needs mg_levels >= 2 (its next level is degree 2)"; return TOSOLVE_EINVAL; }
   if (d.prolongation != 0 && d.prolongation != 1) { *why = "prolongation must be 0 or 1"; return TOSOLVE_EINVAL; }
   if (d.prolongation == 1 && d.family == 1) {
     *why = "the serendipity element takes shape-function transfers (prolongation = 0)";
@@ -131,12 +138,12 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (d.max_rhs < 0 || d.max_rhs > 64) { *why = "max_rhs must be in 0..64"; return TOSOLVE_EINVAL; }
   int L = d.mg_levels;
   if (L == 0) {
-    L = 1;
+    L = d.degree == 3 ? 2 : 1;
     while (L < kMaxLevels && divisible(d, L + 1) && coarse_dofs(d, L) > 1500) ++L;
   }
   if (L < 1 || L > kMaxLevels) { *why = "mg_levels must be in 1..8"; return TOSOLVE_EINVAL; }
   if (!divisible(d, L)) { *why = "nx, ny, nz must be divisible by 2^(mg_levels-1)"; return TOSOLVE_EINVAL; }
-  if (d.n_mr * (1 << (L - 1)) > 1024) { *why = "too many levels for n_mr"; return TOSOLVE_EINVAL; }
+  if (d.n_mr * (1 << level_shift(d, L - 1)) > 1024) { *why = "too many levels for n_mr"; return TOSOLVE_EINVAL; }
   P->L = L;
   P->n = d.n_mr;
   P->m = d.n_mr * d.n_mr * d.n_mr;
@@ -155,19 +162,21 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   size_t keB = 0;
   for (int l = 0; l < L; ++l) {
     Plan::Lv& v = P->lv[l];
-    v.ex = d.nx >> l; v.ey = d.ny >> l; v.ez = d.nz >> l;
-    v.Lx = d.degree * v.ex + 1; v.Ly = d.degree * v.ey + 1; v.Lz = d.degree * v.ez + 1;
+    const int sh = level_shift(d, l), kl = level_degree(d, l);
+    v.ex = d.nx >> sh; v.ey = d.ny >> sh; v.ez = d.nz >> sh;
+    v.Lx = kl * v.ex + 1; v.Ly = kl * v.ey + 1; v.Lz = kl * v.ez + 1;
     v.nn = (long)v.Lx * v.Ly * v.Lz;
     v.ndof = 3 * v.nn;
-    v.nsub = d.n_mr << l;
+    v.nsub = d.n_mr << sh;
     const bool coarsest = l == L - 1;
-    if (d.degree == 2) {  // element matrices instead of stencils
+    if (d.degree >= 2) {  // element matrices instead of stencils
       const size_t E = (size_t)v.ex * v.ey * v.ez;
+      const size_t dd = kl == 3 ? (size_t)kDD3 : (size_t)kDD2;
       const size_t tsz = (fp32 && !x2) ? 4 : 8;
       v.s64 = v.s32 = false;
       B += v.ndof + v.ndof * 8 + 4 * v.ndof * tsz;  // mask, dinv64, b v r z
       if (fp32) B += v.ndof * 4;
-      B += coarsest ? E * kDD2 * 8 : E * kDD2 * (8 + (fp32 ? 4 : 0));
+      B += coarsest ? E * dd * 8 : E * dd * (8 + (fp32 ? 4 : 0));
       if (l > 0) B += E * kNM2 * 8;
       continue;
     }
@@ -188,6 +197,9 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     keB += (size_t)c.ex * c.ey * c.ez * (kSym + 27) * 8;  // coarsest level's own
     if (d.degree == 2)  // apply results + tables instead of the slab scratch
       keB = (size_t)ex[0] * ey[0] * ez[0] * kD2 * 8 + ((size_t)P->m + kNM2) * kDD2 * 8;
+    if (d.degree == 3)  // and the gradients the cubic tables are built from
+      keB = (size_t)ex[0] * ey[0] * ez[0] * kD3 * 8 + ((size_t)P->m * kDD3 + (size_t)kNM2 * kDD2) * 8 +
+            (size_t)P->m * 64 * 64 * 3 * 8;
   }
   P->nc = P->lv[L - 1].ndof;
   if (P->nc > kMaxCoarse) { *why = "coarsest level too large for the dense solve: add levels"; return TOSOLVE_EINVAL; }
@@ -238,7 +250,7 @@ void free_all(tosolve_s* h) {
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
-  F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab);
+  F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab); F(h->ptab3);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv); F(h->Pq);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
@@ -369,6 +381,27 @@ tosolve_status tosolve_footprint(const tosolve_desc* desc, size_t* bytes) {
   return TOSOLVE_OK;
 }
 
+// Degree-2 shape function a (lattice position a % 3, a / 3 % 3, a / 9) at
+// reference point x: the tensor-product Lagrange basis (family 0) or the
+// 20-node serendipity basis (family 1; zero at face and element centres).
+static double quad_shape(int family, int a, const double x[3]) {
+  const int c[3] = {a % 3 - 1, (a / 3) % 3 - 1, a / 9 - 1};
+  if (family == 0) {
+    double v = 1.0;
+    for (int q = 0; q < 3; ++q)
+      v *= c[q] == -1 ? 0.5 * x[q] * (x[q] - 1.0) : (c[q] == 0 ? 1.0 - x[q] * x[q] : 0.5 * x[q] * (x[q] + 1.0));
+    return v;
+  }
+  const int nmid = (c[0] == 0) + (c[1] == 0) + (c[2] == 0);
+  if (nmid >= 2) return 0.0;
+  if (nmid == 0)
+    return (1.0 + x[0] * c[0]) * (1.0 + x[1] * c[1]) * (1.0 + x[2] * c[2]) *
+           (x[0] * c[0] + x[1] * c[1] + x[2] * c[2] - 2.0) / 8.0;
+  double v = 0.25;
+  for (int q = 0; q < 3; ++q) v *= c[q] == 0 ? 1.0 - x[q] * x[q] : 1.0 + x[q] * c[q];
+  return v;
+}
+
 static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_host,
                                   const uint8_t* elem_q1, void* cuda_stream, tosolve_t* out) {
   if (out == nullptr) { g_err = "out is NULL"; return TOSOLVE_EINVAL; }
@@ -447,14 +480,15 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       if (slv[nd]) mask[3 * nd] = mask[3 * nd + 1] = mask[3 * nd + 2] = 1;
   }
   // serendipity: no node at face and element centres, held at 0 on every level
-  auto hold_absent = [&](const Plan::Lv& v, std::vector<uint8_t>& m) {
+  // (degree k lattice: two or three coordinates inside an element edge)
+  auto hold_absent = [&](const Plan::Lv& v, int k, std::vector<uint8_t>& m) {
     if (h->d.family != 1) return;
     for (long nd = 0; nd < v.nn; ++nd) {
       const long i = nd % v.Lx, j = (nd / v.Lx) % v.Ly, l = nd / ((long)v.Lx * v.Ly);
-      if ((i & 1) + (j & 1) + (l & 1) >= 2) m[3 * nd] = m[3 * nd + 1] = m[3 * nd + 2] = 1;
+      if ((i % k != 0) + (j % k != 0) + (l % k != 0) >= 2) m[3 * nd] = m[3 * nd + 1] = m[3 * nd + 2] = 1;
     }
   };
-  hold_absent(P.lv[0], mask);
+  hold_absent(P.lv[0], level_degree(h->d, 0), mask);
   h->free_dofs = 0;
   for (uint8_t m : mask) h->free_dofs += m == 0;
   h->free_base = h->free_dofs;
@@ -474,7 +508,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     L.Lx = v.Lx; L.Ly = v.Ly; L.Lz = v.Lz;
     L.nn = (int)v.nn; L.ndof = (int)v.ndof;
     L.nsub = v.nsub;
-    L.h = (double)(1 << l);
+    L.h = (double)(1 << level_shift(h->d, l));
     L.op64 = !fp32 || l == P.L - 1;
     CKC(dalloc(h, &L.mask, v.ndof));
     CKC(cudaMemcpyAsync(L.mask, mask.data(), v.ndof, cudaMemcpyHostToDevice, st));
@@ -493,13 +527,14 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       CKC(dalloc(h, &L.dinv32, v.ndof));
     }
     if (tf32 && l == 0) CKC(dalloc(h, &L.dinv32, v.ndof));
-    L.k = h->d.degree;
-    if (L.k == 2) {  // element matrices; the coarsest level's go to Kec
+    L.k = level_degree(h->d, l);
+    if (L.k >= 2) {  // element matrices; the coarsest level's go to Kec
       const size_t E = (size_t)v.ex * v.ey * v.ez;
+      const size_t dd = L.k == 3 ? (size_t)kDD3 : (size_t)kDD2;
       CKC(dalloc(h, &L.dinv64, v.ndof));
       if (fp32) CKC(dalloc(h, &L.dinv32, v.ndof));
-      if (l + 1 < P.L || l == 0) CKC(dalloc(h, &L.K64, E * kDD2));  // level 0: the CG's K
-      if (l + 1 < P.L && fp32) CKC(dalloc(h, &L.K32, E * kDD2));
+      if (l + 1 < P.L || l == 0) CKC(dalloc(h, &L.K64, E * dd));  // level 0: the CG's K
+      if (l + 1 < P.L && fp32) CKC(dalloc(h, &L.K32, E * dd));
     }
     const size_t tsz = vt_of(h) == kVtF32 ? 4 : 8;
     void** vecs[4] = {&L.b, &L.v, &L.r, &L.z};
@@ -509,7 +544,36 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       CKC(cudaMemsetAsync(p, 0, v.ndof * tsz, st));
       *pv = p;
     }
-    if (l + 1 < P.L) {  // coarse DOF fixed iff the coincident fine DOF is fixed
+    if (l + 1 < P.L && L.k == 3) {
+      // degree 3 -> 2 on the same elements: a quadratic DOF is fixed iff
+      // every cubic DOF of that component at its place is fixed (per axis a
+      // vertex coordinate 2I meets 3I, a midpoint 2I + 1 meets 3I + 1 and
+      // 3I + 2 inside the same edge)
+      const Plan::Lv& c = P.lv[l + 1];
+      std::vector<uint8_t> cm(c.ndof);
+      auto span = [](int I, int& a, int& b) {
+        if (I % 2 == 0) { a = b = 3 * I / 2; } else { a = 3 * (I - 1) / 2 + 1; b = a + 1; }
+      };
+      for (int K = 0; K < c.Lz; ++K)
+        for (int J = 0; J < c.Ly; ++J)
+          for (int I = 0; I < c.Lx; ++I) {
+            int i0, i1, j0, j1, k0, k1;
+            span(I, i0, i1);
+            span(J, j0, j1);
+            span(K, k0, k1);
+            const long cn = I + (long)c.Lx * (J + (long)c.Ly * K);
+            for (int q = 0; q < 3; ++q) {
+              bool all = true;
+              for (int kk = k0; kk <= k1; ++kk)
+                for (int jj = j0; jj <= j1; ++jj)
+                  for (int ii = i0; ii <= i1; ++ii)
+                    all = all && mask[3 * (ii + (long)v.Lx * (jj + (long)v.Ly * kk)) + q] != 0;
+              cm[3 * cn + q] = all ? 1 : 0;
+            }
+          }
+      hold_absent(c, 2, cm);
+      mask.swap(cm);
+    } else if (l + 1 < P.L) {  // coarse DOF fixed iff the coincident fine DOF is fixed
       const Plan::Lv& c = P.lv[l + 1];
       std::vector<uint8_t> cm(c.ndof);
       for (int K = 0; K < c.Lz; ++K)
@@ -519,15 +583,40 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
             const long fn = 2 * I + (long)v.Lx * (2 * J + (long)v.Ly * 2 * K);
             for (int q = 0; q < 3; ++q) cm[3 * cn + q] = mask[3 * fn + q];
           }
-      hold_absent(c, cm);
+      hold_absent(c, 2, cm);
       mask.swap(cm);
     }
   }
   // tables (Sec. 3.3: the subcell matrices are computed once)
-  if (h->d.degree == 2) {
-    CKC(dalloc(h, &h->tab64, (size_t)P.m * kDD2));
+  if (h->d.degree >= 2) {
+    if (h->d.degree == 3) {
+      double* gscr = nullptr;
+      CKC(dalloc(h, &h->tab64, (size_t)P.m * kDD3));
+      CKC(dalloc(h, &gscr, (size_t)P.m * 64 * 64 * 3));
+      launch_q3_subcell_table(P.n, h->d.nu, 1.0, h->d.family, gscr, h->tab64, st);
+      CKC(cudaStreamSynchronize(st));
+      pool_free(gscr, st);
+      // degree 3 -> 2 transfer: the 27 quadratic shape functions (Lagrange or
+      // serendipity) at the 64 cubic nodes of an element
+      std::vector<float> W(27 * 64, 0.f);
+      for (int a = 0; a < 27; ++a) {
+        const int c[3] = {a % 3 - 1, (a / 3) % 3 - 1, a / 9 - 1};
+        const int nmid = (c[0] == 0) + (c[1] == 0) + (c[2] == 0);
+        if (h->d.family == 1 && nmid >= 2) continue;
+        for (int f = 0; f < 64; ++f) {
+          const double x[3] = {-1.0 + 2.0 * (f % 4) / 3.0, -1.0 + 2.0 * ((f / 4) % 4) / 3.0,
+                               -1.0 + 2.0 * (f / 16) / 3.0};
+          W[a * 64 + f] = (float)quad_shape(h->d.family, a, x);
+        }
+      }
+      CKC(dalloc(h, &h->ptab3, W.size()));
+      CKC(cudaMemcpyAsync(h->ptab3, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+      h->lv[1].ptab = h->ptab3;
+    } else {
+      CKC(dalloc(h, &h->tab64, (size_t)P.m * kDD2));
+      launch_q2_subcell_table(P.n, h->d.nu, 1.0, h->d.family, h->tab64, st);
+    }
     CKC(dalloc(h, &h->cmom64, (size_t)kNM2 * kDD2));
-    launch_q2_subcell_table(P.n, h->d.nu, 1.0, h->d.family, h->tab64, st);
     launch_q2_moment_basis(h->d.nu, h->d.family, h->cmom64, st);
     if (h->d.family == 1 || h->d.prolongation == 0) {
       // shape-function transfers: the 27 coarse shape functions at the 125
@@ -559,10 +648,11 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       }
       CKC(dalloc(h, &h->ptab, W.size()));
       CKC(cudaMemcpyAsync(h->ptab, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-      for (int l = 1; l < P.L; ++l) h->lv[l].ptab = h->ptab;
+      // into every degree-2 level that halves the mesh of the level above
+      for (int l = (h->d.degree == 3 ? 2 : 1); l < P.L; ++l) h->lv[l].ptab = h->ptab;
     }
     const Plan::Lv& v0 = P.lv[0];
-    CKC(dalloc(h, &h->Yq, (size_t)v0.ex * v0.ey * v0.ez * kD2));
+    CKC(dalloc(h, &h->Yq, (size_t)v0.ex * v0.ey * v0.ez * (h->d.degree == 3 ? kD3 : kD2)));
     for (int l = 0; l < P.L; ++l) h->lv[l].Y = h->Yq;
   } else {
     CKC(dalloc(h, &h->tab64, (size_t)P.m * 576));
@@ -633,7 +723,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     for (int l = 0; l < P.L; ++l) { ex[l] = P.lv[l].ex; ey[l] = P.lv[l].ey; ez[l] = P.lv[l].ez; }
     const Plan::Lv& c = P.lv[P.L - 1];
     const size_t Ec = (size_t)c.ex * c.ey * c.ez;
-    if (h->d.degree == 2) {
+    if (h->d.degree >= 2) {
       size_t em = 1;
       for (int l = 1; l + 1 < P.L; ++l) em = std::max(em, (size_t)ex[l] * ey[l] * ez[l]);
       CKC(dalloc(h, &h->Mq, em * kNM2));
@@ -757,7 +847,7 @@ static tosolve_status refresh(tosolve_t h) {
     cst = h->st2;
   }
   Level& C = h->lv[L - 1];
-  if (d.degree == 2) {
+  if (d.degree >= 2) {
     const double* Kc = h->Kec;
     if (L > 1) {
       launch_q2_coarse_elem(C, h->w, h->Dx, h->Dy, h->cmom64, h->Mqc, h->Kec, cst);
@@ -780,7 +870,7 @@ static tosolve_status refresh(tosolve_t h) {
         launch_q2_coarse_elem(Lv, h->w, h->Dx, h->Dy, h->cmom64, h->Mq, Lv.K64, st);
       launch_q2_dinv(true, Lv, Lv.K64, Lv.dinv64, st);
       if (Lv.K32) {
-        launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * kDD2, Lv.K64, Lv.K32, st);
+        launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * (Lv.k == 3 ? kDD3 : kDD2), Lv.K64, Lv.K32, st);
         launch_q2_dinv(false, Lv, Lv.K64, Lv.dinv32, st);
       }
     }
@@ -1158,7 +1248,7 @@ tosolve_status tosolve_compliance_grad(tosolve_t h, const double* u_dev, const d
     CK(cudaMemcpyAsync(&h->hs->c, &h->ds->c, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c_host[r] = h->hs->c;
-    if (want_grad && d.degree == 2)
+    if (want_grad && d.degree >= 2)
       launch_q2_energy_grad(h->lv[0], d.n_mr, u_dev + r * nd, h->tab64, h->rho, d.penal, d.E0 - d.Emin,
                             h->Dx, h->Dy, r == 0, g, h->lv[0].sms, st);
     else if (want_grad)
@@ -1217,7 +1307,7 @@ tosolve_status tosolve_level_dims(tosolve_t h, int level, int* dims) {
 
 tosolve_status tosolve_subcell_table(tosolve_t h, double* table_dev) {
   if (h == nullptr || table_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
-  const size_t dd = h->d.degree == 2 ? (size_t)kDD2 : 576;
+  const size_t dd = h->d.degree == 3 ? (size_t)kDD3 : (h->d.degree == 2 ? (size_t)kDD2 : 576);
   CK(cudaMemcpyAsync(table_dev, h->tab64, (size_t)h->m * dd * 8, cudaMemcpyDeviceToDevice, h->st));
   return TOSOLVE_OK;
 }
@@ -1235,7 +1325,7 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
   if (level < 0 || level >= h->L) return set_err(h, TOSOLVE_EINVAL, "level out of range");
   if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");
   const Level& L = h->lv[level];
-  if (L.k == 2 && (precision == 0 || precision == 1 || precision == 3)) {
+  if (L.k >= 2 && (precision == 0 || precision == 1 || precision == 3)) {
     const bool ok = precision == 0 ? L.K64 != nullptr : L.K32 != nullptr;
     const bool vt_ok = precision == 0 || (precision == 1) == (vt_of(h) == kVtF32);
     if (!ok || !vt_ok) return set_err(h, TOSOLVE_EINVAL, "this level has no operator in that precision");

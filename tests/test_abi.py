@@ -76,7 +76,9 @@ def test_footprint_and_validation_without_gpu(lib):
     bad = [
         T.make_desc(24, 12, 12, mg_levels=5),      # 12 not divisible by 16
         T.make_desc(0, 12, 12),                    # empty mesh
-        T.make_desc(24, 12, 12, degree=3),         # degree not built
+        T.make_desc(24, 12, 12, degree=4),         # degree not built
+        T.make_desc(24, 12, 12, degree=3, mg_levels=1),  # cubic needs its degree-2 level
+        T.make_desc(24, 12, 12, degree=1, family=1),     # no linear serendipity element
         T.make_desc(24, 12, 12, nu=0.5),           # incompressible
         T.make_desc(24, 12, 12, Emin=0.0),         # singular void
         T.make_desc(24, 12, 12, cycle_gamma=2),    # W-cycle not built
@@ -113,7 +115,7 @@ def test_server_validation_without_gpu(lib):
             T.tosolve_server_add_design(s, 7, d, np.zeros(nd, np.uint8), np.zeros((1, nd)), 1)
         assert e.value.status == T.EINVAL
         with pytest.raises(T.TosolveError) as e:  # invalid descriptor
-            T.tosolve_server_add_design(s, 8, T.make_desc(4, 2, 2, degree=3), np.zeros(nd, np.uint8),
+            T.tosolve_server_add_design(s, 8, T.make_desc(4, 2, 2, degree=4), np.zeros(nd, np.uint8),
                                         np.zeros((1, nd)), 1)
         assert e.value.status == T.EINVAL
         with pytest.raises(T.TosolveError) as e:  # unknown design
