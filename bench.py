@@ -657,16 +657,19 @@ def run_fix(args):
     print(json.dumps(line), flush=True)
 
 
-SERENDIPITY = dict(name="cantilever_q2_vs_s2_48x24x24_n2_density_96x48x48", nx=48, ny=24, nz=24, n_mr=2,
-                   rmin=1.5, rtol=1e-8)
+ELEMENTS = dict(name="elements_cantilever_96x16x16_n4_density_384x64x64", nx=96, ny=16, nz=16, n_mr=4,
+                rmin=0.6, rtol=1e-8)
 
 
-def run_serendipity(args):
-    """Sec. 2.1 element families on one mesh: the degree-2 cantilever
-    (48x24x24 elements, n = 2, the C1 density grid and smooth design) with
-    27-node Lagrange and with 20-node serendipity elements.  Cold solves
-    (u0 = 0) to 1e-8, CUDA events, L2 flushed between solves; solved
-    unknowns per second for each family and preconditioner precision."""
+def run_elements(args):
+    """Sec. 2.1 / 7.5 element families on one mesh: the cantilever with
+    96x16x16 displacement elements and n = 4 density cells per edge (the
+    displacement and density meshes of the paper's higher-order test, with
+    its filter radius 0.6), smooth design, solved with trilinear (L1),
+    quadratic Lagrange (L2) and serendipity (S2), cubic Lagrange (L3) and
+    serendipity (S3) elements.  Cold solves (u0 = 0) to 1e-8, CUDA events,
+    L2 flushed between solves; unknowns, PCG iterations, time per solve and
+    solved unknowns per second, FP32X2 and FP64 preconditioners."""
     import torch
 
     import workloads
@@ -676,24 +679,33 @@ def run_serendipity(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    S = SERENDIPITY
-    base = workloads.cantilever(S["nx"], S["ny"], S["nz"], degree=2, n_mr=S["n_mr"], rmin=S["rmin"],
-                                density="smooth", seed=0)
+    S = ELEMENTS
     rows = {}
     sampler = ClockSampler(0)
     sampler.start()
-    for fam, p in (("lagrange", base), ("serendipity", workloads.with_serendipity(base))):
+    for label, k, fam in (("L1", 1, "lagrange"), ("L2", 2, "lagrange"), ("S2", 2, "serendipity"),
+                          ("L3", 3, "lagrange"), ("S3", 3, "serendipity")):
+        p = workloads.cantilever(S["nx"], S["ny"], S["nz"], degree=k, n_mr=S["n_mr"], rmin=S["rmin"],
+                                 density="smooth", seed=0)
+        if fam == "serendipity":
+            p = workloads.with_serendipity(p)
         x = torch.tensor(p.x, device=dev)
         f = torch.tensor(p.f, device=dev)
         u = torch.zeros_like(f)
-        for label, prec in (("fp32x2", T.PREC_FP32X2), ("fp64", T.PREC_FP64)):
-            d = T.make_desc(p.nx, p.ny, p.nz, degree=2, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin, nu=p.nu,
+        for plabel, prec in (("fp32x2", T.PREC_FP32X2), ("fp64", T.PREC_FP64)):
+            d = T.make_desc(p.nx, p.ny, p.nz, degree=k, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin, nu=p.nu,
                             penal=p.penal, precision=prec, max_rhs=1,
                             family=T.FAMILY_SERENDIPITY if fam == "serendipity" else T.FAMILY_LAGRANGE)
             s = T.Solver(d, p.mask, stream)
             ms, its = [], []
             with torch.cuda.stream(stream):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
                 T.tosolve_set_densities(s.h, x)
+                e1.record(stream)
+                stream.synchronize()
+                set_ms = e0.elapsed_time(e1)
                 for rep in range(args.warmup + args.steps):
                     u.zero_()
                     flush.zero_()
@@ -710,17 +722,21 @@ def run_serendipity(args):
                 c = T.tosolve_compliance_grad(s.h, u, f, 1)
             nfree = T.tosolve_free_dofs(s.h)
             med = statistics.median(ms)
-            rows[f"{fam}_{label}"] = {"free_dofs": nfree, "ms": med, "iterations": statistics.median(its),
-                                      "dofs_per_s": nfree / (med * 1e-3), "compliance": float(c[0])}
+            rows[f"{label}_{plabel}"] = {"free_dofs": nfree, "ms": med, "set_densities_ms": set_ms,
+                                         "iterations": statistics.median(its),
+                                         "dofs_per_s": nfree / (med * 1e-3), "compliance": float(c[0]),
+                                         "levels": T.tosolve_level_count(s.h)}
             s.close()
+            torch.cuda.empty_cache()
     clocks = sampler.stop()
-    head = rows["serendipity_fp32x2"]
+    head = rows["S3_fp32x2"]
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "value": head["dofs_per_s"], "ms_per_step": head["ms"],
             "config": {"workload": S["name"], "rtol": S["rtol"], "start": "u0 = 0 every solve",
                        "l2": f"flushed between solves ({L2_FLUSH_BYTES >> 20} MiB write)",
-                       "coarse_levels": "degree-2 Lagrange for both families"},
+                       "hierarchy": "degree 3: the degree-2 mesh of the same family on the same elements next, "
+                                    "then degree-2 levels; degree 2: shape-function transfers"},
             "rows": rows, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
@@ -869,7 +885,7 @@ def main():
                     help="mixed-precision variants timed beside FP64 (comma list)")
     ap.add_argument("--workload", default="cantilever",
                     choices=["cantilever", "bridge_q2", "bridge_mixed", "batch64", "serve", "ibeam_fix",
-                             "serendipity"],
+                             "elements"],
                     help="bridge_q2: the degree-2 bridge; batch64: the 64-instance batched "
                          "solve; serve: the serving loop (each its own JSON line)")
     ap.add_argument("--designs", type=int, default=SERVE["designs"])
@@ -891,8 +907,8 @@ def main():
         run_serve(args)
     elif args.workload == "ibeam_fix":
         run_fix(args)
-    elif args.workload == "serendipity":
-        run_serendipity(args)
+    elif args.workload == "elements":
+        run_elements(args)
     else:
         run_gpu(args)
 

@@ -90,7 +90,7 @@ typedef struct {
                           /*   nx, ny, nz divisible by 2^(levels-1))        */
   int precision;          /* tosolve_precision of the preconditioner        */
   double omega;           /* damped-Jacobi factor (0 => 0.5, Sec. 7 intro;  */
-                          /*   0.3 for the serendipity element)             */
+                          /*   0.4 for cubic Lagrange, 0.3 for serendipity) */
   int cycle_gamma;        /* cycles per level: 1 = V-cycle (0 => 1; the     */
                           /*   only value this build accepts)               */
   int max_rhs;            /* load cases per solve call, >= 1 (0 => 1)       */

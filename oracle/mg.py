@@ -26,8 +26,9 @@ Readings taken here (the paper does not say):
     spaces are nested, so the re-discretised coarse operator is then the
     Galerkin product P^T A P (tested);
   * serendipity levels hold their face and element-centre nodes at 0 like
-    supports, and use omega = 0.3 (damped Jacobi with 0.5 diverges on this
-    element: lambda_max(D^-1 A) is about 5.3).
+    supports, and use omega = 0.3 (damped Jacobi with 0.5 diverges on these
+    elements: lambda_max(D^-1 A) is about 5.3 for degree 2, 5.0 for degree
+    3); cubic Lagrange hierarchies use 0.4 (lambda_max about 4.0).
 """
 from __future__ import annotations
 
@@ -245,7 +246,7 @@ def _cubic_levels(self, prob, rho, levels):
         m2 = (m2.astype(bool) | serendipity_absent(lat2, 2)).astype(np.uint8)
     q.mask = m2
     sub = Hierarchy(q, rho, levels - 1)
-    self.omega = 0.3 if family == "serendipity" else 0.5
+    self.omega = 0.3 if family == "serendipity" else 0.4
     w_cells = simp_weights(rho, prob.E0, prob.Emin, prob.penal)
     F = Level()
     F.nx, F.ny, F.nz = prob.nx, prob.ny, prob.nz

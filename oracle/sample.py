@@ -119,6 +119,30 @@ class Sampler:
                     out[q, c] = u[3 * nd + c]
         return out
 
+    def apply_rows_scale(self, x, u, nodes):
+        """(len(nodes), 3): sum_j |K_ij u_j| of the same rows, the scale of
+        their rounding (K u is much smaller than its terms where u is a
+        converged displacement: the rows nearly cancel to the load)."""
+        held = self.p.mask.astype(bool).copy()
+        if self.slv is not None:
+            held |= np.repeat(self.slv, 3)
+        uf = np.abs(np.where(held, 0.0, u))
+        cache = {}
+        out = np.zeros((len(nodes), 3))
+        for q, nd in enumerate(nodes):
+            for (ex, ey, ez) in self.elements_of(nd):
+                Ke, _ = self.elem_matrix(x, ex, ey, ez, cache)
+                en = self._elem_nodes(ex, ey, ez)
+                T = self._T_e(en)
+                Kr = np.abs(T.T @ Ke @ T)
+                dofs = np.array([3 * m + c for m in en for c in range(3)])
+                a = en.index(nd)
+                out[q] += Kr[3 * a: 3 * a + 3] @ uf[dofs]
+            for c in range(3):
+                if held[3 * nd + c]:
+                    out[q, c] = abs(u[3 * nd + c])
+        return out
+
     # ---- gradient ---------------------------------------------------------
     def drho(self, x, u, cell):
         """dc/drho at one density cell for the (expanded) displacement u."""

@@ -68,3 +68,22 @@ def test_gradient_rounding_scale_bounds_the_error():
         r = S.rho(p.x, c)
         exact = -p.penal * r ** (p.penal - 1.0) * (p.E0 - p.Emin) * float(quad)
         assert abs(d - exact) <= 1e-12 * s
+
+
+def test_row_rounding_scale_bounds_the_rows():
+    p = workloads.cantilever(4, 3, 2, degree=2, n_mr=2, rmin=0.7, seed=3)
+    S = sample.Sampler(p)
+    u = np.random.default_rng(4).normal(size=p.ndof)
+    nodes = list(range(0, p.nnodes, 7))
+    y = S.apply_rows(p.x, u, nodes)
+    sc = S.apply_rows_scale(p.x, u, nodes)
+    assert (sc >= np.abs(y) * (1 - 1e-14)).all() and (sc > 0).all()
+    # a displacement with one sign on free DOFs and a diagonal-only check:
+    # the scale of a row is at least its diagonal term
+    m = fe.Model(p)
+    K = m.assemble(m.weights(m.densities(p.x))).tocsr()
+    for q, nd in enumerate(nodes):
+        for c in range(3):
+            d = 3 * nd + c
+            if p.mask[d] == 0:
+                assert sc[q, c] >= abs(K[d, d] * u[d]) * (1 - 1e-14)
