@@ -171,6 +171,22 @@ class Sampler:
         r = self.rho(x, cell)
         return self.p.penal * r ** (self.p.penal - 1.0) * (self.p.E0 - self.p.Emin) * (ue @ np.abs(self.K[i]) @ ue)
 
+    def dx_scale(self, x, u, cell):
+        """Rounding scale of dx: the filter weights times the drho_scale of
+        every density cell in the ball."""
+        cx, cy, cz = cell % self.Dx, (cell // self.Dx) % self.Dy, cell // (self.Dx * self.Dy)
+        total = 0.0
+        for (di, dj, dk), w in zip(self.offs, self.wts):
+            jx, jy, jz = cx + di, cy + dj, cz + dk
+            if not self._in(jx, jy, jz):
+                continue
+            den = 0.0
+            for (ei, ej, ek), w2 in zip(self.offs, self.wts):
+                if self._in(jx + ei, jy + ej, jz + ek):
+                    den += w2
+            total += w / den * self.drho_scale(x, u, self._cell(jx, jy, jz))
+        return total
+
     def dx(self, x, u, cell):
         """dc/dx at one design cell: sum over the ball of w_ji / omega_j * dc/drho_j."""
         cx, cy, cz = cell % self.Dx, (cell // self.Dx) % self.Dy, cell // (self.Dx * self.Dy)
