@@ -94,6 +94,10 @@ struct Level {
   // degree 2: the operator as element matrices (81 x 81 each, full)
   double* K64 = nullptr;
   float* K32 = nullptr;
+  // serendipity levels: the compact matrices of the element's own DOFs
+  // (60 x 60 for degree 2, 96 x 96 for degree 3), read by the apply
+  double* Kc64 = nullptr;
+  float* Kc32 = nullptr;
   void* Y = nullptr;  // per-element results of an apply (shared scratch)
   uint8_t* mask = nullptr;
   int* tl = nullptr;    // tile order in force (LevelView::tl), or null: index order
@@ -240,6 +244,8 @@ void launch_q2_moment_basis(double nu, int family, double* cmom, cudaStream_t st
 // element): grad_scratch holds n^3 * 64 * 64 * 3 doubles.
 void launch_q3_subcell_table(int n, double nu, double h, int family, double* grad_scratch, double* tab,
                              cudaStream_t st);
+// Serendipity levels: Kc64 / Kc32 from K64 (after every refresh of K64).
+void launch_ser_compact(const Level& L, cudaStream_t st);
 // Degree-2 levels with shape-function transfers (always for the serendipity
 // element): W = the 27 x 125 table of coarse shape values at the fine
 // lattice points of a coarse element (device, FP32).

@@ -660,6 +660,80 @@ __global__ void __launch_bounds__(Deg<K>::TB) k_q2_apply(int ex, int ey, long E,
   }
 }
 
+// Serendipity elements: only the 20 (degree 2) or 32 (degree 3) lattice
+// positions with at most one coordinate inside an edge carry a node.  The
+// element apply reads the compact Dp x Dp matrix of those DOFs (Dp = 60 or
+// 96 instead of 81 or 192), formed from the full one after each refresh.
+template <int K>
+struct Ser {
+  static constexpr int NP = K == 2 ? 20 : 32;
+  static constexpr int DP = 3 * NP;
+  static constexpr int TB = (DP + 31) / 32 * 32;
+};
+
+// Lattice-local position of the p-th serendipity node (in lattice order).
+template <int K>
+__device__ __forceinline__ int ser_pos(int p) {
+  constexpr int NA = K + 1;
+  int cnt = 0;
+  for (int a = 0; a < NA * NA * NA; ++a) {
+    const int ix = a % NA, iy = (a / NA) % NA, iz = a / (NA * NA);
+    const int inner = (ix % K != 0) + (iy % K != 0) + (iz % K != 0);
+    if (inner <= 1) {
+      if (cnt == p) return a;
+      ++cnt;
+    }
+  }
+  return 0;
+}
+
+template <int K, typename T>
+__global__ void k_ser_compact(long E, const double* __restrict__ Kf, T* __restrict__ Kc) {
+  constexpr int D = Deg<K>::D, DP = Ser<K>::DP;
+  __shared__ int pos[Ser<K>::NP];
+  for (int t = threadIdx.x; t < Ser<K>::NP; t += blockDim.x) pos[t] = ser_pos<K>(t);
+  __syncthreads();
+  const long total = E * (long)DP * DP;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long e = t / ((long)DP * DP);
+    const int ent = (int)(t % ((long)DP * DP));
+    const int r = ent / DP, c = ent % DP;
+    const int R = 3 * pos[r / 3] + r % 3, C = 3 * pos[c / 3] + c % 3;
+    Kc[t] = (T)Kf[e * (size_t)D * D + (size_t)R * D + C];
+  }
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(Ser<K>::TB) k_ser_apply(int ex, int ey, long E, int Lx, int Ly,
+                                                          const op_t<T>* __restrict__ Kc,
+                                                          const uint8_t* __restrict__ mask,
+                                                          const T* __restrict__ u, T* __restrict__ Y) {
+  constexpr int D = Deg<K>::D, DP = Ser<K>::DP;
+  __shared__ T ue[DP];
+  __shared__ int pos[Ser<K>::NP];
+  for (int t = threadIdx.x; t < Ser<K>::NP; t += blockDim.x) pos[t] = ser_pos<K>(t);
+  __syncthreads();
+  for (long e = blockIdx.x; e < E; e += gridDim.x) {
+    const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+    bool free_dof = false;
+    if (threadIdx.x < DP) {
+      const int a = pos[threadIdx.x / 3], c = threadIdx.x % 3;
+      const long d = 3 * elem_node_k<K>(exi, eyi, ezi, a, Lx, Ly) + c;
+      free_dof = mask[d] == 0;
+      ue[threadIdx.x] = free_dof ? u[d] : T(0);
+    }
+    if (!__syncthreads_or(free_dof)) continue;  // block-uniform
+    if (threadIdx.x < DP) {
+      const op_t<T>* Kcol = Kc + e * (size_t)DP * DP + threadIdx.x;  // symmetric: column = row
+      Sum<T> acc;
+#pragma unroll 4
+      for (int b = 0; b < DP; ++b) acc.add(Kcol[(size_t)b * DP], ue[b]);
+      Y[e * D + 3 * pos[threadIdx.x / 3] + threadIdx.x % 3] = acc.value();
+    }
+    __syncthreads();
+  }
+}
+
 // y_n = sum of Y_e over the elements containing node n (fixed order), then
 //   mode 0: out = b - y            (residual after the first smoothing)
 //   mode 1: out = v + omega D^-1 (b - y)   (post-smoothing)
@@ -981,6 +1055,20 @@ void launch_q2_elem(const Level& L, int n, const double* w, int Dx, int Dy, cons
     k_q2_elem<2><<<(int)((E + kEB - 1) / kEB), 256, sm, st>>>(L.ex, L.ey, E, n, w, Dx, Dy, tab, Ke);
 }
 
+void launch_ser_compact(const Level& L, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * L.ez;
+  const int DP = L.k == 3 ? Ser<3>::DP : Ser<2>::DP;
+  const int g = grid_for2(E * DP * DP);
+  if (L.Kc64) {
+    if (L.k == 3) k_ser_compact<3, double><<<g, 256, 0, st>>>(E, L.K64, L.Kc64);
+    else k_ser_compact<2, double><<<g, 256, 0, st>>>(E, L.K64, L.Kc64);
+  }
+  if (L.Kc32) {  // from the FP64 matrix, rounded once
+    if (L.k == 3) k_ser_compact<3, float><<<g, 256, 0, st>>>(E, L.K64, L.Kc32);
+    else k_ser_compact<2, float><<<g, 256, 0, st>>>(E, L.K64, L.Kc32);
+  }
+}
+
 void launch_q3_subcell_table(int n, double nu, double h, int family, double* grad_scratch, double* tab,
                              cudaStream_t st) {
   const long ng = (long)n * n * n * 64 * 64;
@@ -1029,8 +1117,28 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
   if (ga > E) ga = E;
   if (ga < 1) ga = 1;
   const int gg = grid_for2(L.nn);
+  // serendipity levels apply their compact matrices
+  const void* Kc = Ke == (const void*)L.K64 ? (const void*)L.Kc64
+                   : (Ke == (const void*)L.K32 ? (const void*)L.Kc32 : nullptr);
   auto run = [&](auto tag) {
     using T = decltype(tag);
+    if (Kc != nullptr) {
+      if (L.k == 3)
+        k_ser_apply<3, T><<<(int)ga, Ser<3>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Kc, L.mask,
+                                                           (const T*)v, (T*)Y);
+      else
+        k_ser_apply<2, T><<<(int)ga, Ser<2>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Kc, L.mask,
+                                                           (const T*)v, (T*)Y);
+      if (L.k == 3)
+        k_q2_gather<3, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
+                                              (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
+                                              (T*)out);
+      else
+        k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
+                                              (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
+                                              (T*)out);
+      return;
+    }
     if (L.k == 3) {
       k_q2_apply<3, T><<<(int)ga, Deg<3>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
                                                         (const T*)v, (T*)Y);

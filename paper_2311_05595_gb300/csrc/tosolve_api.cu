@@ -177,6 +177,10 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
       B += v.ndof + v.ndof * 8 + 4 * v.ndof * tsz;  // mask, dinv64, b v r z
       if (fp32) B += v.ndof * 4;
       B += coarsest ? E * dd * 8 : E * dd * (8 + (fp32 ? 4 : 0));
+      if (d.family == 1 && (!coarsest || l == 0)) {  // compact copies of the serendipity levels
+        const size_t dp = kl == 3 ? 96 : 60;
+        B += E * dp * dp * (8 + (fp32 && !coarsest ? 4 : 0));
+      }
       if (l > 0) B += E * kNM2 * 8;
       continue;
     }
@@ -246,7 +250,7 @@ void free_all(tosolve_s* h) {
   for (int l = 0; l < kMaxLevels; ++l) {
     Level& L = h->lv[l];
     F(L.mask); F(L.S64); F(L.S32); F(L.dinv64); F(L.dinv32); F(L.b); F(L.v); F(L.r); F(L.z);
-    F(L.K64); F(L.K32); F(L.tl_buf); F(L.tcnt_buf);
+    F(L.K64); F(L.K32); F(L.Kc64); F(L.Kc32); F(L.tl_buf); F(L.tcnt_buf);
   }
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
@@ -536,6 +540,11 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       if (fp32) CKC(dalloc(h, &L.dinv32, v.ndof));
       if (l + 1 < P.L || l == 0) CKC(dalloc(h, &L.K64, E * dd));  // level 0: the CG's K
       if (l + 1 < P.L && fp32) CKC(dalloc(h, &L.K32, E * dd));
+      if (h->d.family == 1) {  // compact copies for the apply
+        const size_t dp = L.k == 3 ? 96 : 60;
+        if (L.K64) CKC(dalloc(h, &L.Kc64, E * dp * dp));
+        if (L.K32) CKC(dalloc(h, &L.Kc32, E * dp * dp));
+      }
     }
     const size_t tsz = vt_of(h) == kVtF32 ? 4 : 8;
     void** vecs[4] = {&L.b, &L.v, &L.r, &L.z};
@@ -874,6 +883,7 @@ static tosolve_status refresh(tosolve_t h) {
         launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * (Lv.k == 3 ? kDD3 : kDD2), Lv.K64, Lv.K32, st);
         launch_q2_dinv(false, Lv, Lv.K64, Lv.dinv32, st);
       }
+      if (Lv.Kc64 || Lv.Kc32) launch_ser_compact(Lv, st);
     }
     if (L > 1) {
       CK(cudaEventRecord(h->evj, h->st2));
