@@ -15,6 +15,7 @@
 // 2 ez + az), DOF 3a + c.  Sec. 2.1 (Lagrange elements), Sec. 3.3
 // (Eq. matrixK_mr: K^(e) = sum_i w_i K^(e_i) over the element's n^3
 // subcells), Sec. 2.3 (linear interpolation between node lattices).
+#include <mutex>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -1160,11 +1161,10 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
 
 void launch_q2_constrain(const Level& L, const uint8_t* slv, double* Ke, int sms, cudaStream_t st) {
   const long E = (long)L.ex * L.ey * L.ez;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;  // handles may be created from several threads
+  std::call_once(attr, [] {
     cudaFuncSetAttribute(k_q2_constrain, cudaFuncAttributeMaxDynamicSharedMemorySize, kDD * 8);
-    attr = true;
-  }
+  });
   long g = (long)sms * 4;
   if (g > E) g = E;
   k_q2_constrain<<<(int)g, 256, kDD * 8, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, slv, Ke);
