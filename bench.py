@@ -39,10 +39,16 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DFMA rate at ~1.96 GHz) x 2 flop x 152 SMs x 2070 MHz max SM clock.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # DRAM traffic per launch of the dominant kernel from an ncu capture of the
-# same workload (ncu --set full of the diagnostic FP64 apply timed below, the
-# same tile kernel body as the CG's q = K p), valid while the kernel source
-# is unchanged (keyed by the source hash).
-NCU_TRAFFIC = {("k_apply_diag<double>", "740f79607230"): 60.348928e6 + 0.090112e6}
+# same workload (dram__bytes_read.sum + dram__bytes_write.sum of the FP64
+# apply timed below; for the element form, the element product and the node
+# gather together), valid while the kernel source is unchanged (keyed by the
+# kernel, the source hash and the workload).
+NCU_TRAFFIC = {
+    ("k_apply_diag<double>", "740f79607230", "cantilever_mr_96x48x48_q1_48x24x24_n2"):
+        60.348928e6 + 0.090112e6,
+    ("k_q2_apply<double>", "a9e36f7df2c6", "bridge_q2_64x32x32_n3_density_192x96x96"):
+        3500955648 + 44271872 + 44121088 + 1024,
+}
 
 
 # Adaptive-degree bridge, all elements triquadratic: displacement 64x32x32
@@ -392,13 +398,13 @@ def run_gpu(args):
         flops = 18.0 * pairs
         bytes_alg = nn * (243 * 8 + 3 * 8 * 2)
         kernel = "k_apply_diag<double> (FP64 27-point block stencil, K u)"
-        traffic = NCU_TRAFFIC.get(("k_apply_diag<double>", source_hash("k_solve.cu")))
+        traffic = NCU_TRAFFIC.get(("k_apply_diag<double>", source_hash("k_solve.cu"), spec["name"]))
     else:  # element form: 81x81 FP64 product per element, then the node gather
         E = p.nx * p.ny * p.nz
         flops = 2.0 * 81 * 81 * E
         bytes_alg = E * (81 * 81 * 8 + 81 * 8 * 2) + nn * 3 * 8 * 2
         kernel = "k_q2_apply<double> + k_q2_gather<double> (FP64 element matrices, K u)"
-        traffic = NCU_TRAFFIC.get(("k_q2_apply<double>", source_hash("k_q2.cu")))
+        traffic = NCU_TRAFFIC.get(("k_q2_apply<double>", source_hash("k_q2.cu"), spec["name"]))
     achieved = flops / (us * 1e-6) / 1e12
 
     its = [i[0] for i in mixed["infos"]]
