@@ -4,8 +4,8 @@ MG-PCG, on the multiresolution cantilever (density 96x48x48, Q1 48x24x24,
 n_mr = 2, smooth design field, filter radius 1.5, 4-level V-cycle).
 
 One step = one pass of the whole hot path on device-resident inputs:
-set_densities (filter, SIMP weights, every level's operator, coarse
-Cholesky), solve from u0 = 0 to ||f - K u|| / ||f|| <= 1e-8, compliance and
+set_densities (filter, SIMP weights, every level's operator, the coarse
+operator's inverse), solve from u0 = 0 to ||f - K u|| / ||f|| <= 1e-8, compliance and
 design gradient.  value = free DOFs / step time (all ranks' DOFs over the
 slowest rank's time; one independent replica per GPU under torchrun).
 

@@ -59,8 +59,8 @@ typedef enum {
 } tosolve_status;
 
 /* Precision of the multigrid preconditioner (the outer CG, its dot
- * products, the true residual, the coarse Cholesky factor, the compliance
- * and the gradient are always FP64). */
+ * products, the true residual, the coarse inverse, the compliance and the
+ * gradient are always FP64). */
 typedef enum {
   TOSOLVE_PREC_FP64 = 0, /* plain FP64 MG-PCG                                */
   TOSOLVE_PREC_FP32 = 1, /* FP32 V-cycle operators and vectors, FP32 accum.  */
@@ -235,8 +235,10 @@ tosolve_status tosolve_footprint(const tosolve_desc* desc, size_t* bytes);
 /* New design: x_dev (design grid, FP64) -> rho = H x (Sec. 2.2 Eq.
  * filter_weights, Sec. 3.2 Eq. projdsgn), SIMP weights w = Emin +
  * rho^p (E0 - Emin), and the multigrid refresh of Sec. 7.2: every level's
- * operator from the densities, the Jacobi diagonals and the dense Cholesky
- * factor (with its inverse) of the coarsest operator.  Asynchronous.
+ * operator from the densities, the Jacobi diagonals and the explicit FP64
+ * inverse of the coarsest operator (the direct coarse solve; formed by
+ * blocked symmetric Gauss-Jordan sweeps, whose pivots are those of a
+ * Cholesky factorisation).  Asynchronous.
  * Errors: EINVAL, ECUDA. */
 tosolve_status tosolve_set_densities(tosolve_t h, const double* x_dev);
 

@@ -30,7 +30,7 @@ constexpr int kMaxPart = 608;  // partial sums per reduction (4 blocks per SM)
 constexpr int kMaxLevels = 8;
 constexpr int kEdofQ1 = 24;    // DOFs of a trilinear hexahedron
 constexpr int kSym = 300;      // entries of a 24x24 symmetric upper triangle
-constexpr int kNB = 32;        // block size of the coarse Cholesky
+constexpr int kNB = 32;        // largest pivot block of the coarse sweeps
 constexpr int kTile = 32;      // output tile of the coarse inverse product
 constexpr int kMaxCoarse = 4096;  // largest coarse system (DOFs)
 constexpr int kTN = 32;        // nodes per operator tile
@@ -74,7 +74,7 @@ struct DevState {
   int maxit;
   int status;      // 0 ok, TOSOLVE_EBREAKDOWN on breakdown
   int converged;
-  int coarse_status;  // non-zero if the coarse Cholesky met a bad pivot
+  int coarse_status;  // non-zero if the coarse sweeps met a non-positive pivot
   int tc_status;      // non-zero if a tensor-core tile wait timed out
   int tile_status;    // non-zero if an operator tile copy wait timed out
   int pad;
@@ -180,9 +180,9 @@ void for_each_slab(const Level& L, size_t scratch_bytes, size_t elem_bytes,
                    const std::function<void(int, int, int, int)>& fn);
 void launch_to_fp32(size_t n, const double* a, float* b, cudaStream_t st);
 void launch_coarse_dense(const Level& L, double* A, cudaStream_t st);
-cudaError_t launch_coarse_factor(int n, double* A, double* W, double* Dblk, double* X,
-                                 double* Ainv, double* Pq, int* status, int grid, cudaStream_t st);
-int coarse_factor_grid();
+cudaError_t launch_coarse_invert(int n, double* A, double* W, double* V, double* Ainv, int* status,
+                                 int grid, cudaStream_t st);
+int coarse_sweep_grid();
 
 // ---- launchers (k_tc.cu) -------------------------------------------------
 // Finest-level operator of the TF32 preconditioner on tcgen05.
@@ -314,13 +314,6 @@ inline int parts_for(long nn) {
   return (int)(g < kMaxPart ? (g < 1 ? 1 : g) : kMaxPart);
 }
 
-// Number of q-chunks the coarse inverse product is split into (partial
-// sums scratch of coarse_qchunks(n) * n^2 doubles).
-__host__ __device__ inline int coarse_qchunks(int n) {
-  const int q = (n + 63) / 64;
-  return q < 4 ? (q < 1 ? 1 : q) : 4;
-}
-
 __host__ __device__ inline int sym_index(int r, int c) {
   // r <= c < 24: row-major upper triangle
   return r * kEdofQ1 - (r * (r - 1)) / 2 + (c - r);
@@ -384,11 +377,9 @@ struct tosolve_s {
   // coarse level
   int nc = 0;
   double* Ad = nullptr;
-  double* Wp = nullptr;
-  double* Dblk = nullptr;
-  double* Xinv = nullptr;
+  double* Wp = nullptr;    // block-row scratch of the sweeps, nc x kNB
+  double* Vp = nullptr;    // the same rows before the sweep, nc x kNB
   double* Ainv = nullptr;
-  double* Pq = nullptr;  // partial sums of the coarse inverse product
   int cgrid = 1;
   // PCG
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *f = nullptr;

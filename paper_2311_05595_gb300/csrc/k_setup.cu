@@ -1,8 +1,8 @@
 // Setup kernels: the stacked subcell stiffness table (Sec. 3.3), the density
 // filter (Sec. 2.2 / 3.2), SIMP weights (Eq. matrixK), and the per-design
 // multigrid refresh of Sec. 7.2 (every level's operator and the coarsest
-// level's Cholesky factor are rebuilt for each new density field; the level
-// structure itself is built once).
+// level's direct solve, here its explicit inverse, are rebuilt for each new
+// density field; the level structure itself is built once).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -443,31 +443,30 @@ __global__ void k_coarse_dense(int Lx, int Ly, int Lz, const double* __restrict_
   }
 }
 
-// Dense FP64 Cholesky A = L L^T (blocked, right-looking), then
-// X = L^{-1} (block rows) and A^{-1} = X^T X, in one cooperative launch.
+// The coarsest level's direct solve (Sec. 7.2) as an explicit FP64 inverse,
+// formed by blocked symmetric Gauss-Jordan sweeps in one cooperative launch.
 // The V-cycle's coarse solve is then one dense matrix-vector product spread
-// over many SMs (FP64 issues 4 flop/clk/SM on this part, so a sequential
-// triangular solve on one SM would dominate the cycle).
+// over many SMs.
 //
-// FP64 latency is long here, so the work is shaped for it: one reciprocal
-// square root per pivot; the trailing update, the inverse and the final
-// product are tiled 16x16 with operands staged in shared memory (short,
-// independent FMA chains, coalesced loads); the final product is split
-// into (tile, q-chunk) items whose partial sums are added in a fixed order.
-constexpr int kCT = 16;   // output tile of the parallel phases
-
-__device__ __forceinline__ double dot4(const double* a, int sa, const double* b, int sb, int len) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int q = 0;
-  for (; q + 3 < len; q += 4) {
-    s0 += a[q * sa] * b[q * sb];
-    s1 += a[(q + 1) * sa] * b[(q + 1) * sb];
-    s2 += a[(q + 2) * sa] * b[(q + 2) * sb];
-    s3 += a[(q + 3) * sa] * b[(q + 3) * sb];
-  }
-  for (; q < len; ++q) s0 += a[q * sa] * b[q * sb];
-  return (s0 + s1) + (s2 + s3);
-}
+// Sweeping the pivot block K of a symmetric matrix, with P = A_KK:
+//   A_IJ <- A_IJ - A_IK P^{-1} A_KJ   (I, J outside K)
+//   A_IK <- A_IK P^{-1},  A_KJ <- P^{-1} A_KJ,  A_KK <- -P^{-1}.
+// Sweeping every block in turn leaves -A^{-1}.  The pivot blocks are the
+// Schur complements a block Cholesky factorisation meets, so for an SPD
+// matrix they are SPD and no pivoting is needed; a non-positive scalar pivot
+// sets the status flag (the matrix is not SPD).
+//
+// FP64 on this part issues one warp instruction per ~64 cycles per SM
+// sub-partition with a ~64-cycle dependent latency, and a reciprocal takes
+// ~400 cycles, so the launch is latency-bound at coarse sizes of a few
+// hundred DOFs: the scalar pivots run in a shared-memory sweep of the B x B
+// pivot block (B = 16 up to 640 DOFs, else 32) with two block barriers per
+// pivot, its reciprocal on a warp of its own, the outer product of each
+// entry formed while the reciprocal is in flight; the block-row phase and
+// the update (16x16 tiles of the lower triangle, operands staged in shared
+// memory, both halves written so the matrix stays exactly symmetric) spread
+// over every SM.  Grid barriers: one to symmetrise, two per pivot block.
+constexpr int kCT = 16;   // output tile of the update
 
 // Lower-triangle tile index -> (ti, tj) with tj <= ti.
 __device__ __forceinline__ void tri_tile(int tile, int& ti, int& tj) {
@@ -477,182 +476,152 @@ __device__ __forceinline__ void tri_tile(int tile, int& ti, int& tj) {
   tj = tile - t * (t + 1) / 2;
 }
 
-__global__ void __launch_bounds__(256) k_coarse_factor(int n, double* __restrict__ A,
-                                                       double* __restrict__ W,
-                                                       double* __restrict__ Dblk,
-                                                       double* __restrict__ X,
-                                                       double* __restrict__ Ainv,
-                                                       double* __restrict__ Pq,
-                                                       int* __restrict__ status) {
+template <int B>
+__global__ void __launch_bounds__(256) k_coarse_sweep(int n, double* __restrict__ A,
+                                                      double* __restrict__ W,
+                                                      double* __restrict__ V,
+                                                      double* __restrict__ Ainv,
+                                                      int* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ double a[kNB][kNB + 1];
-  __shared__ double li[kNB][kNB + 1];
-  __shared__ double dinv[kNB];
-  __shared__ double sa[kCT][kNB + 1];  // staged rows (tile i side)
-  __shared__ double sb[kCT][kNB + 1];  // staged rows (tile j side)
+  __shared__ double p[B][B + 1];      // pivot block, swept in place
+  __shared__ double rcp;              // reciprocal of the current scalar pivot
+  __shared__ double sa[kCT][B + 1];   // staged W rows (tile i side)
+  __shared__ double sb[kCT][B + 1];   // staged V rows (tile j side)
   const int tid = threadIdx.x, bd = blockDim.x;
   const long gtid = blockIdx.x * (long)bd + tid, gstride = (long)gridDim.x * bd;
   const int ty = tid / kCT, tx = tid % kCT;  // 16 x 16 threads
-  const int nblk = (n + kNB - 1) / kNB;
+  const int nblk = (n + B - 1) / B;
+  // The lower-triangle entries of the pivot block, on warps 0..6; warp 7
+  // computes the reciprocals.
+  constexpr int kLow = B * (B + 1) / 2;
+  constexpr int kWk = 224;
+  constexpr int kM = (kLow + kWk - 1) / kWk;
+  int ei[kM], ek[kM];
+#pragma unroll
+  for (int m = 0; m < kM; ++m) {
+    const int e = tid + kWk * m;
+    ei[m] = -1;
+    ek[m] = 0;
+    if (tid < kWk && e < kLow) {
+      int ii = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      while (ii * (ii + 1) / 2 > e) --ii;
+      ei[m] = ii;
+      ek[m] = e - ii * (ii + 1) / 2;
+    }
+  }
+  // The operator's lower triangle, mirrored: exactly symmetric from here on.
+  for (long t = gtid; t < (long)n * n; t += gstride) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (j > i) A[(size_t)i * n + j] = A[(size_t)j * n + i];
+  }
+  grid.sync();
+  const int nt = (n + kCT - 1) / kCT;
   for (int kb = 0; kb < nblk; ++kb) {
-    const int k0 = kb * kNB, nb = min(kNB, n - k0);
-    // (A) every block factors the diagonal block in shared memory
-    for (int t = tid; t < kNB * kNB; t += bd) {
-      const int i = t / kNB, j = t % kNB;
-      a[i][j] = (i < nb && j < nb && j <= i) ? A[(size_t)(k0 + i) * n + k0 + j] : 0.0;
-      li[i][j] = (i == j) ? 1.0 : 0.0;
+    const int k0 = kb * B, nb = min(B, n - k0);
+    // (A) every block sweeps P = A_KK into -P^{-1} (identity past nb)
+    for (int t = tid; t < B * B; t += bd) {
+      const int i = t / B, j = t % B;
+      p[i][j] = (i < nb && j < nb) ? A[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
     }
     __syncthreads();
-    for (int jj = 0; jj < nb; ++jj) {
-      if (tid == 0) {
-        double d = a[jj][jj];
+    for (int j = 0; j < nb; ++j) {
+      double pr[kM];
+#pragma unroll
+      for (int m = 0; m < kM; ++m) {
+        pr[m] = 0.0;
+        if (ei[m] >= 0) {
+          const int i = ei[m], k = ek[m];
+          pr[m] = (i >= j ? p[i][j] : p[j][i]) * (k >= j ? p[k][j] : p[j][k]);
+        }
+      }
+      if (tid == kWk) {
+        double d = p[j][j];
         if (!(d > 0.0)) {
           if (blockIdx.x == 0) atomicExch(status, 1);
           d = 1.0;
         }
-        const double ri = rsqrt(d);
-        a[jj][jj] = d * ri;
-        dinv[jj] = ri;
+        rcp = 1.0 / d;
       }
       __syncthreads();
-      const int m = nb - jj - 1;
-      for (int i = jj + 1 + tid; i < nb; i += bd) a[i][jj] *= dinv[jj];
-      __syncthreads();
-      // rank-1 update of the lower triangle only (compact indexing: every
-      // lane of a warp has an entry, one FMA each)
-      for (int t = tid; t < m * (m + 1) / 2; t += bd) {
-        int ii = (int)((sqrt(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-        while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-        while (ii * (ii + 1) / 2 > t) --ii;
-        const int jx = t - ii * (ii + 1) / 2;
-        const int i = jj + 1 + ii, j = jj + 1 + jx;
-        a[i][j] -= a[i][jj] * a[j][jj];
+      const double r = rcp;
+#pragma unroll
+      for (int m = 0; m < kM; ++m) {
+        if (ei[m] >= 0) {
+          const int i = ei[m], k = ek[m];
+          if (i != j && k != j) p[i][k] -= pr[m] * r;
+          else if (i == j && k == j) p[i][k] = -r;
+          else p[i][k] *= r;
+        }
       }
       __syncthreads();
     }
-    // inverse of L_kk, column-parallel forward substitution
-    for (int k = 0; k < nb; ++k) {
-      for (int j = tid; j <= k; j += bd) li[k][j] *= dinv[k];
-      __syncthreads();
-      const int rows = nb - k - 1, cols = k + 1;
-      for (int t = tid; t < rows * cols; t += bd) {
-        const int i = k + 1 + t / cols, j = t % cols;
-        li[i][j] -= a[i][k] * li[k][j];
-      }
-      __syncthreads();
+    for (int t = tid; t < B * B; t += bd) {
+      const int i = t / B, k = t % B;
+      if (k > i) p[i][k] = p[k][i];
     }
-    // (B) panel below the diagonal block: W = A_panel L_kk^{-T}
-    const int rows = n - k0 - nb;
-    for (long t = gtid; t < (long)rows * nb; t += gstride) {
-      const int i = k0 + nb + (int)(t / nb), jj = (int)(t % nb);
-      W[(size_t)i * kNB + jj] = dot4(A + (size_t)i * n + k0, 1, &li[jj][0], 1, jj + 1);
+    __syncthreads();
+    // (B) rows I outside K: W_I = A_IK P^{-1} = -A_IK p, V_I = A_IK
+    for (long t = gtid; t < (long)(n - nb) * nb; t += gstride) {
+      const int ii = (int)(t / nb), c = (int)(t % nb);
+      const int i = ii < k0 ? ii : ii + nb;
+      const double* Ar = A + (size_t)i * n + k0;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int q = 0;
+      for (; q + 3 < nb; q += 4) {
+        s0 += Ar[q] * p[q][c];
+        s1 += Ar[q + 1] * p[q + 1][c];
+        s2 += Ar[q + 2] * p[q + 2][c];
+        s3 += Ar[q + 3] * p[q + 3][c];
+      }
+      for (; q < nb; ++q) s0 += Ar[q] * p[q][c];
+      W[(size_t)i * B + c] = -((s0 + s1) + (s2 + s3));
+      V[(size_t)i * B + c] = Ar[c];
     }
     grid.sync();
-    // (C) write L_kk, its inverse and the panel; trailing update in 16x16 tiles
-    if (blockIdx.x == 0) {
-      for (int t = tid; t < kNB * kNB; t += bd) {
-        const int i = t / kNB, j = t % kNB;
-        if (i < nb && j < nb && j <= i) A[(size_t)(k0 + i) * n + k0 + j] = a[i][j];
-        Dblk[(size_t)kb * kNB * kNB + t] = (i < nb && j < nb && j <= i) ? li[i][j] : 0.0;
-      }
-    }
-    for (long t = gtid; t < (long)rows * nb; t += gstride) {
-      const int i = k0 + nb + (int)(t / nb), jj = (int)(t % nb);
-      A[(size_t)i * n + k0 + jj] = W[(size_t)i * kNB + jj];
-    }
-    const int tr = (rows + kCT - 1) / kCT;
-    for (int tile = blockIdx.x; tile < tr * (tr + 1) / 2; tile += gridDim.x) {
+    // (C) the sweep's update over the lower 16x16 tiles, both halves written
+    for (int tile = blockIdx.x; tile < nt * (nt + 1) / 2; tile += gridDim.x) {
       int ti, tj;
       tri_tile(tile, ti, tj);
-      const int i0 = k0 + nb + ti * kCT, j0 = k0 + nb + tj * kCT;
+      const int i0 = ti * kCT, j0 = tj * kCT;
       __syncthreads();
-      for (int t = tid; t < kCT * kNB; t += bd) {
-        const int r = t / kNB, q = t % kNB;
-        sa[r][q] = (i0 + r < n && q < nb) ? W[(size_t)(i0 + r) * kNB + q] : 0.0;
-        sb[r][q] = (j0 + r < n && q < nb) ? W[(size_t)(j0 + r) * kNB + q] : 0.0;
+      for (int t = tid; t < kCT * B; t += bd) {
+        const int r = t / B, q = t % B;
+        const int gi = i0 + r, gj = j0 + r;
+        sa[r][q] = (gi < n && q < nb && (gi < k0 || gi >= k0 + nb)) ? W[(size_t)gi * B + q] : 0.0;
+        sb[r][q] = (gj < n && q < nb && (gj < k0 || gj >= k0 + nb)) ? V[(size_t)gj * B + q] : 0.0;
       }
       __syncthreads();
       const int i = i0 + ty, j = j0 + tx;
-      if (i < n && j < n && j <= i) {
-        double s0 = 0.0, s1 = 0.0;
+      if (i < n && j < n && (ti != tj || j <= i)) {
+        const bool iK = i >= k0 && i < k0 + nb, jK = j >= k0 && j < k0 + nb;
+        double v;
+        if (!iK && !jK) {
+          double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-        for (int q = 0; q < kNB; q += 2) {
-          s0 += sa[ty][q] * sb[tx][q];
-          s1 += sa[ty][q + 1] * sb[tx][q + 1];
+          for (int q = 0; q < B; q += 2) {
+            s0 += sa[ty][q] * sb[tx][q];
+            s1 += sa[ty][q + 1] * sb[tx][q + 1];
+          }
+          v = A[(size_t)i * n + j] - (s0 + s1);
+        } else if (!iK) {
+          v = sa[ty][j - k0];                    // A_IK <- W_I
+        } else if (!jK) {
+          v = W[(size_t)j * B + (i - k0)];       // A_KJ <- W_J^T
+        } else {
+          v = p[i - k0][j - k0];                 // A_KK <- -P^{-1}
         }
-        A[(size_t)i * n + j] -= s0 + s1;
+        A[(size_t)i * n + j] = v;
+        if (i != j) A[(size_t)j * n + i] = v;
       }
     }
     grid.sync();
   }
-  // X = L^{-1}, one block row at a time: X_ib,jb = -Linv_ib * sum_q L_ib,q X_q,jb
-  for (int ib = 0; ib < nblk; ++ib) {
-    const int i0 = ib * kNB, nbi = min(kNB, n - i0);
-    // T[r][j] = sum_{q=j}^{i0-1} L[i0+r][q] X[q][j]; consecutive threads take
-    // consecutive j and walk the same absolute q (X[q][j] = 0 for q < j, so
-    // starting at the warp's first j is exact): coalesced X rows, L broadcast,
-    // four independent accumulators
-    for (long t = gtid; t < (long)nbi * i0; t += gstride) {
-      const int r = (int)(t / i0), j = (int)(t % i0);
-      const int q0 = j & ~31;
-      Ainv[(size_t)r * n + j] = dot4(A + (size_t)(i0 + r) * n + q0, 1, X + (size_t)q0 * n + j, n, i0 - q0);
-    }
-    grid.sync();
-    const double* Li = Dblk + (size_t)ib * kNB * kNB;
-    for (long t = gtid; t < (long)nbi * (i0 + nbi); t += gstride) {
-      const int r = (int)(t / (i0 + nbi)), j = (int)(t % (i0 + nbi));
-      double v;
-      if (j >= i0) {
-        v = (j - i0 <= r) ? Li[r * kNB + (j - i0)] : 0.0;
-      } else {
-        v = -dot4(Li + r * kNB, 1, Ainv + j, n, r + 1);
-      }
-      X[(size_t)(i0 + r) * n + j] = v;
-    }
-    grid.sync();
-  }
-  // A^{-1} = X^T X: items (16x16 lower tile, 64-wide q chunk) -> partials in
-  // Pq[chunk], then every entry adds its chunks in order.
-  const int nt = (n + kCT - 1) / kCT;
-  const int nq = coarse_qchunks(n);
-  const int kQC = ((n + nq - 1) / nq + kNB - 1) / kNB * kNB;  // q-chunk length
-  const int ntiles = nt * (nt + 1) / 2;
-  for (int item = blockIdx.x; item < ntiles * nq; item += gridDim.x) {
-    const int tile = item / nq, qc = item % nq;
-    int ti, tj;
-    tri_tile(tile, ti, tj);
-    const int i0 = ti * kCT, j0 = tj * kCT;
-    const int qlo = max(qc * kQC, i0), qhi = min((qc + 1) * kQC, n);
-    const int i = i0 + ty, j = j0 + tx;
-    double s0 = 0.0, s1 = 0.0;
-    for (int q0 = qlo; q0 < qhi; q0 += kNB) {
-      __syncthreads();
-      for (int t = tid; t < kCT * kNB; t += bd) {
-        const int c = t / kNB, qq = t % kNB;
-        const int q = q0 + qq;
-        sa[c][qq] = (q < qhi && i0 + c < n) ? X[(size_t)q * n + i0 + c] : 0.0;
-        sb[c][qq] = (q < qhi && j0 + c < n) ? X[(size_t)q * n + j0 + c] : 0.0;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int qq = 0; qq < kNB; qq += 2) {
-        s0 += sa[ty][qq] * sb[tx][qq];
-        s1 += sa[ty][qq + 1] * sb[tx][qq + 1];
-      }
-    }
-    if (i < n && j < n && j <= i) Pq[((size_t)qc * n + i) * n + j] = s0 + s1;
-  }
-  grid.sync();
-  for (long t = gtid; t < (long)n * n; t += gstride) {
-    const int i = (int)(t / n), j = (int)(t % n);
-    if (j > i) continue;
-    double s = 0.0;
-    for (int qc = 0; qc < nq; ++qc)
-      if ((qc + 1) * kQC > ((i / kCT) * kCT)) s += Pq[((size_t)qc * n + i) * n + j];
-    Ainv[(size_t)i * n + j] = s;
-    Ainv[(size_t)j * n + i] = s;
-  }
+  for (long t = gtid; t < (long)n * n; t += gstride) Ainv[t] = -A[t];
 }
+
+// Pivot block of the coarse sweeps for an n x n coarse operator.
+inline int coarse_pivot_block(int n) { return n <= 640 ? 16 : 32; }
 
 inline int grid_for(long n, int bs = kBS, int cap = 4096) {
   long g = (n + bs - 1) / bs;
@@ -784,20 +753,22 @@ void launch_coarse_dense(const Level& L, double* A, cudaStream_t st) {
   k_coarse_dense<<<grid_for((long)L.nn * 27), kBS, 0, st>>>(L.Lx, L.Ly, L.Lz, L.S64, A);
 }
 
-int coarse_factor_grid() {
-  int dev = 0, sms = 0, per = 0;
+int coarse_sweep_grid() {
+  int dev = 0, sms = 0, per16 = 0, per32 = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_factor, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per16, k_coarse_sweep<16>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, k_coarse_sweep<32>, 256, 0);
   // one block per SM (co-resident as long as one block fits, checked here)
-  if (per < 1) return 0;
+  if (per16 < 1 || per32 < 1) return 0;
   return sms;
 }
 
-cudaError_t launch_coarse_factor(int n, double* A, double* W, double* Dblk, double* X,
-                                 double* Ainv, double* Pq, int* status, int grid, cudaStream_t st) {
-  void* args[] = {&n, &A, &W, &Dblk, &X, &Ainv, &Pq, &status};
-  return cudaLaunchCooperativeKernel((void*)k_coarse_factor, dim3(grid), dim3(256), args, 0, st);
+cudaError_t launch_coarse_invert(int n, double* A, double* W, double* V, double* Ainv, int* status,
+                                 int grid, cudaStream_t st) {
+  void* args[] = {&n, &A, &W, &V, &Ainv, &status};
+  void* fn = coarse_pivot_block(n) == 16 ? (void*)k_coarse_sweep<16> : (void*)k_coarse_sweep<32>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, st);
 }
 
 }  // namespace tos

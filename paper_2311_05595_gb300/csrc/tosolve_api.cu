@@ -213,8 +213,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   B += (size_t)P->noff * (sizeof(int4) + 8);
   B += (size_t)P->m * (576 + kSym) * 8 + 27 * kSym * 8;  // tables
   const long nc = P->nc;
-  const long nblk = (nc + kNB - 1) / kNB;
-  B += (size_t)(3 * nc * nc + nc * kNB + nblk * kNB * kNB + (size_t)coarse_qchunks((int)nc) * nc * nc) * 8;
+  B += (size_t)(2 * nc * nc + 2 * nc * kNB) * 8;     // coarse operator, inverse, sweep rows
   B += (size_t)ndof0 * 8 * 7;                         // u r p q f tmpa tmpb
   B += (size_t)ndof0 * 8 * 2 * maxrhs;                // host-step staging f, u
   B += 4 * kMaxPart * 8 + sizeof(DevState) + (size_t)P->ndes * 8 * 2;
@@ -256,7 +255,7 @@ void free_all(tosolve_s* h) {
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
   F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab); F(h->ptab3);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
-  F(h->Ad); F(h->Wp); F(h->Dblk); F(h->Xinv); F(h->Ainv); F(h->Pq);
+  F(h->Ad); F(h->Wp); F(h->Vp); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
   F(h->cnt);
   F(h->hx); F(h->hf); F(h->hu); F(h->hg);
@@ -752,16 +751,13 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   CKC(cudaEventCreateWithFlags(&h->evj, cudaEventDisableTiming));
   // coarse dense solve
   {
-    const long nc = P.nc, nblk = (nc + kNB - 1) / kNB;
+    const long nc = P.nc;
     CKC(dalloc(h, &h->Ad, nc * nc));
     CKC(dalloc(h, &h->Wp, nc * kNB));
-    CKC(dalloc(h, &h->Dblk, nblk * kNB * kNB));
-    CKC(dalloc(h, &h->Xinv, nc * nc));
-    CKC(cudaMemsetAsync(h->Xinv, 0, nc * nc * sizeof(double), st));
+    CKC(dalloc(h, &h->Vp, nc * kNB));
     CKC(dalloc(h, &h->Ainv, nc * nc));
-    CKC(dalloc(h, &h->Pq, (size_t)coarse_qchunks((int)nc) * nc * nc));
-    h->cgrid = coarse_factor_grid();
-    if (h->cgrid < 1) { h->err = "coarse factor kernel cannot be made co-resident"; return fail(TOSOLVE_ECUDA); }
+    h->cgrid = coarse_sweep_grid();
+    if (h->cgrid < 1) { h->err = "coarse sweep kernel cannot be made co-resident"; return fail(TOSOLVE_ECUDA); }
   }
   // PCG
   const long nd = P.lv[0].ndof;
@@ -847,7 +843,7 @@ static tosolve_status refresh(tosolve_t h) {
   const int n = d.n_mr;
   const int L = h->L;
   const bool fp32 = d.precision != TOSOLVE_PREC_FP64;
-  // The coarsest level (FP64 operator, dense matrix, Cholesky and inverse)
+  // The coarsest level (FP64 operator, dense matrix and its inverse)
   // only needs the weights: with more than one level it runs on a second
   // stream, overlapped with the FP64-bound assembly of the finer levels.
   cudaStream_t cst = st;
@@ -869,8 +865,7 @@ static tosolve_status refresh(tosolve_t h) {
     CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), cst));
     launch_q2_dense(C, Kc, h->Ad, cst);
     CK(cudaMemsetAsync(&h->ds->coarse_status, 0, sizeof(int), cst));
-    CK(launch_coarse_factor(h->nc, h->Ad, h->Wp, h->Dblk, h->Xinv, h->Ainv, h->Pq,
-                            &h->ds->coarse_status, h->cgrid, cst));
+    CK(launch_coarse_invert(h->nc, h->Ad, h->Wp, h->Vp, h->Ainv, &h->ds->coarse_status, h->cgrid, cst));
     for (int l = 0; l + 1 < L; ++l) {
       Level& Lv = h->lv[l];
       if (l == 0) {
@@ -908,8 +903,7 @@ static tosolve_status refresh(tosolve_t h) {
   CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), cst));
   launch_coarse_dense(C, h->Ad, cst);
   CK(cudaMemsetAsync(&h->ds->coarse_status, 0, sizeof(int), cst));
-  CK(launch_coarse_factor(h->nc, h->Ad, h->Wp, h->Dblk, h->Xinv, h->Ainv, h->Pq,
-                          &h->ds->coarse_status, h->cgrid, cst));
+  CK(launch_coarse_invert(h->nc, h->Ad, h->Wp, h->Vp, h->Ainv, &h->ds->coarse_status, h->cgrid, cst));
   for (int l = 0; l + 1 < L; ++l) {
     Level& Lv = h->lv[l];
     if (l == 0) {
@@ -1211,7 +1205,7 @@ tosolve_status tosolve_solve(tosolve_t h, const double* f_dev, int nrhs, double*
       last = used;
       if (S.status != 0) {
         result = TOSOLVE_EBREAKDOWN;
-        h->err = S.coarse_status ? "coarse Cholesky met a non-positive pivot" : "PCG breakdown (p^T K p <= 0 or NaN)";
+        h->err = S.coarse_status ? "coarse sweep met a non-positive pivot (coarsest operator not SPD)" : "PCG breakdown (p^T K p <= 0 or NaN)";
         worst = std::fmax(worst, rel);
         break;
       }
@@ -1553,7 +1547,7 @@ tosolve_status tosolve_batch_solve(tosolve_batch_t b, double rtol, int maxit, to
   e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return cuda_fail(e);
   if (result == TOSOLVE_ENOTCONV) g_err = "a load case reached maxit before the tolerance";
-  else if (result == TOSOLVE_EBREAKDOWN) g_err = "breakdown in a load case (PCG or coarse Cholesky)";
+  else if (result == TOSOLVE_EBREAKDOWN) g_err = "breakdown in a load case (PCG, or a non-positive coarse pivot)";
   else if (result == TOSOLVE_ECUDA) g_err = "a tensor-core or operator tile copy did not complete within its bounded wait";
   return result;
 }

@@ -11,8 +11,8 @@ Tolerances (the bar of the task, stated per check):
     FP64 operators agree to 1e-13, so their FP32 roundings differ in at most
     a few entries by one FP32 ulp);
   * one multigrid cycle in FP64: relative 1e-9 (the coarse solve applies an
-    explicit inverse formed from the Cholesky factor instead of two
-    triangular solves; its error is about cond(A_c) * 1e-16);
+    explicit inverse formed by blocked Gauss-Jordan sweeps instead of two
+    Cholesky triangular solves; its error is about cond(A_c) * 1e-16);
   * solves: true relative residual <= rtol (FP64, recomputed independently
     with the oracle's assembled K), displacement relative L2 error <= 1e-6,
     compliance relative error <= 1e-7, gradient relative L2 error <= 1e-6;
