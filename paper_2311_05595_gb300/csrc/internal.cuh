@@ -180,8 +180,8 @@ void for_each_slab(const Level& L, size_t scratch_bytes, size_t elem_bytes,
                    const std::function<void(int, int, int, int)>& fn);
 void launch_to_fp32(size_t n, const double* a, float* b, cudaStream_t st);
 void launch_coarse_dense(const Level& L, double* A, cudaStream_t st);
-cudaError_t launch_coarse_invert(int n, double* A, double* W, double* V, double* Ainv, int* status,
-                                 int grid, cudaStream_t st);
+cudaError_t launch_coarse_invert(int n, double* A, double* W, double* V, double* Pg, double* Ainv,
+                                 int* status, int grid, cudaStream_t st);
 int coarse_sweep_grid();
 
 // ---- launchers (k_tc.cu) -------------------------------------------------
@@ -379,6 +379,7 @@ struct tosolve_s {
   double* Ad = nullptr;
   double* Wp = nullptr;    // block-row scratch of the sweeps, nc x kNB
   double* Vp = nullptr;    // the same rows before the sweep, nc x kNB
+  double* Pg = nullptr;    // the next pivot block's -P^{-1}, kNB x kNB
   double* Ainv = nullptr;
   int cgrid = 1;
   // PCG

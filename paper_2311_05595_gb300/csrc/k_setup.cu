@@ -459,13 +459,16 @@ __global__ void k_coarse_dense(int Lx, int Ly, int Lz, const double* __restrict_
 // FP64 on this part issues one warp instruction per ~64 cycles per SM
 // sub-partition with a ~64-cycle dependent latency, and a reciprocal takes
 // ~400 cycles, so the launch is latency-bound at coarse sizes of a few
-// hundred DOFs: the scalar pivots run in a shared-memory sweep of the B x B
-// pivot block (B = 16 up to 640 DOFs, else 32) with two block barriers per
-// pivot, its reciprocal on a warp of its own, the outer product of each
-// entry formed while the reciprocal is in flight; the block-row phase and
-// the update (16x16 tiles of the lower triangle, operands staged in shared
-// memory, both halves written so the matrix stays exactly symmetric) spread
-// over every SM.  Grid barriers: one to symmetrise, two per pivot block.
+// hundred DOFs, by the chain of scalar pivots.  The pivots of each B x B
+// pivot block (B = 16 up to 640 DOFs, else 32) are swept in shared memory
+// with two block barriers per pivot, the reciprocal on a warp of its own,
+// each entry's update formed while the reciprocal is in flight.  One block
+// looks ahead: in each update phase it updates the next pivot block first
+// and sweeps it while the other blocks update the rest, so the pivot sweeps
+// overlap the updates.  The block-row phase and the update (16x16 tiles of
+// the lower triangle, operands staged in shared memory, both halves written
+// so the matrix stays exactly symmetric) spread over every SM.  Grid
+// barriers: one to symmetrise, two per pivot block.
 constexpr int kCT = 16;   // output tile of the update
 
 // Lower-triangle tile index -> (ti, tj) with tj <= ti.
@@ -476,14 +479,68 @@ __device__ __forceinline__ void tri_tile(int tile, int& ti, int& tj) {
   tj = tile - t * (t + 1) / 2;
 }
 
+// Sweeps the scalar pivots 0..nb-1 of the B x B block p (lower triangle
+// current, identity past nb) into -P^{-1}, then mirrors it.  All threads of
+// the block call it; the lower-triangle entries sit on warps 0..6 (ei, ek),
+// warp 7 forms the reciprocals.
+template <int B>
+__device__ __forceinline__ void sweep_pivots(double (*p)[B + 1], int nb, const int* ei, const int* ek,
+                                             double* rcp, int* status) {
+  constexpr int kLow = B * (B + 1) / 2;
+  constexpr int kWk = 224;
+  constexpr int kM = (kLow + kWk - 1) / kWk;
+  const int tid = threadIdx.x;
+  for (int j = 0; j < nb; ++j) {
+    // Every entry's new value is fma(x, r, y) with r = 1 / p_jj:
+    // p_ik - p_ij p_kj r off row and column j, p_ik r on them, -r at the
+    // pivot. x and y are formed while the reciprocal is in flight, so the
+    // update after the barrier is one FMA per entry and no warp diverges.
+    double ux[kM], uy[kM];
+#pragma unroll
+    for (int m = 0; m < kM; ++m) {
+      ux[m] = 0.0;
+      uy[m] = 0.0;
+      if (ei[m] >= 0) {
+        const int i = ei[m], k = ek[m];
+        const double pik = p[i][k];
+        const double pij = i >= j ? p[i][j] : p[j][i];
+        const double pkj = k >= j ? p[k][j] : p[j][k];
+        const bool off = i != j && k != j, piv = i == j && k == j;
+        ux[m] = off ? -(pij * pkj) : (piv ? -1.0 : pik);
+        uy[m] = off ? pik : 0.0;
+      }
+    }
+    if (tid == kWk) {
+      double d = p[j][j];
+      if (!(d > 0.0)) {
+        atomicExch(status, 1);
+        d = 1.0;
+      }
+      *rcp = 1.0 / d;
+    }
+    __syncthreads();
+    const double r = *rcp;
+#pragma unroll
+    for (int m = 0; m < kM; ++m)
+      if (ei[m] >= 0) p[ei[m]][ek[m]] = fma(ux[m], r, uy[m]);
+    __syncthreads();
+  }
+  for (int t = tid; t < B * B; t += blockDim.x) {
+    const int i = t / B, k = t % B;
+    if (k > i) p[i][k] = p[k][i];
+  }
+  __syncthreads();
+}
+
 template <int B>
 __global__ void __launch_bounds__(256) k_coarse_sweep(int n, double* __restrict__ A,
                                                       double* __restrict__ W,
                                                       double* __restrict__ V,
+                                                      double* __restrict__ Pg,
                                                       double* __restrict__ Ainv,
                                                       int* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ double p[B][B + 1];      // pivot block, swept in place
+  __shared__ double p[B][B + 1];      // -P^{-1} of the current pivot block
   __shared__ double rcp;              // reciprocal of the current scalar pivot
   __shared__ double sa[kCT][B + 1];   // staged W rows (tile i side)
   __shared__ double sb[kCT][B + 1];   // staged V rows (tile j side)
@@ -491,8 +548,7 @@ __global__ void __launch_bounds__(256) k_coarse_sweep(int n, double* __restrict_
   const long gtid = blockIdx.x * (long)bd + tid, gstride = (long)gridDim.x * bd;
   const int ty = tid / kCT, tx = tid % kCT;  // 16 x 16 threads
   const int nblk = (n + B - 1) / B;
-  // The lower-triangle entries of the pivot block, on warps 0..6; warp 7
-  // computes the reciprocals.
+  const int look = gridDim.x - 1;            // the look-ahead block
   constexpr int kLow = B * (B + 1) / 2;
   constexpr int kWk = 224;
   constexpr int kM = (kLow + kWk - 1) / kWk;
@@ -519,48 +575,19 @@ __global__ void __launch_bounds__(256) k_coarse_sweep(int n, double* __restrict_
   const int nt = (n + kCT - 1) / kCT;
   for (int kb = 0; kb < nblk; ++kb) {
     const int k0 = kb * B, nb = min(B, n - k0);
-    // (A) every block sweeps P = A_KK into -P^{-1} (identity past nb)
-    for (int t = tid; t < B * B; t += bd) {
-      const int i = t / B, j = t % B;
-      p[i][j] = (i < nb && j < nb) ? A[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
-    }
-    __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-      double pr[kM];
-#pragma unroll
-      for (int m = 0; m < kM; ++m) {
-        pr[m] = 0.0;
-        if (ei[m] >= 0) {
-          const int i = ei[m], k = ek[m];
-          pr[m] = (i >= j ? p[i][j] : p[j][i]) * (k >= j ? p[k][j] : p[j][k]);
-        }
-      }
-      if (tid == kWk) {
-        double d = p[j][j];
-        if (!(d > 0.0)) {
-          if (blockIdx.x == 0) atomicExch(status, 1);
-          d = 1.0;
-        }
-        rcp = 1.0 / d;
+    // (A) -P^{-1} of this pivot block: swept by every block for the first
+    // one, published by the look-ahead block for the others
+    if (kb == 0) {
+      for (int t = tid; t < B * B; t += bd) {
+        const int i = t / B, j = t % B;
+        p[i][j] = (i < nb && j < nb) ? A[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
       }
       __syncthreads();
-      const double r = rcp;
-#pragma unroll
-      for (int m = 0; m < kM; ++m) {
-        if (ei[m] >= 0) {
-          const int i = ei[m], k = ek[m];
-          if (i != j && k != j) p[i][k] -= pr[m] * r;
-          else if (i == j && k == j) p[i][k] = -r;
-          else p[i][k] *= r;
-        }
-      }
+      sweep_pivots<B>(p, nb, ei, ek, &rcp, status);
+    } else {
+      for (int t = tid; t < B * B; t += bd) p[t / B][t % B] = Pg[t];
       __syncthreads();
     }
-    for (int t = tid; t < B * B; t += bd) {
-      const int i = t / B, k = t % B;
-      if (k > i) p[i][k] = p[k][i];
-    }
-    __syncthreads();
     // (B) rows I outside K: W_I = A_IK P^{-1} = -A_IK p, V_I = A_IK
     for (long t = gtid; t < (long)(n - nb) * nb; t += gstride) {
       const int ii = (int)(t / nb), c = (int)(t % nb);
@@ -579,10 +606,14 @@ __global__ void __launch_bounds__(256) k_coarse_sweep(int n, double* __restrict_
       V[(size_t)i * B + c] = Ar[c];
     }
     grid.sync();
-    // (C) the sweep's update over the lower 16x16 tiles, both halves written
-    for (int tile = blockIdx.x; tile < nt * (nt + 1) / 2; tile += gridDim.x) {
-      int ti, tj;
-      tri_tile(tile, ti, tj);
+    // (C) the sweep's update over the lower 16x16 tiles, both halves
+    // written. The look-ahead block takes the tiles of the next pivot block
+    // (rows and columns [k1, k1 + nb1), k1 a multiple of 16), keeps them in
+    // shared memory and sweeps them while the others update the rest.
+    const bool ahead = kb + 1 < nblk;
+    const int k1 = k0 + B, nb1 = ahead ? min(B, n - k1) : 0;
+    const int tl0 = k1 / kCT, tl1 = (k1 + nb1 + kCT - 1) / kCT;
+    auto tile_update = [&](int ti, int tj, bool keep) {
       const int i0 = ti * kCT, j0 = tj * kCT;
       __syncthreads();
       for (int t = tid; t < kCT * B; t += bd) {
@@ -613,6 +644,32 @@ __global__ void __launch_bounds__(256) k_coarse_sweep(int n, double* __restrict_
         }
         A[(size_t)i * n + j] = v;
         if (i != j) A[(size_t)j * n + i] = v;
+        if (keep) {                              // entries of the next pivot block
+          p[i - k1][j - k1] = v;
+          p[j - k1][i - k1] = v;
+        }
+      }
+    };
+    if (ahead && blockIdx.x == look) {
+      // the next block's tiles lie outside K, so they never read p: it is
+      // reused for P_{k+1}
+      __syncthreads();
+      for (int t = tid; t < B * B; t += bd) {
+        const int i = t / B, j = t % B;
+        if (i >= nb1 || j >= nb1) p[i][j] = (i == j ? 1.0 : 0.0);
+      }
+      for (int ti = tl0; ti < tl1; ++ti)
+        for (int tj = tl0; tj <= ti; ++tj) tile_update(ti, tj, true);
+      __syncthreads();
+      sweep_pivots<B>(p, nb1, ei, ek, &rcp, status);
+      for (int t = tid; t < B * B; t += bd) Pg[t] = p[t / B][t % B];
+    } else {
+      const int workers = ahead ? gridDim.x - 1 : gridDim.x;
+      for (int tile = blockIdx.x; tile < nt * (nt + 1) / 2; tile += workers) {
+        int ti, tj;
+        tri_tile(tile, ti, tj);
+        if (ahead && ti >= tl0 && ti < tl1 && tj >= tl0 && tj < tl1) continue;
+        tile_update(ti, tj, false);
       }
     }
     grid.sync();
@@ -764,9 +821,10 @@ int coarse_sweep_grid() {
   return sms;
 }
 
-cudaError_t launch_coarse_invert(int n, double* A, double* W, double* V, double* Ainv, int* status,
-                                 int grid, cudaStream_t st) {
-  void* args[] = {&n, &A, &W, &V, &Ainv, &status};
+cudaError_t launch_coarse_invert(int n, double* A, double* W, double* V, double* Pg, double* Ainv,
+                                 int* status, int grid, cudaStream_t st) {
+  if (grid < 2) return cudaErrorInvalidConfiguration;  // one block looks ahead
+  void* args[] = {&n, &A, &W, &V, &Pg, &Ainv, &status};
   void* fn = coarse_pivot_block(n) == 16 ? (void*)k_coarse_sweep<16> : (void*)k_coarse_sweep<32>;
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, st);
 }

@@ -213,7 +213,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   B += (size_t)P->noff * (sizeof(int4) + 8);
   B += (size_t)P->m * (576 + kSym) * 8 + 27 * kSym * 8;  // tables
   const long nc = P->nc;
-  B += (size_t)(2 * nc * nc + 2 * nc * kNB) * 8;     // coarse operator, inverse, sweep rows
+  B += (size_t)(2 * nc * nc + 2 * nc * kNB + kNB * kNB) * 8;  // coarse operator, inverse, sweeps
   B += (size_t)ndof0 * 8 * 7;                         // u r p q f tmpa tmpb
   B += (size_t)ndof0 * 8 * 2 * maxrhs;                // host-step staging f, u
   B += 4 * kMaxPart * 8 + sizeof(DevState) + (size_t)P->ndes * 8 * 2;
@@ -255,7 +255,7 @@ void free_all(tosolve_s* h) {
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
   F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab); F(h->ptab3);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
-  F(h->Ad); F(h->Wp); F(h->Vp); F(h->Ainv);
+  F(h->Ad); F(h->Wp); F(h->Vp); F(h->Pg); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
   F(h->cnt);
   F(h->hx); F(h->hf); F(h->hu); F(h->hg);
@@ -755,6 +755,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     CKC(dalloc(h, &h->Ad, nc * nc));
     CKC(dalloc(h, &h->Wp, nc * kNB));
     CKC(dalloc(h, &h->Vp, nc * kNB));
+    CKC(dalloc(h, &h->Pg, kNB * kNB));
     CKC(dalloc(h, &h->Ainv, nc * nc));
     h->cgrid = coarse_sweep_grid();
     if (h->cgrid < 1) { h->err = "coarse sweep kernel cannot be made co-resident"; return fail(TOSOLVE_ECUDA); }
@@ -865,7 +866,8 @@ static tosolve_status refresh(tosolve_t h) {
     CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), cst));
     launch_q2_dense(C, Kc, h->Ad, cst);
     CK(cudaMemsetAsync(&h->ds->coarse_status, 0, sizeof(int), cst));
-    CK(launch_coarse_invert(h->nc, h->Ad, h->Wp, h->Vp, h->Ainv, &h->ds->coarse_status, h->cgrid, cst));
+    CK(launch_coarse_invert(h->nc, h->Ad, h->Wp, h->Vp, h->Pg, h->Ainv, &h->ds->coarse_status,
+                            h->cgrid, cst));
     for (int l = 0; l + 1 < L; ++l) {
       Level& Lv = h->lv[l];
       if (l == 0) {
@@ -903,7 +905,8 @@ static tosolve_status refresh(tosolve_t h) {
   CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), cst));
   launch_coarse_dense(C, h->Ad, cst);
   CK(cudaMemsetAsync(&h->ds->coarse_status, 0, sizeof(int), cst));
-  CK(launch_coarse_invert(h->nc, h->Ad, h->Wp, h->Vp, h->Ainv, &h->ds->coarse_status, h->cgrid, cst));
+  CK(launch_coarse_invert(h->nc, h->Ad, h->Wp, h->Vp, h->Pg, h->Ainv, &h->ds->coarse_status,
+                          h->cgrid, cst));
   for (int l = 0; l + 1 < L; ++l) {
     Level& Lv = h->lv[l];
     if (l == 0) {
