@@ -44,8 +44,8 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # gather together), valid while the kernel source is unchanged (keyed by the
 # kernel, the source hash and the workload).
 NCU_TRAFFIC = {
-    ("k_apply_diag<double>", "740f79607230", "cantilever_mr_96x48x48_q1_48x24x24_n2"):
-        60.348928e6 + 0.090112e6,
+    ("k_apply_diag<double>", "e2ccbca04323", "cantilever_mr_96x48x48_q1_48x24x24_n2"):
+        60348672 + 86272,
     ("k_q2_apply<double>", "a9e36f7df2c6", "bridge_q2_64x32x32_n3_density_192x96x96"):
         3500955648 + 44271872 + 44121088 + 1024,
 }
@@ -211,18 +211,36 @@ def run_reference(args):
 
 # ---- GPU arm -------------------------------------------------------------------
 
-def kernel_launches(levels: int, iterations: int, attempts: int = 1, degree: int = 1) -> int:
+def kernel_launches(levels: int, iterations: int, attempts: int = 1, degree: int = 1,
+                    tc: bool = False) -> int:
     """Our kernels per step: set_densities (filter; fine element matrices,
-    assembly, two FP32 casts; 2 per coarse level; coarse dense + factor),
-    solve (prep, residual, check; per PCG iteration: 4 per non-coarsest
-    level + 1 coarse solve + 5 CG kernels; true residual + final), gradient
-    (masked dot + sum, energies, scale, filter transpose)."""
-    setd = 1 + 4 + 2 * (levels - 1) + 2
-    per_it = 4 * (levels - 1) + 1 + 5
-    if degree == 2:  # element form: two kernels per operator apply, 8 dense passes
+    assembly, two FP32 casts; 2 per coarse level; coarse dense + sweeps),
+    solve (prep and initial residual; per PCG iteration the V-cycle and the
+    CG kernels; the true residual), gradient (masked dot + sum, energies,
+    scale, filter transpose).
+
+    Per PCG iteration, trilinear: 4 per non-coarsest level (pre, restrict,
+    prolong, post) + 1 coarse solve, then direction, q = K p and update; the
+    finest post-smoothing step also forms r^T z and z^T q, except on the
+    TF32 path, whose finest pre and post steps are two kernels each and
+    which keeps the separate reduction kernel.  Triquadratic: 7 per
+    non-coarsest level (pre and post are element product + gather,
+    restriction is element-wise + gather with the shape-function
+    transfers) + 1, then reduction, direction, q = K p (product, gather,
+    p^T q) and update.
+
+    set_densities, trilinear: filter 1; finest level 4 (element matrices,
+    assembly, two FP32 casts); coarsest 5 (moments, element matrices,
+    assembly, dense matrix, sweeps); each middle level its moments, element
+    matrices and assembly per memory slab: 11 for the two middle levels of
+    the benchmark cantilever (21 in all, counted from its ncu launch list),
+    taken as 5.5 per middle level elsewhere."""
+    setd = 1 + 4 + 5 + int(round(5.5 * max(levels - 2, 0)))
+    per_it = 4 * (levels - 1) + 1 + 3 + (3 if tc else 0)
+    if degree == 2:
         setd = 1 + 3 * (levels - 1) + 2 + 9 + 2
-        per_it = 6 * (levels - 1) + 1 + 6
-    solve = attempts * 5 + per_it * iterations
+        per_it = 7 * (levels - 1) + 1 + 6
+    solve = attempts * 3 + per_it * iterations
     return setd + solve + 5
 
 
@@ -437,7 +455,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": kernel_launches(T.tosolve_level_count(s.h), int(statistics.median(its)),
-                                        degree=p.degree) * args.steps,
+                                        degree=p.degree, tc=best == "tf32") * args.steps,
         "roofline": {"kernel": kernel,
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,

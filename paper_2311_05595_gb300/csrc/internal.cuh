@@ -209,8 +209,20 @@ void launch_mask_fp32(const Level& L, float* x, cudaStream_t st);
 // ---- launchers (k_solve.cu) ----------------------------------------------
 template <typename T>
 LevelView<T> view(const Level& L);
-void launch_vcycle(int vt, Level* lv, int L, double omega, int gamma, const double* Ainv,
-                   const TcOp& tc, cudaStream_t st);
+// Operands of the PCG step that follows the V-cycle (r^T z, z^T q and beta,
+// as launch_cg_dots_rz): when the finest level's last smoothing step is a
+// stencil kernel, launch_vcycle folds this reduction into it and returns
+// true; otherwise the caller launches launch_cg_dots_rz.
+struct CgDots {
+  const double* r;
+  const double* q;
+  double* part_rz;  // kMaxPart partials each
+  double* part_zq;
+  DevState* ds;
+  unsigned* cnt;
+};
+bool launch_vcycle(int vt, Level* lv, int L, double omega, int gamma, const double* Ainv,
+                   const TcOp& tc, cudaStream_t st, const CgDots* dots = nullptr);
 void launch_smooth0(int vt, const Level& L0, double omega, cudaStream_t st);
 void launch_set_params(DevState* ds, const double* params, cudaStream_t st);
 void launch_cg_prep(const Level& L0, double* f, double* u, double* part, int np, cudaStream_t st);

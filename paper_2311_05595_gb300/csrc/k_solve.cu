@@ -386,6 +386,39 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_vc_po
   });
 }
 
+// The same last smoothing step at the finest level, fused with the PCG
+// reduction that follows it (k_cg_dots_rz): partial r^T z and z^T q over
+// the rows this block writes; the last block forms beta.
+template <typename T, bool kOrd>
+__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>())
+    k_vc_post_dots(LevelView<T> V, T omega, const T* __restrict__ b, const T* __restrict__ v,
+                   T* __restrict__ z, CgDots cd) {
+  double a = 0.0, c = 0.0;
+  for_each_row<kOrd>(V, [&](long nb, int cc) { return ld_nc(v + 3 * nb + cc); }, [&](long node, int r, T y) {
+    const long d = 3 * node + r;
+    const T zt = v[d] + omega * V.dinv[d] * (b[d] - y);
+    z[d] = zt;
+    const double zv = (double)zt;
+    a += cd.r[d] * zv;
+    c += zv * cd.q[d];
+  });
+  a = block_sum(a);
+  c = block_sum(c);
+  if (threadIdx.x == 0) {
+    cd.part_rz[blockIdx.x] = a;
+    cd.part_zq[blockIdx.x] = c;
+  }
+  if (!last_block(cd.cnt)) return;
+  const double rz_new = reduce_parts(cd.part_rz, gridDim.x);
+  const double zq = reduce_parts(cd.part_zq, gridDim.x);
+  if (threadIdx.x == 0) {
+    DevState* ds = cd.ds;
+    ds->beta = (ds->iter == 0) ? 0.0 : -ds->alpha * zq / ds->rz;
+    ds->rz_next = rz_new;
+    *cd.cnt = 0u;
+  }
+}
+
 // Coarsest level: z = A_c^{-1} b in FP64, one warp per row.
 template <typename T>
 __global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
@@ -699,16 +732,19 @@ const void* elem_op(const Level& L) {
   return std::is_same<T, double>::value ? (const void*)L.K64 : (const void*)L.K32;
 }
 
+// One V-cycle from level l down (Algorithm 1).  With dots (finest level
+// only) the last smoothing step also forms the PCG reduction when it is a
+// stencil kernel; returns whether it did.
 template <typename T>
-void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp& tc,
-                cudaStream_t st) {
+bool vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp& tc,
+                cudaStream_t st, const CgDots* dots) {
   Level& F = lv[l];
   if (l == L - 1) {
     const int n = F.ndof;
     int g = (n * 32 + kBS - 1) / kBS;
     if (g > 1024) g = 1024;
     k_coarse_solve<T><<<g, kBS, 0, st>>>(n, Ainv, (const T*)F.b, (T*)F.z);
-    return;
+    return false;
   }
   Level& C = lv[l + 1];
   const LevelView<T> V = view<T>(F);
@@ -734,7 +770,7 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
     k_vc_restrict<T><<<grid_nodes(C.nn), kRowThreads, 0, st>>>(
         F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, C.mask, (const T*)F.r, (T*)C.b,
         c_coarsest ? nullptr : dinv_of<T>(C), omega, c_coarsest ? nullptr : (T*)C.v);
-  vcycle_rec<T>(lv, l + 1, L, omega, Ainv, tc, st);
+  vcycle_rec<T>(lv, l + 1, L, omega, Ainv, tc, st, nullptr);
   if (C.ptab != nullptr)
     launch_s2_prolong(vt_code<T>(), F, C, C.ptab, st);
   else
@@ -745,16 +781,22 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
       launch_tc_apply(F, tc.m, (const float*)F.v, tc.w32, tc.KT, tc.Ye, tc.err, tc.sms, st);
       launch_tc_gather(F, tc.Ye, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 1,
                        (float*)F.z, st);
-      return;
+      return false;
     }
   }
   if (F.k >= 2) {
     launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, 1, F.z,
                  F.sms, st);
-    return;
+    return false;
+  }
+  if (dots != nullptr) {
+    TILE_ORD(V, (k_vc_post_dots<T, kOrd><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(
+                    V, omega, (const T*)F.b, (const T*)F.v, (T*)F.z, *dots)));
+    return true;
   }
   TILE_ORD(V, (k_vc_post<T, kOrd><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(
                   V, omega, (const T*)F.b, (const T*)F.v, (T*)F.z)));
+  return false;
 }
 
 }  // namespace
@@ -774,10 +816,12 @@ void vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
     }                                         \
   } while (0)
 
-void launch_vcycle(int vt, Level* lv, int L, double omega, int gamma, const double* Ainv,
-                   const TcOp& tc, cudaStream_t st) {
+bool launch_vcycle(int vt, Level* lv, int L, double omega, int gamma, const double* Ainv,
+                   const TcOp& tc, cudaStream_t st, const CgDots* dots) {
   (void)gamma;
-  VT_DISPATCH(vt, vcycle_rec<T>(lv, 0, L, (T)omega, Ainv, tc, st));
+  bool fused = false;
+  VT_DISPATCH(vt, fused = vcycle_rec<T>(lv, 0, L, (T)omega, Ainv, tc, st, dots));
+  return fused;
 }
 
 void launch_set_params(DevState* ds, const double* params, cudaStream_t st) {
@@ -868,6 +912,8 @@ cudaError_t allow_tile_smem() {
   cudaError_t e = cudaFuncSetAttribute(k_vc_pre<T, kOrd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_vc_post<T, kOrd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vc_post_dots<T, kOrd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_apply_diag<T, kOrd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)

@@ -320,8 +320,9 @@ cudaError_t append_solve(tosolve_s* h, cudaStream_t cs, cudaStream_t bs) {
   if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, bs);
-    launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, bs);
+    const CgDots cd{h->r, h->q, part2, part3, h->ds, h->cnt + 1};
+    if (!launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, bs, &cd))
+      launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, bs);
     launch_cg_dir(vt, L0, h->p, np, h->ds, bs);
     launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, bs);
     launch_cg_update(vt, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, hc, 1,
@@ -1132,8 +1133,9 @@ static tosolve_status run_loop_nograph(tosolve_t h) {
   CK(cudaMemcpyAsync(h->hs, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   while (!h->hs->converged && h->hs->status == 0 && h->hs->iter < h->hs->maxit) {
-    launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, st);
-    launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, st);
+    const CgDots cd{h->r, h->q, part2, part3, h->ds, h->cnt + 1};
+    if (!launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, st, &cd))
+      launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, st);
     launch_cg_dir(vt, L0, h->p, np, h->ds, st);
     launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, st);
     launch_cg_update(vt, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, 0, 0,
