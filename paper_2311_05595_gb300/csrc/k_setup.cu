@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <functional>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -751,12 +752,11 @@ void launch_elem_moments(bool fp64, const Level& L, int ze0, int ze1, const doub
     else
       k_moments_block<double><<<E, N * N >= 256 ? 256 : 64, 0, st>>>(L.ex, L.ey, ze0, N, w, Dx, Dy, M);
     const size_t sm = (size_t)(27 * kSym + 32 * 27) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;  // handles may be created from several threads
+    std::call_once(attr, [sm] {
       cudaFuncSetAttribute(k_moments_to_ke<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm);
-      attr = true;
-    }
+    });
     k_moments_to_ke<double, double><<<gk, 256, sm, st>>>(E, L.h, M, cmom, (double*)Ke);
   } else {
     float* M = (float*)Mscr;
@@ -766,12 +766,11 @@ void launch_elem_moments(bool fp64, const Level& L, int ze0, int ze1, const doub
     else
       k_moments_block<float><<<E, N * N >= 256 ? 256 : 64, 0, st>>>(L.ex, L.ey, ze0, N, w, Dx, Dy, M);
     const size_t sm = (size_t)(27 * kSym + 32 * 27) * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;  // handles may be created from several threads
+    std::call_once(attr, [sm] {
       cudaFuncSetAttribute(k_moments_to_ke<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm);
-      attr = true;
-    }
+    });
     k_moments_to_ke<float, float><<<gk, 256, sm, st>>>(E, L.h, M, cmom, (float*)Ke);
   }
 }

@@ -15,6 +15,7 @@
 // bounded (on timeout the kernel raises an error flag, waits once more,
 // frees its TMEM and returns).
 #include <cstdint>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -252,12 +253,12 @@ cudaError_t launch_tc_apply(const Level& L0, int m, const float* v, const float*
   const long E = (long)L0.ex * L0.ey * L0.ez;
   const long ntiles = (E + kTcM - 1) / kTcM;
   const size_t sm = kTcASize + kTcBSize;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_stacked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag attr;  // handles may be created from several threads
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr, [sm] {
+    attr_err = cudaFuncSetAttribute(k_tc_stacked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   const long cap = 2L * sms;  // two CTAs per SM: 2 x 256 TMEM columns fit in 512
   const int g = (int)(ntiles < cap ? ntiles : cap);
   k_tc_stacked<<<g, kTcM, sm, st>>>(L0.ex, L0.ey, L0.ez, m, L0.Lx, L0.Ly, v, w32, KT, Ye, err);
