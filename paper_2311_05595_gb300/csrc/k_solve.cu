@@ -112,12 +112,18 @@ __device__ __forceinline__ T plane_row(const LevelView<T>& V, const op_t<T>* __r
   const long sy[3] = {j > 0 ? -(long)V.Lx : 0L, 0L, j + 1 < V.Ly ? (long)V.Lx : 0L};
   const long zoff = g == 0 ? (l > 0 ? -(long)V.Lx * V.Ly : 0L) : g == 1 ? 0L
                                                                    : (l + 1 < V.Lz ? (long)V.Lx * V.Ly : 0L);
+  // Three accumulators, each product fused into one of them: 27 FMAs per
+  // partial (FP64 issue is the scarce resource on this part), with three
+  // independent dependency chains per thread.
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
     const long nb = node + sx[q % 3] + sy[q / 3] + zoff;
     const op_t<T>* s = sb + ((9 * g + q) * 9 + 3 * r) * kTN;
-    acc[q % 3] += s[0] * ld(nb, 0) + s[kTN] * ld(nb, 1) + s[2 * kTN] * ld(nb, 2);
+    T& a = acc[q % 3];
+    a = fma(s[0], ld(nb, 0), a);
+    a = fma(s[kTN], ld(nb, 1), a);
+    a = fma(s[2 * kTN], ld(nb, 2), a);
   }
   return (acc[0] + acc[1]) + acc[2];
 }
