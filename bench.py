@@ -44,8 +44,8 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # gather together), valid while the kernel source is unchanged (keyed by the
 # kernel, the source hash and the workload).
 NCU_TRAFFIC = {
-    ("k_apply_diag<double>", "75a140ca457b", "cantilever_mr_96x48x48_q1_48x24x24_n2"):
-        60347904 + 87296,
+    ("k_apply_diag<double>", "dae7917f3f1e", "cantilever_mr_96x48x48_q1_48x24x24_n2"):
+        60348672 + 90624,
     ("k_q2_apply<double>", "a9e36f7df2c6", "bridge_q2_64x32x32_n3_density_192x96x96"):
         3500955648 + 44271872 + 44121088 + 1024,
 }

@@ -36,6 +36,12 @@ namespace {
 // tiles.  The operand vector is read from global memory (L1/L2: each value
 // is used by 27 neighbours and 3 rows).
 constexpr int kTileThreads = 9 * kTN;  // 3 rows x 3 neighbour planes
+// FP64 tiles take one more warp: the 9 (plane, row) partials would sit
+// 3/2/2/2 on the SM's four sub-partitions, and FP64 issue is the scarce
+// resource, so the last partial is split over two warps (sub-partitions 0
+// and 1): 90/61/61/58 FP64 instructions per tile become 76/76/61/58.
+template <typename T>
+constexpr int tile_threads() { return std::is_same<T, double>::value ? kTileThreads + 32 : kTileThreads; }
 constexpr int kStages = 3;
 constexpr long kTileSpin = 1L << 22;  // bound of every mbarrier wait
 
@@ -107,7 +113,7 @@ using partial_t = typename Partial<T>::type;
 
 template <typename T, typename LD>
 __device__ __forceinline__ T plane_row(const LevelView<T>& V, const op_t<T>* __restrict__ sb, long node,
-                                       int i, int j, int l, int r, int g, LD ld) {
+                                       int i, int j, int l, int r, int g, LD ld, int qlo = 0, int qhi = 9) {
   const long sx[3] = {i > 0 ? -1L : 0L, 0L, i + 1 < V.Lx ? 1L : 0L};
   const long sy[3] = {j > 0 ? -(long)V.Lx : 0L, 0L, j + 1 < V.Ly ? (long)V.Lx : 0L};
   const long zoff = g == 0 ? (l > 0 ? -(long)V.Lx * V.Ly : 0L) : g == 1 ? 0L
@@ -118,6 +124,7 @@ __device__ __forceinline__ T plane_row(const LevelView<T>& V, const op_t<T>* __r
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
+    if (q < qlo || q >= qhi) continue;  // warp-uniform: neighbours [qlo, qhi) only
     const long nb = node + sx[q % 3] + sy[q / 3] + zoff;
     const op_t<T>* s = sb + ((9 * g + q) * 9 + 3 * r) * kTN;
     T& a = acc[q % 3];
@@ -133,7 +140,8 @@ __device__ __forceinline__ T plane_row(const LevelView<T>& V, const op_t<T>* __r
 // FP32's precision at a few FP32 operations per coefficient.
 template <typename LD>
 __device__ __forceinline__ Dot2 plane_row(const LevelView<dfloat>& V, const float* __restrict__ sb,
-                                          long node, int i, int j, int l, int r, int g, LD ld) {
+                                          long node, int i, int j, int l, int r, int g, LD ld,
+                                          int qlo = 0, int qhi = 9) {
   const long sx[3] = {i > 0 ? -1L : 0L, 0L, i + 1 < V.Lx ? 1L : 0L};
   const long sy[3] = {j > 0 ? -(long)V.Lx : 0L, 0L, j + 1 < V.Ly ? (long)V.Lx : 0L};
   const long zoff = g == 0 ? (l > 0 ? -(long)V.Lx * V.Ly : 0L) : g == 1 ? 0L
@@ -141,6 +149,7 @@ __device__ __forceinline__ Dot2 plane_row(const LevelView<dfloat>& V, const floa
   Dot2 acc[3];
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
+    if (q < qlo || q >= qhi) continue;
     const long nb = node + sx[q % 3] + sy[q / 3] + zoff;
     const float* s = sb + ((9 * g + q) * 9 + 3 * r) * kTN;
     acc[q % 3].add(s[0], ld(nb, 0));
@@ -177,10 +186,15 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
   using O = op_t<T>;
   using PT = partial_t<T>;
   constexpr uint32_t kBytes = tile_bytes<T>();
+  constexpr bool kSplit = tile_threads<T>() > kTileThreads;
   __shared__ PT parts[3][kTileThreads / 3];
+  __shared__ PT tail[kSplit ? kTN : 1];  // second half of the (g 2, row 2) partial
   O* sbuf = reinterpret_cast<O*>(tsm);
   uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + (size_t)kStages * kBytes);
-  const int tid = threadIdx.x, g = tid / 96, rl = tid % 96, r = rl >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const bool extra = kSplit && w == 9;  // the tenth warp: plane 2, row 2, neighbours 5..8
+  const int g = extra ? 2 : w / 3, r = extra ? 2 : w % 3, rl = 32 * r + lane;
+  const int qlo = extra ? 5 : 0, qhi = (kSplit && w == 8) ? 5 : 9;
   const long ntiles = ((long)V.nn + kTN - 1) / kTN;
   const long nact = kOrd ? *V.tcnt : ntiles;
   auto tile_at = [&](long q) { return kOrd ? (long)V.tl[q] : q; };
@@ -204,14 +218,25 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
     const long node = tile_at(blockIdx.x + k * gridDim.x) * kTN + lane;
     const bool live = node < V.nn;
     const int i = node % V.Lx, j = (node / V.Lx) % V.Ly, l = node / ((long)V.Lx * V.Ly);
-    if (live) parts[g][rl] = plane_row(V, sbuf + (size_t)s * 243 * kTN + lane, node, i, j, l, r, g, ld);
+    if (live) {
+      const PT part = plane_row(V, sbuf + (size_t)s * 243 * kTN + lane, node, i, j, l, r, g, ld, qlo, qhi);
+      if (extra) tail[lane] = part;
+      else parts[g][rl] = part;
+    }
     __syncthreads();  // stage s is free; the three parts are in
     if (tid == 0 && k + kStages < nk) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tile_issue(tsm + (size_t)s * kBytes,
                  gsrc + (size_t)tile_at(blockIdx.x + (k + kStages) * gridDim.x) * kBytes, kBytes, &bars[s]);
     }
-    if (g == 0 && live) row(node, r, sum3(parts[0][rl], parts[1][rl], parts[2][rl]));
+    if (g == 0 && !extra && live) {
+      if constexpr (kSplit) {
+        const PT p2 = r == 2 ? parts[2][rl] + tail[lane] : parts[2][rl];
+        row(node, r, sum3(parts[0][rl], parts[1][rl], p2));
+      } else {
+        row(node, r, sum3(parts[0][rl], parts[1][rl], parts[2][rl]));
+      }
+    }
     __syncthreads();  // parts are free
   }
   if (k < nk && tid == 0) {  // timed out: flag, then let the copies in flight land
@@ -220,7 +245,7 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
       tile_wait(&bars[q % kStages], (uint32_t)((q / kStages) & 1));
   }
   if (!kOrd || k < nk) return;
-  if (g == 0)  // tiles of fixed DOFs only: identity rows
+  if (g == 0 && !extra)  // tiles of fixed DOFs only: identity rows
     for (long q = nact + blockIdx.x; q < ntiles; q += gridDim.x) {
       const long node = tile_at(q) * kTN + lane;
       if (node < V.nn) row(node, r, (T)ld(node, r));
@@ -288,7 +313,7 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle hc, int use_
 // ---- multigrid cycle ------------------------------------------------------
 
 template <typename T, bool kOrd>
-__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_vc_pre(LevelView<T> V, const T* __restrict__ b,
+__global__ void __launch_bounds__(tile_threads<T>(), tile_blocks_per_sm<T>()) k_vc_pre(LevelView<T> V, const T* __restrict__ b,
                                                         const T* __restrict__ v, T* __restrict__ r_out) {
   for_each_row<kOrd>(V, [&](long nb, int c) { return ld_nc(v + 3 * nb + c); }, [&](long node, int r, T y) {
     const long d = 3 * node + r;
@@ -384,7 +409,7 @@ __global__ void k_vc_prolong(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc,
 
 // Post-smoothing: z = v + omega D^-1 (b - A v).
 template <typename T, bool kOrd>
-__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_vc_post(LevelView<T> V, T omega, const T* __restrict__ b,
+__global__ void __launch_bounds__(tile_threads<T>(), tile_blocks_per_sm<T>()) k_vc_post(LevelView<T> V, T omega, const T* __restrict__ b,
                                                          const T* __restrict__ v, T* __restrict__ z) {
   for_each_row<kOrd>(V, [&](long nb, int c) { return ld_nc(v + 3 * nb + c); }, [&](long node, int r, T y) {
     const long d = 3 * node + r;
@@ -396,7 +421,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_vc_po
 // reduction that follows it (k_cg_dots_rz): partial r^T z and z^T q over
 // the rows this block writes; the last block forms beta.
 template <typename T, bool kOrd>
-__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>())
+__global__ void __launch_bounds__(tile_threads<T>(), tile_blocks_per_sm<T>())
     k_vc_post_dots(LevelView<T> V, T omega, const T* __restrict__ b, const T* __restrict__ v,
                    T* __restrict__ z, CgDots cd) {
   double a = 0.0, c = 0.0;
@@ -477,7 +502,7 @@ __global__ void k_cg_prep(int nn, const uint8_t* __restrict__ mask, double* __re
 // convergence test (||f||^2 from part_ff) and sets the loop condition;
 // mode 2 (after the loop): the last block stores the true residual.
 template <typename T, bool kOrd>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(tile_threads<double>())
     k_cg_residual(LevelView<double> V, const double* __restrict__ f, const double* __restrict__ u,
                   double* __restrict__ rv, T* __restrict__ b0, const op_t<T>* __restrict__ dinv0,
                   T omega, T* __restrict__ v0, double* part, const double* part_ff, int np_ff,
@@ -560,7 +585,7 @@ __global__ void k_cg_dir(int nn, const T* __restrict__ z, double* __restrict__ p
 // q = K p (FP64) and partial p^T q; the last block forms alpha = rz / p^T q
 // (a non-positive or non-finite value is a breakdown).
 template <bool kOrd>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(tile_threads<double>())
     k_cg_apply(LevelView<double> V, const double* __restrict__ p, double* __restrict__ q, double* part,
                DevState* __restrict__ ds, unsigned* cnt) {
   double s = 0.0;
@@ -681,7 +706,7 @@ __global__ void k_cg_update(int nn, double* __restrict__ u, double* __restrict__
 
 // Diagnostic: y = A x in the level's stored precision, FP64 in and out.
 template <typename T, bool kOrd>
-__global__ void __launch_bounds__(kTileThreads, tile_blocks_per_sm<T>()) k_apply_diag(LevelView<T> V, const double* __restrict__ x,
+__global__ void __launch_bounds__(tile_threads<T>(), tile_blocks_per_sm<T>()) k_apply_diag(LevelView<T> V, const double* __restrict__ x,
                                                             double* __restrict__ y) {
   for_each_row<kOrd>(V, [&](long nb, int c) { return (T)ld_nc(x + 3 * nb + c); },
                [&](long node, int r, T v) { y[3 * node + r] = (double)v; });
@@ -767,7 +792,7 @@ bool vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
     launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, 0, F.r,
                  F.sms, st);
   else if (!use_tc)
-    TILE_ORD(V, (k_vc_pre<T, kOrd><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(
+    TILE_ORD(V, (k_vc_pre<T, kOrd><<<tile_grid<T>(F), tile_threads<T>(), tile_smem<T>(), st>>>(
                     V, (const T*)F.b, (const T*)F.v, (T*)F.r)));
   if (C.ptab != nullptr)  // the coarse shape functions and their transpose
     launch_s2_restrict(vt_code<T>(), F, C, C.ptab, c_coarsest ? nullptr : dinv_of<T>(C), (double)omega,
@@ -796,11 +821,11 @@ bool vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
     return false;
   }
   if (dots != nullptr) {
-    TILE_ORD(V, (k_vc_post_dots<T, kOrd><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(
+    TILE_ORD(V, (k_vc_post_dots<T, kOrd><<<tile_grid<T>(F), tile_threads<T>(), tile_smem<T>(), st>>>(
                     V, omega, (const T*)F.b, (const T*)F.v, (T*)F.z, *dots)));
     return true;
   }
-  TILE_ORD(V, (k_vc_post<T, kOrd><<<tile_grid<T>(F), kTileThreads, tile_smem<T>(), st>>>(
+  TILE_ORD(V, (k_vc_post<T, kOrd><<<tile_grid<T>(F), tile_threads<T>(), tile_smem<T>(), st>>>(
                   V, omega, (const T*)F.b, (const T*)F.v, (T*)F.z)));
   return false;
 }
@@ -856,7 +881,7 @@ void launch_cg_residual(int vt, const Level& L0, double omega, const double* f, 
     return;
   }
   const LevelView<double> V0 = view<double>(L0);
-  VT_DISPATCH(vt, TILE_ORD(V0, (k_cg_residual<T, kOrd><<<tile_grid<double>(L0), kTileThreads,
+  VT_DISPATCH(vt, TILE_ORD(V0, (k_cg_residual<T, kOrd><<<tile_grid<double>(L0), tile_threads<double>(),
                                                          tile_smem<double>(), st>>>(
                                    V0, f, u, r, (T*)L0.b, dinv_of<T>(L0), (T)omega, (T*)L0.v, part,
                                    part_ff, np, mode, ds, cnt, hc, use_cond))));
@@ -881,7 +906,7 @@ void launch_cg_apply(const Level& L0, const double* p, double* q, double* part, 
     return;
   }
   const LevelView<double> V0 = view<double>(L0);
-  TILE_ORD(V0, (k_cg_apply<kOrd><<<tile_grid<double>(L0), kTileThreads, tile_smem<double>(), st>>>(
+  TILE_ORD(V0, (k_cg_apply<kOrd><<<tile_grid<double>(L0), tile_threads<double>(), tile_smem<double>(), st>>>(
                    V0, p, q, part, ds, cnt)));
 }
 
@@ -907,7 +932,7 @@ void launch_apply_diag(int vt, const Level& L, const double* x, double* y, cudaS
     launch_vec_out(vt, nd, L.r, y, st);
     return;
   }
-  VT_DISPATCH(vt, TILE_ORD(view<T>(L), (k_apply_diag<T, kOrd><<<tile_grid<T>(L), kTileThreads,
+  VT_DISPATCH(vt, TILE_ORD(view<T>(L), (k_apply_diag<T, kOrd><<<tile_grid<T>(L), tile_threads<T>(),
                                                                    tile_smem<T>(), st>>>(view<T>(L), x, y))));
 }
 
