@@ -331,6 +331,18 @@ __host__ __device__ inline int sym_index(int r, int c) {
   return r * kEdofQ1 - (r * (r - 1)) / 2 + (c - r);
 }
 
+// x^p of the SIMP law (Eq. matrixK): repeated products when p is a small
+// non-negative integer (the paper's p = 3), else pow.  FP64 is scarce on
+// this part and pow costs dozens of FP64 instructions.
+__device__ __forceinline__ double simp_pow(double x, double p) {
+  if (p >= 0.0 && p <= 8.0 && (double)(int)p == p) {
+    double r = 1.0;
+    for (int q = 0; q < (int)p; ++q) r *= x;
+    return r;
+  }
+  return pow(x, p);
+}
+
 }  // namespace tos
 
 // The opaque handle of the C ABI.

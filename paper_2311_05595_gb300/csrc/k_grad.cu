@@ -14,11 +14,14 @@ __global__ void k_energy_grad(int ex, int ey, int ez, int n, int Lx, int Ly,
                               const double* __restrict__ rho, double penal, double dE, int Dx,
                               int Dy, int first, double* __restrict__ g) {
   const int m = n * n * n;
-  const long total = (long)ex * ey * ez * m;
+  const long E = (long)ex * ey * ez;
+  const long total = E * m;
+  // subcell-major: the lanes of a warp share the subcell s (its 300-entry
+  // table is read once per warp) and take consecutive elements
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
        t += (long)gridDim.x * blockDim.x) {
-    const long e = t / m;
-    const int s = t % m;
+    const long e = t % E;
+    const int s = (int)(t / E);
     const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
     double ue[kEdofQ1];
 #pragma unroll
@@ -42,7 +45,7 @@ __global__ void k_energy_grad(int ex, int ey, int ez, int n, int Lx, int Ly,
     en *= 2.0;
     const int a = s % n, b = (s / n) % n, c = s / (n * n);
     const long cell = (n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c));
-    const double gv = -penal * pow(rho[cell], penal - 1.0) * dE * en;
+    const double gv = -penal * simp_pow(rho[cell], penal - 1.0) * dE * en;
     g[cell] = first ? gv : g[cell] + gv;
   }
 }

@@ -175,7 +175,7 @@ __global__ void k_proj_fwd(ProjGrid P, const double* __restrict__ invom, const d
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
     const double r = proj_row(P, c, x) * invom[c];
     rho[c] = r;
-    w[c] = Emin + pow(r, penal) * dE;
+    w[c] = Emin + simp_pow(r, penal) * dE;
   }
 }
 
@@ -197,7 +197,7 @@ __global__ void k_filter_fwd(int Dx, int Dy, int Dz, int noff, const int4* __res
     }
     const double r = s * invom[c];
     rho[c] = r;
-    w[c] = Emin + pow(r, penal) * dE;
+    w[c] = Emin + simp_pow(r, penal) * dE;
   }
 }
 
