@@ -312,11 +312,13 @@ def run_gpu(args):
 
     sampler = ClockSampler(local)
     out = {}
-    precs = {"fp32": T.PREC_FP32, "tf32": T.PREC_TF32, "fp32x2": T.PREC_FP32X2, "fp64": T.PREC_FP64}
-    mixed_labels = tuple(v for v in args.variants.split(",") if v != "fp64"
-                         and not (v == "tf32" and p.degree != 1))
+    precs = {"fp32": T.PREC_FP32, "tf32": T.PREC_TF32, "fp32x2": T.PREC_FP32X2, "bf16": T.PREC_BF16,
+             "bf16x3": T.PREC_BF16X3, "f16x3": T.PREC_F16X3, "fp64": T.PREC_FP64}
+    q2tc = p.degree == 2 and p.elem_q1 is None
+    tc_ok = {"tf32": p.degree == 1 or q2tc, "bf16": q2tc, "bf16x3": q2tc, "f16x3": q2tc}
+    mixed_labels = tuple(v for v in args.variants.split(",") if v != "fp64" and tc_ok.get(v, True))
     if not mixed_labels or any(v not in precs for v in mixed_labels):
-        raise SystemExit("--variants: a comma list of fp32, tf32, fp32x2 (fp64 always runs)")
+        raise SystemExit("--variants: a comma list of fp32, tf32, bf16, bf16x3, f16x3, fp32x2 (fp64 always runs)")
     solvers = {lab: make(precs[lab]) for lab in mixed_labels + ("fp64",)}
     sampler.start()
     for label in mixed_labels + ("fp64",):

@@ -12,7 +12,7 @@
  *
  * Mesh and numbering (shared by every call):
  *   * nx*ny*nz cubic displacement elements of edge 1 (Sec. 7.1);
- *   * Lagrange degree k (1 or 2): node lattice (k*nx+1)*(k*ny+1)*(k*nz+1),
+ *   * Lagrange degree k (1, 2 or 3): node lattice (k*nx+1)*(k*ny+1)*(k*nz+1),
  *     node id = i + Lx*(j + Ly*l) (x fastest), DOF = 3*node + component;
  *   * each element holds n_mr^3 density cells (Sec. 3.1): the density grid
  *     is (n_mr*nx)*(n_mr*ny)*(n_mr*nz) cells, flattened x fastest; the
@@ -67,18 +67,30 @@ typedef enum {
   TOSOLVE_PREC_TF32 = 2, /* as FP32, but the finest level's operator is the  */
                          /* stacked subcell contraction of Eq. matrixK_mr on */
                          /* the tcgen05 tensor cores (TF32 operands, FP32    */
-                         /* accumulation in TMEM); needs n_mr <= 2           */
-  TOSOLVE_PREC_FP32X2 = 3 /* FP32 V-cycle operators (formed in FP64, then    */
+                         /* accumulation in TMEM); degree 1 with n_mr <= 2,  */
+                         /* or Lagrange degree 2 with n_mr <= 3 (not mixed)  */
+  TOSOLVE_PREC_FP32X2 = 3, /* FP32 V-cycle operators (formed in FP64, then   */
                          /* rounded) and vectors held as float pairs: about */
                          /* 48-bit arithmetic on the FP32 pipes, for        */
                          /* high-contrast densities where FP32 vectors slow */
                          /* convergence                                     */
+  TOSOLVE_PREC_BF16 = 4, /* as TF32 with BF16 operands (8-bit mantissas) and */
+                         /* FP32 accumulation: Lagrange degree 2 with       */
+                         /* n_mr <= 3 (not mixed)                           */
+  TOSOLVE_PREC_BF16X3 = 5, /* degree 2 as BF16, each operand split into a   */
+                         /* BF16 pair (hi + lo, about 16 bits) and three    */
+                         /* products hi hi + lo hi + hi lo                  */
+  TOSOLVE_PREC_F16X3 = 6 /* degree 2 as BF16X3 with FP16 pairs (about 22   */
+                         /* bits; vectors scaled per element and the table  */
+                         /* globally by powers of two into FP16's range):   */
+                         /* FP32-class operator accuracy at the FP16 tensor */
+                         /* rate                                            */
 } tosolve_precision;
 
 /* Problem and solver description (Sec. 2, 3.1, 7 intro). */
 typedef struct {
   int nx, ny, nz;         /* displacement elements per axis, >= 1           */
-  int degree;             /* degree k: 1 or 2 (see family)                  */
+  int degree;             /* degree k: 1, 2 or 3 (see family)               */
   int n_mr;               /* density cells per element edge, 1..8           */
   int d_mr;               /* design cells per element edge, 1..n_mr (0 =   */
                           /* n_mr); below n_mr rmin must be > 0            */
@@ -451,10 +463,11 @@ tosolve_status tosolve_densities(tosolve_t h, double* rho_dev, double* w_dev);
 
 /* y = A_l x for the level-l operator (fixed rows/columns replaced by
  * identity), computed in FP64 (precision 0), in the preconditioner's FP32
- * stencil form (precision 1), on level 0 of a TF32 handle as the
- * tensor-core stacked contraction plus node gather (precision 2), or with
- * the FP32 stencil and float-pair arithmetic of FP32X2 (precision 3); inputs
- * and outputs are FP64.  x_dev, y_dev: 3*nodes(l).
+ * stencil or element form (precision 1), on level 0 of a tensor-core handle
+ * as the stacked contraction plus node gather (precision 2, 4, 5 or 6: the
+ * handle's own), or with the FP32 operator and float-pair arithmetic of
+ * FP32X2 (precision 3); inputs and outputs are FP64.  x_dev, y_dev:
+ * 3*nodes(l).
  * Level 0 FP64 is K(rho) of Eq. matrixK_mr; coarser levels are re-discretised
  * from the density field (Sec. 7.2: system matrices of each mesh level). */
 tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double* x_dev,

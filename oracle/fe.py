@@ -26,6 +26,24 @@ def simp_weights(rho: np.ndarray, E0: float, Emin: float, p: float) -> np.ndarra
     return Emin + rho ** p * (E0 - Emin)
 
 
+def rigid_projector(k: int) -> np.ndarray:
+    """(d, d) orthogonal projector onto the complement of the six rigid
+    motions (translations, infinitesimal rotations omega x x) of one element
+    of degree k, in the Euclidean inner product of its d = 3 (k+1)^3 nodal
+    values, nodes at reference positions -1 + 2 a / k (lattice order, x
+    fastest).  Rigid motions carry no strain, so K^(e_i) P = K^(e_i)."""
+    na = k + 1
+    pos = np.array([[-1.0 + 2.0 * ax / k, -1.0 + 2.0 * ay / k, -1.0 + 2.0 * az / k]
+                    for az in range(na) for ay in range(na) for ax in range(na)])
+    nn = pos.shape[0]
+    R = np.zeros((3 * nn, 6))
+    for a, (x, y, z) in enumerate(pos):
+        R[3 * a: 3 * a + 3, 0:3] = np.identity(3)
+        R[3 * a: 3 * a + 3, 3:6] = [[0.0, z, -y], [-z, 0.0, x], [y, -x, 0.0]]  # omega x pos
+    Q, _ = np.linalg.qr(R)
+    return np.identity(3 * nn) - Q @ Q.T
+
+
 class Model:
     """Everything the oracle needs for one problem (see workloads.Problem)."""
 
@@ -74,6 +92,31 @@ class Model:
         y = self.assemble(w_e) @ uf
         y[mask] = u[mask]
         return y
+
+    def subcell_scale(self, w_e: np.ndarray, u: np.ndarray, deflate: bool = False,
+                      elem_max: bool = False) -> np.ndarray:
+        """Per DOF, sum over the elements e and subcells i of
+        w_{e,i} (|K^(e_i)| |u_e|): the scale of the rounding error of the
+        stacked form of Eq. matrixK_mr, which forms each subcell's product
+        K^(e_i) u_e on its own before the weighted sum (supports: |u|, as
+        identity rows; their columns are zero as in apply).  deflate: u_e
+        minus its least-squares rigid motion (rigid_projector), which every
+        K^(e_i) annihilates, in place of u_e.  elem_max: every |u_e| entry
+        replaced by max |u_e| (the scale of errors relative to an element's
+        largest value, as a power-of-two scaled 16-bit split makes)."""
+        mask = self.p.mask.astype(bool)
+        ue = np.where(mask, 0.0, u)[self.edofs]  # (E, d)
+        if deflate:
+            ue = ue @ rigid_projector(self.k).T
+        ua = np.abs(ue)
+        if elem_max:
+            ua = np.repeat(ua.max(axis=1, keepdims=True), ua.shape[1], axis=1)
+        z = np.einsum("eid,idf,ef->ed", np.broadcast_to(w_e[:, :, None], w_e.shape + (self.Ktab.shape[1],)),
+                      np.abs(self.Ktab), ua, optimize=True)
+        out = np.zeros(self.ndof)
+        np.add.at(out, self.edofs, z)
+        out[mask] = np.abs(u[mask])
+        return out
 
     # -- solve -----------------------------------------------------------
     def solve(self, w_e: np.ndarray, f: np.ndarray, method: str = "auto",

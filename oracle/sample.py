@@ -17,7 +17,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import fem, filt
-from .fe import simp_weights
+from .fe import rigid_projector, simp_weights
 
 
 class Sampler:
@@ -138,6 +138,36 @@ class Sampler:
                 dofs = np.array([3 * m + c for m in en for c in range(3)])
                 a = en.index(nd)
                 out[q] += Kr[3 * a: 3 * a + 3] @ uf[dofs]
+            for c in range(3):
+                if held[3 * nd + c]:
+                    out[q, c] = abs(u[3 * nd + c])
+        return out
+
+    def apply_rows_subcell_scale(self, x, u, nodes, deflate=False, elem_max=False):
+        """(len(nodes), 3): sum over the elements e at the node and their
+        subcells i of w_{e,i} sum_j |K^(e_i)_rj| |u_j| -- the rounding scale
+        of the stacked form of Eq. matrixK_mr (one rounded product per
+        subcell); supports |u|.  Trilinear/triquadratic mixing not covered."""
+        if self.slv is not None:
+            raise ValueError("subcell scale of a mixed mesh is not defined here")
+        held = self.p.mask.astype(bool)
+        uf = np.where(held, 0.0, u)
+        P = rigid_projector(self.k) if deflate else None
+        cache = {}
+        out = np.zeros((len(nodes), 3))
+        for q, nd in enumerate(nodes):
+            for (ex, ey, ez) in self.elements_of(nd):
+                cells = self._elem_cells(ex, ey, ez)
+                rho = np.array([cache.setdefault(c, self.rho(x, c)) for c in cells])
+                w = simp_weights(rho, self.p.E0, self.p.Emin, self.p.penal)
+                en = self._elem_nodes(ex, ey, ez)
+                dofs = np.array([3 * m + c for m in en for c in range(3)])
+                ue = np.abs(uf[dofs] if P is None else P @ uf[dofs])
+                if elem_max:
+                    ue = np.full_like(ue, ue.max())
+                a = en.index(nd)
+                for i in range(len(cells)):
+                    out[q] += w[i] * (np.abs(self.K[i][3 * a: 3 * a + 3]) @ ue)
             for c in range(3):
                 if held[3 * nd + c]:
                     out[q, c] = abs(u[3 * nd + c])

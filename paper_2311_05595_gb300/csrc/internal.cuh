@@ -188,10 +188,16 @@ int coarse_sweep_grid();
 // Finest-level operator of the TF32 preconditioner on tcgen05.
 struct TcOp {
   bool on = false;
+  int deg = 1;              // Lagrange degree of the finest level
+  int mode = 0;             // degree 2: operands (tc2_mode_of: TF32, BF16, BF16X3, F16X3)
+  int prec = 0;             // degree 2: the tosolve_precision this mode serves
+  float tscale = 1.f;       // degree 2, F16X3: power-of-two scale of the table image
   int m = 1;                // subcells per element
   const float* w32 = nullptr;  // E x m element-major weights
-  const float* KT = nullptr;   // m x 24 x 24 FP32 table
-  float* Ye = nullptr;         // E x 24 element results
+  const float* KT = nullptr;   // degree 1: m x 24 x 24 FP32 table
+  float* Ye = nullptr;         // degree 1: E x 24 element results
+  const unsigned char* img = nullptr;  // degree 2: stacked table in the shared-memory image
+  float* Y2 = nullptr;         // degree 2: E x tc2_result_stride() element results
   int* err = nullptr;
   int sms = 1;
 };
@@ -205,6 +211,32 @@ void launch_tc_gather(const Level& L0, const float* Ye, const float* b, const fl
 void launch_weights_elem(const Level& L0, int n, const double* w, int Dx, int Dy, float* w32,
                          cudaStream_t st);
 void launch_mask_fp32(const Level& L, float* x, cudaStream_t st);
+
+// ---- launchers (k_tc2.cu): degree-2 finest level on tcgen05 ---------------
+// n_mr with a tensor-core kernel for degree 2 (m = n^3 subcells: 1, 8, 27).
+bool tc2_supported(int n);
+// Operand mode of a tensor-core precision: TF32 0, BF16 1, BF16X3 2, F16X3 3.
+inline int tc2_mode_of(int precision) {
+  return precision == TOSOLVE_PREC_TF32 ? 0 : precision == TOSOLVE_PREC_BF16 ? 1
+                                         : precision == TOSOLVE_PREC_BF16X3 ? 2 : 3;
+}
+// Bytes of the stacked table's shared-memory image for an operand mode.
+size_t tc2_image_bytes(int mode, int m);
+// Floats per element in the result buffer (81 rounded up to 16 bytes).
+size_t tc2_result_stride();
+// Power-of-two scale of the table image (F16X3: largest entry into
+// [0.5, 1) after dividing by it; else 1), from the host copy of the table.
+float tc2_table_scale(int mode, const double* tab_host, size_t count);
+void launch_tc2_image(int mode, int m, const double* tab, float tscale, unsigned char* img, cudaStream_t st);
+// Y = per-element stacked contraction of the level-0 vector v (fixed DOFs as
+// zero), weights w32 (E x m).
+cudaError_t launch_tc2_apply(int mode, int m, const Level& L0, const float* v, const float* w32,
+                             const unsigned char* img, float tscale, float* Y, int* err, int sms,
+                             cudaStream_t st);
+// Node gather of Y fused with the V-cycle step: mode 0 b - y, 1 v + omega
+// D^-1 (b - y), 2 y; identity rows at fixed DOFs.
+void launch_tc2_gather(const Level& L0, const float* Y, const float* b, const float* v, const float* dinv,
+                       float omega, int mode, float* out, cudaStream_t st);
 
 // ---- launchers (k_solve.cu) ----------------------------------------------
 template <typename T>
@@ -392,6 +424,8 @@ struct tosolve_s {
   float* KT32 = nullptr;       // m x 24 x 24 FP32 (tensor-core operand)
   float* w32 = nullptr;        // E x m element-major FP32 weights
   float* Ye = nullptr;         // E x 24 element results of the tensor-core apply
+  unsigned char* tcimg = nullptr;  // degree 2: the stacked table as shared-memory chunk images
+  float* Y2 = nullptr;         // degree 2: element results of the tensor-core apply
   tos::TcOp tc;
   void* Ke = nullptr;
   size_t ke_bytes = 0;     // size of Ke (slab_scratch_bytes)

@@ -782,13 +782,18 @@ bool vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
   const bool c_coarsest = (l + 1 == L - 1);
   const bool use_tc = tc.on && l == 0;
   if constexpr (std::is_same<T, float>::value) {
-    if (use_tc) {  // r = b - A v with A v from the tensor-core stacked contraction
+    if (use_tc && tc.deg >= 2) {  // r = b - A v, A v from the degree-2 stacked contraction
+      launch_tc2_apply(tc.mode, tc.m, F, (const float*)F.v, tc.w32, tc.img, tc.tscale, tc.Y2, tc.err, tc.sms,
+                       st);
+      launch_tc2_gather(F, tc.Y2, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 0,
+                        (float*)F.r, st);
+    } else if (use_tc) {  // r = b - A v with A v from the tensor-core stacked contraction
       launch_tc_apply(F, tc.m, (const float*)F.v, tc.w32, tc.KT, tc.Ye, tc.err, tc.sms, st);
       launch_tc_gather(F, tc.Ye, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 0,
                        (float*)F.r, st);
     }
   }
-  if (F.k >= 2)
+  if (F.k >= 2 && !use_tc)
     launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, 0, F.r,
                  F.sms, st);
   else if (!use_tc)
@@ -808,6 +813,13 @@ bool vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
     k_vc_prolong<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, F.mask,
                                                               (const T*)C.z, (T*)F.v);
   if constexpr (std::is_same<T, float>::value) {
+    if (use_tc && tc.deg >= 2) {  // z = v + omega D^-1 (b - A v)
+      launch_tc2_apply(tc.mode, tc.m, F, (const float*)F.v, tc.w32, tc.img, tc.tscale, tc.Y2, tc.err, tc.sms,
+                       st);
+      launch_tc2_gather(F, tc.Y2, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 1,
+                        (float*)F.z, st);
+      return false;
+    }
     if (use_tc) {  // z = v + omega D^-1 (b - A v)
       launch_tc_apply(F, tc.m, (const float*)F.v, tc.w32, tc.KT, tc.Ye, tc.err, tc.sms, st);
       launch_tc_gather(F, tc.Ye, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 1,

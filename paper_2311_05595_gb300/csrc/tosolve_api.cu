@@ -121,16 +121,28 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (!(d.penal >= 1.0)) { *why = "penal must be >= 1"; return TOSOLVE_EINVAL; }
   if (!(d.rmin >= 0.0) || d.rmin * d.n_mr > 16.0) { *why = "rmin*n_mr must be in [0, 16]"; return TOSOLVE_EINVAL; }
   if (d.precision != TOSOLVE_PREC_FP64 && d.precision != TOSOLVE_PREC_FP32 &&
-      d.precision != TOSOLVE_PREC_TF32 && d.precision != TOSOLVE_PREC_FP32X2) {
+      d.precision != TOSOLVE_PREC_TF32 && d.precision != TOSOLVE_PREC_FP32X2 &&
+      d.precision != TOSOLVE_PREC_BF16 && d.precision != TOSOLVE_PREC_BF16X3 &&
+      d.precision != TOSOLVE_PREC_F16X3) {
     *why = "unknown precision";
     return TOSOLVE_EINVAL;
   }
-  if (d.precision == TOSOLVE_PREC_TF32 && d.degree != 1) {
-    *why = "the TF32 tensor-core preconditioner is built for degree 1";
+  const bool tcp = d.precision == TOSOLVE_PREC_TF32 || d.precision == TOSOLVE_PREC_BF16 ||
+                   d.precision == TOSOLVE_PREC_BF16X3 || d.precision == TOSOLVE_PREC_F16X3;
+  if (tcp && d.degree == 3) {
+    *why = "the tensor-core preconditioners are built for degree 1 (TF32) and degree 2";
     return TOSOLVE_EINVAL;
   }
-  if (d.precision == TOSOLVE_PREC_TF32 && !tc_supported(d.n_mr)) {
+  if (tcp && d.precision != TOSOLVE_PREC_TF32 && d.degree != 2) {
+    *why = "the BF16, BF16X3 and F16X3 tensor-core preconditioners are built for degree 2";
+    return TOSOLVE_EINVAL;
+  }
+  if (d.precision == TOSOLVE_PREC_TF32 && d.degree == 1 && !tc_supported(d.n_mr)) {
     *why = "TF32 tensor-core preconditioner needs n_mr <= 2 (24 n^3 stacked rows <= 256)";
+    return TOSOLVE_EINVAL;
+  }
+  if (tcp && d.degree == 2 && (d.family != 0 || !tc2_supported(d.n_mr))) {
+    *why = "the degree-2 tensor-core preconditioner needs Lagrange elements and n_mr <= 3";
     return TOSOLVE_EINVAL;
   }
   if (d.omega != 0.0 && !(d.omega > 0.0 && d.omega < 2.0)) { *why = "omega must be in (0, 2)"; return TOSOLVE_EINVAL; }
@@ -155,7 +167,8 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   P->ndes = (long)P->dm * P->dm * P->dm * d.nx * d.ny * d.nz;
   P->noff = count_offsets(d.n_mr, d.rmin);
   const bool fp32 = d.precision != TOSOLVE_PREC_FP64;
-  const bool tf32 = d.precision == TOSOLVE_PREC_TF32 && L > 1;
+  const bool tf32 = d.precision == TOSOLVE_PREC_TF32 && L > 1 && d.degree == 1;
+  const bool tc2 = tcp && L > 1 && d.degree == 2;
   const bool x2 = d.precision == TOSOLVE_PREC_FP32X2;
   const int maxrhs = d.max_rhs > 0 ? d.max_rhs : 1;
   size_t B = 0;
@@ -176,7 +189,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
       v.s64 = v.s32 = false;
       B += v.ndof + v.ndof * 8 + 4 * v.ndof * tsz;  // mask, dinv64, b v r z
       if (fp32) B += v.ndof * 4;
-      B += coarsest ? E * dd * 8 : E * dd * (8 + (fp32 ? 4 : 0));
+      B += coarsest ? E * dd * 8 : E * dd * (8 + (fp32 && !(tc2 && l == 0) ? 4 : 0));
       if (d.family == 1 && (!coarsest || l == 0)) {  // compact copies of the serendipity levels
         const size_t dp = kl == 3 ? 96 : 60;
         B += E * dp * dp * (8 + (fp32 && !coarsest ? 4 : 0));
@@ -223,6 +236,10 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
     B += E0 * (P->m + 24) * 4 + (size_t)P->m * 576 * 4 + P->lv[0].ndof * 4;
   }
+  if (tc2) {  // weights, element results and the table image of the tensor-core level
+    const size_t E0 = (size_t)d.nx * d.ny * d.nz;
+    B += E0 * (P->m + tc2_result_stride()) * 4 + tc2_image_bytes(tc2_mode_of(d.precision), P->m);
+  }
   P->bytes = B;
   return TOSOLVE_OK;
 }
@@ -254,7 +271,7 @@ void free_all(tosolve_s* h) {
   F(h->rho); F(h->w); F(h->invom); F(h->foff); F(h->fwgt); F(h->gtmp);
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
   F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab); F(h->ptab3);
-  F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
+  F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->tcimg); F(h->Y2); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->Ad); F(h->Wp); F(h->Vp); F(h->Pg); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
   F(h->cnt);
@@ -435,7 +452,10 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   h->noff = P.noff;
   h->nc = (int)P.nc;
   const bool fp32 = h->d.precision != TOSOLVE_PREC_FP64;
-  const bool tf32 = h->d.precision == TOSOLVE_PREC_TF32 && P.L > 1;
+  const bool tf32 = h->d.precision == TOSOLVE_PREC_TF32 && P.L > 1 && h->d.degree == 1;
+  const bool tc2 = (h->d.precision == TOSOLVE_PREC_TF32 || h->d.precision == TOSOLVE_PREC_BF16 ||
+                    h->d.precision == TOSOLVE_PREC_BF16X3 || h->d.precision == TOSOLVE_PREC_F16X3) &&
+                   P.L > 1 && h->d.degree == 2;
   auto fail = [&](tosolve_status st) {
     free_all(h);
     g_err = h->err;
@@ -539,7 +559,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       CKC(dalloc(h, &L.dinv64, v.ndof));
       if (fp32) CKC(dalloc(h, &L.dinv32, v.ndof));
       if (l + 1 < P.L || l == 0) CKC(dalloc(h, &L.K64, E * dd));  // level 0: the CG's K
-      if (l + 1 < P.L && fp32) CKC(dalloc(h, &L.K32, E * dd));
+      if (l + 1 < P.L && fp32 && !(tc2 && l == 0)) CKC(dalloc(h, &L.K32, E * dd));  // tensor cores: no level-0 copy
       if (h->d.family == 1) {  // compact copies for the apply
         const size_t dp = L.k == 3 ? 96 : 60;
         if (L.K64) CKC(dalloc(h, &L.Kc64, E * dp * dp));
@@ -671,6 +691,30 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     launch_subcell_table(P.n, h->d.nu, 1.0, h->tab64, st);
     launch_symmetrize(P.m, h->tab64, h->tabsym64, st);
     launch_moment_basis(h->d.nu, h->cmom64, st);
+  }
+  if (tc2) {  // degree 2: weights, results and the stacked table's image
+    const size_t E0 = (size_t)P.lv[0].ex * P.lv[0].ey * P.lv[0].ez;
+    const int mode = tc2_mode_of(h->d.precision);
+    CKC(dalloc(h, &h->tcimg, tc2_image_bytes(mode, P.m)));
+    CKC(dalloc(h, &h->w32, E0 * P.m));
+    CKC(dalloc(h, &h->Y2, E0 * tc2_result_stride()));
+    std::vector<double> tab((size_t)P.m * kDD2);
+    CKC(cudaMemcpyAsync(tab.data(), h->tab64, tab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    const float tscale = tc2_table_scale(mode, tab.data(), tab.size());
+    launch_tc2_image(mode, P.m, h->tab64, tscale, h->tcimg, st);
+    int sms = 1;
+    CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+    h->tc.on = true;
+    h->tc.deg = 2;
+    h->tc.mode = mode;
+    h->tc.prec = h->d.precision;
+    h->tc.tscale = tscale;
+    h->tc.m = P.m;
+    h->tc.w32 = h->w32;
+    h->tc.img = h->tcimg;
+    h->tc.Y2 = h->Y2;
+    h->tc.sms = sms;
   }
   if (tf32) {  // tensor-core operands of the finest level
     const size_t E0 = (size_t)P.lv[0].ex * P.lv[0].ey * P.lv[0].ez;
@@ -816,6 +860,11 @@ tosolve_status tosolve_create_mixed(const tosolve_desc* desc, const uint8_t* mas
   if (desc == nullptr || elem_q1_host == nullptr) { g_err = "NULL argument"; return TOSOLVE_EINVAL; }
   if (desc->degree != 2) { g_err = "a mixed mesh lives on the degree-2 lattice (degree = 2)"; return TOSOLVE_EINVAL; }
   if (desc->family != 0) { g_err = "a mixed mesh couples Lagrange elements (family = 0)"; return TOSOLVE_EINVAL; }
+  if (desc->precision == TOSOLVE_PREC_TF32 || desc->precision == TOSOLVE_PREC_BF16 ||
+      desc->precision == TOSOLVE_PREC_BF16X3 || desc->precision == TOSOLVE_PREC_F16X3) {
+    g_err = "the tensor-core preconditioners are not built for mixed meshes";
+    return TOSOLVE_EINVAL;
+  }
   return create_impl(desc, mask_host, elem_q1_host, cuda_stream, out);
 }
 
@@ -877,10 +926,9 @@ static tosolve_status refresh(tosolve_t h) {
       } else
         launch_q2_coarse_elem(Lv, h->w, h->Dx, h->Dy, h->cmom64, h->Mq, Lv.K64, st);
       launch_q2_dinv(true, Lv, Lv.K64, Lv.dinv64, st);
-      if (Lv.K32) {
-        launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * (Lv.k == 3 ? kDD3 : kDD2), Lv.K64, Lv.K32, st);
-        launch_q2_dinv(false, Lv, Lv.K64, Lv.dinv32, st);
-      }
+      if (Lv.K32) launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * (Lv.k == 3 ? kDD3 : kDD2), Lv.K64, Lv.K32, st);
+      if (Lv.dinv32) launch_q2_dinv(false, Lv, Lv.K64, Lv.dinv32, st);
+      if (l == 0 && h->tc.on) launch_weights_elem(Lv, n, h->w, h->Dx, h->Dy, h->w32, st);
       if (Lv.Kc64 || Lv.Kc32) launch_ser_compact(Lv, st);
     }
     if (L > 1) {
@@ -1346,10 +1394,21 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
   } else if (precision == 1 || precision == 3) {
     if (!L.S32) return set_err(h, TOSOLVE_EINVAL, "this level has no FP32 operator");
     launch_apply_diag(precision == 1 ? kVtF32 : kVtDF, L, x_dev, y_dev, h->st);
-  } else if (precision == 2) {
-    if (level != 0 || !h->tc.on) return set_err(h, TOSOLVE_EINVAL, "no tensor-core operator on this level");
-    // masked copy feeds the elements; the unmasked copy gives the identity rows
+  } else if (precision == 2 || precision >= 4) {
+    if (level != 0 || !h->tc.on || precision != (h->tc.deg == 2 ? h->tc.prec : 2))
+      return set_err(h, TOSOLVE_EINVAL, "no tensor-core operator of that precision on this level");
     Level& L0 = h->lv[0];
+    if (h->tc.deg == 2) {  // the kernel zeroes fixed DOFs itself; the gather keeps them as identity rows
+      launch_cast(false, (size_t)L0.ndof, x_dev, L0.v, true, h->st);
+      CK(launch_tc2_apply(h->tc.mode, h->tc.m, L0, (const float*)L0.v, h->w32, h->tcimg, h->tc.tscale, h->Y2,
+                          h->tc.err, h->tc.sms, h->st));
+      launch_tc2_gather(L0, h->Y2, (const float*)L0.v, (const float*)L0.v, L0.dinv32, 0.f, 2, (float*)L0.r,
+                        h->st);
+      launch_cast(true, (size_t)L0.ndof, L0.r, y_dev, false, h->st);
+      CK(cudaGetLastError());
+      return TOSOLVE_OK;
+    }
+    // masked copy feeds the elements; the unmasked copy gives the identity rows
     launch_cast(false, (size_t)L0.ndof, x_dev, L0.b, true, h->st);
     launch_cast(false, (size_t)L0.ndof, x_dev, L0.v, true, h->st);
     launch_mask_fp32(L0, (float*)L0.v, h->st);
@@ -1357,7 +1416,7 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
     launch_tc_gather(L0, h->Ye, (const float*)L0.b, (const float*)L0.b, L0.dinv32, 0.f, 2, (float*)L0.r, h->st);
     launch_cast(true, (size_t)L0.ndof, L0.r, y_dev, false, h->st);
   } else {
-    return set_err(h, TOSOLVE_EINVAL, "precision must be 0, 1, 2 or 3");
+    return set_err(h, TOSOLVE_EINVAL, "precision must be 0 .. 6");
   }
   CK(cudaGetLastError());
   return TOSOLVE_OK;

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libtosolve.so")
 
 OK, EINVAL, ENOMEM, ENOTCONV, EBREAKDOWN, ECUDA = range(6)
-PREC_FP64, PREC_FP32, PREC_TF32, PREC_FP32X2 = 0, 1, 2, 3
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_FP32X2, PREC_BF16, PREC_BF16X3, PREC_F16X3 = 0, 1, 2, 3, 4, 5, 6
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "EBREAKDOWN", 5: "ECUDA"}
 
 

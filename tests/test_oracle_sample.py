@@ -87,3 +87,76 @@ def test_row_rounding_scale_bounds_the_rows():
             d = 3 * nd + c
             if p.mask[d] == 0:
                 assert sc[q, c] >= abs(K[d, d] * u[d]) * (1 - 1e-14)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_subcell_rounding_scale(n):
+    """The rounding scale of the stacked form: with one subcell per element
+    it is the element scale sum_j |K_ij u_j| (|w K| = w |K|); with more it
+    bounds that scale from above (triangle inequality over subcells); the
+    vectorised whole-mesh version equals the per-node loops of the sampler."""
+    p = workloads.bridge(4, 2, 2, degree=2, n_mr=n, seed=5)
+    m = fe.Model(p)
+    S = sample.Sampler(p)
+    u = np.random.default_rng(7).normal(size=p.ndof)
+    w_e = m.weights(m.densities(p.x))
+    whole = m.subcell_scale(w_e, u).reshape(-1, 3)
+    nodes = list(range(p.nnodes))
+    loops = S.apply_rows_subcell_scale(p.x, u, nodes)
+    np.testing.assert_allclose(loops, whole, rtol=1e-13)
+    elem = S.apply_rows_scale(p.x, u, nodes)
+    if n == 1:
+        np.testing.assert_allclose(whole, elem, rtol=1e-13)
+    else:
+        assert (whole >= elem * (1 - 1e-13)).all()
+        assert (whole > elem * (1 + 1e-6)).any()  # cancellation between subcells exists
+    y = m.apply(w_e, u).reshape(-1, 3)
+    assert (whole >= np.abs(y) * (1 - 1e-13)).all()
+
+
+@pytest.mark.parametrize("k,n", [(1, 2), (2, 3), (3, 1)])
+def test_rigid_projector_keeps_the_subcell_products(k, n):
+    """The deflation behind the tensor-core operand: P is an orthogonal
+    projector of rank d - 6 that every subcell matrix sees as the identity
+    (K^(e_i) P = K^(e_i): rigid motions carry no strain), and it removes
+    translations and rotations exactly."""
+    from oracle import fem
+
+    P = fe.rigid_projector(k)
+    d = 3 * (k + 1) ** 3
+    np.testing.assert_allclose(P @ P, P, atol=1e-13)
+    np.testing.assert_allclose(P, P.T, atol=1e-14)
+    assert round(np.trace(P)) == d - 6
+    K = fem.subcell_stiffness(k, n, 0.3)
+    for Ki in K:
+        np.testing.assert_allclose(Ki @ P, Ki, atol=1e-12 * np.abs(Ki).max())
+    pos = np.array([[-1.0 + 2.0 * ax / k, -1.0 + 2.0 * ay / k, -1.0 + 2.0 * az / k]
+                    for az in range(k + 1) for ay in range(k + 1) for ax in range(k + 1)])
+    om, t = np.array([0.3, -1.1, 0.7]), np.array([2.0, -0.5, 1.5])
+    rigid = (t + np.cross(om, pos)).reshape(-1)
+    assert np.abs(P @ rigid).max() <= 1e-13
+
+
+def test_deflated_scale_equals_between_oracle_forms():
+    p = workloads.bridge(4, 2, 2, degree=2, n_mr=2, seed=5)
+    m = fe.Model(p)
+    S = sample.Sampler(p)
+    u = np.random.default_rng(8).normal(size=p.ndof)
+    w_e = m.weights(m.densities(p.x))
+    whole = m.subcell_scale(w_e, u, deflate=True).reshape(-1, 3)
+    loops = S.apply_rows_subcell_scale(p.x, u, list(range(p.nnodes)), deflate=True)
+    np.testing.assert_allclose(loops, whole, rtol=1e-12)
+    wm = m.subcell_scale(w_e, u, deflate=True, elem_max=True).reshape(-1, 3)
+    lm = S.apply_rows_subcell_scale(p.x, u, list(range(p.nnodes)), deflate=True, elem_max=True)
+    np.testing.assert_allclose(lm, wm, rtol=1e-12)
+    free = (p.mask == 0).reshape(-1, 3)
+    assert (wm[free] >= whole[free] * (1 - 1e-13)).all()  # the element max bounds every entry
+    # a rigid displacement has a zero deflated scale away from the supports
+    pos = np.array([[i, j, l] for l in range(p.lattice[2]) for j in range(p.lattice[1])
+                    for i in range(p.lattice[0])], dtype=float)
+    rigid = (np.array([1.0, 2.0, 3.0]) + np.cross([0.2, 0.1, -0.3], pos)).reshape(-1)
+    free_elems = np.all(p.mask[m.edofs] == 0, axis=1)
+    z = m.subcell_scale(w_e, rigid, deflate=True)
+    touched = np.unique(m.edofs[free_elems])
+    only_free = np.setdiff1d(touched, np.unique(m.edofs[~free_elems]))
+    assert np.abs(z[only_free]).max() <= 1e-12 * np.abs(rigid).max()
