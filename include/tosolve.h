@@ -121,6 +121,15 @@ typedef struct {
                           /*   (the paper's choice for Lagrange elements;   */
                           /*   not for serendipity); degree 1: the two are  */
                           /*   the same trilinear interpolation             */
+  int inner_its;          /* 0: each outer FP64 CG iteration is              */
+                          /*   preconditioned by one V-cycle (Alg. 1);       */
+                          /*   k in 1..64: by k iterations of CG in FP32 on  */
+                          /*   the level-0 operator of the preconditioner    */
+                          /*   (the tensor-core stacked contraction, or the  */
+                          /*   FP32 element matrices), each preconditioned   */
+                          /*   by one V-cycle; the outer CG is flexible, its */
+                          /*   residual, dot products and operator stay FP64 */
+                          /*   (degree 2, FP32-vector precisions only)       */
 } tosolve_desc;
 
 typedef struct {

@@ -78,6 +78,11 @@ struct DevState {
   int tc_status;      // non-zero if a tensor-core tile wait timed out
   int tile_status;    // non-zero if an operator tile copy wait timed out
   int pad;
+  // inner FP32 PCG (the preconditioner of the outer flexible CG)
+  double in_rho;      // ri^T z of the current inner direction
+  double in_rho_next; // ri^T z of the next inner direction
+  double in_alpha;    // inner step
+  double in_beta;     // inner flexible coefficient
 };
 
 struct Level {
@@ -255,6 +260,20 @@ struct CgDots {
 };
 bool launch_vcycle(int vt, Level* lv, int L, double omega, int gamma, const double* Ainv,
                    const TcOp& tc, cudaStream_t st, const CgDots* dots = nullptr);
+// Vectors of the inner FP32 PCG on level 0 (ndof floats each).
+struct InnerPcg {
+  int its = 0;           // inner iterations per outer iteration (0: the V-cycle alone)
+  float* e = nullptr;    // inner solution
+  float* ri = nullptr;   // inner residual
+  float* pi = nullptr;   // inner direction
+  float* qi = nullptr;   // A pi
+};
+// z0 = approximation of A0^-1 b0 by `its` iterations of FP32 PCG on the
+// level-0 preconditioner operator (tensor cores when tc.on, else the FP32
+// element matrices), each preconditioned by one V-cycle; b0 and v0 = omega
+// D^-1 b0 are set by the outer kernels.  Reductions in FP64, fixed order.
+void launch_inner_pcg(Level* lv, int L, double omega, const double* Ainv, const TcOp& tc, const InnerPcg& in,
+                      double* part_a, double* part_b, DevState* ds, unsigned* cnt, cudaStream_t st);
 void launch_smooth0(int vt, const Level& L0, double omega, cudaStream_t st);
 void launch_set_params(DevState* ds, const double* params, cudaStream_t st);
 void launch_cg_prep(const Level& L0, double* f, double* u, double* part, int np, cudaStream_t st);
@@ -298,6 +317,10 @@ void launch_s2_restrict(int vt, const Level& F, const Level& C, const float* W, 
 void launch_s2_prolong(int vt, const Level& F, const Level& C, const float* W, cudaStream_t st);
 void launch_q2_elem(const Level& L, int n, const double* w, int Dx, int Dy, const double* tab,
                     double* Ke, cudaStream_t st);
+// Lagrange degree 2: element matrices of any level by sum factorisation over
+// the moments of its N^3 density cells per element (N = L.nsub <= 64).
+bool q2_elem_sf_supported(int N);
+void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double nu, double* Ke, cudaStream_t st);
 void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, const double* cmom,
                            double* Mscr, double* Ke, cudaStream_t st);
 void launch_q2_dinv(bool fp64, const Level& L, const double* Ke, void* dinv, cudaStream_t st);
@@ -311,6 +334,11 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
 void launch_q2_constrain(const Level& L, const uint8_t* slv, double* Ke, int sms, cudaStream_t st);
 void launch_q2_fold(const Level& L, const uint8_t* slv, double* f, cudaStream_t st);
 void launch_q2_expand(const Level& L, const uint8_t* slv, double* u, cudaStream_t st);
+// Lagrange degree 2: the same sensitivities from the strain energy at the
+// tensor Gauss points, by sum factorisation (n <= 4).
+bool q2_energy_sf_supported(int n);
+void launch_q2_energy_sf(const Level& L0, int n, double nu, const double* u, const double* rho, double penal,
+                         double dE, int Dx, int Dy, bool first, double* g, int sms, cudaStream_t st);
 void launch_q2_energy_grad(const Level& L0, int n, const double* u, const double* tab,
                            const double* rho, double penal, double dE, int Dx, int Dy, bool first,
                            double* g, int sms, cudaStream_t st);
@@ -427,6 +455,7 @@ struct tosolve_s {
   unsigned char* tcimg = nullptr;  // degree 2: the stacked table as shared-memory chunk images
   float* Y2 = nullptr;         // degree 2: element results of the tensor-core apply
   tos::TcOp tc;
+  tos::InnerPcg inner;
   void* Ke = nullptr;
   size_t ke_bytes = 0;     // size of Ke (slab_scratch_bytes)
   double* Kec = nullptr;  // element matrices of the coarsest level (second stream)

@@ -433,6 +433,126 @@ __global__ void k_q2_moments(int ex, int ey, int N, const double* __restrict__ w
   for (int q = threadIdx.x; q < kNM; q += blockDim.x) M[e * kNM + q] = red[q];
 }
 
+// Element matrices of a Lagrange degree-2 level by sum factorisation (any
+// level: the element covers N^3 density cells of constant weight).  With
+// N_a(xi) = phi_ax(xi) phi_ay(eta) phi_az(zeta), the entries of Eq.
+// matrixK_mr are
+//   K[(a,i),(b,j)] = (h/2) (lam F^ij_ab + mu F^ji_ab + mu delta_ij sum_s F^ss_ab),
+//   F^st_ab = int_ref w d_s N_a d_t N_b = sum_alpha M_alpha prod_d c_d(alpha_d)[a_d][b_d],
+// where M_alpha (alpha in {0..4}^3) are the moments of w over the reference
+// element and c_d(p)[x][y] is the coefficient of xi^p in phi_x^(m) phi_y^(n)
+// with m = [s = d], n = [t = d] (Sec. 2.1; the same polynomial identity as
+// the moment basis, but contracted one axis at a time).  Per element: the
+// moments by z-slices of cells (x, then y, then accumulated over z in a
+// fixed order), then for the six pairs s <= t the contractions over
+// alpha_z, alpha_y, alpha_x, then the 81 x 81 assembly (F^ts_ab = F^st_ba).
+// About 6.5e4 FP64 FMAs per element instead of 27 x 6561 (subcell sum) or
+// 125 x 6561 (moment basis).  Block of 256 threads per element.
+constexpr int kSfMaxN = 64;
+struct SfSmem {
+  double cf[4][kP][9];          // c_tau(p)[x * 3 + y], tau = 2 m + n
+  double mu[kP][kSfMaxN];       // mu_p(k): integral of xi^p over interval k
+  double S1[kSfMaxN][kP];       // one z-slice summed along x
+  double S2[kP * kP];           // the same slice summed along x and y
+  double M[kNM];                // moments, alpha = ax + 5 (ay + 5 az)
+  double G[4][kP * kP][9];      // contracted over alpha_z, per z-type
+  double H[6][kP][81];          // contracted over alpha_y, per pair
+  double F[6][729];             // F^st, a = ax + 3 (ay + 3 az), entry a * 27 + b
+};
+__device__ __forceinline__ int sf_pair(int s, int t) {  // s <= t: 00 11 22 01 02 12
+  return s == t ? s : (s == 0 ? (t == 1 ? 3 : 4) : 5);
+}
+
+__global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int N, double h, double nu,
+                                                   const double* __restrict__ w, int Dx, int Dy,
+                                                   double* __restrict__ Ke) {
+  extern __shared__ __align__(16) unsigned char sfraw[];
+  SfSmem& S = *reinterpret_cast<SfSmem*>(sfraw);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < 4 * kP * 9; t += nt) {
+    const int tau = t / (kP * 9), p = (t / 9) % kP, xy = t % 9;
+    double u[3], v[3];
+    lag_coef(xy / 3, tau >> 1, u);
+    lag_coef(xy % 3, tau & 1, v);
+    double c = 0.0;
+    for (int r = 0; r < 3; ++r)
+      if (p - r >= 0 && p - r < 3) c += u[r] * v[p - r];
+    S.cf[tau][p][xy] = c;
+  }
+  for (int t = tid; t < kP * N; t += nt) S.mu[t / N][t % N] = mono_int(t / N, t % N, N);
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = 1.0 / (2.0 * (1.0 + nu));
+  const double hh = 0.5 * h;
+  __syncthreads();
+  for (long e = blockIdx.x; e < E; e += gridDim.x) {
+    const int exi = (int)(e % ex), eyi = (int)((e / ex) % ey), ezi = (int)(e / ((long)ex * ey));
+    for (int q = tid; q < kNM; q += nt) S.M[q] = 0.0;
+    // ---- moments, one z-slice of cells at a time ----
+    for (int c = 0; c < N; ++c) {
+      for (int t = tid; t < N * kP; t += nt) {
+        const int b = t / kP, p = t % kP;
+        const double* row = w + (N * exi) + (long)Dx * ((N * eyi + b) + (long)Dy * (N * ezi + c));
+        double acc = 0.0;
+        for (int a = 0; a < N; ++a) acc += row[a] * S.mu[p][a];
+        S.S1[b][p] = acc;
+      }
+      __syncthreads();
+      for (int t = tid; t < kP * kP; t += nt) {
+        const int px = t % kP, py = t / kP;
+        double acc = 0.0;
+        for (int b = 0; b < N; ++b) acc += S.S1[b][px] * S.mu[py][b];
+        S.S2[t] = acc;
+      }
+      __syncthreads();
+      for (int q = tid; q < kNM; q += nt) S.M[q] += S.S2[q % (kP * kP)] * S.mu[q / (kP * kP)][c];
+      __syncthreads();
+    }
+    // ---- over alpha_z: G[tz][ax + 5 ay][az * 3 + bz] ----
+    for (int t = tid; t < 4 * kP * kP * 9; t += nt) {
+      const int tz = t / (kP * kP * 9), xy = (t / 9) % (kP * kP), zz = t % 9;
+      double acc = 0.0;
+      for (int pz = 0; pz < kP; ++pz) acc += S.M[xy + kP * kP * pz] * S.cf[tz][pz][zz];
+      S.G[tz][xy][zz] = acc;
+    }
+    __syncthreads();
+    // ---- over alpha_y: H[pair][ax][(ay * 3 + by) * 9 + az * 3 + bz] ----
+    for (int t = tid; t < 6 * kP * 81; t += nt) {
+      const int pr = t / (kP * 81), px = (t / 81) % kP, yz = t % 81;
+      const int s = pr < 3 ? pr : (pr == 5 ? 1 : 0), tt = pr < 3 ? pr : (pr == 3 ? 1 : 2);
+      const int ty = 2 * (s == 1) + (tt == 1), tz = 2 * (s == 2) + (tt == 2);
+      const int yy = yz / 9, zz = yz % 9;
+      double acc = 0.0;
+      for (int py = 0; py < kP; ++py) acc += S.cf[ty][py][yy] * S.G[tz][px + kP * py][zz];
+      S.H[pr][px][yz] = acc;
+    }
+    __syncthreads();
+    // ---- over alpha_x: F[pair][a * 27 + b] ----
+    for (int t = tid; t < 6 * 729; t += nt) {
+      const int pr = t / 729, ab = t % 729, a = ab / 27, b = ab % 27;
+      const int s = pr < 3 ? pr : (pr == 5 ? 1 : 0), tt = pr < 3 ? pr : (pr == 3 ? 1 : 2);
+      const int tx = 2 * (s == 0) + (tt == 0);
+      const int xx = (a % 3) * 3 + (b % 3);
+      const int yz = ((a / 3) % 3 * 3 + (b / 3) % 3) * 9 + (a / 9) * 3 + (b / 9);
+      double acc = 0.0;
+      for (int px = 0; px < kP; ++px) acc += S.cf[tx][px][xx] * S.H[pr][px][yz];
+      S.F[pr][ab] = acc;
+    }
+    __syncthreads();
+    // ---- K[(a,i),(b,j)] ----
+    double* out = Ke + e * (size_t)kDD;
+    for (int t = tid; t < kDD; t += nt) {
+      const int R = t / kD, C = t % kD;
+      const int a = R / 3, i = R % 3, b = C / 3, j = C % 3;
+      const double fij = i <= j ? S.F[sf_pair(i, j)][a * 27 + b] : S.F[sf_pair(j, i)][b * 27 + a];
+      const double fji = j <= i ? S.F[sf_pair(j, i)][a * 27 + b] : S.F[sf_pair(i, j)][b * 27 + a];
+      double v = lam * fij + mu * fji;
+      if (i == j) v += mu * (S.F[0][a * 27 + b] + S.F[1][a * 27 + b] + S.F[2][a * 27 + b]);
+      out[t] = hh * v;
+    }
+    __syncthreads();
+  }
+}
+
 // K^(e) = (h/2) sum_alpha M_alpha C_alpha, full 81 x 81, for kEB elements per
 // block (each C_alpha entry read once per block).
 constexpr int kEB = 8;
@@ -871,6 +991,113 @@ __global__ void k_q2_energy_grad(int ex, int ey, long E, int n, int Lx, int Ly,
   }
 }
 
+// Sensitivities of Lagrange degree-2 elements (Sec. 3.4) from the strain
+// energy: s_{e,i} = u_e^T K^(e_i) u_e = int over subcell i of
+// lam (tr eps)^2 + 2 mu eps:eps (E = 1), integrated exactly by 3-point
+// Gauss-Legendre per axis and subcell (the integrand has degree <= 4 per
+// axis): the 3n points per axis form a tensor grid, on which the
+// displacement gradients come by sum factorisation (contract the 27 nodal
+// values over z, then y, then x with the 1D basis values and derivatives).
+// About 4e4 FP64 FMAs per element for n = 3 instead of 27 x 6561, and no
+// cancellation between the terms of the quadratic form (an element that
+// moves almost rigidly has small strains, not a small difference of large
+// numbers).  dc/drho_i = -p rho_i^(p-1) (E0 - Emin) s_{e,i}, accumulated over
+// load cases unless first.  Block of 256 threads per element; each subcell's
+// sum is taken in a fixed order by one thread.
+constexpr int kEgMaxN = 4;
+__host__ __device__ constexpr int eg_smem_doubles(int n) {
+  // U 81 | Tz 3 x 2 x 9 x 3n | Tyz 3 x 3 x 3 x (3n)^2 | energy (3n)^3 | tables 2 x 3n x 3 + 3n
+  return 81 + 3 * 2 * 9 * 3 * n + 27 * 9 * n * n + 27 * n * n * n + 2 * 9 * n + 3 * n;
+}
+__global__ void __launch_bounds__(256) k_q2_energy_sf(int ex, int ey, long E, int n, int Lx, int Ly, double h,
+                                                     double nu, const double* __restrict__ u,
+                                                     const double* __restrict__ rho, double penal, double dE,
+                                                     int Dx, int Dy, int first, double* __restrict__ g) {
+  extern __shared__ double egs[];
+  const int Q = 3 * n;  // quadrature points per axis
+  double* U = egs;                              // [c][az][ay][ax]
+  double* Tz = U + 81;                          // [c][mz][ax + 3 ay][qz]
+  double* Tyz = Tz + 3 * 2 * 9 * Q;             // [c][combo][ax][qy * Q + qz], combo: (my,mz) 00 10 01
+  double* En = Tyz + 27 * Q * Q;                // energy density x weight per point
+  double* B = En + Q * Q * Q;                   // [m][q][alpha]
+  double* Wq = B + 2 * Q * 3;                   // 1D weight per point
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double gp[3] = {-sqrt(0.6), 0.0, sqrt(0.6)};
+  const double gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+  for (int t = tid; t < Q * 3; t += nt) {
+    const int q = t / 3, al = t % 3;
+    const double xi = -1.0 + (2 * (q / 3) + 1) / (double)n + gp[q % 3] / n;
+    B[q * 3 + al] = lag(al, xi);
+    B[Q * 3 + q * 3 + al] = dlag(al, xi);
+    if (al == 0) Wq[q] = gw[q % 3] / n;
+  }
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = 1.0 / (2.0 * (1.0 + nu));
+  const double s2h = 2.0 / h;                 // d/dx = (2/h) d/dxi
+  const double jac = 0.125 * h * h * h;       // dx = (h/2)^3 dxi
+  __syncthreads();
+  for (long e = blockIdx.x; e < E; e += gridDim.x) {
+    const int exi = (int)(e % ex), eyi = (int)((e / ex) % ey), ezi = (int)(e / ((long)ex * ey));
+    for (int t = tid; t < 81; t += nt) {
+      const int c = t % 3, a = t / 3;
+      U[c * 27 + a] = u[3 * elem_node_k<2>(exi, eyi, ezi, a, Lx, Ly) + c];
+    }
+    __syncthreads();
+    for (int t = tid; t < 3 * 2 * 9 * Q; t += nt) {  // over az
+      const int qz = t % Q, xy = (t / Q) % 9, mz = (t / (Q * 9)) % 2, c = t / (Q * 18);
+      const double* bz = B + mz * Q * 3 + qz * 3;
+      const double* uc = U + c * 27 + xy;
+      Tz[t] = bz[0] * uc[0] + bz[1] * uc[9] + bz[2] * uc[18];
+    }
+    __syncthreads();
+    for (int t = tid; t < 27 * Q * Q; t += nt) {  // over ay
+      const int yz = t % (Q * Q), ax = (t / (Q * Q)) % 3, cb = (t / (Q * Q * 3)) % 3, c = t / (Q * Q * 9);
+      const int my = cb == 1, mz = cb == 2;
+      const int qy = yz / Q, qz = yz % Q;
+      const double* by = B + my * Q * 3 + qy * 3;
+      const double* tz = Tz + ((c * 2 + mz) * 9 + ax) * Q + qz;
+      Tyz[t] = by[0] * tz[0] + by[1] * tz[3 * Q] + by[2] * tz[6 * Q];
+    }
+    __syncthreads();
+    for (int t = tid; t < Q * Q * Q; t += nt) {  // over ax, then the energy density at the point
+      const int qx = t % Q, yz = t / Q, qy = yz / Q, qz = yz % Q;
+      const double* b0 = B + qx * 3;
+      const double* b1 = B + Q * 3 + qx * 3;
+      double gr[3][3];  // gr[c][s] = d u_c / d x_s
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int sd = 0; sd < 3; ++sd) {
+          const int cb = sd == 0 ? 0 : sd;  // x: (0,0) with B1 in x; y: combo 1; z: combo 2
+          const double* bx = sd == 0 ? b1 : b0;
+          const double* ty = Tyz + ((c * 3 + cb) * 3) * Q * Q + yz;
+          gr[c][sd] = s2h * (bx[0] * ty[0] + bx[1] * ty[Q * Q] + bx[2] * ty[2 * Q * Q]);
+        }
+      }
+      const double tr = gr[0][0] + gr[1][1] + gr[2][2];
+      const double e01 = 0.5 * (gr[0][1] + gr[1][0]), e02 = 0.5 * (gr[0][2] + gr[2][0]),
+                   e12 = 0.5 * (gr[1][2] + gr[2][1]);
+      const double ee = gr[0][0] * gr[0][0] + gr[1][1] * gr[1][1] + gr[2][2] * gr[2][2] +
+                        2.0 * (e01 * e01 + e02 * e02 + e12 * e12);
+      En[t] = (lam * tr * tr + 2.0 * mu * ee) * Wq[qx] * Wq[qy] * Wq[qz];
+    }
+    __syncthreads();
+    for (int sc = tid; sc < n * n * n; sc += nt) {  // subcell sums, fixed order
+      const int a = sc % n, b = (sc / n) % n, c = sc / (n * n);
+      double acc = 0.0;
+      for (int k = 0; k < 27; ++k) {
+        const int qx = 3 * a + k % 3, qy = 3 * b + (k / 3) % 3, qz = 3 * c + k / 9;
+        acc += En[(qy * Q + qz) * Q + qx];  // the layout of the point loop: x fastest, then z, then y
+      }
+      acc *= jac;
+      const long cell = (n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c));
+      const double gv = -penal * simp_pow(rho[cell], penal - 1.0) * dE * acc;
+      g[cell] = first ? gv : g[cell] + gv;
+    }
+    __syncthreads();
+  }
+}
+
 // Mixed trilinear / triquadratic meshes (the coupling rule of the mixed
 // reading): a non-vertex lattice node touching a trilinear element is slaved
 // to the linear interpolation of the 2^q vertices of its edge, face or cell
@@ -1078,6 +1305,21 @@ void launch_q3_subcell_table(int n, double nu, double h, int family, double* gra
   k_q3_subcell_table<<<grid_for2(nt), 256, 0, st>>>(n, nu, h, grad_scratch, tab);
 }
 
+bool q2_elem_sf_supported(int N) { return N >= 1 && N <= kSfMaxN; }
+
+void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double nu, double* Ke, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * L.ez;
+  const size_t sm = sizeof(SfSmem);
+  static std::once_flag attr;  // handles may be created from several threads
+  std::call_once(attr, [sm] {
+    cudaFuncSetAttribute(k_q2_elem_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  });
+  long g = (long)L.sms * 3;  // three 70 KB blocks per SM
+  if (g > E) g = E;
+  if (g < 1) g = 1;
+  k_q2_elem_sf<<<(int)g, 256, sm, st>>>(L.ex, L.ey, E, L.nsub, L.h, nu, w, Dx, Dy, Ke);
+}
+
 void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, const double* cmom,
                            double* Mscr, double* Ke, cudaStream_t st) {
   const long E = (long)L.ex * L.ey * L.ez;
@@ -1176,6 +1418,23 @@ void launch_q2_fold(const Level& L, const uint8_t* slv, double* f, cudaStream_t 
 
 void launch_q2_expand(const Level& L, const uint8_t* slv, double* u, cudaStream_t st) {
   k_q2_expand<<<grid_for2(L.nn), 256, 0, st>>>(L.Lx, L.Ly, L.Lz, slv, u);
+}
+
+bool q2_energy_sf_supported(int n) { return n >= 1 && n <= kEgMaxN; }
+
+void launch_q2_energy_sf(const Level& L0, int n, double nu, const double* u, const double* rho, double penal,
+                         double dE, int Dx, int Dy, bool first, double* g, int sms, cudaStream_t st) {
+  const long E = (long)L0.ex * L0.ey * L0.ez;
+  const size_t sm = (size_t)eg_smem_doubles(n) * sizeof(double);
+  static std::once_flag attr;  // handles may be created from several threads
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_q2_energy_sf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(eg_smem_doubles(kEgMaxN) * sizeof(double)));
+  });
+  long gr = (long)sms * 4;
+  if (gr > E) gr = E;
+  k_q2_energy_sf<<<(int)gr, 256, sm, st>>>(L0.ex, L0.ey, E, n, L0.Lx, L0.Ly, L0.h, nu, u, rho, penal, dE, Dx,
+                                           Dy, first ? 1 : 0, g);
 }
 
 void launch_q2_energy_grad(const Level& L0, int n, const double* u, const double* tab,

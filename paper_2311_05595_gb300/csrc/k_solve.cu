@@ -704,6 +704,100 @@ __global__ void k_cg_update(int nn, double* __restrict__ u, double* __restrict__
   }
 }
 
+// ---- inner FP32 PCG ----------------------------------------------------------
+// Each outer (FP64) iteration may precondition with a few iterations of PCG
+// in FP32 on the level-0 operator of the preconditioner, each of those
+// preconditioned by one V-cycle: a stronger preconditioner for the outer
+// flexible CG, whose FP64 operator apply then runs far fewer times.  The
+// inner coefficients use the same flexible form as the outer loop.
+
+// ri = b0 (the outer residual in FP32); e = 0.
+__global__ void k_in_init(long n, const float* __restrict__ b0, float* __restrict__ ri, float* __restrict__ e) {
+  DOF_LOOP(n) {
+    ri[d] = b0[d];
+    e[d] = 0.f;
+  }
+}
+
+// rho = ri^T z and zq = z^T qi (qi = A p of the previous inner iteration);
+// the last block forms beta = -alpha zq / rho_old (0 on the first).
+__global__ void k_in_rz(long n, const float* __restrict__ ri, const float* __restrict__ z,
+                        const float* __restrict__ qi, int first, double* part_a, double* part_b,
+                        DevState* __restrict__ ds, unsigned* cnt) {
+  // each thread's few dozen terms in FP32 (FP64 issue is scarce here), the
+  // block and grid sums in FP64; the inner CG runs in FP32 throughout
+  float fa = 0.f, fb = 0.f;
+  DOF_LOOP(n) {
+    const float zv = z[d];
+    fa = fmaf(ri[d], zv, fa);
+    if (!first) fb = fmaf(zv, qi[d], fb);
+  }
+  double a = block_sum((double)fa);
+  double b = block_sum((double)fb);
+  if (threadIdx.x == 0) {
+    part_a[blockIdx.x] = a;
+    part_b[blockIdx.x] = b;
+  }
+  if (!last_block(cnt)) return;
+  const double rz = reduce_parts(part_a, gridDim.x);
+  const double zq = reduce_parts(part_b, gridDim.x);
+  if (threadIdx.x == 0) {
+    const double beta = first ? 0.0 : -ds->in_alpha * zq / ds->in_rho;
+    ds->in_beta = (beta == beta && fabs(beta) < 1e30) ? beta : 0.0;
+    ds->in_rho_next = rz;
+    *cnt = 0u;
+  }
+}
+
+__global__ void k_in_dir(long n, const float* __restrict__ z, float* __restrict__ pi, int first,
+                         const DevState* __restrict__ ds) {
+  const float beta = (float)ds->in_beta;
+  DOF_LOOP(n) pi[d] = first ? z[d] : z[d] + beta * pi[d];
+}
+
+// sigma = pi^T qi; the last block forms alpha = rho / sigma.  A
+// non-positive or non-finite sigma (rounding on a nearly converged inner
+// system) keeps the inner solution: alpha = 0, except on the first inner
+// iteration, where alpha = 1 leaves the V-cycle's output as the result.
+__global__ void k_in_pq(long n, const float* __restrict__ pi, const float* __restrict__ qi, int first,
+                        double* part, DevState* __restrict__ ds, unsigned* cnt) {
+  float fs = 0.f;
+  DOF_LOOP(n) fs = fmaf(pi[d], qi[d], fs);
+  const double s = block_sum((double)fs);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!last_block(cnt)) return;
+  const double sig = reduce_parts(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    const double rz = ds->in_rho_next;
+    const double alpha = rz / sig;
+    const bool ok = sig > 0.0 && alpha == alpha && fabs(alpha) < 1e30;
+    ds->in_alpha = ok ? alpha : (first ? 1.0 : 0.0);
+    ds->in_rho = rz;
+    *cnt = 0u;
+  }
+}
+
+// e += alpha pi; unless last: ri -= alpha qi, b0 = ri, v0 = omega D^-1 ri
+// (the next V-cycle's input and its first smoothing step); last: z0 = e.
+__global__ void k_in_update(long n, float* __restrict__ e, float* __restrict__ ri, const float* __restrict__ pi,
+                            const float* __restrict__ qi, float* __restrict__ b0, const float* __restrict__ dinv0,
+                            float omega, float* __restrict__ v0, float* __restrict__ z0, int last,
+                            const DevState* __restrict__ ds) {
+  const float a = (float)ds->in_alpha;
+  DOF_LOOP(n) {
+    const float ev = e[d] + a * pi[d];
+    if (last) {
+      z0[d] = ev;
+    } else {
+      e[d] = ev;
+      const float rv = ri[d] - a * qi[d];
+      ri[d] = rv;
+      b0[d] = rv;
+      v0[d] = omega * dinv0[d] * rv;
+    }
+  }
+}
+
 // Diagnostic: y = A x in the level's stored precision, FP64 in and out.
 template <typename T, bool kOrd>
 __global__ void __launch_bounds__(tile_threads<T>(), tile_blocks_per_sm<T>()) k_apply_diag(LevelView<T> V, const double* __restrict__ x,
@@ -865,6 +959,32 @@ bool launch_vcycle(int vt, Level* lv, int L, double omega, int gamma, const doub
   bool fused = false;
   VT_DISPATCH(vt, fused = vcycle_rec<T>(lv, 0, L, (T)omega, Ainv, tc, st, dots));
   return fused;
+}
+
+void launch_inner_pcg(Level* lv, int L, double omega, const double* Ainv, const TcOp& tc, const InnerPcg& in,
+                      double* part_a, double* part_b, DevState* ds, unsigned* cnt, cudaStream_t st) {
+  Level& L0 = lv[0];
+  const long n = L0.ndof;
+  const int g = parts_for(L0.nn);  // blocks of the reductions (<= kMaxPart partials)
+  float* b0 = (float*)L0.b;
+  float* v0 = (float*)L0.v;
+  float* z0 = (float*)L0.z;
+  k_in_init<<<g, kRowThreads, 0, st>>>(n, b0, in.ri, in.e);
+  for (int it = 0; it < in.its; ++it) {
+    const int first = it == 0, last = it == in.its - 1;
+    vcycle_rec<float>(lv, 0, L, (float)omega, Ainv, tc, st, nullptr);  // z0 = M^-1 b0
+    k_in_rz<<<g, kRowThreads, 0, st>>>(n, in.ri, z0, in.qi, first, part_a, part_b, ds, cnt);
+    k_in_dir<<<g, kRowThreads, 0, st>>>(n, z0, in.pi, first, ds);
+    if (tc.on && tc.deg >= 2) {  // qi = A pi on the tensor cores
+      launch_tc2_apply(tc.mode, tc.m, L0, in.pi, tc.w32, tc.img, tc.tscale, tc.Y2, tc.err, tc.sms, st);
+      launch_tc2_gather(L0, tc.Y2, in.pi, in.pi, L0.dinv32, 0.f, 2, in.qi, st);
+    } else {  // the FP32 element matrices
+      launch_q2_op(kVtF32, L0, L0.K32, L0.Y, nullptr, in.pi, nullptr, 0.0, 2, in.qi, L0.sms, st);
+    }
+    k_in_pq<<<g, kRowThreads, 0, st>>>(n, in.pi, in.qi, first, part_a, ds, cnt);
+    k_in_update<<<g, kRowThreads, 0, st>>>(n, in.e, in.ri, in.pi, in.qi, b0, L0.dinv32, (float)omega, v0, z0, last,
+                                           ds);
+  }
 }
 
 void launch_set_params(DevState* ds, const double* params, cudaStream_t st) {

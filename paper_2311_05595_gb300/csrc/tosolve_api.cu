@@ -148,6 +148,12 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (d.omega != 0.0 && !(d.omega > 0.0 && d.omega < 2.0)) { *why = "omega must be in (0, 2)"; return TOSOLVE_EINVAL; }
   if (d.cycle_gamma != 0 && d.cycle_gamma != 1) { *why = "only the V-cycle (gamma = 1) is built"; return TOSOLVE_EINVAL; }
   if (d.max_rhs < 0 || d.max_rhs > 64) { *why = "max_rhs must be in 0..64"; return TOSOLVE_EINVAL; }
+  if (d.inner_its < 0 || d.inner_its > 64) { *why = "inner_its must be in 0..64"; return TOSOLVE_EINVAL; }
+  if (d.inner_its > 0 && (d.degree != 2 || d.precision == TOSOLVE_PREC_FP64 || d.precision == TOSOLVE_PREC_FP32X2 ||
+                          d.mg_levels == 1)) {
+    *why = "inner FP32 iterations need degree 2, an FP32-vector precision and a V-cycle (mg_levels != 1)";
+    return TOSOLVE_EINVAL;
+  }
   int L = d.mg_levels;
   if (L == 0) {
     L = d.degree == 3 ? 2 : 1;
@@ -236,6 +242,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
     B += E0 * (P->m + 24) * 4 + (size_t)P->m * 576 * 4 + P->lv[0].ndof * 4;
   }
+  if (d.inner_its > 0) B += 4 * (size_t)P->lv[0].ndof * 4;  // inner PCG vectors
   if (tc2) {  // weights, element results and the table image of the tensor-core level
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
     B += E0 * (P->m + tc2_result_stride()) * 4 + tc2_image_bytes(tc2_mode_of(d.precision), P->m);
@@ -272,6 +279,7 @@ void free_all(tosolve_s* h) {
   F(h->Yq); F(h->Mq); F(h->Mqc); F(h->slv0); F(h->fix0);
   F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab); F(h->ptab3);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->tcimg); F(h->Y2); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
+  F(h->inner.e); F(h->inner.ri); F(h->inner.pi); F(h->inner.qi);
   F(h->Ad); F(h->Wp); F(h->Vp); F(h->Pg); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
   F(h->cnt);
@@ -338,8 +346,12 @@ cudaError_t append_solve(tosolve_s* h, cudaStream_t cs, cudaStream_t bs) {
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     const CgDots cd{h->r, h->q, part2, part3, h->ds, h->cnt + 1};
-    if (!launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, bs, &cd))
+    if (h->inner.its > 0) {
+      launch_inner_pcg(h->lv, h->L, h->d.omega, h->Ainv, h->tc, h->inner, part2, part3, h->ds, h->cnt + 1, bs);
       launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, bs);
+    } else if (!launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, bs, &cd)) {
+      launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, bs);
+    }
     launch_cg_dir(vt, L0, h->p, np, h->ds, bs);
     launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, bs);
     launch_cg_update(vt, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, hc, 1,
@@ -812,6 +824,14 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     CKC(dalloc(h, pv, nd));
     CKC(cudaMemsetAsync(*pv, 0, nd * 8, st));
   }
+  if (h->d.inner_its > 0) {
+    float** iv[4] = {&h->inner.e, &h->inner.ri, &h->inner.pi, &h->inner.qi};
+    for (float** pv : iv) {
+      CKC(dalloc(h, pv, nd));
+      CKC(cudaMemsetAsync(*pv, 0, nd * sizeof(float), st));
+    }
+    h->inner.its = h->d.inner_its;
+  }
   CKC(dalloc(h, &h->part, 4 * kMaxPart));
   CKC(cudaMemsetAsync(h->part, 0, 4 * kMaxPart * 8, st));
   CKC(dalloc(h, &h->cnt, 4));
@@ -905,11 +925,21 @@ static tosolve_status refresh(tosolve_t h) {
   }
   Level& C = h->lv[L - 1];
   if (d.degree >= 2) {
+    // Lagrange degree-2 levels by sum factorisation; the serendipity element
+    // and the cubic finest level by their subcell tables / moment bases
+    auto form = [&](Level& Lv, int l, double* Kdst, double* Mscr, cudaStream_t s) {
+      if (d.family == 0 && Lv.k == 2 && q2_elem_sf_supported(Lv.nsub))
+        launch_q2_elem_sf(Lv, h->w, h->Dx, h->Dy, d.nu, Kdst, s);
+      else if (l == 0)
+        launch_q2_elem(Lv, n, h->w, h->Dx, h->Dy, h->tab64, Kdst, s);
+      else
+        launch_q2_coarse_elem(Lv, h->w, h->Dx, h->Dy, h->cmom64, Mscr, Kdst, s);
+    };
     const double* Kc = h->Kec;
     if (L > 1) {
-      launch_q2_coarse_elem(C, h->w, h->Dx, h->Dy, h->cmom64, h->Mqc, h->Kec, cst);
+      form(C, L - 1, h->Kec, h->Mqc, cst);
     } else {
-      launch_q2_elem(C, n, h->w, h->Dx, h->Dy, h->tab64, C.K64, cst);
+      form(C, 0, C.K64, nullptr, cst);
       if (h->mixed) launch_q2_constrain(C, h->slv0, C.K64, C.sms, cst);
       Kc = C.K64;
     }
@@ -920,11 +950,8 @@ static tosolve_status refresh(tosolve_t h) {
                             h->cgrid, cst));
     for (int l = 0; l + 1 < L; ++l) {
       Level& Lv = h->lv[l];
-      if (l == 0) {
-        launch_q2_elem(Lv, n, h->w, h->Dx, h->Dy, h->tab64, Lv.K64, st);
-        if (h->mixed) launch_q2_constrain(Lv, h->slv0, Lv.K64, Lv.sms, st);
-      } else
-        launch_q2_coarse_elem(Lv, h->w, h->Dx, h->Dy, h->cmom64, h->Mq, Lv.K64, st);
+      form(Lv, l, Lv.K64, h->Mq, st);
+      if (l == 0 && h->mixed) launch_q2_constrain(Lv, h->slv0, Lv.K64, Lv.sms, st);
       launch_q2_dinv(true, Lv, Lv.K64, Lv.dinv64, st);
       if (Lv.K32) launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * (Lv.k == 3 ? kDD3 : kDD2), Lv.K64, Lv.K32, st);
       if (Lv.dinv32) launch_q2_dinv(false, Lv, Lv.K64, Lv.dinv32, st);
@@ -1182,8 +1209,12 @@ static tosolve_status run_loop_nograph(tosolve_t h) {
   CK(cudaStreamSynchronize(st));
   while (!h->hs->converged && h->hs->status == 0 && h->hs->iter < h->hs->maxit) {
     const CgDots cd{h->r, h->q, part2, part3, h->ds, h->cnt + 1};
-    if (!launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, st, &cd))
+    if (h->inner.its > 0) {
+      launch_inner_pcg(h->lv, h->L, h->d.omega, h->Ainv, h->tc, h->inner, part2, part3, h->ds, h->cnt + 1, st);
       launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, st);
+    } else if (!launch_vcycle(vt, h->lv, h->L, h->d.omega, 1, h->Ainv, h->tc, st, &cd)) {
+      launch_cg_dots_rz(vt, L0, h->r, h->q, part2, part3, np, h->ds, h->cnt + 1, st);
+    }
     launch_cg_dir(vt, L0, h->p, np, h->ds, st);
     launch_cg_apply(L0, h->p, h->q, part0, np, h->ds, h->cnt + 2, st);
     launch_cg_update(vt, L0, h->d.omega, h->u, h->r, h->p, h->q, part1, np, h->ds, h->cnt + 3, 0, 0,
@@ -1306,7 +1337,10 @@ tosolve_status tosolve_compliance_grad(tosolve_t h, const double* u_dev, const d
     CK(cudaMemcpyAsync(&h->hs->c, &h->ds->c, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c_host[r] = h->hs->c;
-    if (want_grad && d.degree >= 2)
+    if (want_grad && d.degree == 2 && d.family == 0 && q2_energy_sf_supported(d.n_mr))
+      launch_q2_energy_sf(h->lv[0], d.n_mr, d.nu, u_dev + r * nd, h->rho, d.penal, d.E0 - d.Emin, h->Dx, h->Dy,
+                          r == 0, g, h->lv[0].sms, st);
+    else if (want_grad && d.degree >= 2)
       launch_q2_energy_grad(h->lv[0], d.n_mr, u_dev + r * nd, h->tab64, h->rho, d.penal, d.E0 - d.Emin,
                             h->Dx, h->Dy, r == 0, g, h->lv[0].sms, st);
     else if (want_grad)

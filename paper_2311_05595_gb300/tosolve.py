@@ -29,7 +29,7 @@ class tosolve_desc(C.Structure):
         ("penal", C.c_double), ("rmin", C.c_double),
         ("mg_levels", C.c_int), ("precision", C.c_int),
         ("omega", C.c_double), ("cycle_gamma", C.c_int), ("max_rhs", C.c_int),
-        ("family", C.c_int), ("prolongation", C.c_int),
+        ("family", C.c_int), ("prolongation", C.c_int), ("inner_its", C.c_int),
     ]
 
 
@@ -143,9 +143,9 @@ FAMILY_LAGRANGE, FAMILY_SERENDIPITY = 0, 1
 
 def make_desc(nx, ny, nz, *, degree=1, n_mr=1, d_mr=None, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0,
               rmin=0.0, mg_levels=0, precision=PREC_FP64, omega=0.0, cycle_gamma=1,
-              max_rhs=1, family=FAMILY_LAGRANGE, prolongation=0) -> tosolve_desc:
+              max_rhs=1, family=FAMILY_LAGRANGE, prolongation=0, inner_its=0) -> tosolve_desc:
     return tosolve_desc(nx, ny, nz, degree, n_mr, d_mr or n_mr, E0, Emin, nu, penal, rmin, mg_levels,
-                        precision, omega, cycle_gamma, max_rhs, family, prolongation)
+                        precision, omega, cycle_gamma, max_rhs, family, prolongation, inner_its)
 
 
 # ---- the C ABI, same names ----------------------------------------------------

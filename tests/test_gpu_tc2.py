@@ -163,3 +163,58 @@ def test_tc2_bridge_full_size(prec):
         assert info.iterations <= 120, info.iterations
     _check_sampled(R.T, R, p, u[0], 1e-8, np.random.default_rng(5), nodes=80, cells=20, dcells=4)
     R.close()
+
+
+@pytest.mark.parametrize("prec,inner", [(F16X3, 6), (BF16, 4), (FP32, 5)])
+def test_inner_fp32_iterations_match_direct_solve(prec, inner):
+    """Each outer FP64 iteration preconditioned by a few FP32 PCG iterations
+    on the preconditioner's level-0 operator (inner_its): the converged
+    solution, compliance and gradient are the direct solve's, and the outer
+    FP64 iterations drop well below the single-V-cycle count."""
+    from paper_2311_05595_gb300 import tosolve as T
+
+    p = workloads.bridge(8, 4, 4, degree=2, n_mr=3, rmin=0.0, seed=6, mg_levels=2)
+    ref = fe.Model(p).run(method="splu")
+    R = Run(p, prec)
+    R.set_densities()
+    _, plain = R.solve(rtol=1e-11)
+    R.close()
+    R = Run(p, prec)
+    R.close()
+    R.solver = T.Solver(T.make_desc(p.nx, p.ny, p.nz, degree=2, n_mr=p.n_mr, nu=p.nu, penal=p.penal,
+                                    Emin=p.Emin, mg_levels=2, precision=prec, inner_its=inner),
+                        p.mask, R.stream)
+    R.h = R.solver.h
+    R.set_densities()
+    u, info = R.solve(rtol=1e-11)
+    assert info.rel_residual <= 1e-11
+    assert info.iterations < plain.iterations, (info.iterations, plain.iterations)
+    assert rel(u.cpu().numpy()[0], ref["u"][0]) <= 1e-6
+    c, gx, gr = R.grad(u)
+    assert abs(c[0] - ref["c"][0]) <= 1e-7 * abs(ref["c"][0])
+    assert rel(gr, ref["g_rho"]) <= 1e-6
+    R.close()
+
+
+def test_inner_iterations_on_a_mixed_mesh():
+    """FP32 inner iterations on the element matrices of a mixed trilinear /
+    triquadratic mesh (slaved midside nodes): the mixed oracle's solution."""
+    from oracle import mixed
+    from paper_2311_05595_gb300 import tosolve as T
+
+    p = workloads.with_mixed_degree(workloads.bridge(8, 4, 4, degree=2, n_mr=2, seed=3, mg_levels=2), 0.5, 5)
+    ref = mixed.MixedModel(p).run(method="splu")
+    R = Run(p, FP32)
+    R.close()
+    R.solver = T.Solver(T.make_desc(p.nx, p.ny, p.nz, degree=2, n_mr=p.n_mr, nu=p.nu, penal=p.penal,
+                                    Emin=p.Emin, mg_levels=2, precision=FP32, inner_its=6),
+                        p.mask, R.stream, elem_q1=p.elem_q1)
+    R.h = R.solver.h
+    R.set_densities()
+    u, info = R.solve(rtol=1e-11)
+    assert info.rel_residual <= 1e-11
+    assert rel(u.cpu().numpy()[0], ref["u"][0]) <= 1e-6
+    c, gx, _ = R.grad(u)
+    assert abs(c[0] - ref["c"][0]) <= 1e-7 * abs(ref["c"][0])
+    assert rel(gx, ref["g_x"]) <= 1e-6
+    R.close()
