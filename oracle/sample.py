@@ -147,9 +147,16 @@ class Sampler:
         """(len(nodes), 3): sum over the elements e at the node and their
         subcells i of w_{e,i} sum_j |K^(e_i)_rj| |u_j| -- the rounding scale
         of the stacked form of Eq. matrixK_mr (one rounded product per
-        subcell); supports |u|.  Trilinear/triquadratic mixing not covered."""
+        subcell); supports |u|.  Mixed meshes: a triquadratic element rounds
+        its expanded vector T_e u_e and its result is folded by T_e^T (>= 0
+        entrywise), so it adds T_e^T |K^(e_i)| |T_e u_e|; a trilinear element
+        rounds its vertex vector against the trilinear subcell matrices
+        (T^T K^(e_i) T restricted to the vertices); slaved rows are identity
+        rows.  deflate: each rounded vector minus its least-squares rigid
+        motion (rigid_projector); elem_max: its entries replaced by their
+        largest magnitude."""
         if self.slv is not None:
-            raise ValueError("subcell scale of a mixed mesh is not defined here")
+            return self._mixed_subcell_scale(x, u, nodes, deflate, elem_max)
         held = self.p.mask.astype(bool)
         uf = np.where(held, 0.0, u)
         P = rigid_projector(self.k) if deflate else None
@@ -168,6 +175,51 @@ class Sampler:
                 a = en.index(nd)
                 for i in range(len(cells)):
                     out[q] += w[i] * (np.abs(self.K[i][3 * a: 3 * a + 3]) @ ue)
+            for c in range(3):
+                if held[3 * nd + c]:
+                    out[q, c] = abs(u[3 * nd + c])
+        return out
+
+    def _mixed_subcell_scale(self, x, u, nodes, deflate, elem_max):
+        held = self.p.mask.astype(bool) | np.repeat(self.slv, 3)
+        uf = np.where(held, 0.0, u)
+        P2 = rigid_projector(2) if deflate else None
+        P1 = rigid_projector(1) if deflate else None
+        if not hasattr(self, "K1"):
+            self.K1 = fem.subcell_stiffness(1, self.n, self.p.nu)
+        vloc = [2 * (v & 1) + 3 * (2 * ((v >> 1) & 1)) + 9 * (2 * (v >> 2)) for v in range(8)]
+        cache = {}
+        out = np.zeros((len(nodes), 3))
+        for q, nd in enumerate(nodes):
+            for (ex, ey, ez) in self.elements_of(nd):
+                cells = self._elem_cells(ex, ey, ez)
+                rho = np.array([cache.setdefault(c, self.rho(x, c)) for c in cells])
+                w = simp_weights(rho, self.p.E0, self.p.Emin, self.p.penal)
+                en = self._elem_nodes(ex, ey, ez)
+                a = en.index(nd)
+                dofs = np.array([3 * m + c for m in en for c in range(3)])
+                e = ex + self.p.nx * (ey + self.p.ny * ez)
+                if self.p.elem_q1[e]:
+                    if a not in vloc:
+                        continue  # a slaved node of this element: identity row
+                    vd = np.array([3 * vloc[v] + c for v in range(8) for c in range(3)])
+                    ue = uf[dofs][vd]
+                    ue = np.abs(ue if P1 is None else P1 @ ue)
+                    if elem_max:
+                        ue = np.full_like(ue, ue.max())
+                    v = vloc.index(a)
+                    for i in range(len(cells)):
+                        out[q] += w[i] * (np.abs(self.K1[i][3 * v: 3 * v + 3]) @ ue)
+                else:
+                    T = self._T_e(en)
+                    ue = T @ uf[dofs]
+                    ue = np.abs(ue if P2 is None else P2 @ ue)
+                    if elem_max:
+                        ue = np.full_like(ue, ue.max())
+                    z = np.zeros(3 * len(en))
+                    for i in range(len(cells)):
+                        z += w[i] * (np.abs(self.K[i]) @ ue)
+                    out[q] += (T.T @ z)[3 * a: 3 * a + 3]
             for c in range(3):
                 if held[3 * nd + c]:
                     out[q, c] = abs(u[3 * nd + c])

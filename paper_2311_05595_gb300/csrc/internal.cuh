@@ -104,6 +104,14 @@ struct Level {
   double* Kc64 = nullptr;
   float* Kc32 = nullptr;
   void* Y = nullptr;  // per-element results of an apply (shared scratch)
+  // mixed trilinear / triquadratic level 0: the triquadratic elements (el2,
+  // ne2; sl2 the 27-bit masks of their slaved local nodes) and the
+  // trilinear ones (el1, ne1), ascending; null elsewhere
+  const int* el2 = nullptr;
+  long ne2 = 0;
+  const uint32_t* sl2 = nullptr;
+  const int* el1 = nullptr;
+  long ne1 = 0;
   uint8_t* mask = nullptr;
   int* tl = nullptr;    // tile order in force (LevelView::tl), or null: index order
   int* tcnt = nullptr;  // number of tiles with a free DOF (device), with tl
@@ -197,6 +205,8 @@ struct TcOp {
   int mode = 0;             // degree 2: operands (tc2_mode_of: TF32, BF16, BF16X3, F16X3)
   int prec = 0;             // degree 2: the tosolve_precision this mode serves
   float tscale = 1.f;       // degree 2, F16X3: power-of-two scale of the table image
+  const unsigned char* img1 = nullptr;  // mixed meshes: the trilinear table's image
+  float tscale1 = 1.f;
   int m = 1;                // subcells per element
   const float* w32 = nullptr;  // E x m element-major weights
   const float* KT = nullptr;   // degree 1: m x 24 x 24 FP32 table
@@ -225,19 +235,21 @@ inline int tc2_mode_of(int precision) {
   return precision == TOSOLVE_PREC_TF32 ? 0 : precision == TOSOLVE_PREC_BF16 ? 1
                                          : precision == TOSOLVE_PREC_BF16X3 ? 2 : 3;
 }
-// Bytes of the stacked table's shared-memory image for an operand mode.
-size_t tc2_image_bytes(int mode, int m);
+// Bytes of the stacked table's shared-memory image for an operand mode
+// (dofs 81: the triquadratic table; 24: the trilinear one of a mixed mesh).
+size_t tc2_image_bytes(int mode, int m, int dofs = 81);
 // Floats per element in the result buffer (81 rounded up to 16 bytes).
 size_t tc2_result_stride();
 // Power-of-two scale of the table image (F16X3: largest entry into
 // [0.5, 1) after dividing by it; else 1), from the host copy of the table.
 float tc2_table_scale(int mode, const double* tab_host, size_t count);
-void launch_tc2_image(int mode, int m, const double* tab, float tscale, unsigned char* img, cudaStream_t st);
-// Y = per-element stacked contraction of the level-0 vector v (fixed DOFs as
-// zero), weights w32 (E x m).
-cudaError_t launch_tc2_apply(int mode, int m, const Level& L0, const float* v, const float* w32,
-                             const unsigned char* img, float tscale, float* Y, int* err, int sms,
-                             cudaStream_t st);
+void launch_tc2_image(int mode, int m, int dofs, const double* tab, float tscale, unsigned char* img,
+                      cudaStream_t st);
+// tc.Y2 = per-element stacked contraction of the level-0 vector v (fixed
+// DOFs as zero), weights tc.w32 (E x m); on a mixed level 0 the triquadratic
+// elements with their slaved nodes (T_e^T K T_e) and the trilinear ones on
+// their vertices.
+cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cudaStream_t st);
 // Node gather of Y fused with the V-cycle step: mode 0 b - y, 1 v + omega
 // D^-1 (b - y), 2 y; identity rows at fixed DOFs.
 void launch_tc2_gather(const Level& L0, const float* Y, const float* b, const float* v, const float* dinv,
@@ -439,6 +451,12 @@ struct tosolve_s {
   bool mixed = false;
   long long free_dofs = 0;     // unknowns: DOFs neither supported nor slaved
   uint8_t* slv0 = nullptr;     // per lattice node: 1 = slaved to its vertices
+  int* el2 = nullptr;          // triquadratic elements (ascending)
+  uint32_t* sl2 = nullptr;     // their slaved local nodes (bit a = local node a)
+  int* el1 = nullptr;          // trilinear elements (ascending)
+  long ne2 = 0, ne1 = 0;
+  double* tab64q1 = nullptr;   // trilinear subcell table (tensor cores on a mixed mesh)
+  unsigned char* tcimg1 = nullptr;  // its shared-memory image
   uint8_t* fix0 = nullptr;     // per DOF: the supports alone (level 0 mask adds slaved)
   // fixing variables (Sec. 6.1)
   float* ptab = nullptr;         // shape-function transfer table (27 x 125)

@@ -753,14 +753,18 @@ __global__ void k_s2_restrict_gather(int Lxc, int Lyc, int Lzc, int ecx, int ecy
 // all fixed is skipped (no row of it is ever read: the gather passes fixed
 // DOFs through as identity rows), so suppressed void regions cost no
 // element-matrix traffic.
+// With an element list (mixed meshes: the triquadratic elements) only the
+// listed elements are applied.
 template <int K, typename T>
 __global__ void __launch_bounds__(Deg<K>::TB) k_q2_apply(int ex, int ey, long E, int Lx, int Ly,
                                                          const op_t<T>* __restrict__ Ke,
                                                          const uint8_t* __restrict__ mask,
-                                                         const T* __restrict__ u, T* __restrict__ Y) {
+                                                         const T* __restrict__ u, T* __restrict__ Y,
+                                                         const int* __restrict__ list) {
   constexpr int kD = Deg<K>::D, kDD = Deg<K>::DD;
   __shared__ T ue[kD];
-  for (long e = blockIdx.x; e < E; e += gridDim.x) {
+  for (long t = blockIdx.x; t < E; t += gridDim.x) {
+    const long e = list != nullptr ? (long)list[t] : t;
     const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
     bool free_dof = false;
     if (threadIdx.x < kD) {
@@ -776,6 +780,48 @@ __global__ void __launch_bounds__(Deg<K>::TB) k_q2_apply(int ex, int ey, long E,
 #pragma unroll 9
       for (int b = 0; b < kD; ++b) acc.add(Kc[(size_t)b * kD], ue[b]);
       Y[e * kD + threadIdx.x] = acc.value();
+    }
+    __syncthreads();
+  }
+}
+
+// Trilinear elements of a mixed mesh: their constrained 81 x 81 matrix is
+// T_e^T K T_e with every non-vertex node slaved to the vertices, which is
+// zero outside the 24 vertex DOFs, so the product needs only that block
+// (24 x 24, the trilinear element's matrix).  Results go to the vertex
+// positions of Y; the other positions of these elements belong to slaved
+// nodes, which the gather treats as identity rows.  Four elements per
+// block of 128 threads, thread r < 24 of each group computes vertex DOF r.
+__device__ __forceinline__ int q1v_dof(int r) {  // vertex DOF r -> DOF of the 27-node element
+  const int v = r / 3;
+  return 3 * (2 * (v & 1) + 3 * (2 * ((v >> 1) & 1)) + 9 * (2 * (v >> 2))) + r % 3;
+}
+template <typename T>
+__global__ void __launch_bounds__(128) k_q1v_apply(int ex, int ey, long E1, int Lx, int Ly,
+                                                   const op_t<T>* __restrict__ Ke,
+                                                   const uint8_t* __restrict__ mask, const T* __restrict__ u,
+                                                   T* __restrict__ Y, const int* __restrict__ list) {
+  __shared__ T ue[4][24];
+  const int grp = threadIdx.x >> 5, r = threadIdx.x & 31;
+  for (long t0 = (long)blockIdx.x * 4; t0 < E1; t0 += (long)gridDim.x * 4) {
+    const long t = t0 + grp;
+    const bool live = t < E1 && r < 24;
+    long e = 0;
+    int dr = 0;
+    if (live) {
+      e = list[t];
+      const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+      dr = q1v_dof(r);
+      const long d = 3 * elem_node(exi, eyi, ezi, dr / 3, Lx, Ly) + dr % 3;
+      ue[grp][r] = mask[d] ? T(0) : u[d];
+    }
+    __syncthreads();
+    if (live) {
+      const op_t<T>* Kr = Ke + e * (size_t)kDD;
+      Sum<T> acc;
+#pragma unroll 4
+      for (int c = 0; c < 24; ++c) acc.add(Kr[(size_t)q1v_dof(c) * kD + dr], ue[grp][c]);  // symmetric
+      Y[e * kD + dr] = acc.value();
     }
     __syncthreads();
   }
@@ -1382,15 +1428,31 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
                                               (T*)out);
       return;
     }
+    if (L.el2 != nullptr) {  // mixed level 0: triquadratic list, then the trilinear vertex blocks
+      long g2 = (long)sms * 16;
+      if (g2 > L.ne2) g2 = L.ne2;
+      if (g2 >= 1)
+        k_q2_apply<2, T><<<(int)g2, Deg<2>::TB, 0, st>>>(L.ex, L.ey, L.ne2, L.Lx, L.Ly, (const op_t<T>*)Ke,
+                                                          L.mask, (const T*)v, (T*)Y, L.el2);
+      long g1 = (long)sms * 8;
+      if (g1 > (L.ne1 + 3) / 4) g1 = (L.ne1 + 3) / 4;
+      if (g1 >= 1)
+        k_q1v_apply<T><<<(int)g1, 128, 0, st>>>(L.ex, L.ey, L.ne1, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
+                                                (const T*)v, (T*)Y, L.el1);
+      k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
+                                            (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
+                                            (T*)out);
+      return;
+    }
     if (L.k == 3) {
       k_q2_apply<3, T><<<(int)ga, Deg<3>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
-                                                        (const T*)v, (T*)Y);
+                                                        (const T*)v, (T*)Y, nullptr);
       k_q2_gather<3, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
                                             (T*)out);
     } else {
       k_q2_apply<2, T><<<(int)ga, Deg<2>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
-                                                        (const T*)v, (T*)Y);
+                                                        (const T*)v, (T*)Y, nullptr);
       k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
                                             (T*)out);

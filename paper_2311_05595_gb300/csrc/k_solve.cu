@@ -877,8 +877,7 @@ bool vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
   const bool use_tc = tc.on && l == 0;
   if constexpr (std::is_same<T, float>::value) {
     if (use_tc && tc.deg >= 2) {  // r = b - A v, A v from the degree-2 stacked contraction
-      launch_tc2_apply(tc.mode, tc.m, F, (const float*)F.v, tc.w32, tc.img, tc.tscale, tc.Y2, tc.err, tc.sms,
-                       st);
+      launch_tc2_apply(tc, F, (const float*)F.v, st);
       launch_tc2_gather(F, tc.Y2, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 0,
                         (float*)F.r, st);
     } else if (use_tc) {  // r = b - A v with A v from the tensor-core stacked contraction
@@ -908,8 +907,7 @@ bool vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
                                                               (const T*)C.z, (T*)F.v);
   if constexpr (std::is_same<T, float>::value) {
     if (use_tc && tc.deg >= 2) {  // z = v + omega D^-1 (b - A v)
-      launch_tc2_apply(tc.mode, tc.m, F, (const float*)F.v, tc.w32, tc.img, tc.tscale, tc.Y2, tc.err, tc.sms,
-                       st);
+      launch_tc2_apply(tc, F, (const float*)F.v, st);
       launch_tc2_gather(F, tc.Y2, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 1,
                         (float*)F.z, st);
       return false;
@@ -976,7 +974,7 @@ void launch_inner_pcg(Level* lv, int L, double omega, const double* Ainv, const 
     k_in_rz<<<g, kRowThreads, 0, st>>>(n, in.ri, z0, in.qi, first, part_a, part_b, ds, cnt);
     k_in_dir<<<g, kRowThreads, 0, st>>>(n, z0, in.pi, first, ds);
     if (tc.on && tc.deg >= 2) {  // qi = A pi on the tensor cores
-      launch_tc2_apply(tc.mode, tc.m, L0, in.pi, tc.w32, tc.img, tc.tscale, tc.Y2, tc.err, tc.sms, st);
+      launch_tc2_apply(tc, L0, in.pi, st);
       launch_tc2_gather(L0, tc.Y2, in.pi, in.pi, L0.dinv32, 0.f, 2, in.qi, st);
     } else {  // the FP32 element matrices
       launch_q2_op(kVtF32, L0, L0.K32, L0.Y, nullptr, in.pi, nullptr, 0.0, 2, in.qi, L0.sms, st);

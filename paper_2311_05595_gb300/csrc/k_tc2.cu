@@ -96,7 +96,7 @@ struct Shape {
   static constexpr uint32_t ABYTES = (uint32_t)kTm * KR * O::kEs;
   static constexpr uint32_t BBYTES = (uint32_t)NCH * KR * O::kEs;
   static constexpr size_t SMEM = 2 * (size_t)ABYTES + (size_t)O::kStages * BBYTES;
-  static constexpr int YS = (D + 3) / 4 * 4;  // stride of y_e in the result buffer
+  static constexpr int YS = 84;  // stride of y_e in the result buffer: the 81 DOFs of the 27-node layout
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -184,7 +184,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&q)[32]) {
 
 struct Tc2Args {
   int ex, ey, Lx, Ly;
-  long E;
+  long E;                     // elements to apply (the list's length when there is a list)
+  const int* list;            // element ids, or null: 0 .. E-1
+  const uint32_t* slm;        // per listed element, its slaved local nodes (mixed meshes), or null
   const float* v;             // level-0 vector, 3 per lattice node
   const uint8_t* mask;        // per DOF, 1 = fixed
   const float* w32;           // E x M subcell weights, element-major
@@ -194,26 +196,107 @@ struct Tc2Args {
   int* err;
 };
 
-// Local node a of a triquadratic element (a = ax + 3 (ay + 3 az)) on the lattice.
-__device__ __forceinline__ long q2_node(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
-  const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
-  return (2 * exi + ax) + (long)Lx * ((2 * eyi + ay) + (long)Ly * (2 * ezi + az));
+// The element's nodes on the degree-2 lattice: D = 81, the 27 nodes of a
+// triquadratic element (a = ax + 3 (ay + 3 az)); D = 24, the 8 vertices of a
+// trilinear element of a mixed mesh (v = vx + 2 (vy + 2 vz)), whose
+// results go to the vertex positions of the 27-node layout of Y.
+template <int D>
+struct Elem;
+template <>
+struct Elem<81> {
+  static constexpr int NN = 27;
+  __host__ __device__ static constexpr int off(int a, int d) { return d == 0 ? a % 3 : (d == 1 ? (a / 3) % 3 : a / 9); }
+  __host__ __device__ static constexpr int pos(int a, int d) { return off(a, d) - 1; }  // reference position
+  __host__ __device__ static constexpr int out(int r) { return r; }
+  static constexpr float kRot = 1.f / 36.f;  // 1 / (sum |x|^2 - sum x_d^2) over the nodes
+};
+template <>
+struct Elem<24> {
+  static constexpr int NN = 8;
+  __host__ __device__ static constexpr int off(int v, int d) { return 2 * ((v >> d) & 1); }
+  __host__ __device__ static constexpr int pos(int v, int d) { return off(v, d) - 1; }
+  __host__ __device__ static constexpr int out(int r) {
+    return 3 * (off(r / 3, 0) + 3 * (off(r / 3, 1) + 3 * off(r / 3, 2))) + r % 3;
+  }
+  static constexpr float kRot = 1.f / 16.f;
+};
+template <int D>
+__device__ __forceinline__ long elem_lattice_node(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
+  return (2 * exi + Elem<D>::off(a, 0)) + (long)Lx * ((2 * eyi + Elem<D>::off(a, 1)) + (long)Ly * (2 * ezi + Elem<D>::off(a, 2)));
 }
 
-// u_e minus its least-squares rigid motion t + omega x over the 27 nodes at
-// reference positions x_a in {-1, 0, 1}^3.  Every subcell matrix
+// Mixed meshes: a slaved local node of a triquadratic element carries the
+// linear interpolation of the vertices of its edge, face or cell (u = T_e
+// u, from the element's own vertices), and the element's result is folded
+// back (y <- T_e^T y): T_e^T K^(e) T_e applied without forming it.
+__device__ __forceinline__ void expand_slaved(float* u, uint32_t msk) {
+#pragma unroll
+  for (int a = 0; a < 27; ++a) {
+    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+    if (((ax | ay | az) & 1) == 0) continue;  // vertices are never slaved
+    if (!((msk >> a) & 1u)) continue;
+    const int nx = ax == 1 ? 2 : 1, ny = ay == 1 ? 2 : 1, nz = az == 1 ? 2 : 1;
+    const float wgt = 1.f / (float)(nx * ny * nz);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float acc = 0.f;
+#pragma unroll
+      for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+        for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < 2; ++kx) {
+            if (kx >= nx || ky >= ny || kz >= nz) continue;
+            const int px = ax == 1 ? 2 * kx : ax, py = ay == 1 ? 2 * ky : ay, pz = az == 1 ? 2 * kz : az;
+            acc += u[3 * (px + 3 * (py + 3 * pz)) + c];
+          }
+      u[3 * a + c] = wgt * acc;
+    }
+  }
+}
+__device__ __forceinline__ void fold_slaved(float* y, uint32_t msk) {
+#pragma unroll
+  for (int a = 0; a < 27; ++a) {
+    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+    if (((ax | ay | az) & 1) == 0) continue;
+    if (!((msk >> a) & 1u)) continue;
+    const int nx = ax == 1 ? 2 : 1, ny = ay == 1 ? 2 : 1, nz = az == 1 ? 2 : 1;
+    const float wgt = 1.f / (float)(nx * ny * nz);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float v = wgt * y[3 * a + c];
+#pragma unroll
+      for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+        for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < 2; ++kx) {
+            if (kx >= nx || ky >= ny || kz >= nz) continue;
+            const int px = ax == 1 ? 2 * kx : ax, py = ay == 1 ? 2 * ky : ay, pz = az == 1 ? 2 * kz : az;
+            y[3 * (px + 3 * (py + 3 * pz)) + c] += v;
+          }
+      y[3 * a + c] = 0.f;
+    }
+  }
+}
+
+// u_e minus its least-squares rigid motion t + omega x over the element's
+// nodes at reference positions x_a (the 27 points of {-1, 0, 1}^3, or the 8
+// vertices {-1, 1}^3).  Every subcell matrix
 // annihilates rigid motions (they carry no strain), so K^(e_i) u_e is
 // unchanged in exact arithmetic, but the rounded operands then carry an
 // error relative to the element's deformation instead of its displacement:
 // a smooth multigrid correction is locally almost rigid, and rounding it
 // whole would leave spurious forces of the rounding unit times |K| |u|.
-// For this symmetric lattice sum_a x_a = 0 and sum_a x_a x_a^T = 18 I, so
-// t is the mean and omega = (1/36) sum_a x_a x u_a.
+// For these symmetric node sets sum_a x_a = 0 and sum_a x_a x_a^T = s I
+// (s = 18 resp. 8), so t is the mean and omega = sum_a x_a x u_a / (3 s - s).
+template <int D>
 __device__ __forceinline__ void deflate_rigid(float* u) {
+  constexpr int NN = Elem<D>::NN;
   float t[3] = {0.f, 0.f, 0.f}, om[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int nd = 0; nd < 27; ++nd) {
-    const float px = (float)(nd % 3 - 1), py = (float)((nd / 3) % 3 - 1), pz = (float)(nd / 9 - 1);
+  for (int nd = 0; nd < NN; ++nd) {
+    const float px = (float)Elem<D>::pos(nd, 0), py = (float)Elem<D>::pos(nd, 1), pz = (float)Elem<D>::pos(nd, 2);
     const float ux = u[3 * nd], uy = u[3 * nd + 1], uz = u[3 * nd + 2];
     t[0] += ux;
     t[1] += uy;
@@ -224,12 +307,12 @@ __device__ __forceinline__ void deflate_rigid(float* u) {
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    t[c] *= 1.f / 27.f;
-    om[c] *= 1.f / 36.f;
+    t[c] *= 1.f / (float)NN;
+    om[c] *= Elem<D>::kRot;
   }
 #pragma unroll
-  for (int nd = 0; nd < 27; ++nd) {
-    const float px = (float)(nd % 3 - 1), py = (float)((nd / 3) % 3 - 1), pz = (float)(nd / 9 - 1);
+  for (int nd = 0; nd < NN; ++nd) {
+    const float px = (float)Elem<D>::pos(nd, 0), py = (float)Elem<D>::pos(nd, 1), pz = (float)Elem<D>::pos(nd, 2);
     u[3 * nd] -= t[0] + (om[1] * pz - om[2] * py);
     u[3 * nd + 1] -= t[1] + (om[2] * px - om[0] * pz);
     u[3 * nd + 2] -= t[2] + (om[0] * py - om[1] * px);
@@ -417,8 +500,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
     const int row = 32 * quarter + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
     for (long j = 0; j < ntl; ++j) {
-      const long e = (blockIdx.x + j * gridDim.x) * (long)kTm + row;
-      const bool live = e < a.E;
+      const long ei = (blockIdx.x + j * gridDim.x) * (long)kTm + row;
+      const bool live = ei < a.E;
+      const long e = !live ? 0 : (a.list != nullptr ? (long)a.list[ei] : ei);
       float sc = a.tscale;
       if constexpr (O::kScaled) {
         // the gather of this tile published the row scales before its
@@ -466,12 +550,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
         break;
       }
       if (live) {
-        float4* dst = reinterpret_cast<float4*>(a.Y + e * S::YS);
+        if constexpr (D == 81) {
+          if (a.slm != nullptr) fold_slaved(y, a.slm[ei]);
+          float4* dst = reinterpret_cast<float4*>(a.Y + e * S::YS);
 #pragma unroll
-        for (int t = 0; t < S::YS / 4; ++t) {
-          const int r = 4 * t;
-          dst[t] = make_float4(r < D ? sc * y[r] : 0.f, r + 1 < D ? sc * y[r + 1] : 0.f,
-                               r + 2 < D ? sc * y[r + 2] : 0.f, r + 3 < D ? sc * y[r + 3] : 0.f);
+          for (int t = 0; t < S::YS / 4; ++t) {
+            const int r = 4 * t;
+            dst[t] = make_float4(r < D ? sc * y[r] : 0.f, r + 1 < D ? sc * y[r + 1] : 0.f,
+                                 r + 2 < D ? sc * y[r + 2] : 0.f, r + 3 < D ? sc * y[r + 3] : 0.f);
+          }
+        } else {  // the vertex positions of the 27-node layout (the others are slaved)
+          float* dst = a.Y + e * S::YS;
+#pragma unroll
+          for (int r = 0; r < D; ++r) dst[Elem<D>::out(r)] = sc * y[r];
         }
       }
     }
@@ -486,22 +577,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
 #pragma unroll 1
       for (int rr = 0; rr < 2; ++rr) {
         const int row = 32 * (warp - 6) + lane + 64 * rr;
-        const long e = (blockIdx.x + j * gridDim.x) * (long)kTm + row;
+        const long ei = (blockIdx.x + j * gridDim.x) * (long)kTm + row;
         float u[S::KP];
 #pragma unroll
         for (int k = 0; k < S::KP; ++k) u[k] = 0.f;
-        if (e < a.E) {
+        if (ei < a.E) {
+          const long e = a.list != nullptr ? (long)a.list[ei] : ei;
           const int exi = (int)(e % a.ex), eyi = (int)((e / a.ex) % a.ey), ezi = (int)(e / ((long)a.ex * a.ey));
 #pragma unroll
           for (int nd = 0; nd < D / 3; ++nd) {
-            const long d0 = 3 * q2_node(exi, eyi, ezi, nd, a.Lx, a.Ly);
+            const long d0 = 3 * elem_lattice_node<D>(exi, eyi, ezi, nd, a.Lx, a.Ly);
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) {
               const float x = __ldg(a.v + d0 + cc);
               u[3 * nd + cc] = __ldg(a.mask + d0 + cc) ? 0.f : x;
             }
           }
-          deflate_rigid(u);
+          if constexpr (D == 81)
+            if (a.slm != nullptr) expand_slaved(u, a.slm[ei]);
+          deflate_rigid<D>(u);
         }
         unsigned char* dstrow = sA + (size_t)ab * S::ABYTES + (size_t)(row >> 3) * S::SBO + (row & 7) * 16;
         const float s = store_row<MD, S::KP>(u, dstrow);
@@ -608,23 +702,26 @@ __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, con
   }
 }
 
-template <int MD, int M>
-cudaError_t run_apply(const Level& L0, const float* v, const float* w32, const unsigned char* img, float tscale,
-                      float* Y, int* err, int sms, cudaStream_t st) {
-  using S = Shape<MD, kD2, M>;
+template <int MD, int D, int M>
+cudaError_t run_apply(const Level& L0, long count, const int* list, const uint32_t* slm, const float* v,
+                      const float* w32, const unsigned char* img, float tscale, float* Y, int* err, int sms,
+                      cudaStream_t st) {
+  using S = Shape<MD, D, M>;
   static std::once_flag once;  // handles may be created from several threads
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_tc2_apply<MD, kD2, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)S::SMEM);
+    attr = cudaFuncSetAttribute(k_tc2_apply<MD, D, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   });
   if (attr != cudaSuccess) return attr;
+  if (count <= 0) return cudaSuccess;
   Tc2Args a;
   a.ex = L0.ex;
   a.ey = L0.ey;
   a.Lx = L0.Lx;
   a.Ly = L0.Ly;
-  a.E = (long)L0.ex * L0.ey * L0.ez;
+  a.E = count;
+  a.list = list;
+  a.slm = slm;
   a.v = v;
   a.mask = L0.mask;
   a.w32 = w32;
@@ -632,59 +729,77 @@ cudaError_t run_apply(const Level& L0, const float* v, const float* w32, const u
   a.tscale = tscale;
   a.Y = Y;
   a.err = err;
-  const long ntiles = (a.E + kTm - 1) / kTm;
+  const long ntiles = (count + kTm - 1) / kTm;
   const int g = (int)(ntiles < sms ? ntiles : sms);
-  k_tc2_apply<MD, kD2, M><<<g, kThreads, S::SMEM, st>>>(a);
+  k_tc2_apply<MD, D, M><<<g, kThreads, S::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int MD>
+template <int MD, int D>
 size_t image_bytes_for(int m) {
   switch (m) {
-    case 1: return (size_t)Shape<MD, kD2, 1>::NC * Shape<MD, kD2, 1>::BBYTES;
-    case 8: return (size_t)Shape<MD, kD2, 8>::NC * Shape<MD, kD2, 8>::BBYTES;
-    case 27: return (size_t)Shape<MD, kD2, 27>::NC * Shape<MD, kD2, 27>::BBYTES;
+    case 1: return (size_t)Shape<MD, D, 1>::NC * Shape<MD, D, 1>::BBYTES;
+    case 8: return (size_t)Shape<MD, D, 8>::NC * Shape<MD, D, 8>::BBYTES;
+    case 27: return (size_t)Shape<MD, D, 27>::NC * Shape<MD, D, 27>::BBYTES;
     default: return 0;
   }
 }
 
-template <int MD>
-cudaError_t apply_for(int m, const Level& L0, const float* v, const float* w32, const unsigned char* img,
-                      float tscale, float* Y, int* err, int sms, cudaStream_t st) {
-  if (m == 27) return run_apply<MD, 27>(L0, v, w32, img, tscale, Y, err, sms, st);
-  if (m == 8) return run_apply<MD, 8>(L0, v, w32, img, tscale, Y, err, sms, st);
-  if (m == 1) return run_apply<MD, 1>(L0, v, w32, img, tscale, Y, err, sms, st);
+template <int MD, int D>
+cudaError_t apply_for(int m, const Level& L0, long count, const int* list, const uint32_t* slm, const float* v,
+                      const float* w32, const unsigned char* img, float tscale, float* Y, int* err, int sms,
+                      cudaStream_t st) {
+  if (m == 27) return run_apply<MD, D, 27>(L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
+  if (m == 8) return run_apply<MD, D, 8>(L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
+  if (m == 1) return run_apply<MD, D, 1>(L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
   return cudaErrorInvalidValue;
 }
 
-template <int MD>
+template <int D>
+cudaError_t apply_mode(int mode, int m, const Level& L0, long count, const int* list, const uint32_t* slm,
+                       const float* v, const float* w32, const unsigned char* img, float tscale, float* Y, int* err,
+                       int sms, cudaStream_t st) {
+  switch (mode) {
+    case kTF32: return apply_for<kTF32, D>(m, L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
+    case kBF16: return apply_for<kBF16, D>(m, L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
+    case kBF16X3: return apply_for<kBF16X3, D>(m, L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
+    case kF16X3: return apply_for<kF16X3, D>(m, L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int MD, int D>
 void image_for(int m, const double* tab, double tinv, unsigned char* img, cudaStream_t st) {
-  using S = Shape<MD, kD2, 1>;
+  using S = Shape<MD, D, 1>;
   using O = Opnd<MD>;
-  const size_t bytes = image_bytes_for<MD>(m);
+  const size_t bytes = image_bytes_for<MD, D>(m);
   // one thread per (chunk row, K column of one part)
   const long total = (long)(bytes / O::kEs / O::kParts);
   long g = (total + 255) / 256;
   if (g > 4096) g = 4096;
-  k_tc2_image<<<(int)g, 256, 0, st>>>(MD, kD2, m, O::kNch, S::KP, O::kParts, O::kKc, S::SBO, tinv, tab, img,
-                                      total);
+  k_tc2_image<<<(int)g, 256, 0, st>>>(MD, D, m, O::kNch, S::KP, O::kParts, O::kKc, S::SBO, tinv, tab, img, total);
+}
+
+template <int D>
+size_t image_bytes_mode(int mode, int m) {
+  switch (mode) {
+    case kTF32: return image_bytes_for<kTF32, D>(m);
+    case kBF16: return image_bytes_for<kBF16, D>(m);
+    case kBF16X3: return image_bytes_for<kBF16X3, D>(m);
+    case kF16X3: return image_bytes_for<kF16X3, D>(m);
+    default: return 0;
+  }
 }
 
 }  // namespace
 
 bool tc2_supported(int n) { return n >= 1 && n <= 3; }
 
-size_t tc2_image_bytes(int mode, int m) {
-  switch (mode) {
-    case kTF32: return image_bytes_for<kTF32>(m);
-    case kBF16: return image_bytes_for<kBF16>(m);
-    case kBF16X3: return image_bytes_for<kBF16X3>(m);
-    case kF16X3: return image_bytes_for<kF16X3>(m);
-    default: return 0;
-  }
+size_t tc2_image_bytes(int mode, int m, int dofs) {
+  return dofs == 24 ? image_bytes_mode<24>(mode, m) : image_bytes_mode<81>(mode, m);
 }
 
-size_t tc2_result_stride() { return (size_t)Shape<kTF32, kD2, 1>::YS; }
+size_t tc2_result_stride() { return (size_t)Shape<kTF32, 81, 1>::YS; }
 
 float tc2_table_scale(int mode, const double* tab_host, size_t count) {
   if (mode != kF16X3) return 1.f;
@@ -696,32 +811,44 @@ float tc2_table_scale(int mode, const double* tab_host, size_t count) {
   return (float)std::ldexp(1.0, ex2);
 }
 
-void launch_tc2_image(int mode, int m, const double* tab, float tscale, unsigned char* img, cudaStream_t st) {
+void launch_tc2_image(int mode, int m, int dofs, const double* tab, float tscale, unsigned char* img,
+                      cudaStream_t st) {
   const double tinv = 1.0 / (double)tscale;
+  if (dofs == 24) {
+    switch (mode) {
+      case kTF32: image_for<kTF32, 24>(m, tab, tinv, img, st); break;
+      case kBF16: image_for<kBF16, 24>(m, tab, tinv, img, st); break;
+      case kBF16X3: image_for<kBF16X3, 24>(m, tab, tinv, img, st); break;
+      default: image_for<kF16X3, 24>(m, tab, tinv, img, st); break;
+    }
+    return;
+  }
   switch (mode) {
-    case kTF32: image_for<kTF32>(m, tab, tinv, img, st); break;
-    case kBF16: image_for<kBF16>(m, tab, tinv, img, st); break;
-    case kBF16X3: image_for<kBF16X3>(m, tab, tinv, img, st); break;
-    default: image_for<kF16X3>(m, tab, tinv, img, st); break;
+    case kTF32: image_for<kTF32, 81>(m, tab, tinv, img, st); break;
+    case kBF16: image_for<kBF16, 81>(m, tab, tinv, img, st); break;
+    case kBF16X3: image_for<kBF16X3, 81>(m, tab, tinv, img, st); break;
+    default: image_for<kF16X3, 81>(m, tab, tinv, img, st); break;
   }
 }
 
-cudaError_t launch_tc2_apply(int mode, int m, const Level& L0, const float* v, const float* w32,
-                             const unsigned char* img, float tscale, float* Y, int* err, int sms, cudaStream_t st) {
-  switch (mode) {
-    case kTF32: return apply_for<kTF32>(m, L0, v, w32, img, tscale, Y, err, sms, st);
-    case kBF16: return apply_for<kBF16>(m, L0, v, w32, img, tscale, Y, err, sms, st);
-    case kBF16X3: return apply_for<kBF16X3>(m, L0, v, w32, img, tscale, Y, err, sms, st);
-    case kF16X3: return apply_for<kF16X3>(m, L0, v, w32, img, tscale, Y, err, sms, st);
-    default: return cudaErrorInvalidValue;
+cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cudaStream_t st) {
+  if (L0.el2 != nullptr) {  // mixed mesh: triquadratic elements with their slaved nodes, then trilinear ones
+    cudaError_t e = apply_mode<81>(tc.mode, tc.m, L0, L0.ne2, L0.el2, L0.sl2, v, tc.w32, tc.img, tc.tscale, tc.Y2,
+                                   tc.err, tc.sms, st);
+    if (e != cudaSuccess) return e;
+    return apply_mode<24>(tc.mode, tc.m, L0, L0.ne1, L0.el1, nullptr, v, tc.w32, tc.img1, tc.tscale1, tc.Y2,
+                          tc.err, tc.sms, st);
   }
+  const long E = (long)L0.ex * L0.ey * L0.ez;
+  return apply_mode<81>(tc.mode, tc.m, L0, E, nullptr, nullptr, v, tc.w32, tc.img, tc.tscale, tc.Y2, tc.err,
+                        tc.sms, st);
 }
 
 void launch_tc2_gather(const Level& L0, const float* Y, const float* b, const float* v, const float* dinv,
                        float omega, int mode, float* out, cudaStream_t st) {
   long g = (L0.nn + 255) / 256;
   if (g > 8192) g = 8192;
-  k_tc2_gather<Shape<kTF32, kD2, 1>::YS><<<(int)g, 256, 0, st>>>(L0.Lx, L0.Ly, L0.Lz, L0.ex, L0.ey, L0.ez, Y, b,
+  k_tc2_gather<Shape<kTF32, 81, 1>::YS><<<(int)g, 256, 0, st>>>(L0.Lx, L0.Ly, L0.Lz, L0.ex, L0.ey, L0.ez, Y, b,
                                                                  v, dinv, L0.mask, omega, mode, out);
 }
 

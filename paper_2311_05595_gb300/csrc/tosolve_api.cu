@@ -245,7 +245,8 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (d.inner_its > 0) B += 4 * (size_t)P->lv[0].ndof * 4;  // inner PCG vectors
   if (tc2) {  // weights, element results and the table image of the tensor-core level
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
-    B += E0 * (P->m + tc2_result_stride()) * 4 + tc2_image_bytes(tc2_mode_of(d.precision), P->m);
+    B += E0 * (P->m + tc2_result_stride()) * 4 + tc2_image_bytes(tc2_mode_of(d.precision), P->m) +
+         tc2_image_bytes(tc2_mode_of(d.precision), P->m, 24) + (size_t)P->m * 576 * 8;
   }
   P->bytes = B;
   return TOSOLVE_OK;
@@ -280,6 +281,7 @@ void free_all(tosolve_s* h) {
   F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab); F(h->ptab3);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->tcimg); F(h->Y2); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->inner.e); F(h->inner.ri); F(h->inner.pi); F(h->inner.qi);
+  F(h->el2); F(h->sl2); F(h->el1); F(h->tab64q1); F(h->tcimg1);
   F(h->Ad); F(h->Wp); F(h->Vp); F(h->Pg); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
   F(h->cnt);
@@ -511,6 +513,37 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     h->mixed = true;
     CKC(dalloc(h, &h->slv0, v.nn));
     CKC(cudaMemcpyAsync(h->slv0, slv.data(), v.nn, cudaMemcpyHostToDevice, st));
+    // element lists: triquadratic ones (with the masks of their slaved local
+    // nodes) and trilinear ones, each ascending
+    std::vector<int> l2, l1;
+    std::vector<uint32_t> m2;
+    for (int ez = 0; ez < v.ez; ++ez)
+      for (int ey = 0; ey < v.ey; ++ey)
+        for (int ex = 0; ex < v.ex; ++ex) {
+          const long e = ex + (long)v.ex * (ey + (long)v.ey * ez);
+          if (elem_q1[e]) {
+            l1.push_back((int)e);
+            continue;
+          }
+          uint32_t msk = 0;
+          for (int a = 0; a < 27; ++a)
+            if (slv[(2 * ex + a % 3) + (long)v.Lx * ((2 * ey + (a / 3) % 3) + (long)v.Ly * (2 * ez + a / 9))])
+              msk |= 1u << a;
+          l2.push_back((int)e);
+          m2.push_back(msk);
+        }
+    h->ne2 = (long)l2.size();
+    h->ne1 = (long)l1.size();
+    CKC(dalloc(h, &h->el2, l2.size() + 1));
+    CKC(dalloc(h, &h->sl2, m2.size() + 1));
+    CKC(dalloc(h, &h->el1, l1.size() + 1));
+    if (!l2.empty()) {
+      CKC(cudaMemcpyAsync(h->el2, l2.data(), l2.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+      CKC(cudaMemcpyAsync(h->sl2, m2.data(), m2.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    }
+    if (!l1.empty())
+      CKC(cudaMemcpyAsync(h->el1, l1.data(), l1.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CKC(cudaStreamSynchronize(st));  // the host vectors go out of scope
     CKC(dalloc(h, &h->fix0, v.ndof));
     CKC(cudaMemcpyAsync(h->fix0, mask.data(), v.ndof, cudaMemcpyHostToDevice, st));
     for (long nd = 0; nd < v.nn; ++nd)
@@ -629,6 +662,14 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       mask.swap(cm);
     }
   }
+  if (h->mixed) {
+    Level& L0 = h->lv[0];
+    L0.el2 = h->el2;
+    L0.ne2 = h->ne2;
+    L0.sl2 = h->sl2;
+    L0.el1 = h->el1;
+    L0.ne1 = h->ne1;
+  }
   // tables (Sec. 3.3: the subcell matrices are computed once)
   if (h->d.degree >= 2) {
     if (h->d.degree == 3) {
@@ -714,7 +755,18 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     CKC(cudaMemcpyAsync(tab.data(), h->tab64, tab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));
     const float tscale = tc2_table_scale(mode, tab.data(), tab.size());
-    launch_tc2_image(mode, P.m, h->tab64, tscale, h->tcimg, st);
+    launch_tc2_image(mode, P.m, 81, h->tab64, tscale, h->tcimg, st);
+    if (h->mixed) {  // trilinear elements: the degree-1 subcell table on their vertices
+      CKC(dalloc(h, &h->tab64q1, (size_t)P.m * 576));
+      CKC(dalloc(h, &h->tcimg1, tc2_image_bytes(mode, P.m, 24)));
+      launch_subcell_table(P.n, h->d.nu, 1.0, h->tab64q1, st);
+      std::vector<double> t1((size_t)P.m * 576);
+      CKC(cudaMemcpyAsync(t1.data(), h->tab64q1, t1.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CKC(cudaStreamSynchronize(st));
+      h->tc.tscale1 = tc2_table_scale(mode, t1.data(), t1.size());
+      launch_tc2_image(mode, P.m, 24, h->tab64q1, h->tc.tscale1, h->tcimg1, st);
+      h->tc.img1 = h->tcimg1;
+    }
     int sms = 1;
     CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
     h->tc.on = true;
@@ -880,11 +932,6 @@ tosolve_status tosolve_create_mixed(const tosolve_desc* desc, const uint8_t* mas
   if (desc == nullptr || elem_q1_host == nullptr) { g_err = "NULL argument"; return TOSOLVE_EINVAL; }
   if (desc->degree != 2) { g_err = "a mixed mesh lives on the degree-2 lattice (degree = 2)"; return TOSOLVE_EINVAL; }
   if (desc->family != 0) { g_err = "a mixed mesh couples Lagrange elements (family = 0)"; return TOSOLVE_EINVAL; }
-  if (desc->precision == TOSOLVE_PREC_TF32 || desc->precision == TOSOLVE_PREC_BF16 ||
-      desc->precision == TOSOLVE_PREC_BF16X3 || desc->precision == TOSOLVE_PREC_F16X3) {
-    g_err = "the tensor-core preconditioners are not built for mixed meshes";
-    return TOSOLVE_EINVAL;
-  }
   return create_impl(desc, mask_host, elem_q1_host, cuda_stream, out);
 }
 
@@ -1434,8 +1481,7 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
     Level& L0 = h->lv[0];
     if (h->tc.deg == 2) {  // the kernel zeroes fixed DOFs itself; the gather keeps them as identity rows
       launch_cast(false, (size_t)L0.ndof, x_dev, L0.v, true, h->st);
-      CK(launch_tc2_apply(h->tc.mode, h->tc.m, L0, (const float*)L0.v, h->w32, h->tcimg, h->tc.tscale, h->Y2,
-                          h->tc.err, h->tc.sms, h->st));
+      CK(launch_tc2_apply(h->tc, L0, (const float*)L0.v, h->st));
       launch_tc2_gather(L0, h->Y2, (const float*)L0.v, (const float*)L0.v, L0.dinv32, 0.f, 2, (float*)L0.r,
                         h->st);
       launch_cast(true, (size_t)L0.ndof, L0.r, y_dev, false, h->st);

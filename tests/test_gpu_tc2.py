@@ -218,3 +218,77 @@ def test_inner_iterations_on_a_mixed_mesh():
     assert abs(c[0] - ref["c"][0]) <= 1e-7 * abs(ref["c"][0])
     assert rel(gx, ref["g_x"]) <= 1e-6
     R.close()
+
+
+def _mixed(shape, n, seed, levels=2):
+    return workloads.with_mixed_degree(workloads.bridge(*shape, degree=2, n_mr=n, seed=seed, mg_levels=levels),
+                                       0.5, seed + 1)
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_tc2_mixed_apply_rows_within_rounding_bound(prec):
+    """Mixed trilinear / triquadratic mesh: triquadratic elements expand
+    their slaved nodes and fold the result back (T_e^T K T_e), trilinear
+    ones use the trilinear subcell matrices on their vertices; every row
+    within the rounding bound of what each element rounds."""
+    p = _mixed((8, 4, 4), 3, 7)
+    S = sample.Sampler(p)
+    R = Run(p, prec)
+    R.set_densities()
+    x = np.random.default_rng(3).normal(size=p.ndof)
+    y = R.apply(0, prec, x).reshape(-1, 3)
+    nodes = list(range(p.nnodes))
+    yr = S.apply_rows(p.x, x, nodes)
+    bar = _bar(prec, S.apply_rows_subcell_scale(p.x, x, nodes, deflate=True),
+               S.apply_rows_subcell_scale(p.x, x, nodes, deflate=True, elem_max=True),
+               S.apply_rows_subcell_scale(p.x, x, nodes))
+    held = (p.mask.astype(bool) | np.repeat(S.slv, 3)).reshape(-1, 3)
+    _check_rows(y, yr, bar, held, x.reshape(-1, 3))
+    R.close()
+
+
+@pytest.mark.parametrize("prec,inner", [(F16X3, 0), (BF16X3, 0), (F16X3, 6), (BF16, 5)])
+def test_tc2_mixed_matches_direct_solve(prec, inner):
+    from oracle import mixed
+    from paper_2311_05595_gb300 import tosolve as T
+
+    p = _mixed((8, 4, 4), 3, 9)
+    ref = mixed.MixedModel(p).run(method="splu")
+    R = Run(p, FP32)
+    R.close()
+    R.solver = T.Solver(T.make_desc(p.nx, p.ny, p.nz, degree=2, n_mr=p.n_mr, nu=p.nu, penal=p.penal,
+                                    Emin=p.Emin, mg_levels=2, precision=prec, inner_its=inner),
+                        p.mask, R.stream, elem_q1=p.elem_q1)
+    R.h = R.solver.h
+    R.set_densities()
+    u, info = R.solve(rtol=1e-11)
+    assert info.rel_residual <= 1e-11
+    assert rel(u.cpu().numpy()[0], ref["u"][0]) <= 1e-6
+    c, gx, gr = R.grad(u)
+    assert abs(c[0] - ref["c"][0]) <= 1e-7 * abs(ref["c"][0])
+    assert rel(gr, ref["g_rho"]) <= 1e-6
+    assert rel(gx, ref["g_x"]) <= 1e-6
+    R.close()
+
+
+def test_tc2_mixed_bridge_full_size():
+    """The bridge as specified (64x32x32, n = 3, a seeded half trilinear;
+    519,204 unknowns) with the benchmark's F16X3 preconditioner and inner
+    FP32 iterations: solve to 1e-8, operator rows, compliance and gradient
+    checked on samples."""
+    from paper_2311_05595_gb300 import tosolve as T
+    from tests.test_gpu_fullsize import _check_sampled
+
+    p = workloads.with_mixed_degree(workloads.bridge(64, 32, 32, degree=2, n_mr=3, seed=0), 0.5, 11)
+    R = Run(p, FP32)
+    R.close()
+    R.solver = T.Solver(T.make_desc(p.nx, p.ny, p.nz, degree=2, n_mr=3, nu=p.nu, penal=p.penal, Emin=p.Emin,
+                                    mg_levels=0, precision=F16X3, inner_its=16),
+                        p.mask, R.stream, elem_q1=p.elem_q1)
+    R.h = R.solver.h
+    R.set_densities()
+    u, info = R.solve(rtol=1e-8)
+    assert info.rel_residual <= 1e-8
+    assert R.T.tosolve_free_dofs(R.h) == 519204
+    _check_sampled(R.T, R, p, u[0], 1e-8, np.random.default_rng(3), nodes=100, cells=24, dcells=4)
+    R.close()

@@ -160,3 +160,30 @@ def test_deflated_scale_equals_between_oracle_forms():
     touched = np.unique(m.edofs[free_elems])
     only_free = np.setdiff1d(touched, np.unique(m.edofs[~free_elems]))
     assert np.abs(z[only_free]).max() <= 1e-12 * np.abs(rigid).max()
+
+
+def test_mixed_subcell_scale_bounds_the_rows():
+    """The rounding scale of a mixed mesh's stacked form bounds each row of
+    the mixed operator (T^T K T with slaved identity rows) and, with one
+    subcell per element, equals the element scale of the unslaved rows of
+    triquadratic elements away from trilinear ones."""
+    p = workloads.with_mixed_degree(workloads.bridge(4, 2, 2, degree=2, n_mr=2, seed=5), 0.5, 3)
+    S = sample.Sampler(p)
+    u = np.random.default_rng(6).normal(size=p.ndof)
+    nodes = list(range(p.nnodes))
+    y = S.apply_rows(p.x, u, nodes)
+    sc = S.apply_rows_subcell_scale(p.x, u, nodes)
+    assert (sc >= np.abs(y) * (1 - 1e-13)).all()
+    scd = S.apply_rows_subcell_scale(p.x, u, nodes, deflate=True)
+    scm = S.apply_rows_subcell_scale(p.x, u, nodes, deflate=True, elem_max=True)
+    assert (scm >= scd * (1 - 1e-13)).all()
+    # a rigid displacement of the free nodes: the deflated scale vanishes
+    # in rows whose elements have no support
+    Lx, Ly, Lz = p.lattice
+    pos = np.array([[i, j, l] for l in range(Lz) for j in range(Ly) for i in range(Lx)], dtype=float)
+    rigid = (np.array([1.0, -2.0, 0.5]) + np.cross([0.3, 0.2, -0.1], pos)).reshape(-1)
+    free_nodes = [nd for nd in nodes if not p.mask[3 * nd] and not S.slv[nd]
+                  and all(not p.mask[3 * m] for e in S.elements_of(nd) for m in S._elem_nodes(*e))]
+    if free_nodes:
+        zd = S.apply_rows_subcell_scale(p.x, rigid, free_nodes, deflate=True)
+        assert np.abs(zd).max() <= 1e-12 * np.abs(rigid).max()
