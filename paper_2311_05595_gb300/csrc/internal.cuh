@@ -207,6 +207,8 @@ struct TcOp {
   float tscale = 1.f;       // degree 2, F16X3: power-of-two scale of the table image
   const unsigned char* img1 = nullptr;  // mixed meshes: the trilinear table's image
   float tscale1 = 1.f;
+  unsigned char* apack = nullptr;  // degree 2: the packed A tiles (tc2_pack_bytes)
+  float* escale = nullptr;         // degree 2, F16X3: per listed element, its row scale
   int m = 1;                // subcells per element
   const float* w32 = nullptr;  // E x m element-major weights
   const float* KT = nullptr;   // degree 1: m x 24 x 24 FP32 table
@@ -240,6 +242,8 @@ inline int tc2_mode_of(int precision) {
 size_t tc2_image_bytes(int mode, int m, int dofs = 81);
 // Floats per element in the result buffer (81 rounded up to 16 bytes).
 size_t tc2_result_stride();
+// Bytes of the packed A tiles for E elements (whole work units).
+size_t tc2_pack_bytes(int mode, long E);
 // Power-of-two scale of the table image (F16X3: largest entry into
 // [0.5, 1) after dividing by it; else 1), from the host copy of the table.
 float tc2_table_scale(int mode, const double* tab_host, size_t count);
@@ -471,6 +475,8 @@ struct tosolve_s {
   float* w32 = nullptr;        // E x m element-major FP32 weights
   float* Ye = nullptr;         // E x 24 element results of the tensor-core apply
   unsigned char* tcimg = nullptr;  // degree 2: the stacked table as shared-memory chunk images
+  unsigned char* tcpack = nullptr; // degree 2: packed A tiles of the tensor-core apply
+  float* tcscale = nullptr;        // degree 2: their per-element scales
   float* Y2 = nullptr;         // degree 2: element results of the tensor-core apply
   tos::TcOp tc;
   tos::InnerPcg inner;

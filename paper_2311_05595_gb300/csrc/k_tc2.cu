@@ -8,9 +8,10 @@
 // Orientation: M = 128 elements of a tile (TMEM lanes), N = a chunk of the
 // stacked subcell rows (TMEM columns), K = the 81 element DOFs padded to 88
 // (TF32) or 96 (16-bit operands).  With the elements on the lanes, the
-// weighted reduce over subcells is thread-local in the epilogue: thread e
-// reads its lane's columns and accumulates w_{e,i} Z[i, r] into 81
-// registers, so no cross-lane reduction and a fixed summation order.
+// weighted reduce over subcells is thread-local in the epilogue: the rows
+// are stacked DOF-major (all subcells of output DOF r together), so thread e
+// reads the columns of one output at a time and forms sum_i w_{e,i} Z[i, r]
+// in a fixed order, with no cross-lane reduction.
 //
 // Operand modes:
 //   TF32     one product, TF32 operands (10-bit mantissas), kind::tf32;
@@ -34,16 +35,23 @@
 // shared-memory image, chunk by chunk, and each chunk is moved by one 1D bulk
 // copy (TMA) completing on an mbarrier.
 //
-// Warp roles (256 threads, one CTA per SM, persistent over element tiles):
-//   warp 0     allocates the 512 TMEM columns; lane 0 streams table chunks
-//              into a ring of B stages;
+// Work unit: a pair of 128-element tiles, so each table chunk brought to
+// shared memory serves 256 elements (two MMAs per K-slice, two TMEM
+// accumulators).  Warp roles (192 threads, one CTA per SM, persistent over
+// work units):
+//   warp 0     allocates the 512 TMEM columns; lane 0 brings each unit's A
+//              tiles and streams table chunks into a ring of B stages;
 //   warp 1     lane 0 issues the MMAs of each chunk into one of two TMEM
 //              accumulators and commits their completion to mbarriers;
-//   warps 2-5  epilogue: read the accumulator of each chunk (tcgen05.ld),
-//              weighted reduce over subcells, store y_e;
-//   warps 6-7  gather u_e of the next tile (fixed DOFs as zero), minus its
-//              least-squares rigid motion, into one of two A buffers, two
-//              elements per thread.
+//   warps 2-5  epilogue: read each 32-column group of the accumulator
+//              (tcgen05.ld), weighted sum over its subcells, store the
+//              output DOF; mixed meshes fold slaved nodes afterwards.
+// The A operand rows (u_e with fixed DOFs as zero, slaved nodes expanded,
+// minus the least-squares rigid motion, scaled and split) are assembled by
+// a separate high-occupancy kernel, k_tc2_pack, straight into the
+// shared-memory image of their tiles: the scattered gathers then hide their
+// latency behind thousands of threads, and the producer moves a pair's two
+// A tiles with one bulk copy.
 // Every mbarrier wait is bounded; a timeout raises the error flag and a
 // shared abort flag that ends every role, the MMA thread waits for its last
 // commit and the producer for its copies in flight, and the TMEM is freed.
@@ -59,8 +67,10 @@
 namespace tos {
 namespace {
 
-constexpr int kTm = 128;            // elements per tile
-constexpr int kThreads = 256;       // 8 warps (two per SM sub-partition: up to 255 registers)
+constexpr int kTm = 128;            // elements per tile (TMEM lanes of one MMA)
+constexpr int kPair = 2;            // tiles per work unit: each table chunk serves both
+constexpr int kUnit = kPair * kTm;  // elements per work unit
+constexpr int kThreads = 192;       // 6 warps, one per role below
 constexpr int kTmemCols = 512;      // two accumulators of up to 256 columns
 constexpr long kSpin2 = 1L << 22;   // bound of every mbarrier wait
 
@@ -73,7 +83,7 @@ struct Opnd {
   static constexpr int kEs = MD == kTF32 ? 4 : 2;          // bytes per element
   static constexpr int kKc = 16 / kEs;                     // elements per 16-byte core-matrix row
   static constexpr int kKstep = MD == kTF32 ? 8 : 16;      // K of one MMA
-  static constexpr int kNch = MD == kTF32 ? 192 : (kSplit ? 128 : 256);  // stacked rows per chunk
+  static constexpr int kNch = 128;                         // stacked rows per chunk (2 x 2 x 128 TMEM columns)
   static constexpr int kStages = MD == kBF16 ? 3 : 2;      // B ring
   static constexpr int kParts = kSplit ? 2 : 1;            // hi (and lo) K-slices per row
   static constexpr int kProducts = kSplit ? 3 : 1;
@@ -81,12 +91,18 @@ struct Opnd {
   static constexpr uint32_t kFmt = MD == kTF32 ? 2u : (MD == kF16X3 ? 0u : 1u);
 };
 
+// Stacked rows are DOF-major: row MP r + i holds row r of subcell i (zero
+// for i >= M), with MP = M rounded up to a divisor of 32, so that every
+// 32-column group of an accumulator holds 32 / MP complete outputs and the
+// epilogue is the same short loop for every group.
 template <int MD, int D, int M>
 struct Shape {
   using O = Opnd<MD>;
   static constexpr int KP = (D + O::kKstep - 1) / O::kKstep * O::kKstep;  // padded K of one part
   static constexpr int KR = KP * O::kParts;                                 // K extent of a row
-  static constexpr int ROWS = D * M;                                        // stacked rows
+  static constexpr int MP = M <= 1 ? 1 : (M <= 2 ? 2 : (M <= 4 ? 4 : (M <= 8 ? 8 : (M <= 16 ? 16 : 32))));
+  static constexpr int OPG = 32 / MP;                                       // outputs per 32 columns
+  static constexpr int ROWS = D * MP;                                       // stacked rows
   static constexpr int NCH = O::kNch;
   static constexpr int NC = (ROWS + NCH - 1) / NCH;                         // chunks
   static constexpr int LASTN = ROWS - (NC - 1) * NCH;
@@ -95,8 +111,7 @@ struct Shape {
   static constexpr uint32_t SBO = (uint32_t)(KR / O::kKc) * 128u;
   static constexpr uint32_t ABYTES = (uint32_t)kTm * KR * O::kEs;
   static constexpr uint32_t BBYTES = (uint32_t)NCH * KR * O::kEs;
-  static constexpr size_t SMEM = 2 * (size_t)ABYTES + (size_t)O::kStages * BBYTES;
-  static constexpr int YS = 84;  // stride of y_e in the result buffer: the 81 DOFs of the 27-node layout
+  static constexpr size_t SMEM = (size_t)kPair * ABYTES + (size_t)O::kStages * BBYTES;
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -183,17 +198,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&q)[32]) {
 }
 
 struct Tc2Args {
-  int ex, ey, Lx, Ly;
   long E;                     // elements to apply (the list's length when there is a list)
   const int* list;            // element ids, or null: 0 .. E-1
   const uint32_t* slm;        // per listed element, its slaved local nodes (mixed meshes), or null
-  const float* v;             // level-0 vector, 3 per lattice node
-  const uint8_t* mask;        // per DOF, 1 = fixed
+  const unsigned char* apack; // the packed A tiles (k_tc2_pack), tile t at t * ABYTES
+  const float* escale;        // F16X3: per listed element, the power of two its row was scaled by
   const float* w32;           // E x M subcell weights, element-major
   const unsigned char* img;   // stacked table, NC chunks of BBYTES in the smem image layout
   float tscale;               // F16X3: the table's power-of-two scale to undo (else 1)
-  float* Y;                   // E x YS element results
+  float* Y;                   // element results, DOF-major: Y[r * Ey + e] (r of the 27-node layout)
+  long Ey;                    // elements of the level (the stride of Y)
   int* err;
+};
+
+struct PackArgs {
+  int ex, ey, Lx, Ly;
+  long E, rows;               // listed elements; rows packed (whole work units)
+  const int* list;
+  const uint32_t* slm;
+  const float* v;             // level-0 vector, 3 per lattice node
+  const uint8_t* mask;        // per DOF, 1 = fixed
+  unsigned char* apack;
+  float* escale;
 };
 
 // The element's nodes on the degree-2 lattice: D = 81, the 27 nodes of a
@@ -254,17 +280,34 @@ __device__ __forceinline__ void expand_slaved(float* u, uint32_t msk) {
     }
   }
 }
-__device__ __forceinline__ void fold_slaved(float* y, uint32_t msk) {
+// The same fold on an element's results in the DOF-major buffer (stride
+// ys between DOFs), in place.  Parents are vertices, which are never
+// slaved.  Every value is loaded first (the loads are independent), the
+// fold runs in registers with compile-time parent indices, then the stores.
+__device__ __forceinline__ void fold_slaved_strided(float* y, long ys, uint32_t msk) {
+  float vt[24];  // vertex v = vx + 2 (vy + 2 vz) at local node 2 vx + 3 (2 vy + 3 (2 vz))
+  float sv[81];  // slaved values (non-vertex local nodes only)
+#pragma unroll
+  for (int v = 0; v < 8; ++v)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      vt[3 * v + c] = y[(3 * (2 * (v & 1) + 3 * (2 * ((v >> 1) & 1) + 3 * (2 * (v >> 2)))) + c) * ys];
 #pragma unroll
   for (int a = 0; a < 27; ++a) {
     const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
-    if (((ax | ay | az) & 1) == 0) continue;
-    if (!((msk >> a) & 1u)) continue;
+    const bool sl = ((ax | ay | az) & 1) != 0 && ((msk >> a) & 1u);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sv[3 * a + c] = sl ? y[(3 * a + c) * ys] : 0.f;
+  }
+#pragma unroll
+  for (int a = 0; a < 27; ++a) {
+    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+    if (((ax | ay | az) & 1) == 0) continue;  // a vertex
     const int nx = ax == 1 ? 2 : 1, ny = ay == 1 ? 2 : 1, nz = az == 1 ? 2 : 1;
     const float wgt = 1.f / (float)(nx * ny * nz);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float v = wgt * y[3 * a + c];
+      const float val = wgt * sv[3 * a + c];  // zero unless slaved
 #pragma unroll
       for (int kz = 0; kz < 2; ++kz)
 #pragma unroll
@@ -272,13 +315,25 @@ __device__ __forceinline__ void fold_slaved(float* y, uint32_t msk) {
 #pragma unroll
           for (int kx = 0; kx < 2; ++kx) {
             if (kx >= nx || ky >= ny || kz >= nz) continue;
-            const int px = ax == 1 ? 2 * kx : ax, py = ay == 1 ? 2 * ky : ay, pz = az == 1 ? 2 * kz : az;
-            y[3 * (px + 3 * (py + 3 * pz)) + c] += v;
+            const int vx = ax == 1 ? kx : ax / 2, vy = ay == 1 ? ky : ay / 2, vz = az == 1 ? kz : az / 2;
+            vt[3 * (vx + 2 * (vy + 2 * vz)) + c] += val;
           }
-      y[3 * a + c] = 0.f;
     }
   }
+#pragma unroll
+  for (int v = 0; v < 8; ++v)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      y[(3 * (2 * (v & 1) + 3 * (2 * ((v >> 1) & 1) + 3 * (2 * (v >> 2)))) + c) * ys] = vt[3 * v + c];
+#pragma unroll
+  for (int a = 0; a < 27; ++a) {
+    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+    if (((ax | ay | az) & 1) != 0 && ((msk >> a) & 1u))
+#pragma unroll
+      for (int c = 0; c < 3; ++c) y[(3 * a + c) * ys] = 0.f;
+  }
 }
+
 
 // u_e minus its least-squares rigid motion t + omega x over the element's
 // nodes at reference positions x_a (the 27 points of {-1, 0, 1}^3, or the 8
@@ -376,22 +431,53 @@ __device__ __forceinline__ float store_row(const float* u, unsigned char* dstrow
   return s;
 }
 
+// One element's A row per thread, written into the image of its tile
+// (whole work units: rows past the list are zeros).
+template <int MD, int D>
+__global__ void __launch_bounds__(128) k_tc2_pack(PackArgs a) {
+  using S = Shape<MD, D, 1>;  // the row layout does not depend on M
+  using O = Opnd<MD>;
+  for (long ei = blockIdx.x * (long)blockDim.x + threadIdx.x; ei < a.rows; ei += (long)gridDim.x * blockDim.x) {
+    float u[S::KP];
+#pragma unroll
+    for (int k = 0; k < S::KP; ++k) u[k] = 0.f;
+    if (ei < a.E) {
+      const long e = a.list != nullptr ? (long)a.list[ei] : ei;
+      const int exi = (int)(e % a.ex), eyi = (int)((e / a.ex) % a.ey), ezi = (int)(e / ((long)a.ex * a.ey));
+#pragma unroll
+      for (int nd = 0; nd < D / 3; ++nd) {
+        const long d0 = 3 * elem_lattice_node<D>(exi, eyi, ezi, nd, a.Lx, a.Ly);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) u[3 * nd + cc] = __ldg(a.mask + d0 + cc) ? 0.f : __ldg(a.v + d0 + cc);
+      }
+      if constexpr (D == 81)
+        if (a.slm != nullptr) expand_slaved(u, a.slm[ei]);
+      deflate_rigid<D>(u);
+    }
+    const long tile = ei / kTm;
+    const int lrow = (int)(ei % kTm);
+    unsigned char* dstrow = a.apack + (size_t)tile * S::ABYTES + (size_t)(lrow >> 3) * S::SBO + (lrow & 7) * 16;
+    const float sv = store_row<MD, S::KP>(u, dstrow);
+    if constexpr (O::kScaled) a.escale[ei] = sv;
+  }
+}
+
 template <int MD, int D, int M>
 __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
   using S = Shape<MD, D, M>;
   using O = Opnd<MD>;
   constexpr int NS = O::kStages;
+  static_assert(kThreads == 6 * 32, "one warp per role: producer, MMA, 4 epilogue");
+  static_assert(2 * 2 * S::NCH <= kTmemCols, "two accumulator buffers of a tile pair");
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem;                  // 2 x ABYTES
-  unsigned char* sB = smem + 2 * S::ABYTES;  // NS x BBYTES
-  __shared__ __align__(8) uint64_t bfull[NS], bempty[NS], afull[2], aempty[2], tfull[2], tempty[2], sfull[2],
-      mdone;
-  __shared__ float rscale[2][kTm];  // F16X3: the power of two each element row was scaled by
+  unsigned char* sA = smem;                        // the pair's two A tiles
+  unsigned char* sB = smem + kPair * S::ABYTES;    // NS x BBYTES
+  __shared__ __align__(8) uint64_t bfull[NS], bempty[NS], afull, aempty, tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long ntiles = (a.E + kTm - 1) / kTm;
-  const long ntl = (long)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long nunits = (a.E + kUnit - 1) / kUnit;
+  const long ntl = (long)blockIdx.x < nunits ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
@@ -403,12 +489,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bfull[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bempty[s])));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&afull)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&aempty)));
     for (int s = 0; s < 2; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&afull[s])), "r"(kTm));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&aempty[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&tfull[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&tempty[s])), "r"(kTm));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sfull[s])), "r"(kTm));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mdone)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -420,36 +505,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0) {
-    // ---- producer: table chunks into the B ring ----
+    // ---- producer: each unit's A tiles, then its table chunks into the B ring ----
     if (lane == 0) {
-      long q = 0;
-      const long nq = ntl * S::NC;
-      for (; q < nq; ++q) {
-        const int s = (int)(q % NS), c = (int)(q % S::NC);
-        if (!wait_or_abort(&bempty[s], (uint32_t)(((q / NS) & 1) ^ 1), &abort_flag)) break;
-        const uint32_t bytes = c == S::NC - 1 ? (uint32_t)(S::LASTNP / 8) * S::SBO : S::BBYTES;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bfull[s])),
-                     "r"(bytes)
+      long q = 0, j = 0;
+      bool ok = true;
+      for (; j < ntl && ok; ++j) {
+        if (!(ok = wait_or_abort(&aempty, (uint32_t)((j & 1) ^ 1), &abort_flag))) break;
+        const long unit = blockIdx.x + j * gridDim.x;
+        const uint32_t abytes = (uint32_t)kPair * S::ABYTES;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&afull)), "r"(abytes)
                      : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                su32(sB + (size_t)s * S::BBYTES)),
-            "l"(a.img + (size_t)c * S::BBYTES), "r"(bytes), "r"(su32(&bfull[s]))
+                su32(sA)),
+            "l"(a.apack + (size_t)unit * abytes), "r"(abytes), "r"(su32(&afull))
             : "memory");
+        for (int c = 0; c < S::NC; ++c, ++q) {
+          const int s = (int)(q % NS);
+          if (!(ok = wait_or_abort(&bempty[s], (uint32_t)(((q / NS) & 1) ^ 1), &abort_flag))) break;
+          const uint32_t bytes = c == S::NC - 1 ? (uint32_t)(S::LASTNP / 8) * S::SBO : S::BBYTES;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bfull[s])),
+                       "r"(bytes)
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  su32(sB + (size_t)s * S::BBYTES)),
+              "l"(a.img + (size_t)c * S::BBYTES), "r"(bytes), "r"(su32(&bfull[s]))
+              : "memory");
+        }
       }
-      if (q < nq) {  // aborted: let the copies in flight land before the CTA exits
+      if (!ok) {  // aborted: let the copies in flight land before the CTA exits
         atomicExch(a.err, 1);
         for (long p = q - 1; p >= 0 && p >= q - NS; --p) drain_wait(&bfull[p % NS], (uint32_t)((p / NS) & 1));
+        if (j > 0) drain_wait(&afull, (uint32_t)((j - 1) & 1));
       }
     }
   } else if (warp == 1) {
-    // ---- MMA issue ----
+    // ---- MMA issue: each chunk against both tiles of the pair ----
     if (lane == 0) {
       const uint32_t abase = su32(sA), bbase = su32(sB);
       bool ok = true;
       for (long j = 0; j < ntl && ok; ++j) {
-        const int ab = (int)(j & 1);
-        ok = wait_or_abort(&afull[ab], (uint32_t)((j >> 1) & 1), &abort_flag);
+        ok = wait_or_abort(&afull, (uint32_t)(j & 1), &abort_flag);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         for (int c = 0; c < S::NC; ++c) {
@@ -462,83 +559,85 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
           const uint32_t n = c == S::NC - 1 ? (uint32_t)S::LASTNP : (uint32_t)S::NCH;
           const uint32_t idesc = (1u << 4) | (O::kFmt << 7) | (O::kFmt << 10) | ((n >> 3) << 17) |
                                  ((uint32_t)(kTm >> 4) << 24);
-          const uint32_t dt = tmem + (uint32_t)(acc * 256);
-          const uint32_t ao = abase + (uint32_t)ab * S::ABYTES, bo = bbase + (uint32_t)s * S::BBYTES;
+          const uint32_t bo = bbase + (uint32_t)s * S::BBYTES;
 #pragma unroll
-          for (int t = 0; t < O::kProducts * S::KS; ++t) {
-            // products: a_hi b_hi, a_lo b_hi, a_hi b_lo (K-slice t % KS of each part)
-            const int pr = t / S::KS, ks = t % S::KS;
-            const int apart = pr == 1 ? 1 : 0, bpart = pr == 2 ? 1 : 0;
-            const uint64_t ad = sdesc(ao + 256u * (apart * S::KS + ks), 128u, S::SBO);
-            const uint64_t bd = sdesc(bo + 256u * (bpart * S::KS + ks), 128u, S::SBO);
-            const uint32_t accum = t > 0 ? 1u : 0u;
-            if constexpr (MD == kTF32)
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-            else
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+          for (int tt = 0; tt < kPair; ++tt) {
+            const uint32_t dt = tmem + (uint32_t)(acc * 2 * S::NCH + tt * S::NCH);
+            const uint32_t ao = abase + (uint32_t)tt * S::ABYTES;
+#pragma unroll
+            for (int t = 0; t < O::kProducts * S::KS; ++t) {
+              // products: a_hi b_hi, a_lo b_hi, a_hi b_lo (K-slice t % KS of each part)
+              const int pr = t / S::KS, ks = t % S::KS;
+              const int apart = pr == 1 ? 1 : 0, bpart = pr == 2 ? 1 : 0;
+              const uint64_t ad = sdesc(ao + 256u * (apart * S::KS + ks), 128u, S::SBO);
+              const uint64_t bd = sdesc(bo + 256u * (bpart * S::KS + ks), 128u, S::SBO);
+              const uint32_t accum = t > 0 ? 1u : 0u;
+              if constexpr (MD == kTF32)
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+              else
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+            }
           }
           commit(&bempty[s]);   // the B stage is free once these MMAs are done
-          commit(&tfull[acc]);  // and the accumulator is ready for the epilogue
+          commit(&tfull[acc]);  // and the accumulators are ready for the epilogue
         }
         if (!ok) break;
-        commit(&aempty[ab]);  // all chunks of the tile are issued: A buffer free when done
+        commit(&aempty);  // all chunks of the pair issued: its A tiles are free when done
       }
       if (!ok) atomicExch(a.err, 1);
       // every MMA issued above has completed before the TMEM is freed
       commit(&mdone);
       drain_wait(&mdone, 0);
     }
-  } else if (warp < 6) {
-    // ---- epilogue: weighted reduce over subcells ----
+  } else {
+    // ---- epilogue: weighted sum over the subcells of each output DOF ----
     const int quarter = warp & 3;  // a warp reads the TMEM lanes of its sub-partition
-    const int row = 32 * quarter + lane;
+    const int lrow = 32 * quarter + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
     for (long j = 0; j < ntl; ++j) {
-      const long ei = (blockIdx.x + j * gridDim.x) * (long)kTm + row;
-      const bool live = ei < a.E;
-      const long e = !live ? 0 : (a.list != nullptr ? (long)a.list[ei] : ei);
-      float sc = a.tscale;
-      if constexpr (O::kScaled) {
-        // the gather of this tile published the row scales before its
-        // arrival; the buffer is not rewritten before this tile's MMAs end
-        if (!__all_sync(0xffffffffu, wait_or_abort(&sfull[j & 1], (uint32_t)((j >> 1) & 1), &abort_flag))) {
-          atomicExch(a.err, 1);
-          break;
-        }
-        sc *= rscale[j & 1][row];
+      long ei[kPair], e[kPair];
+      bool live[kPair];
+      float w[kPair][M];
+#pragma unroll
+      for (int tt = 0; tt < kPair; ++tt) {
+        ei[tt] = (blockIdx.x + j * gridDim.x) * (long)kUnit + tt * kTm + lrow;
+        live[tt] = ei[tt] < a.E;
+        e[tt] = !live[tt] ? 0 : (a.list != nullptr ? (long)a.list[ei[tt]] : ei[tt]);
+        float sc = a.tscale;
+        if constexpr (O::kScaled) sc *= live[tt] ? a.escale[ei[tt]] : 0.f;
+#pragma unroll
+        for (int i = 0; i < M; ++i) w[tt][i] = live[tt] ? sc * __ldg(a.w32 + e[tt] * M + i) : 0.f;
       }
-      float w[M];
-#pragma unroll
-      for (int i = 0; i < M; ++i) w[i] = live ? __ldg(a.w32 + e * M + i) : 0.f;
-      float y[D];
-#pragma unroll
-      for (int r = 0; r < D; ++r) y[r] = 0.f;
       bool ok = true;
-#pragma unroll
+#pragma unroll 1
       for (int c = 0; c < S::NC; ++c) {
         const long q = j * S::NC + c;
         const int acc = (int)(q & 1);
         ok = __all_sync(0xffffffffu, wait_or_abort(&tfull[acc], (uint32_t)((q >> 1) & 1), &abort_flag));
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        constexpr int G = S::NCH / 32;
-        const int ng = c == S::NC - 1 ? (S::LASTN + 31) / 32 : G;
+        const int ng = c == S::NC - 1 ? (S::LASTN + 31) / 32 : S::NCH / 32;
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          if (g < ng) {
+        for (int tt = 0; tt < kPair; ++tt) {
+#pragma unroll 1
+          for (int g = 0; g < ng; ++g) {
             uint32_t qv[32];
-            tmem_ld32(tl + (uint32_t)(acc * 256 + 32 * g), qv);
+            tmem_ld32(tl + (uint32_t)(acc * 2 * S::NCH + tt * S::NCH + 32 * g), qv);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int r0 = (c * S::NCH + 32 * g) / S::MP;
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-              const int col = c * S::NCH + 32 * g + t;
-              if (col < S::ROWS) y[col % D] = fmaf(w[col / D], __uint_as_float(qv[t]), y[col % D]);
+            for (int o = 0; o < S::OPG; ++o) {
+              float v = 0.f;
+#pragma unroll
+              for (int i = 0; i < M; ++i) v = fmaf(w[tt][i], __uint_as_float(qv[o * S::MP + i]), v);
+              const int r = r0 + o;
+              if (live[tt] && r < D) a.Y[(long)Elem<D>::out(r) * a.Ey + e[tt]] = v;
             }
           }
         }
@@ -549,62 +648,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
         atomicExch(a.err, 1);
         break;
       }
-      if (live) {
-        if constexpr (D == 81) {
-          if (a.slm != nullptr) fold_slaved(y, a.slm[ei]);
-          float4* dst = reinterpret_cast<float4*>(a.Y + e * S::YS);
-#pragma unroll
-          for (int t = 0; t < S::YS / 4; ++t) {
-            const int r = 4 * t;
-            dst[t] = make_float4(r < D ? sc * y[r] : 0.f, r + 1 < D ? sc * y[r + 1] : 0.f,
-                                 r + 2 < D ? sc * y[r + 2] : 0.f, r + 3 < D ? sc * y[r + 3] : 0.f);
-          }
-        } else {  // the vertex positions of the 27-node layout (the others are slaved)
-          float* dst = a.Y + e * S::YS;
-#pragma unroll
-          for (int r = 0; r < D; ++r) dst[Elem<D>::out(r)] = sc * y[r];
-        }
-      }
-    }
-  } else {
-    // ---- gather u_e of each tile into an A buffer ----
-    for (long j = 0; j < ntl; ++j) {
-      const int ab = (int)(j & 1);
-      if (!wait_or_abort(&aempty[ab], (uint32_t)(((j >> 1) & 1) ^ 1), &abort_flag)) {
-        atomicExch(a.err, 1);
-        break;
-      }
+      if constexpr (D == 81) {
+        if (a.slm != nullptr) {
 #pragma unroll 1
-      for (int rr = 0; rr < 2; ++rr) {
-        const int row = 32 * (warp - 6) + lane + 64 * rr;
-        const long ei = (blockIdx.x + j * gridDim.x) * (long)kTm + row;
-        float u[S::KP];
-#pragma unroll
-        for (int k = 0; k < S::KP; ++k) u[k] = 0.f;
-        if (ei < a.E) {
-          const long e = a.list != nullptr ? (long)a.list[ei] : ei;
-          const int exi = (int)(e % a.ex), eyi = (int)((e / a.ex) % a.ey), ezi = (int)(e / ((long)a.ex * a.ey));
-#pragma unroll
-          for (int nd = 0; nd < D / 3; ++nd) {
-            const long d0 = 3 * elem_lattice_node<D>(exi, eyi, ezi, nd, a.Lx, a.Ly);
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-              const float x = __ldg(a.v + d0 + cc);
-              u[3 * nd + cc] = __ldg(a.mask + d0 + cc) ? 0.f : x;
-            }
+          for (int tt = 0; tt < kPair; ++tt) {  // y <- T_e^T y on this thread's own rows of Y
+            if (!live[tt]) continue;
+            const uint32_t msk = a.slm[ei[tt]];
+            if (msk != 0u) fold_slaved_strided(a.Y + e[tt], a.Ey, msk);
           }
-          if constexpr (D == 81)
-            if (a.slm != nullptr) expand_slaved(u, a.slm[ei]);
-          deflate_rigid<D>(u);
         }
-        unsigned char* dstrow = sA + (size_t)ab * S::ABYTES + (size_t)(row >> 3) * S::SBO + (row & 7) * 16;
-        const float s = store_row<MD, S::KP>(u, dstrow);
-        if constexpr (O::kScaled) {
-          rscale[ab][row] = s;
-          arrive(&sfull[ab]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-        arrive(&afull[ab]);
       }
     }
   }
@@ -616,13 +668,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
 }
 
 // The stacked table in the shared-memory image of its chunks: chunk c, row
-// n (stacked row c * nch + n = 81 i + R: row R of subcell i), K column k (an
-// element DOF; the subcell matrices are symmetric); zero padding beyond the
-// table.  Single modes round once (TF32 to nearest with ties away, BF16 to
+// n (stacked row c * nch + n = mp R + i: row R of subcell i, zero for the
+// padding subcells i >= m), K column k (an element DOF; the subcell
+// matrices are symmetric); zero padding beyond the table.  Single modes round once (TF32 to nearest with ties away, BF16 to
 // nearest even); split modes store hi in columns [0, kp) and lo in
 // [kp, 2 kp), FP16 after scaling the table by tinv (a power of two).
-__global__ void k_tc2_image(int mode, int D, int m, int nch, int kp, int parts, int kc, uint32_t sbo, double tinv,
-                            const double* __restrict__ tab, unsigned char* __restrict__ img, long total) {
+__global__ void k_tc2_image(int mode, int D, int m, int mp, int nch, int kp, int parts, int kc, uint32_t sbo,
+                            double tinv, const double* __restrict__ tab, unsigned char* __restrict__ img,
+                            long total) {
   const int es = mode == kTF32 ? 4 : 2;
   const int kr = kp * parts;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
@@ -631,10 +684,8 @@ __global__ void k_tc2_image(int mode, int D, int m, int nch, int kp, int parts, 
     const int c = (int)(rowg / nch), n = (int)(rowg % nch);
     const long gr = (long)c * nch + n;
     double x = 0.0;
-    if (gr < (long)D * m && k < D) {
-      const long i = gr / D, R = gr % D;
-      x = tab[(i * D + R) * D + k];
-    }
+    const long R = gr / mp, i = gr % mp;  // DOF-major: row mp R + i is row R of subcell i
+    if (R < D && i < m && k < D) x = tab[(i * D + R) * D + k];
     auto at = [&](int kk) {
       return (size_t)c * nch * kr * es + (size_t)(n >> 3) * sbo + (size_t)(kk / kc) * 128 + (size_t)(n & 7) * 16 +
              (size_t)(kk % kc) * es;
@@ -659,12 +710,12 @@ __global__ void k_tc2_image(int mode, int D, int m, int nch, int kp, int parts, 
 // y_n = sum of y_e over the elements containing node n (fixed order), then
 //   mode 0: out = b - y;  mode 1: out = v + omega D^-1 (b - y);  mode 2: out = y.
 // Fixed DOFs are identity rows: y = v there.
-template <int YS>
 __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, const float* __restrict__ Y,
                              const float* __restrict__ b, const float* __restrict__ v,
                              const float* __restrict__ dinv, const uint8_t* __restrict__ mask, float omega,
                              int mode, float* __restrict__ out) {
   const long nn = (long)Lx * Ly * Lz;
+  const long Ey = (long)ex * ey * ez;
   for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn; node += (long)gridDim.x * blockDim.x) {
     const int i = (int)(node % Lx), j = (int)((node / Lx) % Ly), l = (int)(node / ((long)Lx * Ly));
     const int co[3] = {i, j, l}, ext[3] = {ex, ey, ez};
@@ -686,10 +737,10 @@ __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, con
         for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
           const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
           const int la = (i - 2 * ex_) + 3 * ((j - 2 * ey_) + 3 * (l - 2 * ez_));
-          const float* ye = Y + e * YS + 3 * la;
+          const float* ye = Y + (long)(3 * la) * Ey + e;  // DOF-major: coalesced along x
           y[0] += ye[0];
-          y[1] += ye[1];
-          y[2] += ye[2];
+          y[1] += ye[Ey];
+          y[2] += ye[2 * Ey];
         }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -703,9 +754,8 @@ __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, con
 }
 
 template <int MD, int D, int M>
-cudaError_t run_apply(const Level& L0, long count, const int* list, const uint32_t* slm, const float* v,
-                      const float* w32, const unsigned char* img, float tscale, float* Y, int* err, int sms,
-                      cudaStream_t st) {
+cudaError_t run_apply(const TcOp& tc, const Level& L0, long count, const int* list, const uint32_t* slm,
+                      const float* v, const unsigned char* img, float tscale, cudaStream_t st) {
   using S = Shape<MD, D, M>;
   static std::once_flag once;  // handles may be created from several threads
   static cudaError_t attr = cudaSuccess;
@@ -714,23 +764,36 @@ cudaError_t run_apply(const Level& L0, long count, const int* list, const uint32
   });
   if (attr != cudaSuccess) return attr;
   if (count <= 0) return cudaSuccess;
+  const long nunits = (count + kUnit - 1) / kUnit;
+  PackArgs pa;
+  pa.ex = L0.ex;
+  pa.ey = L0.ey;
+  pa.Lx = L0.Lx;
+  pa.Ly = L0.Ly;
+  pa.E = count;
+  pa.rows = nunits * kUnit;
+  pa.list = list;
+  pa.slm = slm;
+  pa.v = v;
+  pa.mask = L0.mask;
+  pa.apack = tc.apack;
+  pa.escale = tc.escale;
+  long gp = (pa.rows + 127) / 128;
+  if (gp > 16L * tc.sms) gp = 16L * tc.sms;
+  k_tc2_pack<MD, D><<<(int)gp, 128, 0, st>>>(pa);
   Tc2Args a;
-  a.ex = L0.ex;
-  a.ey = L0.ey;
-  a.Lx = L0.Lx;
-  a.Ly = L0.Ly;
   a.E = count;
   a.list = list;
   a.slm = slm;
-  a.v = v;
-  a.mask = L0.mask;
-  a.w32 = w32;
+  a.apack = tc.apack;
+  a.escale = tc.escale;
+  a.w32 = tc.w32;
   a.img = img;
   a.tscale = tscale;
-  a.Y = Y;
-  a.err = err;
-  const long ntiles = (count + kTm - 1) / kTm;
-  const int g = (int)(ntiles < sms ? ntiles : sms);
+  a.Y = tc.Y2;
+  a.Ey = (long)L0.ex * L0.ey * L0.ez;
+  a.err = tc.err;
+  const int g = (int)(nunits < tc.sms ? nunits : tc.sms);
   k_tc2_apply<MD, D, M><<<g, kThreads, S::SMEM, st>>>(a);
   return cudaGetLastError();
 }
@@ -746,38 +809,38 @@ size_t image_bytes_for(int m) {
 }
 
 template <int MD, int D>
-cudaError_t apply_for(int m, const Level& L0, long count, const int* list, const uint32_t* slm, const float* v,
-                      const float* w32, const unsigned char* img, float tscale, float* Y, int* err, int sms,
-                      cudaStream_t st) {
-  if (m == 27) return run_apply<MD, D, 27>(L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
-  if (m == 8) return run_apply<MD, D, 8>(L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
-  if (m == 1) return run_apply<MD, D, 1>(L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
+cudaError_t apply_for(const TcOp& tc, const Level& L0, long count, const int* list, const uint32_t* slm,
+                      const float* v, const unsigned char* img, float tscale, cudaStream_t st) {
+  if (tc.m == 27) return run_apply<MD, D, 27>(tc, L0, count, list, slm, v, img, tscale, st);
+  if (tc.m == 8) return run_apply<MD, D, 8>(tc, L0, count, list, slm, v, img, tscale, st);
+  if (tc.m == 1) return run_apply<MD, D, 1>(tc, L0, count, list, slm, v, img, tscale, st);
   return cudaErrorInvalidValue;
 }
 
 template <int D>
-cudaError_t apply_mode(int mode, int m, const Level& L0, long count, const int* list, const uint32_t* slm,
-                       const float* v, const float* w32, const unsigned char* img, float tscale, float* Y, int* err,
-                       int sms, cudaStream_t st) {
-  switch (mode) {
-    case kTF32: return apply_for<kTF32, D>(m, L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
-    case kBF16: return apply_for<kBF16, D>(m, L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
-    case kBF16X3: return apply_for<kBF16X3, D>(m, L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
-    case kF16X3: return apply_for<kF16X3, D>(m, L0, count, list, slm, v, w32, img, tscale, Y, err, sms, st);
+cudaError_t apply_mode(const TcOp& tc, const Level& L0, long count, const int* list, const uint32_t* slm,
+                       const float* v, const unsigned char* img, float tscale, cudaStream_t st) {
+  switch (tc.mode) {
+    case kTF32: return apply_for<kTF32, D>(tc, L0, count, list, slm, v, img, tscale, st);
+    case kBF16: return apply_for<kBF16, D>(tc, L0, count, list, slm, v, img, tscale, st);
+    case kBF16X3: return apply_for<kBF16X3, D>(tc, L0, count, list, slm, v, img, tscale, st);
+    case kF16X3: return apply_for<kF16X3, D>(tc, L0, count, list, slm, v, img, tscale, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <int MD, int D>
 void image_for(int m, const double* tab, double tinv, unsigned char* img, cudaStream_t st) {
-  using S = Shape<MD, D, 1>;
+  using S = Shape<MD, D, 1>;  // the per-row layout does not depend on M
   using O = Opnd<MD>;
   const size_t bytes = image_bytes_for<MD, D>(m);
   // one thread per (chunk row, K column of one part)
   const long total = (long)(bytes / O::kEs / O::kParts);
   long g = (total + 255) / 256;
   if (g > 4096) g = 4096;
-  k_tc2_image<<<(int)g, 256, 0, st>>>(MD, D, m, O::kNch, S::KP, O::kParts, O::kKc, S::SBO, tinv, tab, img, total);
+  const int mp = m <= 1 ? 1 : (m <= 8 ? 8 : 32);
+  k_tc2_image<<<(int)g, 256, 0, st>>>(MD, D, m, mp, O::kNch, S::KP, O::kParts, O::kKc, S::SBO, tinv, tab, img,
+                                      total);
 }
 
 template <int D>
@@ -799,7 +862,7 @@ size_t tc2_image_bytes(int mode, int m, int dofs) {
   return dofs == 24 ? image_bytes_mode<24>(mode, m) : image_bytes_mode<81>(mode, m);
 }
 
-size_t tc2_result_stride() { return (size_t)Shape<kTF32, 81, 1>::YS; }
+size_t tc2_result_stride() { return 84; }  // floats per element of the result buffer (81 used)
 
 float tc2_table_scale(int mode, const double* tab_host, size_t count) {
   if (mode != kF16X3) return 1.f;
@@ -833,22 +896,31 @@ void launch_tc2_image(int mode, int m, int dofs, const double* tab, float tscale
 
 cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cudaStream_t st) {
   if (L0.el2 != nullptr) {  // mixed mesh: triquadratic elements with their slaved nodes, then trilinear ones
-    cudaError_t e = apply_mode<81>(tc.mode, tc.m, L0, L0.ne2, L0.el2, L0.sl2, v, tc.w32, tc.img, tc.tscale, tc.Y2,
-                                   tc.err, tc.sms, st);
+    cudaError_t e = apply_mode<81>(tc, L0, L0.ne2, L0.el2, L0.sl2, v, tc.img, tc.tscale, st);
     if (e != cudaSuccess) return e;
-    return apply_mode<24>(tc.mode, tc.m, L0, L0.ne1, L0.el1, nullptr, v, tc.w32, tc.img1, tc.tscale1, tc.Y2,
-                          tc.err, tc.sms, st);
+    return apply_mode<24>(tc, L0, L0.ne1, L0.el1, nullptr, v, tc.img1, tc.tscale1, st);
   }
   const long E = (long)L0.ex * L0.ey * L0.ez;
-  return apply_mode<81>(tc.mode, tc.m, L0, E, nullptr, nullptr, v, tc.w32, tc.img, tc.tscale, tc.Y2, tc.err,
-                        tc.sms, st);
+  return apply_mode<81>(tc, L0, E, nullptr, nullptr, v, tc.img, tc.tscale, st);
+}
+
+size_t tc2_pack_bytes(int mode, long E) {
+  const long units = (E + kUnit - 1) / kUnit;
+  size_t per_tile = 0;
+  switch (mode) {
+    case kTF32: per_tile = Shape<kTF32, 81, 1>::ABYTES; break;
+    case kBF16: per_tile = Shape<kBF16, 81, 1>::ABYTES; break;
+    case kBF16X3: per_tile = Shape<kBF16X3, 81, 1>::ABYTES; break;
+    default: per_tile = Shape<kF16X3, 81, 1>::ABYTES; break;
+  }
+  return (size_t)units * kPair * per_tile;
 }
 
 void launch_tc2_gather(const Level& L0, const float* Y, const float* b, const float* v, const float* dinv,
                        float omega, int mode, float* out, cudaStream_t st) {
   long g = (L0.nn + 255) / 256;
   if (g > 8192) g = 8192;
-  k_tc2_gather<Shape<kTF32, 81, 1>::YS><<<(int)g, 256, 0, st>>>(L0.Lx, L0.Ly, L0.Lz, L0.ex, L0.ey, L0.ez, Y, b,
+  k_tc2_gather<<<(int)g, 256, 0, st>>>(L0.Lx, L0.Ly, L0.Lz, L0.ex, L0.ey, L0.ez, Y, b,
                                                                  v, dinv, L0.mask, omega, mode, out);
 }
 

@@ -245,7 +245,8 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (d.inner_its > 0) B += 4 * (size_t)P->lv[0].ndof * 4;  // inner PCG vectors
   if (tc2) {  // weights, element results and the table image of the tensor-core level
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
-    B += E0 * (P->m + tc2_result_stride()) * 4 + tc2_image_bytes(tc2_mode_of(d.precision), P->m) +
+    B += E0 * (P->m + tc2_result_stride() + 1) * 4 + tc2_pack_bytes(tc2_mode_of(d.precision), (long)E0) +
+         tc2_image_bytes(tc2_mode_of(d.precision), P->m) +
          tc2_image_bytes(tc2_mode_of(d.precision), P->m, 24) + (size_t)P->m * 576 * 8;
   }
   P->bytes = B;
@@ -281,7 +282,7 @@ void free_all(tosolve_s* h) {
   F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab); F(h->ptab3);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->tcimg); F(h->Y2); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->inner.e); F(h->inner.ri); F(h->inner.pi); F(h->inner.qi);
-  F(h->el2); F(h->sl2); F(h->el1); F(h->tab64q1); F(h->tcimg1);
+  F(h->el2); F(h->sl2); F(h->el1); F(h->tab64q1); F(h->tcimg1); F(h->tcpack); F(h->tcscale);
   F(h->Ad); F(h->Wp); F(h->Vp); F(h->Pg); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
   F(h->cnt);
@@ -751,6 +752,10 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     CKC(dalloc(h, &h->tcimg, tc2_image_bytes(mode, P.m)));
     CKC(dalloc(h, &h->w32, E0 * P.m));
     CKC(dalloc(h, &h->Y2, E0 * tc2_result_stride()));
+    CKC(dalloc(h, &h->tcpack, tc2_pack_bytes(mode, (long)E0)));
+    CKC(dalloc(h, &h->tcscale, E0 + 256));
+    h->tc.apack = h->tcpack;
+    h->tc.escale = h->tcscale;
     std::vector<double> tab((size_t)P.m * kDD2);
     CKC(cudaMemcpyAsync(tab.data(), h->tab64, tab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));
