@@ -1,18 +1,25 @@
 #!/usr/bin/env python3
 """Benchmark: solved DOFs/s to a 1e-8 true residual, mixed-precision vs FP64
-MG-PCG, on the multiresolution cantilever (density 96x48x48, Q1 48x24x24,
-n_mr = 2, smooth design field, filter radius 1.5, 4-level V-cycle).
+MG-PCG, with p50/p99 latency.
+
+Default workload: the adaptive-degree bridge (density 192x96x96, displacement
+mesh 64x32x32 on the degree-2 lattice, n = 3, a seeded half of the elements
+trilinear and the rest triquadratic, four bottom corners pinned, uniform top
+pressure).  The multiresolution cantilever (density 96x48x48, Q1 48x24x24,
+n = 2, 4-level V-cycle) runs beside it and is reported under "c1".
 
 One step = one pass of the whole hot path on device-resident inputs:
 set_densities (filter, SIMP weights, every level's operator, the coarse
 operator's inverse), solve from u0 = 0 to ||f - K u|| / ||f|| <= 1e-8, compliance and
-design gradient.  value = free DOFs / step time (all ranks' DOFs over the
-slowest rank's time; one independent replica per GPU under torchrun).
+design gradient.  value = free DOFs / step time of the fastest mixed
+variant (all ranks' DOFs over the slowest rank's time; one independent
+replica per GPU under torchrun); fp64_value the same with FP64 MG-PCG.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload bridge_mixed|cantilever|bridge_q2|batch64|serve|ibeam_fix|elements]
 
 Prints ONE JSON line (rank 0).  The reference arm times the CPU FP64 oracle
-on the same input on the host cores.
+on a bounded sample of the same workload on the host cores.
 """
 from __future__ import annotations
 
@@ -21,6 +28,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -32,9 +40,15 @@ if ROOT not in sys.path:
 
 WORKLOAD = dict(name="cantilever_mr_96x48x48_q1_48x24x24_n2", nx=48, ny=24, nz=24, n_mr=2,
                 rmin=1.5, density="smooth", seed=0, levels=4, rtol=1e-8)
+DEFAULT_WORKLOAD = "bridge_mixed"
+CPU_STEPS = 4  # oracle steps per replica in cpu_baseline
 METRIC = "Solved DOFs/s to 1e-8 residual (mixed vs FP64 MG-PCG); p50/p99 solve latency"
 UNIT = "DOF/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+try:  # measured copy bandwidth and bf16 GEMM rate of this GPU model
+    MEASURED_PEAKS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+except (OSError, ValueError):
+    MEASURED_PEAKS = {}
 # Derived FP64 peak: 2 DFMA lanes/clk/SM (from the measured 1.19 TFLOP/s
 # DFMA rate at ~1.96 GHz) x 2 flop x 152 SMs x 2070 MHz max SM clock.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
@@ -141,69 +155,101 @@ class ClockSampler:
 
 # ---- CPU oracle (reference arm and cpu_baseline) ------------------------------
 
-def oracle_steps(steps: int, warmup: int, spec_name: str = "cantilever") -> tuple[list, int, int]:
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_ORACLE_CODE = (
+    "import os,sys,time; sys.path.insert(0, %r)\n"
+    "import bench\n"
+    "from oracle import fe, mixed\n"
+    "spec = bench.SPECS[%r]\n"
+    "p = bench.problem(spec, sample='sample' in spec)\n"
+    "def one():\n"
+    "    t = time.perf_counter()\n"
+    "    if p.elem_q1 is not None:\n"
+    "        mixed.MixedModel(p).run(method='splu')\n"
+    "    else:\n"
+    "        fe.Model(p).run(method='mg', rtol=%r, levels=%d)\n"
+    "    return time.perf_counter() - t\n"
+    "for _ in range(%d): one()\n"
+    "ts = [one() for _ in range(%d)]\n"
+    "nfree = mixed.MixedModel(p).free.size if p.elem_q1 is not None else p.nfree\n"
+    "print(' '.join(map(repr, ts)), nfree, p.nrhs)\n")
+
+
+def oracle_steps(steps: int, warmup: int, spec_name: str, procs: int = 1) -> tuple[list, int, int]:
     """Times `steps` full oracle steps (after `warmup` untimed ones) on the
-    workload (its bounded sample where the spec has one), in one fresh
-    single-threaded process (spawned: never forked from a CUDA process).
-    Returns per-step seconds, free DOFs, load cases."""
+    workload (its bounded sample where the spec has one) in `procs`
+    concurrent single-threaded processes (fresh interpreters: never forked
+    from a CUDA process).  Returns each process's per-step seconds, the free
+    DOFs and the load cases."""
     spec = SPECS[spec_name]
     levels = spec["sample"]["levels"] if "sample" in spec else spec["levels"]
-    code = (
-        "import os,sys,time; sys.path.insert(0, %r)\n"
-        "import bench\n"
-        "from oracle import fe\n"
-        "spec = bench.SPECS[%r]\n"
-        "p = bench.problem(spec, sample='sample' in spec)\n"
-        "from oracle import mixed\n"
-        "def one():\n"
-        "    t = time.perf_counter()\n"
-        "    if p.elem_q1 is not None:\n"
-        "        mixed.MixedModel(p).run(method='splu')\n"
-        "    else:\n"
-        "        fe.Model(p).run(method='mg', rtol=%r, levels=%d)\n"
-        "    return time.perf_counter() - t\n"
-        "for _ in range(%d): one()\n"
-        "ts = [one() for _ in range(%d)]\n"
-        "nfree = mixed.MixedModel(p).free.size if p.elem_q1 is not None else p.nfree\n"
-        "print(' '.join(map(repr, ts)), nfree, p.nrhs)\n"
-        % (ROOT, spec_name, spec["rtol"], levels, warmup, steps))
+    code = _ORACLE_CODE % (ROOT, spec_name, spec["rtol"], levels, warmup, steps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       cwd=ROOT, timeout=3600)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    parts = r.stdout.split()
-    return [float(v) for v in parts[:-2]], int(parts[-2]), int(parts[-1])
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True, env=env, cwd=ROOT) for _ in range(procs)]
+    outs = [pr.communicate(timeout=3600) + (pr.returncode,) for pr in ps]
+    times, nfree, nrhs = [], 0, 0
+    for out, err, rc in outs:
+        if rc != 0:
+            raise RuntimeError(err[-2000:])
+        parts = out.split()
+        times.append([float(v) for v in parts[:-2]])
+        nfree, nrhs = int(parts[-2]), int(parts[-1])
+    return times, nfree, nrhs
 
 
-def cpu_baseline_entry(spec_name: str = "cantilever"):
-    ts, nfree, nrhs = oracle_steps(1, 1, spec_name)
-    where = ("the exact benchmark input" if "sample" not in SPECS[spec_name] else
-             "the same recipe at %(nx)dx%(ny)dx%(nz)d (%(levels)d levels)" % SPECS[spec_name]["sample"])
-    solve = ("sparse direct solve of T^T K T (the mixed oracle)" if "q1_fraction" in SPECS[spec_name]
+def sample_text(spec_name: str) -> str:
+    spec = SPECS[spec_name]
+    where = ("the exact benchmark input" if "sample" not in spec else
+             "the same recipe at %(nx)dx%(ny)dx%(nz)d elements" % spec["sample"])
+    solve = ("sparse direct solve of T^T K T (the mixed oracle)" if "q1_fraction" in spec
              else "every MG level's operator, dense Cholesky, MG-PCG to 1e-8")
-    return {"value": nfree * nrhs / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full oracle step (filter, assembly, {solve}, compliance, gradient) on "
-                      f"{where} after one warm-up step, single-threaded: {ts[0]:.2f} s, "
-                      f"{nfree} free DOFs"}
+    return (f"full oracle steps (filter, assembly, {solve}, compliance, gradient) on {where}, "
+            f"one single-threaded process per host core")
+
+
+def cpu_baseline_entry(spec_name: str):
+    """The oracle on the host cores: one single-threaded replica per core,
+    each timing CPU_STEPS steps after one warm-up step; value = all
+    replicas' DOFs over the slowest replica's time.  A single-core run of
+    the same sample is reported beside it."""
+    cores = host_cores()
+    one, nfree, nrhs = oracle_steps(CPU_STEPS, 1, spec_name)
+    t1 = sum(one[0]) / len(one[0])
+    allc, _, _ = oracle_steps(CPU_STEPS, 1, spec_name, procs=cores)
+    slow = max(sum(t) for t in allc)
+    return {"value": cores * CPU_STEPS * nfree * nrhs / slow, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"{sample_text(spec_name)}: {CPU_STEPS} steps each after one warm-up, slowest "
+                      f"replica {slow:.2f} s; {nfree} free DOFs per step",
+            "single_core_value": nfree * nrhs / t1, "single_core_s_per_step": t1}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times, nfree, nrhs = oracle_steps(args.steps, args.warmup)
-    T = sum(times)
-    value = nfree * nrhs * len(times) / T
+    spec_name = args.workload if args.workload in SPECS else DEFAULT_WORKLOAD
+    cores = host_cores()
+    times, nfree, nrhs = oracle_steps(args.steps, args.warmup, spec_name, procs=cores)
+    slow = max(sum(t) for t in times)
+    value = cores * nfree * nrhs * args.steps / slow
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * T / len(times), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * slow / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "precision": "fp64 (CPU oracle, scipy sparse)"},
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
-                         "sample": "each step: one full oracle step on the exact benchmark input"},
+        "config": {"workload": SPECS[spec_name]["name"], "precision": "fp64 (CPU oracle, scipy sparse)",
+                   "sample": sample_text(spec_name)},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                         "sample": f"each step: {sample_text(spec_name)}; {nfree} free DOFs per replica"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -211,30 +257,52 @@ def run_reference(args):
 
 # ---- GPU arm -------------------------------------------------------------------
 
+PREC_NAMES = {"fp64": "PREC_FP64", "fp32": "PREC_FP32", "tf32": "PREC_TF32", "fp32x2": "PREC_FP32X2",
+              "bf16": "PREC_BF16", "bf16x3": "PREC_BF16X3", "f16x3": "PREC_F16X3"}
+TC_PRECS = ("tf32", "bf16", "bf16x3", "f16x3")
+DEFAULT_VARIANTS = {"bridge_mixed": "f16x3+i16,bf16x3+i16,bf16+i8,fp32",
+                    "bridge_q2": "f16x3+i16,bf16x3+i16,bf16+i8,fp32",
+                    "cantilever": "fp32,tf32,fp32x2"}
+
+
+def parse_variant(label: str) -> tuple[str, int]:
+    """'f16x3+i16' -> ('f16x3', 16): the preconditioner's precision and the
+    inner FP32 PCG iterations per outer FP64 iteration (0: one V-cycle)."""
+    name, sep, inner = label.partition("+i")
+    if name not in PREC_NAMES or (sep and not inner.isdigit()):
+        raise ValueError(f"bad variant {label!r}")
+    return name, int(inner or 0)
+
+
+def variant_ok(label: str, p) -> bool:
+    """Whether the library offers this variant on problem p."""
+    name, inner = parse_variant(label)
+    if name == "tf32":
+        return p.degree == 1 and p.n_mr <= 2 or p.degree == 2 and p.n_mr <= 3
+    if name in TC_PRECS:
+        return p.degree == 2 and p.n_mr <= 3
+    if inner:
+        return p.degree == 2 and name not in ("fp64", "fp32x2")
+    return True
+
+
 def kernel_launches(levels: int, iterations: int, attempts: int = 1, degree: int = 1,
                     tc: bool = False) -> int:
-    """Our kernels per step: set_densities (filter; fine element matrices,
-    assembly, two FP32 casts; 2 per coarse level; coarse dense + sweeps),
-    solve (prep and initial residual; per PCG iteration the V-cycle and the
-    CG kernels; the true residual), gradient (masked dot + sum, energies,
-    scale, filter transpose).
+    """ESTIMATE of our kernels in one step, used only when the profiled count
+    (count_launches) is unavailable; it follows the host code of the FP32
+    and TF32 V-cycles without inner iterations.
 
-    Per PCG iteration, trilinear: 4 per non-coarsest level (pre, restrict,
-    prolong, post) + 1 coarse solve, then direction, q = K p and update; the
-    finest post-smoothing step also forms r^T z and z^T q, except on the
-    TF32 path, whose finest pre and post steps are two kernels each and
-    which keeps the separate reduction kernel.  Triquadratic: 7 per
-    non-coarsest level (pre and post are element product + gather,
-    restriction is element-wise + gather with the shape-function
-    transfers) + 1, then reduction, direction, q = K p (product, gather,
-    p^T q) and update.
-
-    set_densities, trilinear: filter 1; finest level 4 (element matrices,
-    assembly, two FP32 casts); coarsest 5 (moments, element matrices,
-    assembly, dense matrix, sweeps); each middle level its moments, element
-    matrices and assembly per memory slab: 11 for the two middle levels of
-    the benchmark cantilever (21 in all, counted from its ncu launch list),
-    taken as 5.5 per middle level elsewhere."""
+    set_densities: filter; finest level element matrices, assembly and two
+    FP32 casts; coarsest moments, element matrices, assembly, dense matrix
+    and sweeps; each middle level about 5.5 (its moments, element matrices
+    and assembly per memory slab).  solve: prep and initial residual, the
+    true residual, and per PCG iteration, trilinear: 4 per non-coarsest
+    level (pre, restrict, prolong, post) + 1 coarse solve, then direction,
+    q = K p and update (the finest post-smoothing step also forms r^T z and
+    z^T q; TF32 adds two kernels to each of its finest pre and post steps
+    and the separate reduction); triquadratic: 7 per non-coarsest level +
+    1, then reduction, direction, q = K p (three kernels) and update.
+    gradient: masked dot and sum, energies, scale, filter transpose."""
     setd = 1 + 4 + 5 + int(round(5.5 * max(levels - 2, 0)))
     per_it = 4 * (levels - 1) + 1 + 3 + (3 if tc else 0)
     if degree == 2:
@@ -244,173 +312,301 @@ def kernel_launches(levels: int, iterations: int, attempts: int = 1, degree: int
     return setd + solve + 5
 
 
-def run_gpu(args):
-    import numpy as np
-    import torch
-    import torch.distributed as dist
+_OURS = re.compile(r"\bk_[a-z0-9_]+")
 
-    from paper_2311_05595_gb300 import tosolve as T
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
-    spec = SPECS[args.workload]
-    p = problem(spec)
-    rtol = spec["rtol"]
-    maxit = 2000
-    stream = torch.cuda.Stream(device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    x = torch.tensor(p.x, device=dev)
-    f = torch.tensor(p.f, device=dev)
-    u = torch.zeros_like(f)
-    gx = torch.zeros_like(x)
+def pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
 
-    def make(precision):
+class GpuContext:
+    def __init__(self, args):
+        import torch
+        import torch.distributed as dist
+
+        from paper_2311_05595_gb300 import tosolve as T
+
+        self.torch, self.dist, self.T = torch, dist, T
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(self.local)
+        if self.world > 1:
+            dist.init_process_group("nccl")
+        self.dev = torch.device("cuda", self.local)
+        self.stream = torch.cuda.Stream(device=self.dev)
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=self.dev)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max_over_ranks(self, v: float) -> float:
+        if self.world == 1:
+            return v
+        t = self.torch.tensor([v], device=self.dev, dtype=self.torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+class Workload:
+    """One benchmark workload on the device: its inputs, a handle per
+    variant, and the step (set_densities, solve from u0 = 0 to the true
+    relative residual rtol, compliance and gradient)."""
+
+    def __init__(self, ctx: GpuContext, spec_name: str):
+        torch = ctx.torch
+        self.ctx, self.spec_name = ctx, spec_name
+        self.spec = SPECS[spec_name]
+        self.p = problem(self.spec)
+        self.x = torch.tensor(self.p.x, device=ctx.dev)
+        self.f = torch.tensor(self.p.f, device=ctx.dev)
+        self.u = torch.zeros_like(self.f)
+        self.gx = torch.zeros_like(self.x)
+        self.rtol, self.maxit = self.spec["rtol"], 2000
+        self.solvers = {}
+
+    def make(self, label: str):
+        T, p = self.ctx.T, self.p
+        name, inner = parse_variant(label)
         d = T.make_desc(p.nx, p.ny, p.nz, degree=p.degree, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin,
-                        nu=p.nu, penal=p.penal, mg_levels=spec["levels"], precision=precision)
-        return T.Solver(d, p.mask, stream, elem_q1=p.elem_q1)
+                        nu=p.nu, penal=p.penal, mg_levels=self.spec["levels"],
+                        precision=getattr(T, PREC_NAMES[name]), inner_its=inner)
+        return T.Solver(d, p.mask, self.ctx.stream, elem_q1=p.elem_q1)
 
-    def step(s):
-        T.tosolve_set_densities(s.h, x)
-        u.zero_()
-        info = T.tosolve_solve(s.h, f, 1, u, rtol, maxit)
-        c = T.tosolve_compliance_grad(s.h, u, f, 1, gx)
+    def step(self, s):
+        T = self.ctx.T
+        T.tosolve_set_densities(s.h, self.x)
+        self.u.zero_()
+        info = T.tosolve_solve(s.h, self.f, 1, self.u, self.rtol, self.maxit)
+        c = T.tosolve_compliance_grad(s.h, self.u, self.f, 1, self.gx)
         return info, c
 
-    def timed(s, steps, warmup):
-        with torch.cuda.stream(stream):
+    def timed(self, s, steps: int, warmup: int):
+        ctx, torch = self.ctx, self.ctx.torch
+        st = ctx.stream
+        with torch.cuda.stream(st):
             for _ in range(warmup):
-                step(s)
-            stream.synchronize()
-            barrier()
+                self.step(s)
+            st.synchronize()
+            ctx.barrier()
             torch.cuda.synchronize()
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                    for _ in range(steps)]
             infos = []
-            t0 = time.perf_counter()
             for e0, e1 in evs:
-                flush.zero_()
-                e0.record(stream)
-                info, c = step(s)
-                e1.record(stream)
-                infos.append((info.iterations, info.total_iterations, info.rel_residual,
-                              info.ms, float(c[0])))
-            stream.synchronize()
+                ctx.flush.zero_()
+                e0.record(st)
+                info, c = self.step(s)
+                e1.record(st)
+                infos.append((info.iterations, info.total_iterations, info.rel_residual, info.ms,
+                              float(c[0])))
+            st.synchronize()
             torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
-            barrier()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        return ms, infos, wall
+            ctx.barrier()
+        return [a.elapsed_time(b) for a, b in evs], infos
 
-    sampler = ClockSampler(local)
-    out = {}
-    precs = {"fp32": T.PREC_FP32, "tf32": T.PREC_TF32, "fp32x2": T.PREC_FP32X2, "bf16": T.PREC_BF16,
-             "bf16x3": T.PREC_BF16X3, "f16x3": T.PREC_F16X3, "fp64": T.PREC_FP64}
-    q2tc = p.degree == 2 and p.elem_q1 is None
-    tc_ok = {"tf32": p.degree == 1 or q2tc, "bf16": q2tc, "bf16x3": q2tc, "f16x3": q2tc}
-    mixed_labels = tuple(v for v in args.variants.split(",") if v != "fp64" and tc_ok.get(v, True))
-    if not mixed_labels or any(v not in precs for v in mixed_labels):
-        raise SystemExit("--variants: a comma list of fp32, tf32, bf16, bf16x3, f16x3, fp32x2 (fp64 always runs)")
-    solvers = {lab: make(precs[lab]) for lab in mixed_labels + ("fp64",)}
-    sampler.start()
-    for label in mixed_labels + ("fp64",):
-        s = solvers[label]
-        ms, infos, wall = timed(s, args.steps, args.warmup)
-        tot = sum(ms)
-        if world > 1:
-            t = torch.tensor([tot], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        solve_ms = sorted(i[3] for i in infos)
-        out[label] = dict(ms=ms, tot=tot, infos=infos, wall=wall, solve_ms=solve_ms, solver=s)
-    clocks = sampler.stop()
-
-    # per-phase device time (separate untimed pass, same step)
-    phases = {}
-    for label in mixed_labels + ("fp64",):
-        s = solvers[label]
+    def phases(self, s, reps: int = 5) -> dict:
+        """Per-phase device time of the same step (separate untimed pass)."""
+        torch, T, st = self.ctx.torch, self.ctx.T, self.ctx.stream
         acc = {"set_densities": 0.0, "solve": 0.0, "gradient": 0.0}
-        nph = 5
-        with torch.cuda.stream(stream):
-            for _ in range(nph):
-                flush.zero_()
+        with torch.cuda.stream(st):
+            for _ in range(reps):
+                self.ctx.flush.zero_()
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-                ev[0].record(stream)
-                T.tosolve_set_densities(s.h, x)
-                u.zero_()
-                ev[1].record(stream)
-                T.tosolve_solve(s.h, f, 1, u, rtol, maxit)
-                ev[2].record(stream)
-                T.tosolve_compliance_grad(s.h, u, f, 1, gx)
-                ev[3].record(stream)
-                stream.synchronize()
-                acc["set_densities"] += ev[0].elapsed_time(ev[1]) / nph
-                acc["solve"] += ev[1].elapsed_time(ev[2]) / nph
-                acc["gradient"] += ev[2].elapsed_time(ev[3]) / nph
-        phases[label] = {k: round(v, 4) for k, v in acc.items()}
-    free_dofs = T.tosolve_free_dofs(solvers["fp64"].h) * p.nrhs
-    best = min(mixed_labels, key=lambda lab: out[lab]["tot"])
-    mixed = out[best]
-    fp64 = out["fp64"]
-    value = world * free_dofs * args.steps / (mixed["tot"] * 1e-3)
-    fp64_value = world * free_dofs * args.steps / (fp64["tot"] * 1e-3)
+                ev[0].record(st)
+                T.tosolve_set_densities(s.h, self.x)
+                self.u.zero_()
+                ev[1].record(st)
+                T.tosolve_solve(s.h, self.f, 1, self.u, self.rtol, self.maxit)
+                ev[2].record(st)
+                T.tosolve_compliance_grad(s.h, self.u, self.f, 1, self.gx)
+                ev[3].record(st)
+                st.synchronize()
+                acc["set_densities"] += ev[0].elapsed_time(ev[1]) / reps
+                acc["solve"] += ev[1].elapsed_time(ev[2]) / reps
+                acc["gradient"] += ev[2].elapsed_time(ev[3]) / reps
+        return {k: round(v, 4) for k, v in acc.items()}
 
-    def pct(v, q):
-        v = sorted(v)
-        return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+    def measure(self, labels, steps: int, warmup: int) -> dict:
+        """Times every variant and FP64; returns the per-variant results."""
+        ctx = self.ctx
+        out = {}
+        for label in tuple(labels) + ("fp64",):
+            s = self.solvers[label] = self.make(label)
+            ms, infos = self.timed(s, steps, warmup)
+            out[label] = dict(ms=ms, tot=ctx.max_over_ranks(sum(ms)), infos=infos,
+                              solve_ms=[i[3] for i in infos])
+        for label in out:
+            out[label]["phases"] = self.phases(self.solvers[label])
+        self.free_dofs = ctx.T.tosolve_free_dofs(self.solvers["fp64"].h) * self.p.nrhs
+        return out
 
-    # ---- end to end through the host-buffer entry point ----
-    s = mixed["solver"]
-    xh = torch.tensor(p.x).pin_memory()
-    fh = torch.tensor(p.f).pin_memory()
-    uh = torch.zeros(p.f.shape, dtype=torch.float64).pin_memory()
-    gh = torch.zeros(p.x.size, dtype=torch.float64).pin_memory()
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            T.tosolve_step_host(s.h, xh.numpy(), fh.numpy(), 1, rtol, maxit, 0, uh.numpy(), gh.numpy())
-        stream.synchronize()
-        barrier()
-        e2e_times = []
-        for _ in range(args.steps):
-            flush.zero_()
-            stream.synchronize()
-            t0 = time.perf_counter()
-            T.tosolve_step_host(s.h, xh.numpy(), fh.numpy(), 1, rtol, maxit, 0, uh.numpy(), gh.numpy())
-            e2e_times.append(time.perf_counter() - t0)
-        barrier()
-    e2e_tot = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_value = world * free_dofs * args.steps / e2e_tot
-    h2d = (p.x.size + p.f.size) * 8
-    d2h = (p.f.size + p.x.size + 1) * 8
+    def summary(self, out: dict, labels, steps: int) -> dict:
+        """value (best mixed variant), fp64_value, latencies, iterations."""
+        world = self.ctx.world
+        best = min(labels, key=lambda lab: out[lab]["tot"])
+        rate = {lab: world * self.free_dofs * steps / (out[lab]["tot"] * 1e-3) for lab in out}
+        m, f = out[best], out["fp64"]
+        return {
+            "best": best, "value": rate[best], "fp64_value": rate["fp64"],
+            "speedup_vs_fp64": rate[best] / rate["fp64"],
+            "ms_per_step": m["tot"] / steps, "fp64_ms_per_step": f["tot"] / steps,
+            "mixed_variants": {lab: rate[lab] for lab in labels},
+            "phase_ms": {lab: out[lab]["phases"] for lab in out},
+            "pcg_iterations": {lab: statistics.median(i[0] for i in out[lab]["infos"]) for lab in out},
+            "pcg_iterations_total": {lab: statistics.median(i[1] for i in out[lab]["infos"])
+                                     for lab in out},
+            "true_rel_residual_max": {lab: max(i[2] for i in out[lab]["infos"]) for lab in out},
+            "compliance_rel_diff_vs_fp64": {
+                lab: abs(out[lab]["infos"][-1][4] - f["infos"][-1][4]) / abs(f["infos"][-1][4])
+                for lab in labels},
+            "solve_latency_ms": {"p50": pct(m["solve_ms"], 0.5), "p99": pct(m["solve_ms"], 0.99),
+                                 "fp64_p50": pct(f["solve_ms"], 0.5), "fp64_p99": pct(f["solve_ms"], 0.99)},
+            "step_latency_ms": {"p50": pct(m["ms"], 0.5), "p99": pct(m["ms"], 0.99),
+                                "fp64_p50": pct(f["ms"], 0.5), "fp64_p99": pct(f["ms"], 0.99)},
+        }
 
-    # ---- dominant kernel: the FP64 operator apply (q = K p in PCG) ----
-    xa = torch.randn(p.ndof, dtype=torch.float64, device=dev)
+    def close(self):
+        for s in self.solvers.values():
+            s.close()
+        self.solvers = {}
+
+
+def _kernel_names(prof) -> list:
+    """Names of the device kernels in a torch.profiler trace."""
+    names = []
+    try:
+        for e in prof.profiler.kineto_results.events():
+            if str(e.device_type()).endswith("CUDA"):
+                names.append(e.name())
+    except Exception:
+        names = []
+    if not names:
+        names = [e.name for e in prof.events() if str(e.device_type).endswith("CUDA")]
+    return names
+
+
+def count_launches(wl: Workload, label: str, host_loop: bool):
+    """Our kernels in one step of `label`, counted from the CUDA activity
+    trace of one step driven by the host loop (the same kernels as the
+    captured graph, whose conditional loop the trace cannot see into).
+    Returns (kernels per step, PCG iterations of that step, None) or
+    (None, None, reason)."""
+    ctx = wl.ctx
+    torch = ctx.torch
+    try:
+        import torch.profiler as tp
+
+        os.environ["TOSOLVE_NO_GRAPH"] = "1"
+        try:
+            s = wl.make(label)
+        finally:
+            if not host_loop:
+                del os.environ["TOSOLVE_NO_GRAPH"]
+        try:
+            with torch.cuda.stream(ctx.stream):
+                wl.step(s)
+                ctx.stream.synchronize()
+                with tp.profile(activities=[tp.ProfilerActivity.CUDA]) as prof:
+                    info, _ = wl.step(s)
+                    ctx.stream.synchronize()
+        finally:
+            s.close()
+        names = _kernel_names(prof)
+        n = sum(1 for nm in names if _OURS.search(nm) and "at::" not in nm)
+        if n == 0:
+            return None, None, f"trace held {len(names)} device events, none of ours"
+        return n, info.iterations, None
+    except Exception as e:
+        return None, None, f"{type(e).__name__}: {str(e)[:200]}"
+
+
+def tc_roofline(wl: Workload, label: str) -> dict:
+    """The stacked subcell contraction kernel alone (the triquadratic
+    elements): operand rows packed once, then the contraction launched
+    between CUDA events on the handle's stream, L2 flushed before each
+    launch (cold) and back to back (warm).  Algorithmic flops per launch:
+    2 m d^2 per triquadratic element (m subcells, d = 81); executed tensor
+    flops add the split products and the padding of K, of the stacked rows
+    and of the element tiles."""
+    ctx, torch, T, st = wl.ctx, wl.ctx.torch, wl.ctx.T, wl.ctx.stream
+    s = wl.solvers[label]
+    p = wl.p
+    name, _ = parse_variant(label)
+    xa = torch.randn(p.ndof, dtype=torch.float64, device=ctx.dev)
+    with torch.cuda.stream(st):
+        T.tosolve_set_densities(s.h, wl.x)
+        T.tosolve_tc_stage(s.h, 0, 1, xa)
+        for _ in range(5):
+            T.tosolve_tc_stage(s.h, 0, 2)
+        cold = []
+        for _ in range(50):
+            ctx.flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            T.tosolve_tc_stage(s.h, 0, 2)
+            e1.record(st)
+            cold.append((e0, e1))
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record(st)
+        for _ in range(200):
+            T.tosolve_tc_stage(s.h, 0, 2)
+        w1.record(st)
+        st.synchronize()
+    us = 1e3 * statistics.mean(a.elapsed_time(b) for a, b in cold)
+    us_warm = 1e3 * w0.elapsed_time(w1) / 200
+    E = p.nx * p.ny * p.nz
+    E2 = E - int(p.elem_q1.sum()) if p.elem_q1 is not None else E
+    m = p.n_mr ** 3
+    flops = 2.0 * m * 81 * 81 * E2
+    kstep = 8 if name == "tf32" else 16
+    kp = (81 + kstep - 1) // kstep * kstep
+    mp = 1 if m <= 1 else next(v for v in (2, 4, 8, 16, 32) if m <= v)
+    rows = 81 * mp
+    products = 3 if name in ("bf16x3", "f16x3") else 1
+    units = (E2 + 255) // 256
+    executed = 2.0 * products * kp * rows * units * 256
+    peak = MEASURED_PEAKS.get("bf16_tflops")  # bf16 and f16 share the dense rate; TF32 half of it
+    peak_note = "bf16_tflops (burst) of measured"
+    if name == "tf32" and peak:
+        peak, peak_note = peak / 2, "bf16_tflops (burst) of measured x 1/2 (nominal TF32 : BF16 ratio)"
+    achieved = flops / (us * 1e-6) / 1e12
+    kern = {"f16x3": "k_tc2_apply<F16X3, 81, 27>", "bf16x3": "k_tc2_apply<BF16X3, 81, 27>",
+            "bf16": "k_tc2_apply<BF16, 81, 27>", "tf32": "k_tc2_apply<TF32, 81, 27>"}[name]
+    key = ("k_tc2_apply", name, source_hash("k_tc2.cu"), wl.spec["name"])
+    return {"kernel": kern + " (tcgen05 stacked subcell contraction of the triquadratic elements)",
+            "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "traffic": NCU_TRAFFIC.get(key),
+            "us_per_launch": us, "us_per_launch_warm_l2": us_warm,
+            "alg_flops_per_launch": flops, "elements": E2, "subcells": m,
+            "executed_tensor_flops_per_launch": executed,
+            "executed_tflops": executed / (us * 1e-6) / 1e12,
+            "peak_note": peak_note}
+
+
+def fp64_roofline(wl: Workload) -> dict:
+    """The FP64 operator apply (q = K p of the outer CG)."""
+    ctx, torch, T, st = wl.ctx, wl.ctx.torch, wl.ctx.T, wl.ctx.stream
+    s = wl.solvers["fp64"]
+    p = wl.p
+    xa = torch.randn(p.ndof, dtype=torch.float64, device=ctx.dev)
     ya = torch.zeros_like(xa)
-    nrep = 200
-    with torch.cuda.stream(stream):
-        T.tosolve_set_densities(s.h, x)
-        for _ in range(10):
+    with torch.cuda.stream(st):
+        T.tosolve_set_densities(s.h, wl.x)
+        for _ in range(5):
             T.tosolve_apply(s.h, 0, 0, xa, ya)
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(nrep):
+        ev = []
+        for _ in range(50):
+            ctx.flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
             T.tosolve_apply(s.h, 0, 0, xa, ya)
-        a1.record(stream)
-        stream.synchronize()
-    us = a0.elapsed_time(a1) * 1e3 / nrep
+            e1.record(st)
+            ev.append((e0, e1))
+        st.synchronize()
+    us = 1e3 * statistics.mean(a.elapsed_time(b) for a, b in ev)
     Lx, Ly, Lz = p.lattice
     nn = Lx * Ly * Lz
     if p.degree == 1:
@@ -418,66 +614,141 @@ def run_gpu(args):
         flops = 18.0 * pairs
         bytes_alg = nn * (243 * 8 + 3 * 8 * 2)
         kernel = "k_apply_diag<double> (FP64 27-point block stencil, K u)"
-        traffic = NCU_TRAFFIC.get(("k_apply_diag<double>", source_hash("k_solve.cu"), spec["name"]))
+        traffic = NCU_TRAFFIC.get(("k_apply_diag<double>", source_hash("k_solve.cu"), wl.spec["name"]))
     else:  # element form: 81x81 FP64 product per element, then the node gather
         E = p.nx * p.ny * p.nz
         flops = 2.0 * 81 * 81 * E
         bytes_alg = E * (81 * 81 * 8 + 81 * 8 * 2) + nn * 3 * 8 * 2
         kernel = "k_q2_apply<double> + k_q2_gather<double> (FP64 element matrices, K u)"
-        traffic = NCU_TRAFFIC.get(("k_q2_apply<double>", source_hash("k_q2.cu"), spec["name"]))
+        traffic = NCU_TRAFFIC.get(("k_q2_apply<double>", source_hash("k_q2.cu"), wl.spec["name"]))
     achieved = flops / (us * 1e-6) / 1e12
+    hbm = MEASURED_PEAKS.get("hbm_gbs")
+    return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "us_per_launch": us, "alg_bytes_per_launch": bytes_alg,
+            "achieved_gbs": bytes_alg / (us * 1e-6) / 1e9,
+            "peak_note": f"FP64 peak derived from unit count and 2070 MHz; HBM peak {hbm} GB/s of measured"}
 
-    its = [i[0] for i in mixed["infos"]]
-    res = max(i[2] for i in mixed["infos"])
+
+def run_gpu(args):
+    import numpy as np
+
+    ctx = GpuContext(args)
+    T, torch = ctx.T, ctx.torch
+    wl = Workload(ctx, args.workload)
+    p = wl.p
+    labels = [v for v in (args.variants or DEFAULT_VARIANTS[args.workload]).split(",") if v != "fp64"]
+    for v in labels:
+        parse_variant(v)
+    labels = tuple(v for v in labels if variant_ok(v, p))
+    if not labels:
+        raise SystemExit("--variants: none of them applies to this workload")
+    sampler = ClockSampler(ctx.local)
+    sampler.start()
+    out = wl.measure(labels, args.steps, args.warmup)
+    c1 = None
+    if args.workload != "cantilever" and not args.no_c1:
+        cw = Workload(ctx, "cantilever")
+        c1labels = tuple(v for v in DEFAULT_VARIANTS["cantilever"].split(",") if variant_ok(v, cw.p))
+        cout = cw.measure(c1labels, args.steps, args.warmup)
+        c1 = dict(workload=cw.spec["name"], free_dofs=cw.free_dofs, **cw.summary(cout, c1labels, args.steps))
+        cw.close()
+    clocks = sampler.stop()
+    sm = wl.summary(out, labels, args.steps)
+    best = sm["best"]
+    free_dofs = wl.free_dofs
+
+    # ---- end to end through the host-buffer entry point ----
+    s = wl.solvers[best]
+    xh = torch.tensor(p.x).pin_memory()
+    fh = torch.tensor(p.f).pin_memory()
+    uh = torch.zeros(p.f.shape, dtype=torch.float64).pin_memory()
+    gh = torch.zeros(p.x.size, dtype=torch.float64).pin_memory()
+    with torch.cuda.stream(ctx.stream):
+        for _ in range(args.warmup):
+            T.tosolve_step_host(s.h, xh.numpy(), fh.numpy(), 1, wl.rtol, wl.maxit, 0, uh.numpy(), gh.numpy())
+        ctx.stream.synchronize()
+        ctx.barrier()
+        e2e_times = []
+        for _ in range(args.steps):
+            ctx.flush.zero_()
+            ctx.stream.synchronize()
+            t0 = time.perf_counter()
+            T.tosolve_step_host(s.h, xh.numpy(), fh.numpy(), 1, wl.rtol, wl.maxit, 0, uh.numpy(), gh.numpy())
+            e2e_times.append(time.perf_counter() - t0)
+        ctx.barrier()
+    e2e_tot = ctx.max_over_ranks(sum(e2e_times))
+    e2e_value = ctx.world * free_dofs * args.steps / e2e_tot
+    h2d = (p.x.size + p.f.size) * 8
+    d2h = (p.f.size + p.x.size + 1) * 8
+
+    # ---- dominant kernel ----
+    name, inner = parse_variant(best)
+    roof = tc_roofline(wl, best) if name in TC_PRECS and p.degree == 2 else fp64_roofline(wl)
+
+    # ---- our kernel launches: counted from one traced step ----
+    per_step, its_traced, why = count_launches(wl, best, args.host_loop)
+    its = int(statistics.median(i[0] for i in out[best]["infos"]))
+    if per_step is not None:
+        launches = per_step * args.steps
+        launch_src = (f"counted: CUDA activity trace of one host-loop step of the same variant "
+                      f"({per_step} kernels, {its_traced} PCG iterations; the timed steps took {its})")
+    else:
+        launches = kernel_launches(T.tosolve_level_count(s.h), its, degree=p.degree,
+                                   tc=name == "tf32") * args.steps
+        launch_src = f"estimate from the host code's launch sequence (trace unavailable: {why})"
+
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": mixed["tot"] / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": sm["value"], "unit": UNIT, "n_gpus": ctx.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sm["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": spec["name"], "free_dofs": free_dofs // p.nrhs, "load_cases": p.nrhs,
-                   "degree": p.degree, "density_cells": int(p.x.size),
-                   "mg_levels": spec["levels"] or "auto",
+        "config": {"workload": wl.spec["name"], "free_dofs": free_dofs // p.nrhs, "load_cases": p.nrhs,
+                   "degree": p.degree if p.elem_q1 is None else "mixed 1/2",
+                   "trilinear_elements": int(p.elem_q1.sum()) if p.elem_q1 is not None else 0,
+                   "density_cells": int(p.x.size), "mg_levels": wl.spec["levels"] or "auto",
                    "smoother": "damped Jacobi omega=0.5, 1+1, V-cycle",
-                   "precision": f"FP64 CG + {best.upper()} V-cycle (value; TF32 = finest level "
-                                f"on tcgen05, FP32X2 = FP32 operators with float-pair vectors); "
-                                f"FP64 MG-PCG (fp64_value)",
-                   "rtol": rtol, "start": "u0 = 0 every step",
+                   "precision": f"FP64 outer CG + {best} preconditioner (value: fastest variant; "
+                                f"+iN = N inner FP32 PCG iterations per outer one); FP64 MG-PCG "
+                                f"(fp64_value)",
+                   "rtol": wl.rtol, "start": "u0 = 0 every step",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                   "parallelism": f"replicas x{world}"},
-        "fp64_value": fp64_value, "speedup_vs_fp64": value / fp64_value,
-        "mixed_variants": {lab: world * free_dofs * args.steps / (out[lab]["tot"] * 1e-3)
-                           for lab in mixed_labels},
-        "fp64_ms_per_step": fp64["tot"] / args.steps,
-        "phase_ms": phases,
-        "pcg_iterations": {lab: statistics.median(i[0] for i in out[lab]["infos"])
-                           for lab in mixed_labels + ("fp64",)},
-        "true_rel_residual_max": res,
-        "solve_latency_ms": {"p50": pct(mixed["solve_ms"], 0.5), "p99": pct(mixed["solve_ms"], 0.99),
-                             "fp64_p50": pct(fp64["solve_ms"], 0.5),
-                             "fp64_p99": pct(fp64["solve_ms"], 0.99)},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": kernel_launches(T.tosolve_level_count(s.h), int(statistics.median(its)),
-                                        degree=p.degree, tc=best == "tf32") * args.steps,
-        "roofline": {"kernel": kernel,
-                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "us_per_launch": us, "alg_bytes_per_launch": bytes_alg,
-                     "achieved_gbs": bytes_alg / (us * 1e-6) / 1e9,
-                     "peak_note": "FP64 peak derived from unit count and 2070 MHz; "
-                                  "HBM peak 6797.9 GB/s of measured"},
+                   "parallelism": f"replicas x{ctx.world}"},
+        **{k: v for k, v in sm.items() if k not in ("best", "value", "ms_per_step")},
+        "best_variant": best,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "call": "tosolve_step_host (pinned host x, f in; u, compliance, gradient out)"},
+        "gpu_launches": launches, "gpu_launches_source": launch_src,
+        "roofline": roof,
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if c1 is not None:
+        line["c1"] = c1
+    wl.close()
+    if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_entry(args.workload)
         except Exception as e:  # reported, never silently dropped
             line["cpu_baseline"] = {"error": str(e)[-300:]}
-    for lab in mixed_labels + ("fp64",):
-        out[lab]["solver"].close()
-    if rank == 0:
+    if ctx.rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    if ctx.world > 1:
+        ctx.dist.destroy_process_group()
+
+
+def run_single_step(args):
+    """One step of the first listed variant (no timing): the command that
+    profiles capture, with --host-loop so that every kernel is a plain
+    launch.  Prints the PCG iterations and the true residual."""
+    ctx = GpuContext(args)
+    wl = Workload(ctx, args.workload)
+    label = (args.variants or DEFAULT_VARIANTS[args.workload]).split(",")[0]
+    s = wl.make(label)
+    with ctx.torch.cuda.stream(ctx.stream):
+        info, c = wl.step(s)
+        ctx.stream.synchronize()
+    s.close()
+    print(json.dumps({"workload": wl.spec["name"], "variant": label, "iterations": info.iterations,
+                      "rel_residual": info.rel_residual, "compliance": float(c[0])}), flush=True)
 
 
 # nx is rounded to a multiple of 16 (not 8) so that every instance coarsens
@@ -907,16 +1178,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="fp32,tf32,fp32x2",
-                    help="mixed-precision variants timed beside FP64 (comma list)")
-    ap.add_argument("--workload", default="cantilever",
-                    choices=["cantilever", "bridge_q2", "bridge_mixed", "batch64", "serve", "ibeam_fix",
+    ap.add_argument("--no-c1", action="store_true", help="skip the cantilever run reported under c1")
+    ap.add_argument("--variants", default=None,
+                    help="mixed-precision variants timed beside FP64, a comma list of "
+                         "fp32, tf32, fp32x2, bf16, bf16x3, f16x3, each optionally +iN "
+                         "(N inner FP32 PCG iterations, degree 2)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=["bridge_mixed", "cantilever", "bridge_q2", "batch64", "serve", "ibeam_fix",
                              "elements"],
-                    help="bridge_q2: the degree-2 bridge; batch64: the 64-instance batched "
-                         "solve; serve: the serving loop (each its own JSON line)")
+                    help="bridge_mixed: the adaptive-degree bridge (default); cantilever: the "
+                         "multiresolution Q1 cantilever; bridge_q2: the bridge with every element "
+                         "triquadratic; batch64: the 64-instance batched solve; serve: the serving "
+                         "loop (each its own JSON line)")
     ap.add_argument("--designs", type=int, default=SERVE["designs"])
     ap.add_argument("--requests", type=int, default=SERVE["requests"])
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--single-step", action="store_true",
+                    help="run one untimed step of the first variant (for profilers)")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the PCG loop from the host (same kernels, no CUDA graph): "
                          "ncu cannot profile kernels inside a graph with a conditional node")
@@ -927,6 +1205,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.single_step:
+        run_single_step(args)
     elif args.workload == "batch64":
         run_batch(args)
     elif args.workload == "serve":

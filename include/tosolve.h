@@ -482,6 +482,21 @@ tosolve_status tosolve_densities(tosolve_t h, double* rho_dev, double* w_dev);
 tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double* x_dev,
                              double* y_dev);
 
+/* Instrumentation of the level-0 tensor-core operator (preconditioner
+ * precision TF32 on degree 2, BF16, BF16X3 or F16X3), so that a caller can
+ * time its stacked subcell contraction (Sec. 3.2, Eq. 10: K_e u_e =
+ * sum_i w_{e,i} K_i u_e) alone between its own events on the handle's
+ * stream.  part 0 = the triquadratic elements (every element of a
+ * single-degree mesh), 1 = the trilinear elements of a mixed mesh.  stages
+ * bit 0: round x_dev (FP64, device, length 3*nodes(0)) to FP32 and pack the
+ * part's operand rows (masked, deflated, split) into the handle's scratch;
+ * bit 1: run the contraction kernel on the rows packed last, writing the
+ * per-element results to the handle's scratch (nothing is returned: use
+ * tosolve_apply for K x).  x_dev is read only with bit 0 (may be NULL
+ * otherwise).  Rows packed for one part are overwritten by a pack of the
+ * other.  Errors: TOSOLVE_EINVAL (no such operator, bad part or stages). */
+tosolve_status tosolve_tc_stage(tosolve_t h, int part, int stages, const double* x_dev);
+
 /* z = B b: one multigrid cycle (Algorithm 1, recursive, zero initial guess)
  * of the preconditioner in its configured precision; b_dev, z_dev FP64,
  * length 3*nodes(0); b must be 0 at fixed DOFs. */

@@ -252,8 +252,11 @@ void launch_tc2_image(int mode, int m, int dofs, const double* tab, float tscale
 // tc.Y2 = per-element stacked contraction of the level-0 vector v (fixed
 // DOFs as zero), weights tc.w32 (E x m); on a mixed level 0 the triquadratic
 // elements with their slaved nodes (T_e^T K T_e) and the trilinear ones on
-// their vertices.
-cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cudaStream_t st);
+// their vertices.  part: -1 every element, 0 the triquadratic (all on a
+// single-degree mesh), 1 the trilinear ones of a mixed mesh; stages: bit 0
+// packs the operand rows, bit 1 runs the contraction on the packed rows.
+cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cudaStream_t st, int part = -1,
+                             int stages = 3);
 // Node gather of Y fused with the V-cycle step: mode 0 b - y, 1 v + omega
 // D^-1 (b - y), 2 y; identity rows at fixed DOFs.
 void launch_tc2_gather(const Level& L0, const float* Y, const float* b, const float* v, const float* dinv,

@@ -755,7 +755,7 @@ __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, con
 
 template <int MD, int D, int M>
 cudaError_t run_apply(const TcOp& tc, const Level& L0, long count, const int* list, const uint32_t* slm,
-                      const float* v, const unsigned char* img, float tscale, cudaStream_t st) {
+                      const float* v, const unsigned char* img, float tscale, int stages, cudaStream_t st) {
   using S = Shape<MD, D, M>;
   static std::once_flag once;  // handles may be created from several threads
   static cudaError_t attr = cudaSuccess;
@@ -780,7 +780,8 @@ cudaError_t run_apply(const TcOp& tc, const Level& L0, long count, const int* li
   pa.escale = tc.escale;
   long gp = (pa.rows + 127) / 128;
   if (gp > 16L * tc.sms) gp = 16L * tc.sms;
-  k_tc2_pack<MD, D><<<(int)gp, 128, 0, st>>>(pa);
+  if (stages & 1) k_tc2_pack<MD, D><<<(int)gp, 128, 0, st>>>(pa);
+  if (!(stages & 2)) return cudaGetLastError();
   Tc2Args a;
   a.E = count;
   a.list = list;
@@ -810,21 +811,21 @@ size_t image_bytes_for(int m) {
 
 template <int MD, int D>
 cudaError_t apply_for(const TcOp& tc, const Level& L0, long count, const int* list, const uint32_t* slm,
-                      const float* v, const unsigned char* img, float tscale, cudaStream_t st) {
-  if (tc.m == 27) return run_apply<MD, D, 27>(tc, L0, count, list, slm, v, img, tscale, st);
-  if (tc.m == 8) return run_apply<MD, D, 8>(tc, L0, count, list, slm, v, img, tscale, st);
-  if (tc.m == 1) return run_apply<MD, D, 1>(tc, L0, count, list, slm, v, img, tscale, st);
+                      const float* v, const unsigned char* img, float tscale, int stages, cudaStream_t st) {
+  if (tc.m == 27) return run_apply<MD, D, 27>(tc, L0, count, list, slm, v, img, tscale, stages, st);
+  if (tc.m == 8) return run_apply<MD, D, 8>(tc, L0, count, list, slm, v, img, tscale, stages, st);
+  if (tc.m == 1) return run_apply<MD, D, 1>(tc, L0, count, list, slm, v, img, tscale, stages, st);
   return cudaErrorInvalidValue;
 }
 
 template <int D>
 cudaError_t apply_mode(const TcOp& tc, const Level& L0, long count, const int* list, const uint32_t* slm,
-                       const float* v, const unsigned char* img, float tscale, cudaStream_t st) {
+                       const float* v, const unsigned char* img, float tscale, int stages, cudaStream_t st) {
   switch (tc.mode) {
-    case kTF32: return apply_for<kTF32, D>(tc, L0, count, list, slm, v, img, tscale, st);
-    case kBF16: return apply_for<kBF16, D>(tc, L0, count, list, slm, v, img, tscale, st);
-    case kBF16X3: return apply_for<kBF16X3, D>(tc, L0, count, list, slm, v, img, tscale, st);
-    case kF16X3: return apply_for<kF16X3, D>(tc, L0, count, list, slm, v, img, tscale, st);
+    case kTF32: return apply_for<kTF32, D>(tc, L0, count, list, slm, v, img, tscale, stages, st);
+    case kBF16: return apply_for<kBF16, D>(tc, L0, count, list, slm, v, img, tscale, stages, st);
+    case kBF16X3: return apply_for<kBF16X3, D>(tc, L0, count, list, slm, v, img, tscale, stages, st);
+    case kF16X3: return apply_for<kF16X3, D>(tc, L0, count, list, slm, v, img, tscale, stages, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -894,14 +895,18 @@ void launch_tc2_image(int mode, int m, int dofs, const double* tab, float tscale
   }
 }
 
-cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cudaStream_t st) {
+cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cudaStream_t st, int part,
+                             int stages) {
   if (L0.el2 != nullptr) {  // mixed mesh: triquadratic elements with their slaved nodes, then trilinear ones
-    cudaError_t e = apply_mode<81>(tc, L0, L0.ne2, L0.el2, L0.sl2, v, tc.img, tc.tscale, st);
-    if (e != cudaSuccess) return e;
-    return apply_mode<24>(tc, L0, L0.ne1, L0.el1, nullptr, v, tc.img1, tc.tscale1, st);
+    if (part != 1) {
+      cudaError_t e = apply_mode<81>(tc, L0, L0.ne2, L0.el2, L0.sl2, v, tc.img, tc.tscale, stages, st);
+      if (e != cudaSuccess || part == 0) return e;
+    }
+    return apply_mode<24>(tc, L0, L0.ne1, L0.el1, nullptr, v, tc.img1, tc.tscale1, stages, st);
   }
+  if (part == 1) return cudaSuccess;  // no trilinear elements
   const long E = (long)L0.ex * L0.ey * L0.ez;
-  return apply_mode<81>(tc, L0, E, nullptr, nullptr, v, tc.img, tc.tscale, st);
+  return apply_mode<81>(tc, L0, E, nullptr, nullptr, v, tc.img, tc.tscale, stages, st);
 }
 
 size_t tc2_pack_bytes(int mode, long E) {

@@ -1507,6 +1507,21 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
   return TOSOLVE_OK;
 }
 
+tosolve_status tosolve_tc_stage(tosolve_t h, int part, int stages, const double* x_dev) {
+  if (h == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
+  if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");
+  if (!h->tc.on || h->tc.deg != 2) return set_err(h, TOSOLVE_EINVAL, "the handle has no degree-2 tensor-core operator");
+  if (part < 0 || part > 1 || stages < 1 || stages > 3) return set_err(h, TOSOLVE_EINVAL, "part must be 0 or 1, stages 1 .. 3");
+  if (part == 1 && !h->mixed) return set_err(h, TOSOLVE_EINVAL, "part 1 needs a mixed mesh");
+  Level& L0 = h->lv[0];
+  if (stages & 1) {
+    if (x_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
+    launch_cast(false, (size_t)L0.ndof, x_dev, L0.v, true, h->st);
+  }
+  CK(launch_tc2_apply(h->tc, L0, (const float*)L0.v, h->st, part, stages));
+  return TOSOLVE_OK;
+}
+
 tosolve_status tosolve_precondition(tosolve_t h, const double* b_dev, double* z_dev) {
   if (h == nullptr || b_dev == nullptr || z_dev == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
   if (!h->have_rho) return set_err(h, TOSOLVE_EINVAL, "call tosolve_set_densities first");

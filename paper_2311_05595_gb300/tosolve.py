@@ -86,6 +86,7 @@ def _load():
         "tosolve_densities": ([vp, vp, vp], i),
         "tosolve_apply": ([vp, i, i, vp, vp], i),
         "tosolve_precondition": ([vp, vp, vp], i),
+        "tosolve_tc_stage": ([vp, i, i, vp], i),
         "tosolve_batch_create": ([P(vp), i, P(i), P(vp), P(vp), P(vp)], i),
         "tosolve_batch_solve": ([vp, d, i, vp], i),
         "tosolve_batch_destroy": ([vp], None),
@@ -395,6 +396,11 @@ def tosolve_densities(h, rho_dev=None, w_dev=None) -> None:
 
 def tosolve_apply(h, level: int, precision: int, x_dev, y_dev) -> None:
     _check(h, _lib.tosolve_apply(h, level, precision, _ptr(x_dev), _ptr(y_dev)), "tosolve_apply")
+
+
+def tosolve_tc_stage(h, part: int, stages: int, x_dev=None) -> None:
+    _check(h, _lib.tosolve_tc_stage(h, part, stages, _ptr(x_dev)),
+           "tosolve_tc_stage")
 
 
 def tosolve_precondition(h, b_dev, z_dev) -> None:
