@@ -431,7 +431,7 @@ void tosolve_server_destroy(tosolve_server_t s);
 #define TOSOLVE_NOALLOC_SCRATCH_BYTES 77824
 
 /* c_dev[r] = f_r^T u_r summed over the free DOFs, r < nrhs: the compliance
- * of tosolve_compliance_grad (Sec. 3.4), for callers that may not allocate
+ * that tosolve_compliance_grad returns, for callers that may not allocate
  * device memory when they need it (code confined to buffers a host
  * application hands it, or a latency-critical loop that cannot afford the
  * device-wide synchronisation a cudaMalloc can cause).  The paper has no
@@ -447,9 +447,11 @@ void tosolve_server_destroy(tosolve_server_t s);
  * TOSOLVE_NOALLOC_SCRATCH_BYTES per device, shared by every call and keeping
  * what the last call wrote; each call overwrites every entry it reads.
  * Calls whose kernels may overlap on the GPU race on that array: order them
- * (one stream, or events).  The first call on a device, with that device
- * current, looks up the array's address with cudaGetSymbolAddress; make that
- * first call before any stream capture begins.  Asynchronous (does not
+ * (one stream, or events).  A call made outside a stream capture looks up
+ * the array's address on the current device with cudaGetSymbolAddress; a
+ * call inside a capture reuses the address of the last call made outside
+ * one on that device, so make one call before capturing (again after a
+ * cudaDeviceReset, which moves the array).  Asynchronous (does not
  * synchronise).  Errors: EINVAL (NULL pointer, ndof or nrhs out of range;
  * checked before any CUDA call), ECUDA.  Message: tosolve_last_error(NULL). */
 tosolve_status tosolve_compliance_noalloc(const double* f_dev, const double* u_dev,

@@ -74,19 +74,27 @@ __global__ void __launch_bounds__(kThreads) k_noalloc_total(const double* __rest
   if (threadIdx.x == 0) c[r] = v;
 }
 
-// Device address of the array on the current device, looked up on the first
-// call made with that device current and remembered afterwards.
-cudaError_t part_address(double** out) {
+// Device address of the array on the current device.  Outside a stream
+// capture it is looked up afresh on every call (a context torn down by
+// cudaDeviceReset and created again reloads the module at a new address);
+// during a capture, where the lookup may not run, the address of the last
+// call made outside capture on that device is used.
+cudaError_t part_address(cudaStream_t st, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_part_ptr[dev] == nullptr) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_part);
     if (e != cudaSuccess) return e;
     g_part_ptr[dev] = static_cast<double*>(p);
+  } else if (g_part_ptr[dev] == nullptr) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_part_ptr[dev];
   return cudaSuccess;
@@ -111,14 +119,17 @@ extern "C" tosolve_status tosolve_compliance_noalloc(const double* f_dev, const 
         "live in a fixed device array of 16 x 608 doubles");
     return TOSOLVE_EINVAL;
   }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   double* part = nullptr;
-  cudaError_t e = part_address(&part);
+  cudaError_t e = part_address(st, &part);
   if (e != cudaSuccess) {
-    tos::set_last_error("tosolve_compliance_noalloc: cudaGetSymbolAddress of the scratch array failed");
+    tos::set_last_error(e == cudaErrorStreamCaptureUnsupported
+                            ? "tosolve_compliance_noalloc: the first call on a device (and the first after a "
+                              "context reset) must come before any stream capture"
+                            : "tosolve_compliance_noalloc: cudaGetSymbolAddress of the scratch array failed");
     cudaGetLastError();
     return TOSOLVE_ECUDA;
   }
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const size_t blocks = (ndof + kThreads - 1) / kThreads;
   const int parts = (int)(blocks < (size_t)kParts ? blocks : (size_t)kParts);
   k_noalloc_partial<<<dim3(parts, nrhs), kThreads, 0, st>>>((long)ndof, mask_dev, f_dev, u_dev, part);

@@ -1298,6 +1298,7 @@ tosolve_status tosolve_solve(tosolve_t h, const double* f_dev, int nrhs, double*
   tosolve_status result = TOSOLVE_OK;
   int total = 0, last = 0;
   double worst = 0.0;
+  auto worse = [](double a, double b) { return (a == a && b == b) ? std::fmax(a, b) : NAN; };  // NaN stays
   if (cudaEventRecord(h->ev0, st) != cudaSuccess) return finish(set_err(h, TOSOLVE_ECUDA, "event record failed"));
   for (int r = 0; r < nrhs && result == TOSOLVE_OK; ++r) {
     const double* fr = f_dev + r * nd;
@@ -1342,12 +1343,12 @@ tosolve_status tosolve_solve(tosolve_t h, const double* f_dev, int nrhs, double*
       if (S.status != 0) {
         result = TOSOLVE_EBREAKDOWN;
         h->err = S.coarse_status ? "coarse sweep met a non-positive pivot (coarsest operator not SPD)" : "PCG breakdown (p^T K p <= 0 or NaN)";
-        worst = std::fmax(worst, rel);
+        worst = worse(worst, rel);
         break;
       }
-      if (rel <= rtol) { worst = std::fmax(worst, rel); break; }
+      if (rel <= rtol) { worst = worse(worst, rel); break; }
       if (used >= maxit || attempt == 3) {
-        worst = std::fmax(worst, rel);
+        worst = worse(worst, rel);
         result = TOSOLVE_ENOTCONV;
         h->err = used >= maxit ? "maxit reached before the tolerance"
                                : "the true residual stayed above the tolerance after 3 restarts";

@@ -222,10 +222,11 @@ def test_cantilever_24x12x12_matches_direct_solve(precision, seed):
     R.close()
 
 
-@pytest.mark.parametrize("precision", [FP32, TF32, FP32X2])
+@pytest.mark.parametrize("precision", [FP64, FP32, TF32, FP32X2])
 def test_multiresolution_48x24x24_full_size(precision):
     """Config: density 96x48x48, Q1 48x24x24 (n = 2), smooth field, r = 1.5,
-    4 levels, FP32 / TF32 preconditioner -- the benchmark workload."""
+    4 levels, FP64 / FP32 / TF32 / FP32X2 preconditioner -- the cantilever
+    workload of the benchmark."""
     p = workloads.cantilever(48, 24, 24, n_mr=2, rmin=1.5, density="smooth", seed=0, mg_levels=4)
     m = fe.Model(p)
     ref = _c1_reference(m)
@@ -336,4 +337,27 @@ def test_host_buffer_step_matches_device_calls():
     assert info2.iterations == info.iterations
     np.testing.assert_array_equal(uh, u.cpu().numpy())
     assert ch[0] == c[0] and np.array_equal(gh, gx)
+    R.close()
+
+
+def test_nan_in_load_is_a_breakdown():
+    """A NaN in f makes the first residual norm NaN: the solve stops with
+    TOSOLVE_EBREAKDOWN at once, fills info (status, iterations 0, NaN
+    residual) and leaves the handle usable for the next, finite load."""
+    import torch
+
+    p = workloads.cantilever(8, 4, 4, n_mr=2, rmin=1.0, seed=5, mg_levels=2)
+    R = Run(p, FP32)
+    R.set_densities()
+    T = R.T
+    good = R.f.clone()
+    R.f[0, 17] = float("nan")
+    u, info = R.solve(rtol=1e-8, raise_on_error=False)
+    assert info.status == T.EBREAKDOWN
+    assert info.iterations == 0
+    assert not np.isfinite(info.rel_residual)
+    assert "breakdown" in T.tosolve_last_error(R.h).lower()
+    R.f.copy_(good)
+    u, info = R.solve(rtol=1e-8)
+    assert info.status == T.OK and info.rel_residual <= 1e-8
     R.close()

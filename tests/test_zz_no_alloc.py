@@ -68,3 +68,28 @@ def test_noalloc_rejects_too_many_load_cases():
     T.tosolve_compliance_noalloc(f, f, mask, n, T.NOALLOC_MAX_RHS, c)
     torch.cuda.synchronize()
     assert np.all(c.cpu().numpy()[: T.NOALLOC_MAX_RHS] == n)
+
+
+def test_noalloc_grid_stride_sixteen_load_cases():
+    """ndof above 608 blocks x 256 threads, so every block strides over the
+    vector several times; 16 load cases with a random mask against the
+    float64 sum over the free DOFs (numpy, pairwise order)."""
+    torch = pytest.importorskip("torch")
+    from tests.gpu_helpers import lib
+
+    T = lib()
+    n, nrhs = 200_003, T.NOALLOC_MAX_RHS
+    rng = np.random.default_rng(41)
+    f = rng.normal(size=(nrhs, n))
+    u = rng.normal(size=(nrhs, n))
+    mask = (rng.random(n) < 0.3).astype(np.uint8)
+    ref = (f * u)[:, mask == 0].sum(axis=1)
+    dev = torch.device("cuda:0")
+    fd, ud = torch.tensor(f, device=dev), torch.tensor(u, device=dev)
+    md = torch.tensor(mask, device=dev)
+    c = torch.full((nrhs,), float("nan"), dtype=torch.float64, device=dev)
+    T.tosolve_compliance_noalloc(fd, ud, md, n, nrhs, c)
+    torch.cuda.synchronize()
+    # sum of |f u| bounds the rounding of either order
+    scale = np.abs(f * u)[:, mask == 0].sum(axis=1)
+    np.testing.assert_array_less(np.abs(c.cpu().numpy() - ref), 1e-13 * scale)
