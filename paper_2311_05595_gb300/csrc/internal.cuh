@@ -96,6 +96,7 @@ struct Level {
   int* err = nullptr;  // set when an operator tile copy times out
   int k = 1;        // Lagrange degree of the level's elements
   const float* ptab = nullptr;  // shape-function transfers into this level: the table W (else null)
+  bool lag = false;             // ... products of 1D quadratic Lagrange transfers (degree 2 -> 2)
   // degree 2: the operator as element matrices (81 x 81 each, full)
   double* K64 = nullptr;
   float* K32 = nullptr;
@@ -337,9 +338,17 @@ void launch_s2_prolong(int vt, const Level& F, const Level& C, const float* W, c
 void launch_q2_elem(const Level& L, int n, const double* w, int Dx, int Dy, const double* tab,
                     double* Ke, cudaStream_t st);
 // Lagrange degree 2: element matrices of any level by sum factorisation over
-// the moments of its N^3 density cells per element (N = L.nsub <= 64).
+// the moments of its N^3 density cells per element (N = L.nsub <= 64); with
+// a list only the listed elements; with slv (per lattice node, 1 = slaved)
+// each element's matrix is constrained, T_e^T K T_e.
 bool q2_elem_sf_supported(int N);
-void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double nu, double* Ke, cudaStream_t st);
+void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double nu, const int* list, long count,
+                       const uint8_t* slv, double* Ke, cudaStream_t st);
+// Trilinear elements of a mixed level 0 (L.el1): sum of the n^3 weighted
+// trilinear subcell matrices tab1 (m x 24 x 24), on the vertex DOFs of each
+// element's 81 x 81 slot, zero elsewhere.
+void launch_q1v_elem(const Level& L, int n, const double* w, int Dx, int Dy, const double* tab1, double* Ke,
+                     cudaStream_t st);
 void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, const double* cmom,
                            double* Mscr, double* Ke, cudaStream_t st);
 void launch_q2_dinv(bool fp64, const Level& L, const double* Ke, void* dinv, cudaStream_t st);
@@ -348,9 +357,7 @@ void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t s
 // 2 Av (identity rows at fixed DOFs).  Ke is FP64 for kVtF64, else FP32.
 void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b, const void* v,
                   const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st);
-// Mixed degree: K^(e) <- T_e^T K^(e) T_e; f <- T^T f; u <- T u (slv: per
-// lattice node, 1 = slaved).
-void launch_q2_constrain(const Level& L, const uint8_t* slv, double* Ke, int sms, cudaStream_t st);
+// Mixed degree: f <- T^T f; u <- T u (slv: per lattice node, 1 = slaved).
 void launch_q2_fold(const Level& L, const uint8_t* slv, double* f, cudaStream_t st);
 void launch_q2_expand(const Level& L, const uint8_t* slv, double* u, cudaStream_t st);
 // Lagrange degree 2: the same sensitivities from the strain energy at the

@@ -433,6 +433,53 @@ __global__ void k_q2_moments(int ex, int ey, int N, const double* __restrict__ w
   for (int q = threadIdx.x; q < kNM; q += blockDim.x) M[e * kNM + q] = red[q];
 }
 
+template <int K>
+__device__ __forceinline__ long elem_node_k(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
+  constexpr int NA = K + 1;
+  return (K * exi + a % NA) + (long)Lx * ((K * eyi + (a / NA) % NA) + (long)Ly * (K * ezi + a / (NA * NA)));
+}
+__device__ __forceinline__ long elem_node(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
+  return elem_node_k<2>(exi, eyi, ezi, a, Lx, Ly);
+}
+
+// Parent vertices of local node a of a 27-node element (the corners of the
+// edge, face or cell whose midpoint a is); returns how many.
+__device__ __forceinline__ int local_parents(int a, int par[8]) {
+  const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+  const int xs[2] = {ax == 1 ? 0 : ax, ax == 1 ? 2 : ax};
+  const int ys[2] = {ay == 1 ? 0 : ay, ay == 1 ? 2 : ay};
+  const int zs[2] = {az == 1 ? 0 : az, az == 1 ? 2 : az};
+  const int nx = ax == 1 ? 2 : 1, ny = ay == 1 ? 2 : 1, nz = az == 1 ? 2 : 1;
+  int k = 0;
+  for (int c = 0; c < nz; ++c)
+    for (int b = 0; b < ny; ++b)
+      for (int q = 0; q < nx; ++q) par[k++] = xs[q] + 3 * (ys[b] + 3 * zs[c]);
+  return k;
+}
+
+// The same as a table in constant memory (read uniformly by a warp).
+struct ParentTab {
+  signed char p[27][8];
+  unsigned char n[27];
+};
+constexpr ParentTab make_parent_tab() {
+  ParentTab t{};
+  for (int a = 0; a < 27; ++a) {
+    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
+    const int nx = ax == 1 ? 2 : 1, ny = ay == 1 ? 2 : 1, nz = az == 1 ? 2 : 1;
+    int k = 0;
+    for (int c = 0; c < nz; ++c)
+      for (int b = 0; b < ny; ++b)
+        for (int q = 0; q < nx; ++q) {
+          const int px = ax == 1 ? 2 * q : ax, py = ay == 1 ? 2 * b : ay, pz = az == 1 ? 2 * c : az;
+          t.p[a][k++] = (signed char)(px + 3 * (py + 3 * pz));
+        }
+    t.n[a] = (unsigned char)k;
+  }
+  return t;
+}
+__constant__ ParentTab c_parents = make_parent_tab();
+
 // Element matrices of a Lagrange degree-2 level by sum factorisation (any
 // level: the element covers N^3 density cells of constant weight).  With
 // N_a(xi) = phi_ax(xi) phi_ay(eta) phi_az(zeta), the entries of Eq.
@@ -465,9 +512,11 @@ __device__ __forceinline__ int sf_pair(int s, int t) {  // s <= t: 00 11 22 01 0
 
 __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int N, double h, double nu,
                                                    const double* __restrict__ w, int Dx, int Dy,
-                                                   double* __restrict__ Ke) {
+                                                   const int* __restrict__ list, const uint8_t* __restrict__ slv,
+                                                   int Lx, int Ly, double* __restrict__ Ke) {
   extern __shared__ __align__(16) unsigned char sfraw[];
   SfSmem& S = *reinterpret_cast<SfSmem*>(sfraw);
+  __shared__ unsigned slaved;  // bit a: local node a is slaved (mixed meshes)
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int t = tid; t < 4 * kP * 9; t += nt) {
     const int tau = t / (kP * 9), p = (t / 9) % kP, xy = t % 9;
@@ -484,9 +533,13 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
   const double mu = 1.0 / (2.0 * (1.0 + nu));
   const double hh = 0.5 * h;
   __syncthreads();
-  for (long e = blockIdx.x; e < E; e += gridDim.x) {
+  for (long idx = blockIdx.x; idx < E; idx += gridDim.x) {
+    const long e = list ? (long)list[idx] : idx;
     const int exi = (int)(e % ex), eyi = (int)((e / ex) % ey), ezi = (int)(e / ((long)ex * ey));
+    if (tid == 0) slaved = 0u;
     for (int q = tid; q < kNM; q += nt) S.M[q] = 0.0;
+    __syncthreads();
+    if (slv != nullptr && tid < kNE && slv[elem_node(exi, eyi, ezi, tid, Lx, Ly)]) atomicOr(&slaved, 1u << tid);
     // ---- moments, one z-slice of cells at a time ----
     for (int c = 0; c < N; ++c) {
       for (int t = tid; t < N * kP; t += nt) {
@@ -538,16 +591,53 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
       S.F[pr][ab] = acc;
     }
     __syncthreads();
+    // ---- slaved nodes (mixed meshes): T^T K T = the assembly of T_n^T F T_n ----
+    // T = T_n (x) I_3 acts on the nodes alone, so the congruence is applied to
+    // every 27 x 27 F^st before the assembly: the column of a slaved node s is
+    // added, times 1 / (its parents), to the columns of its parent vertices and
+    // cleared (thread per row, s in increasing order), then the same on rows.
+    const unsigned sm = slaved;
+    if (sm) {
+      for (int t = tid; t < 6 * 27; t += nt) {
+        double* row = &S.F[t / 27][(t % 27) * 27];
+        for (int a = 0; a < kNE; ++a) {
+          if (!((sm >> a) & 1u)) continue;  // uniform across the block
+          const int np = c_parents.n[a];
+          const double v = row[a] * (1.0 / np);
+          for (int q = 0; q < np; ++q) row[c_parents.p[a][q]] += v;
+          row[a] = 0.0;
+        }
+      }
+      __syncthreads();
+      for (int t = tid; t < 6 * 27; t += nt) {
+        double* col = &S.F[t / 27][t % 27];
+        for (int a = 0; a < kNE; ++a) {
+          if (!((sm >> a) & 1u)) continue;
+          const int np = c_parents.n[a];
+          const double v = col[a * 27] * (1.0 / np);
+          for (int q = 0; q < np; ++q) col[c_parents.p[a][q] * 27] += v;
+          col[a * 27] = 0.0;
+        }
+      }
+      __syncthreads();
+    }
     // ---- K[(a,i),(b,j)] ----
+    // K is symmetric: the upper triangle R <= C is formed and written to
+    // both places (u = R * 81 - R (R - 1) / 2 + C - R)
     double* out = Ke + e * (size_t)kDD;
-    for (int t = tid; t < kDD; t += nt) {
-      const int R = t / kD, C = t % kD;
+    for (int u = tid; u < kD * (kD + 1) / 2; u += nt) {
+      int R = (int)((2 * kD + 1 - sqrtf((float)((2 * kD + 1) * (2 * kD + 1) - 8 * u))) * 0.5f);
+      while (R > 0 && R * kD - R * (R - 1) / 2 > u) --R;
+      while ((R + 1) * kD - (R + 1) * R / 2 <= u) ++R;
+      const int C = R + u - (R * kD - R * (R - 1) / 2);
       const int a = R / 3, i = R % 3, b = C / 3, j = C % 3;
       const double fij = i <= j ? S.F[sf_pair(i, j)][a * 27 + b] : S.F[sf_pair(j, i)][b * 27 + a];
       const double fji = j <= i ? S.F[sf_pair(j, i)][a * 27 + b] : S.F[sf_pair(i, j)][b * 27 + a];
       double v = lam * fij + mu * fji;
       if (i == j) v += mu * (S.F[0][a * 27 + b] + S.F[1][a * 27 + b] + S.F[2][a * 27 + b]);
-      out[t] = hh * v;
+      v *= hh;
+      out[R * kD + C] = v;
+      out[C * kD + R] = v;
     }
     __syncthreads();
   }
@@ -610,15 +700,6 @@ __global__ void k_q2_elem(int ex, int ey, long E, int n, const double* __restric
     }
     for (int q = 0; q < ne; ++q) Ke[(e0 + q) * (size_t)kDD + ent] = acc[q];
   }
-}
-
-template <int K>
-__device__ __forceinline__ long elem_node_k(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
-  constexpr int NA = K + 1;
-  return (K * exi + a % NA) + (long)Lx * ((K * eyi + (a / NA) % NA) + (long)Ly * (K * ezi + a / (NA * NA)));
-}
-__device__ __forceinline__ long elem_node(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
-  return elem_node_k<2>(exi, eyi, ezi, a, Lx, Ly);
 }
 
 // Elements along one axis that contain lattice coordinate c (degree K, e
@@ -712,6 +793,122 @@ __global__ void __launch_bounds__(96) k_s2_restrict_elem(int Lxf, int Lyf, int e
         if (wgt != 0.f) acc.add(wgt, rs[f][c]);
       }
       Y[e * kD + threadIdx.x] = acc.value();
+    }
+  }
+}
+
+// Lagrange degree 2 -> 2 (a coarse element spans 2 x 2 x 2 fine elements,
+// 4 fine lattice intervals per axis): the coarse shape functions are products
+// of 1D quadratics, so the transfers are products of 1D transfers.  Along one
+// axis a fine node at offset f = 0..4 in its coarse element takes the coarse
+// node at f / 2 with weight 1 when f is even, else all three with the values
+// of the quadratics at -1/2 (f = 1: 3/8, 3/4, -1/8) or +1/2 (f = 3: -1/8,
+// 3/4, 3/8).  Every weight and every product of three is dyadic, exact in
+// FP32, and equal to the corresponding entry of the 27 x 125 table.
+__device__ __forceinline__ int l2_taps(int i, int e_max, int* c, float* w) {
+  const int e = min(i >> 2, e_max), f = i - 4 * e;
+  if (!(f & 1)) {
+    c[0] = 2 * e + (f >> 1);
+    w[0] = 1.f;
+    return 1;
+  }
+  c[0] = 2 * e;
+  c[1] = 2 * e + 1;
+  c[2] = 2 * e + 2;
+  w[0] = f == 1 ? 0.375f : -0.125f;
+  w[1] = 0.75f;
+  w[2] = f == 1 ? -0.125f : 0.375f;
+  return 3;
+}
+
+// v_f += (P z_c)_f at the free fine DOFs, one thread per fine node.
+template <typename T>
+__global__ void k_l2_prolong(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int ecx, int ecy, int ecz,
+                             const uint8_t* __restrict__ maskf, const T* __restrict__ zc, T* __restrict__ v) {
+  const long nnf = (long)Lxf * Lyf * Lzf;
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nnf;
+       node += (long)gridDim.x * blockDim.x) {
+    const int i = node % Lxf, j = (node / Lxf) % Lyf, l = node / ((long)Lxf * Lyf);
+    int cx[3], cy[3], cz[3];
+    float wx[3], wy[3], wz[3];
+    const int nx = l2_taps(i, ecx - 1, cx, wx), ny = l2_taps(j, ecy - 1, cy, wy), nz = l2_taps(l, ecz - 1, cz, wz);
+    Sum<T> acc[3];
+    for (int c = 0; c < nz; ++c)
+      for (int b = 0; b < ny; ++b) {
+        const float wzy = wz[c] * wy[b];
+        const long row = (long)Lxc * (cy[b] + (long)Lyc * cz[c]);
+        for (int a = 0; a < nx; ++a) {
+          const float wgt = wzy * wx[a];
+          const T* zp = zc + 3 * (row + cx[a]);
+          acc[0].add(wgt, zp[0]);
+          acc[1].add(wgt, zp[1]);
+          acc[2].add(wgt, zp[2]);
+        }
+      }
+    for (int c = 0; c < 3; ++c)
+      if (!maskf[3 * node + c]) v[3 * node + c] += acc[c].value();
+  }
+}
+
+// Coarse-node taps of the transpose: coarse lattice index I gathers the fine
+// nodes 2I - 1, 2I, 2I + 1 (weights 3/4, 1, 3/4) when I is odd (a mid-edge
+// node), else 2I - 3, 2I - 1, 2I, 2I + 1, 2I + 3 (-1/8, 3/8, 1, 3/8, -1/8),
+// clipped to the fine lattice: the same products as the prolongation.  Five
+// fixed slots, absent ones with weight 0 on node 2I (always in range).
+__device__ __forceinline__ void l2_rtaps(int I, int Lf, int (&f)[5], float (&w)[5]) {
+  const bool odd = I & 1;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int off = odd ? (q < 3 ? q - 1 : 0) : (q == 0 ? -3 : (q == 4 ? 3 : q - 2));
+    const float wq = odd ? (q == 1 ? 1.f : (q < 3 ? 0.75f : 0.f))
+                         : (q == 2 ? 1.f : ((q == 1 || q == 3) ? 0.375f : -0.125f));
+    const int i = 2 * I + off;
+    const bool in = i >= 0 && i < Lf && wq != 0.f;
+    f[q] = in ? i : 2 * I;
+    w[q] = in ? wq : 0.f;
+  }
+}
+
+// b_c = R r_f = P^T r_f (zero at the fixed coarse DOFs) and, unless vc is
+// null, the first smoothing step v_c = omega D^-1 b_c; one thread per coarse
+// node, the fine nodes in a fixed order.
+template <typename T>
+__global__ void k_l2_restrict(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int Lzc, const T* __restrict__ rf,
+                              const uint8_t* __restrict__ maskc, T* __restrict__ bc,
+                              const op_t<T>* __restrict__ dinvc, T omega, T* __restrict__ vc) {
+  const long nnc = (long)Lxc * Lyc * Lzc;
+  for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nnc;
+       node += (long)gridDim.x * blockDim.x) {
+    const int I = node % Lxc, J = (node / Lxc) % Lyc, K = node / ((long)Lxc * Lyc);
+    int fx[5], fy[5], fz[5];
+    float wx[5], wy[5], wz[5];
+    l2_rtaps(I, Lxf, fx, wx);
+    l2_rtaps(J, Lyf, fy, wy);
+    l2_rtaps(K, Lzf, fz, wz);
+    Sum<T> acc[3];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      if (wz[c] == 0.f) continue;
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        const float wzy = wz[c] * wy[b];
+        if (wzy == 0.f) continue;
+        const long row = (long)Lxf * (fy[b] + (long)Lyf * fz[c]);
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+          const float wgt = wzy * wx[a];
+          const T* rp = rf + 3 * (row + fx[a]);
+          acc[0].add(wgt, rp[0]);
+          acc[1].add(wgt, rp[1]);
+          acc[2].add(wgt, rp[2]);
+        }
+      }
+    }
+    for (int c = 0; c < 3; ++c) {
+      const long d = 3 * node + c;
+      const T bv = maskc[d] ? T(0) : acc[c].value();
+      bc[d] = bv;
+      if (vc != nullptr) vc[d] = omega * dinvc[d] * bv;
     }
   }
 }
@@ -1148,68 +1345,71 @@ __global__ void __launch_bounds__(256) k_q2_energy_sf(int ex, int ey, long E, in
 // reading): a non-vertex lattice node touching a trilinear element is slaved
 // to the linear interpolation of the 2^q vertices of its edge, face or cell
 // (q = number of its odd lattice coordinates, weight 2^-q each).  The slaved
-// values of an element come from its own corners, so the constraint is local:
-// K^(e) <- T_e^T K^(e) T_e.  Block per element, the matrix staged in shared
-// memory; elements without slaved nodes are left as they are.
-__device__ __forceinline__ int local_parents(int a, int par[8]) {
-  const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
-  const int xs[2] = {ax == 1 ? 0 : ax, ax == 1 ? 2 : ax};
-  const int ys[2] = {ay == 1 ? 0 : ay, ay == 1 ? 2 : ay};
-  const int zs[2] = {az == 1 ? 0 : az, az == 1 ? 2 : az};
-  const int nx = ax == 1 ? 2 : 1, ny = ay == 1 ? 2 : 1, nz = az == 1 ? 2 : 1;
-  int k = 0;
-  for (int c = 0; c < nz; ++c)
-    for (int b = 0; b < ny; ++b)
-      for (int q = 0; q < nx; ++q) par[k++] = xs[q] + 3 * (ys[b] + 3 * zs[c]);
-  return k;
-}
+// values of an element come from its own corners, so the constraint is local,
+// K^(e) <- T_e^T K^(e) T_e: the triquadratic elements apply it inside their
+// sum-factorised set-up (k_q2_elem_sf), the trilinear ones carry their own
+// 24 x 24 matrix on the vertices (k_q1v_elem).
 
-__global__ void k_q2_constrain(int ex, int ey, long E, int Lx, int Ly, const uint8_t* __restrict__ slv,
-                               double* __restrict__ Ke) {
-  extern __shared__ double Ks[];  // 81 x 81
-  __shared__ int sl[kNE];
-  for (long e = blockIdx.x; e < E; e += gridDim.x) {
-    const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
-    if (threadIdx.x < kNE) sl[threadIdx.x] = slv[elem_node(exi, eyi, ezi, threadIdx.x, Lx, Ly)];
+// Trilinear elements of a mixed level 0: K1^(e) = sum_i w_{e,i} K1_i over the
+// n^3 subcells (the trilinear subcell table at this element size), written
+// into the element's 81 x 81 slot on its vertex DOFs, zero elsewhere (the
+// slot is read by the apply's vertex block, the Jacobi diagonal and a
+// one-level dense coarse operator).  kEB elements per block: the 300 entries
+// of the symmetric 24 x 24 block share each table read, are staged in shared
+// memory, and the slots are then written whole (coalesced).
+__device__ __forceinline__ int q1v_slot_vertex(int r27) {  // 27-node local index -> vertex 0..7, or -1
+  const int x = r27 % 3, y = (r27 / 3) % 3, z = r27 / 9;
+  return ((x | y | z) & 1) ? -1 : (x >> 1) + 2 * (y >> 1) + 4 * (z >> 1);
+}
+__global__ void __launch_bounds__(256) k_q1v_elem(int ex, int ey, long E1, const int* __restrict__ list, int n,
+                                                  const double* __restrict__ w, int Dx, int Dy,
+                                                  const double* __restrict__ tab1, double* __restrict__ Ke) {
+  extern __shared__ double q1sm[];  // wq[kEB * m], then Kq[kEB][576]
+  const int m = n * n * n;
+  double* wq = q1sm;
+  double* Kq = q1sm + kEB * m;
+  for (long e0 = blockIdx.x * (long)kEB; e0 < E1; e0 += (long)gridDim.x * kEB) {
+    const int ne = (int)min((long)kEB, E1 - e0);
     __syncthreads();
-    int any = 0;
-    for (int a = 0; a < kNE; ++a) any |= sl[a];
-    if (any) {
-      double* K = Ke + e * (size_t)kDD;
-      for (int t = threadIdx.x; t < kDD; t += blockDim.x) Ks[t] = K[t];
-      __syncthreads();
-      // K T: column groups; thread per row, slaved columns folded into their
-      // parents, in a fixed order
-      for (int R = threadIdx.x; R < kD; R += blockDim.x)
-        for (int a = 0; a < kNE; ++a) {
-          if (!sl[a]) continue;
-          int par[8];
-          const int np = local_parents(a, par);
-          const double w = 1.0 / np;
-          for (int c = 0; c < 3; ++c) {
-            const double v = Ks[R * kD + 3 * a + c];
-            for (int q = 0; q < np; ++q) Ks[R * kD + 3 * par[q] + c] += w * v;
-            Ks[R * kD + 3 * a + c] = 0.0;
-          }
-        }
-      __syncthreads();
-      // T^T (K T): the same on rows, thread per column
-      for (int Cc = threadIdx.x; Cc < kD; Cc += blockDim.x)
-        for (int a = 0; a < kNE; ++a) {
-          if (!sl[a]) continue;
-          int par[8];
-          const int np = local_parents(a, par);
-          const double w = 1.0 / np;
-          for (int c = 0; c < 3; ++c) {
-            const double v = Ks[(3 * a + c) * kD + Cc];
-            for (int q = 0; q < np; ++q) Ks[(3 * par[q] + c) * kD + Cc] += w * v;
-            Ks[(3 * a + c) * kD + Cc] = 0.0;
-          }
-        }
-      __syncthreads();
-      for (int t = threadIdx.x; t < kDD; t += blockDim.x) K[t] = Ks[t];
+    for (int t = threadIdx.x; t < kEB * m; t += blockDim.x) {
+      const int q = t / m, s = t % m;
+      double v = 0.0;
+      if (q < ne) {
+        const long e = list[e0 + q];
+        const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+        const int a = s % n, b = (s / n) % n, c = s / (n * n);
+        v = w[(n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c))];
+      }
+      wq[t] = v;
     }
     __syncthreads();
+    for (int u = threadIdx.x; u < 300; u += blockDim.x) {  // upper triangle of the 24 x 24 block
+      int r = 0, off = 0;
+      while (off + (24 - r) <= u) { off += 24 - r; ++r; }
+      const int c = r + u - off;
+      double acc[kEB];
+#pragma unroll
+      for (int q = 0; q < kEB; ++q) acc[q] = 0.0;
+      for (int s = 0; s < m; ++s) {
+        const double tv = tab1[(size_t)s * 576 + r * 24 + c];
+#pragma unroll
+        for (int q = 0; q < kEB; ++q) acc[q] += wq[q * m + s] * tv;
+      }
+#pragma unroll
+      for (int q = 0; q < kEB; ++q) {
+        Kq[q * 576 + r * 24 + c] = acc[q];
+        Kq[q * 576 + c * 24 + r] = acc[q];
+      }
+    }
+    __syncthreads();
+    for (int q = 0; q < ne; ++q) {
+      double* out = Ke + (size_t)list[e0 + q] * kDD;
+      for (int t = threadIdx.x; t < kDD; t += blockDim.x) {
+        const int R = t / kD, Cc = t % kD;
+        const int rv = q1v_slot_vertex(R / 3), cv = q1v_slot_vertex(Cc / 3);
+        out[t] = (rv >= 0 && cv >= 0) ? Kq[q * 576 + (3 * rv + R % 3) * 24 + 3 * cv + Cc % 3] : 0.0;
+      }
+    }
   }
 }
 
@@ -1291,6 +1491,11 @@ void launch_s2_restrict(int vt, const Level& F, const Level& C, const float* W, 
   const bool pdeg = F.k == 3;  // degree 3 -> 2 on the same elements
   auto run = [&](auto tag) {
     using T = decltype(tag);
+    if (C.lag && !pdeg) {  // products of 1D Lagrange transfers, one pass
+      k_l2_restrict<T><<<g, 256, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, (const T*)F.r, C.mask, (T*)C.b,
+                                          (const op_t<T>*)dinvc, (T)omega, (T*)vc);
+      return;
+    }
     if (pdeg)
       k_s2_restrict_elem<3, T><<<(int)ge, 96, 0, st>>>(F.Lx, F.Ly, C.ex, C.ey, Ec, W, (const T*)F.r, (T*)C.Y);
     else
@@ -1307,6 +1512,11 @@ void launch_s2_prolong(int vt, const Level& F, const Level& C, const float* W, c
   const int g = grid_for2(F.nn);
   auto run = [&](auto tag) {
     using T = decltype(tag);
+    if (C.lag && F.k == 2) {
+      k_l2_prolong<T><<<g, 256, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.ex, C.ey, C.ez, F.mask, (const T*)C.z,
+                                         (T*)F.v);
+      return;
+    }
     if (F.k == 3)
       k_s2_prolong<3, T><<<g, 256, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.ex, C.ey, C.ez, W, F.mask,
                                             (const T*)C.z, (T*)F.v);
@@ -1353,8 +1563,10 @@ void launch_q3_subcell_table(int n, double nu, double h, int family, double* gra
 
 bool q2_elem_sf_supported(int N) { return N >= 1 && N <= kSfMaxN; }
 
-void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double nu, double* Ke, cudaStream_t st) {
-  const long E = (long)L.ex * L.ey * L.ez;
+void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double nu, const int* list, long count,
+                       const uint8_t* slv, double* Ke, cudaStream_t st) {
+  const long E = list ? count : (long)L.ex * L.ey * L.ez;
+  if (E <= 0) return;
   const size_t sm = sizeof(SfSmem);
   static std::once_flag attr;  // handles may be created from several threads
   std::call_once(attr, [sm] {
@@ -1363,7 +1575,7 @@ void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double n
   long g = (long)L.sms * 3;  // three 70 KB blocks per SM
   if (g > E) g = E;
   if (g < 1) g = 1;
-  k_q2_elem_sf<<<(int)g, 256, sm, st>>>(L.ex, L.ey, E, L.nsub, L.h, nu, w, Dx, Dy, Ke);
+  k_q2_elem_sf<<<(int)g, 256, sm, st>>>(L.ex, L.ey, E, L.nsub, L.h, nu, w, Dx, Dy, list, slv, L.Lx, L.Ly, Ke);
 }
 
 void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, const double* cmom,
@@ -1463,15 +1675,14 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
   else run(dfloat(0.f, 0.f));
 }
 
-void launch_q2_constrain(const Level& L, const uint8_t* slv, double* Ke, int sms, cudaStream_t st) {
-  const long E = (long)L.ex * L.ey * L.ez;
-  static std::once_flag attr;  // handles may be created from several threads
-  std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_q2_constrain, cudaFuncAttributeMaxDynamicSharedMemorySize, kDD * 8);
-  });
-  long g = (long)sms * 4;
-  if (g > E) g = E;
-  k_q2_constrain<<<(int)g, 256, kDD * 8, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, slv, Ke);
+void launch_q1v_elem(const Level& L, int n, const double* w, int Dx, int Dy, const double* tab1, double* Ke,
+                     cudaStream_t st) {
+  if (L.ne1 <= 0) return;
+  const int m = n * n * n;
+  long g = (L.ne1 + kEB - 1) / kEB;
+  if (g > (long)L.sms * 8) g = (long)L.sms * 8;
+  k_q1v_elem<<<(int)g, 256, (size_t)kEB * (m + 576) * sizeof(double), st>>>(L.ex, L.ey, L.ne1, L.el1, n, w, Dx,
+                                                                             Dy, tab1, Ke);
 }
 
 void launch_q2_fold(const Level& L, const uint8_t* slv, double* f, cudaStream_t st) {

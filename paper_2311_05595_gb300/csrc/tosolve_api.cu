@@ -670,6 +670,9 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     L0.sl2 = h->sl2;
     L0.el1 = h->el1;
     L0.ne1 = h->ne1;
+    // the trilinear elements' subcell table (Sec. 3.3) at the level-0 size
+    CKC(dalloc(h, &h->tab64q1, (size_t)P.m * 576));
+    launch_subcell_table(P.n, h->d.nu, L0.h, h->tab64q1, st);
   }
   // tables (Sec. 3.3: the subcell matrices are computed once)
   if (h->d.degree >= 2) {
@@ -733,7 +736,10 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       CKC(dalloc(h, &h->ptab, W.size()));
       CKC(cudaMemcpyAsync(h->ptab, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, st));
       // into every degree-2 level that halves the mesh of the level above
-      for (int l = (h->d.degree == 3 ? 2 : 1); l < P.L; ++l) h->lv[l].ptab = h->ptab;
+      for (int l = (h->d.degree == 3 ? 2 : 1); l < P.L; ++l) {
+        h->lv[l].ptab = h->ptab;
+        h->lv[l].lag = h->d.family == 0;
+      }
     }
     const Plan::Lv& v0 = P.lv[0];
     CKC(dalloc(h, &h->Yq, (size_t)v0.ex * v0.ey * v0.ez * (h->d.degree == 3 ? kD3 : kD2)));
@@ -762,9 +768,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     const float tscale = tc2_table_scale(mode, tab.data(), tab.size());
     launch_tc2_image(mode, P.m, 81, h->tab64, tscale, h->tcimg, st);
     if (h->mixed) {  // trilinear elements: the degree-1 subcell table on their vertices
-      CKC(dalloc(h, &h->tab64q1, (size_t)P.m * 576));
       CKC(dalloc(h, &h->tcimg1, tc2_image_bytes(mode, P.m, 24)));
-      launch_subcell_table(P.n, h->d.nu, 1.0, h->tab64q1, st);
       std::vector<double> t1((size_t)P.m * 576);
       CKC(cudaMemcpyAsync(t1.data(), h->tab64q1, t1.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
       CKC(cudaStreamSynchronize(st));
@@ -980,8 +984,11 @@ static tosolve_status refresh(tosolve_t h) {
     // Lagrange degree-2 levels by sum factorisation; the serendipity element
     // and the cubic finest level by their subcell tables / moment bases
     auto form = [&](Level& Lv, int l, double* Kdst, double* Mscr, cudaStream_t s) {
-      if (d.family == 0 && Lv.k == 2 && q2_elem_sf_supported(Lv.nsub))
-        launch_q2_elem_sf(Lv, h->w, h->Dx, h->Dy, d.nu, Kdst, s);
+      if (l == 0 && h->mixed) {  // triquadratic elements constrained, trilinear ones on their vertices
+        launch_q2_elem_sf(Lv, h->w, h->Dx, h->Dy, d.nu, Lv.el2, Lv.ne2, h->slv0, Kdst, s);
+        launch_q1v_elem(Lv, n, h->w, h->Dx, h->Dy, h->tab64q1, Kdst, s);
+      } else if (d.family == 0 && Lv.k == 2 && q2_elem_sf_supported(Lv.nsub))
+        launch_q2_elem_sf(Lv, h->w, h->Dx, h->Dy, d.nu, nullptr, 0, nullptr, Kdst, s);
       else if (l == 0)
         launch_q2_elem(Lv, n, h->w, h->Dx, h->Dy, h->tab64, Kdst, s);
       else
@@ -992,7 +999,6 @@ static tosolve_status refresh(tosolve_t h) {
       form(C, L - 1, h->Kec, h->Mqc, cst);
     } else {
       form(C, 0, C.K64, nullptr, cst);
-      if (h->mixed) launch_q2_constrain(C, h->slv0, C.K64, C.sms, cst);
       Kc = C.K64;
     }
     CK(cudaMemsetAsync(h->Ad, 0, (size_t)h->nc * h->nc * sizeof(double), cst));
@@ -1003,7 +1009,6 @@ static tosolve_status refresh(tosolve_t h) {
     for (int l = 0; l + 1 < L; ++l) {
       Level& Lv = h->lv[l];
       form(Lv, l, Lv.K64, h->Mq, st);
-      if (l == 0 && h->mixed) launch_q2_constrain(Lv, h->slv0, Lv.K64, Lv.sms, st);
       launch_q2_dinv(true, Lv, Lv.K64, Lv.dinv64, st);
       if (Lv.K32) launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * (Lv.k == 3 ? kDD3 : kDD2), Lv.K64, Lv.K32, st);
       if (Lv.dinv32) launch_q2_dinv(false, Lv, Lv.K64, Lv.dinv32, st);
