@@ -28,7 +28,16 @@ Readings taken here (the paper does not say):
   * serendipity levels hold their face and element-centre nodes at 0 like
     supports, and use omega = 0.3 (damped Jacobi with 0.5 diverges on these
     elements: lambda_max(D^-1 A) is about 5.3 for degree 2, 5.0 for degree
-    3); cubic Lagrange hierarchies use 0.4 (lambda_max about 4.0).
+    3); cubic Lagrange hierarchies use 0.4 (lambda_max about 4.0);
+  * Chebyshev smoothing (the alternative to damped Jacobi that the method
+    statement names; the paper itself smooths degree >= 2 with SSOR,
+    Sec. 7.5): the Chebyshev iteration of Saad, Iterative Methods for Sparse
+    Linear Systems, Sec. 12.3, on D^-1 A over [0.3 b, b] with b = 1.1 x the
+    largest eigenvalue of D^-1 A as estimated by `lanczos_steps` Lanczos
+    steps from a fixed start vector (the Weyl sequence frac(d phi) - 1/2 over
+    the DOF index d, zero at fixed DOFs), `cheb_degree` steps before and
+    after the coarse correction.  The same polynomial pre and post keeps the
+    cycle symmetric.
 """
 from __future__ import annotations
 
@@ -159,6 +168,79 @@ def p_coarse_mask(mask3: np.ndarray, mesh_shape) -> np.ndarray:
     return out.reshape(-1)
 
 
+GOLDEN = 0.6180339887498949  # (sqrt 5 - 1) / 2
+
+
+def weyl_start(ndof: int, mask: np.ndarray) -> np.ndarray:
+    """The Lanczos start vector: frac(d * phi) - 1/2 for DOF index d
+    (a Weyl sequence), 0 at the fixed DOFs."""
+    x = np.arange(ndof, dtype=np.float64) * GOLDEN
+    x = x - np.floor(x) - 0.5
+    x[np.asarray(mask) != 0] = 0.0
+    return x
+
+
+def lanczos_lmax(A, Dinv: np.ndarray, mask: np.ndarray, steps: int) -> float:
+    """Estimate of the largest eigenvalue of D^-1 A: the largest Ritz value
+    after `steps` Lanczos steps on the symmetric D^-1/2 A D^-1/2 from
+    D^1/2 weyl_start, written in the unscaled vectors p = D^-1/2 q:
+        alpha_j = p_j^T A p_j,
+        s = D^-1 A p_j - alpha_j p_j - beta_j p_{j-1},
+        beta_{j+1} = (s^T D s)^1/2,  p_{j+1} = s / beta_{j+1},
+    with p_1^T D p_1 = 1; the Ritz values are the eigenvalues of the
+    tridiagonal matrix (alpha; beta_2 ..), each at most lambda_max."""
+    from scipy.linalg import eigvalsh_tridiagonal
+
+    p = weyl_start(A.shape[0], mask)
+    p = p / np.sqrt(p @ (p / Dinv))
+    p_prev = np.zeros_like(p)
+    alphas, betas = [], []
+    beta = 0.0
+    for j in range(steps):
+        y = A @ p
+        alpha = p @ y
+        alphas.append(alpha)
+        if j == steps - 1:
+            break
+        sv = Dinv * y - alpha * p - beta * p_prev
+        beta = np.sqrt(sv @ (sv / Dinv))
+        betas.append(beta)
+        p_prev, p = p, sv / beta
+    return float(eigvalsh_tridiagonal(np.array(alphas), np.array(betas))[-1])
+
+
+def chebyshev_coefficients(lmax_est: float, degree: int):
+    """Interval [0.3 b, b], b = 1.1 lmax_est: centre theta, half-width delta.
+    Returns 1/theta (the first step, x1 = x0 + D^-1 r0 / theta) and, for each
+    further step i, (rho_i rho_{i-1}, 2 rho_i / delta) with rho_0 =
+    delta / theta and rho_i = 1 / (2 theta / delta - rho_{i-1}) (Saad,
+    Algorithm 12.1 on D^-1 A)."""
+    hi = 1.1 * lmax_est
+    lo = 0.3 * hi
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    coefs = []
+    for _ in range(1, degree):
+        rho_n = 1.0 / (2.0 * sigma - rho)
+        coefs.append((rho_n * rho, 2.0 * rho_n / delta))
+        rho = rho_n
+    return 1.0 / theta, coefs, theta, delta
+
+
+def chebyshev_smooth(L, b: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """cheb_degree Chebyshev steps on A x = b from x: x1 = x0 + D^-1 (b - A
+    x0) / theta, then x_i = x_{i-1} + c1_i (x_{i-1} - x_{i-2}) + c2_i D^-1 (b
+    - A x_{i-1})."""
+    inv_theta, coefs = L.cheb[0], L.cheb[1]
+    x_prev = x
+    x = x + inv_theta * L.Dinv * (b - L.A @ x)
+    for c1, c2 in coefs:
+        x_new = x + c1 * (x - x_prev) + c2 * L.Dinv * (b - L.A @ x)
+        x_prev, x = x, x_new
+    return x
+
+
 def coarse_mask(mask_f: np.ndarray, lat_fine) -> np.ndarray:
     """Coarse DOF fixed iff the coincident fine DOF is fixed."""
     Lx, Ly, Lz = lat_fine
@@ -174,9 +256,14 @@ class Hierarchy:
     """Level operators A_l (supports -> identity), Jacobi diagonals, P_l and
     the dense Cholesky factor of the coarsest operator."""
 
-    def __init__(self, prob, rho: np.ndarray, levels: int, transfer: str | None = None):
+    def __init__(self, prob, rho: np.ndarray, levels: int, transfer: str | None = None,
+                 smoother: str = "jacobi", cheb_degree: int = 2, lanczos_steps: int = 8):
+        if smoother not in ("jacobi", "chebyshev"):
+            raise ValueError("smoother is 'jacobi' or 'chebyshev'")
+        self.smoother = smoother
         if prob.degree == 3:
-            self._init_cubic(prob, rho, levels)
+            self._init_cubic(prob, rho, levels, smoother, cheb_degree, lanczos_steps)
+            self._init_chebyshev(cheb_degree, lanczos_steps)
             return
         k, n = prob.degree, prob.n_mr
         family = getattr(prob, "family", "lagrange")
@@ -225,9 +312,16 @@ class Hierarchy:
             F.P = (Mf @ P @ Mc).tocsr()
         last = self.levels[-1]
         last.chol = sla.cho_factor(last.A.toarray(), lower=True)
+        self._init_chebyshev(cheb_degree, lanczos_steps)
+
+    def _init_chebyshev(self, degree: int, steps: int):
+        """Chebyshev data of every level but the coarsest (Jacobi: none)."""
+        for L in self.levels[:-1]:
+            L.lmax = lanczos_lmax(L.A, L.Dinv, L.mask, steps) if self.smoother == "chebyshev" else None
+            L.cheb = chebyshev_coefficients(L.lmax, degree) if L.lmax is not None else None
 
 
-def _cubic_levels(self, prob, rho, levels):
+def _cubic_levels(self, prob, rho, levels, smoother="jacobi", cheb_degree=2, lanczos_steps=8):
     """Degree 3 (Lagrange or serendipity): level 0 is the degree-3 mesh,
     level 1 the degree-2 mesh of the same family on the same elements (the
     degree is coarsened first, Sec. 2.3's shape-function interpolation as
@@ -245,7 +339,7 @@ def _cubic_levels(self, prob, rho, levels):
     if family == "serendipity":
         m2 = (m2.astype(bool) | serendipity_absent(lat2, 2)).astype(np.uint8)
     q.mask = m2
-    sub = Hierarchy(q, rho, levels - 1)
+    sub = Hierarchy(q, rho, levels - 1, smoother=smoother, cheb_degree=cheb_degree, lanczos_steps=lanczos_steps)
     self.omega = 0.3 if family == "serendipity" else 0.4
     w_cells = simp_weights(rho, prob.E0, prob.Emin, prob.penal)
     F = Level()
@@ -282,9 +376,10 @@ def vcycle(h: Hierarchy, b: np.ndarray, l: int = 0, omega: float | None = None, 
     L = h.levels[l]
     if l == len(h.levels) - 1:
         return sla.cho_solve(L.chol, b)
+    cheb = getattr(h, "smoother", "jacobi") == "chebyshev"
     v = np.zeros_like(b)
-    for _ in range(eta1):  # step 1: pre-smoothing, damped Jacobi
-        v = v + omega * L.Dinv * (b - L.A @ v)
+    for _ in range(eta1):  # step 1: pre-smoothing, damped Jacobi or Chebyshev
+        v = chebyshev_smooth(L, b, v) if cheb else v + omega * L.Dinv * (b - L.A @ v)
     r = b - L.A @ v  # step 2: residual
     rH = L.P.T @ r  # step 3: restriction R = P^T
     eH = np.zeros_like(rH)
@@ -292,7 +387,7 @@ def vcycle(h: Hierarchy, b: np.ndarray, l: int = 0, omega: float | None = None, 
         eH = eH + vcycle(h, rH - h.levels[l + 1].A @ eH, l + 1, omega, eta1, eta2, gamma)
     v = v + L.P @ eH  # steps 5-6: prolong and correct
     for _ in range(eta2):  # step 7: post-smoothing
-        v = v + omega * L.Dinv * (b - L.A @ v)
+        v = chebyshev_smooth(L, b, v) if cheb else v + omega * L.Dinv * (b - L.A @ v)
     return v
 
 

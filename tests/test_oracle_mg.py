@@ -9,7 +9,14 @@
   * a cycle with eta1 = eta2 and the same Jacobi smoother is a symmetric
     operator (Algorithm 1 pre/post structure);
   * with a single level the cycle is the exact (Cholesky) solve;
-  * MG-PCG converges to the direct solution.
+  * MG-PCG converges to the direct solution;
+  * Chebyshev smoothing: k steps take the error to p_k(D^-1 A) e0, the
+    scaled Chebyshev polynomial evaluated independently (numpy's Chebyshev
+    series on the eigenvalues of D^-1 A); one step is damped Jacobi with
+    omega = 1/theta; the Lanczos estimate is a lower bound of lambda_max
+    within 10 % (exact on a diagonal matrix with as many steps as
+    eigenvalues); the cycle stays symmetric; PCG reaches the direct solution
+    in fewer iterations than with Jacobi.
 """
 import numpy as np
 import pytest
@@ -157,3 +164,104 @@ def test_degree3_p_coarsening_is_galerkin_and_converges(family):
     u, its, _ = mg.pcg(h, f, rtol=1e-11)
     ref = m.run(method="splu")
     assert np.linalg.norm(u - ref["u"][0]) <= 1e-8 * np.linalg.norm(ref["u"][0])
+
+
+# ---- Chebyshev smoothing ------------------------------------------------------
+
+def _cheb_case(deg=2, family="lagrange", levels=2, k=2):
+    p = workloads.cantilever(4, 2, 2, degree=deg, n_mr=2, rmin=0.0, seed=6, mg_levels=levels)
+    if family == "serendipity":
+        p = workloads.with_serendipity(p)
+    m = fe.Model(p)
+    h = mg.Hierarchy(p, m.densities(p.x), levels, smoother="chebyshev", cheb_degree=k)
+    return p, h
+
+
+def _scaled_eigen(L):
+    """Eigenpairs of D^-1 A through the symmetric D^-1/2 A D^-1/2."""
+    A = L.A.toarray()
+    dh = np.sqrt(L.Dinv)
+    lam, Q = np.linalg.eigh(dh[:, None] * A * dh[None, :])
+    return lam, Q, dh
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_chebyshev_error_is_the_scaled_chebyshev_polynomial(k):
+    """k smoothing steps map the error e0 to p_k(D^-1 A) e0 with
+    p_k(t) = T_k((theta - t) / delta) / T_k(theta / delta), evaluated here
+    by numpy's Chebyshev series on the eigenvalues of D^-1 A."""
+    from numpy.polynomial import chebyshev as C
+
+    p, h = _cheb_case(k=k)
+    L = h.levels[0]
+    _, _, theta, delta = mg.chebyshev_coefficients(L.lmax, k)
+    lam, Q, dh = _scaled_eigen(L)
+    rng = np.random.default_rng(5)
+    xs = rng.normal(size=L.A.shape[0])
+    x0 = rng.normal(size=L.A.shape[0])
+    b = L.A @ xs
+    e = mg.chebyshev_smooth(L, b, x0) - xs
+    Tk = np.zeros(k + 1)
+    Tk[k] = 1.0
+    pk = C.chebval((theta - lam) / delta, Tk) / C.chebval(theta / delta, Tk)
+    # D^-1 A = D^-1/2 S D^1/2, S = Q diag(lam) Q^T
+    ref = (Q * pk) @ (Q.T @ ((x0 - xs) / dh)) * dh
+    np.testing.assert_allclose(e, ref, atol=1e-11 * np.abs(x0 - xs).max())
+
+
+def test_chebyshev_degree_one_is_damped_jacobi():
+    p, h = _cheb_case(k=1)
+    L = h.levels[0]
+    rng = np.random.default_rng(2)
+    b, x = rng.normal(size=L.A.shape[0]), rng.normal(size=L.A.shape[0])
+    omega = L.cheb[0]
+    np.testing.assert_allclose(mg.chebyshev_smooth(L, b, x), x + omega * L.Dinv * (b - L.A @ x), rtol=1e-14)
+
+
+def test_lanczos_estimate_is_a_close_lower_bound():
+    p, h = _cheb_case()
+    for L in h.levels[:-1]:
+        lam = _scaled_eigen(L)[0]
+        assert L.lmax <= lam.max() * (1 + 1e-12)
+        assert L.lmax >= 0.9 * lam.max()
+        # the smoothing interval's upper end covers the spectrum
+        assert 1.1 * L.lmax >= lam.max()
+
+
+def test_lanczos_is_exact_on_a_small_diagonal_matrix():
+    """With as many steps as distinct eigenvalues, the largest Ritz value is
+    the largest eigenvalue (here of diag(1..6) scaled by D = 2 I)."""
+    import scipy.sparse as sp
+
+    A = sp.diags(2.0 * np.arange(1.0, 7.0)).tocsr()
+    Dinv = np.full(6, 0.5)
+    est = mg.lanczos_lmax(A, Dinv, np.zeros(6, dtype=np.uint8), 6)
+    assert abs(est - 6.0) <= 1e-12
+
+
+@pytest.mark.parametrize("deg,family", [(2, "lagrange"), (2, "serendipity"), (3, "lagrange")])
+def test_chebyshev_cycle_is_symmetric(deg, family):
+    p, h = _cheb_case(deg=deg, family=family, levels=2 if deg == 2 else 3)
+    free = h.levels[0].mask == 0
+    rng = np.random.default_rng(8)
+    x = np.where(free, rng.normal(size=free.size), 0.0)
+    y = np.where(free, rng.normal(size=free.size), 0.0)
+    a, b = y @ mg.vcycle(h, x), x @ mg.vcycle(h, y)
+    assert abs(a - b) <= 1e-12 * max(abs(a), 1.0)
+
+
+@pytest.mark.parametrize("deg,family", [(2, "lagrange"), (2, "serendipity"), (3, "serendipity")])
+def test_chebyshev_pcg_converges_to_direct_solution_in_fewer_iterations(deg, family):
+    p = workloads.cantilever(8, 4, 4, degree=deg, n_mr=2 * deg, rmin=0.0, seed=1, mg_levels=2)
+    if family == "serendipity":
+        p = workloads.with_serendipity(p)
+    m = fe.Model(p)
+    rho = m.densities(p.x)
+    f = p.f[0].copy()
+    f[p.mask.astype(bool)] = 0.0
+    levels = 2 if deg == 2 else 3
+    ref = m.run(method="splu")["u"][0]
+    u_c, its_c, _ = mg.pcg(mg.Hierarchy(p, rho, levels, smoother="chebyshev"), f, rtol=1e-10)
+    u_j, its_j, _ = mg.pcg(mg.Hierarchy(p, rho, levels), f, rtol=1e-10)
+    assert np.linalg.norm(u_c - ref) <= 1e-7 * np.linalg.norm(ref)
+    assert its_c < its_j
