@@ -966,7 +966,8 @@ def run_elements(args):
     quadratic Lagrange (L2) and serendipity (S2), cubic Lagrange (L3) and
     serendipity (S3) elements.  Cold solves (u0 = 0) to 1e-8, CUDA events,
     L2 flushed between solves; unknowns, PCG iterations, time per solve and
-    solved unknowns per second, FP32X2 and FP64 preconditioners."""
+    solved unknowns per second: FP32X2 and FP64 preconditioners with damped
+    Jacobi, and at degree >= 2 an FP32 one with Chebyshev smoothing."""
     import torch
 
     import workloads
@@ -989,10 +990,13 @@ def run_elements(args):
         x = torch.tensor(p.x, device=dev)
         f = torch.tensor(p.f, device=dev)
         u = torch.zeros_like(f)
-        for plabel, prec in (("fp32x2", T.PREC_FP32X2), ("fp64", T.PREC_FP64)):
+        variants = [("fp32x2", T.PREC_FP32X2, {}), ("fp64", T.PREC_FP64, {})]
+        if k >= 2:  # Chebyshev smoothing (degree >= 2 hierarchies)
+            variants.insert(1, ("fp32_cheb", T.PREC_FP32, dict(smoother=T.SMOOTH_CHEBYSHEV, cheb_degree=2)))
+        for plabel, prec, extra in variants:
             d = T.make_desc(p.nx, p.ny, p.nz, degree=k, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin, nu=p.nu,
                             penal=p.penal, precision=prec, max_rhs=1,
-                            family=T.FAMILY_SERENDIPITY if fam == "serendipity" else T.FAMILY_LAGRANGE)
+                            family=T.FAMILY_SERENDIPITY if fam == "serendipity" else T.FAMILY_LAGRANGE, **extra)
             s = T.Solver(d, p.mask, stream)
             ms, its = [], []
             with torch.cuda.stream(stream):

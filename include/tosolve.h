@@ -130,6 +130,16 @@ typedef struct {
                           /*   by one V-cycle; the outer CG is flexible, its */
                           /*   residual, dot products and operator stay FP64 */
                           /*   (degree 2, FP32-vector precisions only)       */
+  int smoother;           /* 0: damped Jacobi (Sec. 7 intro; omega above);  */
+                          /*   1: Chebyshev on D^-1 A (degree 2 and 3, not  */
+                          /*   FP32X2): at each tosolve_set_densities a     */
+                          /*   few Lanczos steps estimate lambda_max of     */
+                          /*   every level's smoothing operator, and the    */
+                          /*   smoother is the Chebyshev iteration over     */
+                          /*   [0.3 b, b], b = 1.1 lambda_max (Saad, Alg.   */
+                          /*   12.1); omega is then ignored                 */
+  int cheb_degree;        /* Chebyshev steps before and after the coarse    */
+                          /*   correction, 1..4 (0: 2)                      */
 } tosolve_desc;
 
 typedef struct {
@@ -467,6 +477,12 @@ tosolve_status tosolve_level_dims(tosolve_t h, int level, int* dims);
 /* Copies the stacked subcell stiffness table of the finest level, m x d x d
  * FP64 (m = n_mr^3, d = 24, E = 1), into table_dev (Sec. 3.3). */
 tosolve_status tosolve_subcell_table(tosolve_t h, double* table_dev);
+
+/* Chebyshev smoothing: the Lanczos estimate of lambda_max(D^-1 A) of level
+ * l's smoothing operator from the last tosolve_set_densities, into
+ * *lmax_host (synchronises the handle's stream).  Errors: EINVAL (no
+ * Chebyshev smoother, level out of range or the coarsest level). */
+tosolve_status tosolve_smoother_lmax(tosolve_t h, int level, double* lmax_host);
 
 /* Copies the densities rho and SIMP weights w of the last set_densities
  * (density grid, FP64) into rho_dev / w_dev (either may be NULL). */

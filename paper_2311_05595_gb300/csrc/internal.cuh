@@ -85,6 +85,19 @@ struct DevState {
   double in_beta;     // inner flexible coefficient
 };
 
+// One Chebyshev smoothing step fused into an operator gather (mode 3):
+//   out = v + c1 dprev + c2 D^-1 (b - A v),  dout = out - v,
+// with c1 = coef[2 ci], c2 = coef[2 ci + 1] for ci >= 0, and c1 = 0, c2 = 1
+// for ci < 0 (the first step from a nonzero iterate: the level's D^-1 is
+// already divided by theta).  dprev null: the previous iterate was 0, so
+// dprev = v.  out may alias v and dout dprev (element-wise updates).
+struct ChebStep {
+  const void* dprev = nullptr;
+  void* dout = nullptr;
+  const void* coef = nullptr;  // the level's coefficients in the vector type
+  int ci = -1;
+};
+
 struct Level {
   int ex, ey, ez;   // elements per axis
   int Lx, Ly, Lz;   // node lattice
@@ -122,6 +135,13 @@ struct Level {
   float* S32 = nullptr;    // FP32 stencil (FP32 preconditioner levels)
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
+  // Chebyshev smoothing (degree >= 2 hierarchies): steps before and after
+  // the coarse correction (0: damped Jacobi), the step difference vector,
+  // and the coefficients (c1, c2 theta) of steps 2.. in FP64 and FP32
+  int cheb = 0;
+  void* d = nullptr;
+  double* cheb64 = nullptr;
+  float* cheb32 = nullptr;
   void* b = nullptr;  // V-cycle vectors in the preconditioner precision
   void* v = nullptr;
   void* r = nullptr;
@@ -261,7 +281,7 @@ cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cu
 // Node gather of Y fused with the V-cycle step: mode 0 b - y, 1 v + omega
 // D^-1 (b - y), 2 y; identity rows at fixed DOFs.
 void launch_tc2_gather(const Level& L0, const float* Y, const float* b, const float* v, const float* dinv,
-                       float omega, int mode, float* out, cudaStream_t st);
+                       float omega, int mode, float* out, cudaStream_t st, const ChebStep* cs = nullptr);
 
 // ---- launchers (k_solve.cu) ----------------------------------------------
 template <typename T>
@@ -292,6 +312,14 @@ struct InnerPcg {
 // level-0 preconditioner operator (tensor cores when tc.on, else the FP32
 // element matrices), each preconditioned by one V-cycle; b0 and v0 = omega
 // D^-1 b0 are set by the outer kernels.  Reductions in FP64, fixed order.
+// Chebyshev smoothing set-up: for every level with lv[l].cheb > 0, `steps`
+// Lanczos steps estimate lambda_max(D^-1 A) of its smoothing operator, the
+// step coefficients go to lv[l].cheb64 / cheb32 and the level's D^-1 (of the
+// vector type vt, FP64 or FP32) is divided by theta.  part: kMaxPart
+// doubles, cnt a zeroed counter, lz 64 doubles of scratch; lmax_out (device,
+// optional) receives each level's estimate.
+void launch_cheb_setup(int vt, Level* lv, int L, const TcOp& tc, int steps, double* part, unsigned* cnt,
+                       double* lz, double* lmax_out, cudaStream_t st);
 void launch_inner_pcg(Level* lv, int L, double omega, const double* Ainv, const TcOp& tc, const InnerPcg& in,
                       double* part_a, double* part_b, DevState* ds, unsigned* cnt, cudaStream_t st);
 void launch_smooth0(int vt, const Level& L0, double omega, cudaStream_t st);
@@ -356,7 +384,8 @@ void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t s
 // out = f(A_l v) in vector type vt: mode 0 b - Av, 1 v + omega D^-1 (b - Av),
 // 2 Av (identity rows at fixed DOFs).  Ke is FP64 for kVtF64, else FP32.
 void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b, const void* v,
-                  const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st);
+                  const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st,
+                  const ChebStep* cs = nullptr);
 // Mixed degree: f <- T^T f; u <- T u (slv: per lattice node, 1 = slaved).
 void launch_q2_fold(const Level& L, const uint8_t* slv, double* f, cudaStream_t st);
 void launch_q2_expand(const Level& L, const uint8_t* slv, double* u, cudaStream_t st);
@@ -471,6 +500,10 @@ struct tosolve_s {
   long ne2 = 0, ne1 = 0;
   double* tab64q1 = nullptr;   // trilinear subcell table (tensor cores on a mixed mesh)
   unsigned char* tcimg1 = nullptr;  // its shared-memory image
+  // Chebyshev smoothing: Lanczos scratch (64) and each level's estimate of
+  // lambda_max(D^-1 A) (mg_levels)
+  double* lz = nullptr;
+  double* lmax = nullptr;
   uint8_t* fix0 = nullptr;     // per DOF: the supports alone (level 0 mask adds slaved)
   // fixing variables (Sec. 6.1)
   float* ptab = nullptr;         // shape-function transfer table (27 x 125)

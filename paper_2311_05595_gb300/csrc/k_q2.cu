@@ -1107,7 +1107,7 @@ template <int K, typename T>
 __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, const T* __restrict__ Y,
                             const T* __restrict__ b, const T* __restrict__ v,
                             const op_t<T>* __restrict__ dinv, const uint8_t* __restrict__ mask,
-                            T omega, int mode, T* __restrict__ out) {
+                            T omega, int mode, T* __restrict__ out, ChebStep cs) {
   constexpr int kD = Deg<K>::D, NA = K + 1;
   const long nn = (long)Lx * Ly * Lz;
   for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
@@ -1134,9 +1134,23 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
     for (int c = 0; c < 3; ++c) {
       const long d = 3 * node + c;
       const T yc = mask[d] ? v[d] : y[c];
-      if (mode == 0) out[d] = b[d] - yc;
-      else if (mode == 1) out[d] = v[d] + omega * dinv[d] * (b[d] - yc);
-      else out[d] = yc;
+      if (mode == 0) {
+        out[d] = b[d] - yc;
+      } else if (mode == 1) {
+        out[d] = v[d] + omega * dinv[d] * (b[d] - yc);
+      } else if (mode == 3) {
+        if constexpr (std::is_same<T, float>::value || std::is_same<T, double>::value) {
+          const T* co = static_cast<const T*>(cs.coef);
+          const T c1 = cs.ci < 0 ? T(0) : co[2 * cs.ci], c2 = cs.ci < 0 ? T(1) : co[2 * cs.ci + 1];
+          const T vd = v[d];
+          const T dp = cs.dprev ? static_cast<const T*>(cs.dprev)[d] : vd;
+          const T o = vd + c1 * dp + c2 * dinv[d] * (b[d] - yc);
+          static_cast<T*>(cs.dout)[d] = o - vd;
+          out[d] = o;
+        }
+      } else {
+        out[d] = yc;
+      }
     }
   }
 }
@@ -1612,7 +1626,9 @@ void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t s
 // y = A_l v (element apply + gather) with the given mode; T is the vector
 // type (double, float, dfloat), the element matrices are op_t<T>.
 void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b, const void* v,
-                  const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st) {
+                  const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st,
+                  const ChebStep* cs) {
+  const ChebStep chs = cs ? *cs : ChebStep{};
   const long E = (long)L.ex * L.ey * L.ez;
   long ga = (long)sms * 16;
   if (ga > E) ga = E;
@@ -1633,11 +1649,11 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
       if (L.k == 3)
         k_q2_gather<3, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                               (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
-                                              (T*)out);
+                                              (T*)out, chs);
       else
         k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                               (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
-                                              (T*)out);
+                                              (T*)out, chs);
       return;
     }
     if (L.el2 != nullptr) {  // mixed level 0: triquadratic list, then the trilinear vertex blocks
@@ -1653,7 +1669,7 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
                                                 (const T*)v, (T*)Y, L.el1);
       k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
-                                            (T*)out);
+                                            (T*)out, chs);
       return;
     }
     if (L.k == 3) {
@@ -1661,13 +1677,13 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
                                                         (const T*)v, (T*)Y, nullptr);
       k_q2_gather<3, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
-                                            (T*)out);
+                                            (T*)out, chs);
     } else {
       k_q2_apply<2, T><<<(int)ga, Deg<2>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
                                                         (const T*)v, (T*)Y, nullptr);
       k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
-                                            (T*)out);
+                                            (T*)out, chs);
     }
   };
   if (vt == kVtF64) run(double());

@@ -857,6 +857,152 @@ const void* elem_op(const Level& L) {
   return std::is_same<T, double>::value ? (const void*)L.K64 : (const void*)L.K32;
 }
 
+// ---- Chebyshev smoothing: lambda_max(D^-1 A) by Lanczos at set-up --------
+// Lanczos on the symmetric D^-1/2 A D^-1/2, written in the unscaled vectors
+// p = D^-1/2 q (alpha_j = p_j^T A p_j, s = D^-1 A p_j - alpha_j p_j - beta_j
+// p_{j-1}, beta_{j+1} = (s^T D s)^1/2, p_{j+1} = s / beta_{j+1}), from the
+// Weyl vector frac(d phi) - 1/2 (0 at fixed DOFs) normalised in the D-norm.
+// The operator is the level's own smoothing operator in its vector type.
+// Every reduction is FP64 in a fixed order.  State in lz: alpha_j at j,
+// beta_j at kLzMax + j, then the D-norm, the estimate and theta.
+constexpr int kLzMax = 16;
+constexpr int kLzNrm = 2 * kLzMax, kLzLmax = kLzNrm + 1, kLzTheta = kLzNrm + 2;
+constexpr double kGolden = 0.6180339887498949;
+
+template <typename T>
+__global__ void k_lz_start(long n, const uint8_t* __restrict__ mask, const T* __restrict__ dinv, T* __restrict__ p,
+                           double* __restrict__ part, unsigned* cnt, double* __restrict__ lz) {
+  double s = 0.0;
+  DOF_LOOP(n) {
+    double x = (double)d * kGolden;
+    x = mask[d] ? 0.0 : x - floor(x) - 0.5;
+    const T xt = (T)x;
+    p[d] = xt;
+    s += (double)xt * (double)xt / (double)dinv[d];
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!last_block(cnt)) return;
+  const double tot = reduce_parts(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    lz[kLzNrm] = sqrt(tot);
+    *cnt = 0u;
+  }
+}
+
+template <typename T>
+__global__ void k_lz_scale(long n, T* __restrict__ p, const double* __restrict__ lz) {
+  const T inv = (T)(1.0 / lz[kLzNrm]);
+  DOF_LOOP(n) p[d] *= inv;
+}
+
+// alpha_j = p^T y (y = A p)
+template <typename T>
+__global__ void k_lz_alpha(long n, const T* __restrict__ p, const T* __restrict__ y, double* __restrict__ part,
+                           unsigned* cnt, double* __restrict__ lz, int j) {
+  double s = 0.0;
+  DOF_LOOP(n) s += (double)p[d] * (double)y[d];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!last_block(cnt)) return;
+  const double tot = reduce_parts(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    lz[j] = tot;
+    *cnt = 0u;
+  }
+}
+
+// q <- s = D^-1 y - alpha_j p - beta_j q (q holds p_{j-1}), beta_{j+1}
+template <typename T>
+__global__ void k_lz_next(long n, const T* __restrict__ p, const T* __restrict__ y, T* __restrict__ q,
+                          const T* __restrict__ dinv, double* __restrict__ part, unsigned* cnt,
+                          double* __restrict__ lz, int j) {
+  const T alpha = (T)lz[j], beta = j == 0 ? T(0) : (T)lz[kLzMax + j];
+  double s = 0.0;
+  DOF_LOOP(n) {
+    const T sv = dinv[d] * y[d] - alpha * p[d] - beta * q[d];
+    q[d] = sv;
+    s += (double)sv * (double)sv / (double)dinv[d];
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!last_block(cnt)) return;
+  const double tot = reduce_parts(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    lz[kLzMax + j + 1] = sqrt(tot);
+    *cnt = 0u;
+  }
+}
+
+// p_{j+1} = s / beta_{j+1}, and q takes p_j
+template <typename T>
+__global__ void k_lz_swap(long n, T* __restrict__ p, T* __restrict__ q, const double* __restrict__ lz, int j) {
+  const T inv = (T)(1.0 / lz[kLzMax + j + 1]);
+  DOF_LOOP(n) {
+    const T t = p[d];
+    p[d] = q[d] * inv;
+    q[d] = t;
+  }
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal a[0..k) and off-diagonal b[1..k) (Sturm sequence of the LDL^T
+// pivots).
+__device__ int sturm_below(const double* a, const double* b, int k, double x) {
+  int c = 0;
+  double q = a[0] - x;
+  for (int i = 0;; ++i) {
+    if (q == 0.0) q = -1e-300;
+    c += q < 0.0;
+    if (i + 1 == k) break;
+    q = a[i + 1] - x - b[i + 1] * b[i + 1] / q;
+  }
+  return c;
+}
+
+// The largest Ritz value by bisection on the Sturm count, then the
+// Chebyshev interval [0.3 hi, hi], hi = 1.1 lambda, and the coefficients of
+// steps 2..k (Saad, Algorithm 12.1 on D^-1 A): c1 = rho_i rho_{i-1} and
+// c2 = 2 rho_i / delta, stored as (c1, c2 theta) because the level's D^-1 is
+// divided by theta afterwards (the first step is then D^-1 r with weight 1).
+__global__ void k_lz_finish(int steps, int degree, double* __restrict__ lz, double* __restrict__ c64,
+                            float* __restrict__ c32) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double* a = lz;
+  const double* b = lz + kLzMax;  // b[i] couples i - 1 and i
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < steps; ++i) {
+    const double r = (i > 0 ? fabs(b[i]) : 0.0) + (i + 1 < steps ? fabs(b[i + 1]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * fmax(fabs(hi), 1.0); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_below(a, b, steps, mid) <= steps - 1) lo = mid;
+    else hi = mid;
+  }
+  const double lam = 0.5 * (lo + hi);
+  const double top = 1.1 * lam, bot = 0.3 * top;
+  const double theta = 0.5 * (top + bot), delta = 0.5 * (top - bot), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  for (int i = 1; i < degree; ++i) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    c64[2 * (i - 1)] = rn * rho;
+    c64[2 * (i - 1) + 1] = 2.0 * rn / delta * theta;
+    c32[2 * (i - 1)] = (float)(rn * rho);
+    c32[2 * (i - 1) + 1] = (float)(2.0 * rn / delta * theta);
+    rho = rn;
+  }
+  lz[kLzLmax] = lam;
+  lz[kLzTheta] = theta;
+}
+
+template <typename T>
+__global__ void k_lz_scale_dinv(long n, T* __restrict__ dinv, const double* __restrict__ lz) {
+  const T inv = (T)(1.0 / lz[kLzTheta]);
+  DOF_LOOP(n) dinv[d] *= inv;
+}
+
 // One V-cycle from level l down (Algorithm 1).  With dots (finest level
 // only) the last smoothing step also forms the PCG reduction when it is a
 // stencil kernel; returns whether it did.
@@ -875,18 +1021,46 @@ bool vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
   const LevelView<T> V = view<T>(F);
   const bool c_coarsest = (l + 1 == L - 1);
   const bool use_tc = tc.on && l == 0;
-  if constexpr (std::is_same<T, float>::value) {
+  // element-form levels: out = f(A v) in gather mode `mode` (the degree-2
+  // stacked contraction on tensor cores at level 0 when it is on)
+  auto elem_op_step = [&](int mode, void* out, const ChebStep* cs) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (use_tc && tc.deg >= 2) {
+        launch_tc2_apply(tc, F, (const float*)F.v, st);
+        launch_tc2_gather(F, tc.Y2, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, mode,
+                          (float*)out, st, cs);
+        return;
+      }
+    }
+    launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, mode, out, F.sms,
+                 st, cs);
+  };
+  const bool elem_form = F.k >= 2 && (!use_tc || tc.deg >= 2);
+  const void* coef = std::is_same<T, double>::value ? (const void*)F.cheb64 : (const void*)F.cheb32;
+  if (elem_form && F.cheb > 0) {
+    // Chebyshev: v holds the first step from 0 (D^-1 b / theta, formed with
+    // the coarse right-hand side); steps 2..k, then the residual
+    for (int i = 2; i <= F.cheb; ++i) {
+      ChebStep cs;
+      cs.dprev = i == 2 ? nullptr : F.d;
+      cs.dout = F.d;
+      cs.coef = coef;
+      cs.ci = i - 2;
+      elem_op_step(3, F.v, &cs);
+    }
+    elem_op_step(0, F.r, nullptr);
+  } else if constexpr (std::is_same<T, float>::value) {
     if (use_tc && tc.deg >= 2) {  // r = b - A v, A v from the degree-2 stacked contraction
-      launch_tc2_apply(tc, F, (const float*)F.v, st);
-      launch_tc2_gather(F, tc.Y2, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 0,
-                        (float*)F.r, st);
+      elem_op_step(0, F.r, nullptr);
     } else if (use_tc) {  // r = b - A v with A v from the tensor-core stacked contraction
       launch_tc_apply(F, tc.m, (const float*)F.v, tc.w32, tc.KT, tc.Ye, tc.err, tc.sms, st);
       launch_tc_gather(F, tc.Ye, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 0,
                        (float*)F.r, st);
     }
   }
-  if (F.k >= 2 && !use_tc)
+  if (elem_form && F.cheb > 0) {
+    // residual formed above
+  } else if (F.k >= 2 && !use_tc)
     launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, F.b, F.v, dinv_of<T>(F), (double)omega, 0, F.r,
                  F.sms, st);
   else if (!use_tc)
@@ -905,11 +1079,20 @@ bool vcycle_rec(Level* lv, int l, int L, T omega, const double* Ainv, const TcOp
   else
     k_vc_prolong<T><<<grid_nodes(F.nn), kRowThreads, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, F.mask,
                                                               (const T*)C.z, (T*)F.v);
+  if (elem_form && F.cheb > 0) {  // Chebyshev post-smoothing: k steps from the corrected v, the last into z
+    for (int i = 1; i <= F.cheb; ++i) {
+      ChebStep cs;
+      cs.dprev = i == 1 ? nullptr : F.d;
+      cs.dout = F.d;
+      cs.coef = coef;
+      cs.ci = i == 1 ? -1 : i - 2;
+      elem_op_step(3, i == F.cheb ? F.z : F.v, &cs);
+    }
+    return false;
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (use_tc && tc.deg >= 2) {  // z = v + omega D^-1 (b - A v)
-      launch_tc2_apply(tc, F, (const float*)F.v, st);
-      launch_tc2_gather(F, tc.Y2, (const float*)F.b, (const float*)F.v, F.dinv32, (float)omega, 1,
-                        (float*)F.z, st);
+      elem_op_step(1, F.z, nullptr);
       return false;
     }
     if (use_tc) {  // z = v + omega D^-1 (b - A v)
@@ -987,6 +1170,48 @@ void launch_inner_pcg(Level* lv, int L, double omega, const double* Ainv, const 
 
 void launch_set_params(DevState* ds, const double* params, cudaStream_t st) {
   k_set_params<<<1, 32, 0, st>>>(ds, params);
+}
+
+void launch_cheb_setup(int vt, Level* lv, int L, const TcOp& tc, int steps, double* part, unsigned* cnt,
+                       double* lz, double* lmax_out, cudaStream_t st) {
+  for (int l = 0; l + 1 < L; ++l) {
+    Level& F = lv[l];
+    if (F.cheb <= 0) continue;
+    auto run = [&](auto tag) {
+      using T = decltype(tag);
+      const long n = F.ndof;
+      int g = (int)((n + kRowThreads - 1) / kRowThreads);
+      if (g > kMaxPart) g = kMaxPart;
+      T* P = (T*)F.v;
+      T* Q = (T*)F.d;
+      T* Y = (T*)F.r;
+      T* dinv = const_cast<T*>(dinv_of<T>(F));
+      const bool use_tc = tc.on && l == 0 && tc.deg >= 2;
+      k_lz_start<T><<<g, kRowThreads, 0, st>>>(n, F.mask, dinv, P, part, cnt, lz);
+      k_lz_scale<T><<<g, kRowThreads, 0, st>>>(n, P, lz);
+      cudaMemsetAsync(Q, 0, (size_t)n * sizeof(T), st);
+      for (int j = 0; j < steps; ++j) {
+        if constexpr (std::is_same<T, float>::value) {
+          if (use_tc) {
+            launch_tc2_apply(tc, F, P, st);
+            launch_tc2_gather(F, tc.Y2, nullptr, P, F.dinv32, 0.f, 2, Y, st);
+          }
+        }
+        if (!use_tc)
+          launch_q2_op(vt_code<T>(), F, elem_op<T>(F), F.Y, nullptr, P, dinv, 0.0, 2, Y, F.sms, st);
+        k_lz_alpha<T><<<g, kRowThreads, 0, st>>>(n, P, Y, part, cnt, lz, j);
+        if (j + 1 < steps) {
+          k_lz_next<T><<<g, kRowThreads, 0, st>>>(n, P, Y, Q, dinv, part, cnt, lz, j);
+          k_lz_swap<T><<<g, kRowThreads, 0, st>>>(n, P, Q, lz, j);
+        }
+      }
+      k_lz_finish<<<1, 32, 0, st>>>(steps, F.cheb, lz, F.cheb64, F.cheb32);
+      if (lmax_out != nullptr) cudaMemcpyAsync(lmax_out + l, lz + kLzLmax, sizeof(double), cudaMemcpyDeviceToDevice, st);
+      k_lz_scale_dinv<T><<<g, kRowThreads, 0, st>>>(n, dinv, lz);
+    };
+    if (vt == kVtF64) run(double());
+    else run(float());
+  }
 }
 
 void launch_smooth0(int vt, const Level& L0, double omega, cudaStream_t st) {

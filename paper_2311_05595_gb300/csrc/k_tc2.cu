@@ -713,7 +713,7 @@ __global__ void k_tc2_image(int mode, int D, int m, int mp, int nch, int kp, int
 __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, const float* __restrict__ Y,
                              const float* __restrict__ b, const float* __restrict__ v,
                              const float* __restrict__ dinv, const uint8_t* __restrict__ mask, float omega,
-                             int mode, float* __restrict__ out) {
+                             int mode, float* __restrict__ out, ChebStep cs) {
   const long nn = (long)Lx * Ly * Lz;
   const long Ey = (long)ex * ey * ez;
   for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn; node += (long)gridDim.x * blockDim.x) {
@@ -746,9 +746,21 @@ __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, con
     for (int c = 0; c < 3; ++c) {
       const long d = 3 * node + c;
       const float yc = mask[d] ? v[d] : y[c];
-      if (mode == 0) out[d] = b[d] - yc;
-      else if (mode == 1) out[d] = v[d] + omega * dinv[d] * (b[d] - yc);
-      else out[d] = yc;
+      if (mode == 0) {
+        out[d] = b[d] - yc;
+      } else if (mode == 1) {
+        out[d] = v[d] + omega * dinv[d] * (b[d] - yc);
+      } else if (mode == 3) {  // a Chebyshev step (ChebStep)
+        const float* co = static_cast<const float*>(cs.coef);
+        const float c1 = cs.ci < 0 ? 0.f : co[2 * cs.ci], c2 = cs.ci < 0 ? 1.f : co[2 * cs.ci + 1];
+        const float vd = v[d];
+        const float dp = cs.dprev ? static_cast<const float*>(cs.dprev)[d] : vd;
+        const float o = vd + c1 * dp + c2 * dinv[d] * (b[d] - yc);
+        static_cast<float*>(cs.dout)[d] = o - vd;
+        out[d] = o;
+      } else {
+        out[d] = yc;
+      }
     }
   }
 }
@@ -922,11 +934,11 @@ size_t tc2_pack_bytes(int mode, long E) {
 }
 
 void launch_tc2_gather(const Level& L0, const float* Y, const float* b, const float* v, const float* dinv,
-                       float omega, int mode, float* out, cudaStream_t st) {
+                       float omega, int mode, float* out, cudaStream_t st, const ChebStep* cs) {
   long g = (L0.nn + 255) / 256;
   if (g > 8192) g = 8192;
-  k_tc2_gather<<<(int)g, 256, 0, st>>>(L0.Lx, L0.Ly, L0.Lz, L0.ex, L0.ey, L0.ez, Y, b,
-                                                                 v, dinv, L0.mask, omega, mode, out);
+  k_tc2_gather<<<(int)g, 256, 0, st>>>(L0.Lx, L0.Ly, L0.Lz, L0.ex, L0.ey, L0.ez, Y, b, v, dinv, L0.mask, omega,
+                                       mode, out, cs ? *cs : ChebStep{});
 }
 
 }  // namespace tos

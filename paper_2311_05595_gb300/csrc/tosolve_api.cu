@@ -154,6 +154,12 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     *why = "inner FP32 iterations need degree 2, an FP32-vector precision and a V-cycle (mg_levels != 1)";
     return TOSOLVE_EINVAL;
   }
+  if (d.smoother != 0 && d.smoother != 1) { *why = "smoother is 0 (Jacobi) or 1 (Chebyshev)"; return TOSOLVE_EINVAL; }
+  if (d.smoother == 1 && (d.degree < 2 || d.precision == TOSOLVE_PREC_FP32X2)) {
+    *why = "Chebyshev smoothing needs degree 2 or 3 and a precision other than FP32X2";
+    return TOSOLVE_EINVAL;
+  }
+  if (d.cheb_degree < 0 || d.cheb_degree > 4) { *why = "cheb_degree must be in 0..4"; return TOSOLVE_EINVAL; }
   int L = d.mg_levels;
   if (L == 0) {
     L = d.degree == 3 ? 2 : 1;
@@ -243,6 +249,8 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     B += E0 * (P->m + 24) * 4 + (size_t)P->m * 576 * 4 + P->lv[0].ndof * 4;
   }
   if (d.inner_its > 0) B += 4 * (size_t)P->lv[0].ndof * 4;  // inner PCG vectors
+  if (d.smoother == 1)  // step difference vectors, coefficients, Lanczos scratch
+    for (int l = 0; l + 1 < L; ++l) B += (size_t)P->lv[l].ndof * 8 + 16 * 12 + 64 * 8;
   if (tc2) {  // weights, element results and the table image of the tensor-core level
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
     B += E0 * (P->m + tc2_result_stride() + 1) * 4 + tc2_pack_bytes(tc2_mode_of(d.precision), (long)E0) +
@@ -283,6 +291,7 @@ void free_all(tosolve_s* h) {
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->tcimg); F(h->Y2); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->inner.e); F(h->inner.ri); F(h->inner.pi); F(h->inner.qi);
   F(h->el2); F(h->sl2); F(h->el1); F(h->tab64q1); F(h->tcimg1); F(h->tcpack); F(h->tcscale);
+  F(h->lz); F(h->lmax);
   F(h->Ad); F(h->Wp); F(h->Vp); F(h->Pg); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
   F(h->cnt);
@@ -397,6 +406,8 @@ tosolve_status build_graph(tosolve_s* h) {
   return TOSOLVE_OK;
 }
 
+constexpr int kChebLanczos = 8;  // Lanczos steps of the lambda_max estimate
+
 tosolve_status set_err(tosolve_t h, tosolve_status s, const char* msg) {
   if (h) h->err = msg;
   g_err = msg;
@@ -455,6 +466,12 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   // serendipity degree 2 5.3, degree 3 5.0; so 0.4 for cubic Lagrange and
   // 0.3 for serendipity (about 1.6 / lambda_max)
   if (h->d.omega == 0.0) h->d.omega = h->d.family == 1 ? 0.3 : (h->d.degree == 3 ? 0.4 : 0.5);
+  // Chebyshev: each level's D^-1 is divided by theta at set-up, so the first
+  // step of every smoothing sweep is D^-1 r with weight 1
+  if (h->d.smoother == 1) {
+    h->d.omega = 1.0;
+    if (h->d.cheb_degree == 0) h->d.cheb_degree = 2;
+  }
   if (h->d.cycle_gamma == 0) h->d.cycle_gamma = 1;
   if (h->d.max_rhs == 0) h->d.max_rhs = 1;
   h->d.d_mr = P.dm;
@@ -613,12 +630,18 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       }
     }
     const size_t tsz = vt_of(h) == kVtF32 ? 4 : 8;
-    void** vecs[4] = {&L.b, &L.v, &L.r, &L.z};
-    for (void** pv : vecs) {
+    void** vecs[5] = {&L.b, &L.v, &L.r, &L.z, &L.d};
+    const int nv = (h->d.smoother == 1 && l + 1 < P.L) ? 5 : 4;
+    for (int q = 0; q < nv; ++q) {
       char* p = nullptr;
       CKC(dalloc(h, &p, v.ndof * tsz));
       CKC(cudaMemsetAsync(p, 0, v.ndof * tsz, st));
-      *pv = p;
+      *vecs[q] = p;
+    }
+    if (nv == 5) {  // Chebyshev coefficients of steps 2..4
+      L.cheb = h->d.cheb_degree;
+      CKC(dalloc(h, &L.cheb64, 8));
+      CKC(dalloc(h, &L.cheb32, 8));
     }
     if (l + 1 < P.L && L.k == 3) {
       // degree 3 -> 2 on the same elements: a quadratic DOF is fixed iff
@@ -918,6 +941,11 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   CKC(dalloc(h, &h->hf, nd * h->hrhs));
   CKC(dalloc(h, &h->hu, nd * h->hrhs));
   CKC(dalloc(h, &h->hg, P.ndes));
+  if (h->d.smoother == 1) {
+    CKC(dalloc(h, &h->lz, 64));
+    CKC(dalloc(h, &h->lmax, P.L));
+    CKC(cudaMemsetAsync(h->lmax, 0, P.L * sizeof(double), st));
+  }
   CKC(cudaEventCreate(&h->ev0));
   CKC(cudaEventCreate(&h->ev1));
   CKC(cudaStreamSynchronize(st));
@@ -1019,6 +1047,8 @@ static tosolve_status refresh(tosolve_t h) {
       CK(cudaEventRecord(h->evj, h->st2));
       CK(cudaStreamWaitEvent(st, h->evj, 0));
     }
+    if (d.smoother == 1)  // lambda_max of every smoothing operator, then the Chebyshev coefficients
+      launch_cheb_setup(vt_of(h), h->lv, L, h->tc, kChebLanczos, h->part, h->cnt, h->lz, h->lmax, st);
     CK(cudaGetLastError());
     return TOSOLVE_OK;
   }
@@ -1525,6 +1555,15 @@ tosolve_status tosolve_tc_stage(tosolve_t h, int part, int stages, const double*
     launch_cast(false, (size_t)L0.ndof, x_dev, L0.v, true, h->st);
   }
   CK(launch_tc2_apply(h->tc, L0, (const float*)L0.v, h->st, part, stages));
+  return TOSOLVE_OK;
+}
+
+tosolve_status tosolve_smoother_lmax(tosolve_t h, int level, double* lmax_host) {
+  if (h == nullptr || lmax_host == nullptr) return set_err(h, TOSOLVE_EINVAL, "NULL argument");
+  if (h->d.smoother != 1) return set_err(h, TOSOLVE_EINVAL, "the handle smooths with damped Jacobi");
+  if (level < 0 || level + 1 >= h->L) return set_err(h, TOSOLVE_EINVAL, "level must be below the coarsest");
+  CK(cudaMemcpyAsync(lmax_host, h->lmax + level, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
   return TOSOLVE_OK;
 }
 

@@ -18,6 +18,7 @@ _LIB_PATH = os.path.join(_HERE, "libtosolve.so")
 
 OK, EINVAL, ENOMEM, ENOTCONV, EBREAKDOWN, ECUDA = range(6)
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_FP32X2, PREC_BF16, PREC_BF16X3, PREC_F16X3 = 0, 1, 2, 3, 4, 5, 6
+SMOOTH_JACOBI, SMOOTH_CHEBYSHEV = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "EBREAKDOWN", 5: "ECUDA"}
 
 
@@ -30,6 +31,7 @@ class tosolve_desc(C.Structure):
         ("mg_levels", C.c_int), ("precision", C.c_int),
         ("omega", C.c_double), ("cycle_gamma", C.c_int), ("max_rhs", C.c_int),
         ("family", C.c_int), ("prolongation", C.c_int), ("inner_its", C.c_int),
+        ("smoother", C.c_int), ("cheb_degree", C.c_int),
     ]
 
 
@@ -87,6 +89,7 @@ def _load():
         "tosolve_apply": ([vp, i, i, vp, vp], i),
         "tosolve_precondition": ([vp, vp, vp], i),
         "tosolve_tc_stage": ([vp, i, i, vp], i),
+        "tosolve_smoother_lmax": ([vp, i, vp], i),
         "tosolve_batch_create": ([P(vp), i, P(i), P(vp), P(vp), P(vp)], i),
         "tosolve_batch_solve": ([vp, d, i, vp], i),
         "tosolve_batch_destroy": ([vp], None),
@@ -144,9 +147,11 @@ FAMILY_LAGRANGE, FAMILY_SERENDIPITY = 0, 1
 
 def make_desc(nx, ny, nz, *, degree=1, n_mr=1, d_mr=None, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0,
               rmin=0.0, mg_levels=0, precision=PREC_FP64, omega=0.0, cycle_gamma=1,
-              max_rhs=1, family=FAMILY_LAGRANGE, prolongation=0, inner_its=0) -> tosolve_desc:
+              max_rhs=1, family=FAMILY_LAGRANGE, prolongation=0, inner_its=0, smoother=SMOOTH_JACOBI,
+              cheb_degree=0) -> tosolve_desc:
     return tosolve_desc(nx, ny, nz, degree, n_mr, d_mr or n_mr, E0, Emin, nu, penal, rmin, mg_levels,
-                        precision, omega, cycle_gamma, max_rhs, family, prolongation, inner_its)
+                        precision, omega, cycle_gamma, max_rhs, family, prolongation, inner_its, smoother,
+                        cheb_degree)
 
 
 # ---- the C ABI, same names ----------------------------------------------------
@@ -401,6 +406,12 @@ def tosolve_apply(h, level: int, precision: int, x_dev, y_dev) -> None:
 def tosolve_tc_stage(h, part: int, stages: int, x_dev=None) -> None:
     _check(h, _lib.tosolve_tc_stage(h, part, stages, _ptr(x_dev)),
            "tosolve_tc_stage")
+
+
+def tosolve_smoother_lmax(h, level: int) -> float:
+    v = C.c_double(0.0)
+    _check(h, _lib.tosolve_smoother_lmax(h, level, C.byref(v)), "tosolve_smoother_lmax")
+    return v.value
 
 
 def tosolve_precondition(h, b_dev, z_dev) -> None:

@@ -14,18 +14,19 @@ def lib():
     return T
 
 
-def desc_for(T, p, precision, levels=None, max_rhs=None):
+def desc_for(T, p, precision, levels=None, max_rhs=None, **extra):
+    """extra: further descriptor fields (smoother, cheb_degree, inner_its)."""
     return T.make_desc(p.nx, p.ny, p.nz, degree=p.degree, n_mr=p.n_mr, d_mr=getattr(p, "d_mr", None),
                        E0=p.E0, Emin=p.Emin, nu=p.nu,
                        penal=p.penal, rmin=p.rmin, mg_levels=levels or p.mg_levels,
                        precision=precision, max_rhs=max_rhs or p.nrhs,
-                       family=1 if getattr(p, "family", "lagrange") == "serendipity" else 0)
+                       family=1 if getattr(p, "family", "lagrange") == "serendipity" else 0, **extra)
 
 
 class Run:
     """A problem set up on the GPU: handle, stream, device copies of x and f."""
 
-    def __init__(self, p, precision, levels=None, max_rhs=None):
+    def __init__(self, p, precision, levels=None, max_rhs=None, **extra):
         import torch
 
         self.T = T = lib()
@@ -33,7 +34,7 @@ class Run:
         self.p = p
         self.dev = torch.device("cuda:0")
         self.stream = torch.cuda.Stream()
-        self.solver = T.Solver(desc_for(T, p, precision, levels, max_rhs), p.mask, self.stream,
+        self.solver = T.Solver(desc_for(T, p, precision, levels, max_rhs, **extra), p.mask, self.stream,
                                elem_q1=getattr(p, "elem_q1", None))
         self.h = self.solver.h
         self.x = torch.tensor(p.x, device=self.dev)
