@@ -267,16 +267,34 @@ DEFAULT_VARIANTS = {"bridge_mixed": "f16x3+i16,bf16x3+i16,bf16+i8,fp32",
 
 def parse_variant(label: str) -> tuple[str, int]:
     """'f16x3+i16' -> ('f16x3', 16): the preconditioner's precision and the
-    inner FP32 PCG iterations per outer FP64 iteration (0: one V-cycle)."""
-    name, sep, inner = label.partition("+i")
-    if name not in PREC_NAMES or (sep and not inner.isdigit()):
+    inner FP32 PCG iterations per outer FP64 iteration (0: one V-cycle).  A
+    further '+cK' selects Chebyshev smoothing of degree K (cheb_of)."""
+    name, *mods = label.split("+")
+    inner = 0
+    for m in mods:
+        if len(m) >= 2 and m[0] in "ic" and m[1:].isdigit():
+            if m[0] == "i":
+                inner = int(m[1:])
+        else:
+            raise ValueError(f"bad variant {label!r}")
+    if name not in PREC_NAMES or not mods and "+" in label:
         raise ValueError(f"bad variant {label!r}")
-    return name, int(inner or 0)
+    return name, inner
+
+
+def cheb_of(label: str) -> int:
+    """Chebyshev degree of a variant label ('+cK'), 0 for damped Jacobi."""
+    for m in label.split("+")[1:]:
+        if m[0] == "c":
+            return int(m[1:])
+    return 0
 
 
 def variant_ok(label: str, p) -> bool:
     """Whether the library offers this variant on problem p."""
     name, inner = parse_variant(label)
+    if cheb_of(label) and (p.degree < 2 or name == "fp32x2" or not 1 <= cheb_of(label) <= 4):
+        return False
     if name == "tf32":
         return p.degree == 1 and p.n_mr <= 2 or p.degree == 2 and p.n_mr <= 3
     if name in TC_PRECS:
@@ -370,9 +388,11 @@ class Workload:
     def make(self, label: str):
         T, p = self.ctx.T, self.p
         name, inner = parse_variant(label)
+        ck = cheb_of(label)
         d = T.make_desc(p.nx, p.ny, p.nz, degree=p.degree, n_mr=p.n_mr, rmin=p.rmin, Emin=p.Emin,
                         nu=p.nu, penal=p.penal, mg_levels=self.spec["levels"],
-                        precision=getattr(T, PREC_NAMES[name]), inner_its=inner)
+                        precision=getattr(T, PREC_NAMES[name]), inner_its=inner,
+                        smoother=1 if ck else 0, cheb_degree=ck)
         return T.Solver(d, p.mask, self.ctx.stream, elem_q1=p.elem_q1)
 
     def step(self, s):
@@ -762,7 +782,10 @@ def run_batch(args):
     """64 uneven Q1 instances (nx = 32 * 2^U(0,2) rounded to 16, ny = nz =
     nx/2, 1-3 edge load cases each, x ~ U[0.01, 1]) solved from u0 = 0 by
     one batched graph launch; also the same instances solved one handle at
-    a time, and the batch in FP64.  Prints one JSON line."""
+    a time, the batch in FP64, and the batch with the preconditioner
+    variant of each mesh-shape class chosen by the autotuner
+    (tosolve_tune / tosolve_tune_pick).  Prints one JSON line."""
+    import numpy as np
     import torch
 
     import workloads
@@ -779,11 +802,15 @@ def run_batch(args):
     fs = [torch.tensor(p.f, device=dev) for p in probs]
     us = [torch.zeros_like(f) for f in fs]
 
+    def desc(p, precision):
+        return T.make_desc(p.nx, p.ny, p.nz, Emin=p.Emin, nu=p.nu, penal=p.penal, precision=precision,
+                           max_rhs=p.nrhs)
+
     def build(precision):
+        """precision: one for all instances, or a list (one per instance)."""
         sol = []
-        for p, x in zip(probs, xs):
-            d = T.make_desc(p.nx, p.ny, p.nz, Emin=p.Emin, nu=p.nu, penal=p.penal,
-                            precision=precision, max_rhs=p.nrhs)
+        for i, (p, x) in enumerate(zip(probs, xs)):
+            d = desc(p, precision[i] if isinstance(precision, list) else precision)
             s = T.Solver(d, p.mask, stream)
             T.tosolve_set_densities(s.h, x)
             sol.append(s)
@@ -843,6 +870,32 @@ def run_batch(args):
         T.tosolve_batch_destroy(b)
         for s in sol:
             s.close()
+    # autotuning: per mesh-shape class, time the candidate variants on its
+    # first instance and let tosolve_tune_pick choose (5 % minimum gain over
+    # the default, FP32X2)
+    cands = [("fp32x2", T.PREC_FP32X2), ("fp32", T.PREC_FP32), ("tf32", T.PREC_TF32)]
+    classes = {}
+    for i, p in enumerate(probs):
+        classes.setdefault((p.nx, p.ny, p.nz), []).append(i)
+    t0 = time.perf_counter()
+    tms = []
+    with torch.cuda.stream(stream):
+        for shape, idx in classes.items():
+            p = probs[idx[0]]
+            tms.append(T.tosolve_tune([desc(p, c[1]) for c in cands], p.mask, xs[idx[0]], fs[idx[0]], p.nrhs,
+                                      rtol, maxit, 3, stream))
+    tune_s = time.perf_counter() - t0
+    choice = T.tosolve_tune_pick(np.array(tms), 0.05)
+    per_inst = [None] * len(probs)
+    for (shape, idx), c in zip(classes.items(), choice):
+        for i in idx:
+            per_inst[i] = cands[max(int(c), 0)][1]
+    sol, b = build(per_inst)
+    ms, its = time_batch(b)
+    res["tuned"] = dict(ms=ms, its=its)
+    T.tosolve_batch_destroy(b)
+    for s in sol:
+        s.close()
     clocks = sampler.stop()
     med = {k: statistics.median(v["ms"]) for k, v in res.items()}
     best = min(("fp32x2", "fp32"), key=lambda k: med[k])
@@ -868,6 +921,14 @@ def run_batch(args):
         "pcg_iterations_total": {k: statistics.median(res[k]["its"])
                                  for k in ("fp32x2", "fp32", "fp64")},
         "device_gib": mem,
+        "tuned": {"value": dofs / (med["tuned"] * 1e-3), "ms": med["tuned"],
+                  "gain_over_fixed_fp32x2": med["fp32x2"] / med["tuned"],
+                  "tuning_s": tune_s, "candidates": [c[0] for c in cands], "min_gain": 0.05,
+                  "choice": {f"{k[0]}x{k[1]}x{k[2]}": cands[max(int(c), 0)][0]
+                             for k, c in zip(classes, choice)},
+                  "class_median_ms": {f"{k[0]}x{k[1]}x{k[2]}": [round(float(np.median(t[j])), 3)
+                                                                  for j in range(len(cands))]
+                                      for k, t in zip(classes, tms)}},
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -1186,7 +1247,8 @@ def main():
     ap.add_argument("--variants", default=None,
                     help="mixed-precision variants timed beside FP64, a comma list of "
                          "fp32, tf32, fp32x2, bf16, bf16x3, f16x3, each optionally +iN "
-                         "(N inner FP32 PCG iterations, degree 2)")
+                         "(N inner FP32 PCG iterations, degree 2) and +cK (Chebyshev "
+                         "smoothing of degree K, degree 2)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["bridge_mixed", "cantilever", "bridge_q2", "batch64", "serve", "ibeam_fix",
                              "elements"],

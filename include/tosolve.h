@@ -346,6 +346,36 @@ tosolve_status tosolve_batch_solve(tosolve_batch_t b, double rtol, int maxit, to
 /* Frees the batch (not the handles).  NULL is accepted. */
 void tosolve_batch_destroy(tosolve_batch_t b);
 
+/* ---- Autotuning (the batching pattern's variant choice) ---------------- */
+
+/* Times candidate descriptors of one instance class.  For each candidate c
+ * a handle is created on cuda_stream (mask_host and elem_q1_host as in
+ * tosolve_create / tosolve_create_mixed; elem_q1_host may be NULL), its
+ * densities are set from x_dev, one untimed solve runs from u = 0, then
+ * `reps` timed solves from u = 0 of the nrhs load cases f_dev (layout as
+ * in tosolve_solve) to rtol; ms_out[c * reps + r] receives the device time
+ * of solve r (info.ms).  A candidate that cannot be created or does not
+ * reach rtol records +infinity; the others still run.  The handles and the
+ * solution buffer are freed before return.  Synchronises; allocates.
+ * Errors: EINVAL (a NULL pointer, ncand or reps outside 1..64, nrhs < 1),
+ * ECUDA. */
+tosolve_status tosolve_tune(const tosolve_desc* cand, int ncand, const uint8_t* mask_host,
+                            const uint8_t* elem_q1_host, const double* x_dev, const double* f_dev,
+                            int nrhs, double rtol, int maxit, int reps, void* cuda_stream,
+                            double* ms_out);
+
+/* The choice from timings (host only; touches no device).
+ * ms[(k * ncand + c) * reps + r] is repeat r of candidate c in class k.
+ * Per class and candidate the median of the finite repeats is taken (it is
+ * infinite when fewer than half are finite); the fastest candidate wins,
+ * ties to the lower index, but candidate 0, the default, is kept unless the
+ * winner is faster by more than the fraction min_gain of its time
+ * (0 <= min_gain < 1).  choice[k] = -1 when no candidate of class k has a
+ * finite median.  Errors: EINVAL (NULL, sizes outside 1..4096, 1..64,
+ * 1..64, min_gain outside [0, 1)). */
+tosolve_status tosolve_tune_pick(const double* ms, int nclass, int ncand, int reps, double min_gain,
+                                 int* choice);
+
 /* Device memory of handles and servers comes from one stream-ordered pool
  * per device.  Memory freed by tosolve_destroy (or a server eviction) stays
  * reserved in that pool for the next build; this returns the unused part

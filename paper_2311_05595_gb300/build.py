@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtosolve.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["k_setup.cu", "k_solve.cu", "k_grad.cu", "k_tc.cu", "k_tc2.cu", "k_noalloc.cu", "k_q2.cu", "k_fix.cu", "k_thresh.cu", "tosolve_api.cu", "tosolve_server.cpp", "pool.cpp"]
+UNITS = ["k_setup.cu", "k_solve.cu", "k_grad.cu", "k_tc.cu", "k_tc2.cu", "k_noalloc.cu", "k_q2.cu", "k_fix.cu", "k_thresh.cu", "tosolve_api.cu", "tosolve_server.cpp", "pool.cpp", "tune.cpp"]
 
 
 def _nvcc() -> str:

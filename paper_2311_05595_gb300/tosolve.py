@@ -90,6 +90,8 @@ def _load():
         "tosolve_precondition": ([vp, vp, vp], i),
         "tosolve_tc_stage": ([vp, i, i, vp], i),
         "tosolve_smoother_lmax": ([vp, i, vp], i),
+        "tosolve_tune": ([vp, i, vp, vp, vp, vp, i, C.c_double, i, i, vp, vp], i),
+        "tosolve_tune_pick": ([vp, i, i, i, C.c_double, vp], i),
         "tosolve_batch_create": ([P(vp), i, P(i), P(vp), P(vp), P(vp)], i),
         "tosolve_batch_solve": ([vp, d, i, vp], i),
         "tosolve_batch_destroy": ([vp], None),
@@ -412,6 +414,30 @@ def tosolve_smoother_lmax(h, level: int) -> float:
     v = C.c_double(0.0)
     _check(h, _lib.tosolve_smoother_lmax(h, level, C.byref(v)), "tosolve_smoother_lmax")
     return v.value
+
+
+def tosolve_tune(cands, mask: np.ndarray, x_dev, f_dev, nrhs: int, rtol: float, maxit: int, reps: int,
+                 stream=None, elem_q1=None) -> np.ndarray:
+    """Times each candidate descriptor (a list of tosolve_desc) on one
+    instance; returns ms[ncand, reps] (+inf where a candidate failed)."""
+    n = len(cands)
+    arr = (tosolve_desc * n)(*cands)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    eq = None if elem_q1 is None else np.ascontiguousarray(elem_q1, dtype=np.uint8)
+    out = np.zeros(n * reps)
+    st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(None, _lib.tosolve_tune(arr, n, _ptr(mask), _ptr(eq), _ptr(x_dev), _ptr(f_dev), nrhs, rtol, maxit,
+                                   reps, st, _ptr(out)), "tosolve_tune")
+    return out.reshape(n, reps)
+
+
+def tosolve_tune_pick(ms: np.ndarray, min_gain: float) -> np.ndarray:
+    """ms[nclass, ncand, reps] -> the chosen candidate per class (-1: none)."""
+    ms = np.ascontiguousarray(ms, dtype=np.float64)
+    k, c, r = ms.shape
+    out = np.zeros(k, dtype=np.int32)
+    _check(None, _lib.tosolve_tune_pick(_ptr(ms), k, c, r, min_gain, _ptr(out)), "tosolve_tune_pick")
+    return out
 
 
 def tosolve_precondition(h, b_dev, z_dev) -> None:

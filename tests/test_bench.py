@@ -38,7 +38,9 @@ def test_variant_labels():
     assert bench.parse_variant("f16x3+i16") == ("f16x3", 16)
     assert bench.parse_variant("fp32") == ("fp32", 0)
     assert bench.parse_variant("bf16+i8") == ("bf16", 8)
-    for bad in ("f16", "fp32+i", "fp32+ix", "int8"):
+    assert bench.parse_variant("f16x3+i16+c2") == ("f16x3", 16) and bench.cheb_of("f16x3+i16+c2") == 2
+    assert bench.cheb_of("fp32+i4") == 0
+    for bad in ("f16", "fp32+i", "fp32+ix", "int8", "fp32+", "fp32+x2"):
         with pytest.raises(ValueError):
             bench.parse_variant(bad)
     for wl, text in bench.DEFAULT_VARIANTS.items():
@@ -56,6 +58,8 @@ def test_variants_offered_per_problem():
         for v in ("f16x3+i16", "bf16x3", "bf16+i8", "tf32", "fp32+i4", "fp32"):
             assert bench.variant_ok(v, p), v
         assert not bench.variant_ok("fp32x2+i4", p)
+        assert bench.variant_ok("f16x3+i16+c2", p) and not bench.variant_ok("fp32x2+c2", p)
+    assert not bench.variant_ok("fp32+c2", q1)
     # the default workload's variants are all offered on it
     p = bench.problem(bench.SPECS[bench.DEFAULT_WORKLOAD], sample=True)
     assert all(bench.variant_ok(v, p) for v in bench.DEFAULT_VARIANTS[bench.DEFAULT_WORKLOAD].split(","))

@@ -102,3 +102,26 @@ def test_batch_new_densities_zero_load_and_errors():
         T.tosolve_batch_destroy(b)
         for R in runs:
             R.close()
+
+
+def test_tune_times_candidates_and_skips_those_not_offered():
+    """tosolve_tune on a small cantilever: FP32X2 and FP32 candidates get
+    finite, positive solve times; a candidate the library does not offer
+    (Chebyshev smoothing at degree 1) records +inf; the pick is one of the
+    finite ones."""
+    import torch
+
+    from tests.gpu_helpers import desc_for, lib
+
+    T = lib()
+    p = workloads.cantilever(16, 8, 8, seed=4)
+    dev = torch.device("cuda:0")
+    x = torch.tensor(p.x, device=dev)
+    f = torch.tensor(np.asarray(p.f), device=dev)
+    cands = [desc_for(T, p, 3), desc_for(T, p, 1), desc_for(T, p, 1, smoother=1)]
+    ms = T.tosolve_tune(cands, p.mask, x, f, p.nrhs, 1e-8, 500, 3)
+    assert ms.shape == (3, 3)
+    assert np.all(np.isfinite(ms[:2])) and np.all(ms[:2] > 0)
+    assert np.all(np.isinf(ms[2]))
+    c = T.tosolve_tune_pick(ms[None], 0.05)
+    assert c[0] in (0, 1)
