@@ -126,6 +126,9 @@ struct Level {
   const uint32_t* sl2 = nullptr;
   const int* el1 = nullptr;
   long ne1 = 0;
+  const uint8_t* slv = nullptr;  // per lattice node, 1 = slaved (mixed level 0 on tensor cores)
+  float* yraw = nullptr;         // its raw assembled products before the fold (ndof)
+  const uint32_t* vnb = nullptr; // per vertex of the lattice, its slaved neighbours (27-bit)
   uint8_t* mask = nullptr;
   int* tl = nullptr;    // tile order in force (LevelView::tl), or null: index order
   int* tcnt = nullptr;  // number of tiles with a free DOF (device), with tl
@@ -498,8 +501,10 @@ struct tosolve_s {
   uint32_t* sl2 = nullptr;     // their slaved local nodes (bit a = local node a)
   int* el1 = nullptr;          // trilinear elements (ascending)
   long ne2 = 0, ne1 = 0;
-  double* tab64q1 = nullptr;   // trilinear subcell table (tensor cores on a mixed mesh)
+  double* tab64q1 = nullptr;   // trilinear subcell table of a mixed mesh
   unsigned char* tcimg1 = nullptr;  // its shared-memory image
+  float* tcyraw = nullptr;          // raw assembled products before the slaved fold
+  uint32_t* tcvnb = nullptr;        // per lattice vertex, its slaved neighbours (bit (dx+1)+3(dy+1)+9(dz+1))
   // Chebyshev smoothing: Lanczos scratch (64) and each level's estimate of
   // lambda_max(D^-1 A) (mg_levels)
   double* lz = nullptr;

@@ -45,7 +45,10 @@
 //              accumulators and commits their completion to mbarriers;
 //   warps 2-5  epilogue: read each 32-column group of the accumulator
 //              (tcgen05.ld), weighted sum over its subcells, store the
-//              output DOF; mixed meshes fold slaved nodes afterwards.
+//              output DOF.
+// Every CTA walks the table chunks in its own rotated order (the chunks'
+// outputs are independent), so the CTAs do not all stream the same chunk
+// from L2 at the same moment.
 // The A operand rows (u_e with fixed DOFs as zero, slaved nodes expanded,
 // minus the least-squares rigid motion, scaled and split) are assembled by
 // a separate high-occupancy kernel, k_tc2_pack, straight into the
@@ -200,7 +203,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&q)[32]) {
 struct Tc2Args {
   long E;                     // elements to apply (the list's length when there is a list)
   const int* list;            // element ids, or null: 0 .. E-1
-  const uint32_t* slm;        // per listed element, its slaved local nodes (mixed meshes), or null
   const unsigned char* apack; // the packed A tiles (k_tc2_pack), tile t at t * ABYTES
   const float* escale;        // F16X3: per listed element, the power of two its row was scaled by
   const float* w32;           // E x M subcell weights, element-major
@@ -253,8 +255,10 @@ __device__ __forceinline__ long elem_lattice_node(int exi, int eyi, int ezi, int
 
 // Mixed meshes: a slaved local node of a triquadratic element carries the
 // linear interpolation of the vertices of its edge, face or cell (u = T_e
-// u, from the element's own vertices), and the element's result is folded
-// back (y <- T_e^T y): T_e^T K^(e) T_e applied without forming it.
+// u, from the element's own vertices).  The results are folded back after
+// assembly, y <- T^T y on the node lattice: the constraint T is local to each
+// element, so sum_e T_e^T y_e = T^T sum_e y_e, and T_e^T K^(e) T_e is
+// applied without forming it.
 __device__ __forceinline__ void expand_slaved(float* u, uint32_t msk) {
 #pragma unroll
   for (int a = 0; a < 27; ++a) {
@@ -278,59 +282,6 @@ __device__ __forceinline__ void expand_slaved(float* u, uint32_t msk) {
           }
       u[3 * a + c] = wgt * acc;
     }
-  }
-}
-// The same fold on an element's results in the DOF-major buffer (stride
-// ys between DOFs), in place.  Parents are vertices, which are never
-// slaved.  Every value is loaded first (the loads are independent), the
-// fold runs in registers with compile-time parent indices, then the stores.
-__device__ __forceinline__ void fold_slaved_strided(float* y, long ys, uint32_t msk) {
-  float vt[24];  // vertex v = vx + 2 (vy + 2 vz) at local node 2 vx + 3 (2 vy + 3 (2 vz))
-  float sv[81];  // slaved values (non-vertex local nodes only)
-#pragma unroll
-  for (int v = 0; v < 8; ++v)
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      vt[3 * v + c] = y[(3 * (2 * (v & 1) + 3 * (2 * ((v >> 1) & 1) + 3 * (2 * (v >> 2)))) + c) * ys];
-#pragma unroll
-  for (int a = 0; a < 27; ++a) {
-    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
-    const bool sl = ((ax | ay | az) & 1) != 0 && ((msk >> a) & 1u);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) sv[3 * a + c] = sl ? y[(3 * a + c) * ys] : 0.f;
-  }
-#pragma unroll
-  for (int a = 0; a < 27; ++a) {
-    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
-    if (((ax | ay | az) & 1) == 0) continue;  // a vertex
-    const int nx = ax == 1 ? 2 : 1, ny = ay == 1 ? 2 : 1, nz = az == 1 ? 2 : 1;
-    const float wgt = 1.f / (float)(nx * ny * nz);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float val = wgt * sv[3 * a + c];  // zero unless slaved
-#pragma unroll
-      for (int kz = 0; kz < 2; ++kz)
-#pragma unroll
-        for (int ky = 0; ky < 2; ++ky)
-#pragma unroll
-          for (int kx = 0; kx < 2; ++kx) {
-            if (kx >= nx || ky >= ny || kz >= nz) continue;
-            const int vx = ax == 1 ? kx : ax / 2, vy = ay == 1 ? ky : ay / 2, vz = az == 1 ? kz : az / 2;
-            vt[3 * (vx + 2 * (vy + 2 * vz)) + c] += val;
-          }
-    }
-  }
-#pragma unroll
-  for (int v = 0; v < 8; ++v)
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      y[(3 * (2 * (v & 1) + 3 * (2 * ((v >> 1) & 1) + 3 * (2 * (v >> 2)))) + c) * ys] = vt[3 * v + c];
-#pragma unroll
-  for (int a = 0; a < 27; ++a) {
-    const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
-    if (((ax | ay | az) & 1) != 0 && ((msk >> a) & 1u))
-#pragma unroll
-      for (int c = 0; c < 3; ++c) y[(3 * a + c) * ys] = 0.f;
   }
 }
 
@@ -478,6 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long nunits = (a.E + kUnit - 1) / kUnit;
   const long ntl = (long)blockIdx.x < nunits ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int rot = (int)(((long)blockIdx.x * S::NC) / gridDim.x) % S::NC;  // first chunk of this CTA
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
@@ -522,15 +474,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
             : "memory");
         for (int c = 0; c < S::NC; ++c, ++q) {
           const int s = (int)(q % NS);
+          const int cc = (c + rot) % S::NC;  // this CTA's chunk order
           if (!(ok = wait_or_abort(&bempty[s], (uint32_t)(((q / NS) & 1) ^ 1), &abort_flag))) break;
-          const uint32_t bytes = c == S::NC - 1 ? (uint32_t)(S::LASTNP / 8) * S::SBO : S::BBYTES;
+          const uint32_t bytes = cc == S::NC - 1 ? (uint32_t)(S::LASTNP / 8) * S::SBO : S::BBYTES;
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bfull[s])),
                        "r"(bytes)
                        : "memory");
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                   su32(sB + (size_t)s * S::BBYTES)),
-              "l"(a.img + (size_t)c * S::BBYTES), "r"(bytes), "r"(su32(&bfull[s]))
+              "l"(a.img + (size_t)cc * S::BBYTES), "r"(bytes), "r"(su32(&bfull[s]))
               : "memory");
         }
       }
@@ -556,7 +509,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
                wait_or_abort(&tempty[acc], (uint32_t)(((q >> 1) & 1) ^ 1), &abort_flag);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t n = c == S::NC - 1 ? (uint32_t)S::LASTNP : (uint32_t)S::NCH;
+          const int cc = (c + rot) % S::NC;
+          const uint32_t n = cc == S::NC - 1 ? (uint32_t)S::LASTNP : (uint32_t)S::NCH;
           const uint32_t idesc = (1u << 4) | (O::kFmt << 7) | (O::kFmt << 10) | ((n >> 3) << 17) |
                                  ((uint32_t)(kTm >> 4) << 24);
           const uint32_t bo = bbase + (uint32_t)s * S::BBYTES;
@@ -622,7 +576,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
         ok = __all_sync(0xffffffffu, wait_or_abort(&tfull[acc], (uint32_t)((q >> 1) & 1), &abort_flag));
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int ng = c == S::NC - 1 ? (S::LASTN + 31) / 32 : S::NCH / 32;
+        const int cc = (c + rot) % S::NC;
+        const int ng = cc == S::NC - 1 ? (S::LASTN + 31) / 32 : S::NCH / 32;
 #pragma unroll
         for (int tt = 0; tt < kPair; ++tt) {
 #pragma unroll 1
@@ -630,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
             uint32_t qv[32];
             tmem_ld32(tl + (uint32_t)(acc * 2 * S::NCH + tt * S::NCH + 32 * g), qv);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int r0 = (c * S::NCH + 32 * g) / S::MP;
+            const int r0 = (cc * S::NCH + 32 * g) / S::MP;
 #pragma unroll
             for (int o = 0; o < S::OPG; ++o) {
               float v = 0.f;
@@ -647,16 +602,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
       if (!ok) {
         atomicExch(a.err, 1);
         break;
-      }
-      if constexpr (D == 81) {
-        if (a.slm != nullptr) {
-#pragma unroll 1
-          for (int tt = 0; tt < kPair; ++tt) {  // y <- T_e^T y on this thread's own rows of Y
-            if (!live[tt]) continue;
-            const uint32_t msk = a.slm[ei[tt]];
-            if (msk != 0u) fold_slaved_strided(a.Y + e[tt], a.Ey, msk);
-          }
-        }
       }
     }
   }
@@ -707,13 +652,41 @@ __global__ void k_tc2_image(int mode, int D, int m, int mp, int nch, int kp, int
   }
 }
 
+// The per-DOF result of an operator gather, y the assembled A v at DOF d
+// (fixed DOFs are identity rows: y = v there):
+//   mode 0: out = b - y;  mode 1: out = v + omega D^-1 (b - y);  mode 2: out = y;
+//   mode 3: a Chebyshev step (ChebStep).
+__device__ __forceinline__ void gather_out(int mode, long d, float y, const float* __restrict__ b,
+                                           const float* __restrict__ v, const float* __restrict__ dinv,
+                                           const uint8_t* __restrict__ mask, float omega, float* __restrict__ out,
+                                           const ChebStep& cs) {
+  const float yc = mask[d] ? v[d] : y;
+  if (mode == 0) {
+    out[d] = b[d] - yc;
+  } else if (mode == 1) {
+    out[d] = v[d] + omega * dinv[d] * (b[d] - yc);
+  } else if (mode == 3) {
+    const float* co = static_cast<const float*>(cs.coef);
+    const float c1 = cs.ci < 0 ? 0.f : co[2 * cs.ci], c2 = cs.ci < 0 ? 1.f : co[2 * cs.ci + 1];
+    const float vd = v[d];
+    const float dp = cs.dprev ? static_cast<const float*>(cs.dprev)[d] : vd;
+    const float o = vd + c1 * dp + c2 * dinv[d] * (b[d] - yc);
+    static_cast<float*>(cs.dout)[d] = o - vd;
+    out[d] = o;
+  } else {
+    out[d] = yc;
+  }
+}
+
 // y_n = sum of y_e over the elements containing node n (fixed order), then
-//   mode 0: out = b - y;  mode 1: out = v + omega D^-1 (b - y);  mode 2: out = y.
-// Fixed DOFs are identity rows: y = v there.
+// gather_out.  On a mixed mesh (slv != null) the vertices and the slaved
+// nodes also keep their raw assembled y in yraw for k_tc2_fold, which
+// finishes the vertices.
 __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, const float* __restrict__ Y,
                              const float* __restrict__ b, const float* __restrict__ v,
                              const float* __restrict__ dinv, const uint8_t* __restrict__ mask, float omega,
-                             int mode, float* __restrict__ out, ChebStep cs) {
+                             int mode, float* __restrict__ out, ChebStep cs, const uint8_t* __restrict__ slv,
+                             float* __restrict__ yraw) {
   const long nn = (long)Lx * Ly * Lz;
   const long Ey = (long)ex * ey * ez;
   for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn; node += (long)gridDim.x * blockDim.x) {
@@ -730,9 +703,11 @@ __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, con
         e1[ax] = (c >> 1) > ext[ax] - 1 ? ext[ax] - 1 : (c >> 1);
       }
     }
-    const bool all_fixed = mask[3 * node] && mask[3 * node + 1] && mask[3 * node + 2];
+    const bool slaved = slv != nullptr && slv[node];
+    const bool vertex = slv != nullptr && !((i | j | l) & 1);  // finished by k_tc2_fold
+    const bool skip = !slaved && mask[3 * node] && mask[3 * node + 1] && mask[3 * node + 2];
     float y[3] = {0.f, 0.f, 0.f};
-    for (int ez_ = e0[2]; !all_fixed && ez_ <= e1[2]; ++ez_)
+    for (int ez_ = e0[2]; !skip && ez_ <= e1[2]; ++ez_)
       for (int ey_ = e0[1]; ey_ <= e1[1]; ++ey_)
         for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
           const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
@@ -745,23 +720,43 @@ __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, con
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long d = 3 * node + c;
-      const float yc = mask[d] ? v[d] : y[c];
-      if (mode == 0) {
-        out[d] = b[d] - yc;
-      } else if (mode == 1) {
-        out[d] = v[d] + omega * dinv[d] * (b[d] - yc);
-      } else if (mode == 3) {  // a Chebyshev step (ChebStep)
-        const float* co = static_cast<const float*>(cs.coef);
-        const float c1 = cs.ci < 0 ? 0.f : co[2 * cs.ci], c2 = cs.ci < 0 ? 1.f : co[2 * cs.ci + 1];
-        const float vd = v[d];
-        const float dp = cs.dprev ? static_cast<const float*>(cs.dprev)[d] : vd;
-        const float o = vd + c1 * dp + c2 * dinv[d] * (b[d] - yc);
-        static_cast<float*>(cs.dout)[d] = o - vd;
-        out[d] = o;
-      } else {
-        out[d] = yc;
-      }
+      if (slaved || vertex) yraw[d] = y[c];
+      if (!vertex) gather_out(mode, d, y[c], b, v, dinv, mask, omega, out, cs);
     }
+  }
+}
+
+// Mixed meshes: y <- T^T y at the vertices of the node lattice: each adds
+// 2^-q times the raw y of every slaved neighbour (q = the neighbour's
+// coordinates off the vertex: edge, face or cell midpoint), then
+// gather_out.  vnb[t] holds vertex t's slaved neighbours as bits k = (dx + 1)
+// + 3 (dy + 1) + 9 (dz + 1) (fixed at set-up).  Slaved nodes are fixed DOFs
+// (identity rows); every other node was finished by the gather.  One thread
+// per vertex.
+__global__ void k_tc2_fold(int Lx, int Ly, int Lz, const uint32_t* __restrict__ vnb, const float* __restrict__ yr,
+                           const float* __restrict__ b, const float* __restrict__ v,
+                           const float* __restrict__ dinv, const uint8_t* __restrict__ mask, float omega, int mode,
+                           float* __restrict__ out, ChebStep cs) {
+  const int Vx = (Lx + 1) / 2, Vy = (Ly + 1) / 2, Vz = (Lz + 1) / 2;
+  const long nv = (long)Vx * Vy * Vz;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nv; t += (long)gridDim.x * blockDim.x) {
+    const int i = 2 * (int)(t % Vx), j = 2 * (int)((t / Vx) % Vy), l = 2 * (int)(t / ((long)Vx * Vy));
+    const long node = i + (long)Lx * (j + (long)Ly * l);
+    float y[3] = {yr[3 * node], yr[3 * node + 1], yr[3 * node + 2]};
+    const uint32_t nb = vnb[t];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+      if (!((nb >> k) & 1u)) continue;
+      const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+      const int q = (dx != 0) + (dy != 0) + (dz != 0);
+      const float w = q == 1 ? 0.5f : (q == 2 ? 0.25f : 0.125f);
+      const long sn = node + dx + (long)Lx * (dy + (long)Ly * dz);
+      y[0] += w * yr[3 * sn];
+      y[1] += w * yr[3 * sn + 1];
+      y[2] += w * yr[3 * sn + 2];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gather_out(mode, 3 * node + c, y[c], b, v, dinv, mask, omega, out, cs);
   }
 }
 
@@ -797,7 +792,6 @@ cudaError_t run_apply(const TcOp& tc, const Level& L0, long count, const int* li
   Tc2Args a;
   a.E = count;
   a.list = list;
-  a.slm = slm;
   a.apack = tc.apack;
   a.escale = tc.escale;
   a.w32 = tc.w32;
@@ -937,8 +931,16 @@ void launch_tc2_gather(const Level& L0, const float* Y, const float* b, const fl
                        float omega, int mode, float* out, cudaStream_t st, const ChebStep* cs) {
   long g = (L0.nn + 255) / 256;
   if (g > 8192) g = 8192;
+  const ChebStep c = cs ? *cs : ChebStep{};
   k_tc2_gather<<<(int)g, 256, 0, st>>>(L0.Lx, L0.Ly, L0.Lz, L0.ex, L0.ey, L0.ez, Y, b, v, dinv, L0.mask, omega,
-                                       mode, out, cs ? *cs : ChebStep{});
+                                       mode, out, c, L0.slv, L0.yraw);
+  if (L0.slv != nullptr) {  // mixed mesh: fold the slaved nodes onto the vertices and finish them
+    const long nv = (long)((L0.Lx + 1) / 2) * ((L0.Ly + 1) / 2) * ((L0.Lz + 1) / 2);
+    long gv = (nv + 255) / 256;
+    if (gv > 8192) gv = 8192;
+    k_tc2_fold<<<(int)gv, 256, 0, st>>>(L0.Lx, L0.Ly, L0.Lz, L0.vnb, L0.yraw, b, v, dinv, L0.mask, omega, mode,
+                                        out, c);
+  }
 }
 
 }  // namespace tos

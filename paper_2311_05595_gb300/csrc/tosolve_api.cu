@@ -255,7 +255,8 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
     B += E0 * (P->m + tc2_result_stride() + 1) * 4 + tc2_pack_bytes(tc2_mode_of(d.precision), (long)E0) +
          tc2_image_bytes(tc2_mode_of(d.precision), P->m) +
-         tc2_image_bytes(tc2_mode_of(d.precision), P->m, 24) + (size_t)P->m * 576 * 8;
+         tc2_image_bytes(tc2_mode_of(d.precision), P->m, 24) + (size_t)P->m * 576 * 8 +
+         (size_t)P->lv[0].ndof * 4 + (size_t)P->lv[0].nn / 2;  // the mixed fold's raw assembly, vertex masks
   }
   P->bytes = B;
   return TOSOLVE_OK;
@@ -290,7 +291,7 @@ void free_all(tosolve_s* h) {
   F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab); F(h->ptab3);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->tcimg); F(h->Y2); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->inner.e); F(h->inner.ri); F(h->inner.pi); F(h->inner.qi);
-  F(h->el2); F(h->sl2); F(h->el1); F(h->tab64q1); F(h->tcimg1); F(h->tcpack); F(h->tcscale);
+  F(h->el2); F(h->sl2); F(h->el1); F(h->tab64q1); F(h->tcyraw); F(h->tcvnb); F(h->tcimg1); F(h->tcpack); F(h->tcscale);
   F(h->lz); F(h->lmax);
   F(h->Ad); F(h->Wp); F(h->Vp); F(h->Pg); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
@@ -781,6 +782,9 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     CKC(dalloc(h, &h->tcimg, tc2_image_bytes(mode, P.m)));
     CKC(dalloc(h, &h->w32, E0 * P.m));
     CKC(dalloc(h, &h->Y2, E0 * tc2_result_stride()));
+    // positions no product writes (the non-vertex rows of trilinear elements
+    // of a mixed mesh) stay 0: the mixed fold assembles every node raw
+    CKC(cudaMemsetAsync(h->Y2, 0, E0 * tc2_result_stride() * sizeof(float), st));
     CKC(dalloc(h, &h->tcpack, tc2_pack_bytes(mode, (long)E0)));
     CKC(dalloc(h, &h->tcscale, E0 + 256));
     h->tc.apack = h->tcpack;
@@ -798,6 +802,31 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       h->tc.tscale1 = tc2_table_scale(mode, t1.data(), t1.size());
       launch_tc2_image(mode, P.m, 24, h->tab64q1, h->tc.tscale1, h->tcimg1, st);
       h->tc.img1 = h->tcimg1;
+      // the node lattice's fold of the slaved nodes after assembly
+      CKC(dalloc(h, &h->tcyraw, (size_t)h->lv[0].ndof));
+      {
+        const Level& L0 = h->lv[0];
+        std::vector<uint8_t> sv(L0.nn);
+        CKC(cudaMemcpyAsync(sv.data(), h->slv0, L0.nn, cudaMemcpyDeviceToHost, st));
+        CKC(cudaStreamSynchronize(st));
+        const int Vx = (L0.Lx + 1) / 2, Vy = (L0.Ly + 1) / 2, Vz = (L0.Lz + 1) / 2;
+        std::vector<uint32_t> nb((size_t)Vx * Vy * Vz, 0u);
+        for (int c = 0; c < Vz; ++c)
+          for (int b = 0; b < Vy; ++b)
+            for (int a = 0; a < Vx; ++a)
+              for (int k = 0; k < 27; ++k) {
+                const int ii = 2 * a + k % 3 - 1, jj = 2 * b + (k / 3) % 3 - 1, ll = 2 * c + k / 9 - 1;
+                if (k == 13 || ii < 0 || ii >= L0.Lx || jj < 0 || jj >= L0.Ly || ll < 0 || ll >= L0.Lz) continue;
+                if (sv[ii + (size_t)L0.Lx * (jj + (size_t)L0.Ly * ll)])
+                  nb[a + (size_t)Vx * (b + (size_t)Vy * c)] |= 1u << k;
+              }
+        CKC(dalloc(h, &h->tcvnb, nb.size()));
+        CKC(cudaMemcpyAsync(h->tcvnb, nb.data(), nb.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        CKC(cudaStreamSynchronize(st));
+      }
+      h->lv[0].slv = h->slv0;
+      h->lv[0].yraw = h->tcyraw;
+      h->lv[0].vnb = h->tcvnb;
     }
     int sms = 1;
     CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
