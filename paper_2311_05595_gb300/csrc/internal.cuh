@@ -110,7 +110,9 @@ struct Level {
   int k = 1;        // Lagrange degree of the level's elements
   const float* ptab = nullptr;  // shape-function transfers into this level: the table W (else null)
   bool lag = false;             // ... products of 1D quadratic Lagrange transfers (degree 2 -> 2)
-  // degree 2: the operator as element matrices (81 x 81 each, full)
+  // degree 2: the operator as element matrices (81 x 81 each, full, or
+  // packed symmetric when sym: kPS2 entries per element)
+  bool sym = false;
   double* K64 = nullptr;
   float* K32 = nullptr;
   // serendipity levels: the compact matrices of the element's own DOFs
@@ -352,6 +354,20 @@ constexpr int kDD2 = 81 * 81;
 constexpr int kNM2 = 125;     // moments of a degree-2 element matrix
 constexpr int kD3 = 192;      // DOFs of a tricubic element
 constexpr int kDD3 = 192 * 192;
+// Lagrange degree-2 levels formed by sum factorisation keep each element
+// matrix as its packed upper triangle, row by row (kSym2 entries, stride
+// kPS2 so that every element starts on a 16-byte boundary); the others keep
+// the full kD x kD matrix.
+constexpr int kSym2 = 81 * 82 / 2;
+constexpr int kPS2 = 3324;
+__host__ __device__ inline int sym2_idx(int R, int C) {
+  if (R > C) {
+    const int t = R;
+    R = C;
+    C = t;
+  }
+  return R * 81 - R * (R - 1) / 2 + C - R;
+}
 void launch_q2_subcell_table(int n, double nu, double h, int family, double* tab, cudaStream_t st);
 void launch_q2_moment_basis(double nu, int family, double* cmom, cudaStream_t st);
 // Degree-3 subcell tables (family 0 Lagrange, 1 the 32-node serendipity
@@ -373,6 +389,7 @@ void launch_q2_elem(const Level& L, int n, const double* w, int Dx, int Dy, cons
 // a list only the listed elements; with slv (per lattice node, 1 = slaved)
 // each element's matrix is constrained, T_e^T K T_e.
 bool q2_elem_sf_supported(int N);
+inline bool elem_sym(int family, int k, int nsub) { return family == 0 && k == 2 && q2_elem_sf_supported(nsub); }
 void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double nu, const int* list, long count,
                        const uint8_t* slv, double* Ke, cudaStream_t st);
 // Trilinear elements of a mixed level 0 (L.el1): sum of the n^3 weighted
@@ -384,6 +401,10 @@ void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, cons
                            double* Mscr, double* Ke, cudaStream_t st);
 void launch_q2_dinv(bool fp64, const Level& L, const double* Ke, void* dinv, cudaStream_t st);
 void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t st);
+// Entries per element matrix of a degree >= 2 level.
+inline size_t elem_stride(const Level& L) {
+  return L.sym ? (size_t)kPS2 : (L.k == 3 ? (size_t)kDD3 : (size_t)kDD2);
+}
 // out = f(A_l v) in vector type vt: mode 0 b - Av, 1 v + omega D^-1 (b - Av),
 // 2 Av (identity rows at fixed DOFs).  Ke is FP64 for kVtF64, else FP32.
 void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b, const void* v,

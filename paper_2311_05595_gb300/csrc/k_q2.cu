@@ -513,7 +513,7 @@ __device__ __forceinline__ int sf_pair(int s, int t) {  // s <= t: 00 11 22 01 0
 __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int N, double h, double nu,
                                                    const double* __restrict__ w, int Dx, int Dy,
                                                    const int* __restrict__ list, const uint8_t* __restrict__ slv,
-                                                   int Lx, int Ly, double* __restrict__ Ke) {
+                                                   int Lx, int Ly, int sym, double* __restrict__ Ke) {
   extern __shared__ __align__(16) unsigned char sfraw[];
   SfSmem& S = *reinterpret_cast<SfSmem*>(sfraw);
   __shared__ unsigned slaved;  // bit a: local node a is slaved (mixed meshes)
@@ -622,9 +622,9 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
       __syncthreads();
     }
     // ---- K[(a,i),(b,j)] ----
-    // K is symmetric: the upper triangle R <= C is formed and written to
-    // both places (u = R * 81 - R (R - 1) / 2 + C - R)
-    double* out = Ke + e * (size_t)kDD;
+    // K is symmetric: the upper triangle R <= C is formed (u = R * 81 -
+    // R (R - 1) / 2 + C - R) and stored packed (sym) or in both places
+    double* out = Ke + e * (size_t)(sym ? kPS2 : kDD);
     for (int u = tid; u < kD * (kD + 1) / 2; u += nt) {
       int R = (int)((2 * kD + 1 - sqrtf((float)((2 * kD + 1) * (2 * kD + 1) - 8 * u))) * 0.5f);
       while (R > 0 && R * kD - R * (R - 1) / 2 > u) --R;
@@ -636,8 +636,12 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
       double v = lam * fij + mu * fji;
       if (i == j) v += mu * (S.F[0][a * 27 + b] + S.F[1][a * 27 + b] + S.F[2][a * 27 + b]);
       v *= hh;
-      out[R * kD + C] = v;
-      out[C * kD + R] = v;
+      if (sym) {
+        out[u] = v;
+      } else {
+        out[R * kD + C] = v;
+        out[C * kD + R] = v;
+      }
     }
     __syncthreads();
   }
@@ -982,6 +986,102 @@ __global__ void __launch_bounds__(Deg<K>::TB) k_q2_apply(int ex, int ey, long E,
   }
 }
 
+// The same for packed symmetric element matrices (Lagrange degree 2, kPS2
+// per element: the upper triangle row by row): each element's packed matrix
+// is brought into shared memory by one bulk copy (a two-stage ring, so the
+// next element's copy runs under this element's products), then thread a
+// forms row a: half the matrix traffic of the full form.  Every wait is bounded; on a timeout the block sets *err, lets its
+// copies land and stops.
+constexpr long kSymSpin = 1L << 22;
+__device__ __forceinline__ void sym_issue(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(bytes), "r"(b)
+               : "memory");
+}
+__device__ __forceinline__ bool sym_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  for (long it = 0; it < kSymSpin && !done; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(b), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+template <typename T>
+__global__ void __launch_bounds__(96) k_q2_apply_sym(int ex, int ey, long E, int Lx, int Ly,
+                                                     const op_t<T>* __restrict__ Ke,
+                                                     const uint8_t* __restrict__ mask, const T* __restrict__ u,
+                                                     T* __restrict__ Y, const int* __restrict__ list, int* err) {
+  using O = op_t<T>;
+  constexpr uint32_t kBytes = (uint32_t)(kPS2 * sizeof(O));
+  extern __shared__ __align__(128) unsigned char symsm[];  // 2 stages of kPS2 entries
+  O* ks0 = reinterpret_cast<O*>(symsm);
+  __shared__ T ue[kD];
+  __shared__ int cofs[kD];  // off(b) - b: entry (b, a), b <= a, is at cofs[b] + a
+  __shared__ __align__(8) uint64_t bar[2];
+  const int tid = threadIdx.x;
+  if (tid < kD) cofs[tid] = sym2_idx(tid, tid) - tid;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bar[q])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const long nk = (long)blockIdx.x < E ? (E - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto elem_at = [&](long k) {
+    const long t = blockIdx.x + k * gridDim.x;
+    return list != nullptr ? (long)list[t] : t;
+  };
+  if (tid == 0)
+    for (long k = 0; k < 2 && k < nk; ++k) sym_issue(ks0 + k * kPS2, Ke + elem_at(k) * (size_t)kPS2, kBytes, &bar[k]);
+  long k = 0;
+  for (; k < nk; ++k) {
+    const int st = (int)(k & 1);
+    const long e = elem_at(k);
+    const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+    bool free_dof = false;
+    if (tid < kD) {
+      const int a = tid / 3, c = tid % 3;
+      const long d = 3 * elem_node(exi, eyi, ezi, a, Lx, Ly) + c;
+      free_dof = mask[d] == 0;
+      ue[tid] = free_dof ? u[d] : T(0);
+    }
+    const bool any = __syncthreads_or(free_dof) != 0;
+    const bool got = sym_wait(&bar[st], (uint32_t)((k >> 1) & 1));
+    if (__syncthreads_or(!got)) break;
+    if (any && tid < kD) {  // an element with every DOF fixed is skipped (its rows are identity rows)
+      // row a in the cyclic order b = a, a + 1, ..: every lane does 81 steps,
+      // so no lane idles while the others finish (FP64 issue is the scarce
+      // resource); entry (a, b) is at cofs[min] + max
+      const O* ks = ks0 + st * kPS2;
+      Sum<T> acc;
+      int b = tid;
+#pragma unroll 3
+      for (int q = 0; q < kD; ++q) {
+        const int lo = b < tid ? b : tid, hi = b < tid ? tid : b;
+        acc.add(ks[cofs[lo] + hi], ue[b]);
+        b = b + 1 == kD ? 0 : b + 1;
+      }
+      Y[e * kD + tid] = acc.value();
+    }
+    __syncthreads();  // stage st and ue are free
+    if (tid == 0 && k + 2 < nk) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      sym_issue(ks0 + st * kPS2, Ke + elem_at(k + 2) * (size_t)kPS2, kBytes, &bar[st]);
+    }
+  }
+  if (k < nk && tid == 0) {  // timed out: flag, then let the copies in flight land
+    atomicExch(err, 1);
+    for (long q = k; q < nk && q < k + 2; ++q) sym_wait(&bar[q & 1], (uint32_t)((q >> 1) & 1));
+  }
+}
+
 // Trilinear elements of a mixed mesh: their constrained 81 x 81 matrix is
 // T_e^T K T_e with every non-vertex node slaved to the vertices, which is
 // zero outside the 24 vertex DOFs, so the product needs only that block
@@ -997,7 +1097,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_q1v_apply(int ex, int ey, long E1, int Lx, int Ly,
                                                    const op_t<T>* __restrict__ Ke,
                                                    const uint8_t* __restrict__ mask, const T* __restrict__ u,
-                                                   T* __restrict__ Y, const int* __restrict__ list) {
+                                                   T* __restrict__ Y, const int* __restrict__ list, int sym) {
   __shared__ T ue[4][24];
   const int grp = threadIdx.x >> 5, r = threadIdx.x & 31;
   for (long t0 = (long)blockIdx.x * 4; t0 < E1; t0 += (long)gridDim.x * 4) {
@@ -1014,10 +1114,11 @@ __global__ void __launch_bounds__(128) k_q1v_apply(int ex, int ey, long E1, int 
     }
     __syncthreads();
     if (live) {
-      const op_t<T>* Kr = Ke + e * (size_t)kDD;
+      const op_t<T>* Kr = Ke + e * (size_t)(sym ? kPS2 : kDD);
       Sum<T> acc;
 #pragma unroll 4
-      for (int c = 0; c < 24; ++c) acc.add(Kr[(size_t)q1v_dof(c) * kD + dr], ue[grp][c]);  // symmetric
+      for (int c = 0; c < 24; ++c)  // symmetric: column dr is row dr
+        acc.add(Kr[sym ? sym2_idx(q1v_dof(c), dr) : q1v_dof(c) * kD + dr], ue[grp][c]);
       Y[e * kD + dr] = acc.value();
     }
     __syncthreads();
@@ -1158,7 +1259,7 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
 // Inverse Jacobi diagonal: 1 / sum_e K^(e)_{3a+c, 3a+c}; fixed DOFs 1.
 template <int K, typename T>
 __global__ void k_q2_dinv(int Lx, int Ly, int Lz, int ex, int ey, int ez, const double* __restrict__ Ke,
-                          const uint8_t* __restrict__ mask, T* __restrict__ dinv) {
+                          const uint8_t* __restrict__ mask, T* __restrict__ dinv, int sym) {
   constexpr int kD = Deg<K>::D, kDD = Deg<K>::DD, NA = K + 1;
   const long nn = (long)Lx * Ly * Lz;
   for (long node = blockIdx.x * (long)blockDim.x + threadIdx.x; node < nn;
@@ -1173,7 +1274,9 @@ __global__ void k_q2_dinv(int Lx, int Ly, int Lz, int ex, int ey, int ez, const 
         for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
           const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
           const int a = (i - K * ex_) + NA * ((j - K * ey_) + NA * (l - K * ez_));
-          for (int c = 0; c < 3; ++c) dg[c] += Ke[e * (size_t)kDD + (size_t)(3 * a + c) * kD + 3 * a + c];
+          for (int c = 0; c < 3; ++c)
+            dg[c] += sym ? Ke[e * (size_t)kPS2 + sym2_idx(3 * a + c, 3 * a + c)]
+                         : Ke[e * (size_t)kDD + (size_t)(3 * a + c) * kD + 3 * a + c];
         }
     for (int c = 0; c < 3; ++c) {
       const long d = 3 * node + c;
@@ -1185,7 +1288,7 @@ __global__ void k_q2_dinv(int Lx, int Ly, int Lz, int ex, int ey, int ez, const 
 // Dense matrix of the coarsest level: elements of one parity class (no two
 // share a node) add their matrices; fixed rows and columns are identity.
 __global__ void k_q2_dense(int ex, int ey, int ez, int Lx, int Ly, int par, const double* __restrict__ Ke,
-                           const uint8_t* __restrict__ mask, long n, double* __restrict__ A) {
+                           const uint8_t* __restrict__ mask, long n, double* __restrict__ A, int sym) {
   const int px = par & 1, py = (par >> 1) & 1, pz = par >> 2;
   const int cx = (ex - px + 1) / 2, cy = (ey - py + 1) / 2, cz = (ez - pz + 1) / 2;
   const long Ec = (long)cx * cy * cz;
@@ -1200,7 +1303,7 @@ __global__ void k_q2_dense(int ex, int ey, int ez, int Lx, int Ly, int par, cons
     const long dr = 3 * elem_node(exi, eyi, ezi, R / 3, Lx, Ly) + R % 3;
     const long dc = 3 * elem_node(exi, eyi, ezi, C / 3, Lx, Ly) + C % 3;
     if (mask[dr] || mask[dc]) continue;
-    A[dr * n + dc] += Ke[e * (size_t)kDD + ent];
+    A[dr * n + dc] += sym ? Ke[e * (size_t)kPS2 + sym2_idx(R, C)] : Ke[e * (size_t)kDD + ent];
   }
 }
 
@@ -1377,7 +1480,8 @@ __device__ __forceinline__ int q1v_slot_vertex(int r27) {  // 27-node local inde
 }
 __global__ void __launch_bounds__(256) k_q1v_elem(int ex, int ey, long E1, const int* __restrict__ list, int n,
                                                   const double* __restrict__ w, int Dx, int Dy,
-                                                  const double* __restrict__ tab1, double* __restrict__ Ke) {
+                                                  const double* __restrict__ tab1, int sym,
+                                                  double* __restrict__ Ke) {
   extern __shared__ double q1sm[];  // wq[kEB * m], then Kq[kEB][576]
   const int m = n * n * n;
   double* wq = q1sm;
@@ -1417,11 +1521,12 @@ __global__ void __launch_bounds__(256) k_q1v_elem(int ex, int ey, long E1, const
     }
     __syncthreads();
     for (int q = 0; q < ne; ++q) {
-      double* out = Ke + (size_t)list[e0 + q] * kDD;
+      double* out = Ke + (size_t)list[e0 + q] * (sym ? kPS2 : kDD);
       for (int t = threadIdx.x; t < kDD; t += blockDim.x) {
         const int R = t / kD, Cc = t % kD;
+        if (sym && R > Cc) continue;
         const int rv = q1v_slot_vertex(R / 3), cv = q1v_slot_vertex(Cc / 3);
-        out[t] = (rv >= 0 && cv >= 0) ? Kq[q * 576 + (3 * rv + R % 3) * 24 + 3 * cv + Cc % 3] : 0.0;
+        out[sym ? sym2_idx(R, Cc) : t] = (rv >= 0 && cv >= 0) ? Kq[q * 576 + (3 * rv + R % 3) * 24 + 3 * cv + Cc % 3] : 0.0;
       }
     }
   }
@@ -1589,7 +1694,8 @@ void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double n
   long g = (long)L.sms * 3;  // three 70 KB blocks per SM
   if (g > E) g = E;
   if (g < 1) g = 1;
-  k_q2_elem_sf<<<(int)g, 256, sm, st>>>(L.ex, L.ey, E, L.nsub, L.h, nu, w, Dx, Dy, list, slv, L.Lx, L.Ly, Ke);
+  k_q2_elem_sf<<<(int)g, 256, sm, st>>>(L.ex, L.ey, E, L.nsub, L.h, nu, w, Dx, Dy, list, slv, L.Lx, L.Ly,
+                                        L.sym ? 1 : 0, Ke);
 }
 
 void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, const double* cmom,
@@ -1604,14 +1710,16 @@ void launch_q2_dinv(bool fp64, const Level& L, const double* Ke, void* dinv, cud
   const int g = grid_for2(L.nn);
   if (L.k == 3) {
     if (fp64)
-      k_q2_dinv<3, double><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (double*)dinv);
+      k_q2_dinv<3, double><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (double*)dinv, 0);
     else
-      k_q2_dinv<3, float><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (float*)dinv);
+      k_q2_dinv<3, float><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (float*)dinv, 0);
   } else {
     if (fp64)
-      k_q2_dinv<2, double><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (double*)dinv);
+      k_q2_dinv<2, double><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (double*)dinv,
+                                              L.sym ? 1 : 0);
     else
-      k_q2_dinv<2, float><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (float*)dinv);
+      k_q2_dinv<2, float><<<g, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, Ke, L.mask, (float*)dinv,
+                                             L.sym ? 1 : 0);
   }
 }
 
@@ -1619,7 +1727,7 @@ void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t s
   const long n = L.ndof;
   for (int par = 0; par < 8; ++par)
     k_q2_dense<<<grid_for2((long)L.ex * L.ey * L.ez * kDD / 8 + 1), 256, 0, st>>>(
-        L.ex, L.ey, L.ez, L.Lx, L.Ly, par, Ke, L.mask, n, A);
+        L.ex, L.ey, L.ez, L.Lx, L.Ly, par, Ke, L.mask, n, A, L.sym ? 1 : 0);
   k_q2_dense_fixed<<<grid_for2(n), 256, 0, st>>>(n, L.mask, A);
 }
 
@@ -1629,6 +1737,10 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
                   const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st,
                   const ChebStep* cs) {
   const ChebStep chs = cs ? *cs : ChebStep{};
+  static std::once_flag sym_attr;  // the FP64 ring needs more than the default 48 KB
+  std::call_once(sym_attr, [] {
+    cudaFuncSetAttribute(k_q2_apply_sym<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kPS2 * 8);
+  });
   const long E = (long)L.ex * L.ey * L.ez;
   long ga = (long)sms * 16;
   if (ga > E) ga = E;
@@ -1659,14 +1771,17 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
     if (L.el2 != nullptr) {  // mixed level 0: triquadratic list, then the trilinear vertex blocks
       long g2 = (long)sms * 16;
       if (g2 > L.ne2) g2 = L.ne2;
-      if (g2 >= 1)
+      if (g2 >= 1 && L.sym)
+        k_q2_apply_sym<T><<<(int)g2, 96, 2 * kPS2 * sizeof(op_t<T>), st>>>(
+            L.ex, L.ey, L.ne2, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask, (const T*)v, (T*)Y, L.el2, L.err);
+      else if (g2 >= 1)
         k_q2_apply<2, T><<<(int)g2, Deg<2>::TB, 0, st>>>(L.ex, L.ey, L.ne2, L.Lx, L.Ly, (const op_t<T>*)Ke,
                                                           L.mask, (const T*)v, (T*)Y, L.el2);
       long g1 = (long)sms * 8;
       if (g1 > (L.ne1 + 3) / 4) g1 = (L.ne1 + 3) / 4;
       if (g1 >= 1)
         k_q1v_apply<T><<<(int)g1, 128, 0, st>>>(L.ex, L.ey, L.ne1, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
-                                                (const T*)v, (T*)Y, L.el1);
+                                                (const T*)v, (T*)Y, L.el1, L.sym ? 1 : 0);
       k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
                                             (T*)out, chs);
@@ -1679,8 +1794,12 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
                                             (T*)out, chs);
     } else {
-      k_q2_apply<2, T><<<(int)ga, Deg<2>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
-                                                        (const T*)v, (T*)Y, nullptr);
+      if (L.sym)
+        k_q2_apply_sym<T><<<(int)ga, 96, 2 * kPS2 * sizeof(op_t<T>), st>>>(
+            L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask, (const T*)v, (T*)Y, nullptr, L.err);
+      else
+        k_q2_apply<2, T><<<(int)ga, Deg<2>::TB, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
+                                                          (const T*)v, (T*)Y, nullptr);
       k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
                                             (T*)out, chs);
@@ -1698,7 +1817,7 @@ void launch_q1v_elem(const Level& L, int n, const double* w, int Dx, int Dy, con
   long g = (L.ne1 + kEB - 1) / kEB;
   if (g > (long)L.sms * 8) g = (long)L.sms * 8;
   k_q1v_elem<<<(int)g, 256, (size_t)kEB * (m + 576) * sizeof(double), st>>>(L.ex, L.ey, L.ne1, L.el1, n, w, Dx,
-                                                                             Dy, tab1, Ke);
+                                                                             Dy, tab1, L.sym ? 1 : 0, Ke);
 }
 
 void launch_q2_fold(const Level& L, const uint8_t* slv, double* f, cudaStream_t st) {

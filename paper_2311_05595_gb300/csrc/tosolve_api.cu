@@ -196,7 +196,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
     const bool coarsest = l == L - 1;
     if (d.degree >= 2) {  // element matrices instead of stencils
       const size_t E = (size_t)v.ex * v.ey * v.ez;
-      const size_t dd = kl == 3 ? (size_t)kDD3 : (size_t)kDD2;
+      const size_t dd = kl == 3 ? (size_t)kDD3 : (elem_sym(d.family, kl, v.nsub) ? (size_t)kPS2 : (size_t)kDD2);
       const size_t tsz = (fp32 && !x2) ? 4 : 8;
       v.s64 = v.s32 = false;
       B += v.ndof + v.ndof * 8 + 4 * v.ndof * tsz;  // mask, dinv64, b v r z
@@ -619,7 +619,8 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     L.k = level_degree(h->d, l);
     if (L.k >= 2) {  // element matrices; the coarsest level's go to Kec
       const size_t E = (size_t)v.ex * v.ey * v.ez;
-      const size_t dd = L.k == 3 ? (size_t)kDD3 : (size_t)kDD2;
+      L.sym = elem_sym(h->d.family, L.k, v.nsub);
+      const size_t dd = elem_stride(L);
       CKC(dalloc(h, &L.dinv64, v.ndof));
       if (fp32) CKC(dalloc(h, &L.dinv32, v.ndof));
       if (l + 1 < P.L || l == 0) CKC(dalloc(h, &L.K64, E * dd));  // level 0: the CG's K
@@ -907,7 +908,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       for (int l = 1; l + 1 < P.L; ++l) em = std::max(em, (size_t)ex[l] * ey[l] * ez[l]);
       CKC(dalloc(h, &h->Mq, em * kNM2));
       CKC(dalloc(h, &h->Mqc, Ec * kNM2));
-      CKC(dalloc(h, &h->Kec, Ec * kDD2));
+      CKC(dalloc(h, &h->Kec, Ec * (elem_sym(h->d.family, level_degree(h->d, P.L - 1), c.nsub) ? kPS2 : kDD2)));
     } else {
       h->ke_bytes = slab_scratch_bytes(ex, ey, ez, P.L > 1 ? P.L - 1 : 1);
       CKC(dalloc(h, (char**)&h->Ke, h->ke_bytes));
@@ -1067,7 +1068,7 @@ static tosolve_status refresh(tosolve_t h) {
       Level& Lv = h->lv[l];
       form(Lv, l, Lv.K64, h->Mq, st);
       launch_q2_dinv(true, Lv, Lv.K64, Lv.dinv64, st);
-      if (Lv.K32) launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * (Lv.k == 3 ? kDD3 : kDD2), Lv.K64, Lv.K32, st);
+      if (Lv.K32) launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * elem_stride(Lv), Lv.K64, Lv.K32, st);
       if (Lv.dinv32) launch_q2_dinv(false, Lv, Lv.K64, Lv.dinv32, st);
       if (l == 0 && h->tc.on) launch_weights_elem(Lv, n, h->w, h->Dx, h->Dy, h->w32, st);
       if (Lv.Kc64 || Lv.Kc32) launch_ser_compact(Lv, st);
