@@ -53,15 +53,14 @@ except (OSError, ValueError):
 # DFMA rate at ~1.96 GHz) x 2 flop x 152 SMs x 2070 MHz max SM clock.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # DRAM traffic per launch of the dominant kernel from an ncu capture of the
-# same workload (dram__bytes_read.sum + dram__bytes_write.sum of the FP64
-# apply timed below; for the element form, the element product and the node
-# gather together), valid while the kernel source is unchanged (keyed by the
-# kernel, the source hash and the workload).
+# same workload (dram__bytes_read.sum + dram__bytes_write.sum), valid while
+# the kernel's source file is unchanged (keyed by the kernel, its operand
+# mode where it has one, the source hash and the workload).
 NCU_TRAFFIC = {
-    ("k_apply_diag<double>", "dae7917f3f1e", "cantilever_mr_96x48x48_q1_48x24x24_n2"):
-        60348672 + 90624,
-    ("k_q2_apply<double>", "a9e36f7df2c6", "bridge_q2_64x32x32_n3_density_192x96x96"):
-        3500955648 + 44271872 + 44121088 + 1024,
+    ("k_apply_diag<double>", "982cb0288947", "cantilever_mr_96x48x48_q1_48x24x24_n2"):
+        60361728 + 10240,  # the same tile body captured as k_cg_apply (FP64 variant)
+    ("k_tc2_apply", "f16x3", "bca1cfb26e18", "bridge_mixed_q1q2_64x32x32_n3_density_192x96x96"):
+        22499328 + 3189504,
 }
 
 
@@ -635,12 +634,12 @@ def fp64_roofline(wl: Workload) -> dict:
         bytes_alg = nn * (243 * 8 + 3 * 8 * 2)
         kernel = "k_apply_diag<double> (FP64 27-point block stencil, K u)"
         traffic = NCU_TRAFFIC.get(("k_apply_diag<double>", source_hash("k_solve.cu"), wl.spec["name"]))
-    else:  # element form: 81x81 FP64 product per element, then the node gather
+    else:  # element form: packed symmetric 81x81 FP64 product per element, then the node gather
         E = p.nx * p.ny * p.nz
         flops = 2.0 * 81 * 81 * E
-        bytes_alg = E * (81 * 81 * 8 + 81 * 8 * 2) + nn * 3 * 8 * 2
-        kernel = "k_q2_apply<double> + k_q2_gather<double> (FP64 element matrices, K u)"
-        traffic = NCU_TRAFFIC.get(("k_q2_apply<double>", source_hash("k_q2.cu"), wl.spec["name"]))
+        bytes_alg = E * (3321 * 8 + 81 * 8 * 2) + nn * 3 * 8 * 2
+        kernel = "k_q2_apply_sym<double> + k_q2_gather<double> (FP64 packed element matrices, K u)"
+        traffic = NCU_TRAFFIC.get(("k_q2_apply_sym<double>", source_hash("k_q2.cu"), wl.spec["name"]))
     achieved = flops / (us * 1e-6) / 1e12
     hbm = MEASURED_PEAKS.get("hbm_gbs")
     return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
