@@ -28,7 +28,6 @@ import hashlib
 import json
 import math
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -329,9 +328,6 @@ def kernel_launches(levels: int, iterations: int, attempts: int = 1, degree: int
     return setd + solve + 5
 
 
-_OURS = re.compile(r"\bk_[a-z0-9_]+")
-
-
 def pct(v, q):
     v = sorted(v)
     return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
@@ -493,31 +489,57 @@ class Workload:
         self.solvers = {}
 
 
-def _kernel_names(prof) -> list:
-    """Names of the device kernels in a torch.profiler trace."""
-    names = []
-    try:
-        for e in prof.profiler.kineto_results.events():
-            if str(e.device_type()).endswith("CUDA"):
-                names.append(e.name())
-    except Exception:
-        names = []
-    if not names:
-        names = [e.name for e in prof.events() if str(e.device_type).endswith("CUDA")]
-    return names
+class LaunchCounter:
+    """Counts this library's kernel launches (kernels in namespace tos) made
+    from the host, with CUPTI runtime-API callbacks on the launch entry
+    points (cudaLaunchKernel, its per-thread-stream and cooperative forms,
+    cudaLaunchKernelExC)."""
+
+    CBIDS = (211, 214, 269, 430)  # cupti_runtime_cbid.h
+    DOMAIN_RUNTIME = 2            # CUPTI_CB_DOMAIN_RUNTIME_API
+
+    def __init__(self):
+        import ctypes as C
+        import glob
+
+        libs = sorted(glob.glob("/usr/local/cuda*/targets/*/lib/libcupti.so*"))
+        if not libs:
+            raise RuntimeError("libcupti not found")
+        self.C = C
+        self.lib = C.CDLL(libs[0])
+
+        class CbData(C.Structure):
+            _fields_ = [("callbackSite", C.c_int), ("functionName", C.c_char_p), ("functionParams", C.c_void_p),
+                        ("functionReturnValue", C.c_void_p), ("symbolName", C.c_char_p), ("context", C.c_void_p),
+                        ("contextUid", C.c_uint32), ("correlationData", C.c_void_p), ("correlationId", C.c_uint32)]
+
+        self.n = 0
+
+        def cb(userdata, domain, cbid, data):
+            d = C.cast(data, C.POINTER(CbData)).contents
+            if d.callbackSite == 0 and d.symbolName and b"3tos" in d.symbolName:
+                self.n += 1
+
+        self._cb = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_uint32, C.c_void_p)(cb)
+        self.sub = C.c_void_p()
+        if self.lib.cuptiSubscribe(C.byref(self.sub), self._cb, None) != 0:
+            raise RuntimeError("cuptiSubscribe failed")
+        for cbid in self.CBIDS:
+            self.lib.cuptiEnableCallback(1, self.sub, self.DOMAIN_RUNTIME, cbid)
+
+    def close(self):
+        self.lib.cuptiUnsubscribe(self.sub)
 
 
 def count_launches(wl: Workload, label: str, host_loop: bool):
-    """Our kernels in one step of `label`, counted from the CUDA activity
-    trace of one step driven by the host loop (the same kernels as the
-    captured graph, whose conditional loop the trace cannot see into).
-    Returns (kernels per step, PCG iterations of that step, None) or
-    (None, None, reason)."""
+    """Our kernels in one step of `label`, counted (LaunchCounter) over one
+    step driven by the host loop: the same kernels as the captured graph,
+    whose launches happen inside the graph and are not host calls.  Returns
+    (kernels per step, PCG iterations of that step, None) or (None, None,
+    reason)."""
     ctx = wl.ctx
     torch = ctx.torch
     try:
-        import torch.profiler as tp
-
         os.environ["TOSOLVE_NO_GRAPH"] = "1"
         try:
             s = wl.make(label)
@@ -528,16 +550,17 @@ def count_launches(wl: Workload, label: str, host_loop: bool):
             with torch.cuda.stream(ctx.stream):
                 wl.step(s)
                 ctx.stream.synchronize()
-                with tp.profile(activities=[tp.ProfilerActivity.CUDA]) as prof:
+                counter = LaunchCounter()
+                try:
                     info, _ = wl.step(s)
                     ctx.stream.synchronize()
+                finally:
+                    counter.close()
         finally:
             s.close()
-        names = _kernel_names(prof)
-        n = sum(1 for nm in names if _OURS.search(nm) and "at::" not in nm)
-        if n == 0:
-            return None, None, f"trace held {len(names)} device events, none of ours"
-        return n, info.iterations, None
+        if counter.n == 0:
+            return None, None, "no launch of this library was seen"
+        return counter.n, info.iterations, None
     except Exception as e:
         return None, None, f"{type(e).__name__}: {str(e)[:200]}"
 
@@ -705,12 +728,12 @@ def run_gpu(args):
     name, inner = parse_variant(best)
     roof = tc_roofline(wl, best) if name in TC_PRECS and p.degree == 2 else fp64_roofline(wl)
 
-    # ---- our kernel launches: counted from one traced step ----
+    # ---- our kernel launches: counted over one host-loop step ----
     per_step, its_traced, why = count_launches(wl, best, args.host_loop)
     its = int(statistics.median(i[0] for i in out[best]["infos"]))
     if per_step is not None:
         launches = per_step * args.steps
-        launch_src = (f"counted: CUDA activity trace of one host-loop step of the same variant "
+        launch_src = (f"counted: CUPTI launch callbacks over one host-loop step of the same variant "
                       f"({per_step} kernels, {its_traced} PCG iterations; the timed steps took {its})")
     else:
         launches = kernel_launches(T.tosolve_level_count(s.h), its, degree=p.degree,

@@ -1469,14 +1469,13 @@ __global__ void __launch_bounds__(256) k_q2_energy_sf(int ex, int ey, long E, in
 
 // Trilinear elements of a mixed level 0: K1^(e) = sum_i w_{e,i} K1_i over the
 // n^3 subcells (the trilinear subcell table at this element size), written
-// into the element's 81 x 81 slot on its vertex DOFs, zero elsewhere (the
-// slot is read by the apply's vertex block, the Jacobi diagonal and a
-// one-level dense coarse operator).  kEB elements per block: the 300 entries
-// of the symmetric 24 x 24 block share each table read, are staged in shared
-// memory, and the slots are then written whole (coalesced).
-__device__ __forceinline__ int q1v_slot_vertex(int r27) {  // 27-node local index -> vertex 0..7, or -1
-  const int x = r27 % 3, y = (r27 / 3) % 3, z = r27 / 9;
-  return ((x | y | z) & 1) ? -1 : (x >> 1) + 2 * (y >> 1) + 4 * (z >> 1);
+// into the vertex DOFs of the element's 81 x 81 slot; the rest of the slot
+// is zero from create and never written (the slot is read by the apply's
+// vertex block, the Jacobi diagonal and a one-level dense coarse operator).
+// kEB elements per block: the 300 entries of the symmetric 24 x 24 block
+// share each table read and are staged in shared memory.
+__device__ __forceinline__ int q1v_vertex_node(int v) {  // vertex 0..7 -> its 27-node local index
+  return 2 * (v & 1) + 3 * (2 * ((v >> 1) & 1)) + 9 * (2 * (v >> 2));
 }
 __global__ void __launch_bounds__(256) k_q1v_elem(int ex, int ey, long E1, const int* __restrict__ list, int n,
                                                   const double* __restrict__ w, int Dx, int Dy,
@@ -1520,13 +1519,13 @@ __global__ void __launch_bounds__(256) k_q1v_elem(int ex, int ey, long E1, const
       }
     }
     __syncthreads();
-    for (int q = 0; q < ne; ++q) {
+    for (int q = 0; q < ne; ++q) {  // the vertex block only: the rest of the slot stays 0 from create
       double* out = Ke + (size_t)list[e0 + q] * (sym ? kPS2 : kDD);
-      for (int t = threadIdx.x; t < kDD; t += blockDim.x) {
-        const int R = t / kD, Cc = t % kD;
+      for (int t = threadIdx.x; t < 576; t += blockDim.x) {
+        const int r = t / 24, c = t % 24;
+        const int R = 3 * q1v_vertex_node(r / 3) + r % 3, Cc = 3 * q1v_vertex_node(c / 3) + c % 3;
         if (sym && R > Cc) continue;
-        const int rv = q1v_slot_vertex(R / 3), cv = q1v_slot_vertex(Cc / 3);
-        out[sym ? sym2_idx(R, Cc) : t] = (rv >= 0 && cv >= 0) ? Kq[q * 576 + (3 * rv + R % 3) * 24 + 3 * cv + Cc % 3] : 0.0;
+        out[sym ? sym2_idx(R, Cc) : R * kD + Cc] = Kq[q * 576 + t];
       }
     }
   }

@@ -624,6 +624,8 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       CKC(dalloc(h, &L.dinv64, v.ndof));
       if (fp32) CKC(dalloc(h, &L.dinv32, v.ndof));
       if (l + 1 < P.L || l == 0) CKC(dalloc(h, &L.K64, E * dd));  // level 0: the CG's K
+      if (l == 0 && elem_q1 != nullptr)  // trilinear slots: only their vertex blocks are ever written
+        CKC(cudaMemsetAsync(L.K64, 0, E * dd * sizeof(double), st));
       if (l + 1 < P.L && fp32 && !(tc2 && l == 0)) CKC(dalloc(h, &L.K32, E * dd));  // tensor cores: no level-0 copy
       if (h->d.family == 1) {  // compact copies for the apply
         const size_t dp = L.k == 3 ? 96 : 60;
