@@ -917,6 +917,75 @@ __global__ void k_l2_restrict(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int L
   }
 }
 
+// The same restriction with five lanes per coarse node, one per z tap
+// (six nodes per warp): each lane sums its 5 x 5 (x, y) taps and the five
+// partials meet by shuffles, added in tap order.  Five times the threads of
+// the one-lane form and a fifth of its dependent chain: the small coarse
+// levels, whose launches are latency bound, gain most.
+template <typename T>
+__global__ void k_l2_restrict5(int Lxf, int Lyf, int Lzf, int Lxc, int Lyc, int Lzc, const T* __restrict__ rf,
+                               const uint8_t* __restrict__ maskc, T* __restrict__ bc,
+                               const op_t<T>* __restrict__ dinvc, T omega, T* __restrict__ vc) {
+  const long nnc = (long)Lxc * Lyc * Lzc;
+  const int lane = threadIdx.x & 31;
+  const long nwarp = ((long)gridDim.x * blockDim.x) >> 5;
+  for (long wg = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wg * 6 < nnc; wg += nwarp) {
+    const long node = wg * 6 + lane / 5;
+    const int cz = lane % 5;
+    const bool live = lane < 30 && node < nnc;
+    T acc[3] = {T(0), T(0), T(0)};
+    if (live) {
+      const int I = node % Lxc, J = (node / Lxc) % Lyc, K = node / ((long)Lxc * Lyc);
+      int fx[5], fy[5], fz[5];
+      float wx[5], wy[5], wz[5];
+      l2_rtaps(I, Lxf, fx, wx);
+      l2_rtaps(J, Lyf, fy, wy);
+      l2_rtaps(K, Lzf, fz, wz);
+      float wzc = 0.f;
+      int fzc = 0;
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        if (c == cz) {
+          wzc = wz[c];
+          fzc = fz[c];
+        }
+      if (wzc != 0.f) {
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          const float wzy = wzc * wy[b];
+          if (wzy == 0.f) continue;
+          const long row = (long)Lxf * (fy[b] + (long)Lyf * fzc);
+#pragma unroll
+          for (int a = 0; a < 5; ++a) {
+            const float wgt = wzy * wx[a];
+            const T* rp = rf + 3 * (row + fx[a]);
+            acc[0] += (T)wgt * rp[0];
+            acc[1] += (T)wgt * rp[1];
+            acc[2] += (T)wgt * rp[2];
+          }
+        }
+      }
+    }
+    const int base = lane < 30 ? (lane / 5) * 5 : 0;
+    T tot[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T sum = T(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sum += __shfl_sync(0xffffffffu, acc[c], base + k);
+      tot[c] = sum;
+    }
+    if (live && cz == 0)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const long d = 3 * node + c;
+        const T bv = maskc[d] ? T(0) : tot[c];
+        bc[d] = bv;
+        if (vc != nullptr) vc[d] = omega * dinvc[d] * bv;
+      }
+  }
+}
+
 template <typename T>
 __global__ void k_s2_restrict_gather(int Lxc, int Lyc, int Lzc, int ecx, int ecy, int ecz,
                                      const T* __restrict__ Y, const uint8_t* __restrict__ maskc,
@@ -1610,8 +1679,15 @@ void launch_s2_restrict(int vt, const Level& F, const Level& C, const float* W, 
   auto run = [&](auto tag) {
     using T = decltype(tag);
     if (C.lag && !pdeg) {  // products of 1D Lagrange transfers, one pass
-      k_l2_restrict<T><<<g, 256, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, (const T*)F.r, C.mask, (T*)C.b,
-                                          (const op_t<T>*)dinvc, (T)omega, (T*)vc);
+      if constexpr (std::is_same<T, float>::value || std::is_same<T, double>::value) {
+        long g5 = (C.nn + 35) / 36;  // 192 threads: 6 warps of 6 nodes
+        if (g5 > 65536) g5 = 65536;
+        k_l2_restrict5<T><<<(int)g5, 192, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, (const T*)F.r, C.mask,
+                                                   (T*)C.b, (const op_t<T>*)dinvc, (T)omega, (T*)vc);
+      } else {
+        k_l2_restrict<T><<<g, 256, 0, st>>>(F.Lx, F.Ly, F.Lz, C.Lx, C.Ly, C.Lz, (const T*)F.r, C.mask, (T*)C.b,
+                                            (const op_t<T>*)dinvc, (T)omega, (T*)vc);
+      }
       return;
     }
     if (pdeg)

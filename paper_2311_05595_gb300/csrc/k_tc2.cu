@@ -46,9 +46,10 @@
 //   warps 2-5  epilogue: read each 32-column group of the accumulator
 //              (tcgen05.ld), weighted sum over its subcells, store the
 //              output DOF.
-// Every CTA walks the table chunks in its own rotated order (the chunks'
-// outputs are independent), so the CTAs do not all stream the same chunk
-// from L2 at the same moment.
+// The (unit, chunk) work items are split evenly over one CTA per SM, so
+// every SM works and the CTAs start at different chunks (the chunks'
+// outputs are independent) instead of all streaming the same chunk from L2
+// at the same moment.
 // The A operand rows (u_e with fixed DOFs as zero, slaved nodes expanded,
 // minus the least-squares rigid motion, scaled and split) are assembled by
 // a separate high-occupancy kernel, k_tc2_pack, straight into the
@@ -427,9 +428,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // Work items are (unit, chunk) pairs in unit order; CTA b takes the
+  // contiguous range [i0, i1), which touches ntl units (segments): every SM
+  // works, and the CTAs start at different chunks.
   const long nunits = (a.E + kUnit - 1) / kUnit;
-  const long ntl = (long)blockIdx.x < nunits ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int rot = (int)(((long)blockIdx.x * S::NC) / gridDim.x) % S::NC;  // first chunk of this CTA
+  const long nitems = nunits * S::NC;
+  const long i0 = (long)blockIdx.x * nitems / gridDim.x, i1 = ((long)blockIdx.x + 1) * nitems / gridDim.x;
+  const long u0 = i0 / S::NC;
+  const long ntl = i1 > i0 ? (i1 - 1) / S::NC - u0 + 1 : 0;
+  auto segment = [&](long j, long& unit, int& c0, int& c1) {  // chunks [c0, c1) of unit u0 + j
+    unit = u0 + j;
+    c0 = unit == u0 ? (int)(i0 - unit * S::NC) : 0;
+    c1 = (unit + 1) * S::NC <= i1 ? S::NC : (int)(i1 - unit * S::NC);
+  };
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
@@ -463,7 +474,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
       bool ok = true;
       for (; j < ntl && ok; ++j) {
         if (!(ok = wait_or_abort(&aempty, (uint32_t)((j & 1) ^ 1), &abort_flag))) break;
-        const long unit = blockIdx.x + j * gridDim.x;
+        long unit;
+        int c0, c1;
+        segment(j, unit, c0, c1);
         const uint32_t abytes = (uint32_t)kPair * S::ABYTES;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&afull)), "r"(abytes)
                      : "memory");
@@ -472,9 +485,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
                 su32(sA)),
             "l"(a.apack + (size_t)unit * abytes), "r"(abytes), "r"(su32(&afull))
             : "memory");
-        for (int c = 0; c < S::NC; ++c, ++q) {
+        for (int c = c0; c < c1; ++c, ++q) {
           const int s = (int)(q % NS);
-          const int cc = (c + rot) % S::NC;  // this CTA's chunk order
+          const int cc = c;
           if (!(ok = wait_or_abort(&bempty[s], (uint32_t)(((q / NS) & 1) ^ 1), &abort_flag))) break;
           const uint32_t bytes = cc == S::NC - 1 ? (uint32_t)(S::LASTNP / 8) * S::SBO : S::BBYTES;
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bfull[s])),
@@ -498,19 +511,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
     if (lane == 0) {
       const uint32_t abase = su32(sA), bbase = su32(sB);
       bool ok = true;
+      long q = 0;
       for (long j = 0; j < ntl && ok; ++j) {
+        long unit;
+        int c0, c1;
+        segment(j, unit, c0, c1);
         ok = wait_or_abort(&afull, (uint32_t)(j & 1), &abort_flag);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int c = 0; c < S::NC; ++c) {
-          const long q = j * S::NC + c;
+        for (int c = c0; c < c1; ++c, ++q) {
           const int s = (int)(q % NS), acc = (int)(q & 1);
           ok = wait_or_abort(&bfull[s], (uint32_t)((q / NS) & 1), &abort_flag) &&
                wait_or_abort(&tempty[acc], (uint32_t)(((q >> 1) & 1) ^ 1), &abort_flag);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int cc = (c + rot) % S::NC;
-          const uint32_t n = cc == S::NC - 1 ? (uint32_t)S::LASTNP : (uint32_t)S::NCH;
+          const uint32_t n = c == S::NC - 1 ? (uint32_t)S::LASTNP : (uint32_t)S::NCH;
           const uint32_t idesc = (1u << 4) | (O::kFmt << 7) | (O::kFmt << 10) | ((n >> 3) << 17) |
                                  ((uint32_t)(kTm >> 4) << 24);
           const uint32_t bo = bbase + (uint32_t)s * S::BBYTES;
@@ -554,13 +569,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
     const int quarter = warp & 3;  // a warp reads the TMEM lanes of its sub-partition
     const int lrow = 32 * quarter + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
+    long q = 0;
     for (long j = 0; j < ntl; ++j) {
+      long unit;
+      int c0, c1;
+      segment(j, unit, c0, c1);
       long ei[kPair], e[kPair];
       bool live[kPair];
       float w[kPair][M];
 #pragma unroll
       for (int tt = 0; tt < kPair; ++tt) {
-        ei[tt] = (blockIdx.x + j * gridDim.x) * (long)kUnit + tt * kTm + lrow;
+        ei[tt] = unit * (long)kUnit + tt * kTm + lrow;
         live[tt] = ei[tt] < a.E;
         e[tt] = !live[tt] ? 0 : (a.list != nullptr ? (long)a.list[ei[tt]] : ei[tt]);
         float sc = a.tscale;
@@ -570,13 +589,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
       }
       bool ok = true;
 #pragma unroll 1
-      for (int c = 0; c < S::NC; ++c) {
-        const long q = j * S::NC + c;
+      for (int c = c0; c < c1; ++c, ++q) {
         const int acc = (int)(q & 1);
         ok = __all_sync(0xffffffffu, wait_or_abort(&tfull[acc], (uint32_t)((q >> 1) & 1), &abort_flag));
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int cc = (c + rot) % S::NC;
+        const int cc = c;
         const int ng = cc == S::NC - 1 ? (S::LASTN + 31) / 32 : S::NCH / 32;
 #pragma unroll
         for (int tt = 0; tt < kPair; ++tt) {
@@ -800,7 +818,12 @@ cudaError_t run_apply(const TcOp& tc, const Level& L0, long count, const int* li
   a.Y = tc.Y2;
   a.Ey = (long)L0.ex * L0.ey * L0.ez;
   a.err = tc.err;
-  const int g = (int)(nunits < tc.sms ? nunits : tc.sms);
+  // (unit, chunk) work items split evenly over one CTA per SM; a table of few
+  // chunks (the trilinear one) keeps whole units per CTA, where a second
+  // unit's A tiles would cost more than the balance gains
+  const long nitems = nunits * S::NC;
+  const long per = S::NC >= 12 ? nitems : nunits;
+  const int g = (int)(per < tc.sms ? per : tc.sms);
   k_tc2_apply<MD, D, M><<<g, kThreads, S::SMEM, st>>>(a);
   return cudaGetLastError();
 }
