@@ -1812,6 +1812,10 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
                   const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st,
                   const ChebStep* cs) {
   const ChebStep chs = cs ? *cs : ChebStep{};
+  // packed symmetric storage is the FP64 operator's; the FP32 copy is full
+  // (its apply streams the matrix, which is faster than the packed form's
+  // shared-memory phase)
+  const bool symK = L.sym && Ke == (const void*)L.K64;
   static std::once_flag sym_attr;  // the FP64 ring needs more than the default 48 KB
   std::call_once(sym_attr, [] {
     cudaFuncSetAttribute(k_q2_apply_sym<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kPS2 * 8);
@@ -1846,7 +1850,7 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
     if (L.el2 != nullptr) {  // mixed level 0: triquadratic list, then the trilinear vertex blocks
       long g2 = (long)sms * 16;
       if (g2 > L.ne2) g2 = L.ne2;
-      if (g2 >= 1 && L.sym)
+      if (g2 >= 1 && symK)
         k_q2_apply_sym<T><<<(int)g2, 96, 2 * kPS2 * sizeof(op_t<T>), st>>>(
             L.ex, L.ey, L.ne2, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask, (const T*)v, (T*)Y, L.el2, L.err);
       else if (g2 >= 1)
@@ -1856,7 +1860,7 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
       if (g1 > (L.ne1 + 3) / 4) g1 = (L.ne1 + 3) / 4;
       if (g1 >= 1)
         k_q1v_apply<T><<<(int)g1, 128, 0, st>>>(L.ex, L.ey, L.ne1, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask,
-                                                (const T*)v, (T*)Y, L.el1, L.sym ? 1 : 0);
+                                                (const T*)v, (T*)Y, L.el1, symK ? 1 : 0);
       k_q2_gather<2, T><<<gg, 256, 0, st>>>(L.Lx, L.Ly, L.Lz, L.ex, L.ey, L.ez, (const T*)Y, (const T*)b,
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
                                             (T*)out, chs);
@@ -1869,7 +1873,7 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
                                             (T*)out, chs);
     } else {
-      if (L.sym)
+      if (symK)
         k_q2_apply_sym<T><<<(int)ga, 96, 2 * kPS2 * sizeof(op_t<T>), st>>>(
             L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask, (const T*)v, (T*)Y, nullptr, L.err);
       else
@@ -1883,6 +1887,25 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
   if (vt == kVtF64) run(double());
   else if (vt == kVtF32) run(float());
   else run(dfloat(0.f, 0.f));
+}
+
+// FP32 copy of a level's packed symmetric FP64 element matrices, expanded
+// to the full 81 x 81 (the FP32 apply streams the full matrix).
+__global__ void k_unpack32(long E, const double* __restrict__ Kp, float* __restrict__ Kf) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < E * kDD; t += (long)gridDim.x * blockDim.x) {
+    const long e = t / kDD;
+    const int ent = (int)(t % kDD);
+    Kf[t] = (float)Kp[e * kPS2 + sym2_idx(ent / kD, ent % kD)];
+  }
+}
+
+void launch_elem_fp32(const Level& L, const double* K64, float* K32, cudaStream_t st) {
+  const long E = (long)L.ex * L.ey * L.ez;
+  if (L.sym) {
+    k_unpack32<<<grid_for2(E * kDD, 16 * 4096), 256, 0, st>>>(E, K64, K32);
+    return;
+  }
+  launch_to_fp32((size_t)E * elem_stride(L), K64, K32, st);
 }
 
 void launch_q1v_elem(const Level& L, int n, const double* w, int Dx, int Dy, const double* tab1, double* Ke,

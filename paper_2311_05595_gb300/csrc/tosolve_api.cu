@@ -201,7 +201,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
       v.s64 = v.s32 = false;
       B += v.ndof + v.ndof * 8 + 4 * v.ndof * tsz;  // mask, dinv64, b v r z
       if (fp32) B += v.ndof * 4;
-      B += coarsest ? E * dd * 8 : E * dd * (8 + (fp32 && !(tc2 && l == 0) ? 4 : 0));
+      B += coarsest ? E * dd * 8 : E * (dd * 8 + (fp32 && !(tc2 && l == 0) ? (kl == 3 ? kDD3 : kDD2) * 4 : 0));
       if (d.family == 1 && (!coarsest || l == 0)) {  // compact copies of the serendipity levels
         const size_t dp = kl == 3 ? 96 : 60;
         B += E * dp * dp * (8 + (fp32 && !coarsest ? 4 : 0));
@@ -626,7 +626,8 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       if (l + 1 < P.L || l == 0) CKC(dalloc(h, &L.K64, E * dd));  // level 0: the CG's K
       if (l == 0 && elem_q1 != nullptr)  // trilinear slots: only their vertex blocks are ever written
         CKC(cudaMemsetAsync(L.K64, 0, E * dd * sizeof(double), st));
-      if (l + 1 < P.L && fp32 && !(tc2 && l == 0)) CKC(dalloc(h, &L.K32, E * dd));  // tensor cores: no level-0 copy
+      if (l + 1 < P.L && fp32 && !(tc2 && l == 0))  // tensor cores: no level-0 copy; FP32 copies are full
+        CKC(dalloc(h, &L.K32, E * (L.k == 3 ? (size_t)kDD3 : (size_t)kDD2)));
       if (h->d.family == 1) {  // compact copies for the apply
         const size_t dp = L.k == 3 ? 96 : 60;
         if (L.K64) CKC(dalloc(h, &L.Kc64, E * dp * dp));
@@ -1070,7 +1071,7 @@ static tosolve_status refresh(tosolve_t h) {
       Level& Lv = h->lv[l];
       form(Lv, l, Lv.K64, h->Mq, st);
       launch_q2_dinv(true, Lv, Lv.K64, Lv.dinv64, st);
-      if (Lv.K32) launch_to_fp32((size_t)Lv.ex * Lv.ey * Lv.ez * elem_stride(Lv), Lv.K64, Lv.K32, st);
+      if (Lv.K32) launch_elem_fp32(Lv, Lv.K64, Lv.K32, st);
       if (Lv.dinv32) launch_q2_dinv(false, Lv, Lv.K64, Lv.dinv32, st);
       if (l == 0 && h->tc.on) launch_weights_elem(Lv, n, h->w, h->Dx, h->Dy, h->w32, st);
       if (Lv.Kc64 || Lv.Kc32) launch_ser_compact(Lv, st);
