@@ -1427,16 +1427,24 @@ __global__ void k_q2_energy_grad(int ex, int ey, long E, int n, int Lx, int Ly,
 // axis): the 3n points per axis form a tensor grid, on which the
 // displacement gradients come by sum factorisation (contract the 27 nodal
 // values over z, then y, then x with the 1D basis values and derivatives).
-// About 4e4 FP64 FMAs per element for n = 3 instead of 27 x 6561, and no
-// cancellation between the terms of the quadratic form (an element that
-// moves almost rigidly has small strains, not a small difference of large
-// numbers).  dc/drho_i = -p rho_i^(p-1) (E0 - Emin) s_{e,i}, accumulated over
-// load cases unless first.  Block of 256 threads per element; each subcell's
-// sum is taken in a fixed order by one thread.
+// The strain energy vanishes on rigid motions, so the element's
+// least-squares rigid motion t + w x x (w = 1/36 sum_a x_a x u_a on the
+// nodes x_a in {-1, 0, 1}^3, where sum x x^T = 18 I) is removed in FP64
+// first; the remaining field is the strain part alone, and the passes and
+// the energy densities run in FP32 (64 times FP64's issue rate on this
+// part) with no cancellation of large terms.  The subcell sums are FP64.
+// dc/drho_i = -p rho_i^(p-1) (E0 - Emin) s_{e,i}, accumulated over load
+// cases unless first.  Block of 256 threads per element; each subcell's sum
+// is taken in a fixed order by one thread.
+// Coordinate d of local node a of the 27-node element, in {-1, 0, 1}.
+__device__ __forceinline__ int node_x(int a, int d) {
+  return d == 0 ? a % 3 - 1 : (d == 1 ? (a / 3) % 3 - 1 : a / 9 - 1);
+}
 constexpr int kEgMaxN = 4;
 __host__ __device__ constexpr int eg_smem_doubles(int n) {
-  // U 81 | Tz 3 x 2 x 9 x 3n | Tyz 3 x 3 x 3 x (3n)^2 | energy (3n)^3 | tables 2 x 3n x 3 + 3n
-  return 81 + 3 * 2 * 9 * 3 * n + 27 * 9 * n * n + 27 * n * n * n + 2 * 9 * n + 3 * n;
+  // U 81 + rigid motion 8 (FP64) | then FP32: Uf 81 | Tz 3 x 2 x 9 x 3n | Tyz 3 x 3 x 3 x (3n)^2 |
+  // energy (3n)^3 | tables 2 x 3n x 3 + 3n  (counted in doubles, rounded up)
+  return 89 + (81 + 3 * 2 * 9 * 3 * n + 27 * 9 * n * n + 27 * n * n * n + 2 * 9 * n + 3 * n + 1) / 2;
 }
 __global__ void __launch_bounds__(256) k_q2_energy_sf(int ex, int ey, long E, int n, int Lx, int Ly, double h,
                                                      double nu, const double* __restrict__ u,
@@ -1444,25 +1452,27 @@ __global__ void __launch_bounds__(256) k_q2_energy_sf(int ex, int ey, long E, in
                                                      int Dx, int Dy, int first, double* __restrict__ g) {
   extern __shared__ double egs[];
   const int Q = 3 * n;  // quadrature points per axis
-  double* U = egs;                              // [c][az][ay][ax]
-  double* Tz = U + 81;                          // [c][mz][ax + 3 ay][qz]
-  double* Tyz = Tz + 3 * 2 * 9 * Q;             // [c][combo][ax][qy * Q + qz], combo: (my,mz) 00 10 01
-  double* En = Tyz + 27 * Q * Q;                // energy density x weight per point
-  double* B = En + Q * Q * Q;                   // [m][q][alpha]
-  double* Wq = B + 2 * Q * 3;                   // 1D weight per point
+  double* U = egs;                              // [c][az][ay][ax], FP64
+  double* rig = U + 81;                         // t (3), w (3)
+  float* Uf = reinterpret_cast<float*>(egs + 89);  // the deflated field, FP32
+  float* Tz = Uf + 81;                          // [c][mz][ax + 3 ay][qz]
+  float* Tyz = Tz + 3 * 2 * 9 * Q;              // [c][combo][ax][qy * Q + qz], combo: (my,mz) 00 10 01
+  float* En = Tyz + 27 * Q * Q;                 // energy density x weight per point
+  float* B = En + Q * Q * Q;                    // [m][q][alpha]
+  float* Wq = B + 2 * Q * 3;                    // 1D weight per point
   const int tid = threadIdx.x, nt = blockDim.x;
   const double gp[3] = {-sqrt(0.6), 0.0, sqrt(0.6)};
   const double gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
   for (int t = tid; t < Q * 3; t += nt) {
     const int q = t / 3, al = t % 3;
     const double xi = -1.0 + (2 * (q / 3) + 1) / (double)n + gp[q % 3] / n;
-    B[q * 3 + al] = lag(al, xi);
-    B[Q * 3 + q * 3 + al] = dlag(al, xi);
-    if (al == 0) Wq[q] = gw[q % 3] / n;
+    B[q * 3 + al] = (float)lag(al, xi);
+    B[Q * 3 + q * 3 + al] = (float)dlag(al, xi);
+    if (al == 0) Wq[q] = (float)(gw[q % 3] / n);
   }
-  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-  const double mu = 1.0 / (2.0 * (1.0 + nu));
-  const double s2h = 2.0 / h;                 // d/dx = (2/h) d/dxi
+  const float lam = (float)(nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+  const float mu = (float)(1.0 / (2.0 * (1.0 + nu)));
+  const float s2h = (float)(2.0 / h);         // d/dx = (2/h) d/dxi
   const double jac = 0.125 * h * h * h;       // dx = (h/2)^3 dxi
   __syncthreads();
   for (long e = blockIdx.x; e < E; e += gridDim.x) {
@@ -1472,10 +1482,30 @@ __global__ void __launch_bounds__(256) k_q2_energy_sf(int ex, int ey, long E, in
       U[c * 27 + a] = u[3 * elem_node_k<2>(exi, eyi, ezi, a, Lx, Ly) + c];
     }
     __syncthreads();
+    if (tid < 6) {  // t_c = mean of component c; w = (1/36) sum_a x_a x u_a (sum x_a = 0)
+      double acc = 0.0;
+      if (tid < 3) {
+        for (int a = 0; a < 27; ++a) acc += U[tid * 27 + a];
+        acc *= 1.0 / 27.0;
+      } else {
+        const int k = tid - 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;  // (x x u)_k = x_k1 u_k2 - x_k2 u_k1
+        for (int a = 0; a < 27; ++a) acc += node_x(a, k1) * U[k2 * 27 + a] - node_x(a, k2) * U[k1 * 27 + a];
+        acc *= 1.0 / 36.0;
+      }
+      rig[tid] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < 81; t += nt) {  // u - t - w x x, rounded to FP32
+      const int c = t / 27, a = t % 27;
+      const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+      const double wx = rig[3 + c1] * node_x(a, c2) - rig[3 + c2] * node_x(a, c1);  // (w x x)_c
+      Uf[t] = (float)(U[t] - rig[c] - wx);
+    }
+    __syncthreads();
     for (int t = tid; t < 3 * 2 * 9 * Q; t += nt) {  // over az
       const int qz = t % Q, xy = (t / Q) % 9, mz = (t / (Q * 9)) % 2, c = t / (Q * 18);
-      const double* bz = B + mz * Q * 3 + qz * 3;
-      const double* uc = U + c * 27 + xy;
+      const float* bz = B + mz * Q * 3 + qz * 3;
+      const float* uc = Uf + c * 27 + xy;
       Tz[t] = bz[0] * uc[0] + bz[1] * uc[9] + bz[2] * uc[18];
     }
     __syncthreads();
@@ -1483,40 +1513,40 @@ __global__ void __launch_bounds__(256) k_q2_energy_sf(int ex, int ey, long E, in
       const int yz = t % (Q * Q), ax = (t / (Q * Q)) % 3, cb = (t / (Q * Q * 3)) % 3, c = t / (Q * Q * 9);
       const int my = cb == 1, mz = cb == 2;
       const int qy = yz / Q, qz = yz % Q;
-      const double* by = B + my * Q * 3 + qy * 3;
-      const double* tz = Tz + ((c * 2 + mz) * 9 + ax) * Q + qz;
+      const float* by = B + my * Q * 3 + qy * 3;
+      const float* tz = Tz + ((c * 2 + mz) * 9 + ax) * Q + qz;
       Tyz[t] = by[0] * tz[0] + by[1] * tz[3 * Q] + by[2] * tz[6 * Q];
     }
     __syncthreads();
     for (int t = tid; t < Q * Q * Q; t += nt) {  // over ax, then the energy density at the point
       const int qx = t % Q, yz = t / Q, qy = yz / Q, qz = yz % Q;
-      const double* b0 = B + qx * 3;
-      const double* b1 = B + Q * 3 + qx * 3;
-      double gr[3][3];  // gr[c][s] = d u_c / d x_s
+      const float* b0 = B + qx * 3;
+      const float* b1 = B + Q * 3 + qx * 3;
+      float gr[3][3];  // gr[c][s] = d u_c / d x_s
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
 #pragma unroll
         for (int sd = 0; sd < 3; ++sd) {
           const int cb = sd == 0 ? 0 : sd;  // x: (0,0) with B1 in x; y: combo 1; z: combo 2
-          const double* bx = sd == 0 ? b1 : b0;
-          const double* ty = Tyz + ((c * 3 + cb) * 3) * Q * Q + yz;
+          const float* bx = sd == 0 ? b1 : b0;
+          const float* ty = Tyz + ((c * 3 + cb) * 3) * Q * Q + yz;
           gr[c][sd] = s2h * (bx[0] * ty[0] + bx[1] * ty[Q * Q] + bx[2] * ty[2 * Q * Q]);
         }
       }
-      const double tr = gr[0][0] + gr[1][1] + gr[2][2];
-      const double e01 = 0.5 * (gr[0][1] + gr[1][0]), e02 = 0.5 * (gr[0][2] + gr[2][0]),
-                   e12 = 0.5 * (gr[1][2] + gr[2][1]);
-      const double ee = gr[0][0] * gr[0][0] + gr[1][1] * gr[1][1] + gr[2][2] * gr[2][2] +
-                        2.0 * (e01 * e01 + e02 * e02 + e12 * e12);
-      En[t] = (lam * tr * tr + 2.0 * mu * ee) * Wq[qx] * Wq[qy] * Wq[qz];
+      const float tr = gr[0][0] + gr[1][1] + gr[2][2];
+      const float e01 = 0.5f * (gr[0][1] + gr[1][0]), e02 = 0.5f * (gr[0][2] + gr[2][0]),
+                  e12 = 0.5f * (gr[1][2] + gr[2][1]);
+      const float ee = gr[0][0] * gr[0][0] + gr[1][1] * gr[1][1] + gr[2][2] * gr[2][2] +
+                       2.0f * (e01 * e01 + e02 * e02 + e12 * e12);
+      En[t] = (lam * tr * tr + 2.0f * mu * ee) * Wq[qx] * Wq[qy] * Wq[qz];
     }
     __syncthreads();
-    for (int sc = tid; sc < n * n * n; sc += nt) {  // subcell sums, fixed order
+    for (int sc = tid; sc < n * n * n; sc += nt) {  // subcell sums, fixed order, FP64
       const int a = sc % n, b = (sc / n) % n, c = sc / (n * n);
       double acc = 0.0;
       for (int k = 0; k < 27; ++k) {
         const int qx = 3 * a + k % 3, qy = 3 * b + (k / 3) % 3, qz = 3 * c + k / 9;
-        acc += En[(qy * Q + qz) * Q + qx];  // the layout of the point loop: x fastest, then z, then y
+        acc += (double)En[(qy * Q + qz) * Q + qx];  // the layout of the point loop: x fastest, then z, then y
       }
       acc *= jac;
       const long cell = (n * exi + a) + (long)Dx * ((n * eyi + b) + (long)Dy * (n * ezi + c));
