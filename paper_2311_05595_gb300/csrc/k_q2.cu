@@ -1290,9 +1290,16 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
     T y[3] = {T(0), T(0), T(0)};
     // a node with all DOFs fixed does not use y (its elements may be skipped)
     const bool all_fixed = mask[3 * node] && mask[3 * node + 1] && mask[3 * node + 2];
-    for (int ez_ = e0[2]; !all_fixed && ez_ <= e1[2]; ++ez_)
-      for (int ey_ = e0[1]; ey_ <= e1[1]; ++ey_)
-        for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
+    // the (at most) 2 x 2 x 2 elements, unrolled with predicates so that all
+    // their loads are in flight together; summed in the order z, y, x
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx) {
+          const int ex_ = e0[0] + kx, ey_ = e0[1] + ky, ez_ = e0[2] + kz;
+          if (all_fixed || ex_ > e1[0] || ey_ > e1[1] || ez_ > e1[2]) continue;
           const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
           const int a = (i - K * ex_) + NA * ((j - K * ey_) + NA * (l - K * ez_));
           const T* Ye = Y + e * kD + 3 * a;

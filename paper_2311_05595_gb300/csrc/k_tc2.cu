@@ -725,9 +725,16 @@ __global__ void k_tc2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, con
     const bool vertex = slv != nullptr && !((i | j | l) & 1);  // finished by k_tc2_fold
     const bool skip = !slaved && mask[3 * node] && mask[3 * node + 1] && mask[3 * node + 2];
     float y[3] = {0.f, 0.f, 0.f};
-    for (int ez_ = e0[2]; !skip && ez_ <= e1[2]; ++ez_)
-      for (int ey_ = e0[1]; ey_ <= e1[1]; ++ey_)
-        for (int ex_ = e0[0]; ex_ <= e1[0]; ++ex_) {
+    // the (at most) 2 x 2 x 2 elements, unrolled with predicates so that all
+    // their loads are in flight together; summed in the order z, y, x
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx) {
+          const int ex_ = e0[0] + kx, ey_ = e0[1] + ky, ez_ = e0[2] + kz;
+          if (skip || ex_ > e1[0] || ey_ > e1[1] || ez_ > e1[2]) continue;
           const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
           const int la = (i - 2 * ex_) + 3 * ((j - 2 * ey_) + 3 * (l - 2 * ez_));
           const float* ye = Y + (long)(3 * la) * Ey + e;  // DOF-major: coalesced along x
