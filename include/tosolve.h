@@ -535,14 +535,17 @@ tosolve_status tosolve_apply(tosolve_t h, int level, int precision, const double
  * time its stacked subcell contraction (Sec. 3.2, Eq. 10: K_e u_e =
  * sum_i w_{e,i} K_i u_e) alone between its own events on the handle's
  * stream.  part 0 = the triquadratic elements (every element of a
- * single-degree mesh), 1 = the trilinear elements of a mixed mesh.  stages
- * bit 0: round x_dev (FP64, device, length 3*nodes(0)) to FP32 and pack the
- * part's operand rows (masked, deflated, split) into the handle's scratch;
- * bit 1: run the contraction kernel on the rows packed last, writing the
- * per-element results to the handle's scratch (nothing is returned: use
- * tosolve_apply for K x).  x_dev is read only with bit 0 (may be NULL
- * otherwise).  Rows packed for one part are overwritten by a pack of the
- * other.  Errors: TOSOLVE_EINVAL (no such operator, bad part or stages). */
+ * single-degree mesh), 1 = the trilinear elements of a mixed mesh, whose
+ * 24 x 24 vertex blocks are applied in FP32 on the CUDA cores (in a solve
+ * they run in the same launch as the triquadratic rows' packing).  stages
+ * bit 0: round x_dev (FP64, device, length 3*nodes(0)) to FP32 and, for
+ * part 0, pack the operand rows (masked, deflated, split) into the handle's
+ * scratch; bit 1: run the part's product (part 0: the contraction kernel on
+ * the rows packed last; part 1: the FP32 products from the rounded x),
+ * writing the per-element results to the handle's scratch (nothing is
+ * returned: use tosolve_apply for K x).  x_dev is read only with bit 0 (may
+ * be NULL otherwise).  Errors: TOSOLVE_EINVAL (no such operator, bad part
+ * or stages). */
 tosolve_status tosolve_tc_stage(tosolve_t h, int part, int stages, const double* x_dev);
 
 /* z = B b: one multigrid cycle (Algorithm 1, recursive, zero initial guess)

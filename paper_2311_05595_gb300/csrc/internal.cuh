@@ -231,8 +231,6 @@ struct TcOp {
   int mode = 0;             // degree 2: operands (tc2_mode_of: TF32, BF16, BF16X3, F16X3)
   int prec = 0;             // degree 2: the tosolve_precision this mode serves
   float tscale = 1.f;       // degree 2, F16X3: power-of-two scale of the table image
-  const unsigned char* img1 = nullptr;  // mixed meshes: the trilinear table's image
-  float tscale1 = 1.f;
   unsigned char* apack = nullptr;  // degree 2: the packed A tiles (tc2_pack_bytes)
   float* escale = nullptr;         // degree 2, F16X3: per listed element, its row scale
   int m = 1;                // subcells per element
@@ -241,6 +239,7 @@ struct TcOp {
   float* Ye = nullptr;         // degree 1: E x 24 element results
   const unsigned char* img = nullptr;  // degree 2: stacked table in the shared-memory image
   float* Y2 = nullptr;         // degree 2: E x tc2_result_stride() element results
+  const float* K1v = nullptr;  // mixed meshes: ne1 x kQ1Sym FP32 trilinear vertex blocks (packed)
   int* err = nullptr;
   int sms = 1;
 };
@@ -258,14 +257,19 @@ void launch_mask_fp32(const Level& L, float* x, cudaStream_t st);
 // ---- launchers (k_tc2.cu): degree-2 finest level on tcgen05 ---------------
 // n_mr with a tensor-core kernel for degree 2 (m = n^3 subcells: 1, 8, 27).
 bool tc2_supported(int n);
+// Packed upper triangle of a trilinear element's 24 x 24 vertex block.
+constexpr int kQ1Sym = 24 * 25 / 2;
+// FP32 packed vertex blocks of the trilinear elements of a mixed level 0
+// (L0.el1 order) from the level's FP64 element matrices K64.
+void launch_q1v_compact32(const Level& L0, const double* K64, float* K1v, cudaStream_t st);
 // Operand mode of a tensor-core precision: TF32 0, BF16 1, BF16X3 2, F16X3 3.
 inline int tc2_mode_of(int precision) {
   return precision == TOSOLVE_PREC_TF32 ? 0 : precision == TOSOLVE_PREC_BF16 ? 1
                                          : precision == TOSOLVE_PREC_BF16X3 ? 2 : 3;
 }
-// Bytes of the stacked table's shared-memory image for an operand mode
-// (dofs 81: the triquadratic table; 24: the trilinear one of a mixed mesh).
-size_t tc2_image_bytes(int mode, int m, int dofs = 81);
+// Bytes of the stacked triquadratic table's shared-memory image for an
+// operand mode.
+size_t tc2_image_bytes(int mode, int m);
 // Floats per element in the result buffer (81 rounded up to 16 bytes).
 size_t tc2_result_stride();
 // Bytes of the packed A tiles for E elements (whole work units).
@@ -273,14 +277,16 @@ size_t tc2_pack_bytes(int mode, long E);
 // Power-of-two scale of the table image (F16X3: largest entry into
 // [0.5, 1) after dividing by it; else 1), from the host copy of the table.
 float tc2_table_scale(int mode, const double* tab_host, size_t count);
-void launch_tc2_image(int mode, int m, int dofs, const double* tab, float tscale, unsigned char* img,
-                      cudaStream_t st);
+void launch_tc2_image(int mode, int m, const double* tab, float tscale, unsigned char* img, cudaStream_t st);
 // tc.Y2 = per-element stacked contraction of the level-0 vector v (fixed
 // DOFs as zero), weights tc.w32 (E x m); on a mixed level 0 the triquadratic
-// elements with their slaved nodes (T_e^T K T_e) and the trilinear ones on
-// their vertices.  part: -1 every element, 0 the triquadratic (all on a
-// single-degree mesh), 1 the trilinear ones of a mixed mesh; stages: bit 0
-// packs the operand rows, bit 1 runs the contraction on the packed rows.
+// elements with their slaved nodes (T_e^T K T_e), and the trilinear ones on
+// their vertices by FP32 products with tc.K1v on the CUDA cores.  part: -1
+// every element, 0 the triquadratic (all on a single-degree mesh), 1 the
+// trilinear ones of a mixed mesh; stages: bit 0 packs the operand rows,
+// bit 1 runs the contraction on the packed rows (and, with part 1 or with
+// part -1 without bit 0, the trilinear products; part -1 with both bits
+// runs them beside the row packing).
 cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cudaStream_t st, int part = -1,
                              int stages = 3);
 // Node gather of Y fused with the V-cycle step: mode 0 b - y, 1 v + omega
@@ -526,8 +532,8 @@ struct tosolve_s {
   int* el1 = nullptr;          // trilinear elements (ascending)
   long ne2 = 0, ne1 = 0;
   double* tab64q1 = nullptr;   // trilinear subcell table of a mixed mesh
-  unsigned char* tcimg1 = nullptr;  // its shared-memory image
   float* tcyraw = nullptr;          // raw assembled products before the slaved fold
+  float* tck1v = nullptr;           // FP32 packed vertex blocks of the trilinear elements
   uint32_t* tcvnb = nullptr;        // per lattice vertex, its slaved neighbours (bit (dx+1)+3(dy+1)+9(dz+1))
   // Chebyshev smoothing: Lanczos scratch (64) and each level's estimate of
   // lambda_max(D^-1 A) (mg_levels)

@@ -223,12 +223,19 @@ struct PackArgs {
   const uint8_t* mask;        // per DOF, 1 = fixed
   unsigned char* apack;
   float* escale;
+  long pblocks;               // blocks that pack rows; the others multiply trilinear elements
+  long E1;                    // trilinear elements of a mixed mesh (L0.el1 order), or 0
+  const int* list1;
+  const float* K1;            // their FP32 packed vertex blocks (kQ1Sym each)
+  float* Y;                   // element results, DOF-major: Y[r * Ey + e]
+  long Ey;
 };
 
 // The element's nodes on the degree-2 lattice: D = 81, the 27 nodes of a
-// triquadratic element (a = ax + 3 (ay + 3 az)); D = 24, the 8 vertices of a
-// trilinear element of a mixed mesh (v = vx + 2 (vy + 2 vz)), whose
-// results go to the vertex positions of the 27-node layout of Y.
+// triquadratic element (a = ax + 3 (ay + 3 az)), the rows of the stacked
+// contraction; D = 24, the 8 vertices of a trilinear element of a mixed mesh
+// (v = vx + 2 (vy + 2 vz)), whose FP32 products go to the vertex positions
+// of the 27-node layout of Y.
 template <int D>
 struct Elem;
 template <>
@@ -241,13 +248,10 @@ struct Elem<81> {
 };
 template <>
 struct Elem<24> {
-  static constexpr int NN = 8;
   __host__ __device__ static constexpr int off(int v, int d) { return 2 * ((v >> d) & 1); }
-  __host__ __device__ static constexpr int pos(int v, int d) { return off(v, d) - 1; }
   __host__ __device__ static constexpr int out(int r) {
     return 3 * (off(r / 3, 0) + 3 * (off(r / 3, 1) + 3 * off(r / 3, 2))) + r % 3;
   }
-  static constexpr float kRot = 1.f / 16.f;
 };
 template <int D>
 __device__ __forceinline__ long elem_lattice_node(int exi, int eyi, int ezi, int a, int Lx, int Ly) {
@@ -288,15 +292,15 @@ __device__ __forceinline__ void expand_slaved(float* u, uint32_t msk) {
 
 
 // u_e minus its least-squares rigid motion t + omega x over the element's
-// nodes at reference positions x_a (the 27 points of {-1, 0, 1}^3, or the 8
-// vertices {-1, 1}^3).  Every subcell matrix
+// nodes at reference positions x_a (the 27 points of {-1, 0, 1}^3).  Every
+// subcell matrix
 // annihilates rigid motions (they carry no strain), so K^(e_i) u_e is
 // unchanged in exact arithmetic, but the rounded operands then carry an
 // error relative to the element's deformation instead of its displacement:
 // a smooth multigrid correction is locally almost rigid, and rounding it
 // whole would leave spurious forces of the rounding unit times |K| |u|.
-// For these symmetric node sets sum_a x_a = 0 and sum_a x_a x_a^T = s I
-// (s = 18 resp. 8), so t is the mean and omega = sum_a x_a x u_a / (3 s - s).
+// For this symmetric node set sum_a x_a = 0 and sum_a x_a x_a^T = s I
+// (s = 18), so t is the mean and omega = sum_a x_a x u_a / (3 s - s).
 template <int D>
 __device__ __forceinline__ void deflate_rigid(float* u) {
   constexpr int NN = Elem<D>::NN;
@@ -383,13 +387,90 @@ __device__ __forceinline__ float store_row(const float* u, unsigned char* dstrow
   return s;
 }
 
+// Trilinear elements of a mixed mesh: y_e = K^(e) u_e on their 24 vertex
+// DOFs in FP32 on the CUDA cores.  With 576 products per element (against
+// 27 x 6561 for a triquadratic one) the tensor-core pipeline would spend
+// these elements in its fixed latencies; here the FP32 matrices are the
+// packed upper triangles of the elements' vertex blocks (k_q1v_compact32,
+// after each refresh), 1.2 KB per element.  A warp takes four consecutive
+// listed elements: their matrices go to shared memory by asynchronous
+// 16-byte copies (no registers held), lane 8 s + q gathers vertex q of
+// element s (fixed DOFs as zero), then forms its vertex's three rows
+// (columns, by symmetry) in a fixed order and writes them to their places
+// in the 27-node layout of Y.  Blocks blk = 0 .. nblk-1 of 128 threads; the
+// row packing of the triquadratic elements launches these blocks beside its
+// own, so that the two latency-bound gathers overlap.
+constexpr int kQ1Warps = 4;
+constexpr int kQ1PerWarp = 4;
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void q1v_rows(const PackArgs& a, long blk, long nblk) {
+  __shared__ __align__(16) float ks[kQ1Warps][kQ1PerWarp * kQ1Sym];
+  __shared__ float us[kQ1Warps][kQ1PerWarp][24];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = lane >> 3, vq = lane & 7;
+  const long stride = nblk * kQ1Warps * kQ1PerWarp;
+  for (long t0 = (blk * kQ1Warps + w) * kQ1PerWarp; t0 < a.E1; t0 += stride) {  // warp-uniform
+    const int nel = a.E1 - t0 < kQ1PerWarp ? (int)(a.E1 - t0) : kQ1PerWarp;
+    const float4* src = reinterpret_cast<const float4*>(a.K1 + t0 * kQ1Sym);
+    float4* dst = reinterpret_cast<float4*>(ks[w]);
+    for (int q = lane; q < nel * (kQ1Sym / 4); q += 32) cp_async16(dst + q, src + q);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const bool live = sub < nel;
+    int e = 0;
+    if (live) {
+      e = a.list1[t0 + sub];
+      const int exi = e % a.ex, eyi = (e / a.ex) % a.ey, ezi = e / (a.ex * a.ey);
+      const long d = 3 * elem_lattice_node<24>(exi, eyi, ezi, vq, a.Lx, a.Ly);
+      float vd[3];
+      uint8_t md[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        vd[c] = a.v[d + c];
+        md[c] = a.mask[d + c];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) us[w][sub][3 * vq + c] = md[c] ? 0.f : vd[c];
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    if (live) {
+      const float* km = ks[w] + sub * kQ1Sym;
+      const float* um = us[w][sub];
+#pragma unroll
+      for (int c3 = 0; c3 < 3; ++c3) {
+        // entry (min, max) of the packed rows: along column c < r the index
+        // steps by 23 - c, along row r (c >= r) by 1
+        const int r = 3 * vq + c3;
+        float acc = 0.f;
+        int idx = r;  // (0, r)
+#pragma unroll
+        for (int c = 0; c < 24; ++c) {
+          acc += km[idx] * um[c];
+          idx += c < r ? 23 - c : 1;
+        }
+        a.Y[(long)Elem<24>::out(r) * a.Ey + e] = acc;
+      }
+    }
+    __syncwarp();
+  }
+}
+__global__ void __launch_bounds__(32 * kQ1Warps, 8) k_q1v_apply32(PackArgs a) { q1v_rows(a, blockIdx.x, gridDim.x); }
+
 // One element's A row per thread, written into the image of its tile
 // (whole work units: rows past the list are zeros).
 template <int MD, int D>
 __global__ void __launch_bounds__(128) k_tc2_pack(PackArgs a) {
   using S = Shape<MD, D, 1>;  // the row layout does not depend on M
   using O = Opnd<MD>;
-  for (long ei = blockIdx.x * (long)blockDim.x + threadIdx.x; ei < a.rows; ei += (long)gridDim.x * blockDim.x) {
+  if constexpr (D == 81) {
+    if ((long)blockIdx.x >= a.pblocks) {  // the trilinear elements' products
+      q1v_rows(a, (long)blockIdx.x - a.pblocks, (long)gridDim.x - a.pblocks);
+      return;
+    }
+  }
+  for (long ei = blockIdx.x * (long)blockDim.x + threadIdx.x; ei < a.rows; ei += a.pblocks * blockDim.x) {
     float u[S::KP];
 #pragma unroll
     for (int k = 0; k < S::KP; ++k) u[k] = 0.f;
@@ -785,9 +866,50 @@ __global__ void k_tc2_fold(int Lx, int Ly, int Lz, const uint32_t* __restrict__ 
   }
 }
 
+// FP32 packed upper triangles (row by row, kQ1Sym entries) of the trilinear
+// elements' 24 x 24 vertex blocks, read from their slots of the level's FP64
+// element matrices (packed symmetric 81 x 81 when sym, else full).
+__global__ void k_q1v_compact32(long E1, const int* __restrict__ list, const double* __restrict__ K64, int sym,
+                                float* __restrict__ K1) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < E1 * kQ1Sym; q += (long)gridDim.x * blockDim.x) {
+    const long t = q / kQ1Sym;
+    int rem = (int)(q % kQ1Sym), R = 0;
+    while (rem >= 24 - R) {
+      rem -= 24 - R;
+      ++R;
+    }
+    const int C = R + rem;
+    const int a = Elem<24>::out(R), b = Elem<24>::out(C);
+    const long e = list[t];
+    K1[q] = (float)(sym ? K64[e * (long)kPS2 + sym2_idx(a, b)] : K64[e * (long)kDD2 + (long)a * 81 + b]);
+  }
+}
+
+// Arguments of the trilinear products (PackArgs fields), in blocks of their own.
+void set_q1v(PackArgs& pa, const TcOp& tc, const Level& L0, const float* v) {
+  pa.ex = L0.ex;
+  pa.ey = L0.ey;
+  pa.Lx = L0.Lx;
+  pa.Ly = L0.Ly;
+  pa.v = v;
+  pa.mask = L0.mask;
+  pa.E1 = L0.ne1;
+  pa.list1 = L0.el1;
+  pa.K1 = tc.K1v;
+  pa.Y = tc.Y2;
+  pa.Ey = (long)L0.ex * L0.ey * L0.ez;
+}
+long q1v_blocks(const TcOp& tc, long E1) {
+  long g = (E1 + kQ1Warps * kQ1PerWarp - 1) / (kQ1Warps * kQ1PerWarp);
+  return g > 8L * tc.sms ? 8L * tc.sms : g;
+}
+
+// tri: the row packing also launches the trilinear elements' products
+// (mixed meshes, D = 81).
 template <int MD, int D, int M>
 cudaError_t run_apply(const TcOp& tc, const Level& L0, long count, const int* list, const uint32_t* slm,
-                      const float* v, const unsigned char* img, float tscale, int stages, cudaStream_t st) {
+                      const float* v, const unsigned char* img, float tscale, int stages, bool tri,
+                      cudaStream_t st) {
   using S = Shape<MD, D, M>;
   static std::once_flag once;  // handles may be created from several threads
   static cudaError_t attr = cudaSuccess;
@@ -798,21 +920,19 @@ cudaError_t run_apply(const TcOp& tc, const Level& L0, long count, const int* li
   if (count <= 0) return cudaSuccess;
   const long nunits = (count + kUnit - 1) / kUnit;
   PackArgs pa;
-  pa.ex = L0.ex;
-  pa.ey = L0.ey;
-  pa.Lx = L0.Lx;
-  pa.Ly = L0.Ly;
+  set_q1v(pa, tc, L0, v);
+  if (!tri) pa.E1 = 0;
   pa.E = count;
   pa.rows = nunits * kUnit;
   pa.list = list;
   pa.slm = slm;
-  pa.v = v;
-  pa.mask = L0.mask;
   pa.apack = tc.apack;
   pa.escale = tc.escale;
   long gp = (pa.rows + 127) / 128;
   if (gp > 16L * tc.sms) gp = 16L * tc.sms;
-  if (stages & 1) k_tc2_pack<MD, D><<<(int)gp, 128, 0, st>>>(pa);
+  pa.pblocks = gp;
+  const long gt = D == 81 && pa.E1 > 0 ? q1v_blocks(tc, pa.E1) : 0;
+  if (stages & 1) k_tc2_pack<MD, D><<<(int)(gp + gt), 128, 0, st>>>(pa);
   if (!(stages & 2)) return cudaGetLastError();
   Tc2Args a;
   a.E = count;
@@ -826,8 +946,8 @@ cudaError_t run_apply(const TcOp& tc, const Level& L0, long count, const int* li
   a.Ey = (long)L0.ex * L0.ey * L0.ez;
   a.err = tc.err;
   // (unit, chunk) work items split evenly over one CTA per SM; a table of few
-  // chunks (the trilinear one) keeps whole units per CTA, where a second
-  // unit's A tiles would cost more than the balance gains
+  // chunks (n_mr = 1 or 2) keeps whole units per CTA, where a second unit's
+  // A tiles would cost more than the balance gains
   const long nitems = nunits * S::NC;
   const long per = S::NC >= 12 ? nitems : nunits;
   const int g = (int)(per < tc.sms ? per : tc.sms);
@@ -847,21 +967,23 @@ size_t image_bytes_for(int m) {
 
 template <int MD, int D>
 cudaError_t apply_for(const TcOp& tc, const Level& L0, long count, const int* list, const uint32_t* slm,
-                      const float* v, const unsigned char* img, float tscale, int stages, cudaStream_t st) {
-  if (tc.m == 27) return run_apply<MD, D, 27>(tc, L0, count, list, slm, v, img, tscale, stages, st);
-  if (tc.m == 8) return run_apply<MD, D, 8>(tc, L0, count, list, slm, v, img, tscale, stages, st);
-  if (tc.m == 1) return run_apply<MD, D, 1>(tc, L0, count, list, slm, v, img, tscale, stages, st);
+                      const float* v, const unsigned char* img, float tscale, int stages, bool tri,
+                      cudaStream_t st) {
+  if (tc.m == 27) return run_apply<MD, D, 27>(tc, L0, count, list, slm, v, img, tscale, stages, tri, st);
+  if (tc.m == 8) return run_apply<MD, D, 8>(tc, L0, count, list, slm, v, img, tscale, stages, tri, st);
+  if (tc.m == 1) return run_apply<MD, D, 1>(tc, L0, count, list, slm, v, img, tscale, stages, tri, st);
   return cudaErrorInvalidValue;
 }
 
 template <int D>
 cudaError_t apply_mode(const TcOp& tc, const Level& L0, long count, const int* list, const uint32_t* slm,
-                       const float* v, const unsigned char* img, float tscale, int stages, cudaStream_t st) {
+                       const float* v, const unsigned char* img, float tscale, int stages, bool tri,
+                       cudaStream_t st) {
   switch (tc.mode) {
-    case kTF32: return apply_for<kTF32, D>(tc, L0, count, list, slm, v, img, tscale, stages, st);
-    case kBF16: return apply_for<kBF16, D>(tc, L0, count, list, slm, v, img, tscale, stages, st);
-    case kBF16X3: return apply_for<kBF16X3, D>(tc, L0, count, list, slm, v, img, tscale, stages, st);
-    case kF16X3: return apply_for<kF16X3, D>(tc, L0, count, list, slm, v, img, tscale, stages, st);
+    case kTF32: return apply_for<kTF32, D>(tc, L0, count, list, slm, v, img, tscale, stages, tri, st);
+    case kBF16: return apply_for<kBF16, D>(tc, L0, count, list, slm, v, img, tscale, stages, tri, st);
+    case kBF16X3: return apply_for<kBF16X3, D>(tc, L0, count, list, slm, v, img, tscale, stages, tri, st);
+    case kF16X3: return apply_for<kF16X3, D>(tc, L0, count, list, slm, v, img, tscale, stages, tri, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -895,9 +1017,7 @@ size_t image_bytes_mode(int mode, int m) {
 
 bool tc2_supported(int n) { return n >= 1 && n <= 3; }
 
-size_t tc2_image_bytes(int mode, int m, int dofs) {
-  return dofs == 24 ? image_bytes_mode<24>(mode, m) : image_bytes_mode<81>(mode, m);
-}
+size_t tc2_image_bytes(int mode, int m) { return image_bytes_mode<81>(mode, m); }
 
 size_t tc2_result_stride() { return 84; }  // floats per element of the result buffer (81 used)
 
@@ -911,18 +1031,8 @@ float tc2_table_scale(int mode, const double* tab_host, size_t count) {
   return (float)std::ldexp(1.0, ex2);
 }
 
-void launch_tc2_image(int mode, int m, int dofs, const double* tab, float tscale, unsigned char* img,
-                      cudaStream_t st) {
+void launch_tc2_image(int mode, int m, const double* tab, float tscale, unsigned char* img, cudaStream_t st) {
   const double tinv = 1.0 / (double)tscale;
-  if (dofs == 24) {
-    switch (mode) {
-      case kTF32: image_for<kTF32, 24>(m, tab, tinv, img, st); break;
-      case kBF16: image_for<kBF16, 24>(m, tab, tinv, img, st); break;
-      case kBF16X3: image_for<kBF16X3, 24>(m, tab, tinv, img, st); break;
-      default: image_for<kF16X3, 24>(m, tab, tinv, img, st); break;
-    }
-    return;
-  }
   switch (mode) {
     case kTF32: image_for<kTF32, 81>(m, tab, tinv, img, st); break;
     case kBF16: image_for<kBF16, 81>(m, tab, tinv, img, st); break;
@@ -933,16 +1043,31 @@ void launch_tc2_image(int mode, int m, int dofs, const double* tab, float tscale
 
 cudaError_t launch_tc2_apply(const TcOp& tc, const Level& L0, const float* v, cudaStream_t st, int part,
                              int stages) {
-  if (L0.el2 != nullptr) {  // mixed mesh: triquadratic elements with their slaved nodes, then trilinear ones
+  if (L0.el2 != nullptr) {  // mixed mesh: triquadratic elements with their slaved nodes, trilinear ones
+    const bool tri = part != 0 && (stages & 2) && L0.ne1 > 0;
+    // the whole operator: the trilinear products ride on the row packing
+    const bool fused = tri && part < 0 && (stages & 1) && L0.ne2 > 0;
     if (part != 1) {
-      cudaError_t e = apply_mode<81>(tc, L0, L0.ne2, L0.el2, L0.sl2, v, tc.img, tc.tscale, stages, st);
-      if (e != cudaSuccess || part == 0) return e;
+      const cudaError_t e = apply_mode<81>(tc, L0, L0.ne2, L0.el2, L0.sl2, v, tc.img, tc.tscale, stages, fused, st);
+      if (e != cudaSuccess) return e;
     }
-    return apply_mode<24>(tc, L0, L0.ne1, L0.el1, nullptr, v, tc.img1, tc.tscale1, stages, st);
+    if (tri && !fused) {
+      PackArgs pa{};
+      set_q1v(pa, tc, L0, v);
+      k_q1v_apply32<<<(int)q1v_blocks(tc, pa.E1), 32 * kQ1Warps, 0, st>>>(pa);
+    }
+    return cudaGetLastError();
   }
   if (part == 1) return cudaSuccess;  // no trilinear elements
   const long E = (long)L0.ex * L0.ey * L0.ez;
-  return apply_mode<81>(tc, L0, E, nullptr, nullptr, v, tc.img, tc.tscale, stages, st);
+  return apply_mode<81>(tc, L0, E, nullptr, nullptr, v, tc.img, tc.tscale, stages, false, st);
+}
+
+void launch_q1v_compact32(const Level& L0, const double* K64, float* K1v, cudaStream_t st) {
+  if (L0.ne1 <= 0) return;
+  long g = (L0.ne1 * kQ1Sym + 255) / 256;
+  if (g > 8192) g = 8192;
+  k_q1v_compact32<<<(int)g, 256, 0, st>>>(L0.ne1, L0.el1, K64, L0.sym ? 1 : 0, K1v);
 }
 
 size_t tc2_pack_bytes(int mode, long E) {

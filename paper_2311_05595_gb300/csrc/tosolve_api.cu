@@ -254,9 +254,9 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
   if (tc2) {  // weights, element results and the table image of the tensor-core level
     const size_t E0 = (size_t)d.nx * d.ny * d.nz;
     B += E0 * (P->m + tc2_result_stride() + 1) * 4 + tc2_pack_bytes(tc2_mode_of(d.precision), (long)E0) +
-         tc2_image_bytes(tc2_mode_of(d.precision), P->m) +
-         tc2_image_bytes(tc2_mode_of(d.precision), P->m, 24) + (size_t)P->m * 576 * 8 +
-         (size_t)P->lv[0].ndof * 4 + (size_t)P->lv[0].nn / 2;  // the mixed fold's raw assembly, vertex masks
+         tc2_image_bytes(tc2_mode_of(d.precision), P->m) + (size_t)P->m * 576 * 8 +
+         (size_t)P->lv[0].ndof * 4 + (size_t)P->lv[0].nn / 2 +  // the mixed fold's raw assembly, vertex masks
+         (E0 * kQ1Sym + 4) * 4;  // FP32 trilinear vertex blocks (at most every element trilinear)
   }
   P->bytes = B;
   return TOSOLVE_OK;
@@ -291,7 +291,7 @@ void free_all(tosolve_s* h) {
   F(h->base0); F(h->ecls); F(h->efix); F(h->xfix); F(h->ptab); F(h->ptab3);
   F(h->tab64); F(h->tabsym64); F(h->cmom64); F(h->KT32); F(h->w32); F(h->Ye); F(h->tcimg); F(h->Y2); F(h->Ke); F(h->Kec); F(h->Mom); F(h->Momc);
   F(h->inner.e); F(h->inner.ri); F(h->inner.pi); F(h->inner.qi);
-  F(h->el2); F(h->sl2); F(h->el1); F(h->tab64q1); F(h->tcyraw); F(h->tcvnb); F(h->tcimg1); F(h->tcpack); F(h->tcscale);
+  F(h->el2); F(h->sl2); F(h->el1); F(h->tab64q1); F(h->tcyraw); F(h->tck1v); F(h->tcvnb); F(h->tcpack); F(h->tcscale);
   F(h->lz); F(h->lmax);
   F(h->Ad); F(h->Wp); F(h->Vp); F(h->Pg); F(h->Ainv);
   F(h->u); F(h->r); F(h->p); F(h->q); F(h->f); F(h->tmpa); F(h->tmpb); F(h->part); F(h->ds);
@@ -797,15 +797,11 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
     CKC(cudaMemcpyAsync(tab.data(), h->tab64, tab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));
     const float tscale = tc2_table_scale(mode, tab.data(), tab.size());
-    launch_tc2_image(mode, P.m, 81, h->tab64, tscale, h->tcimg, st);
-    if (h->mixed) {  // trilinear elements: the degree-1 subcell table on their vertices
-      CKC(dalloc(h, &h->tcimg1, tc2_image_bytes(mode, P.m, 24)));
-      std::vector<double> t1((size_t)P.m * 576);
-      CKC(cudaMemcpyAsync(t1.data(), h->tab64q1, t1.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CKC(cudaStreamSynchronize(st));
-      h->tc.tscale1 = tc2_table_scale(mode, t1.data(), t1.size());
-      launch_tc2_image(mode, P.m, 24, h->tab64q1, h->tc.tscale1, h->tcimg1, st);
-      h->tc.img1 = h->tcimg1;
+    launch_tc2_image(mode, P.m, h->tab64, tscale, h->tcimg, st);
+    if (h->mixed) {
+      // trilinear elements: FP32 copies of their vertex blocks (k_q1v_apply32)
+      CKC(dalloc(h, &h->tck1v, (size_t)h->ne1 * kQ1Sym + 4));
+      h->tc.K1v = h->tck1v;
       // the node lattice's fold of the slaved nodes after assembly
       CKC(dalloc(h, &h->tcyraw, (size_t)h->lv[0].ndof));
       {
@@ -1080,6 +1076,7 @@ static tosolve_status refresh(tosolve_t h) {
       CK(cudaEventRecord(h->evj, h->st2));
       CK(cudaStreamWaitEvent(st, h->evj, 0));
     }
+    if (h->tck1v) launch_q1v_compact32(h->lv[0], h->lv[0].K64, h->tck1v, st);
     if (d.smoother == 1)  // lambda_max of every smoothing operator, then the Chebyshev coefficients
       launch_cheb_setup(vt_of(h), h->lv, L, h->tc, kChebLanczos, h->part, h->cnt, h->lz, h->lmax, st);
     CK(cudaGetLastError());
