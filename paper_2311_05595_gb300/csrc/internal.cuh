@@ -407,8 +407,7 @@ void launch_q2_coarse_elem(const Level& L, const double* w, int Dx, int Dy, cons
                            double* Mscr, double* Ke, cudaStream_t st);
 void launch_q2_dinv(bool fp64, const Level& L, const double* Ke, void* dinv, cudaStream_t st);
 void launch_q2_dense(const Level& L, const double* Ke, double* A, cudaStream_t st);
-// The FP32 copy of a level's element matrices (full 81 x 81 even where the
-// FP64 ones are packed).
+// The FP32 copy of a level's element matrices (in the FP64 ones' layout).
 void launch_elem_fp32(const Level& L, const double* K64, float* K32, cudaStream_t st);
 // Entries per element matrix of a degree >= 2 level.
 inline size_t elem_stride(const Level& L) {

@@ -1151,6 +1151,86 @@ __global__ void __launch_bounds__(96) k_q2_apply_sym(int ex, int ey, long E, int
   }
 }
 
+// The FP32 form of the packed apply (the preconditioner's copies): the same
+// two-stage ring of bulk copies, with u_e of the next element gathered while
+// this one is multiplied, and row a formed in column order c = 0 .. 80 (u_c
+// is then one broadcast read per warp): entry (min(a, c), max(a, c)) steps
+// by 80 - c along column a above the diagonal and by 1 along row a.
+__global__ void __launch_bounds__(96) k_q2_apply_sym32(int ex, int ey, long E, int Lx, int Ly,
+                                                      const float* __restrict__ Ke,
+                                                      const uint8_t* __restrict__ mask, const float* __restrict__ u,
+                                                      float* __restrict__ Y, const int* __restrict__ list,
+                                                      int* err) {
+  constexpr uint32_t kBytes = (uint32_t)(kPS2 * sizeof(float));
+  __shared__ __align__(128) float ks0[2][kPS2];
+  __shared__ float ue[2][kD];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bar[q])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const long nk = (long)blockIdx.x < E ? (E - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto elem_at = [&](long k) {
+    const long t = blockIdx.x + k * gridDim.x;
+    return list != nullptr ? (long)list[t] : t;
+  };
+  // u_e of element k (fixed DOFs as zero) into registers; whether any is free
+  auto gather = [&](long k, float& uv, bool& fr) {
+    uv = 0.f;
+    fr = false;
+    if (k < nk && tid < kD) {
+      const long e = elem_at(k);
+      const int exi = e % ex, eyi = (e / ex) % ey, ezi = e / ((long)ex * ey);
+      const long d = 3 * elem_node(exi, eyi, ezi, tid / 3, Lx, Ly) + tid % 3;
+      const float vd = u[d];
+      fr = mask[d] == 0;
+      uv = fr ? vd : 0.f;
+    }
+  };
+  if (tid == 0)
+    for (long k = 0; k < 2 && k < nk; ++k) sym_issue(ks0[k], Ke + elem_at(k) * (size_t)kPS2, kBytes, &bar[k]);
+  float uv;
+  bool fr;
+  gather(0, uv, fr);
+  if (tid < kD) ue[0][tid] = uv;
+  long k = 0;
+  for (; k < nk; ++k) {
+    const int st = (int)(k & 1);
+    const bool any = __syncthreads_or(fr) != 0;  // ue[st] is complete
+    float un;
+    bool fn;
+    gather(k + 1, un, fn);  // in flight during this element's products
+    const bool got = sym_wait(&bar[st], (uint32_t)((k >> 1) & 1));
+    if (__syncthreads_or(!got)) break;
+    if (any && tid < kD) {  // an element with every DOF fixed is skipped (its rows are identity rows)
+      const float* ks = ks0[st];
+      const float* uk = ue[st];
+      float acc = 0.f;
+      int idx = tid;  // (0, a)
+#pragma unroll
+      for (int c = 0; c < kD; ++c) {
+        acc = fmaf(ks[idx], uk[c], acc);
+        idx += c < tid ? 80 - c : 1;
+      }
+      Y[elem_at(k) * kD + tid] = acc;
+    }
+    if (tid < kD) ue[st ^ 1][tid] = un;  // read by element k - 1, finished before the barriers above
+    fr = fn;
+    __syncthreads();  // stage st is free
+    if (tid == 0 && k + 2 < nk) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      sym_issue(ks0[st], Ke + elem_at(k + 2) * (size_t)kPS2, kBytes, &bar[st]);
+    }
+  }
+  if (k < nk && tid == 0) {  // timed out: flag, then let the copies in flight land
+    atomicExch(err, 1);
+    for (long q = k; q < nk && q < k + 2; ++q) sym_wait(&bar[q & 1], (uint32_t)((q >> 1) & 1));
+  }
+}
+
 // Trilinear elements of a mixed mesh: their constrained 81 x 81 matrix is
 // T_e^T K T_e with every non-vertex node slaved to the vertices, which is
 // zero outside the 24 vertex DOFs, so the product needs only that block
@@ -1849,10 +1929,8 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
                   const void* dinv, double omega, int mode, void* out, int sms, cudaStream_t st,
                   const ChebStep* cs) {
   const ChebStep chs = cs ? *cs : ChebStep{};
-  // packed symmetric storage is the FP64 operator's; the FP32 copy is full
-  // (its apply streams the matrix, which is faster than the packed form's
-  // shared-memory phase)
-  const bool symK = L.sym && Ke == (const void*)L.K64;
+  // packed symmetric storage: the FP64 operator and its FP32 copy
+  const bool symK = L.sym && (Ke == (const void*)L.K64 || Ke == (const void*)L.K32);
   static std::once_flag sym_attr;  // the FP64 ring needs more than the default 48 KB
   std::call_once(sym_attr, [] {
     cudaFuncSetAttribute(k_q2_apply_sym<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kPS2 * 8);
@@ -1887,7 +1965,10 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
     if (L.el2 != nullptr) {  // mixed level 0: triquadratic list, then the trilinear vertex blocks
       long g2 = (long)sms * 16;
       if (g2 > L.ne2) g2 = L.ne2;
-      if (g2 >= 1 && symK)
+      if (g2 >= 1 && symK && std::is_same<T, float>::value)
+        k_q2_apply_sym32<<<(int)(g2 < 8L * sms ? g2 : 8L * sms), 96, 0, st>>>(L.ex, L.ey, L.ne2, L.Lx, L.Ly, (const float*)Ke, L.mask,
+                                                 (const float*)v, (float*)Y, L.el2, L.err);
+      else if (g2 >= 1 && symK)
         k_q2_apply_sym<T><<<(int)g2, 96, 2 * kPS2 * sizeof(op_t<T>), st>>>(
             L.ex, L.ey, L.ne2, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask, (const T*)v, (T*)Y, L.el2, L.err);
       else if (g2 >= 1)
@@ -1910,7 +1991,10 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
                                             (const T*)v, (const op_t<T>*)dinv, L.mask, (T)omega, mode,
                                             (T*)out, chs);
     } else {
-      if (symK)
+      if (symK && std::is_same<T, float>::value)  // 8 blocks of 27 KB per SM
+        k_q2_apply_sym32<<<(int)(ga < 8L * sms ? ga : 8L * sms), 96, 0, st>>>(L.ex, L.ey, E, L.Lx, L.Ly, (const float*)Ke, L.mask,
+                                                 (const float*)v, (float*)Y, nullptr, L.err);
+      else if (symK)
         k_q2_apply_sym<T><<<(int)ga, 96, 2 * kPS2 * sizeof(op_t<T>), st>>>(
             L.ex, L.ey, E, L.Lx, L.Ly, (const op_t<T>*)Ke, L.mask, (const T*)v, (T*)Y, nullptr, L.err);
       else
@@ -1926,23 +2010,8 @@ void launch_q2_op(int vt, const Level& L, const void* Ke, void* Y, const void* b
   else run(dfloat(0.f, 0.f));
 }
 
-// FP32 copy of a level's packed symmetric FP64 element matrices, expanded
-// to the full 81 x 81 (the FP32 apply streams the full matrix).
-__global__ void k_unpack32(long E, const double* __restrict__ Kp, float* __restrict__ Kf) {
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < E * kDD; t += (long)gridDim.x * blockDim.x) {
-    const long e = t / kDD;
-    const int ent = (int)(t % kDD);
-    Kf[t] = (float)Kp[e * kPS2 + sym2_idx(ent / kD, ent % kD)];
-  }
-}
-
 void launch_elem_fp32(const Level& L, const double* K64, float* K32, cudaStream_t st) {
-  const long E = (long)L.ex * L.ey * L.ez;
-  if (L.sym) {
-    k_unpack32<<<grid_for2(E * kDD, 16 * 4096), 256, 0, st>>>(E, K64, K32);
-    return;
-  }
-  launch_to_fp32((size_t)E * elem_stride(L), K64, K32, st);
+  launch_to_fp32((size_t)L.ex * L.ey * L.ez * elem_stride(L), K64, K32, st);
 }
 
 void launch_q1v_elem(const Level& L, int n, const double* w, int Dx, int Dy, const double* tab1, double* Ke,

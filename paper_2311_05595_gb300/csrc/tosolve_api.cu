@@ -201,7 +201,7 @@ tosolve_status plan_for(const tosolve_desc* dp, Plan* P, std::string* why) {
       v.s64 = v.s32 = false;
       B += v.ndof + v.ndof * 8 + 4 * v.ndof * tsz;  // mask, dinv64, b v r z
       if (fp32) B += v.ndof * 4;
-      B += coarsest ? E * dd * 8 : E * (dd * 8 + (fp32 && !(tc2 && l == 0) ? (kl == 3 ? kDD3 : kDD2) * 4 : 0));
+      B += coarsest ? E * dd * 8 : E * dd * (8 + (fp32 && !(tc2 && l == 0) ? 4 : 0));
       if (d.family == 1 && (!coarsest || l == 0)) {  // compact copies of the serendipity levels
         const size_t dp = kl == 3 ? 96 : 60;
         B += E * dp * dp * (8 + (fp32 && !coarsest ? 4 : 0));
@@ -626,8 +626,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
       if (l + 1 < P.L || l == 0) CKC(dalloc(h, &L.K64, E * dd));  // level 0: the CG's K
       if (l == 0 && elem_q1 != nullptr)  // trilinear slots: only their vertex blocks are ever written
         CKC(cudaMemsetAsync(L.K64, 0, E * dd * sizeof(double), st));
-      if (l + 1 < P.L && fp32 && !(tc2 && l == 0))  // tensor cores: no level-0 copy; FP32 copies are full
-        CKC(dalloc(h, &L.K32, E * (L.k == 3 ? (size_t)kDD3 : (size_t)kDD2)));
+      if (l + 1 < P.L && fp32 && !(tc2 && l == 0)) CKC(dalloc(h, &L.K32, E * dd));  // tensor cores: no level-0 copy
       if (h->d.family == 1) {  // compact copies for the apply
         const size_t dp = L.k == 3 ? 96 : 60;
         if (L.K64) CKC(dalloc(h, &L.Kc64, E * dp * dp));
