@@ -1367,9 +1367,23 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
     int e0[3], e1[3];
     const int co[3] = {i, j, l}, ext[3] = {ex, ey, ez};
     for (int ax = 0; ax < 3; ++ax) elems_of<K>(co[ax], ext[ax], e0[ax], e1[ax]);
+    // the output's vector inputs first, in flight together with the element loads
+    constexpr bool kCheb = std::is_same<T, float>::value || std::is_same<T, double>::value;
+    uint8_t mk[3];
+    T vv[3], bb[3], dp[3];
+    op_t<T> di[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long d = 3 * node + c;
+      mk[c] = mask[d];
+      vv[c] = v[d];
+      bb[c] = mode != 2 ? b[d] : T(0);
+      di[c] = mode == 1 || mode == 3 ? dinv[d] : op_t<T>(0);
+      dp[c] = vv[c];
+      if constexpr (kCheb)
+        if (mode == 3 && cs.dprev) dp[c] = static_cast<const T*>(cs.dprev)[d];
+    }
     T y[3] = {T(0), T(0), T(0)};
-    // a node with all DOFs fixed does not use y (its elements may be skipped)
-    const bool all_fixed = mask[3 * node] && mask[3 * node + 1] && mask[3 * node + 2];
     // the (at most) 2 x 2 x 2 elements, unrolled with predicates so that all
     // their loads are in flight together; summed in the order z, y, x
 #pragma unroll
@@ -1379,7 +1393,7 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
 #pragma unroll
         for (int kx = 0; kx < 2; ++kx) {
           const int ex_ = e0[0] + kx, ey_ = e0[1] + ky, ez_ = e0[2] + kz;
-          if (all_fixed || ex_ > e1[0] || ey_ > e1[1] || ez_ > e1[2]) continue;
+          if (ex_ > e1[0] || ey_ > e1[1] || ez_ > e1[2]) continue;
           const long e = ex_ + (long)ex * (ey_ + (long)ey * ez_);
           const int a = (i - K * ex_) + NA * ((j - K * ey_) + NA * (l - K * ez_));
           const T* Ye = Y + e * kD + 3 * a;
@@ -1390,19 +1404,17 @@ __global__ void k_q2_gather(int Lx, int Ly, int Lz, int ex, int ey, int ez, cons
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long d = 3 * node + c;
-      const T yc = mask[d] ? v[d] : y[c];
+      const T yc = mk[c] ? vv[c] : y[c];
       if (mode == 0) {
-        out[d] = b[d] - yc;
+        out[d] = bb[c] - yc;
       } else if (mode == 1) {
-        out[d] = v[d] + omega * dinv[d] * (b[d] - yc);
+        out[d] = vv[c] + omega * di[c] * (bb[c] - yc);
       } else if (mode == 3) {
-        if constexpr (std::is_same<T, float>::value || std::is_same<T, double>::value) {
+        if constexpr (kCheb) {
           const T* co = static_cast<const T*>(cs.coef);
           const T c1 = cs.ci < 0 ? T(0) : co[2 * cs.ci], c2 = cs.ci < 0 ? T(1) : co[2 * cs.ci + 1];
-          const T vd = v[d];
-          const T dp = cs.dprev ? static_cast<const T*>(cs.dprev)[d] : vd;
-          const T o = vd + c1 * dp + c2 * dinv[d] * (b[d] - yc);
-          static_cast<T*>(cs.dout)[d] = o - vd;
+          const T o = vv[c] + c1 * dp[c] + c2 * di[c] * (bb[c] - yc);
+          static_cast<T*>(cs.dout)[d] = o - vv[c];
           out[d] = o;
         }
       } else {
