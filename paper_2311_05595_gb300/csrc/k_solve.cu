@@ -711,6 +711,16 @@ __global__ void k_cg_update(int nn, double* __restrict__ u, double* __restrict__
 // flexible CG, whose FP64 operator apply then runs far fewer times.  The
 // inner coefficients use the same flexible form as the outer loop.
 
+// The vector kernels of the inner iteration stride over the DOFs four at a
+// time, loading all four before any store, so that each thread has four
+// independent loads in flight (the reductions' grids are capped at kMaxPart
+// blocks, about fourteen DOFs per thread on a 1.6 M DOF level); a thread
+// visits its DOFs in the same order as a plain grid-stride loop.
+constexpr int kU = 4;
+#define DOF_LOOP_U(ndof)                                                               \
+  for (long d0 = blockIdx.x * (long)blockDim.x + threadIdx.x, sd = (long)gridDim.x * blockDim.x; \
+       d0 < (ndof); d0 += kU * sd)
+
 // ri = b0 (the outer residual in FP32); e = 0.
 __global__ void k_in_init(long n, const float* __restrict__ b0, float* __restrict__ ri, float* __restrict__ e) {
   DOF_LOOP(n) {
@@ -727,10 +737,21 @@ __global__ void k_in_rz(long n, const float* __restrict__ ri, const float* __res
   // each thread's few dozen terms in FP32 (FP64 issue is scarce here), the
   // block and grid sums in FP64; the inner CG runs in FP32 throughout
   float fa = 0.f, fb = 0.f;
-  DOF_LOOP(n) {
-    const float zv = z[d];
-    fa = fmaf(ri[d], zv, fa);
-    if (!first) fb = fmaf(zv, qi[d], fb);
+  DOF_LOOP_U(n) {
+    float zv[kU], rv[kU], qv[kU];
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const long d = d0 + q * sd;
+      zv[q] = d < n ? z[d] : 0.f;
+      rv[q] = d < n ? ri[d] : 0.f;
+      qv[q] = d < n && !first ? qi[d] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      if (d0 + q * sd >= n) break;
+      fa = fmaf(rv[q], zv[q], fa);
+      if (!first) fb = fmaf(zv[q], qv[q], fb);
+    }
   }
   double a = block_sum((double)fa);
   double b = block_sum((double)fb);
@@ -752,7 +773,20 @@ __global__ void k_in_rz(long n, const float* __restrict__ ri, const float* __res
 __global__ void k_in_dir(long n, const float* __restrict__ z, float* __restrict__ pi, int first,
                          const DevState* __restrict__ ds) {
   const float beta = (float)ds->in_beta;
-  DOF_LOOP(n) pi[d] = first ? z[d] : z[d] + beta * pi[d];
+  DOF_LOOP_U(n) {
+    float zv[kU], pv[kU];
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const long d = d0 + q * sd;
+      zv[q] = d < n ? z[d] : 0.f;
+      pv[q] = d < n && !first ? pi[d] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const long d = d0 + q * sd;
+      if (d < n) pi[d] = first ? zv[q] : zv[q] + beta * pv[q];
+    }
+  }
 }
 
 // sigma = pi^T qi; the last block forms alpha = rho / sigma.  A
@@ -762,7 +796,20 @@ __global__ void k_in_dir(long n, const float* __restrict__ z, float* __restrict_
 __global__ void k_in_pq(long n, const float* __restrict__ pi, const float* __restrict__ qi, int first,
                         double* part, DevState* __restrict__ ds, unsigned* cnt) {
   float fs = 0.f;
-  DOF_LOOP(n) fs = fmaf(pi[d], qi[d], fs);
+  DOF_LOOP_U(n) {
+    float pv[kU], qv[kU];
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const long d = d0 + q * sd;
+      pv[q] = d < n ? pi[d] : 0.f;
+      qv[q] = d < n ? qi[d] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      if (d0 + q * sd >= n) break;
+      fs = fmaf(pv[q], qv[q], fs);
+    }
+  }
   const double s = block_sum((double)fs);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   if (!last_block(cnt)) return;
@@ -784,16 +831,32 @@ __global__ void k_in_update(long n, float* __restrict__ e, float* __restrict__ r
                             float omega, float* __restrict__ v0, float* __restrict__ z0, int last,
                             const DevState* __restrict__ ds) {
   const float a = (float)ds->in_alpha;
-  DOF_LOOP(n) {
-    const float ev = e[d] + a * pi[d];
-    if (last) {
-      z0[d] = ev;
-    } else {
-      e[d] = ev;
-      const float rv = ri[d] - a * qi[d];
-      ri[d] = rv;
-      b0[d] = rv;
-      v0[d] = omega * dinv0[d] * rv;
+  DOF_LOOP_U(n) {
+    float ev[kU], pv[kU], rv[kU], qv[kU], dv[kU];
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const long d = d0 + q * sd;
+      const bool in = d < n;
+      ev[q] = in ? e[d] : 0.f;
+      pv[q] = in ? pi[d] : 0.f;
+      rv[q] = in && !last ? ri[d] : 0.f;
+      qv[q] = in && !last ? qi[d] : 0.f;
+      dv[q] = in && !last ? dinv0[d] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const long d = d0 + q * sd;
+      if (d >= n) break;
+      const float evn = ev[q] + a * pv[q];
+      if (last) {
+        z0[d] = evn;
+      } else {
+        e[d] = evn;
+        const float r = rv[q] - a * qv[q];
+        ri[d] = r;
+        b0[d] = r;
+        v0[d] = omega * dv[q] * r;
+      }
     }
   }
 }
@@ -1147,6 +1210,7 @@ void launch_inner_pcg(Level* lv, int L, double omega, const double* Ainv, const 
   Level& L0 = lv[0];
   const long n = L0.ndof;
   const int g = parts_for(L0.nn);  // blocks of the reductions (<= kMaxPart partials)
+  const int gv = (int)((n + kU * kRowThreads - 1) / (kU * kRowThreads));  // the others: one pass
   float* b0 = (float*)L0.b;
   float* v0 = (float*)L0.v;
   float* z0 = (float*)L0.z;
@@ -1155,7 +1219,7 @@ void launch_inner_pcg(Level* lv, int L, double omega, const double* Ainv, const 
     const int first = it == 0, last = it == in.its - 1;
     vcycle_rec<float>(lv, 0, L, (float)omega, Ainv, tc, st, nullptr);  // z0 = M^-1 b0
     k_in_rz<<<g, kRowThreads, 0, st>>>(n, in.ri, z0, in.qi, first, part_a, part_b, ds, cnt);
-    k_in_dir<<<g, kRowThreads, 0, st>>>(n, z0, in.pi, first, ds);
+    k_in_dir<<<gv, kRowThreads, 0, st>>>(n, z0, in.pi, first, ds);
     if (tc.on && tc.deg >= 2) {  // qi = A pi on the tensor cores
       launch_tc2_apply(tc, L0, in.pi, st);
       launch_tc2_gather(L0, tc.Y2, in.pi, in.pi, L0.dinv32, 0.f, 2, in.qi, st);
@@ -1163,8 +1227,8 @@ void launch_inner_pcg(Level* lv, int L, double omega, const double* Ainv, const 
       launch_q2_op(kVtF32, L0, L0.K32, L0.Y, nullptr, in.pi, nullptr, 0.0, 2, in.qi, L0.sms, st);
     }
     k_in_pq<<<g, kRowThreads, 0, st>>>(n, in.pi, in.qi, first, part_a, ds, cnt);
-    k_in_update<<<g, kRowThreads, 0, st>>>(n, in.e, in.ri, in.pi, in.qi, b0, L0.dinv32, (float)omega, v0, z0, last,
-                                           ds);
+    k_in_update<<<gv, kRowThreads, 0, st>>>(n, in.e, in.ri, in.pi, in.qi, b0, L0.dinv32, (float)omega, v0, z0,
+                                            last, ds);
   }
 }
 
