@@ -605,8 +605,12 @@ def tc_roofline(wl: Workload, label: str) -> dict:
     flops = 2.0 * m * 81 * 81 * E2
     kstep = 8 if name == "tf32" else 16
     kp = (81 + kstep - 1) // kstep * kstep
-    mp = 1 if m <= 1 else next(v for v in (2, 4, 8, 16, 32) if m <= v)
-    rows = 81 * mp
+    # stacked rows the MMAs run over: chunks of 128 // m outputs (m rows each)
+    # padded to a multiple of 16, the last chunk's outputs likewise
+    opc = 128 // m if m < 128 else 1
+    nch = (opc * m + 15) // 16 * 16
+    nc = (81 + opc - 1) // opc
+    rows = (nc - 1) * nch + ((81 - (nc - 1) * opc) * m + 15) // 16 * 16
     products = 3 if name in ("bf16x3", "f16x3") else 1
     units = (E2 + 255) // 256
     executed = 2.0 * products * kp * rows * units * 256

@@ -87,7 +87,6 @@ struct Opnd {
   static constexpr int kEs = MD == kTF32 ? 4 : 2;          // bytes per element
   static constexpr int kKc = 16 / kEs;                     // elements per 16-byte core-matrix row
   static constexpr int kKstep = MD == kTF32 ? 8 : 16;      // K of one MMA
-  static constexpr int kNch = 128;                         // stacked rows per chunk (2 x 2 x 128 TMEM columns)
   static constexpr int kStages = MD == kBF16 ? 3 : 2;      // B ring
   static constexpr int kParts = kSplit ? 2 : 1;            // hi (and lo) K-slices per row
   static constexpr int kProducts = kSplit ? 3 : 1;
@@ -95,28 +94,33 @@ struct Opnd {
   static constexpr uint32_t kFmt = MD == kTF32 ? 2u : (MD == kF16X3 ? 0u : 1u);
 };
 
-// Stacked rows are DOF-major: row MP r + i holds row r of subcell i (zero
-// for i >= M), with MP = M rounded up to a divisor of 32, so that every
-// 32-column group of an accumulator holds 32 / MP complete outputs and the
-// epilogue is the same short loop for every group.
+// Stacked rows are DOF-major and unpadded: chunk c holds the OPC outputs
+// r = c OPC + o (OPC = 128 / M, at most 128), output o's M subcell rows at
+// columns [M o, M o + M) of the chunk, then zero rows up to NCH (a multiple
+// of 16, the MMA's N).  Every accumulator has a 128-column TMEM slot.  Where
+// M divides 32 every 32-column group holds whole outputs; otherwise (M = 27:
+// four outputs in 112 columns instead of one per 32) an output may straddle
+// two groups and the epilogue keeps a partial sum per output of the chunk.
 template <int MD, int D, int M>
 struct Shape {
   using O = Opnd<MD>;
   static constexpr int KP = (D + O::kKstep - 1) / O::kKstep * O::kKstep;  // padded K of one part
   static constexpr int KR = KP * O::kParts;                                 // K extent of a row
-  static constexpr int MP = M <= 1 ? 1 : (M <= 2 ? 2 : (M <= 4 ? 4 : (M <= 8 ? 8 : (M <= 16 ? 16 : 32))));
-  static constexpr int OPG = 32 / MP;                                       // outputs per 32 columns
-  static constexpr int ROWS = D * MP;                                       // stacked rows
-  static constexpr int NCH = O::kNch;
-  static constexpr int NC = (ROWS + NCH - 1) / NCH;                         // chunks
-  static constexpr int LASTN = ROWS - (NC - 1) * NCH;
+  static constexpr int OPC = M >= 128 ? 1 : 128 / M;                        // outputs per chunk
+  static constexpr int NCH = (OPC * M + 15) / 16 * 16;                      // rows of a chunk (MMA N)
+  static constexpr int NC = (D + OPC - 1) / OPC;                            // chunks
+  static constexpr int LASTO = D - (NC - 1) * OPC;                          // outputs of the last
+  static constexpr int LASTN = LASTO * M;
   static constexpr int LASTNP = (LASTN + 15) / 16 * 16;                     // MMA N of the last
+  static constexpr int NG = (NCH + 31) / 32;                                // 32-column groups of a chunk
+  static constexpr bool kWhole = 32 % M == 0;                               // groups hold whole outputs
   static constexpr int KS = KP / O::kKstep;                                 // MMAs of one product
   static constexpr uint32_t SBO = (uint32_t)(KR / O::kKc) * 128u;
   static constexpr uint32_t ABYTES = (uint32_t)kTm * KR * O::kEs;
   static constexpr uint32_t BBYTES = (uint32_t)NCH * KR * O::kEs;
   static constexpr size_t SMEM = (size_t)kPair * ABYTES + (size_t)O::kStages * BBYTES;
 };
+constexpr int kAccCols = 128;  // TMEM columns of one accumulator slot
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -501,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
   using O = Opnd<MD>;
   constexpr int NS = O::kStages;
   static_assert(kThreads == 6 * 32, "one warp per role: producer, MMA, 4 epilogue");
-  static_assert(2 * 2 * S::NCH <= kTmemCols, "two accumulator buffers of a tile pair");
+  static_assert(S::NCH <= kAccCols && 2 * 2 * kAccCols <= kTmemCols, "two accumulator buffers of a tile pair");
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                        // the pair's two A tiles
   unsigned char* sB = smem + kPair * S::ABYTES;    // NS x BBYTES
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
           const uint32_t bo = bbase + (uint32_t)s * S::BBYTES;
 #pragma unroll
           for (int tt = 0; tt < kPair; ++tt) {
-            const uint32_t dt = tmem + (uint32_t)(acc * 2 * S::NCH + tt * S::NCH);
+            const uint32_t dt = tmem + (uint32_t)(acc * 2 * kAccCols + tt * kAccCols);
             const uint32_t ao = abase + (uint32_t)tt * S::ABYTES;
 #pragma unroll
             for (int t = 0; t < O::kProducts * S::KS; ++t) {
@@ -676,22 +680,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int cc = c;
-        const int ng = cc == S::NC - 1 ? (S::LASTN + 31) / 32 : S::NCH / 32;
+        const int ng = cc == S::NC - 1 ? (S::LASTN + 31) / 32 : S::NG;
 #pragma unroll
         for (int tt = 0; tt < kPair; ++tt) {
+          const uint32_t ta = tl + (uint32_t)(acc * 2 * kAccCols + tt * kAccCols);
+          if constexpr (S::kWhole) {
 #pragma unroll 1
-          for (int g = 0; g < ng; ++g) {
-            uint32_t qv[32];
-            tmem_ld32(tl + (uint32_t)(acc * 2 * S::NCH + tt * S::NCH + 32 * g), qv);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int r0 = (cc * S::NCH + 32 * g) / S::MP;
+            for (int g = 0; g < ng; ++g) {
+              uint32_t qv[32];
+              tmem_ld32(ta + 32 * g, qv);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int o = 0; o < S::OPG; ++o) {
-              float v = 0.f;
+              for (int o = 0; o < 32 / M; ++o) {
+                float v = 0.f;
 #pragma unroll
-              for (int i = 0; i < M; ++i) v = fmaf(w[tt][i], __uint_as_float(qv[o * S::MP + i]), v);
-              const int r = r0 + o;
-              if (live[tt] && r < D) a.Y[(long)Elem<D>::out(r) * a.Ey + e[tt]] = v;
+                for (int i = 0; i < M; ++i) v = fmaf(w[tt][i], __uint_as_float(qv[o * M + i]), v);
+                const int r = cc * S::OPC + (32 * g) / M + o;
+                if (live[tt] && r < D) a.Y[(long)Elem<D>::out(r) * a.Ey + e[tt]] = v;
+              }
+            }
+          } else {
+            // partial sums of the chunk's outputs, each over i = 0 .. M-1 in order
+            float part[S::OPC];
+#pragma unroll
+            for (int o = 0; o < S::OPC; ++o) part[o] = 0.f;
+#pragma unroll
+            for (int g = 0; g < S::NG; ++g) {
+              if (g < ng) {
+                uint32_t qv[32];
+                tmem_ld32(ta + 32 * g, qv);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                  const int col = 32 * g + t;
+                  if (col < S::OPC * M) part[col / M] = fmaf(w[tt][col % M], __uint_as_float(qv[t]), part[col / M]);
+                }
+              }
+            }
+#pragma unroll
+            for (int o = 0; o < S::OPC; ++o) {
+              const int r = cc * S::OPC + o;
+              if (live[tt] && r < D) a.Y[(long)Elem<D>::out(r) * a.Ey + e[tt]] = part[o];
             }
           }
         }
@@ -712,12 +741,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2_apply(Tc2Args a) {
 }
 
 // The stacked table in the shared-memory image of its chunks: chunk c, row
-// n (stacked row c * nch + n = mp R + i: row R of subcell i, zero for the
-// padding subcells i >= m), K column k (an element DOF; the subcell
-// matrices are symmetric); zero padding beyond the table.  Single modes round once (TF32 to nearest with ties away, BF16 to
+// n = m o + i (o < opc) is row R = c opc + o of subcell i, rows n >= m opc
+// and R >= D are zero; K column k (an element DOF; the subcell matrices are
+// symmetric); zero padding beyond the table.  Single modes round once (TF32 to nearest with ties away, BF16 to
 // nearest even); split modes store hi in columns [0, kp) and lo in
 // [kp, 2 kp), FP16 after scaling the table by tinv (a power of two).
-__global__ void k_tc2_image(int mode, int D, int m, int mp, int nch, int kp, int parts, int kc, uint32_t sbo,
+__global__ void k_tc2_image(int mode, int D, int m, int opc, int nch, int kp, int parts, int kc, uint32_t sbo,
                             double tinv, const double* __restrict__ tab, unsigned char* __restrict__ img,
                             long total) {
   const int es = mode == kTF32 ? 4 : 2;
@@ -726,10 +755,9 @@ __global__ void k_tc2_image(int mode, int D, int m, int mp, int nch, int kp, int
     const int k = (int)(t % kp);
     const long rowg = t / kp;
     const int c = (int)(rowg / nch), n = (int)(rowg % nch);
-    const long gr = (long)c * nch + n;
     double x = 0.0;
-    const long R = gr / mp, i = gr % mp;  // DOF-major: row mp R + i is row R of subcell i
-    if (R < D && i < m && k < D) x = tab[(i * D + R) * D + k];
+    const int R = c * opc + n / m, i = n % m;
+    if (n < m * opc && R < D && k < D) x = tab[((long)i * D + R) * D + k];
     auto at = [&](int kk) {
       return (size_t)c * nch * kr * es + (size_t)(n >> 3) * sbo + (size_t)(kk / kc) * 128 + (size_t)(n & 7) * 16 +
              (size_t)(kk % kc) * es;
@@ -988,18 +1016,22 @@ cudaError_t apply_mode(const TcOp& tc, const Level& L0, long count, const int* l
   }
 }
 
-template <int MD, int D>
-void image_for(int m, const double* tab, double tinv, unsigned char* img, cudaStream_t st) {
-  using S = Shape<MD, D, 1>;  // the per-row layout does not depend on M
+template <int MD, int D, int M>
+void image_for_m(const double* tab, double tinv, unsigned char* img, cudaStream_t st) {
+  using S = Shape<MD, D, M>;
   using O = Opnd<MD>;
-  const size_t bytes = image_bytes_for<MD, D>(m);
   // one thread per (chunk row, K column of one part)
-  const long total = (long)(bytes / O::kEs / O::kParts);
+  const long total = (long)S::NC * S::NCH * S::KP;
   long g = (total + 255) / 256;
   if (g > 4096) g = 4096;
-  const int mp = m <= 1 ? 1 : (m <= 8 ? 8 : 32);
-  k_tc2_image<<<(int)g, 256, 0, st>>>(MD, D, m, mp, O::kNch, S::KP, O::kParts, O::kKc, S::SBO, tinv, tab, img,
+  k_tc2_image<<<(int)g, 256, 0, st>>>(MD, D, M, S::OPC, S::NCH, S::KP, O::kParts, O::kKc, S::SBO, tinv, tab, img,
                                       total);
+}
+template <int MD, int D>
+void image_for(int m, const double* tab, double tinv, unsigned char* img, cudaStream_t st) {
+  if (m == 27) image_for_m<MD, D, 27>(tab, tinv, img, st);
+  else if (m == 8) image_for_m<MD, D, 8>(tab, tinv, img, st);
+  else if (m == 1) image_for_m<MD, D, 1>(tab, tinv, img, st);
 }
 
 template <int D>
