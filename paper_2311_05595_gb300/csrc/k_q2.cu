@@ -443,21 +443,8 @@ __device__ __forceinline__ long elem_node(int exi, int eyi, int ezi, int a, int 
 }
 
 // Parent vertices of local node a of a 27-node element (the corners of the
-// edge, face or cell whose midpoint a is); returns how many.
-__device__ __forceinline__ int local_parents(int a, int par[8]) {
-  const int ax = a % 3, ay = (a / 3) % 3, az = a / 9;
-  const int xs[2] = {ax == 1 ? 0 : ax, ax == 1 ? 2 : ax};
-  const int ys[2] = {ay == 1 ? 0 : ay, ay == 1 ? 2 : ay};
-  const int zs[2] = {az == 1 ? 0 : az, az == 1 ? 2 : az};
-  const int nx = ax == 1 ? 2 : 1, ny = ay == 1 ? 2 : 1, nz = az == 1 ? 2 : 1;
-  int k = 0;
-  for (int c = 0; c < nz; ++c)
-    for (int b = 0; b < ny; ++b)
-      for (int q = 0; q < nx; ++q) par[k++] = xs[q] + 3 * (ys[b] + 3 * zs[c]);
-  return k;
-}
-
-// The same as a table in constant memory (read uniformly by a warp).
+// edge, face or cell whose midpoint a is), as a table in constant memory
+// (read uniformly by a warp).
 struct ParentTab {
   signed char p[27][8];
   unsigned char n[27];
@@ -493,18 +480,26 @@ __constant__ ParentTab c_parents = make_parent_tab();
 // moments by z-slices of cells (x, then y, then accumulated over z in a
 // fixed order), then for the six pairs s <= t the contractions over
 // alpha_z, alpha_y, alpha_x, then the 81 x 81 assembly (F^ts_ab = F^st_ba).
-// About 6.5e4 FP64 FMAs per element instead of 27 x 6561 (subcell sum) or
-// 125 x 6561 (moment basis).  Block of 256 threads per element.
+// About 6.5e4 FMAs per element instead of 27 x 6561 (subcell sum) or
+// 125 x 6561 (moment basis).  Only the moments are formed in FP64: FP64
+// issues at 1/64 of the FP32 rate here, so the rest runs on the FP32 pipes
+// in float pairs (about 48 significant bits).  The coefficients c are
+// dyadic rationals, exact in FP32, so the three contractions are
+// compensated dot products (Dot2) of FP32 coefficients with float pairs;
+// the slaved-node congruence (weights 1/2, 1/4, 1/8: exact scalings) and
+// the assembly with lambda, mu and h/2 follow in float-pair arithmetic,
+// each entry rounded to FP64 once.  Block of 256 threads per element.
 constexpr int kSfMaxN = 64;
 struct SfSmem {
-  double cf[4][kP][9];          // c_tau(p)[x * 3 + y], tau = 2 m + n
+  float cf[4][kP][9];           // c_tau(p)[x * 3 + y], tau = 2 m + n (exact)
   double mu[kP][kSfMaxN];       // mu_p(k): integral of xi^p over interval k
   double S1[kSfMaxN][kP];       // one z-slice summed along x
   double S2[kP * kP];           // the same slice summed along x and y
   double M[kNM];                // moments, alpha = ax + 5 (ay + 5 az)
-  double G[4][kP * kP][9];      // contracted over alpha_z, per z-type
-  double H[6][kP][81];          // contracted over alpha_y, per pair
-  double F[6][729];             // F^st, a = ax + 3 (ay + 3 az), entry a * 27 + b
+  dfloat Md[kNM];               // the same as float pairs
+  dfloat G[4][kP * kP][9];      // contracted over alpha_z, per z-type
+  dfloat H[6][kP][81];          // contracted over alpha_y, per pair
+  dfloat F[6][729];             // F^st, a = ax + 3 (ay + 3 az), entry a * 27 + b
 };
 __device__ __forceinline__ int sf_pair(int s, int t) {  // s <= t: 00 11 22 01 02 12
   return s == t ? s : (s == 0 ? (t == 1 ? 3 : 4) : 5);
@@ -526,12 +521,13 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
     double c = 0.0;
     for (int r = 0; r < 3; ++r)
       if (p - r >= 0 && p - r < 3) c += u[r] * v[p - r];
-    S.cf[tau][p][xy] = c;
+    S.cf[tau][p][xy] = (float)c;
   }
   for (int t = tid; t < kP * N; t += nt) S.mu[t / N][t % N] = mono_int(t / N, t % N, N);
   const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   const double mu = 1.0 / (2.0 * (1.0 + nu));
   const double hh = 0.5 * h;
+  const dfloat lamd(lam), mud(mu), hhd(hh);
   __syncthreads();
   for (long idx = blockIdx.x; idx < E; idx += gridDim.x) {
     const long e = list ? (long)list[idx] : idx;
@@ -560,12 +556,14 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
       for (int q = tid; q < kNM; q += nt) S.M[q] += S.S2[q % (kP * kP)] * S.mu[q / (kP * kP)][c];
       __syncthreads();
     }
+    for (int q = tid; q < kNM; q += nt) S.Md[q] = dfloat(S.M[q]);
+    __syncthreads();
     // ---- over alpha_z: G[tz][ax + 5 ay][az * 3 + bz] ----
     for (int t = tid; t < 4 * kP * kP * 9; t += nt) {
       const int tz = t / (kP * kP * 9), xy = (t / 9) % (kP * kP), zz = t % 9;
-      double acc = 0.0;
-      for (int pz = 0; pz < kP; ++pz) acc += S.M[xy + kP * kP * pz] * S.cf[tz][pz][zz];
-      S.G[tz][xy][zz] = acc;
+      Dot2 acc;
+      for (int pz = 0; pz < kP; ++pz) acc.add(S.cf[tz][pz][zz], S.Md[xy + kP * kP * pz]);
+      S.G[tz][xy][zz] = acc.value();
     }
     __syncthreads();
     // ---- over alpha_y: H[pair][ax][(ay * 3 + by) * 9 + az * 3 + bz] ----
@@ -574,9 +572,9 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
       const int s = pr < 3 ? pr : (pr == 5 ? 1 : 0), tt = pr < 3 ? pr : (pr == 3 ? 1 : 2);
       const int ty = 2 * (s == 1) + (tt == 1), tz = 2 * (s == 2) + (tt == 2);
       const int yy = yz / 9, zz = yz % 9;
-      double acc = 0.0;
-      for (int py = 0; py < kP; ++py) acc += S.cf[ty][py][yy] * S.G[tz][px + kP * py][zz];
-      S.H[pr][px][yz] = acc;
+      Dot2 acc;
+      for (int py = 0; py < kP; ++py) acc.add(S.cf[ty][py][yy], S.G[tz][px + kP * py][zz]);
+      S.H[pr][px][yz] = acc.value();
     }
     __syncthreads();
     // ---- over alpha_x: F[pair][a * 27 + b] ----
@@ -586,9 +584,9 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
       const int tx = 2 * (s == 0) + (tt == 0);
       const int xx = (a % 3) * 3 + (b % 3);
       const int yz = ((a / 3) % 3 * 3 + (b / 3) % 3) * 9 + (a / 9) * 3 + (b / 9);
-      double acc = 0.0;
-      for (int px = 0; px < kP; ++px) acc += S.cf[tx][px][xx] * S.H[pr][px][yz];
-      S.F[pr][ab] = acc;
+      Dot2 acc;
+      for (int px = 0; px < kP; ++px) acc.add(S.cf[tx][px][xx], S.H[pr][px][yz]);
+      S.F[pr][ab] = acc.value();
     }
     __syncthreads();
     // ---- slaved nodes (mixed meshes): T^T K T = the assembly of T_n^T F T_n ----
@@ -599,24 +597,26 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
     const unsigned sm = slaved;
     if (sm) {
       for (int t = tid; t < 6 * 27; t += nt) {
-        double* row = &S.F[t / 27][(t % 27) * 27];
+        dfloat* row = &S.F[t / 27][(t % 27) * 27];
         for (int a = 0; a < kNE; ++a) {
           if (!((sm >> a) & 1u)) continue;  // uniform across the block
           const int np = c_parents.n[a];
-          const double v = row[a] * (1.0 / np);
+          const float sc = 1.f / (float)np;  // a power of two: the scaled pair is exact
+          const dfloat v(row[a].hi * sc, row[a].lo * sc);
           for (int q = 0; q < np; ++q) row[c_parents.p[a][q]] += v;
-          row[a] = 0.0;
+          row[a] = dfloat(0.f, 0.f);
         }
       }
       __syncthreads();
       for (int t = tid; t < 6 * 27; t += nt) {
-        double* col = &S.F[t / 27][t % 27];
+        dfloat* col = &S.F[t / 27][t % 27];
         for (int a = 0; a < kNE; ++a) {
           if (!((sm >> a) & 1u)) continue;
           const int np = c_parents.n[a];
-          const double v = col[a * 27] * (1.0 / np);
+          const float sc = 1.f / (float)np;
+          const dfloat v(col[a * 27].hi * sc, col[a * 27].lo * sc);
           for (int q = 0; q < np; ++q) col[c_parents.p[a][q] * 27] += v;
-          col[a * 27] = 0.0;
+          col[a * 27] = dfloat(0.f, 0.f);
         }
       }
       __syncthreads();
@@ -631,11 +631,11 @@ __global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int 
       while ((R + 1) * kD - (R + 1) * R / 2 <= u) ++R;
       const int C = R + u - (R * kD - R * (R - 1) / 2);
       const int a = R / 3, i = R % 3, b = C / 3, j = C % 3;
-      const double fij = i <= j ? S.F[sf_pair(i, j)][a * 27 + b] : S.F[sf_pair(j, i)][b * 27 + a];
-      const double fji = j <= i ? S.F[sf_pair(j, i)][a * 27 + b] : S.F[sf_pair(i, j)][b * 27 + a];
-      double v = lam * fij + mu * fji;
-      if (i == j) v += mu * (S.F[0][a * 27 + b] + S.F[1][a * 27 + b] + S.F[2][a * 27 + b]);
-      v *= hh;
+      const dfloat fij = i <= j ? S.F[sf_pair(i, j)][a * 27 + b] : S.F[sf_pair(j, i)][b * 27 + a];
+      const dfloat fji = j <= i ? S.F[sf_pair(j, i)][a * 27 + b] : S.F[sf_pair(i, j)][b * 27 + a];
+      dfloat vp = lamd * fij + mud * fji;
+      if (i == j) vp += mud * (S.F[0][a * 27 + b] + S.F[1][a * 27 + b] + S.F[2][a * 27 + b]);
+      const double v = (double)(hhd * vp);
       if (sym) {
         out[u] = v;
       } else {
