@@ -58,8 +58,8 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 NCU_TRAFFIC = {
     ("k_apply_diag<double>", "982cb0288947", "cantilever_mr_96x48x48_q1_48x24x24_n2"):
         60361728 + 10240,  # the same tile body captured as k_cg_apply (FP64 variant)
-    ("k_tc2_apply", "f16x3", "bca1cfb26e18", "bridge_mixed_q1q2_64x32x32_n3_density_192x96x96"):
-        22499328 + 3189504,
+    ("k_tc2_apply", "f16x3", "de6bb3451308", "bridge_mixed_q1q2_64x32x32_n3_density_192x96x96"):
+        22769920 + 3585536,
 }
 
 
