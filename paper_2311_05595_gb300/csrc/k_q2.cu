@@ -488,7 +488,7 @@ __constant__ ParentTab c_parents = make_parent_tab();
 // compensated dot products (Dot2) of FP32 coefficients with float pairs;
 // the slaved-node congruence (weights 1/2, 1/4, 1/8: exact scalings) and
 // the assembly with lambda, mu and h/2 follow in float-pair arithmetic,
-// each entry rounded to FP64 once.  Block of 256 threads per element.
+// each entry rounded to FP64 once.  Block of 512 threads per element.
 constexpr int kSfMaxN = 64;
 struct SfSmem {
   float cf[4][kP][9];           // c_tau(p)[x * 3 + y], tau = 2 m + n (exact)
@@ -505,7 +505,7 @@ __device__ __forceinline__ int sf_pair(int s, int t) {  // s <= t: 00 11 22 01 0
   return s == t ? s : (s == 0 ? (t == 1 ? 3 : 4) : 5);
 }
 
-__global__ void __launch_bounds__(256) k_q2_elem_sf(int ex, int ey, long E, int N, double h, double nu,
+__global__ void __launch_bounds__(512) k_q2_elem_sf(int ex, int ey, long E, int N, double h, double nu,
                                                    const double* __restrict__ w, int Dx, int Dy,
                                                    const int* __restrict__ list, const uint8_t* __restrict__ slv,
                                                    int Lx, int Ly, int sym, double* __restrict__ Ke) {
@@ -1895,10 +1895,10 @@ void launch_q2_elem_sf(const Level& L, const double* w, int Dx, int Dy, double n
   std::call_once(attr, [sm] {
     cudaFuncSetAttribute(k_q2_elem_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   });
-  long g = (long)L.sms * 3;  // three 70 KB blocks per SM
+  long g = (long)L.sms * 3;  // three 70 KB blocks of 512 threads per SM
   if (g > E) g = E;
   if (g < 1) g = 1;
-  k_q2_elem_sf<<<(int)g, 256, sm, st>>>(L.ex, L.ey, E, L.nsub, L.h, nu, w, Dx, Dy, list, slv, L.Lx, L.Ly,
+  k_q2_elem_sf<<<(int)g, 512, sm, st>>>(L.ex, L.ey, E, L.nsub, L.h, nu, w, Dx, Dy, list, slv, L.Lx, L.Ly,
                                         L.sym ? 1 : 0, Ke);
 }
 

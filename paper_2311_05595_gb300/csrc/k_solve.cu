@@ -187,8 +187,10 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
   using PT = partial_t<T>;
   constexpr uint32_t kBytes = tile_bytes<T>();
   constexpr bool kSplit = tile_threads<T>() > kTileThreads;
-  __shared__ PT parts[3][kTileThreads / 3];
-  __shared__ PT tail[kSplit ? kTN : 1];  // second half of the (g 2, row 2) partial
+  // partials double-buffered by tile parity: the combine of tile k (warps of
+  // plane 0) overlaps the other warps' start on tile k + 1
+  __shared__ PT parts[2][3][kTileThreads / 3];
+  __shared__ PT tail[2][kSplit ? kTN : 1];  // second half of the (g 2, row 2) partial
   O* sbuf = reinterpret_cast<O*>(tsm);
   uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + (size_t)kStages * kBytes);
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -213,17 +215,24 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
   long k = 0;
   for (; k < nk; ++k) {
     const int s = (int)(k % kStages);
+    // every thread waits (bounded) for the tile; a timeout is agreed on at
+    // the barrier below, so a warp that finished combining the previous
+    // tile does not hold the others back
     const bool got = tile_wait(&bars[s], (uint32_t)((k / kStages) & 1));
-    if (__syncthreads_or(!got)) break;
     const long node = tile_at(blockIdx.x + k * gridDim.x) * kTN + lane;
     const bool live = node < V.nn;
     const int i = node % V.Lx, j = (node / V.Lx) % V.Ly, l = node / ((long)V.Lx * V.Ly);
+    const int pb = (int)(k & 1);
     if (live) {
       const PT part = plane_row(V, sbuf + (size_t)s * 243 * kTN + lane, node, i, j, l, r, g, ld, qlo, qhi);
-      if (extra) tail[lane] = part;
-      else parts[g][rl] = part;
+      if (extra) tail[pb][lane] = part;
+      else parts[pb][g][rl] = part;
     }
-    __syncthreads();  // stage s is free; the three parts are in
+    // stage s is free; the three parts are in (a timed-out tile's are never
+    // combined).  Buffer pb is written again by tile k + 2, after the next
+    // tile's barrier, which the combining warps reach only once they have
+    // read it.
+    if (__syncthreads_or(!got)) break;
     if (tid == 0 && k + kStages < nk) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tile_issue(tsm + (size_t)s * kBytes,
@@ -231,13 +240,12 @@ __device__ __forceinline__ void for_each_row(const LevelView<T>& V, LD ld, ROW r
     }
     if (g == 0 && !extra && live) {
       if constexpr (kSplit) {
-        const PT p2 = r == 2 ? parts[2][rl] + tail[lane] : parts[2][rl];
-        row(node, r, sum3(parts[0][rl], parts[1][rl], p2));
+        const PT p2 = r == 2 ? parts[pb][2][rl] + tail[pb][lane] : parts[pb][2][rl];
+        row(node, r, sum3(parts[pb][0][rl], parts[pb][1][rl], p2));
       } else {
-        row(node, r, sum3(parts[0][rl], parts[1][rl], parts[2][rl]));
+        row(node, r, sum3(parts[pb][0][rl], parts[pb][1][rl], parts[pb][2][rl]));
       }
     }
-    __syncthreads();  // parts are free
   }
   if (k < nk && tid == 0) {  // timed out: flag, then let the copies in flight land
     atomicExch(V.err, 1);
