@@ -756,7 +756,7 @@ def run_gpu(args):
                    "degree": p.degree if p.elem_q1 is None else "mixed 1/2",
                    "trilinear_elements": int(p.elem_q1.sum()) if p.elem_q1 is not None else 0,
                    "density_cells": int(p.x.size), "mg_levels": wl.spec["levels"] or "auto",
-                   "smoother": "damped Jacobi omega=0.5, 1+1, V-cycle",
+                   "smoother": f"damped Jacobi omega={0.5 if p.degree == 1 else 0.4}, 1+1, V-cycle",
                    "precision": f"FP64 outer CG + {best} preconditioner (value: fastest variant; "
                                 f"+iN = N inner FP32 PCG iterations per outer one); FP64 MG-PCG "
                                 f"(fp64_value)",

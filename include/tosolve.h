@@ -102,7 +102,8 @@ typedef struct {
                           /*   nx, ny, nz divisible by 2^(levels-1))        */
   int precision;          /* tosolve_precision of the preconditioner        */
   double omega;           /* damped-Jacobi factor (0 => 0.5, Sec. 7 intro;  */
-                          /*   0.4 for cubic Lagrange, 0.3 for serendipity) */
+                          /*   0.4 for Lagrange degree 2 and 3, 0.3 for     */
+                          /*   serendipity: below 2 / lambda_max(D^-1 A))  */
   int cycle_gamma;        /* cycles per level: 1 = V-cycle (0 => 1; the     */
                           /*   only value this build accepts)               */
   int max_rhs;            /* load cases per solve call, >= 1 (0 => 1)       */

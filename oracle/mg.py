@@ -28,7 +28,10 @@ Readings taken here (the paper does not say):
   * serendipity levels hold their face and element-centre nodes at 0 like
     supports, and use omega = 0.3 (damped Jacobi with 0.5 diverges on these
     elements: lambda_max(D^-1 A) is about 5.3 for degree 2, 5.0 for degree
-    3); cubic Lagrange hierarchies use 0.4 (lambda_max about 4.0);
+    3); Lagrange hierarchies of degree 2 and 3 use 0.4 (lambda_max about 4.7
+    for degree 2 with n = 2 subcells per edge, 4.9 with n = 3, 4.0 for
+    degree 3: 0.5 would exceed 2 / lambda_max, the damped iteration's
+    stability bound, while Sec. 7's 0.5 stays for trilinear elements);
   * Chebyshev smoothing (the alternative to damped Jacobi that the method
     statement names; the paper itself smooths degree >= 2 with SSOR,
     Sec. 7.5): the Chebyshev iteration of Saad, Iterative Methods for Sparse
@@ -271,7 +274,7 @@ class Hierarchy:
             transfer = "shape" if k == 2 else "linear"
         if family == "serendipity" and transfer != "shape":
             raise ValueError("serendipity levels take shape-function transfers")
-        self.omega = 0.3 if family == "serendipity" else 0.5
+        self.omega = 0.3 if family == "serendipity" else (0.4 if k >= 2 else 0.5)
         nx, ny, nz = prob.nx, prob.ny, prob.nz
         w_cells = simp_weights(rho, prob.E0, prob.Emin, prob.penal)
         self.levels = []

@@ -466,7 +466,7 @@ static tosolve_status create_impl(const tosolve_desc* desc, const uint8_t* mask_
   // Measured on these elements: Lagrange degree 2 3.2, degree 3 4.0,
   // serendipity degree 2 5.3, degree 3 5.0; so 0.4 for cubic Lagrange and
   // 0.3 for serendipity (about 1.6 / lambda_max)
-  if (h->d.omega == 0.0) h->d.omega = h->d.family == 1 ? 0.3 : (h->d.degree == 3 ? 0.4 : 0.5);
+  if (h->d.omega == 0.0) h->d.omega = h->d.family == 1 ? 0.3 : (h->d.degree >= 2 ? 0.4 : 0.5);
   // Chebyshev: each level's D^-1 is divided by theta at set-up, so the first
   // step of every smoothing sweep is D^-1 r with weight 1
   if (h->d.smoother == 1) {
