@@ -262,7 +262,7 @@ TC_PRECS = ("tf32", "bf16", "bf16x3", "f16x3")
 # one is reported).  Longer inner FP32 iterations trade outer FP64 iterations
 # (one FP64 operator apply each) for V-cycles: on the mixed bridge 16 inner
 # iterations take 5 outer ones, 24 and 28 take 3.
-DEFAULT_VARIANTS = {"bridge_mixed": "f16x3+i24,f16x3+i28,f16x3+i16,bf16x3+i16,bf16+i8,fp32",
+DEFAULT_VARIANTS = {"bridge_mixed": "f16x3+i24,bf16+i12,f16x3+i28,f16x3+i16,bf16x3+i16,fp32",
                     "bridge_q2": "f16x3+i16,bf16x3+i16,bf16+i8,fp32",
                     "cantilever": "fp32,tf32,fp32x2"}
 
