@@ -60,6 +60,8 @@ NCU_TRAFFIC = {
         60361728 + 10240,  # the same tile body captured as k_cg_apply (FP64 variant)
     ("k_tc2_apply", "f16x3", "de6bb3451308", "bridge_mixed_q1q2_64x32x32_n3_density_192x96x96"):
         22769920 + 3585536,
+    ("k_tc2_apply", "bf16", "de6bb3451308", "bridge_mixed_q1q2_64x32x32_n3_density_192x96x96"):
+        16186112 + 3863296,
 }
 
 
