@@ -271,11 +271,13 @@ def test_tc2_mixed_matches_direct_solve(prec, inner):
     R.close()
 
 
-def test_tc2_mixed_bridge_full_size():
+@pytest.mark.parametrize("prec,inner", [(F16X3, 16), (BF16, 12), (F16X3, 24)])
+def test_tc2_mixed_bridge_full_size(prec, inner):
     """The bridge as specified (64x32x32, n = 3, a seeded half trilinear;
-    519,204 unknowns) with the benchmark's F16X3 preconditioner and inner
-    FP32 iterations: solve to 1e-8, operator rows, compliance and gradient
-    checked on samples."""
+    519,204 unknowns) with the benchmark's tensor-core preconditioners
+    (BF16 with 12 inner FP32 iterations per outer one, F16X3 with 16 and
+    24): solve to 1e-8, operator rows, compliance and gradient checked on
+    samples."""
     from paper_2311_05595_gb300 import tosolve as T
     from tests.test_gpu_fullsize import _check_sampled
 
@@ -283,7 +285,7 @@ def test_tc2_mixed_bridge_full_size():
     R = Run(p, FP32)
     R.close()
     R.solver = T.Solver(T.make_desc(p.nx, p.ny, p.nz, degree=2, n_mr=3, nu=p.nu, penal=p.penal, Emin=p.Emin,
-                                    mg_levels=0, precision=F16X3, inner_its=16),
+                                    mg_levels=0, precision=prec, inner_its=inner),
                         p.mask, R.stream, elem_q1=p.elem_q1)
     R.h = R.solver.h
     R.set_densities()
