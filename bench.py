@@ -734,7 +734,7 @@ def run_gpu(args):
     h2d = (p.x.size + p.f.size) * 8
     d2h = (p.f.size + p.x.size + 1) * 8
 
-    # ---- dominant kernel ----
+    # ---- roofline: the tensor-core contraction on degree 2, else the FP64 operator ----
     name, inner = parse_variant(best)
     roof = tc_roofline(wl, best) if name in TC_PRECS and p.degree == 2 else fp64_roofline(wl)
 
