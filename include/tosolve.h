@@ -68,7 +68,8 @@ typedef enum {
                          /* stacked subcell contraction of Eq. matrixK_mr on */
                          /* the tcgen05 tensor cores (TF32 operands, FP32    */
                          /* accumulation in TMEM); degree 1 with n_mr <= 2,  */
-                         /* or Lagrange degree 2 with n_mr <= 3 (not mixed)  */
+                         /* or Lagrange degree 2 with n_mr <= 3, mixed       */
+                         /* trilinear/triquadratic meshes included           */
   TOSOLVE_PREC_FP32X2 = 3, /* FP32 V-cycle operators (formed in FP64, then   */
                          /* rounded) and vectors held as float pairs: about */
                          /* 48-bit arithmetic on the FP32 pipes, for        */
@@ -76,7 +77,7 @@ typedef enum {
                          /* convergence                                     */
   TOSOLVE_PREC_BF16 = 4, /* as TF32 with BF16 operands (8-bit mantissas) and */
                          /* FP32 accumulation: Lagrange degree 2 with       */
-                         /* n_mr <= 3 (not mixed)                           */
+                         /* n_mr <= 3, mixed meshes included                */
   TOSOLVE_PREC_BF16X3 = 5, /* degree 2 as BF16, each operand split into a   */
                          /* BF16 pair (hi + lo, about 16 bits) and three    */
                          /* products hi hi + lo hi + hi lo                  */
