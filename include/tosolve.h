@@ -169,17 +169,18 @@ tosolve_status tosolve_create(const tosolve_desc* desc, const uint8_t* mask_host
                               void* cuda_stream, tosolve_t* out);
 
 /* A mesh that mixes trilinear and triquadratic elements on the degree-2
- * lattice (desc->degree = 2).  elem_q1_host: nx*ny*nz bytes (x fastest),
- * 1 = trilinear element.  Every element carries the triquadratic matrix of
- * Eq. matrixK_mr; a lattice node that is not an element vertex and touches
- * a trilinear element is slaved to the linear interpolation of the vertices
- * of its edge, face or cell (the coupling is conforming and a trilinear
- * element keeps exactly its trilinear matrix; the paper raises the degree
- * of the whole mesh, Sec. 7.4, and does not spell a mixed coupling out).
- * The solve is on u = T u_r with T^T K T u_r = T^T f; u_dev returns the
- * expanded field, loads f_dev are the degree-2 consistent loads on the whole
- * lattice, compliance and gradient use the expanded u.  Otherwise as
- * tosolve_create (TF32 is not available).  Errors: EINVAL, ENOMEM, ECUDA. */
+ * lattice (desc->degree = 2, family 0).  elem_q1_host: nx*ny*nz bytes (x
+ * fastest), 1 = trilinear element.  A triquadratic element carries its
+ * matrix of Eq. matrixK_mr, a trilinear element its trilinear 24 x 24
+ * matrix on its 8 vertices; a lattice node that is not an element vertex
+ * and touches a trilinear element is slaved to the linear interpolation of
+ * the vertices of its edge, face or cell (the coupling is conforming; the
+ * paper raises the degree of the whole mesh, Sec. 7.4, and does not spell a
+ * mixed coupling out).  The solve is on u = T u_r with T^T K T u_r = T^T f;
+ * u_dev returns the expanded field, loads f_dev are the degree-2 consistent
+ * loads on the whole lattice, compliance and gradient use the expanded u.
+ * Otherwise as tosolve_create, every precision included.  Errors: EINVAL,
+ * ENOMEM, ECUDA. */
 tosolve_status tosolve_create_mixed(const tosolve_desc* desc, const uint8_t* mask_host,
                                     const uint8_t* elem_q1_host, void* cuda_stream, tosolve_t* out);
 
